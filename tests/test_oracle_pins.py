@@ -1,0 +1,412 @@
+"""Pins for the FP64 CPU oracle (no GPU).
+
+Each check compares the oracle with something other than itself:
+  * LAPACK (numpy.linalg) for the dense Cholesky and dense solves,
+  * hand-derived fixtures under tests/golden/ (each with its citation),
+  * closed forms (Toeplitz kron I spectrum; scalar Thomas recurrence),
+  * structural facts of the multi-stage permutation (fill pattern, counts),
+  * invariants (log-det of every ordering, uniqueness of the Cholesky factor).
+
+The mutation tests at the end plant plausible mistakes (transposed operand,
+dropped term, wrong sign, wrong stride) in a copy of the oracle's C source and
+check that at least one pin fails for each.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_03754_gb300 import gen
+
+
+# ---------------------------------------------------------------- helpers ---
+
+def permuted_dense(A, order, n):
+    idx = np.concatenate([np.arange(o * n, (o + 1) * n) for o in order])
+    return A[np.ix_(idx, idx)]
+
+
+def predicted_nd_pairs(N):
+    """Off-diagonal blocks of the P_inf factor, predicted from Sec. 4.3:
+    at level l (stride s = 2^(l-1)) the surviving nodes s, 2s, 3s, ... couple
+    pairwise as (k s, (k+1) s), k = 1 .. floor(N/s) - 1 (1-based). In the factor
+    the nonzero block sits in the column of whichever of the two is eliminated
+    at that level (the odd multiple of s). Returned as 0-based (row, col)."""
+    out = set()
+    s = 1
+    while s <= N:
+        for k in range(1, N // s):
+            a, b = k * s, (k + 1) * s
+            col, row = (a, b) if k % 2 == 1 else (b, a)
+            out.add((row - 1, col - 1))
+        s *= 2
+    return out
+
+
+def thomas(d, e, rhs):
+    """Scalar symmetric tridiagonal solve T_N(d, e) y = rhs (textbook recurrence)."""
+    N = len(rhs)
+    c = np.zeros(N)
+    g = np.zeros(N)
+    c[0] = e / d
+    g[0] = rhs[0] / d
+    for i in range(1, N):
+        den = d - e * c[i - 1]
+        c[i] = e / den
+        g[i] = (rhs[i] - e * g[i - 1]) / den
+    y = np.zeros(N)
+    y[-1] = g[-1]
+    for i in range(N - 2, -1, -1):
+        y[i] = g[i] - c[i] * y[i + 1]
+    return y
+
+
+# ------------------------------------------------------------ pin checks ---
+# Each returns None on success and raises AssertionError (or an oracle error) otherwise.
+
+def check_chol_vs_lapack(seed=0):
+    rng = np.random.default_rng(seed)
+    for n in (1, 2, 3, 7, 16):
+        M = rng.standard_normal((n, n))
+        A = M @ M.T + n * np.eye(n)
+        np.testing.assert_allclose(oracle.chol(A), np.linalg.cholesky(A), rtol=1e-13, atol=1e-13)
+
+
+def check_seq_factor_vs_dense(N=6, n=3, seed=1):
+    D, B = gen.bt_random(N, n, delta=0.5, seed=seed)
+    Dh, Eh = oracle.seq_factor(D, B)
+    A = oracle.assemble(D, B)
+    Lref = np.linalg.cholesky(A)
+    for i in range(N):
+        np.testing.assert_allclose(Dh[i], Lref[i * n:(i + 1) * n, i * n:(i + 1) * n], rtol=1e-12, atol=1e-12)
+    for i in range(N - 1):
+        np.testing.assert_allclose(Eh[i], Lref[(i + 1) * n:(i + 2) * n, i * n:(i + 1) * n], rtol=1e-12,
+                                   atol=1e-12)
+
+
+def check_seq_solve_vs_lapack(N=5, n=3, m=2, seed=2):
+    D, B = gen.bt_random(N, n, delta=0.1, seed=seed)
+    b = gen.rhs(N, n, m, seed=seed)
+    x = oracle.solve(D, B, b)
+    A = oracle.assemble(D, B)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(x, oracle.gepp_solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+def check_nd_factor_vs_dense(N=11, n=2, seed=3):
+    D, B = gen.bt_random(N, n, delta=0.2, seed=seed)
+    order, Ld, pairs, Loff = oracle.nd_factor(D, B)
+    A = oracle.assemble(D, B)
+    L = np.linalg.cholesky(permuted_dense(A, order, n))
+    pos = np.empty(N, dtype=int)
+    pos[order] = np.arange(N)
+    for i in range(N):
+        p = pos[i]
+        np.testing.assert_allclose(Ld[i], L[p * n:(p + 1) * n, p * n:(p + 1) * n], rtol=1e-12, atol=1e-12)
+    seen = set()
+    for (r, c), blk in zip(pairs, Loff):
+        pr, pc = pos[r], pos[c]
+        assert pr > pc
+        np.testing.assert_allclose(blk, L[pr * n:(pr + 1) * n, pc * n:(pc + 1) * n], rtol=1e-11, atol=1e-12)
+        seen.add((pr, pc))
+    # every nonzero block of the dense factor is listed
+    for pr in range(N):
+        for pc in range(pr):
+            if np.abs(L[pr * n:(pr + 1) * n, pc * n:(pc + 1) * n]).max() > 1e-12:
+                assert (pr, pc) in seen
+
+
+def check_resid_vs_dense(N=4, n=3, m=2, seed=4):
+    D, B = gen.bt_random(N, n, delta=1.0, seed=seed)
+    # make the upper triangles of D garbage: only the lower triangle may be read
+    Dg = D.copy()
+    for i in range(N):
+        Dg[i][np.triu_indices(n, 1)] = 1e3
+    x = gen.rhs(N, n, m, seed=seed + 1)
+    b = gen.rhs(N, n, m, seed=seed + 2)
+    A = oracle.assemble(D, B)
+    r, a, xn = oracle.resid(Dg, B, x, b)
+    assert math.isclose(r, np.abs(b - A @ x).max(), rel_tol=1e-12)
+    assert math.isclose(a, np.abs(A).sum(axis=1).max(), rel_tol=1e-12)
+    assert math.isclose(xn, np.abs(x).max(), rel_tol=1e-15)
+
+
+def check_nd_order_golden(golden_dir):
+    with open(os.path.join(golden_dir, "nd_order_N20.json")) as f:
+        g = json.load(f)
+    order, levels = oracle.nd_order(g["N"])
+    assert list(order + 1) == g["order_1based"]
+    assert levels == g["levels"]
+
+
+def check_worked_example(golden_dir):
+    with open(os.path.join(golden_dir, "nd_worked_example_N3.json")) as f:
+        g = json.load(f)
+    D, B = np.array(g["D"]), np.array(g["B"])
+    order, Ld, pairs, Loff = oracle.nd_factor(D, B)
+    assert list(order) == g["order_0based"]
+    np.testing.assert_allclose(Ld, np.array(g["Ldiag"]), rtol=1e-15)
+    got = {(int(r), int(c)): blk for (r, c), blk in zip(pairs, Loff)}
+    assert len(got) == len(g["Loff"])
+    for e in g["Loff"]:
+        np.testing.assert_allclose(got[(e["row"], e["col"])], np.array(e["value"]), rtol=1e-15)
+    assert math.isclose(math.exp(oracle.logdet_from_diag(Ld)), g["det"], rel_tol=1e-14)
+    x = oracle.solve(D, B, np.array(g["b"]))
+    np.testing.assert_allclose(x, np.array(g["x"]), atol=1e-15)
+
+
+def check_toeplitz_closed_form(N=13, n=2, d=3.0, e=1.2):
+    D, B = gen.toeplitz_kron(N, n, d, e)
+    k = np.arange(1, N + 1)
+    logdet = n * np.log(d + 2 * e * np.cos(k * np.pi / (N + 1))).sum()
+    Dh, _ = oracle.seq_factor(D, B)
+    assert math.isclose(oracle.logdet_from_diag(Dh), logdet, rel_tol=1e-13)
+    _, Ld, _, _ = oracle.nd_factor(D, B)
+    assert math.isclose(oracle.logdet_from_diag(Ld), logdet, rel_tol=1e-13)
+    rhs = gen.rhs(N, n, 1, seed=5)[:, 0]
+    x = oracle.solve(D, B, rhs)
+    for comp in range(n):
+        np.testing.assert_allclose(x[comp::n], thomas(d, e, rhs[comp::n]), rtol=1e-12, atol=1e-13)
+
+
+# ------------------------------------------------------------ the tests ---
+
+def test_chol_matches_lapack():
+    check_chol_vs_lapack()
+
+
+def test_chol_reports_first_bad_pivot():
+    A = np.array([[4.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 1.0]])  # second pivot 1 - 1 = 0
+    with pytest.raises(oracle.NotSPD) as ei:
+        oracle.chol(A)
+    assert ei.value.info == 2
+
+
+def test_gepp_matches_lapack_and_pivots():
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((9, 9))
+    A[0, 0] = 0.0  # forces a row exchange at step 1
+    b = rng.standard_normal((9, 3))
+    np.testing.assert_allclose(oracle.gepp_solve(A, b), np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+def test_dense_chol_matches_lapack():
+    D, B = gen.bt_random(4, 3, seed=9)
+    A = oracle.assemble(D, B)
+    np.testing.assert_allclose(oracle.dense_chol(A), np.linalg.cholesky(A), rtol=1e-12, atol=1e-13)
+
+
+def test_assemble_is_symmetric_block_tridiagonal():
+    D, B = gen.bt_random(5, 2, seed=10)
+    A = oracle.assemble(D, B)
+    np.testing.assert_array_equal(A, A.T)
+    np.testing.assert_array_equal(A[2:4, 0:2], B[0])
+    assert np.all(A[4:6, 0:2] == 0)
+
+
+@pytest.mark.parametrize("N,n", [(1, 3), (2, 2), (6, 3), (8, 1)])
+def test_seq_factor_equals_dense_cholesky(N, n):
+    check_seq_factor_vs_dense(N, n)
+
+
+@pytest.mark.parametrize("N,n,m", [(1, 4, 1), (5, 3, 2), (8, 2, 3)])
+def test_seq_solve_equals_lapack_and_gepp(N, n, m):
+    check_seq_solve_vs_lapack(N, n, m)
+
+
+def test_resid_matches_dense():
+    check_resid_vs_dense()
+
+
+def test_nd_order_matches_hand_written_N20(golden_dir):
+    check_nd_order_golden(golden_dir)
+
+
+@pytest.mark.parametrize("N", list(range(1, 65)))
+def test_nd_order_is_a_permutation_with_floor_log2_plus_1_levels(N):
+    order, levels = oracle.nd_order(N)
+    assert sorted(order) == list(range(N))
+    assert levels == int(math.floor(math.log2(N))) + 1
+
+
+def test_worked_example_N3(golden_dir):
+    check_worked_example(golden_dir)
+
+
+@pytest.mark.parametrize("N,n", [(3, 1), (7, 2), (11, 2), (16, 3), (21, 2)])
+def test_nd_factor_equals_dense_cholesky_of_permuted(N, n):
+    check_nd_factor_vs_dense(N, n, seed=N)
+
+
+@pytest.mark.parametrize("N", list(range(1, 65)))
+def test_nd_fill_pattern_matches_prediction(N):
+    D, B = gen.bt_random(N, 1, seed=N)
+    order, Ld, pairs, Loff = oracle.nd_factor(D, B)
+    got = {(int(r), int(c)) for r, c in pairs}
+    pred = predicted_nd_pairs(N)
+    assert got == pred
+    # counts: off-diagonal blocks = sum over levels (floor(N/s) - 1); fill = that - (N - 1)
+    etot = sum(N // (2 ** l) - 1 for l in range(int(math.log2(N)) + 1))
+    assert len(got) == etot
+    if N & (N - 1) == 0:  # N = 2^k: fill = N - log2(N) - 1
+        assert etot - (N - 1) == N - int(math.log2(N)) - 1
+
+
+def test_identity_order_reproduces_alg1():
+    D, B = gen.bt_random(9, 3, seed=11)
+    Ld, pairs, Loff = oracle.bs_chol(D, B, np.arange(9))
+    Dh, Eh = oracle.seq_factor(D, B)
+    np.testing.assert_allclose(Ld, Dh, rtol=1e-13, atol=1e-14)
+    assert sorted((int(r), int(c)) for r, c in pairs) == [(i + 1, i) for i in range(8)]
+    for (r, c), blk in zip(pairs, Loff):
+        np.testing.assert_allclose(blk, Eh[c], rtol=1e-13, atol=1e-14)
+
+
+def test_logdet_is_order_invariant():
+    D, B = gen.bt_random(13, 3, delta=0.05, seed=12)
+    sign, ref = np.linalg.slogdet(oracle.assemble(D, B))
+    assert sign > 0
+    Dh, _ = oracle.seq_factor(D, B)
+    _, Ld, _, _ = oracle.nd_factor(D, B)
+    rng = np.random.default_rng(0)
+    Lr, _, _ = oracle.bs_chol(D, B, rng.permutation(13))
+    for L in (Dh, Ld, Lr):
+        assert math.isclose(oracle.logdet_from_diag(L), ref, rel_tol=1e-12)
+
+
+def test_toeplitz_closed_form():
+    check_toeplitz_closed_form()
+
+
+def test_zero_coupling_gives_blockdiag_and_zero_fill():
+    D, B = gen.bt_random(12, 3, seed=13)
+    B[:] = 0.0
+    order, Ld, pairs, Loff = oracle.nd_factor(D, B)
+    for i in range(12):
+        np.testing.assert_allclose(Ld[i], np.linalg.cholesky(D[i]), rtol=1e-13)
+    assert np.all(Loff == 0.0)
+
+
+def test_N2_nd_equals_natural_order():
+    D, B = gen.bt_random(2, 4, seed=14)
+    order, Ld, pairs, Loff = oracle.nd_factor(D, B)
+    assert list(order) == [0, 1]
+    Dh, Eh = oracle.seq_factor(D, B)
+    np.testing.assert_array_equal(Ld, Dh)
+    np.testing.assert_array_equal(Loff[0], Eh[0])
+
+
+def test_reconstruction_identity_and_its_sensitivity():
+    D, B = gen.bt_random(17, 3, delta=0.1, seed=15)
+    order, Ld, pairs, Loff = oracle.nd_factor(D, B)
+    assert oracle.bs_reconstruct(D, B, order, Ld, pairs, Loff) < 1e-14
+    bad = Loff.copy()
+    bad[3] = bad[3].T
+    assert oracle.bs_reconstruct(D, B, order, Ld, pairs, bad) > 1e-6
+
+
+def test_nd_and_sequential_solutions_agree():
+    N, n = 33, 3
+    D, B = gen.bt_random(N, n, delta=0.01, seed=16)
+    b = gen.rhs(N, n, 2, seed=16)
+    x_seq = oracle.solve(D, B, b)
+    # solve with the ND factor: P^T L L^T P x = b, dense on this small case
+    order, Ld, pairs, Loff = oracle.nd_factor(D, B)
+    M = N * n
+    pos = np.empty(N, dtype=int)
+    pos[order] = np.arange(N)
+    L = np.zeros((M, M))
+    for i in range(N):
+        p = pos[i]
+        L[p * n:(p + 1) * n, p * n:(p + 1) * n] = Ld[i]
+    for (r, c), blk in zip(pairs, Loff):
+        L[pos[r] * n:(pos[r] + 1) * n, pos[c] * n:(pos[c] + 1) * n] = blk
+    idx = np.concatenate([np.arange(o * n, (o + 1) * n) for o in order])
+    y = np.linalg.solve(L, b[idx])
+    z = np.linalg.solve(L.T, y)
+    x_nd = np.empty_like(z)
+    x_nd[idx] = z
+    np.testing.assert_allclose(x_nd, x_seq, rtol=1e-9, atol=1e-11)
+    assert oracle.relres(D, B, x_seq, b) < 1e-15
+
+
+def test_generator_is_spd_with_eigenvalues_above_delta():
+    for delta in (1.0, 1e-2):
+        D, B = gen.bt_random(10, 4, delta=delta, seed=17)
+        w = np.linalg.eigvalsh(oracle.assemble(D, B))
+        assert w.min() >= delta * (1 - 1e-9)
+
+
+def test_mpc_generator_is_G_Gt_of_the_dynamics():
+    """The MPC blocks equal G G^T for the constraint matrix G of
+    x_{k+1} - A_k x_k - Bu_k u_k = 0 (variables x_1..x_N, u_0..u_{N-1}), built here
+    column by column; G has full row rank, so Psi is SPD."""
+    N, n = 7, 4
+    D, B, A, Bu = gen.mpc(N, n, seed=18, return_parts=True)
+    h = n // 2
+    G = np.zeros((N * n, N * n + N * h))
+    xcol = lambda k: slice((k - 1) * n, k * n)  # x_k, k = 1..N
+    ucol = lambda k: slice(N * n + k * h, N * n + (k + 1) * h)  # u_k, k = 0..N-1
+    for k in range(N):
+        rows = slice(k * n, (k + 1) * n)
+        G[rows, xcol(k + 1)] = np.eye(n)
+        if k >= 1:
+            G[rows, xcol(k)] = -A[k]
+        G[rows, ucol(k)] = -Bu[k]
+    np.testing.assert_allclose(oracle.assemble(D, B), G @ G.T, rtol=1e-13, atol=1e-14)
+    assert np.linalg.eigvalsh(G @ G.T).min() > 0
+    assert np.allclose(np.abs(np.linalg.eigvals(A)).max(axis=1), 0.95)
+
+
+# -------------------------------------------------------- mutation tests ---
+
+MUTATIONS = [
+    # (tag, original text, planted mistake, which pin must catch it)
+    ("chol_transposed_index", "v -= L[i * ldl + k] * L[j * ldl + k];", "v -= L[i * ldl + k] * L[k * ldl + j];",
+     "chol"),
+    ("trsm_transposed_operand", "for (int k = 0; k < j; ++k) v -= x[k] * L[j * n + k];",
+     "for (int k = 0; k < j; ++k) v -= x[k] * L[k * n + j];", "seq"),
+    ("syrk_dropped", "    gemm_nt_sub(n, Ehat + (i - 1) * bs, Ehat + (i - 1) * bs, S);\n", "\n", "seq"),
+    ("gemm_transposed_operand", "v += A[i * n + k] * B[j * n + k];", "v += A[i * n + k] * B[k * n + j];", "seq"),
+    ("backsolve_transposed", "for (int k = 0; k < n; ++k) v += E[k * n + r] * xn[k * m + c];",
+     "for (int k = 0; k < n; ++k) v += E[r * n + k] * xn[k * m + c];", "solve"),
+    ("bs_scatter_orientation", "blk[r * n + c] = p > q ? B[i * bs + r * n + c] : B[i * bs + c * n + r];",
+     "blk[r * n + c] = B[i * bs + r * n + c];", "nd"),
+    ("bs_update_wrong_sign", "gemm_nt_sub(n, T[(size_t)i * N + k], T[(size_t)j * N + k], *slot);",
+     "gemm_nt_sub(n, T[(size_t)j * N + k], T[(size_t)i * N + k], *slot);", "nd"),
+    ("nd_order_stride", "for (long i = s; i <= N; i += 2 * s)", "for (long i = s; i <= N; i += s + 1)", "order"),
+    ("resid_sign", "v -= B[(i - 1) * bs + r * n + c] * x[((size_t)(i - 1) * n + c) * m + col];",
+     "v += B[(i - 1) * bs + r * n + c] * x[((size_t)(i - 1) * n + c) * m + col];", "resid"),
+    ("resid_upper_transposed", "v -= B[i * bs + c * n + r] * x[((size_t)(i + 1) * n + c) * m + col];",
+     "v -= B[i * bs + r * n + c] * x[((size_t)(i + 1) * n + c) * m + col];", "resid"),
+]
+
+
+def _run_pins(which, golden_dir):
+    if which == "chol":
+        check_chol_vs_lapack()
+    elif which == "seq":
+        check_seq_factor_vs_dense()
+        check_seq_solve_vs_lapack()
+    elif which == "solve":
+        check_seq_solve_vs_lapack()
+    elif which == "nd":
+        check_nd_factor_vs_dense()
+        check_worked_example(golden_dir)
+    elif which == "order":
+        check_nd_order_golden(golden_dir)
+    elif which == "resid":
+        check_resid_vs_dense()
+
+
+@pytest.mark.parametrize("tag,old,new,which", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tag, old, new, which, golden_dir):
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation anchor for {tag} not found exactly once"
+    _run_pins(which, golden_dir)  # the real oracle passes
+    with oracle.use_variant(src.replace(old, new), tag):
+        with pytest.raises((AssertionError, oracle.NotSPD, ZeroDivisionError, ValueError, IndexError)):
+            _run_pins(which, golden_dir)
