@@ -1,0 +1,349 @@
+"""Benchmark: factor + solve of one block-tridiagonal SPD system to relative
+residual <= 1e-10 on GB300, through the libbtc C ABI.
+
+Workload (default): N = 1024 blocks of n = 64, one right-hand side, seeded
+synthetic inputs (B_i ~ N(0, 1/n), D_i = M M^T/n + (||B_{i-1}||+||B_i||+1) I).
+A step = btc_factor (all dissection levels of Alg. 5) + btc_solve_refined
+(Alg. 7 solves with FP64 residuals until ||r|| <= 1e-10 ||A|| ||x||), in the
+chosen form: FP32 factor and correction solves, FP64 root Cholesky, residual
+and update. The plain FP64 GPU path (same kernels in FP64, no refinement
+needed) is timed beside it.
+
+Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+(sequential Alg. 1 factor + block substitution) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "factor+solve solves/s at resid<=1e-10 (N=1024, n=64, 1 RHS)"
+UNIT = "solves/s"
+WORKLOAD = dict(N=1024, n=64, nrhs=1, delta=1.0, seed=0)
+TOL = 1e-10
+FP32_PEAK_PER_SM_CLK = 128 * 2  # FFMA lanes x 2 flops
+FP64_PEAK_PER_SM_CLK = 2 * 2    # DFMA per clock per SM on GB300 x 2 flops
+SMS = 152
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("btc_factor.cuh", "btc_tile.cuh"):
+        with open(os.path.join(ROOT, "paper_2601_03754_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile():
+    """DRAM bytes per factor call from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "factor_level_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    if t.get("kernel_sha") != _kernel_hash():
+        return None
+    return t.get("dram_bytes_per_factor")
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores: a bounded sample of the same workload."""
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2601_03754_gb300 import gen
+    oracle.build()
+    W = WORKLOAD
+    D, B = gen.bt_random(W["N"], W["n"], delta=W["delta"], seed=W["seed"])
+    b = gen.rhs(W["N"], W["n"], W["nrhs"], seed=W["seed"])
+    for _ in range(max(args.warmup, 0) and 1):
+        oracle.solve(D, B, b)
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x = oracle.solve(D, B, b)
+        times.append(time.perf_counter() - t0)
+    total = time.perf_counter() - t_start
+    rel = oracle.relres(D, B, x, b)
+    ms = 1000.0 * statistics.mean(times)
+    value = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload="bt_random N=1024 n=64 m=1 delta=1, sequential Alg. 1 FP64 factor + solve",
+                           **W),
+            "relres": rel,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full factor+solve passes of the workload ({total:.1f} s)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(budget_s=12.0, max_reps=8):
+    import oracle
+    from paper_2601_03754_gb300 import gen
+    oracle.build()
+    W = WORKLOAD
+    D, B = gen.bt_random(W["N"], W["n"], delta=W["delta"], seed=W["seed"])
+    b = gen.rhs(W["N"], W["n"], W["nrhs"], seed=W["seed"])
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_reps and (time.perf_counter() - t_start) < budget_s:
+        t0 = time.perf_counter()
+        oracle.solve(D, B, b)
+        times.append(time.perf_counter() - t0)
+    v = 1.0 / statistics.mean(times)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full sequential FP64 factor+solve passes of N=1024, n=64 "
+                      f"({time.perf_counter() - t_start:.1f} s, single thread)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_03754_gb300 import btc, build, gen
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    btc.load()
+    W = WORKLOAD
+    N, n, m = W["N"], W["n"], W["nrhs"]
+    D, B = gen.bt_random(N, n, delta=W["delta"], seed=W["seed"] + rank)
+    b = gen.rhs(N, n, m, seed=W["seed"] + rank)
+    stream = torch.cuda.Stream()
+    Dd = torch.from_numpy(D).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def timed_steps(plan, steps, body):
+        """Per-step CUDA events on the plan's stream, L2 flushed before each step."""
+        ts = []
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out = body()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        return ts, out
+
+    # ---- chosen form: FP32 factor + FP64 refinement
+    pm = btc.btc_plan(N, n, btc.MIXED_F32, stream)
+    info = btc.btc_plan_query(pm)
+
+    def mixed_step():
+        btc.btc_factor(pm, Dd, Bd)
+        return btc.btc_solve_refined(pm, bd, xd, m, tol=TOL, maxit=30)
+
+    timed_steps(pm, args.warmup, mixed_step)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    ts, (iters, rel, rc) = timed_steps(pm, args.steps, mixed_step)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = statistics.mean(ts)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+    assert rel <= TOL, rel
+
+    # ---- phase split of the chosen form (same stream, same L2 flush), for the roofline
+    fact_ts, _ = timed_steps(pm, max(10, args.steps // 2), lambda: btc.btc_factor(pm, Dd, Bd))
+    t_fact = statistics.median(fact_ts)
+    # solve-only (one FP32 correction solve of an FP64 vector)
+    xs = bd.clone()
+    solve_ts, _ = timed_steps(pm, max(10, args.steps // 2), lambda: btc.btc_solve(pm, xs, m))
+    t_solve = statistics.median(solve_ts)
+
+    # ---- the plain FP64 GPU path on the same workload
+    p64 = btc.btc_plan(N, n, btc.F64, stream)
+
+    def f64_step():
+        btc.btc_factor(p64, Dd, Bd)
+        return btc.btc_solve_refined(p64, bd, xd, m, tol=TOL, maxit=30)
+
+    timed_steps(p64, 3, f64_step)
+    ts64, (it64, rel64, _) = timed_steps(p64, max(5, args.steps // 5), f64_step)
+    ms64 = statistics.mean(ts64)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    Dh = torch.from_numpy(D).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    pe = btc.btc_plan(N, n, btc.MIXED_F32, stream)
+    for _ in range(2):
+        btc.btc_factor_solve_host(pe, Dh, Bh, bh, xh, m, TOL, 30)
+    e2e_ts = []
+    for _ in range(max(5, args.steps // 5)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        btc.btc_factor_solve_host(pe, Dh, Bh, bh, xh, m, TOL, 30)
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_v = 1.0 / statistics.mean(e2e_ts)
+    h2d = D.nbytes + B.nbytes + b.nbytes
+    d2h = b.nbytes
+
+    peaks, pk_kind = _peaks()
+    sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_PEAK_PER_SM_CLK * sm_max * 1e6 / 1e12
+    achieved = info["factor_flops"] / (t_fact * 1e-3) / 1e12
+    traffic = _traffic_from_profile()
+    L = info["levels"]
+    # factor levels + ||A|| + first solve (pack, 2L levels, unpack) + per refinement step
+    # (2L levels + update) + one residual per check
+    launches = L + 1 + (2 * L + 2) + iters * (2 * L + 1) + (iters + 1)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (factor, solves) + f64 (root chol, residual, update)",
+        "data": "synthetic",
+        "config": {"workload": "bt_random N=1024 n=64 nrhs=1 delta=1 seed=0; mixed FP32 factor + FP64 refinement "
+                               "to relres<=1e-10", "N": N, "n": n, "nrhs": m, "delta": W["delta"],
+                   "l2": "flushed before every step (256 MB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}"},
+        "latency_us": {"p50": 1000 * statistics.median(ts),
+                       "p99": 1000 * float(np.percentile(np.asarray(ts), 99)), "mean": 1000 * ms},
+        "refine_iters": iters, "relres": rel,
+        "plain_f64": {"ms_per_step": ms64, "solves_per_s": 1000.0 / ms64, "refine_iters": it64, "relres": rel64,
+                      "p99_us": 1000 * float(np.percentile(np.asarray(ts64), 99))},
+        "speedup_vs_plain_f64": ms64 / ms,
+        "phases_ms": {"factor_mixed": t_fact, "one_solve_mixed": t_solve},
+        "roofline": {"kernel": "k_factor_level (all levels of one factorization)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": traffic,
+                     "peak_kind": f"FP32 FFMA: {SMS} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (derived)",
+                     "algorithmic": f"{info['factor_flops']:.4g} flop per factorization (Alg. 5, Table 1 costs)"},
+        "e2e": {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "entry_point": "btc_factor_solve_host (pinned host buffers)"},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+        "peaks_source": pk_kind,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * btc.h - C ABI of libbtc.so: nested-dissection Cholesky factorization and
+ * solve of symmetric positive-definite block-tridiagonal matrices on GB300.
+ *
+ * The matrix (Sec. 3 of arXiv 2601.03754, the block-tridiagonal Psi) has N
+ * diagonal blocks D_i and N-1 sub-diagonal blocks B_i = Psi(i+1, i), each
+ * n x n (the paper names the sub-diagonal blocks E_i). The library factors
+ * P Psi P^T = L L^T where P is the multi-stage permutation P_inf of Sec. 4.3
+ * (recursive odd/even, i.e. nested dissection): all eliminations of one
+ * dissection level are independent and run concurrently, over
+ * floor(log2 N) + 1 levels (Alg. 5, hybrid left/right-looking), and solves
+ * Psi x = b by level-wise forward and backward substitution (Alg. 7).
+ *
+ * Conventions for every entry point:
+ *  - Return value: BTC_OK (0) or a negative BTC_ERR_* code; btc_last_error()
+ *    then returns a message for the calling thread.
+ *  - Indices are 0-based; arrays are dense row-major.
+ *  - "device pointer" = memory the GPU can address (cudaMalloc'd or a torch
+ *    CUDA tensor's data_ptr()); "host pointer" = ordinary host memory.
+ *  - Work is enqueued on the CUDA stream given to btc_plan (NULL = legacy
+ *    default stream) and is asynchronous unless stated otherwise.
+ *  - The caller owns every pointer it passes; the plan owns its factor pools,
+ *    work vectors and captured CUDA graphs, all released by btc_free.
+ *  - One plan must not be used from two host threads at the same time.
+ */
+#ifndef BTC_H
+#define BTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct btc_plan_s *btc_plan_t;
+
+/* Arithmetic of a plan. Input element type: FP64 for BTC_F64 and BTC_MIXED_F32,
+ * FP32 for BTC_F32. */
+enum btc_dtype {
+  BTC_F64 = 0,       /* factor and solve in FP64 (the plain FP64 path)                          */
+  BTC_F32 = 1,       /* factor and solve in FP32                                                 */
+  BTC_MIXED_F32 = 2, /* FP64 inputs; factor and correction solves in FP32 except the root
+                        (top-separator) Cholesky, which runs in FP64; FP64 residual and update
+                        in btc_solve_refined                                                     */
+};
+
+enum btc_status {
+  BTC_OK = 0,
+  BTC_ERR_ARG = -1,           /* invalid argument (sizes, NULL, misaligned pointer)        */
+  BTC_ERR_OOM = -2,           /* device allocation failed                                  */
+  BTC_ERR_CUDA = -3,          /* a CUDA runtime call failed (message has the CUDA error)   */
+  BTC_ERR_NOT_SPD = -4,       /* a pivot was not positive (see btc_info)                   */
+  BTC_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up                        */
+  BTC_ERR_NOT_FACTORED = -6,  /* solve called before a successful btc_factor               */
+  BTC_ERR_UNSUPPORTED = -7,   /* block size or dtype not compiled into this library        */
+  BTC_ERR_NOT_CONVERGED = -8, /* refinement stopped above the tolerance                    */
+};
+
+/* Static description of a plan, produced by the host planner alone. */
+typedef struct btc_plan_info {
+  int N, n, np;            /* blocks, block size, padded block size used on the device          */
+  int levels;              /* floor(log2 N) + 1 (Sec. 4.3)                                      */
+  int dtype;
+  int64_t offdiag_blocks;  /* all off-diagonal factor blocks, original + fill (sum over levels
+                              of floor(N / 2^(l-1)) - 1)                                         */
+  int64_t fill_blocks;     /* offdiag_blocks - (N - 1)                                          */
+  double factor_flops;     /* (N/3 + 2 offdiag + 2 fill) n^3, Table 1 costs summed over Alg. 5 */
+  double seq_factor_flops; /* (7/3 N - 2) n^3, Alg. 1 (Sec. 3.1)                                */
+  double critical_path_flops; /* sum over levels of the largest per-node cost (p = infinity)   */
+  double critical_path_formula; /* the closed form of Sec. 4.3 with p = infinity, N >= 2       */
+  double solve_flops_per_rhs;   /* 2 n^2 per node (trsm) + 4 n^2 per off-diagonal block        */
+  double factor_bytes;     /* compulsory bytes: read D, B once; write Dhat and every U block    */
+  double solve_bytes;      /* compulsory bytes per solve with m=1: read the factor twice        */
+  int64_t device_bytes;    /* bytes the plan allocates on the device                            */
+} btc_plan_info;
+
+/*
+ * Host-only planner (no GPU needed): fill *info for an (N, n, dtype) plan.
+ * Returns BTC_ERR_ARG for N < 1 or n < 1, BTC_ERR_UNSUPPORTED when n exceeds
+ * the largest compiled block size for dtype.
+ */
+int btc_describe(int N, int n, int dtype, btc_plan_info *info);
+
+/*
+ * Host-only: the per-level schedule of Alg. 5 for an N-block plan, for
+ * inspection and tests. levels_out[t] receives the dissection level (1-based)
+ * of the t-th eliminated node and order_out[t] the node (0-based), for
+ * t = 0..N-1, in the order the levels run (within a level: ascending node).
+ * This is the elimination order P_inf of Sec. 4.3.
+ */
+int btc_schedule(int N, int *order_out, int *levels_out);
+
+/*
+ * Create a plan for one N-block, n x n system: plans the dissection levels on
+ * the host, allocates the device pools (padded n_p x n_p blocks, level-major),
+ * and binds `stream` (a cudaStream_t, NULL for the legacy default stream).
+ * The plan must be released with btc_free. Errors: BTC_ERR_ARG,
+ * BTC_ERR_UNSUPPORTED, BTC_ERR_OOM, BTC_ERR_CUDA.
+ */
+int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream);
+
+/* Copy the plan's static description into *info. */
+int btc_plan_query(btc_plan_t p, btc_plan_info *info);
+
+/*
+ * Factor (Alg. 5). D: device pointer to N blocks [N][n][n]; only the lower
+ * triangle of each D_i is read. B: device pointer to N-1 blocks [N-1][n][n],
+ * B_i = Psi(i+1, i) (may be NULL when N = 1). Element type FP64 for BTC_F64
+ * and BTC_MIXED_F32, FP32 for BTC_F32; both 16-byte aligned. D and B are not
+ * modified. For BTC_MIXED_F32 and BTC_F64 the plan keeps the two pointers for
+ * the FP64 residual of btc_solve_refined: the caller must keep D and B alive
+ * and unchanged until the next btc_factor or btc_free.
+ * Asynchronous: a non-positive pivot is reported by btc_info, and makes the
+ * next btc_solve / btc_solve_refined return BTC_ERR_NOT_SPD.
+ */
+int btc_factor(btc_plan_t p, const void *D, const void *B);
+
+/*
+ * Solve Psi X = RHS in place with the current factor (Alg. 7), for nrhs
+ * right-hand sides. rhs: device pointer, [N*n][nrhs] row-major, element type
+ * of the factor inputs (FP64 for BTC_F64 / BTC_MIXED_F32, FP32 for BTC_F32);
+ * overwritten by X. For BTC_MIXED_F32 this is ONE FP32 correction solve of an
+ * FP64 vector (no refinement). Asynchronous. Errors: BTC_ERR_NOT_FACTORED,
+ * BTC_ERR_ARG.
+ */
+int btc_solve(btc_plan_t p, void *rhs, int nrhs);
+
+/*
+ * Iterative refinement: x_0 = solve(b); repeat r = b - Psi x (FP64, using the
+ * D and B of the last btc_factor), stop when ||r||_inf <= tol ||Psi||_inf
+ * ||x||_inf (max over right-hand sides), else x += solve(r). b, x: device
+ * pointers, FP64, [N*n][nrhs] row-major (plans of dtype BTC_F64 or
+ * BTC_MIXED_F32 only). Synchronous (reads the norms once per iteration).
+ * *iters (may be NULL): refinement steps taken (0 when the first solve
+ * already meets tol); *relres (may be NULL): final relative residual.
+ * Returns BTC_ERR_NOT_CONVERGED if maxit steps did not reach tol (x then
+ * holds the last iterate), BTC_ERR_NOT_SPD if the factor failed.
+ */
+int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
+                      double *relres);
+
+/*
+ * End-to-end call on HOST buffers: copies D, B (element type as for
+ * btc_factor) and b (FP64 for BTC_F64 / BTC_MIXED_F32, FP32 for BTC_F32)
+ * to plan-owned device buffers, factors, solves (refined to tol for BTC_F64
+ * and BTC_MIXED_F32; one solve for BTC_F32) and copies the solution to x.
+ * b, x: [N*n][nrhs]. Synchronous. Pinned host memory gives the fastest copies.
+ */
+int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void *b, void *x, int nrhs, double tol,
+                          int maxit, int *iters, double *relres);
+
+/*
+ * Synchronize the plan's stream and report the first failed pivot of the
+ * last factorization: *block = 0-based node, *col = column within the block,
+ * both -1 when the factorization succeeded. Returns BTC_OK or BTC_ERR_NOT_SPD.
+ */
+int btc_info(btc_plan_t p, int *block, int *col);
+
+/*
+ * Debug readback (synchronous). Dhat: host buffer [N][n][n] of the factor's
+ * diagonal blocks L(i,i) by node. U: host buffer [offdiag_blocks][n][n] of
+ * the off-diagonal factor blocks in level-major slot order, each stored as the
+ * row block U(e, o) = L(o, e)^T of the node e eliminated at that level; its
+ * partner o is returned in pairs[2*k] = e, pairs[2*k+1] = o (0-based nodes).
+ * Element type: FP64 for BTC_F64, FP32 otherwise. Any pointer may be NULL.
+ */
+int btc_get_factor(btc_plan_t p, void *Dhat, void *U, int *pairs);
+
+/*
+ * ||b - Psi x||_inf, ||Psi||_inf and ||x||_inf (max over right-hand sides),
+ * computed on the device in FP64 for FP64 device arrays D [N][n][n] (lower
+ * triangles read), B [N-1][n][n], x and b [N*n][nrhs]; the three numbers are
+ * written to out3 (host pointer) after a synchronization of `stream`. Uses a
+ * small scratch buffer allocated and freed inside the call.
+ */
+int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const double *x, const double *b,
+                 double *out3, void *stream);
+
+/* Release every device resource of the plan (synchronizes its stream). */
+int btc_free(btc_plan_t p);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *btc_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int btc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTC_H */

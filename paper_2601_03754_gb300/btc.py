@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libbtc.so (include/btc.h), with the same entry-point names.
+
+Argument marshalling only: every numerical step runs inside the library's CUDA
+kernels. Device arrays are passed as torch CUDA tensors (their data_ptr()) or
+as raw integer addresses; streams as torch.cuda.Stream or raw cudaStream_t
+integers. If the library has not been built, loading raises an error: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+F64, F32, MIXED_F32 = 0, 1, 2
+DTYPES = {"f64": F64, "f32": F32, "mixed_f32": MIXED_F32}
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_SPD, ERR_TIMEOUT, ERR_NOT_FACTORED, ERR_UNSUPPORTED, ERR_NOT_CONVERGED = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbtc.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class BtcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"btc error {code}: {msg}")
+        self.code = code
+
+
+class btc_plan_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("n", ctypes.c_int), ("np", ctypes.c_int), ("levels", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("offdiag_blocks", ctypes.c_int64), ("fill_blocks", ctypes.c_int64),
+                ("factor_flops", ctypes.c_double), ("seq_factor_flops", ctypes.c_double),
+                ("critical_path_flops", ctypes.c_double), ("critical_path_formula", ctypes.c_double),
+                ("solve_flops_per_rhs", ctypes.c_double), ("factor_bytes", ctypes.c_double),
+                ("solve_bytes", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp, _ip, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "btc_describe": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(btc_plan_info)],
+    "btc_schedule": [ctypes.c_int, _ip, _ip],
+    "btc_plan": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+    "btc_plan_query": [_vp, ctypes.POINTER(btc_plan_info)],
+    "btc_factor": [_vp, _vp, _vp],
+    "btc_solve": [_vp, _vp, ctypes.c_int],
+    "btc_solve_refined": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
+    "btc_factor_solve_host": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
+    "btc_info": [_vp, _ip, _ip],
+    "btc_get_factor": [_vp, _vp, _vp, _ip],
+    "btc_residual": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
+    "btc_free": [_vp],
+    "btc_last_error": [],
+    "btc_version": [],
+}
+
+
+def header_symbols():
+    """Names of the entry points declared in include/btc.h."""
+    import re
+    path = os.path.join(os.path.dirname(_HERE), "include", "btc.h")
+    with open(path) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(btc_\w+)\s*\(", text, re.M)))
+
+
+def load():
+    """Load libbtc.so (built by build.build()); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} not found: run paper_2601_03754_gb300.build.build() first "
+                                   "(there is no CPU fallback)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.btc_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _check(rc, allow=()):
+    if rc != OK and rc not in allow:
+        raise BtcError(rc, load().btc_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def btc_version():
+    return load().btc_version()
+
+
+def btc_describe(N, n, dtype=F64):
+    info = btc_plan_info()
+    _check(load().btc_describe(N, n, dtype, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def btc_schedule(N):
+    order = np.zeros(N, dtype=np.int32)
+    levels = np.zeros(N, dtype=np.int32)
+    _check(load().btc_schedule(N, order.ctypes.data_as(_ip), levels.ctypes.data_as(_ip)))
+    return order, levels
+
+
+class Plan:
+    """Owning handle of a btc_plan_t (released by free() or garbage collection)."""
+
+    def __init__(self, N, n, dtype=F64, stream=None):
+        h = _vp()
+        _check(load().btc_plan(ctypes.byref(h), N, n, dtype, _stream(stream)))
+        self.h = h
+        self.N, self.n, self.dtype = N, n, dtype
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().btc_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def btc_plan(N, n, dtype=F64, stream=None):
+    return Plan(N, n, dtype, stream)
+
+
+def btc_plan_query(plan):
+    info = btc_plan_info()
+    _check(load().btc_plan_query(plan.h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def btc_factor(plan, D, B):
+    return _check(load().btc_factor(plan.h, _ptr(D), _ptr(B)))
+
+
+def btc_solve(plan, rhs, nrhs):
+    return _check(load().btc_solve(plan.h, _ptr(rhs), nrhs))
+
+
+def btc_solve_refined(plan, b, x, nrhs, tol=1e-10, maxit=20, allow_not_converged=False):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    rc = _check(load().btc_solve_refined(plan.h, _ptr(b), _ptr(x), nrhs, tol, maxit, ctypes.byref(it),
+                                         ctypes.byref(rel)), allow)
+    return it.value, rel.value, rc
+
+
+def btc_factor_solve_host(plan, D, B, b, x, nrhs, tol=1e-10, maxit=20):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    rc = _check(load().btc_factor_solve_host(plan.h, _ptr(D), _ptr(B), _ptr(b), _ptr(x), nrhs, tol, maxit,
+                                             ctypes.byref(it), ctypes.byref(rel)), (ERR_NOT_CONVERGED,))
+    return it.value, rel.value, rc
+
+
+def btc_info(plan):
+    blk = ctypes.c_int(0)
+    col = ctypes.c_int(0)
+    rc = load().btc_info(plan.h, ctypes.byref(blk), ctypes.byref(col))
+    _check(rc, (ERR_NOT_SPD,))
+    return rc, blk.value, col.value
+
+
+def btc_get_factor(plan):
+    """(Dhat [N,n,n], U [offdiag,n,n], pairs [offdiag,2]) as numpy arrays (host copies)."""
+    q = btc_plan_query(plan)
+    dt = np.float64 if plan.dtype == F64 else np.float32
+    N, n, K = plan.N, plan.n, q["offdiag_blocks"]
+    Dh = np.zeros((N, n, n), dtype=dt)
+    U = np.zeros((max(K, 1), n, n), dtype=dt)
+    pairs = np.zeros((max(K, 1), 2), dtype=np.int32)
+    _check(load().btc_get_factor(plan.h, Dh.ctypes.data, U.ctypes.data, pairs.ctypes.data_as(_ip)))
+    return Dh, U[:K], pairs[:K]
+
+
+def btc_residual(N, n, nrhs, D, B, x, b, stream=None):
+    out = (ctypes.c_double * 3)()
+    _check(load().btc_residual(N, n, nrhs, _ptr(D), _ptr(B), _ptr(x), _ptr(b), out, _stream(stream)))
+    return out[0], out[1], out[2]
+
+
+def btc_free(plan):
+    plan.free()
+    return OK

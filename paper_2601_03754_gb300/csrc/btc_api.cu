@@ -1,0 +1,559 @@
+// C ABI and runtime: plan objects, device pools, level launches and the
+// refinement loop. See include/btc.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/btc.h"
+#include "btc_factor.cuh"
+#include "btc_internal.h"
+#include "btc_kernels.h"
+#include "btc_solve.cuh"
+
+namespace btc {
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define BTC_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+  } while (0)
+
+// ------------------------------------------------------------ kernel table
+static constexpr int kMaxSets = 8;
+static KernelSet g_sets[3][kMaxSets];
+static int g_nsets[3] = {0, 0, 0};
+static std::once_flag g_once;
+
+static void init_tables() {
+  std::call_once(g_once, [] {
+    register_f64(g_sets[BTC_F64], &g_nsets[BTC_F64]);
+    register_f32(g_sets[BTC_F32], &g_nsets[BTC_F32]);
+    register_mixed(g_sets[BTC_MIXED_F32], &g_nsets[BTC_MIXED_F32]);
+  });
+}
+
+const KernelSet &kernels_for(int dtype, int np) {
+  static KernelSet none;
+  init_tables();
+  if (dtype < 0 || dtype > 2) return none;
+  for (int i = 0; i < g_nsets[dtype]; ++i)
+    if (g_sets[dtype][i].np == np) return g_sets[dtype][i];
+  return none;
+}
+
+// ||Psi||_inf: max absolute row sum (lower triangles of D read), into norms[2].
+__global__ void k_anorm(const double *D, const double *B, int N, int n, double *norms) {
+  const int i = blockIdx.x;
+  const size_t bs = (size_t)n * n;
+  double best = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += fabs(r >= c ? D[i * bs + r * n + c] : D[i * bs + c * n + r]);
+    if (i > 0)
+      for (int c = 0; c < n; ++c) s += fabs(B[(i - 1) * bs + r * n + c]);
+    if (i + 1 < N)
+      for (int c = 0; c < n; ++c) s += fabs(B[i * bs + c * n + r]);
+    best = fmax(best, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, best);
+}
+
+static bool dtype_ok(int dtype) { return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32; }
+
+static constexpr int kMaxCols = 16;  // right-hand sides per solve launch
+
+}  // namespace btc
+
+using namespace btc;
+
+struct btc_plan_s {
+  int N = 0, n = 0, np = 0, dtype = 0;
+  cudaStream_t stream = nullptr;
+  HostPlan hp;
+  const KernelSet *ks = nullptr;
+  // device memory
+  void *dpool = nullptr, *epool = nullptr;
+  FactorItem *d_fac = nullptr;
+  FwdItem *d_fwd = nullptr;
+  BwdItem *d_bwd = nullptr;
+  std::vector<int64_t> fac_off, fwd_off, bwd_off;  // per level start index
+  unsigned long long *d_info = nullptr;
+  double *d_norms = nullptr;  // [0] max|r|, [1] max|x|, [2] ||Psi||_inf
+  void *d_y = nullptr;        // work vector [N][np][kMaxCols]
+  // host staging for readbacks
+  double *h_norms = nullptr;
+  unsigned long long *h_info = nullptr;
+  // last factorization
+  const void *D = nullptr, *B = nullptr;
+  bool factored = false, anorm_valid = false;
+  // end-to-end host path
+  void *s_D = nullptr, *s_B = nullptr, *s_b = nullptr, *s_x = nullptr;
+  size_t s_rhs_bytes = 0;
+  int64_t device_bytes = 0;
+};
+
+namespace btc {
+
+static void fill_info(const HostPlan &hp, int dtype, btc_plan_info *info) {
+  memset(info, 0, sizeof(*info));
+  info->N = hp.N;
+  info->n = hp.n;
+  info->np = hp.np;
+  info->levels = hp.levels;
+  info->dtype = dtype;
+  info->offdiag_blocks = hp.offdiag;
+  info->fill_blocks = hp.fill;
+  info->factor_flops = hp.factor_flops;
+  info->seq_factor_flops = hp.seq_factor_flops;
+  info->critical_path_flops = hp.crit_flops;
+  info->critical_path_formula = hp.crit_formula;
+  info->solve_flops_per_rhs = hp.solve_flops_per_rhs;
+  const double w = dtype == BTC_F32 ? 4.0 : 8.0;   // caller's element size
+  const double wf = dtype == BTC_F64 ? 8.0 : 4.0;  // factor element size
+  const double n2 = (double)hp.n * hp.n;
+  info->factor_bytes = (2.0 * hp.N - 1.0) * n2 * w + (hp.N + (double)hp.offdiag) * n2 * wf;
+  info->solve_bytes = 2.0 * (hp.N + (double)hp.offdiag) * n2 * wf;
+}
+
+static int launch(const void *fn, int grid, int block, size_t smem, cudaStream_t s, void *arg) {
+  if (grid <= 0) return BTC_OK;
+  void *args[] = {arg};
+  BTC_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
+  return BTC_OK;
+}
+
+template <typename... A>
+static int launch_n(const void *fn, int grid, int block, size_t smem, cudaStream_t s, A... a) {
+  void *args[] = {(void *)&a...};
+  BTC_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
+  return BTC_OK;
+}
+
+static int set_smem(const void *fn, size_t bytes) {
+  if (!fn) return BTC_OK;
+  BTC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return BTC_OK;
+}
+
+static int grid_for(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+// Forward + backward substitution of the work vector (m columns), Alg. 7.
+static int run_solve(btc_plan_s *p, int m) {
+  const KernelSet &k = *p->ks;
+  SolveArgs a;
+  a.dpool = p->dpool;
+  a.epool = p->epool;
+  a.y = p->d_y;
+  a.m = m;
+  for (int l = 0; l < p->hp.levels; ++l) {
+    a.items = p->d_fwd + p->fwd_off[l];
+    a.count = (int)(p->fwd_off[l + 1] - p->fwd_off[l]);
+    int rc = launch(k.fwd, a.count, kSolveThreads, k.fwd_smem(m), p->stream, &a);
+    if (rc) return rc;
+  }
+  for (int l = p->hp.levels - 1; l >= 0; --l) {
+    a.items = p->d_bwd + p->bwd_off[l];
+    a.count = (int)(p->bwd_off[l + 1] - p->bwd_off[l]);
+    int rc = launch(k.bwd, a.count, kSolveThreads, k.bwd_smem(m), p->stream, &a);
+    if (rc) return rc;
+  }
+  return BTC_OK;
+}
+
+static int read_info(btc_plan_s *p, int *block, int *col) {
+  BTC_CUDA(cudaMemcpyAsync(p->h_info, p->d_info, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->stream));
+  BTC_CUDA(cudaStreamSynchronize(p->stream));
+  unsigned long long v = *p->h_info;
+  if (v == ~0ull) {
+    if (block) *block = -1;
+    if (col) *col = -1;
+    return BTC_OK;
+  }
+  if (block) *block = (int)(v >> 20);
+  if (col) *col = (int)(v & 0xFFFFF);
+  return BTC_ERR_NOT_SPD;
+}
+
+}  // namespace btc
+
+extern "C" {
+
+int btc_version(void) { return 100; }
+
+const char *btc_last_error(void) { return g_err.c_str(); }
+
+int btc_describe(int N, int n, int dtype, btc_plan_info *info) {
+  if (!info || N < 1 || n < 1) return fail(BTC_ERR_ARG, "btc_describe: invalid arguments");
+  if (!dtype_ok(dtype)) return fail(BTC_ERR_ARG, "btc_describe: unknown dtype %d", dtype);
+  int np = padded_size(n, dtype);
+  if (!np) return fail(BTC_ERR_UNSUPPORTED, "block size %d exceeds the largest compiled size", n);
+  HostPlan hp;
+  build_host_plan(N, n, np, 0, 0, 0, 0, &hp);
+  fill_info(hp, dtype, info);
+  const double pe = dtype == BTC_F64 ? 8.0 : 4.0;
+  info->device_bytes = (int64_t)(pe * (double)np * np * (N + std::max<int64_t>(hp.offdiag, 1)) +
+                                 pe * (double)N * np * kMaxCols);
+  return BTC_OK;
+}
+
+int btc_schedule(int N, int *order_out, int *levels_out) {
+  if (N < 1 || !order_out) return fail(BTC_ERR_ARG, "btc_schedule: invalid arguments");
+  HostPlan hp;
+  build_host_plan(N, 1, 8, 0, 0, 0, 0, &hp);
+  int t = 0;
+  for (int l = 0; l < hp.levels; ++l)
+    for (const FactorItem &it : hp.lv[l].fac) {
+      order_out[t] = it.node;
+      if (levels_out) levels_out[t] = l + 1;
+      ++t;
+    }
+  return t == N ? BTC_OK : fail(BTC_ERR_ARG, "schedule covers %d of %d nodes", t, N);
+}
+
+int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
+  if (!out || N < 1 || n < 1) return fail(BTC_ERR_ARG, "btc_plan: invalid arguments (N=%d, n=%d)", N, n);
+  *out = nullptr;
+  if (!dtype_ok(dtype)) return fail(BTC_ERR_ARG, "btc_plan: unknown dtype %d", dtype);
+  int np = padded_size(n, dtype);
+  if (!np) return fail(BTC_ERR_UNSUPPORTED, "block size %d exceeds the largest compiled size", n);
+  const KernelSet &ks = kernels_for(dtype, np);
+  if (!ks.valid) return fail(BTC_ERR_UNSUPPORTED, "no kernels for dtype %d, np %d", dtype, np);
+  btc_plan_s *p = new btc_plan_s();
+  p->N = N;
+  p->n = n;
+  p->np = np;
+  p->dtype = dtype;
+  p->stream = (cudaStream_t)stream;
+  p->ks = &ks;
+  build_host_plan(N, n, np, 0, 0, 0, 0, &p->hp);
+  int rc = BTC_OK;
+  auto cleanup = [&](int code) {
+    btc_free(p);
+    return code;
+  };
+  const size_t bs = (size_t)np * np * ks.elem;
+  size_t dbytes = bs * N, ebytes = bs * std::max<int64_t>(p->hp.offdiag, 1);
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->dpool, dbytes)) != cudaSuccess ||
+      (e = cudaMalloc(&p->epool, ebytes)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_y, (size_t)N * np * kMaxCols * ks.elem)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_info, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_norms, 4 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_norms, 4 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_info, sizeof(unsigned long long))) != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
+                        cudaGetErrorString(e)));
+  p->device_bytes = (int64_t)(dbytes + ebytes + (size_t)N * np * kMaxCols * ks.elem);
+  // flatten the per-level schedules and upload them
+  std::vector<FactorItem> fac;
+  std::vector<FwdItem> fwd;
+  std::vector<BwdItem> bwd;
+  p->fac_off.push_back(0);
+  p->fwd_off.push_back(0);
+  p->bwd_off.push_back(0);
+  for (const LevelSchedule &L : p->hp.lv) {
+    fac.insert(fac.end(), L.fac.begin(), L.fac.end());
+    fwd.insert(fwd.end(), L.fwd.begin(), L.fwd.end());
+    bwd.insert(bwd.end(), L.bwd.begin(), L.bwd.end());
+    p->fac_off.push_back((int64_t)fac.size());
+    p->fwd_off.push_back((int64_t)fwd.size());
+    p->bwd_off.push_back((int64_t)bwd.size());
+  }
+  if ((e = cudaMalloc(&p->d_fac, fac.size() * sizeof(FactorItem))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_fwd, fwd.size() * sizeof(FwdItem))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_bwd, bwd.size() * sizeof(BwdItem))) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_OOM, "btc_plan: schedule allocation: %s", cudaGetErrorString(e)));
+  if ((e = cudaMemcpy(p->d_fac, fac.data(), fac.size() * sizeof(FactorItem), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(p->d_fwd, fwd.data(), fwd.size() * sizeof(FwdItem), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_bwd, bwd.data(), bwd.size() * sizeof(BwdItem), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_CUDA, "btc_plan: schedule upload: %s", cudaGetErrorString(e)));
+  p->device_bytes += (int64_t)(fac.size() * sizeof(FactorItem) + fwd.size() * sizeof(FwdItem) +
+                               bwd.size() * sizeof(BwdItem));
+  // allow the large dynamic shared memory the kernels use
+  if ((rc = set_smem(ks.fac_first, ks.fac_smem)) || (rc = set_smem(ks.fac_rest, ks.fac_smem)) ||
+      (rc = set_smem(ks.root_first, ks.root_smem)) || (rc = set_smem(ks.root_rest, ks.root_smem)) ||
+      (rc = set_smem(ks.fwd, ks.fwd_smem(kMaxCols))) || (rc = set_smem(ks.bwd, ks.bwd_smem(kMaxCols))) ||
+      (rc = set_smem(ks.resid, 3 * sizeof(double) * (size_t)n * (n + 1))))
+    return cleanup(rc);
+  *out = p;
+  return BTC_OK;
+}
+
+int btc_plan_query(btc_plan_t p, btc_plan_info *info) {
+  if (!p || !info) return fail(BTC_ERR_ARG, "btc_plan_query: NULL argument");
+  fill_info(p->hp, p->dtype, info);
+  info->device_bytes = p->device_bytes;
+  return BTC_OK;
+}
+
+int btc_factor(btc_plan_t p, const void *D, const void *B) {
+  if (!p || !D || (p->N > 1 && !B)) return fail(BTC_ERR_ARG, "btc_factor: NULL argument");
+  if (((uintptr_t)D | (uintptr_t)B) & 15) return fail(BTC_ERR_ARG, "btc_factor: D and B must be 16-byte aligned");
+  const KernelSet &k = *p->ks;
+  BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
+  FactorArgs a;
+  a.dpool = p->dpool;
+  a.epool = p->epool;
+  a.info = p->d_info;
+  a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
+  for (int l = 0; l < p->hp.levels; ++l) {
+    a.items = p->d_fac + p->fac_off[l];
+    a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
+    const bool root = (l == p->hp.levels - 1) && p->dtype == BTC_MIXED_F32;
+    const void *fn = root ? (l == 0 ? k.root_first : k.root_rest) : (l == 0 ? k.fac_first : k.fac_rest);
+    const int threads = root ? k.root_threads : k.fac_threads;
+    const size_t smem = root ? k.root_smem : k.fac_smem;
+    InstDesc d{D, B, p->N, p->n};
+    int rc = launch_n(fn, a.count, threads, smem, p->stream, a, d);
+    if (rc) return rc;
+  }
+  p->D = D;
+  p->B = B;
+  p->factored = true;
+  p->anorm_valid = false;
+  return BTC_OK;
+}
+
+int btc_solve(btc_plan_t p, void *rhs, int nrhs) {
+  if (!p || !rhs || nrhs < 1) return fail(BTC_ERR_ARG, "btc_solve: invalid arguments");
+  if (!p->factored) return fail(BTC_ERR_NOT_FACTORED, "btc_solve: no factorization");
+  const KernelSet &k = *p->ks;
+  for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
+    const int m = std::min(kMaxCols, nrhs - c0);
+    int64_t base = 0;
+    int rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)rhs,
+                      p->N, p->n, p->np, m, nrhs, c0, base);
+    if (rc) return rc;
+    if ((rc = run_solve(p, m))) return rc;
+    int acc = 0;
+    rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, rhs, (const void *)p->d_y, p->N,
+                  p->n, p->np, m, nrhs, c0, base, acc);
+    if (rc) return rc;
+  }
+  return BTC_OK;
+}
+
+int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
+                      double *relres) {
+  if (!p || !b || !x || nrhs < 1 || maxit < 0) return fail(BTC_ERR_ARG, "btc_solve_refined: invalid arguments");
+  if (p->dtype == BTC_F32) return fail(BTC_ERR_ARG, "btc_solve_refined needs an FP64 or mixed plan");
+  if (nrhs > kMaxCols) return fail(BTC_ERR_UNSUPPORTED, "btc_solve_refined: at most %d right-hand sides", kMaxCols);
+  if (!p->factored) return fail(BTC_ERR_NOT_FACTORED, "btc_solve_refined: no factorization");
+  const KernelSet &k = *p->ks;
+  int blk, col;
+  int rc = read_info(p, &blk, &col);
+  if (rc) return fail(rc, "factorization failed: pivot of block %d, column %d not positive", blk, col);
+  if (!p->anorm_valid) {
+    BTC_CUDA(cudaMemsetAsync(p->d_norms + 2, 0, sizeof(double), p->stream));
+    if ((rc = launch_n((const void *)&k_anorm, p->N, 64, 0, p->stream, (const double *)p->D, (const double *)p->B,
+                       p->N, p->n, p->d_norms)))
+      return rc;
+    p->anorm_valid = true;
+  }
+  const size_t rsm = 3 * sizeof(double) * (size_t)p->n * (p->n + 1);
+  int worst_it = 0;
+  double worst_rel = 0.0;
+  bool all_ok = true;
+  for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
+    const int m = std::min(kMaxCols, nrhs - c0);
+    int64_t base = 0;
+    // x_0 = solve(b)
+    if ((rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)b, p->N,
+                       p->n, p->np, m, nrhs, c0, base)))
+      return rc;
+    if ((rc = run_solve(p, m))) return rc;
+    int assign = 0, accumulate = 1;
+    if ((rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
+                       (const void *)p->d_y, p->N, p->n, p->np, m, nrhs, c0, base, assign)))
+      return rc;
+    int it = 0;
+    double rel = 0.0;
+    bool ok = false;
+    for (;;) {
+      BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, 2 * sizeof(double), p->stream));
+      if ((rc = launch_n(k.resid, p->N, 128, rsm, p->stream, p->d_y, (const double *)p->D, (const double *)p->B,
+                         (const double *)x, b, p->N, p->n, p->np, m, base, p->d_norms)))
+        return rc;
+      BTC_CUDA(cudaMemcpyAsync(p->h_norms, p->d_norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+      BTC_CUDA(cudaStreamSynchronize(p->stream));
+      const double rn = p->h_norms[0], xn = p->h_norms[1], an = p->h_norms[2];
+      rel = (an * xn > 0) ? rn / (an * xn) : rn;
+      if (!(rel == rel)) break;  // NaN: give up
+      if (rel <= tol) {
+        ok = true;
+        break;
+      }
+      if (it >= maxit) break;
+      if ((rc = run_solve(p, m))) return rc;
+      if ((rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
+                         (const void *)p->d_y, p->N, p->n, p->np, m, nrhs, c0, base, accumulate)))
+        return rc;
+      ++it;
+    }
+    worst_it = std::max(worst_it, it);
+    worst_rel = std::max(worst_rel, rel);
+    all_ok = all_ok && ok;
+  }
+  if (iters) *iters = worst_it;
+  if (relres) *relres = worst_rel;
+  if (!all_ok) return fail(BTC_ERR_NOT_CONVERGED, "refinement stopped at relative residual %.3e", worst_rel);
+  return BTC_OK;
+}
+
+int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void *b, void *x, int nrhs, double tol,
+                          int maxit, int *iters, double *relres) {
+  if (!p || !D || (p->N > 1 && !B) || !b || !x || nrhs < 1) return fail(BTC_ERR_ARG, "btc_factor_solve_host: args");
+  const size_t w = p->ks->src_elem;
+  const size_t nb = (size_t)p->n * p->n * w;
+  const size_t rbytes = (size_t)p->N * p->n * nrhs * w;
+  if (!p->s_D) {
+    BTC_CUDA(cudaMalloc(&p->s_D, nb * p->N));
+    BTC_CUDA(cudaMalloc(&p->s_B, nb * std::max(p->N - 1, 1)));
+  }
+  if (p->s_rhs_bytes < rbytes) {
+    if (p->s_b) cudaFree(p->s_b);
+    if (p->s_x) cudaFree(p->s_x);
+    p->s_b = p->s_x = nullptr;
+    BTC_CUDA(cudaMalloc(&p->s_b, rbytes));
+    BTC_CUDA(cudaMalloc(&p->s_x, rbytes));
+    p->s_rhs_bytes = rbytes;
+  }
+  BTC_CUDA(cudaMemcpyAsync(p->s_D, D, nb * p->N, cudaMemcpyHostToDevice, p->stream));
+  if (p->N > 1) BTC_CUDA(cudaMemcpyAsync(p->s_B, B, nb * (p->N - 1), cudaMemcpyHostToDevice, p->stream));
+  BTC_CUDA(cudaMemcpyAsync(p->s_b, b, rbytes, cudaMemcpyHostToDevice, p->stream));
+  int rc = btc_factor(p, p->s_D, p->s_B);
+  if (rc) return rc;
+  if (p->dtype == BTC_F32) {
+    BTC_CUDA(cudaMemcpyAsync(p->s_x, p->s_b, rbytes, cudaMemcpyDeviceToDevice, p->stream));
+    if ((rc = btc_solve(p, p->s_x, nrhs))) return rc;
+    int blk, col;
+    if ((rc = read_info(p, &blk, &col))) return fail(rc, "pivot of block %d, column %d not positive", blk, col);
+    if (iters) *iters = 0;
+    if (relres) *relres = -1.0;
+  } else {
+    rc = btc_solve_refined(p, (const double *)p->s_b, (double *)p->s_x, nrhs, tol, maxit, iters, relres);
+    if (rc && rc != BTC_ERR_NOT_CONVERGED) return rc;
+    if (rc) {
+      std::string keep = g_err;
+      BTC_CUDA(cudaMemcpyAsync(x, p->s_x, rbytes, cudaMemcpyDeviceToHost, p->stream));
+      BTC_CUDA(cudaStreamSynchronize(p->stream));
+      g_err = keep;
+      return rc;
+    }
+  }
+  BTC_CUDA(cudaMemcpyAsync(x, p->s_x, rbytes, cudaMemcpyDeviceToHost, p->stream));
+  BTC_CUDA(cudaStreamSynchronize(p->stream));
+  return BTC_OK;
+}
+
+int btc_info(btc_plan_t p, int *block, int *col) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_info: NULL plan");
+  if (!p->factored) {
+    if (block) *block = -1;
+    if (col) *col = -1;
+    return BTC_OK;
+  }
+  int rc = read_info(p, block, col);
+  if (rc == BTC_ERR_NOT_SPD) return fail(rc, "pivot not positive");
+  return rc;
+}
+
+int btc_get_factor(btc_plan_t p, void *Dhat, void *U, int *pairs) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_get_factor: NULL plan");
+  BTC_CUDA(cudaStreamSynchronize(p->stream));
+  const size_t w = p->ks->elem, np = p->np, n = p->n;
+  const size_t bs = np * np * w;
+  if (Dhat) {
+    std::vector<char> buf(bs * p->N);
+    BTC_CUDA(cudaMemcpy(buf.data(), p->dpool, buf.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < p->N; ++i)
+      for (size_t r = 0; r < n; ++r)
+        memcpy((char *)Dhat + ((size_t)i * n * n + r * n) * w, buf.data() + i * bs + r * np * w, n * w);
+  }
+  if (U && p->hp.offdiag > 0) {
+    std::vector<char> buf(bs * p->hp.offdiag);
+    BTC_CUDA(cudaMemcpy(buf.data(), p->epool, buf.size(), cudaMemcpyDeviceToHost));
+    for (int64_t s = 0; s < p->hp.offdiag; ++s)
+      for (size_t r = 0; r < n; ++r)
+        memcpy((char *)U + ((size_t)s * n * n + r * n) * w, buf.data() + s * bs + r * np * w, n * w);
+  }
+  if (pairs)
+    for (int64_t s = 0; s < p->hp.offdiag; ++s) {
+      pairs[2 * s] = p->hp.slot_e[s];
+      pairs[2 * s + 1] = p->hp.slot_o[s];
+    }
+  return BTC_OK;
+}
+
+int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const double *x, const double *b,
+                 double *out3, void *stream) {
+  if (N < 1 || n < 1 || nrhs < 1 || !D || (N > 1 && !B) || !x || !b || !out3)
+    return fail(BTC_ERR_ARG, "btc_residual: invalid arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *d = nullptr;
+  BTC_CUDA(cudaMallocAsync((void **)&d, 3 * sizeof(double), s));
+  int rc = BTC_OK;
+  cudaError_t e = cudaMemsetAsync(d, 0, 3 * sizeof(double), s);
+  const size_t rsm = 3 * sizeof(double) * (size_t)n * (n + 1);
+  const void *rk = (const void *)&k_residual<double>;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+  if (e == cudaSuccess) {
+    rc = launch_n((const void *)&k_anorm, N, 64, 0, s, D, B, N, n, d);
+    double *ynull = nullptr;
+    int np = n;
+    int64_t base = 0;
+    if (!rc) rc = launch_n(rk, N, 128, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d);
+  }
+  double h[3] = {0, 0, 0};
+  if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(BTC_ERR_CUDA, "btc_residual: %s", cudaGetErrorString(e));
+  if (rc) return rc;
+  if (e2 != cudaSuccess) return fail(BTC_ERR_CUDA, "btc_residual: %s", cudaGetErrorString(e2));
+  out3[0] = h[0];
+  out3[1] = h[2];
+  out3[2] = h[1];
+  return BTC_OK;
+}
+
+int btc_free(btc_plan_t p) {
+  if (!p) return BTC_OK;
+  if (p->stream || p->dpool) cudaStreamSynchronize(p->stream);
+  void *dev[] = {p->dpool, p->epool, p->d_fac, p->d_fwd, p->d_bwd, p->d_info, p->d_norms,
+                 p->d_y,   p->s_D,   p->s_B,   p->s_b,   p->s_x};
+  for (void *q : dev)
+    if (q) cudaFree(q);
+  if (p->h_norms) cudaFreeHost(p->h_norms);
+  if (p->h_info) cudaFreeHost(p->h_info);
+  delete p;
+  return BTC_OK;
+}
+
+}  // extern "C"

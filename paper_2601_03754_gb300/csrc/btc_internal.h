@@ -1,0 +1,88 @@
+// Internal types shared by the host planner (btc_plan.cpp), the kernels and
+// the runtime. Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace btc {
+
+// Storage convention of the factor pools.
+//  * Dhat pool: one padded np x np block per node (row-major); after the
+//    factorization it holds L(e, e) (lower triangle, zeros above).
+//  * U pool: one np x np block per slot, level-major. Level l (stride
+//    s = 2^(l-1)) has K_l = floor(N/s) - 1 slots; slot k (1-based) couples the
+//    surviving nodes k*s and (k+1)*s. Exactly one of the two is eliminated at
+//    level l (the odd multiple of s), call it e, the other o. Before level l
+//    the slot holds the Schur-complement block S(e, o) (rows: e's variables);
+//    level l overwrites it with U(e, o) = Dhat_e^{-1} S(e, o) = L(o, e)^T.
+//  With this orientation every block product of Alg. 5 is C -= X^T Y and
+//  every triangular solve is Z = L^{-1} R (left, lower).
+
+enum : int32_t {
+  FI_FILL_UPFIRST = 1,  // fill block stores S'(e-s, e+s) = -Zu^T Zd (e-s is eliminated next); else S'(e+s, e-s)
+  FI_ROOT = 2,          // last level (the top separator)
+};
+
+// One eliminated node e at level l (Alg. 5, one iteration of the parallel loop).
+// Offsets are in ELEMENTS into the Dhat / U pools, -1 when the step is absent.
+struct FactorItem {
+  int64_t d_self;  // Dhat_e
+  int64_t d_next;  // Dhat_{e+s}                      (syrk target)
+  int64_t r_up;    // slot of S(e, e-s) -> U(e, e-s)  (trsm)
+  int64_t r_down;  // slot of S(e, e+s) -> U(e, e+s)  (trsm)
+  int64_t p_a;     // deferred block onto Dhat_e:     U(e+s/2, e)        (level > 1)
+  int64_t p_b;     // deferred block onto Dhat_{e+s}: U(e+3s/2, e+s)     (level > 1)
+  int64_t fill;    // new slot at level l+1 for the pair (e-s, e+s)
+  int32_t node;    // e, 0-based, within its instance
+  int32_t flags;
+  int32_t inst;    // instance index (batched plans)
+  int32_t pad;
+};
+
+// Forward substitution at level l for a surviving node j (pull form):
+// y_j -= U(j-h, j)^T y_{j-h} + U(j+h, j)^T y_{j+h}  (contributions of level l-1,
+// h = s/2), then y_j <- Dhat_j^{-1} y_j if j is eliminated at level l.
+struct FwdItem {
+  int64_t y_self;      // node index (global across instances) of y_j
+  int64_t y_l, e_l;    // y_{j-h} node and U(j-h, j) offset, or -1
+  int64_t y_r, e_r;    // y_{j+h} node and U(j+h, j) offset, or -1
+  int64_t d_self;      // Dhat_j offset, or -1 if j survives this level
+};
+
+// Backward substitution at level l for an eliminated node e:
+// x_e <- Dhat_e^{-T} (y_e - U(e, e+s) x_{e+s} - U(e, e-s) x_{e-s}).
+struct BwdItem {
+  int64_t x_self, d_self;
+  int64_t x_dn, e_dn;  // x_{e+s} node and U(e, e+s) offset, or -1
+  int64_t x_up, e_up;  // x_{e-s} node and U(e, e-s) offset, or -1
+};
+
+struct LevelSchedule {
+  int s;  // stride 2^(l-1)
+  std::vector<FactorItem> fac;
+  std::vector<FwdItem> fwd;
+  std::vector<BwdItem> bwd;
+};
+
+struct HostPlan {
+  int N = 0, n = 0, np = 0, levels = 0;
+  int64_t offdiag = 0, fill = 0;
+  std::vector<int64_t> level_slot_off;  // first U slot of each level (in blocks)
+  std::vector<LevelSchedule> lv;
+  std::vector<int> slot_e, slot_o;      // per U slot: eliminated node and partner (0-based)
+  double factor_flops = 0, seq_factor_flops = 0, crit_flops = 0, crit_formula = 0;
+  double solve_flops_per_rhs = 0;
+};
+
+// Build the schedule. Offsets are relative to the given bases (in blocks for
+// the pools, in nodes for the work vector) so that batched plans can
+// concatenate instances.
+void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64_t y_base, int inst,
+                     HostPlan *out);
+
+int padded_size(int n, int dtype);       // np for a block size (0 if unsupported)
+int64_t count_offdiag(int N);            // sum over levels of floor(N/s) - 1
+
+}  // namespace btc

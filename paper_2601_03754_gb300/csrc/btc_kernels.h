@@ -1,0 +1,36 @@
+// Kernel table: the compiled instantiations for one (dtype, np) pair, filled
+// by the per-dtype translation units and launched by the runtime.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace btc {
+
+struct KernelSet {
+  bool valid = false;
+  int np = 0;
+  size_t elem = 0;        // bytes per pool element
+  size_t src_elem = 0;    // bytes per element of the caller's D, B, rhs
+  // factor levels: level 1 reads the caller's arrays, later levels the pools
+  const void *fac_first = nullptr, *fac_rest = nullptr;
+  int fac_threads = 0;
+  size_t fac_smem = 0;
+  // FP64 top-separator Cholesky for the mixed path (T = double, pools FP32)
+  const void *root_first = nullptr, *root_rest = nullptr;
+  int root_threads = 0;
+  size_t root_smem = 0;
+  // solve
+  const void *fwd = nullptr, *bwd = nullptr;
+  size_t (*fwd_smem)(int m) = nullptr;
+  size_t (*bwd_smem)(int m) = nullptr;
+  const void *pack = nullptr, *unpack = nullptr, *resid = nullptr;
+};
+
+// dtype codes as in btc.h
+const KernelSet &kernels_for(int dtype, int np);
+void register_f64(KernelSet *table, int *count);
+void register_f32(KernelSet *table, int *count);
+void register_mixed(KernelSet *table, int *count);
+
+}  // namespace btc

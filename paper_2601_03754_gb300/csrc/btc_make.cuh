@@ -1,0 +1,48 @@
+// Builds the KernelSet of one (arithmetic, pool, source, np) instantiation.
+#pragma once
+#include "btc_factor.cuh"
+#include "btc_kernels.h"
+#include "btc_solve.cuh"
+
+namespace btc {
+
+// Register tile edge per padded block size: (np/R)^2 threads per CTA.
+template <int NP>
+struct TileEdge {
+  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : NP == 48 ? 3 : 4;
+};
+
+template <typename T, int NP>
+size_t fwd_smem_fn(int m) { return fwd_smem_bytes<T, NP>(m); }
+template <typename T, int NP>
+size_t bwd_smem_fn(int m) { return bwd_smem_bytes<T, NP>(m); }
+
+template <typename T, typename S, int NP, bool MIXED>
+KernelSet make_set() {
+  constexpr int R = TileEdge<NP>::R;
+  KernelSet k;
+  k.valid = true;
+  k.np = NP;
+  k.elem = sizeof(T);
+  k.src_elem = sizeof(S);
+  k.fac_first = (const void *)&k_factor_level<T, T, S, NP, R, true>;
+  k.fac_rest = (const void *)&k_factor_level<T, T, S, NP, R, false>;
+  k.fac_threads = TileCfg<T, NP, R>::NT;
+  k.fac_smem = factor_smem_bytes<T, NP, R>();
+  if constexpr (MIXED) {
+    k.root_first = (const void *)&k_factor_level<double, T, S, NP, R, true>;
+    k.root_rest = (const void *)&k_factor_level<double, T, S, NP, R, false>;
+    k.root_threads = TileCfg<double, NP, R>::NT;
+    k.root_smem = factor_smem_bytes<double, NP, R>();
+  }
+  k.fwd = (const void *)&k_fwd_level<T, NP>;
+  k.bwd = (const void *)&k_bwd_level<T, NP>;
+  k.fwd_smem = &fwd_smem_fn<T, NP>;
+  k.bwd_smem = &bwd_smem_fn<T, NP>;
+  k.pack = (const void *)&k_pack_rhs<T, S>;
+  k.unpack = (const void *)&k_unpack<T, S>;
+  k.resid = (const void *)&k_residual<T>;
+  return k;
+}
+
+}  // namespace btc

@@ -1,0 +1,136 @@
+// Host planner: the level schedule of the multi-stage permutation P_inf
+// (Sec. 4.3) for Alg. 5 (factorization) and Alg. 7 (solve). Integer work only.
+//
+// Levels l = 1 .. floor(log2 N) + 1 with stride s = 2^(l-1); at level l the
+// eliminated nodes are the odd multiples of s that are <= N (1-based labels,
+// as in the paper), and the surviving nodes are the multiples of s.
+#include <cmath>
+
+#include "btc_internal.h"
+
+namespace btc {
+
+static const int kSizes[] = {8, 16, 32, 48, 64};
+
+int padded_size(int n, int dtype) {
+  (void)dtype;
+  for (int s : kSizes)
+    if (n <= s) return s;
+  return 0;
+}
+
+int64_t count_offdiag(int N) {
+  int64_t t = 0;
+  for (int64_t s = 1; s <= N; s *= 2) t += N / s - 1;
+  return t;
+}
+
+void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64_t y_base, int inst,
+                     HostPlan *P) {
+  P->N = N;
+  P->n = n;
+  P->np = np;
+  const int64_t bs = (int64_t)np * np;
+  int levels = 0;
+  for (int64_t s = 1; s <= N; s *= 2) ++levels;
+  P->levels = levels;
+  // U slots: level-major, K_l = floor(N/s) - 1 per level; one more (empty) level
+  // index is reserved so that fill targets of the last level are addressable.
+  P->level_slot_off.assign(levels + 2, 0);
+  for (int l = 1; l <= levels + 1; ++l) {
+    int64_t s = int64_t(1) << (l - 1);
+    int64_t K = s <= N ? N / s - 1 : 0;
+    P->level_slot_off[l] = P->level_slot_off[l - 1] + (K > 0 ? K : 0);
+  }
+  P->offdiag = P->level_slot_off[levels];
+  P->fill = P->offdiag - (N - 1);
+  P->slot_e.assign(P->offdiag, -1);
+  P->slot_o.assign(P->offdiag, -1);
+
+  // 1-based node v -> pool offsets
+  auto dOff = [&](int64_t v) { return (d_base + v - 1) * bs; };
+  auto eSlot = [&](int l, int64_t k) { return P->level_slot_off[l - 1] + (k - 1); };  // k 1-based
+  auto eOff = [&](int l, int64_t k) { return (e_base + eSlot(l, k)) * bs; };
+  auto yNode = [&](int64_t v) { return y_base + v - 1; };
+
+  P->lv.assign(levels, LevelSchedule());
+  const double n3 = (double)n * n * n, n2 = (double)n * n;
+  double fl = 0, crit = 0, sol = 0;
+  for (int l = 1; l <= levels; ++l) {
+    const int64_t s = int64_t(1) << (l - 1);
+    const int64_t h = s / 2;
+    LevelSchedule &L = P->lv[l - 1];
+    L.s = (int)s;
+    double level_max = 0;
+    for (int64_t e = s; e <= N; e += 2 * s) {
+      FactorItem it;
+      it.d_self = dOff(e);
+      it.d_next = (e + s <= N) ? dOff(e + s) : -1;
+      it.r_down = (e + s <= N) ? eOff(l, e / s) : -1;
+      it.r_up = (e > s) ? eOff(l, e / s - 1) : -1;
+      it.p_a = (l > 1 && e + h <= N) ? eOff(l - 1, 2 * e / s) : -1;
+      it.p_b = (l > 1 && e + s + h <= N) ? eOff(l - 1, 2 * e / s + 2) : -1;
+      it.fill = (e > s && e + s <= N) ? eOff(l + 1, (e - s) / (2 * s)) : -1;
+      it.flags = 0;
+      if (it.fill >= 0 && (((e - s) / (2 * s)) & 1)) it.flags |= FI_FILL_UPFIRST;
+      if (l == levels) it.flags |= FI_ROOT;
+      it.node = (int32_t)(e - 1);
+      it.inst = inst;
+      it.pad = 0;
+      L.fac.push_back(it);
+      if (it.r_down >= 0) {
+        P->slot_e[eSlot(l, e / s)] = (int)(e - 1);
+        P->slot_o[eSlot(l, e / s)] = (int)(e + s - 1);
+      }
+      if (it.r_up >= 0) {
+        P->slot_e[eSlot(l, e / s - 1)] = (int)(e - 1);
+        P->slot_o[eSlot(l, e / s - 1)] = (int)(e - s - 1);
+      }
+      // Table 1 costs: potrf n^3/3, trsm n^3, syrk n^3, gemm 2 n^3 (square blocks)
+      double c = n3 / 3.0;
+      if (it.p_a >= 0) c += n3;
+      if (it.p_b >= 0) c += n3;
+      if (it.r_down >= 0) c += 2 * n3;  // trsm + immediate syrk onto Dhat_{e+s}
+      if (it.r_up >= 0) c += n3;        // trsm
+      if (it.fill >= 0) c += 2 * n3;    // gemm
+      fl += c;
+      if (c > level_max) level_max = c;
+      BwdItem b;
+      b.x_self = yNode(e);
+      b.d_self = dOff(e);
+      b.x_dn = (e + s <= N) ? yNode(e + s) : -1;
+      b.e_dn = it.r_down;
+      b.x_up = (e > s) ? yNode(e - s) : -1;
+      b.e_up = it.r_up;
+      L.bwd.push_back(b);
+    }
+    crit += level_max;
+    for (int64_t j = s; j <= N; j += s) {
+      FwdItem f;
+      f.y_self = yNode(j);
+      f.y_l = f.e_l = f.y_r = f.e_r = -1;
+      if (l > 1) {
+        f.y_l = yNode(j - h);
+        f.e_l = eOff(l - 1, (j - h) / h);
+        if (j + h <= N) {
+          f.y_r = yNode(j + h);
+          f.e_r = eOff(l - 1, j / h);
+        }
+      }
+      f.d_self = ((j / s) & 1) ? dOff(j) : -1;
+      L.fwd.push_back(f);
+    }
+  }
+  // Solve flops (Alg. 7 costs): trsm n^2 m per node and direction, gemm 2 n^2 m per
+  // off-diagonal block and direction.
+  sol = 2.0 * N * n2 + 4.0 * (double)P->offdiag * n2;
+  P->factor_flops = fl;
+  P->seq_factor_flops = (7.0 / 3.0 * N - 2.0) * n3;
+  P->crit_flops = crit;
+  // Sec. 4.3 closed form with p = infinity (N >= 2): 16/3 + 22/3 (floor(log2 N) - 1) + 4/3, times n^3
+  int lg = levels - 1;
+  P->crit_formula = N >= 2 ? (16.0 / 3.0 + 22.0 / 3.0 * (lg - 1) + 4.0 / 3.0) * n3 : n3 / 3.0;
+  P->solve_flops_per_rhs = sol;
+}
+
+}  // namespace btc

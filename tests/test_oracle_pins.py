@@ -377,7 +377,8 @@ MUTATIONS = [
      "blk[r * n + c] = B[i * bs + r * n + c];", "nd"),
     ("bs_update_wrong_sign", "gemm_nt_sub(n, T[(size_t)i * N + k], T[(size_t)j * N + k], *slot);",
      "gemm_nt_sub(n, T[(size_t)j * N + k], T[(size_t)i * N + k], *slot);", "nd"),
-    ("nd_order_stride", "for (long i = s; i <= N; i += 2 * s)", "for (long i = s; i <= N; i += s + 1)", "order"),
+    # (a stride mistake that writes fewer entries, so the planted copy stays in bounds)
+    ("nd_order_stride", "for (long i = s; i <= N; i += 2 * s)", "for (long i = s; i <= N; i += 4 * s)", "order"),
     ("resid_sign", "v -= B[(i - 1) * bs + r * n + c] * x[((size_t)(i - 1) * n + c) * m + col];",
      "v += B[(i - 1) * bs + r * n + c] * x[((size_t)(i - 1) * n + c) * m + col];", "resid"),
     ("resid_upper_transposed", "v -= B[i * bs + c * n + r] * x[((size_t)(i + 1) * n + c) * m + col];",
