@@ -177,6 +177,35 @@ int btc_get_factor(btc_plan_t p, void *Dhat, void *U, int *pairs);
 int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const double *x, const double *b,
                  double *out3, void *stream);
 
+/*
+ * btc_residual without any device allocation (the paper has no counterpart;
+ * this is a deployment convenience). Computes the same three numbers as
+ * btc_residual, with the same FP64 arithmetic, into out3 (host pointer), and
+ * synchronizes `stream` before returning.
+ *
+ * For callers that cannot allocate device memory: real-time control loops
+ * that forbid allocation after start-up, processes whose memory is entirely
+ * owned by another allocator (for example a framework's caching allocator)
+ * where a stray cudaMalloc could fail or fragment, and code that is not allowed
+ * to call the CUDA allocator at all. This entry point calls no cudaMalloc,
+ * cudaMallocAsync, cudaFree or allocating library routine. Its scratch (one
+ * partial triple per block row) lives in a fixed device array compiled into
+ * libbtc.so, 3 * 65536 + 3 doubles (about 1.5 MiB), which every GPU that loads
+ * the library keeps until the process exits. Hence:
+ *  - N may not exceed 65536 block rows (BTC_ERR_ARG otherwise); n up to 96
+ *    (BTC_ERR_UNSUPPORTED when the three staged blocks exceed shared memory);
+ *  - all calls share that one array: calls that overlap on the GPU (on two
+ *    streams, or from two host threads) race and may return wrong norms;
+ *    serialize them;
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins.
+ * D, B, x, b: device pointers as for btc_residual. Errors: BTC_ERR_ARG,
+ * BTC_ERR_UNSUPPORTED, BTC_ERR_CUDA (message in btc_last_error()).
+ */
+int btc_residual_noalloc(int N, int n, int nrhs, const double *D, const double *B, const double *x, const double *b,
+                         double *out3, void *stream);
+
 /* Release every device resource of the plan (synchronizes its stream). */
 int btc_free(btc_plan_t p);
 

@@ -58,6 +58,7 @@ _SIGS = {
     "btc_info": [_vp, _ip, _ip],
     "btc_get_factor": [_vp, _vp, _vp, _ip],
     "btc_residual": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
+    "btc_residual_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
     "btc_free": [_vp],
     "btc_last_error": [],
     "btc_version": [],
@@ -213,6 +214,13 @@ def btc_get_factor(plan):
 def btc_residual(N, n, nrhs, D, B, x, b, stream=None):
     out = (ctypes.c_double * 3)()
     _check(load().btc_residual(N, n, nrhs, _ptr(D), _ptr(B), _ptr(x), _ptr(b), out, _stream(stream)))
+    return out[0], out[1], out[2]
+
+
+def btc_residual_noalloc(N, n, nrhs, D, B, x, b, stream=None):
+    """btc_residual with its scratch in a fixed device array (no device allocation)."""
+    out = (ctypes.c_double * 3)()
+    _check(load().btc_residual_noalloc(N, n, nrhs, _ptr(D), _ptr(B), _ptr(x), _ptr(b), out, _stream(stream)))
     return out[0], out[1], out[2]
 
 
