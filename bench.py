@@ -179,6 +179,30 @@ def cpu_baseline_sample(budget_s=12.0, max_reps=8):
                       f"({time.perf_counter() - t_start:.1f} s, single thread)"}
 
 
+def run_profile(which):
+    """The benchmark workload without timing: warm-up pass + one pass, for ncu launch lists."""
+    import torch
+    from paper_2601_03754_gb300 import btc, build, gen
+    build.build()
+    btc.load()
+    W = WORKLOAD
+    N, n, m = W["N"], W["n"], W["nrhs"]
+    D, B = gen.bt_random(N, n, delta=W["delta"], seed=W["seed"])
+    b = gen.rhs(N, n, m, seed=W["seed"])
+    Dd, Bd, bd = (torch.from_numpy(a).cuda() for a in (D, B, b))
+    xd = torch.zeros_like(bd)
+    dts = {"mixed": [btc.MIXED_F32], "f64": [btc.F64], "both": [btc.MIXED_F32, btc.F64]}[which]
+    for dt in dts:
+        p = btc.btc_plan(N, n, dt)
+        for _ in range(2):
+            btc.btc_factor(p, Dd, Bd)
+            it, rel, rc = btc.btc_solve_refined(p, bd, xd, m, tol=TOL, maxit=30)
+        print(f"profile dtype={dt} iters={it} relres={rel:.3e}")
+        p.free()
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,7 +210,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["mixed", "f64", "both"], default=None,
+                    help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args.profile)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

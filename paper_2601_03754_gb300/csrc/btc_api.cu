@@ -82,6 +82,37 @@ __global__ void k_anorm(const double *D, const double *B, int N, int n, double *
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, best);
 }
 
+// Lower bound of ||Psi||_inf (into norms[2]) for the stopping test of the
+// refinement: each |a_ij| is rounded toward zero to FP32 and the row sums
+// accumulate with round-toward-zero additions, so the result never exceeds the
+// exact norm and the test ||r|| <= tol ||Psi|| ||x|| is never met early.
+__global__ void k_anorm_lb(const double *D, const double *B, int N, int n, double *norms) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i = blockIdx.x;
+  const int ld = f64_ld(n);
+  double *Ds = reinterpret_cast<double *>(smem_raw);
+  double *Bl = Ds + n * ld;
+  double *Br = Bl + n * ld;
+  const size_t bs = (size_t)n * n;
+  stage_f64(Ds, D + i * bs, n);
+  if (i > 0) stage_f64(Bl, B + (i - 1) * bs, n);
+  if (i + 1 < N) stage_f64(Br, B + i * bs, n);
+  cp_async_wait_all_s();
+  __syncthreads();
+  float best = 0.0f;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    float s = 0.0f;
+    for (int c = 0; c < n; ++c) s = __fadd_rz(s, __double2float_rz(fabs(r >= c ? Ds[r * ld + c] : Ds[c * ld + r])));
+    if (i > 0)
+      for (int c = 0; c < n; ++c) s = __fadd_rz(s, __double2float_rz(fabs(Bl[r * ld + c])));
+    if (i + 1 < N)
+      for (int c = 0; c < n; ++c) s = __fadd_rz(s, __double2float_rz(fabs(Br[c * ld + r])));
+    best = fmaxf(best, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, (double)best);
+}
+
 static bool dtype_ok(int dtype) { return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32; }
 
 static constexpr int kMaxCols = 16;  // right-hand sides per solve launch
@@ -301,7 +332,8 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   if ((rc = set_smem(ks.fac_first, ks.fac_smem)) || (rc = set_smem(ks.fac_rest, ks.fac_smem)) ||
       (rc = set_smem(ks.root_first, ks.root_smem)) || (rc = set_smem(ks.root_rest, ks.root_smem)) ||
       (rc = set_smem(ks.fwd, ks.fwd_smem(kMaxCols))) || (rc = set_smem(ks.bwd, ks.bwd_smem(kMaxCols))) ||
-      (rc = set_smem(ks.resid, 3 * sizeof(double) * (size_t)n * (n + 1))))
+      (rc = set_smem(ks.resid, 3 * sizeof(double) * (size_t)n * f64_ld(n))) ||
+      (rc = set_smem((const void *)&k_anorm_lb, 3 * sizeof(double) * (size_t)n * f64_ld(n))))
     return cleanup(rc);
   *out = p;
   return BTC_OK;
@@ -373,12 +405,13 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
   if (rc) return fail(rc, "factorization failed: pivot of block %d, column %d not positive", blk, col);
   if (!p->anorm_valid) {
     BTC_CUDA(cudaMemsetAsync(p->d_norms + 2, 0, sizeof(double), p->stream));
-    if ((rc = launch_n((const void *)&k_anorm, p->N, 64, 0, p->stream, (const double *)p->D, (const double *)p->B,
-                       p->N, p->n, p->d_norms)))
+    const size_t asm_ = 3 * sizeof(double) * (size_t)p->n * f64_ld(p->n);
+    if ((rc = launch_n((const void *)&k_anorm_lb, p->N, 128, asm_, p->stream, (const double *)p->D,
+                       (const double *)p->B, p->N, p->n, p->d_norms)))
       return rc;
     p->anorm_valid = true;
   }
-  const size_t rsm = 3 * sizeof(double) * (size_t)p->n * (p->n + 1);
+  const size_t rsm = 3 * sizeof(double) * (size_t)p->n * f64_ld(p->n);
   int worst_it = 0;
   double worst_rel = 0.0;
   bool all_ok = true;
@@ -494,9 +527,11 @@ int btc_get_factor(btc_plan_t p, void *Dhat, void *U, int *pairs) {
   if (Dhat) {
     std::vector<char> buf(bs * p->N);
     BTC_CUDA(cudaMemcpy(buf.data(), p->dpool, buf.size(), cudaMemcpyDeviceToHost));
+    // the pool holds the upper factor U_e = L(e,e)^T: transpose on the way out
     for (int i = 0; i < p->N; ++i)
       for (size_t r = 0; r < n; ++r)
-        memcpy((char *)Dhat + ((size_t)i * n * n + r * n) * w, buf.data() + i * bs + r * np * w, n * w);
+        for (size_t c = 0; c < n; ++c)
+          memcpy((char *)Dhat + ((size_t)i * n * n + r * n + c) * w, buf.data() + i * bs + (c * np + r) * w, w);
   }
   if (U && p->hp.offdiag > 0) {
     std::vector<char> buf(bs * p->hp.offdiag);
@@ -522,7 +557,7 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
   BTC_CUDA(cudaMallocAsync((void **)&d, 3 * sizeof(double), s));
   int rc = BTC_OK;
   cudaError_t e = cudaMemsetAsync(d, 0, 3 * sizeof(double), s);
-  const size_t rsm = 3 * sizeof(double) * (size_t)n * (n + 1);
+  const size_t rsm = 3 * sizeof(double) * (size_t)n * f64_ld(n);
   const void *rk = (const void *)&k_residual<double>;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
   if (e == cudaSuccess) {

@@ -9,7 +9,7 @@ namespace btc {
 // Register tile edge per padded block size: (np/R)^2 threads per CTA.
 template <int NP>
 struct TileEdge {
-  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : NP == 48 ? 3 : 4;
+  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : 4;
 };
 
 template <typename T, int NP>

@@ -13,31 +13,53 @@ namespace btc {
 
 constexpr int kSolveThreads = 128;
 
-template <int NP>
+template <typename T, int NP>
 struct SolveCfg {
-  static constexpr int LDL = NP + 1;  // padded leading dimension: conflict-free row and column reads
+  // padded leading dimension; rows stay 16-byte aligned for cp.async
+  static constexpr int LDL = NP + 16 / (int)sizeof(T);
 };
+
+__device__ __forceinline__ void cp_async16_s(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_s() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_bcast(T v, int lane) {
   return __shfl_sync(0xffffffffu, v, lane);
 }
 
-// Dense lower block L (np x np, row-major, global) -> shared memory with
-// leading dimension NP+1, and 1/L_jj into dinv.
+// Pool block (np x np, row-major) -> shared memory with leading dimension LDL,
+// by cp.async (completes at cp_async_wait_all_s() + __syncthreads()).
 template <typename T, int NP>
-__device__ __forceinline__ void stage_lower(T *Ls, T *dinv, const T *g) {
-  constexpr int LDL = SolveCfg<NP>::LDL;
-  for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) Ls[(q / NP) * LDL + q % NP] = g[q];
-  __syncthreads();
-  for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Ls[j * LDL + j];
+__device__ __forceinline__ void stage_block(T *dst, const T *g) {
+  constexpr int LDL = SolveCfg<T, NP>::LDL;
+  constexpr int V = 16 / sizeof(T);
+  constexpr int CPR = NP / V;
+  constexpr int CHUNKS = NP * CPR;
+#pragma unroll 4
+  for (int q = threadIdx.x; q < CHUNKS; q += kSolveThreads) {
+    const int row = q / CPR, col = (q % CPR) * V;
+    cp_async16_s(dst + row * LDL + col, g + (size_t)row * NP + col);
+  }
 }
 
-// y <- L^{-1} y for the m columns of Y (np x m in shared memory), by warps:
-// warp w takes columns w, w + nwarps, ...; lane t holds rows t and t + 32.
+// Contiguous vector of `count` elements (count * sizeof(T) a multiple of 16) -> shared memory.
+template <typename T>
+__device__ __forceinline__ void stage_vec(T *dst, const T *g, int count) {
+  constexpr int V = 16 / sizeof(T);
+  for (int q = threadIdx.x; q < count / V; q += blockDim.x) cp_async16_s(dst + q * V, g + q * V);
+}
+
+// Y <- U^{-T} Y (forward, with the upper factor U) for the m columns of Y
+// (np x m in shared memory), by warps: warp w takes columns w, w + nwarps, ...;
+// lane t holds rows t and t + 32. Row j of U is read (U[j][i], i > j).
 template <typename T, int NP>
-__device__ __forceinline__ void warp_trsv_lower(T *Y, int m, const T *Ls, const T *dinv) {
-  constexpr int LDL = SolveCfg<NP>::LDL;
+__device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *dinv) {
+  constexpr int LDL = SolveCfg<T, NP>::LDL;
   constexpr int RPL = (NP + 31) / 32;  // rows per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = warp; q < m; q += nw) {
@@ -49,12 +71,12 @@ __device__ __forceinline__ void warp_trsv_lower(T *Y, int m, const T *Ls, const 
     }
 #pragma unroll 4
     for (int j = 0; j < NP; ++j) {
-      const T yj = warp_bcast((RPL == 1 || j < 32) ? v[0] : v[RPL - 1], j & 31) * dinv[j];
+      const T zj = warp_bcast((RPL == 1 || j < 32) ? v[0] : v[RPL - 1], j & 31) * dinv[j];
 #pragma unroll
       for (int s = 0; s < RPL; ++s) {
         const int i = lane + 32 * s;
-        if (i > j && i < NP) v[s] = fma(-Ls[i * LDL + j], yj, v[s]);
-        if (i == j) v[s] = yj;
+        if (i > j && i < NP) v[s] = fma(-Us[j * LDL + i], zj, v[s]);
+        if (i == j) v[s] = zj;
       }
     }
 #pragma unroll
@@ -65,10 +87,10 @@ __device__ __forceinline__ void warp_trsv_lower(T *Y, int m, const T *Ls, const 
   }
 }
 
-// x <- L^{-T} x (backward substitution with the transpose).
+// Y <- U^{-1} Y (backward substitution with the upper factor; column j of U read).
 template <typename T, int NP>
-__device__ __forceinline__ void warp_trsv_lower_t(T *Y, int m, const T *Ls, const T *dinv) {
-  constexpr int LDL = SolveCfg<NP>::LDL;
+__device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *dinv) {
+  constexpr int LDL = SolveCfg<T, NP>::LDL;
   constexpr int RPL = (NP + 31) / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = warp; q < m; q += nw) {
@@ -84,7 +106,7 @@ __device__ __forceinline__ void warp_trsv_lower_t(T *Y, int m, const T *Ls, cons
 #pragma unroll
       for (int s = 0; s < RPL; ++s) {
         const int i = lane + 32 * s;
-        if (i < j) v[s] = fma(-Ls[j * LDL + i], xj, v[s]);
+        if (i < j) v[s] = fma(-Us[i * LDL + j], xj, v[s]);
         if (i == j) v[s] = xj;
       }
     }
@@ -106,60 +128,67 @@ struct SolveArgs {
 };
 
 // Forward step of one level (pull form): one CTA per surviving node j.
+//   y_j -= U(j-h, j)^T y_{j-h} + U(j+h, j)^T y_{j+h}   (contributions of level l-1)
+//   y_j <- U_j^{-T} y_j                                 (if j is eliminated at level l)
 template <typename T, int NP>
 __global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
-  constexpr int LDL = SolveCfg<NP>::LDL;
+  constexpr int LDL = SolveCfg<T, NP>::LDL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
-  T *Ls = reinterpret_cast<T *>(smem_raw);  // NP * LDL
-  T *dinv = Ls + NP * LDL;                  // NP
+  T *Us = reinterpret_cast<T *>(smem_raw);  // U_j
+  T *Ul = Us + NP * LDL;                    // U(j-h, j)
+  T *Ur = Ul + NP * LDL;                    // U(j+h, j)
+  T *dinv = Ur + NP * LDL;                  // NP
   T *ys = dinv + NP;                        // NP*m
-  T *yl = ys + NP * m;                      // NP*m
-  T *yr = yl + NP * m;                      // NP*m
+  T *yl = ys + NP * m;
+  T *yr = yl + NP * m;
   const FwdItem it = reinterpret_cast<const FwdItem *>(a.items)[blockIdx.x];
   T *y = reinterpret_cast<T *>(a.y);
   const T *dpool = reinterpret_cast<const T *>(a.dpool);
   const T *epool = reinterpret_cast<const T *>(a.epool);
   const int nm = NP * m;
   T *yself = y + it.y_self * nm;
-  for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-    ys[q] = yself[q];
-    if (it.y_l >= 0) yl[q] = y[it.y_l * nm + q];
-    if (it.y_r >= 0) yr[q] = y[it.y_r * nm + q];
-  }
-  if (it.d_self >= 0) stage_lower<T, NP>(Ls, dinv, dpool + it.d_self);
+  if (it.d_self >= 0) stage_block<T, NP>(Us, dpool + it.d_self);
+  if (it.y_l >= 0) stage_block<T, NP>(Ul, epool + it.e_l);
+  if (it.y_r >= 0) stage_block<T, NP>(Ur, epool + it.e_r);
+  stage_vec<T>(ys, yself, nm);
+  if (it.y_l >= 0) stage_vec<T>(yl, y + it.y_l * nm, nm);
+  if (it.y_r >= 0) stage_vec<T>(yr, y + it.y_r * nm, nm);
+  cp_async_wait_all_s();
   __syncthreads();
+  if (it.d_self >= 0)
+    for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
   if (it.y_l >= 0) {
-    const T *Ul = epool + it.e_l;
-    const T *Ur = it.y_r >= 0 ? epool + it.e_r : nullptr;
+    const bool right = it.y_r >= 0;
     for (int q = threadIdx.x; q < nm; q += blockDim.x) {
       const int c = q / m, col = q % m;
       T acc = ys[q];
 #pragma unroll 8
-      for (int r = 0; r < NP; ++r) acc = fma(-Ul[r * NP + c], yl[r * m + col], acc);
-      if (Ur)
+      for (int r = 0; r < NP; ++r) acc = fma(-Ul[r * LDL + c], yl[r * m + col], acc);
+      if (right)
 #pragma unroll 8
-        for (int r = 0; r < NP; ++r) acc = fma(-Ur[r * NP + c], yr[r * m + col], acc);
+        for (int r = 0; r < NP; ++r) acc = fma(-Ur[r * LDL + c], yr[r * m + col], acc);
       ys[q] = acc;
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (it.d_self >= 0) {
-    warp_trsv_lower<T, NP>(ys, m, Ls, dinv);
+    warp_trsv_ut<T, NP>(ys, m, Us, dinv);
     __syncthreads();
   }
   for (int q = threadIdx.x; q < nm; q += blockDim.x) yself[q] = ys[q];
 }
 
 // Backward step of one level: one CTA per eliminated node e.
+//   x_e <- U_e^{-1} (y_e - U(e, e+s) x_{e+s} - U(e, e-s) x_{e-s})
 template <typename T, int NP>
 __global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
-  constexpr int LDL = SolveCfg<NP>::LDL;
+  constexpr int LDL = SolveCfg<T, NP>::LDL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
-  T *Ls = reinterpret_cast<T *>(smem_raw);  // NP * LDL
-  T *Ud = Ls + NP * LDL;                    // NP * LDL
-  T *Uu = Ud + NP * LDL;                    // NP * LDL
+  T *Us = reinterpret_cast<T *>(smem_raw);  // U_e
+  T *Ud = Us + NP * LDL;                    // U(e, e+s)
+  T *Uu = Ud + NP * LDL;                    // U(e, e-s)
   T *dinv = Uu + NP * LDL;                  // NP
   T *ys = dinv + NP;                        // NP*m
   T *xd = ys + NP * m;
@@ -170,44 +199,42 @@ __global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
   const T *epool = reinterpret_cast<const T *>(a.epool);
   const int nm = NP * m;
   T *yself = y + it.x_self * nm;
-  for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-    ys[q] = yself[q];
-    if (it.x_dn >= 0) xd[q] = y[it.x_dn * nm + q];
-    if (it.x_up >= 0) xu[q] = y[it.x_up * nm + q];
-  }
-  for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) {
-    const int r = q / NP, c = q % NP;
-    if (it.x_dn >= 0) Ud[r * LDL + c] = epool[it.e_dn + q];
-    if (it.x_up >= 0) Uu[r * LDL + c] = epool[it.e_up + q];
-  }
-  stage_lower<T, NP>(Ls, dinv, dpool + it.d_self);
+  stage_block<T, NP>(Us, dpool + it.d_self);
+  if (it.x_dn >= 0) stage_block<T, NP>(Ud, epool + it.e_dn);
+  if (it.x_up >= 0) stage_block<T, NP>(Uu, epool + it.e_up);
+  stage_vec<T>(ys, yself, nm);
+  if (it.x_dn >= 0) stage_vec<T>(xd, y + it.x_dn * nm, nm);
+  if (it.x_up >= 0) stage_vec<T>(xu, y + it.x_up * nm, nm);
+  cp_async_wait_all_s();
   __syncthreads();
+  for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
   if (it.x_dn >= 0 || it.x_up >= 0) {
+    const bool dn = it.x_dn >= 0, up = it.x_up >= 0;
     for (int q = threadIdx.x; q < nm; q += blockDim.x) {
       const int r = q / m, col = q % m;
       T acc = ys[q];
-      if (it.x_dn >= 0)
+      if (dn)
 #pragma unroll 8
         for (int c = 0; c < NP; ++c) acc = fma(-Ud[r * LDL + c], xd[c * m + col], acc);
-      if (it.x_up >= 0)
+      if (up)
 #pragma unroll 8
         for (int c = 0; c < NP; ++c) acc = fma(-Uu[r * LDL + c], xu[c * m + col], acc);
       ys[q] = acc;
     }
-    __syncthreads();
   }
-  warp_trsv_lower_t<T, NP>(ys, m, Ls, dinv);
+  __syncthreads();
+  warp_trsv_u<T, NP>(ys, m, Us, dinv);
   __syncthreads();
   for (int q = threadIdx.x; q < nm; q += blockDim.x) yself[q] = ys[q];
 }
 
 template <typename T, int NP>
 constexpr size_t fwd_smem_bytes(int m) {
-  return sizeof(T) * ((size_t)NP * SolveCfg<NP>::LDL + NP + 3 * (size_t)NP * m);
+  return sizeof(T) * (3 * (size_t)NP * SolveCfg<T, NP>::LDL + NP + 3 * (size_t)NP * m);
 }
 template <typename T, int NP>
 constexpr size_t bwd_smem_bytes(int m) {
-  return sizeof(T) * (3 * (size_t)NP * SolveCfg<NP>::LDL + NP + 3 * (size_t)NP * m);
+  return sizeof(T) * (3 * (size_t)NP * SolveCfg<T, NP>::LDL + NP + 3 * (size_t)NP * m);
 }
 
 // ---------------------------------------------------------------- vectors
@@ -243,6 +270,39 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// Leading dimension of a staged n x n FP64 block: rows 16-byte aligned when n is even.
+__host__ __device__ constexpr int f64_ld(int n) { return (n % 2 == 0) ? n + 2 : n + 1; }
+
+// Copy an n x n FP64 block (row-major, contiguous) into shared memory with
+// leading dimension f64_ld(n): cp.async of 16-byte chunks when n is even (the
+// block and its rows are then 16-byte aligned), batched scalar loads otherwise.
+// Completes at cp_async_wait_all_s() + __syncthreads().
+__device__ __forceinline__ void stage_f64(double *dst, const double *src, int n) {
+  const int ld = f64_ld(n);
+  if (n % 2 == 0) {
+    const int cpr = n / 2, total = n * cpr;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int row = q / cpr, col = (q % cpr) * 2;
+      cp_async16_s(dst + row * ld + col, src + (size_t)row * n + col);
+    }
+    return;
+  }
+  const int total = n * n;
+  for (int base = threadIdx.x; base < total; base += 8 * blockDim.x) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = base + u * blockDim.x;
+      v[u] = q < total ? __ldg(src + q) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = base + u * blockDim.x;
+      if (q < total) dst[(q / n) * ld + q % n] = v[u];
+    }
+  }
+}
+
 // r = b - Psi x in FP64 for one block row per CTA; writes r (converted to T)
 // into the padded work vector y when y != nullptr, and max|r|, max|x| into
 // norms[0], norms[1]. D: lower triangles read.
@@ -251,23 +311,21 @@ __global__ void k_residual(T *y, const double *D, const double *B, const double 
                            int np, int m, int64_t node_base, double *norms) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i = blockIdx.x;
-  const int ld = n + 1;
+  const int ld = f64_ld(n);
   double *Ds = reinterpret_cast<double *>(smem_raw);
   double *Bl = Ds + n * ld;  // B_{i-1}: row i's left block
   double *Br = Bl + n * ld;  // B_i:     transposed: row i's right block
   const size_t bs = (size_t)n * n;
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-    const int r = q / n, c = q % n;
-    Ds[r * ld + c] = D[i * bs + q];
-    if (i > 0) Bl[r * ld + c] = B[(i - 1) * bs + q];
-    if (i + 1 < N) Br[r * ld + c] = B[i * bs + q];
-  }
+  stage_f64(Ds, D + i * bs, n);
+  if (i > 0) stage_f64(Bl, B + (i - 1) * bs, n);
+  if (i + 1 < N) stage_f64(Br, B + i * bs, n);
+  cp_async_wait_all_s();
   __syncthreads();
   double rmax = 0.0, xmax = 0.0;
+  const double *xi = x + (size_t)i * n * m;
   for (int q = threadIdx.x; q < n * m; q += blockDim.x) {
     const int r = q / m, col = q % m;
     double v = b[((size_t)i * n + r) * m + col];
-    const double *xi = x + (size_t)i * n * m;
     for (int c = 0; c < n; ++c) v = fma(-(r >= c ? Ds[r * ld + c] : Ds[c * ld + r]), xi[c * m + col], v);
     if (i > 0) {
       const double *xp = x + (size_t)(i - 1) * n * m;

@@ -1,11 +1,18 @@
-// Register-tiled block operations on one padded np x np block per CTA.
+// Block operations on padded np x np blocks held in shared memory, for one
+// CTA per node elimination.
 //
-// Thread layout: the CTA's NT = (NP/R)^2 threads form a (NP/R) x (NP/R) grid;
-// thread (ty, tx) owns the R x R tile of rows [ty*R, ty*R+R) and columns
-// [tx*R, tx*R+R) of every np x np operand and keeps it in registers.
-// Shared-memory copies of blocks use a padded leading dimension LD so that the
-// row reads of the X^T Y products and the transposed writes are bank-conflict
-// free (rows stay 16-byte aligned).
+// Thread layout for the dense products: the CTA's NT = (NP/R)^2 threads form a
+// (NP/R) x (NP/R) grid; thread (ty, tx) owns the R x R register tile of rows
+// [ty*R, ty*R+R) and columns [tx*R, tx*R+R). Every product of the elimination
+// is written as C -= X^T Y (row reads of X and Y only), which is the
+// bank-conflict-free access pattern for row-major blocks with the padded
+// leading dimension LD.
+//
+// The Cholesky factor is kept in UPPER form, S = U^T U (U = L^T), so that the
+// blocked factorization and the triangular solves are also X^T Y products:
+//   panel row:      U[p, j>p] = U_pp^{-T} S[p, j]        (column-wise substitution)
+//   trailing:       S[i, j]  -= U[p, i]^T U[p, j]        (X^T Y, K = panel width)
+//   solve:          Z = U^{-T} R                          (same two steps on R)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,8 +27,11 @@ struct TileCfg {
   static constexpr int NT = TXN * TXN;
   static constexpr int PAD = sizeof(T) == 4 ? 4 : 2;
   static constexpr int LD = NP + PAD;
-  static constexpr int BLK = NP * LD;  // elements of one shared-memory block
+  static constexpr int BLK = NP * LD;            // elements of one shared-memory block
+  static constexpr int PB = NP >= 16 ? 16 : NP;  // panel width of the blocked factorization
+  static constexpr int NPAN = NP / PB;
   static_assert(NP % R == 0, "tile must divide the block");
+  static_assert(NP % PB == 0 && PB % R == 0, "panels must align with tiles");
 };
 
 // ---------------------------------------------------------------- vector io
@@ -84,8 +94,136 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[R]) {
   }
 }
 
-// ------------------------------------------------------------ tile transfer
-// Global pool block (np x np, row-major, contiguous; element type P) -> registers (type T).
+// ------------------------------------------------------------ async copies
+// 16-byte global -> shared copy that bypasses registers (cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+
+// ------------------------------------------------------------ block transfer
+// Pool block (np x np, type T) -> padded shared memory (same type) with cp.async;
+// completes at cp_async_commit_wait_all() + __syncthreads().
+template <class C, typename T>
+__device__ __forceinline__ void block_to_smem_async(T *s, const T *g) {
+  constexpr int V = 16 / sizeof(T);
+  constexpr int CPR = C::NP / V;
+  constexpr int TOTAL = C::NP * CPR;
+#pragma unroll
+  for (int q = threadIdx.x; q < TOTAL; q += C::NT) {
+    const int row = q / CPR, col = (q % CPR) * V;
+    cp_async16(s + row * C::LD + col, g + (size_t)row * C::NP + col);
+  }
+}
+
+// Pool block (np x np, row-major, element type P) -> padded shared memory (type T),
+// cooperative 16-byte loads, all issued before any store.
+template <class C, typename T, typename P>
+__device__ __forceinline__ void block_to_smem(T *s, const P *g) {
+  constexpr int V = 16 / sizeof(P);  // source elements per 16-byte chunk
+  constexpr int CPR = C::NP / V;     // chunks per row
+  constexpr int TOTAL = C::NP * CPR;
+  constexpr int ITER = (TOTAL + C::NT - 1) / C::NT;
+  float4 raw[ITER];
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int q = threadIdx.x + it * C::NT;
+    if (q < TOTAL) {
+      const int row = q / CPR, col = (q % CPR) * V;
+      raw[it] = __ldg(reinterpret_cast<const float4 *>(g + (size_t)row * C::NP + col));
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int q = threadIdx.x + it * C::NT;
+    if (q < TOTAL) {
+      const int row = q / CPR, col = (q % CPR) * V;
+      const P *src = reinterpret_cast<const P *>(&raw[it]);
+      if constexpr (sizeof(T) == sizeof(P)) {
+        *reinterpret_cast<float4 *>(s + row * C::LD + col) = raw[it];
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) s[row * C::LD + col + i] = (T)src[i];
+      }
+    }
+  }
+}
+
+// Padded shared memory (type T) -> pool block (type P), cooperative.
+// lower_zero: write zeros below the diagonal (the final U factor).
+template <class C, typename T, typename P>
+__device__ __forceinline__ void smem_to_block(P *g, const T *s, bool lower_zero) {
+  constexpr int V = 16 / sizeof(P);
+  constexpr int CPR = C::NP / V;
+  constexpr int TOTAL = C::NP * CPR;
+  for (int q = threadIdx.x; q < TOTAL; q += C::NT) {
+    const int row = q / CPR, col = (q % CPR) * V;
+    float4 raw;
+    P *dst = reinterpret_cast<P *>(&raw);
+#pragma unroll
+    for (int i = 0; i < V; ++i) dst[i] = (lower_zero && col + i < row) ? P(0) : (P)s[row * C::LD + col + i];
+    *reinterpret_cast<float4 *>(g + (size_t)row * C::NP + col) = raw;
+  }
+}
+
+// Caller's block (n x n row-major, type S) -> padded shared memory (type T).
+// trans: element (i, k) of the result is src(k, i). Padding: `diag` on the
+// padded diagonal, 0 elsewhere.
+template <class C, typename T, typename S>
+__device__ __forceinline__ void user_to_smem(T *s, const S *src, int n, bool trans, T diag) {
+  constexpr int TOTAL = C::NP * C::NP;
+  for (int q = threadIdx.x; q < TOTAL; q += C::NT) {
+    // consecutive threads read consecutive source elements
+    const int a = q / C::NP, b = q % C::NP;  // source row a, column b
+    T v;
+    if (a < n && b < n) v = (T)__ldg(src + (size_t)a * n + b);
+    else v = (a == b) ? diag : T(0);
+    if (trans) s[b * C::LD + a] = v;
+    else s[a * C::LD + b] = v;
+  }
+}
+
+// Caller's block (n x n row-major, type S) -> one register tile, padded like
+// user_to_smem. trans: element (i, k) is src(k, i).
+template <class C, typename T, typename S>
+__device__ __forceinline__ void tile_from_user(T (&a)[C::R][C::R], const S *src, int n, int r0, int c0, bool trans,
+                                               T diag) {
+#pragma unroll
+  for (int r = 0; r < C::R; ++r)
+#pragma unroll
+    for (int c = 0; c < C::R; ++c) {
+      const int i = r0 + r, k = c0 + c;
+      T v;
+      if (i < n && k < n) v = (T)(trans ? __ldg(src + (size_t)k * n + i) : __ldg(src + (size_t)i * n + k));
+      else v = (i == k) ? diag : T(0);
+      a[r][c] = v;
+    }
+}
+
+// ------------------------------------------------------------ tile algebra
+template <class C, typename T>
+__device__ __forceinline__ void tile_zero(T (&a)[C::R][C::R]) {
+#pragma unroll
+  for (int r = 0; r < C::R; ++r)
+#pragma unroll
+    for (int c = 0; c < C::R; ++c) a[r][c] = T(0);
+}
+
+template <class C, typename T>
+__device__ __forceinline__ void tile_from_smem(T (&a)[C::R][C::R], const T *s, int r0, int c0) {
+#pragma unroll
+  for (int r = 0; r < C::R; ++r) vload<T, C::R>(s + (r0 + r) * C::LD + c0, a[r]);
+}
+
+template <class C, typename T>
+__device__ __forceinline__ void tile_to_smem(T *s, const T (&a)[C::R][C::R], int r0, int c0) {
+#pragma unroll
+  for (int r = 0; r < C::R; ++r) vstore<T, C::R>(s + (r0 + r) * C::LD + c0, a[r]);
+}
+
 template <class C, typename T, typename P>
 __device__ __forceinline__ void tile_from_pool(T (&a)[C::R][C::R], const P *g, int r0, int c0) {
 #pragma unroll
@@ -108,55 +246,13 @@ __device__ __forceinline__ void tile_to_pool(P *g, const T (&a)[C::R][C::R], int
   }
 }
 
-template <class C, typename T>
-__device__ __forceinline__ void tile_to_smem(T *s, const T (&a)[C::R][C::R], int r0, int c0) {
-#pragma unroll
-  for (int r = 0; r < C::R; ++r) vstore<T, C::R>(s + (r0 + r) * C::LD + c0, a[r]);
-}
-
-// User block (n x n row-major, source type S) -> registers, padded to np with
-// `diag` on the padded diagonal and 0 elsewhere. trans: read element (k, i).
-template <class C, typename T, typename S>
-__device__ __forceinline__ void tile_from_user(T (&a)[C::R][C::R], const S *src, int n, int r0, int c0, bool trans,
-                                               T diag) {
-#pragma unroll
-  for (int r = 0; r < C::R; ++r)
-#pragma unroll
-    for (int c = 0; c < C::R; ++c) {
-      const int i = r0 + r, k = c0 + c;
-      T v;
-      if (i < n && k < n)
-        v = (T)(trans ? __ldg(src + (size_t)k * n + i) : __ldg(src + (size_t)i * n + k));
-      else
-        v = (i == k) ? diag : T(0);
-      a[r][c] = v;
-    }
-}
-
-// Cooperative copy of a pool block (type P) into padded shared memory (type T).
-template <class C, typename T, typename P>
-__device__ __forceinline__ void block_to_smem(T *s, const P *g) {
-  constexpr int V = 16 / sizeof(P);  // source elements per 16-byte chunk
-  constexpr int CPR = C::NP / V;     // chunks per row
-  for (int q = threadIdx.x; q < C::NP * CPR; q += C::NT) {
-    const int row = q / CPR, col = (q % CPR) * V;
-    const float4 raw = __ldg(reinterpret_cast<const float4 *>(g + (size_t)row * C::NP + col));
-    const P *src = reinterpret_cast<const P *>(&raw);
-    if constexpr (sizeof(T) == sizeof(P)) {
-      *reinterpret_cast<float4 *>(s + row * C::LD + col) = raw;
-    } else {
-#pragma unroll
-      for (int i = 0; i < V; ++i) s[row * C::LD + col + i] = (T)src[i];
-    }
-  }
-}
-
-// ------------------------------------------------------------ block algebra
-// a -= X^T Y over k = 0..np-1 (X, Y in shared memory): a[r][c] -= sum_k X[k][r0+r] Y[k][c0+c].
-template <class C, typename T>
-__device__ __forceinline__ void tile_sub_xty(T (&a)[C::R][C::R], const T *X, const T *Y, int r0, int c0) {
+// a -= X^T Y over k in [k0, k0 + KLEN): a[r][c] -= sum_k X[k][r0+r] Y[k][c0+c].
+template <class C, int KLEN, typename T>
+__device__ __forceinline__ void tile_sub_xty(T (&a)[C::R][C::R], const T *X, const T *Y, int r0, int c0,
+                                             int k0 = 0) {
 #pragma unroll 4
-  for (int k = 0; k < C::NP; ++k) {
+  for (int kk = 0; kk < KLEN; ++kk) {
+    const int k = k0 + kk;
     T x[C::R], y[C::R];
     vload<T, C::R>(X + k * C::LD + r0, x);
     vload<T, C::R>(Y + k * C::LD + c0, y);
@@ -172,106 +268,185 @@ __device__ __forceinline__ unsigned long long pack_info(int node, int col) {
   return ((unsigned long long)(unsigned)node << 20) | (unsigned)col;
 }
 
-// In-register Cholesky of the symmetric block held by the lower tiles (ty >= tx):
-// right-looking, one column per step, one barrier per step. Step j publishes
-// column j (double-buffered in colbuf[2][np]) and every owner of an element
-// (i, k) with i >= k > j applies a_ik -= a_ij a_kj / a_jj; the columns are
-// scaled by 1/sqrt(pivot) at the end, giving L = chol(S) in `a` (zeros above
-// the diagonal). Also writes L^T into LT (shared, padded) and 1/L_jj into dinv.
-// A pivot that is not positive is reported through *info and replaced by 1
-// so that the remaining arithmetic stays finite.
+// ----------------------------------------------------- blocked factorization
+// Unblocked upper Cholesky of the PB x PB diagonal block at (p0, p0) of S, by
+// one warp (shared memory + __syncwarp). Right-looking with unscaled rows:
+// step k applies S[t][j] -= S[k][t] S[k][j] / d_k for k < t <= j, and the rows
+// are scaled by 1/sqrt(d_k) at the end. Writes dinv[p0+k] = 1/U_kk. A pivot
+// that is not positive (or NaN) is reported and replaced by 1 so that the
+// remaining arithmetic stays finite. Must be called by all lanes of one warp.
 template <class C, typename T>
-__device__ __forceinline__ void tile_potrf(T (&a)[C::R][C::R], int r0, int c0, bool lower, T *colbuf, T *LT,
-                                           T *dinv, unsigned long long *info, int node) {
-  constexpr int R = C::R;
-  T piv_own[R];
+__device__ __forceinline__ void warp_chol_diag(T *S, int p0, T *dinv, unsigned long long *info, int node) {
+  constexpr int PB = C::PB;
+  constexpr int LD = C::LD;
+  constexpr int MAXE = PB * (PB + 1) / 2;  // upper-triangle elements of the diagonal block
+  constexpr int NE = (MAXE + 31) / 32;     // per lane
+  const int lane = threadIdx.x & 31;
+  T *B = S + p0 * LD + p0;
+  // this lane's elements (t, j), t <= j, of the upper triangle
+  int tt[NE], jj[NE];
 #pragma unroll
-  for (int c = 0; c < R; ++c) piv_own[c] = T(1);
-  for (int j = 0; j < C::NP; ++j) {
-    T *cb = colbuf + (j & 1) * C::NP;
-    if (lower && j >= c0 && j < c0 + R) {
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int c = 0; c < R; ++c)
-          if (c0 + c == j) cb[r0 + r] = a[r][c];
+  for (int i = 0; i < NE; ++i) {
+    int q = lane + 32 * i, t = 0;
+    if (q >= MAXE) {
+      tt[i] = -1;
+      jj[i] = 0;
+      continue;
     }
-    __syncthreads();
-    T piv = cb[j];
-    if (!(piv > T(0))) {
-      if (threadIdx.x == 0 && info) atomicMin(info, pack_info(node, j));
-      piv = T(1);
+    while (q >= PB - t) {
+      q -= PB - t;
+      ++t;
     }
+    tt[i] = t;
+    jj[i] = t + q;
+  }
+  for (int k = 0; k < PB; ++k) {
+    T d = B[k * LD + k];
+    if (!(d > T(0))) {  // uniform across the warp
+      if (lane == 0 && info) atomicMin(info, pack_info(node, p0 + k));
+      d = T(1);
+      __syncwarp();
+      if (lane == 0) B[k * LD + k] = T(1);
+    }
+    const T inv = T(1) / d;
 #pragma unroll
-    for (int c = 0; c < R; ++c)
-      if (c0 + c == j) piv_own[c] = piv;
-    if (lower) {
-      const T inv = T(1) / piv;
-      T ci[R], ck[R];
+    for (int i = 0; i < NE; ++i)
+      if (tt[i] > k) B[tt[i] * LD + jj[i]] = fma(-B[k * LD + tt[i]] * inv, B[k * LD + jj[i]], B[tt[i] * LD + jj[i]]);
+    __syncwarp();
+  }
+  // scale rows: U_kj = S_kj / sqrt(d_k), U_kk = sqrt(d_k)
+  for (int k = lane; k < PB; k += 32) dinv[p0 + k] = T(1) / sqrt(B[k * LD + k]);
+  __syncwarp();
 #pragma unroll
-      for (int r = 0; r < R; ++r) ci[r] = cb[r0 + r] * inv;
+  for (int i = 0; i < NE; ++i) {
+    const int t = tt[i], j = jj[i];
+    if (t >= 0) B[t * LD + j] = (t == j) ? sqrt(B[t * LD + t]) : B[t * LD + j] * dinv[p0 + t];
+  }
+  __syncwarp();
+}
+
+// Column-wise forward substitution with the transposed diagonal block:
+// X[p0 .. p0+PB)[col] <- U_pp^{-T} X[p0 .. p0+PB)[col] for one column of a
+// shared-memory block X (U_pp read from S, reciprocal diagonal from dinv).
+template <class C, typename T>
+__device__ __forceinline__ void col_subst_ut(T *X, int col, const T *S, const T *dinv, int p0) {
+  constexpr int PB = C::PB;
+  constexpr int LD = C::LD;
+  T w[PB];
 #pragma unroll
-      for (int c = 0; c < R; ++c) ck[c] = cb[c0 + c];
+  for (int t = 0; t < PB; ++t) w[t] = X[(p0 + t) * LD + col];
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+  for (int t = 0; t < PB; ++t) {
+    w[t] *= dinv[p0 + t];
 #pragma unroll
-        for (int c = 0; c < R; ++c)
-          if (c0 + c > j && r0 + r >= c0 + c) a[r][c] = fma(-ci[r], ck[c], a[r][c]);
+    for (int u = t + 1; u < PB; ++u) w[u] = fma(-S[(p0 + t) * LD + p0 + u], w[t], w[u]);
+  }
+#pragma unroll
+  for (int t = 0; t < PB; ++t) X[(p0 + t) * LD + col] = w[t];
+}
+
+// One warp factors the PB-row panel of S (rows p0 .. p0+PB, columns p0 .. NP)
+// in registers: right-looking upper Cholesky of the diagonal block fused with
+// the solve of the panel's right part, U[p, j] = U_pp^{-T} S[p, j]. Lane l
+// holds column p0 + l + 32 s (all PB rows) in v[s][.]; step k broadcasts the
+// pivot (lane k) and the scaled row k (lanes k+1 .. PB-1) with shuffles.
+// Entries below the diagonal are left stale. A pivot that is not positive (or
+// NaN) is reported and replaced by 1 so that the remaining arithmetic stays
+// finite. Writes 1/U_kk to dinv.
+template <class C, typename T>
+__device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned long long *info, int node) {
+  constexpr int PB = C::PB, NP = C::NP, LD = C::LD;
+  constexpr int CPL = (NP + 31) / 32;  // column slots per lane
+  const int lane = threadIdx.x & 31;
+  T v[CPL][PB];
+#pragma unroll
+  for (int s = 0; s < CPL; ++s) {
+    const int j = p0 + lane + 32 * s;
+#pragma unroll
+    for (int t = 0; t < PB; ++t) v[s][t] = j < NP ? S[(p0 + t) * LD + j] : T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < PB; ++k) {
+    T d = __shfl_sync(0xffffffffu, v[0][k], k);
+    if (!(d > T(0))) {  // uniform across the warp
+      if (lane == 0 && info) atomicMin(info, pack_info(node, p0 + k));
+      d = T(1);
+      if (lane == k) v[0][k] = T(1);
+    }
+    const T rs = rsqrt(d);
+    if (lane == 0) dinv[p0 + k] = rs;
+#pragma unroll
+    for (int s = 0; s < CPL; ++s) v[s][k] *= rs;  // row k of U (the pivot becomes sqrt(d))
+#pragma unroll
+    for (int t = k + 1; t < PB; ++t) {
+      const T ukt = __shfl_sync(0xffffffffu, v[0][k], t);  // U[k][p0 + t]
+#pragma unroll
+      for (int s = 0; s < CPL; ++s) v[s][t] = fma(-ukt, v[s][k], v[s][t]);
     }
   }
-  // scale columns: L_ik = a_ik / sqrt(d_k), L_kk = sqrt(d_k)
-  T sq[R], isq[R];
 #pragma unroll
-  for (int c = 0; c < R; ++c) {
-    sq[c] = sqrt(piv_own[c]);
-    isq[c] = T(1) / sq[c];
-  }
+  for (int s = 0; s < CPL; ++s) {
+    const int j = p0 + lane + 32 * s;
+    if (j < NP)
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const int i = r0 + r, k = c0 + c;
-      T v = (i > k && lower) ? a[r][c] * isq[c] : (i == k ? sq[c] : T(0));
-      a[r][c] = v;
-      if (lower) LT[k * C::LD + i] = v;
-    }
-  if (lower && r0 == c0) {
-#pragma unroll
-    for (int c = 0; c < R; ++c) dinv[c0 + c] = isq[c];
+      for (int t = 0; t < PB; ++t) S[(p0 + t) * LD + j] = v[s][t];
   }
 }
 
-// Z <- L^{-1} Z for the np x np block Z held in registers (all tiles), with L
-// given by its transpose LT and the reciprocal diagonal dinv in shared memory:
-// forward substitution by rows, one barrier per row (rowbuf[2][np] double buffer).
+// Blocked upper Cholesky S = U^T U in place (upper triangle of S read; U
+// written to the upper triangle; entries below the diagonal are left stale).
 template <class C, typename T>
-__device__ __forceinline__ void tile_trsm_llnn(T (&z)[C::R][C::R], int r0, int c0, const T *LT, const T *dinv,
-                                               T *rowbuf) {
-  constexpr int R = C::R;
-  for (int j = 0; j < C::NP; ++j) {
-    T *rb = rowbuf + (j & 1) * C::NP;
-    if (j >= r0 && j < r0 + R) {
-      const T dj = dinv[j];
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (r0 + r == j) {
-#pragma unroll
-          for (int c = 0; c < R; ++c) z[r][c] *= dj;
-          vstore<T, R>(rb + c0, z[r]);
-        }
+__device__ __forceinline__ void block_potrf_upper(T *S, T *dinv, unsigned long long *info, int node, int r0, int c0) {
+  constexpr int PB = C::PB;
+#pragma unroll 1
+  for (int p = 0; p < C::NPAN; ++p) {
+    const int p0 = p * PB;
+    if (threadIdx.x < 32) warp_panel_potrf<C>(S, p0, dinv, info, node);
+    __syncthreads();
+    // trailing update of the upper tiles right/below the panel
+    if (p + 1 < C::NPAN) {
+      if (r0 >= p0 + PB && c0 >= r0) {
+        T a[C::R][C::R];
+        tile_from_smem<C>(a, S, r0, c0);
+        tile_sub_xty<C, PB>(a, S, S, r0, c0, p0);
+        tile_to_smem<C>(S, a, r0, c0);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Z <- U^{-T} Z for up to two right-hand-side blocks Z0, Z1 (either may be
+// null), blocked by panels: column substitution with U_pp, then the trailing
+// rows are updated with X^T Y products.
+template <class C, typename T>
+__device__ __forceinline__ void block_trsm_ut(T *Z0, T *Z1, const T *S, const T *dinv, int r0, int c0) {
+  constexpr int PB = C::PB;
+  const int nz = (Z0 ? 1 : 0) + (Z1 ? 1 : 0);
+  if (nz == 0) return;
+#pragma unroll 1
+  for (int p = 0; p < C::NPAN; ++p) {
+    const int p0 = p * PB;
+    for (int q = threadIdx.x; q < 2 * C::NP; q += C::NT) {
+      T *Z = q < C::NP ? Z0 : Z1;
+      if (Z) col_subst_ut<C>(Z, q % C::NP, S, dinv, p0);
     }
     __syncthreads();
-    if (r0 + R - 1 > j) {
-      T zr[R], l[R];
-      vload<T, R>(rb + c0, zr);
-      vload<T, R>(LT + j * C::LD + r0, l);
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (r0 + r > j) {
-#pragma unroll
-          for (int c = 0; c < R; ++c) z[r][c] = fma(-l[r], zr[c], z[r][c]);
-        }
+    if (p + 1 < C::NPAN && r0 >= p0 + PB) {
+      if (Z0) {
+        T a[C::R][C::R];
+        tile_from_smem<C>(a, Z0, r0, c0);
+        tile_sub_xty<C, PB>(a, S, Z0, r0, c0, p0);  // Z[i][j] -= sum_k U[k][i] Z[k][j], k in panel p
+        tile_to_smem<C>(Z0, a, r0, c0);
+      }
+      if (Z1) {
+        T a[C::R][C::R];
+        tile_from_smem<C>(a, Z1, r0, c0);
+        tile_sub_xty<C, PB>(a, S, Z1, r0, c0, p0);
+        tile_to_smem<C>(Z1, a, r0, c0);
+      }
     }
+    __syncthreads();
   }
 }
 
