@@ -100,6 +100,19 @@ int btc_schedule(int N, int *order_out, int *levels_out);
  */
 int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream);
 
+/*
+ * Launch schedule of a plan's factor and solve (default BTC_SCHED_FLOW).
+ * BTC_SCHED_LEVELS: one kernel launch per dissection level (Alg. 5 and 7 run
+ * level by level, the launches ordered on the stream). BTC_SCHED_FLOW: one
+ * persistent launch for all levels; each node starts as soon as the (at most
+ * three) nodes of the previous level that produce its inputs are done, with
+ * bounded device-side waits (BTC_ERR_TIMEOUT from btc_info if one gives up).
+ * Both schedules perform identical arithmetic per node, so their results are
+ * bitwise equal.
+ */
+enum btc_schedule_mode { BTC_SCHED_LEVELS = 0, BTC_SCHED_FLOW = 1 };
+int btc_plan_set_schedule(btc_plan_t p, int mode);
+
 /* Copy the plan's static description into *info. */
 int btc_plan_query(btc_plan_t p, btc_plan_info *info);
 
@@ -153,7 +166,9 @@ int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void
 /*
  * Synchronize the plan's stream and report the first failed pivot of the
  * last factorization: *block = 0-based node, *col = column within the block,
- * both -1 when the factorization succeeded. Returns BTC_OK or BTC_ERR_NOT_SPD.
+ * both -1 when the factorization succeeded. Returns BTC_OK, BTC_ERR_NOT_SPD,
+ * or BTC_ERR_TIMEOUT when a bounded device-side wait of a persistent launch
+ * gave up (results are then undefined).
  */
 int btc_info(btc_plan_t p, int *block, int *col);
 

@@ -51,6 +51,7 @@ _SIGS = {
     "btc_schedule": [ctypes.c_int, _ip, _ip],
     "btc_plan": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
     "btc_plan_query": [_vp, ctypes.POINTER(btc_plan_info)],
+    "btc_plan_set_schedule": [_vp, ctypes.c_int],
     "btc_factor": [_vp, _vp, _vp],
     "btc_solve": [_vp, _vp, ctypes.c_int],
     "btc_solve_refined": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
@@ -158,6 +159,13 @@ class Plan:
 
 def btc_plan(N, n, dtype=F64, stream=None):
     return Plan(N, n, dtype, stream)
+
+
+SCHED_LEVELS, SCHED_FLOW = 0, 1
+
+
+def btc_plan_set_schedule(plan, mode):
+    return _check(load().btc_plan_set_schedule(plan.h, mode))
 
 
 def btc_plan_query(plan):

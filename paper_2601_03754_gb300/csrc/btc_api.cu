@@ -86,27 +86,23 @@ __global__ void k_anorm(const double *D, const double *B, int N, int n, double *
 // refinement: each |a_ij| is rounded toward zero to FP32 and the row sums
 // accumulate with round-toward-zero additions, so the result never exceeds the
 // exact norm and the test ||r|| <= tol ||Psi|| ||x|| is never met early.
+// One CTA per block row, one thread per row; entries read from global memory.
 __global__ void k_anorm_lb(const double *D, const double *B, int N, int n, double *norms) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i = blockIdx.x;
-  const int ld = f64_ld(n);
-  double *Ds = reinterpret_cast<double *>(smem_raw);
-  double *Bl = Ds + n * ld;
-  double *Br = Bl + n * ld;
   const size_t bs = (size_t)n * n;
-  stage_f64(Ds, D + i * bs, n);
-  if (i > 0) stage_f64(Bl, B + (i - 1) * bs, n);
-  if (i + 1 < N) stage_f64(Br, B + i * bs, n);
-  cp_async_wait_all_s();
-  __syncthreads();
+  const double *Di = D + i * bs;
   float best = 0.0f;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     float s = 0.0f;
-    for (int c = 0; c < n; ++c) s = __fadd_rz(s, __double2float_rz(fabs(r >= c ? Ds[r * ld + c] : Ds[c * ld + r])));
-    if (i > 0)
-      for (int c = 0; c < n; ++c) s = __fadd_rz(s, __double2float_rz(fabs(Bl[r * ld + c])));
-    if (i + 1 < N)
-      for (int c = 0; c < n; ++c) s = __fadd_rz(s, __double2float_rz(fabs(Br[c * ld + r])));
+    for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(r >= c ? Di[r * n + c] : Di[c * n + r]));
+    if (i > 0) {
+      const double *Bl = B + (i - 1) * bs;
+      for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(Bl[r * n + c]));
+    }
+    if (i + 1 < N) {
+      const double *Br = B + i * bs;
+      for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(Br[c * n + r]));
+    }
     best = fmaxf(best, s);
   }
   for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -135,9 +131,17 @@ struct btc_plan_s {
   unsigned long long *d_info = nullptr;
   double *d_norms = nullptr;  // [0] max|r|, [1] max|x|, [2] ||Psi||_inf
   void *d_y = nullptr;        // work vector [N][np][kMaxCols]
+  // persistent dataflow launches
+  int sched = BTC_SCHED_FLOW;
+  int32_t *d_fac_deps = nullptr;
+  SolveFlowItem *d_solve_flow = nullptr;
+  int n_fac = 0, n_solve = 0;
+  int *d_flow = nullptr;  // [0] factor ticket, [1] solve ticket, [2] status, then done flags
+  int fac_grid = 0, solve_grid = 0;
   // host staging for readbacks
   double *h_norms = nullptr;
   unsigned long long *h_info = nullptr;
+  int *h_status = nullptr;
   // last factorization
   const void *D = nullptr, *B = nullptr;
   bool factored = false, anorm_valid = false;
@@ -195,6 +199,16 @@ static int grid_for(int64_t total) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
 }
 
+static constexpr int kFlowHeader = 4;  // ints before the done flags
+
+static FlowSync flow_sync(btc_plan_s *p, int which) {
+  FlowSync fs;
+  fs.ticket = p->d_flow + which;
+  fs.status = p->d_flow + 2;
+  fs.done = p->d_flow + kFlowHeader;
+  return fs;
+}
+
 // Forward + backward substitution of the work vector (m columns), Alg. 7.
 static int run_solve(btc_plan_s *p, int m) {
   const KernelSet &k = *p->ks;
@@ -203,6 +217,14 @@ static int run_solve(btc_plan_s *p, int m) {
   a.epool = p->epool;
   a.y = p->d_y;
   a.m = m;
+  if (p->sched == BTC_SCHED_FLOW) {
+    BTC_CUDA(cudaMemsetAsync(p->d_flow + 1, 0, sizeof(int), p->stream));
+    BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_solve, p->stream));
+    a.items = p->d_solve_flow;
+    a.count = p->n_solve;
+    return launch_n(k.solve_flow, std::min(p->solve_grid, p->n_solve), kSolveThreads, k.fwd_smem(m), p->stream, a,
+                    flow_sync(p, 1));
+  }
   for (int l = 0; l < p->hp.levels; ++l) {
     a.items = p->d_fwd + p->fwd_off[l];
     a.count = (int)(p->fwd_off[l + 1] - p->fwd_off[l]);
@@ -220,7 +242,9 @@ static int run_solve(btc_plan_s *p, int m) {
 
 static int read_info(btc_plan_s *p, int *block, int *col) {
   BTC_CUDA(cudaMemcpyAsync(p->h_info, p->d_info, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->stream));
+  BTC_CUDA(cudaMemcpyAsync(p->h_status, p->d_flow + 2, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   BTC_CUDA(cudaStreamSynchronize(p->stream));
+  if (*p->h_status != 0) return BTC_ERR_TIMEOUT;
   unsigned long long v = *p->h_info;
   if (v == ~0ull) {
     if (block) *block = -1;
@@ -298,7 +322,8 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
       (e = cudaMalloc(&p->d_info, sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_norms, 4 * sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost(&p->h_norms, 4 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&p->h_info, sizeof(unsigned long long))) != cudaSuccess)
+      (e = cudaMallocHost(&p->h_info, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_status, sizeof(int))) != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
                         cudaGetErrorString(e)));
   p->device_bytes = (int64_t)(dbytes + ebytes + (size_t)N * np * kMaxCols * ks.elem);
@@ -328,14 +353,47 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
     return cleanup(fail(BTC_ERR_CUDA, "btc_plan: schedule upload: %s", cudaGetErrorString(e)));
   p->device_bytes += (int64_t)(fac.size() * sizeof(FactorItem) + fwd.size() * sizeof(FwdItem) +
                                bwd.size() * sizeof(BwdItem));
+  // dataflow form
+  p->n_fac = (int)fac.size();
+  p->n_solve = (int)p->hp.solve_flow.size();
+  const size_t nflags = kFlowHeader + (size_t)std::max(p->n_fac, p->n_solve);
+  if ((e = cudaMalloc(&p->d_fac_deps, p->hp.fac_deps.size() * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_solve_flow, p->hp.solve_flow.size() * sizeof(SolveFlowItem))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_flow, nflags * sizeof(int))) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_OOM, "btc_plan: flow allocation: %s", cudaGetErrorString(e)));
+  if ((e = cudaMemcpy(p->d_fac_deps, p->hp.fac_deps.data(), p->hp.fac_deps.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_solve_flow, p->hp.solve_flow.data(), p->hp.solve_flow.size() * sizeof(SolveFlowItem),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(p->d_flow, 0, nflags * sizeof(int))) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_CUDA, "btc_plan: flow upload: %s", cudaGetErrorString(e)));
   // allow the large dynamic shared memory the kernels use
   if ((rc = set_smem(ks.fac_first, ks.fac_smem)) || (rc = set_smem(ks.fac_rest, ks.fac_smem)) ||
       (rc = set_smem(ks.root_first, ks.root_smem)) || (rc = set_smem(ks.root_rest, ks.root_smem)) ||
       (rc = set_smem(ks.fwd, ks.fwd_smem(kMaxCols))) || (rc = set_smem(ks.bwd, ks.bwd_smem(kMaxCols))) ||
-      (rc = set_smem(ks.resid, 3 * sizeof(double) * (size_t)n * f64_ld(n))) ||
-      (rc = set_smem((const void *)&k_anorm_lb, 3 * sizeof(double) * (size_t)n * f64_ld(n))))
+      (rc = set_smem(ks.resid, residual_smem_bytes(n, kMaxCols))) ||
+      (rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.solve_flow, ks.fwd_smem(kMaxCols))))
     return cleanup(rc);
+  {
+    int dev = 0, sms = 0, bf = 0, bs_ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, ks.fac_flow, ks.fac_threads, ks.fac_smem)) !=
+            cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs_, ks.solve_flow, kSolveThreads,
+                                                           ks.fwd_smem(kMaxCols))) != cudaSuccess)
+      return cleanup(fail(BTC_ERR_CUDA, "btc_plan: occupancy: %s", cudaGetErrorString(e)));
+    p->fac_grid = std::max(1, bf * sms);
+    p->solve_grid = std::max(1, bs_ * sms);
+  }
   *out = p;
+  return BTC_OK;
+}
+
+int btc_plan_set_schedule(btc_plan_t p, int mode) {
+  if (!p || (mode != BTC_SCHED_LEVELS && mode != BTC_SCHED_FLOW))
+    return fail(BTC_ERR_ARG, "btc_plan_set_schedule: invalid arguments");
+  p->sched = mode;
   return BTC_OK;
 }
 
@@ -356,6 +414,39 @@ int btc_factor(btc_plan_t p, const void *D, const void *B) {
   a.epool = p->epool;
   a.info = p->d_info;
   a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
+  const bool mixed_root = p->dtype == BTC_MIXED_F32;
+  if (p->sched == BTC_SCHED_FLOW) {
+    // all levels but the FP64 root (mixed path) in one persistent launch
+    const int last = p->hp.levels - 1;
+    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
+    const int nfirst = (int)p->fac_off[1];
+    InstDesc d{D, B, p->N, p->n};
+    if (nflow > 0) {
+      BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+      BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
+      BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
+      a.items = p->d_fac;
+      a.count = nflow;
+      const int32_t *deps = p->d_fac_deps;
+      int rc = launch_n(k.fac_flow, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps,
+                        nfirst, flow_sync(p, 0));
+      if (rc) return rc;
+    } else {
+      BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
+    }
+    if (mixed_root) {
+      a.items = p->d_fac + p->fac_off[last];
+      a.count = 1;
+      int rc = launch_n(last == 0 ? k.root_first : k.root_rest, 1, k.root_threads, k.root_smem, p->stream, a, d);
+      if (rc) return rc;
+    }
+    p->D = D;
+    p->B = B;
+    p->factored = true;
+    p->anorm_valid = false;
+    return BTC_OK;
+  }
+  BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
   for (int l = 0; l < p->hp.levels; ++l) {
     a.items = p->d_fac + p->fac_off[l];
     a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
@@ -402,16 +493,15 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
   const KernelSet &k = *p->ks;
   int blk, col;
   int rc = read_info(p, &blk, &col);
+  if (rc == BTC_ERR_TIMEOUT) return fail(rc, "factorization failed: a bounded device-side wait gave up");
   if (rc) return fail(rc, "factorization failed: pivot of block %d, column %d not positive", blk, col);
   if (!p->anorm_valid) {
     BTC_CUDA(cudaMemsetAsync(p->d_norms + 2, 0, sizeof(double), p->stream));
-    const size_t asm_ = 3 * sizeof(double) * (size_t)p->n * f64_ld(p->n);
-    if ((rc = launch_n((const void *)&k_anorm_lb, p->N, 128, asm_, p->stream, (const double *)p->D,
+    if ((rc = launch_n((const void *)&k_anorm_lb, p->N, 64, 0, p->stream, (const double *)p->D,
                        (const double *)p->B, p->N, p->n, p->d_norms)))
       return rc;
     p->anorm_valid = true;
   }
-  const size_t rsm = 3 * sizeof(double) * (size_t)p->n * f64_ld(p->n);
   int worst_it = 0;
   double worst_rel = 0.0;
   bool all_ok = true;
@@ -432,8 +522,9 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
     bool ok = false;
     for (;;) {
       BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, 2 * sizeof(double), p->stream));
-      if ((rc = launch_n(k.resid, p->N, 128, rsm, p->stream, p->d_y, (const double *)p->D, (const double *)p->B,
-                         (const double *)x, b, p->N, p->n, p->np, m, base, p->d_norms)))
+      if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
+                         (const double *)p->D, (const double *)p->B, (const double *)x, b, p->N, p->n, p->np, m, base,
+                         p->d_norms)))
         return rc;
       BTC_CUDA(cudaMemcpyAsync(p->h_norms, p->d_norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
       BTC_CUDA(cudaStreamSynchronize(p->stream));
@@ -516,6 +607,7 @@ int btc_info(btc_plan_t p, int *block, int *col) {
   }
   int rc = read_info(p, block, col);
   if (rc == BTC_ERR_NOT_SPD) return fail(rc, "pivot not positive");
+  if (rc == BTC_ERR_TIMEOUT) return fail(rc, "a bounded device-side wait gave up");
   return rc;
 }
 
@@ -557,7 +649,8 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
   BTC_CUDA(cudaMallocAsync((void **)&d, 3 * sizeof(double), s));
   int rc = BTC_OK;
   cudaError_t e = cudaMemsetAsync(d, 0, 3 * sizeof(double), s);
-  const size_t rsm = 3 * sizeof(double) * (size_t)n * f64_ld(n);
+  const size_t rsm = residual_smem_bytes(n, nrhs);
+  if (rsm > 220 * 1024) return fail(BTC_ERR_UNSUPPORTED, "btc_residual: n * nrhs too large for one block row");
   const void *rk = (const void *)&k_residual<double>;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
   if (e == cudaSuccess) {
@@ -565,7 +658,7 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
     double *ynull = nullptr;
     int np = n;
     int64_t base = 0;
-    if (!rc) rc = launch_n(rk, N, 128, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d);
+    if (!rc) rc = launch_n(rk, N, kResThreads, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d);
   }
   double h[3] = {0, 0, 0};
   if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -583,12 +676,14 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
 int btc_free(btc_plan_t p) {
   if (!p) return BTC_OK;
   if (p->stream || p->dpool) cudaStreamSynchronize(p->stream);
-  void *dev[] = {p->dpool, p->epool, p->d_fac, p->d_fwd, p->d_bwd, p->d_info, p->d_norms,
-                 p->d_y,   p->s_D,   p->s_B,   p->s_b,   p->s_x};
+  void *dev[] = {p->dpool, p->epool, p->d_fac, p->d_fwd,        p->d_bwd,      p->d_info,
+                 p->d_norms, p->d_y,   p->s_D,   p->d_fac_deps, p->d_solve_flow, p->d_flow,
+                 p->s_B,     p->s_b,   p->s_x};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_norms) cudaFreeHost(p->h_norms);
   if (p->h_info) cudaFreeHost(p->h_info);
+  if (p->h_status) cudaFreeHost(p->h_status);
   delete p;
   return BTC_OK;
 }

@@ -44,16 +44,15 @@ constexpr size_t factor_smem_bytes() {
 // caller's D and B (read at level 1 only). The FP64 top-separator Cholesky of
 // the mixed-precision path is the instantiation T = double, P = float.
 template <typename T, typename P, typename S, int NP, int R, bool FIRST>
-__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT) k_factor_level(FactorArgs args, InstDesc single) {
+__device__ __forceinline__ void factor_node(const FactorItem &it, const FactorArgs &args, const InstDesc &single,
+                                            unsigned char *smem_raw) {
   using C = TileCfg<T, NP, R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sS = reinterpret_cast<T *>(smem_raw);  // S_e -> U_e
   T *sP = sS + C::BLK;                      // P_a, later P_b
   T *sA = sP + C::BLK;                      // S(e,e-s) -> U(e,e-s)
   T *sB = sA + C::BLK;                      // S(e,e+s) -> U(e,e+s)
   T *dinv = sB + C::BLK;                    // 1 / U_kk
 
-  const FactorItem it = args.items[blockIdx.x];
   P *dpool = reinterpret_cast<P *>(args.dpool);
   P *epool = reinterpret_cast<P *>(args.epool);
   const int tid = threadIdx.x;
@@ -135,6 +134,44 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT) k_factor_level(FactorAr
     if (it.flags & FI_FILL_UPFIRST) tile_sub_xty<C, NP>(f, sA, sB, r0, c0);  // S'(e-s, e+s) = -U_up^T U_dn
     else tile_sub_xty<C, NP>(f, sB, sA, r0, c0);                             // S'(e+s, e-s) = -U_dn^T U_up
     tile_to_pool<C>(epool + it.fill, f, r0, c0);
+  }
+}
+
+// One launch per dissection level: CTA b eliminates item b of the level.
+template <typename T, typename P, typename S, int NP, int R, bool FIRST>
+__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT) k_factor_level(FactorArgs args, InstDesc single) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const FactorItem it = args.items[blockIdx.x];
+  factor_node<T, P, S, NP, R, FIRST>(it, args, single, smem_raw);
+}
+
+// Persistent dataflow form: all levels in one launch. CTAs claim items in
+// level order and wait only for the (<= 3) items of the previous level that
+// produce their inputs (deps, 3 per item). The first `nfirst` items are
+// level 1 and read the caller's arrays.
+template <typename T, int NP, int R>
+struct FlowMinBlocks {  // resident CTAs per SM the shared memory allows (caps registers accordingly)
+  static constexpr size_t smem = factor_smem_bytes<T, NP, R>();
+  static constexpr int by_smem = (int)((220 * 1024) / smem);
+  static constexpr int by_threads = 2048 / TileCfg<T, NP, R>::NT;
+  static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads) > 4 ? 4
+                                                : (by_smem < by_threads ? by_smem : by_threads);
+};
+
+template <typename T, typename P, typename S, int NP, int R>
+__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R>::value))
+    k_factor_flow(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_slot, s_ok;
+  for (;;) {
+    const int t = flow_claim(fs, args.count, &s_slot);
+    if (t < 0) break;
+    const FactorItem it = args.items[t];
+    if (flow_wait(fs, deps + 3 * t, 3, &s_ok)) {
+      if (t < nfirst) factor_node<T, P, S, NP, R, true>(it, args, single, smem_raw);
+      else factor_node<T, P, S, NP, R, false>(it, args, single, smem_raw);
+    }
+    flow_publish(fs, t);
   }
 }
 

@@ -59,6 +59,19 @@ struct BwdItem {
   int64_t x_up, e_up;  // x_{e-s} node and U(e, e-s) offset, or -1
 };
 
+// One item of the fused forward+backward solve of the persistent kernel
+// (forward items of all levels, then backward items from the top level down).
+// kind 0 (forward, survivor j):  y_j -= U(a)^T y_a + U(b)^T y_b; if d_self: y_j <- U_j^{-T} y_j
+// kind 1 (backward, eliminated e): y_e <- U_e^{-1} (y_e - U(a) y_a - U(b) y_b)
+struct SolveFlowItem {
+  int64_t y_self;
+  int64_t y_a, e_a;  // fwd: left contribution; bwd: down neighbour
+  int64_t y_b, e_b;  // fwd: right contribution; bwd: up neighbour
+  int64_t d_self;
+  int32_t kind;
+  int32_t dep[3];    // indices of the items this one waits for (-1: none), all smaller
+};
+
 struct LevelSchedule {
   int s;  // stride 2^(l-1)
   std::vector<FactorItem> fac;
@@ -68,6 +81,10 @@ struct LevelSchedule {
 
 struct HostPlan {
   int N = 0, n = 0, np = 0, levels = 0;
+  // dataflow form: factor items in level order with the (<= 3) items of the
+  // previous level that produce their inputs, and the fused solve list
+  std::vector<int32_t> fac_deps;           // 3 per factor item (flat level order), -1: none
+  std::vector<SolveFlowItem> solve_flow;
   int64_t offdiag = 0, fill = 0;
   std::vector<int64_t> level_slot_off;  // first U slot of each level (in blocks)
   std::vector<LevelSchedule> lv;

@@ -20,6 +20,8 @@ struct KernelSet {
   const void *root_first = nullptr, *root_rest = nullptr;
   int root_threads = 0;
   size_t root_smem = 0;
+  // persistent dataflow forms (all levels in one launch)
+  const void *fac_flow = nullptr, *solve_flow = nullptr;
   // solve
   const void *fwd = nullptr, *bwd = nullptr;
   size_t (*fwd_smem)(int m) = nullptr;

@@ -35,6 +35,8 @@ KernelSet make_set() {
     k.root_threads = TileCfg<double, NP, R>::NT;
     k.root_smem = factor_smem_bytes<double, NP, R>();
   }
+  k.fac_flow = (const void *)&k_factor_flow<T, T, S, NP, R>;
+  k.solve_flow = (const void *)&k_solve_flow<T, NP>;
   k.fwd = (const void *)&k_fwd_level<T, NP>;
   k.bwd = (const void *)&k_bwd_level<T, NP>;
   k.fwd_smem = &fwd_smem_fn<T, NP>;

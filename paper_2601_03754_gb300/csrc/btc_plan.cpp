@@ -121,6 +121,80 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
       L.fwd.push_back(f);
     }
   }
+  // ---- dataflow dependencies (indices into the flat level-ordered lists)
+  // Factor item (e, l), h = s/2, reads Dhat_e and the fill S(e-s, e) written at level
+  // l-1 by node e-h; P_a, S(e, e+s) and Dhat_{e+s} written by node e+h; P_b written by
+  // node e+3h. Every one of these nodes is eliminated at level l-1.
+  {
+    std::vector<int32_t> fac_index(N + 1, -1);  // node (1-based) -> flat factor index
+    int32_t idx = 0;
+    for (int l = 1; l <= levels; ++l)
+      for (const FactorItem &it : P->lv[l - 1].fac) fac_index[it.node + 1] = idx++;
+    P->fac_deps.assign(3 * (size_t)idx, -1);
+    idx = 0;
+    for (int l = 1; l <= levels; ++l) {
+      const int64_t s = int64_t(1) << (l - 1), h = s / 2;
+      for (const FactorItem &it : P->lv[l - 1].fac) {
+        const int64_t e = it.node + 1;
+        if (l > 1) {
+          const int64_t cand[3] = {e - h, e + h, e + 3 * h};
+          for (int k = 0; k < 3; ++k)
+            if (cand[k] >= 1 && cand[k] <= N) P->fac_deps[3 * (size_t)idx + k] = fac_index[cand[k]];
+        }
+        ++idx;
+      }
+    }
+    // Solve: forward items (j, l) for every survivor j at every level, then backward
+    // items (e, l) from the top level down. Forward (j, l) waits for (j-h, l-1),
+    // (j, l-1), (j+h, l-1); backward (e, l) waits for the backward items of e-s and
+    // e+s (finished at higher levels) and for the forward item that finished y_e.
+    std::vector<std::vector<int32_t>> fwd_index(levels + 1);
+    std::vector<int32_t> fwd_final(N + 1, -1), bwd_index(N + 1, -1);
+    P->solve_flow.clear();
+    for (int l = 1; l <= levels; ++l) {
+      const int64_t s = int64_t(1) << (l - 1), h = s / 2;
+      fwd_index[l].assign(N + 1, -1);
+      for (const FwdItem &f : P->lv[l - 1].fwd) {
+        const int64_t j = f.y_self - y_base + 1;
+        SolveFlowItem q;
+        q.y_self = f.y_self;
+        q.y_a = f.y_l;
+        q.e_a = f.e_l;
+        q.y_b = f.y_r;
+        q.e_b = f.e_r;
+        q.d_self = f.d_self;
+        q.kind = 0;
+        q.dep[0] = q.dep[1] = q.dep[2] = -1;
+        if (l > 1) {
+          const int64_t cand[3] = {j - h, j, j + h};
+          for (int k = 0; k < 3; ++k)
+            if (cand[k] >= 1 && cand[k] <= N) q.dep[k] = fwd_index[l - 1][cand[k]];
+        }
+        fwd_index[l][j] = (int32_t)P->solve_flow.size();
+        if (f.d_self >= 0) fwd_final[j] = (int32_t)P->solve_flow.size();
+        P->solve_flow.push_back(q);
+      }
+    }
+    for (int l = levels; l >= 1; --l) {
+      for (const BwdItem &b : P->lv[l - 1].bwd) {
+        const int64_t e = b.x_self - y_base + 1;
+        SolveFlowItem q;
+        q.y_self = b.x_self;
+        q.y_a = b.x_dn;
+        q.e_a = b.e_dn;
+        q.y_b = b.x_up;
+        q.e_b = b.e_up;
+        q.d_self = b.d_self;
+        q.kind = 1;
+        const int64_t s = int64_t(1) << (l - 1);
+        q.dep[0] = (e + s <= N) ? bwd_index[e + s] : -1;
+        q.dep[1] = (e - s >= 1) ? bwd_index[e - s] : -1;
+        q.dep[2] = fwd_final[e];
+        bwd_index[e] = (int32_t)P->solve_flow.size();
+        P->solve_flow.push_back(q);
+      }
+    }
+  }
   // Solve flops (Alg. 7 costs): trsm n^2 m per node and direction, gemm 2 n^2 m per
   // off-diagonal block and direction.
   sol = 2.0 * N * n2 + 4.0 * (double)P->offdiag * n2;

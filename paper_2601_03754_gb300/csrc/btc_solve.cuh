@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "btc_internal.h"
+#include "btc_tile.cuh"
 
 namespace btc {
 
@@ -127,13 +128,13 @@ struct SolveArgs {
   int m;
 };
 
-// Forward step of one level (pull form): one CTA per surviving node j.
+// Forward step for one surviving node j (pull form, Alg. 7 forward sweep):
 //   y_j -= U(j-h, j)^T y_{j-h} + U(j+h, j)^T y_{j+h}   (contributions of level l-1)
-//   y_j <- U_j^{-T} y_j                                 (if j is eliminated at level l)
+//   y_j <- U_j^{-T} y_j                                 (if j is eliminated at this level)
 template <typename T, int NP>
-__global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
+__device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_l, int64_t y_r, int64_t e_r,
+                                         int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
   constexpr int LDL = SolveCfg<T, NP>::LDL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
   T *Us = reinterpret_cast<T *>(smem_raw);  // U_j
   T *Ul = Us + NP * LDL;                    // U(j-h, j)
@@ -142,24 +143,23 @@ __global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
   T *ys = dinv + NP;                        // NP*m
   T *yl = ys + NP * m;
   T *yr = yl + NP * m;
-  const FwdItem it = reinterpret_cast<const FwdItem *>(a.items)[blockIdx.x];
   T *y = reinterpret_cast<T *>(a.y);
   const T *dpool = reinterpret_cast<const T *>(a.dpool);
   const T *epool = reinterpret_cast<const T *>(a.epool);
   const int nm = NP * m;
-  T *yself = y + it.y_self * nm;
-  if (it.d_self >= 0) stage_block<T, NP>(Us, dpool + it.d_self);
-  if (it.y_l >= 0) stage_block<T, NP>(Ul, epool + it.e_l);
-  if (it.y_r >= 0) stage_block<T, NP>(Ur, epool + it.e_r);
+  T *yself = y + y_self * nm;
+  if (d_self >= 0) stage_block<T, NP>(Us, dpool + d_self);
+  if (y_l >= 0) stage_block<T, NP>(Ul, epool + e_l);
+  if (y_r >= 0) stage_block<T, NP>(Ur, epool + e_r);
   stage_vec<T>(ys, yself, nm);
-  if (it.y_l >= 0) stage_vec<T>(yl, y + it.y_l * nm, nm);
-  if (it.y_r >= 0) stage_vec<T>(yr, y + it.y_r * nm, nm);
+  if (y_l >= 0) stage_vec<T>(yl, y + y_l * nm, nm);
+  if (y_r >= 0) stage_vec<T>(yr, y + y_r * nm, nm);
   cp_async_wait_all_s();
   __syncthreads();
-  if (it.d_self >= 0)
+  if (d_self >= 0)
     for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
-  if (it.y_l >= 0) {
-    const bool right = it.y_r >= 0;
+  if (y_l >= 0) {
+    const bool right = y_r >= 0;
     for (int q = threadIdx.x; q < nm; q += blockDim.x) {
       const int c = q / m, col = q % m;
       T acc = ys[q];
@@ -172,19 +172,26 @@ __global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
     }
   }
   __syncthreads();
-  if (it.d_self >= 0) {
+  if (d_self >= 0) {
     warp_trsv_ut<T, NP>(ys, m, Us, dinv);
     __syncthreads();
   }
   for (int q = threadIdx.x; q < nm; q += blockDim.x) yself[q] = ys[q];
 }
 
-// Backward step of one level: one CTA per eliminated node e.
+template <typename T, int NP>
+__global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const FwdItem it = reinterpret_cast<const FwdItem *>(a.items)[blockIdx.x];
+  fwd_node<T, NP>(it.y_self, it.y_l, it.e_l, it.y_r, it.e_r, it.d_self, a, smem_raw);
+}
+
+// Backward step for one eliminated node e (Alg. 7 backward sweep):
 //   x_e <- U_e^{-1} (y_e - U(e, e+s) x_{e+s} - U(e, e-s) x_{e-s})
 template <typename T, int NP>
-__global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
+__device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e_dn, int64_t x_up, int64_t e_up,
+                                         int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
   constexpr int LDL = SolveCfg<T, NP>::LDL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = a.m;
   T *Us = reinterpret_cast<T *>(smem_raw);  // U_e
   T *Ud = Us + NP * LDL;                    // U(e, e+s)
@@ -193,23 +200,22 @@ __global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
   T *ys = dinv + NP;                        // NP*m
   T *xd = ys + NP * m;
   T *xu = xd + NP * m;
-  const BwdItem it = reinterpret_cast<const BwdItem *>(a.items)[blockIdx.x];
   T *y = reinterpret_cast<T *>(a.y);
   const T *dpool = reinterpret_cast<const T *>(a.dpool);
   const T *epool = reinterpret_cast<const T *>(a.epool);
   const int nm = NP * m;
-  T *yself = y + it.x_self * nm;
-  stage_block<T, NP>(Us, dpool + it.d_self);
-  if (it.x_dn >= 0) stage_block<T, NP>(Ud, epool + it.e_dn);
-  if (it.x_up >= 0) stage_block<T, NP>(Uu, epool + it.e_up);
+  T *yself = y + x_self * nm;
+  stage_block<T, NP>(Us, dpool + d_self);
+  if (x_dn >= 0) stage_block<T, NP>(Ud, epool + e_dn);
+  if (x_up >= 0) stage_block<T, NP>(Uu, epool + e_up);
   stage_vec<T>(ys, yself, nm);
-  if (it.x_dn >= 0) stage_vec<T>(xd, y + it.x_dn * nm, nm);
-  if (it.x_up >= 0) stage_vec<T>(xu, y + it.x_up * nm, nm);
+  if (x_dn >= 0) stage_vec<T>(xd, y + x_dn * nm, nm);
+  if (x_up >= 0) stage_vec<T>(xu, y + x_up * nm, nm);
   cp_async_wait_all_s();
   __syncthreads();
   for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
-  if (it.x_dn >= 0 || it.x_up >= 0) {
-    const bool dn = it.x_dn >= 0, up = it.x_up >= 0;
+  if (x_dn >= 0 || x_up >= 0) {
+    const bool dn = x_dn >= 0, up = x_up >= 0;
     for (int q = threadIdx.x; q < nm; q += blockDim.x) {
       const int r = q / m, col = q % m;
       T acc = ys[q];
@@ -226,6 +232,33 @@ __global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
   warp_trsv_u<T, NP>(ys, m, Us, dinv);
   __syncthreads();
   for (int q = threadIdx.x; q < nm; q += blockDim.x) yself[q] = ys[q];
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BwdItem it = reinterpret_cast<const BwdItem *>(a.items)[blockIdx.x];
+  bwd_node<T, NP>(it.x_self, it.x_dn, it.e_dn, it.x_up, it.e_up, it.d_self, a, smem_raw);
+}
+
+// Persistent dataflow form of the whole solve (forward items of all levels,
+// then backward items top-down) in one launch; each item waits only for the
+// items that produce its inputs.
+template <typename T, int NP>
+__global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowSync fs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_slot, s_ok;
+  const SolveFlowItem *items = reinterpret_cast<const SolveFlowItem *>(a.items);
+  for (;;) {
+    const int t = flow_claim(fs, a.count, &s_slot);
+    if (t < 0) break;
+    const SolveFlowItem it = items[t];
+    if (flow_wait(fs, it.dep, 3, &s_ok)) {
+      if (it.kind == 0) fwd_node<T, NP>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
+      else bwd_node<T, NP>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
+    }
+    flow_publish(fs, t);
+  }
 }
 
 template <typename T, int NP>
@@ -305,39 +338,57 @@ __device__ __forceinline__ void stage_f64(double *dst, const double *src, int n)
 
 // r = b - Psi x in FP64 for one block row per CTA; writes r (converted to T)
 // into the padded work vector y when y != nullptr, and max|r|, max|x| into
-// norms[0], norms[1]. D: lower triangles read.
+// norms[0], norms[1]. D: lower triangles read. Each output's 3n-term dot
+// product is split into kResParts contiguous partial sums, added in a fixed
+// order (deterministic). Matrix entries are read straight from global memory
+// (each block's rows stay in L1 across the partial sums); x_{i-1}, x_i,
+// x_{i+1} are staged in shared memory. Dynamic shared memory:
+// (3 + kResParts) * n * m doubles.
+constexpr int kResParts = 4;
+constexpr int kResThreads = 256;
+
 template <typename T>
-__global__ void k_residual(T *y, const double *D, const double *B, const double *x, const double *b, int N, int n,
-                           int np, int m, int64_t node_base, double *norms) {
+__global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D, const double *B, const double *x,
+                                                          const double *b, int N, int n, int np, int m,
+                                                          int64_t node_base, double *norms) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i = blockIdx.x;
-  const int ld = f64_ld(n);
-  double *Ds = reinterpret_cast<double *>(smem_raw);
-  double *Bl = Ds + n * ld;  // B_{i-1}: row i's left block
-  double *Br = Bl + n * ld;  // B_i:     transposed: row i's right block
+  const int nm = n * m;
+  double *xs = reinterpret_cast<double *>(smem_raw);  // [3][n*m]: x_{i-1}, x_i, x_{i+1}
+  double *ps = xs + 3 * nm;                            // [kResParts][n*m]
   const size_t bs = (size_t)n * n;
-  stage_f64(Ds, D + i * bs, n);
-  if (i > 0) stage_f64(Bl, B + (i - 1) * bs, n);
-  if (i + 1 < N) stage_f64(Br, B + i * bs, n);
-  cp_async_wait_all_s();
+  for (int q = threadIdx.x; q < 3 * nm; q += blockDim.x) {
+    const int which = q / nm, off = q % nm, row = i - 1 + which;
+    xs[q] = (row >= 0 && row < N) ? x[(size_t)row * nm + off] : 0.0;
+  }
+  __syncthreads();
+  const double *Di = D + i * bs;
+  const double *Bl = i > 0 ? B + (i - 1) * bs : nullptr;
+  const double *Br = i + 1 < N ? B + i * bs : nullptr;
+  const int chunk = (n + kResParts - 1) / kResParts;
+  for (int idx = threadIdx.x; idx < kResParts * nm; idx += blockDim.x) {
+    const int part = idx / nm, q = idx % nm;
+    const int r = q / m, col = q % m;
+    const int c0 = part * chunk, c1 = min(n, c0 + chunk);
+    double v = 0.0;
+    for (int c = c0; c < c1; ++c) v = fma(r >= c ? Di[r * n + c] : Di[c * n + r], xs[nm + c * m + col], v);
+    if (Bl)
+      for (int c = c0; c < c1; ++c) v = fma(Bl[r * n + c], xs[c * m + col], v);
+    if (Br)
+      for (int c = c0; c < c1; ++c) v = fma(Br[c * n + r], xs[2 * nm + c * m + col], v);
+    ps[part * nm + q] = v;
+  }
   __syncthreads();
   double rmax = 0.0, xmax = 0.0;
-  const double *xi = x + (size_t)i * n * m;
-  for (int q = threadIdx.x; q < n * m; q += blockDim.x) {
+  for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+    double ax = 0.0;
+#pragma unroll
+    for (int k = 0; k < kResParts; ++k) ax += ps[k * nm + q];
     const int r = q / m, col = q % m;
-    double v = b[((size_t)i * n + r) * m + col];
-    for (int c = 0; c < n; ++c) v = fma(-(r >= c ? Ds[r * ld + c] : Ds[c * ld + r]), xi[c * m + col], v);
-    if (i > 0) {
-      const double *xp = x + (size_t)(i - 1) * n * m;
-      for (int c = 0; c < n; ++c) v = fma(-Bl[r * ld + c], xp[c * m + col], v);
-    }
-    if (i + 1 < N) {
-      const double *xn = x + (size_t)(i + 1) * n * m;
-      for (int c = 0; c < n; ++c) v = fma(-Br[c * ld + r], xn[c * m + col], v);
-    }
+    const double v = b[(size_t)i * nm + q] - ax;
     if (y) y[(node_base + i) * np * m + r * m + col] = (T)v;
     rmax = fmax(rmax, fabs(v));
-    xmax = fmax(xmax, fabs(xi[r * m + col]));
+    xmax = fmax(xmax, fabs(xs[nm + q]));
   }
   if (y) {
     for (int q = threadIdx.x; q < (np - n) * m; q += blockDim.x) y[(node_base + i) * np * m + n * m + q] = T(0);
@@ -350,6 +401,20 @@ __global__ void k_residual(T *y, const double *D, const double *B, const double 
     atomic_max_nonneg(norms + 0, rmax);
     atomic_max_nonneg(norms + 1, xmax);
   }
+}
+
+inline size_t residual_smem_bytes(int n, int m) { return sizeof(double) * (size_t)(3 + kResParts) * n * m; }
+
+// |a| rounded toward zero to FP32 with integer operations only (the FP64 ->
+// FP32 conversion instruction runs on the slow FP64 pipe of this GPU): keep
+// the exponent and the top 23 mantissa bits. Magnitudes below the FP32
+// normal range give 0 and above it FLT_MAX, both lower bounds of |a|.
+__device__ __forceinline__ float abs_lower_f32(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+  const int e = (int)(u >> 52) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return 3.402823466e38f;
+  return __int_as_float((e << 23) | (int)((u >> 29) & 0x7fffff));
 }
 
 }  // namespace btc

@@ -133,7 +133,7 @@ __device__ __forceinline__ void block_to_smem(T *s, const P *g) {
     const int q = threadIdx.x + it * C::NT;
     if (q < TOTAL) {
       const int row = q / CPR, col = (q % CPR) * V;
-      raw[it] = __ldg(reinterpret_cast<const float4 *>(g + (size_t)row * C::NP + col));
+      raw[it] = __ldcg(reinterpret_cast<const float4 *>(g + (size_t)row * C::NP + col));
     }
   }
 #pragma unroll
@@ -224,12 +224,42 @@ __device__ __forceinline__ void tile_to_smem(T *s, const T (&a)[C::R][C::R], int
   for (int r = 0; r < C::R; ++r) vstore<T, C::R>(s + (r0 + r) * C::LD + c0, a[r]);
 }
 
+// Global load that bypasses L1 (pool blocks may have been written by another
+// CTA of the same persistent launch).
+template <typename T, int R>
+__device__ __forceinline__ void vload_cg(const T *p, T (&v)[R]) {
+  if constexpr (sizeof(T) * R == 16) {
+    const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+    const T *s = reinterpret_cast<const T *>(&q);
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = s[i];
+  } else if constexpr (sizeof(T) * R == 32) {
+    const float4 q0 = __ldcg(reinterpret_cast<const float4 *>(p));
+    const float4 q1 = __ldcg(reinterpret_cast<const float4 *>(p) + 1);
+    const T *s0 = reinterpret_cast<const T *>(&q0);
+    const T *s1 = reinterpret_cast<const T *>(&q1);
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      v[i] = s0[i];
+      v[i + R / 2] = s1[i];
+    }
+  } else if constexpr (sizeof(T) * R == 8) {
+    const float2 q = __ldcg(reinterpret_cast<const float2 *>(p));
+    const T *s = reinterpret_cast<const T *>(&q);
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = s[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = __ldcg(p + i);
+  }
+}
+
 template <class C, typename T, typename P>
 __device__ __forceinline__ void tile_from_pool(T (&a)[C::R][C::R], const P *g, int r0, int c0) {
 #pragma unroll
   for (int r = 0; r < C::R; ++r) {
     P v[C::R];
-    vload<P, C::R>(g + (size_t)(r0 + r) * C::NP + c0, v);
+    vload_cg<P, C::R>(g + (size_t)(r0 + r) * C::NP + c0, v);
 #pragma unroll
     for (int c = 0; c < C::R; ++c) a[r][c] = (T)v[c];
   }
@@ -260,6 +290,73 @@ __device__ __forceinline__ void tile_sub_xty(T (&a)[C::R][C::R], const T *X, con
     for (int r = 0; r < C::R; ++r)
 #pragma unroll
       for (int c = 0; c < C::R; ++c) a[r][c] = fma(-x[r], y[c], a[r][c]);
+  }
+}
+
+// ------------------------------------------------------- dataflow signalling
+// Completion flags of a persistent launch: the producer CTA publishes with a
+// release store after a CTA barrier; consumers poll with acquire loads. Every
+// wait is bounded: after kMaxPolls polls (about a second) the CTA records
+// kFlowTimeout in *status and gives up; a nonzero status makes every later
+// wait give up at once, so a failed launch drains quickly.
+constexpr long long kMaxPolls = 1ll << 23;
+constexpr int kFlowTimeout = 1;
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct FlowSync {
+  int *ticket;  // next item to claim
+  int *done;    // one flag per item
+  int *status;  // 0 = ok; kFlowTimeout when a wait gave up
+};
+
+// Claim the next item (ticket order = dependency order). Returns the item
+// index, or -1 when all `total` items are taken. All threads of the CTA call it.
+__device__ __forceinline__ int flow_claim(const FlowSync &fs, int total, int *s_slot) {
+  __syncthreads();  // the previous item's shared memory is no longer read
+  if (threadIdx.x == 0) *s_slot = atomicAdd(fs.ticket, 1);
+  __syncthreads();
+  const int t = *s_slot;
+  return t < total ? t : -1;
+}
+
+// Wait until the listed items (index < 0: none) are done. Thread 0 polls;
+// returns false (for every thread) when the wait gave up.
+__device__ __forceinline__ bool flow_wait(const FlowSync &fs, const int32_t *deps, int ndeps, int *s_ok) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    for (int k = 0; k < ndeps && ok; ++k) {
+      const int d = deps[k];
+      if (d < 0) continue;
+      long long polls = 0;
+      while (ld_acquire_gpu(fs.done + d) == 0) {
+        if (++polls > kMaxPolls || *((volatile int *)fs.status) != 0) {
+          atomicOr(fs.status, kFlowTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Publish item t as done (after all of this CTA's global writes for it).
+__device__ __forceinline__ void flow_publish(const FlowSync &fs, int t) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_gpu(fs.done + t, 1);
   }
 }
 
