@@ -203,6 +203,52 @@ def run_profile(which):
     return 0
 
 
+def batched_measure(btc, gen, torch, steps, stream, flush):
+    """Config: 512 instances, n uniform in {8,16,32,64}, N log-uniform in [32, 2048], one RHS each,
+    delta = 1e-2; mixed FP32 factor + FP64 refinement to 1e-10, beside the plain FP64 batch."""
+    specs = gen.batch_specs(512, seed=0)
+    Ds, Bs, bs, xs = [], [], [], []
+    for k, (N, n) in enumerate(specs):
+        D, B = gen.bt_random_torch(N, n, delta=1e-2, seed=1000 + k)
+        Ds.append(D)
+        Bs.append(B if B.numel() else torch.zeros((1, n, n), dtype=torch.float64, device="cuda"))
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5000 + k)
+        bs.append(torch.randn((N * n, 1), generator=g, device="cuda", dtype=torch.float64))
+        xs.append(torch.zeros_like(bs[-1]))
+    Ns = [N for N, _ in specs]
+    ns = [n for _, n in specs]
+    out = {"instances": len(specs), "nodes": int(sum(Ns)), "n_mix": sorted(set(ns))}
+    for name, dt in (("mixed", btc.MIXED_F32), ("plain_f64", btc.F64)):
+        batch = btc.btc_batch_plan(Ns, ns, dt, stream)
+        q = btc.btc_batch_query(batch)
+
+        def step():
+            btc.btc_batch_factor(batch, Ds, Bs)
+            return btc.btc_batch_solve_refined(batch, bs, xs, tol=TOL, maxit=30)
+
+        reps = steps if dt == btc.MIXED_F32 else max(2, steps // 4)
+        with torch.cuda.stream(stream):
+            step()
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                it, rel, rc = step()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.mean(ts)
+        out[name] = {"ms_per_batch": ms, "solves_per_s": len(specs) * 1000.0 / ms, "refine_iters": it,
+                     "max_relres": rel, "factor_tflops": q["factor_flops"] / (ms * 1e-3) / 1e12,
+                     "groups": q["groups"], "device_gb": q["device_bytes"] / 1e9}
+        batch.free()
+    out["speedup_vs_plain_f64"] = out["plain_f64"]["ms_per_batch"] / out["mixed"]["ms_per_batch"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,6 +256,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--profile", choices=["mixed", "f64", "both"], default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
@@ -325,6 +372,8 @@ def main():
     h2d = D.nbytes + B.nbytes + b.nbytes
     d2h = b.nbytes
 
+    batched = batched_measure(btc, gen, torch, max(3, args.steps // 5), stream, flush) if not args.no_batch else None
+
     peaks, pk_kind = _peaks()
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_PEAK_PER_SM_CLK * sm_max * 1e6 / 1e12
@@ -361,6 +410,7 @@ def main():
         "gpu_launches": launches * args.steps,
         "clocks": clk,
         "peaks_source": pk_kind,
+        "batched": batched,
         "wall_s_timed": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:

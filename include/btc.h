@@ -224,6 +224,46 @@ int btc_residual_noalloc(int N, int n, int nrhs, const double *D, const double *
 /* Release every device resource of the plan (synchronizes its stream). */
 int btc_free(btc_plan_t p);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent systems of different (N_k, n_k) in one plan. Instances are
+ * grouped by padded block size; each group runs one persistent launch for the
+ * factor and one for each solve, whose work items are the (instance, node)
+ * eliminations of Alg. 5 / the substitutions of Alg. 7 of all its instances,
+ * in level order, each waiting only for the producer nodes of its own instance.
+ * Pointer arrays are HOST arrays of `count` DEVICE pointers; one right-hand
+ * side per instance; rhs/x of instance k have N_k * n_k entries.
+ */
+typedef struct btc_batch_s *btc_batch_t;
+
+/* Plan a batch (host planning + device pools). N, n: host arrays of `count`
+ * sizes. Errors: BTC_ERR_ARG, BTC_ERR_UNSUPPORTED, BTC_ERR_OOM, BTC_ERR_CUDA. */
+int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int dtype, void *stream);
+
+/* Number of block-size groups, total Alg. 5 flops, device bytes of the batch. */
+int btc_batch_query(btc_batch_t b, int *groups, double *factor_flops, int64_t *device_bytes);
+
+/* Factor every instance (element types as btc_factor). Asynchronous. The D and
+ * B arrays must stay alive and unchanged for btc_batch_solve_refined. */
+int btc_batch_factor(btc_batch_t b, const void *const *D, const void *const *B);
+
+/* One solve per instance: x_k = Psi_k^{-1} rhs_k (for BTC_MIXED_F32 one FP32
+ * correction solve of FP64 vectors). Asynchronous. */
+int btc_batch_solve(btc_batch_t b, const void *const *rhs, void *const *x);
+
+/* Refined solve of every instance until max_k ||r_k||/(||Psi_k|| ||x_k||) <= tol
+ * (FP64 residuals; plans of dtype BTC_F64 or BTC_MIXED_F32). Synchronous.
+ * *iters: refinement steps; *max_relres: the largest final relative residual. */
+int btc_batch_solve_refined(btc_batch_t b, const double *const *rhs, double *const *x, double tol, int maxit,
+                            int *iters, double *max_relres);
+
+/* Synchronize; report the first instance whose factorization met a pivot that
+ * was not positive (*failed_instance = -1 if none). BTC_OK, BTC_ERR_NOT_SPD or
+ * BTC_ERR_TIMEOUT. */
+int btc_batch_info(btc_batch_t b, int *failed_instance, int *block, int *col);
+
+/* Release the batch (synchronizes its stream). */
+int btc_batch_free(btc_batch_t b);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *btc_last_error(void);
 

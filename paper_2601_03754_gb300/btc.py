@@ -61,6 +61,14 @@ _SIGS = {
     "btc_residual": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
     "btc_residual_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
     "btc_free": [_vp],
+    "btc_batch_plan": [ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, ctypes.c_int, _vp],
+    "btc_batch_query": [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)],
+    "btc_batch_factor": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
+    "btc_batch_solve": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
+    "btc_batch_solve_refined": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_double, ctypes.c_int, _ip,
+                                _dp],
+    "btc_batch_info": [_vp, _ip, _ip, _ip],
+    "btc_batch_free": [_vp],
     "btc_last_error": [],
     "btc_version": [],
 }
@@ -234,4 +242,78 @@ def btc_residual_noalloc(N, n, nrhs, D, B, x, b, stream=None):
 
 def btc_free(plan):
     plan.free()
+    return OK
+
+
+def _ptr_array(xs):
+    arr = (_vp * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+class Batch:
+    """Owning handle of a btc_batch_t."""
+
+    def __init__(self, Ns, ns, dtype=MIXED_F32, stream=None):
+        Ns = np.ascontiguousarray(Ns, dtype=np.int32)
+        ns = np.ascontiguousarray(ns, dtype=np.int32)
+        h = _vp()
+        _check(load().btc_batch_plan(ctypes.byref(h), len(Ns), Ns.ctypes.data_as(_ip), ns.ctypes.data_as(_ip), dtype,
+                                     _stream(stream)))
+        self.h = h
+        self.count, self.dtype = len(Ns), dtype
+        self.Ns, self.ns = Ns, ns
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().btc_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def btc_batch_plan(Ns, ns, dtype=MIXED_F32, stream=None):
+    return Batch(Ns, ns, dtype, stream)
+
+
+def btc_batch_query(batch):
+    g = ctypes.c_int(0)
+    f = ctypes.c_double(0)
+    d = ctypes.c_int64(0)
+    _check(load().btc_batch_query(batch.h, ctypes.byref(g), ctypes.byref(f), ctypes.byref(d)))
+    return {"groups": g.value, "factor_flops": f.value, "device_bytes": d.value}
+
+
+def btc_batch_factor(batch, Ds, Bs):
+    return _check(load().btc_batch_factor(batch.h, _ptr_array(Ds), _ptr_array(Bs)))
+
+
+def btc_batch_solve(batch, bs, xs):
+    return _check(load().btc_batch_solve(batch.h, _ptr_array(bs), _ptr_array(xs)))
+
+
+def btc_batch_solve_refined(batch, bs, xs, tol=1e-10, maxit=30):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    rc = _check(load().btc_batch_solve_refined(batch.h, _ptr_array(bs), _ptr_array(xs), tol, maxit, ctypes.byref(it),
+                                               ctypes.byref(rel)), (ERR_NOT_CONVERGED,))
+    return it.value, rel.value, rc
+
+
+def btc_batch_info(batch):
+    k = ctypes.c_int(0)
+    blk = ctypes.c_int(0)
+    col = ctypes.c_int(0)
+    rc = load().btc_batch_info(batch.h, ctypes.byref(k), ctypes.byref(blk), ctypes.byref(col))
+    _check(rc, (ERR_NOT_SPD,))
+    return rc, k.value, blk.value, col.value
+
+
+def btc_batch_free(batch):
+    batch.free()
     return OK

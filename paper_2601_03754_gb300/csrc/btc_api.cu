@@ -16,6 +16,7 @@
 #include "btc_internal.h"
 #include "btc_kernels.h"
 #include "btc_solve.cuh"
+#include "btc_runtime.h"
 
 namespace btc {
 
@@ -23,7 +24,7 @@ static thread_local std::string g_err;
 
 void set_error_message(const char *msg) { g_err = msg; }
 
-static int fail(int code, const char *fmt, ...) {
+int fail(int code, const char *fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -33,13 +34,6 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
-#define BTC_CUDA(call)                                                                       \
-  do {                                                                                       \
-    cudaError_t e_ = (call);                                                                 \
-    if (e_ != cudaSuccess)                                                                   \
-      return fail(e_ == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "%s: %s (%s:%d)", #call, \
-                  cudaGetErrorString(e_), __FILE__, __LINE__);                               \
-  } while (0)
 
 // ------------------------------------------------------------ kernel table
 static constexpr int kMaxSets = 8;
@@ -109,9 +103,7 @@ __global__ void k_anorm_lb(const double *D, const double *B, int N, int n, doubl
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, (double)best);
 }
 
-static bool dtype_ok(int dtype) { return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32; }
-
-static constexpr int kMaxCols = 16;  // right-hand sides per solve launch
+bool dtype_ok(int dtype) { return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32; }
 
 }  // namespace btc
 
@@ -181,25 +173,12 @@ static int launch(const void *fn, int grid, int block, size_t smem, cudaStream_t
   return BTC_OK;
 }
 
-template <typename... A>
-static int launch_n(const void *fn, int grid, int block, size_t smem, cudaStream_t s, A... a) {
-  void *args[] = {(void *)&a...};
-  BTC_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
-  return BTC_OK;
-}
-
-static int set_smem(const void *fn, size_t bytes) {
+int set_smem(const void *fn, size_t bytes) {
   if (!fn) return BTC_OK;
   BTC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return BTC_OK;
 }
 
-static int grid_for(int64_t total) {
-  int64_t g = (total + 255) / 256;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
-}
-
-static constexpr int kFlowHeader = 4;  // ints before the done flags
 
 static FlowSync flow_sync(btc_plan_s *p, int which) {
   FlowSync fs;

@@ -1,0 +1,46 @@
+// Helpers shared by the single-instance (btc_api.cu) and batched
+// (btc_batch.cu) runtimes. Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "../../include/btc.h"
+#include "btc_kernels.h"
+
+namespace btc {
+
+// Record a formatted message for btc_last_error() and return `code`.
+int fail(int code, const char *fmt, ...);
+int set_smem(const void *fn, size_t bytes);
+bool dtype_ok(int dtype);
+
+constexpr int kMaxCols = 16;     // right-hand sides per solve launch
+constexpr int kFlowHeader = 4;   // ints before the done flags of a flow state array
+
+#define BTC_CUDA(call)                                                                                       \
+  do {                                                                                                       \
+    cudaError_t e_ = (call);                                                                                 \
+    if (e_ != cudaSuccess)                                                                                   \
+      return ::btc::fail(e_ == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);                                        \
+  } while (0)
+
+template <typename... A>
+inline int launch_n(const void *fn, int grid, int block, size_t smem, cudaStream_t s, A... a) {
+  if (grid <= 0) return BTC_OK;
+  void *args[] = {(void *)&a...};
+  BTC_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
+  return BTC_OK;
+}
+
+inline int grid_for(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+// Lower bound of the infinity norm per block row (refinement stopping test).
+__global__ void k_anorm_lb(const double *D, const double *B, int N, int n, double *norms);
+
+}  // namespace btc

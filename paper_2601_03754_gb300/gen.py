@@ -59,6 +59,36 @@ def bt_random(N: int, n: int, delta: float = 1.0, seed: int = 0):
     return np.ascontiguousarray(D), np.ascontiguousarray(B)
 
 
+def spectral_norms_torch(B):
+    """Largest singular value of each block of B [k, n, n] (a torch tensor on
+    any device): sqrt of the largest eigenvalue of B^T B from a batched
+    symmetric eigensolver on the host CPU (fast and exact to rounding, unlike a
+    batched SVD on the GPU for many small blocks)."""
+    import torch
+    Bc = B.detach().to("cpu")
+    w = torch.linalg.eigvalsh(Bc.transpose(1, 2) @ Bc)
+    return w[:, -1].clamp_min(0).sqrt().to(B.device)
+
+
+def bt_random_torch(N: int, n: int, delta: float = 1.0, seed: int = 0, device="cuda", dtype=None):
+    """The bt_random recipe drawn with torch's generator directly on `device`
+    (for large batched workloads; the numbers differ from bt_random's)."""
+    import torch
+    dtype = dtype or torch.float64
+    gen_ = torch.Generator(device=device)
+    gen_.manual_seed(seed)
+    B = torch.randn((max(N - 1, 0), n, n), generator=gen_, device=device, dtype=dtype) / math.sqrt(n)
+    M = torch.randn((N, n, n), generator=gen_, device=device, dtype=dtype)
+    D = M @ M.transpose(1, 2) / n
+    shift = torch.full((N,), float(delta), device=device, dtype=dtype)
+    if N > 1:
+        s = spectral_norms_torch(B)
+        shift[:-1] += s
+        shift[1:] += s
+    D += shift[:, None, None] * torch.eye(n, device=device, dtype=dtype)[None]
+    return D.contiguous(), B.contiguous()
+
+
 def _stable_dynamics(rng, count, n, radius=0.95):
     A = rng.standard_normal((count, n, n))
     if count == 0:
