@@ -197,3 +197,21 @@ def test_full_size_c2_against_oracle():
     x = dev(b, torch.float64)
     btc.btc_solve(p, x, 1)
     assert oracle.relres(D, B, x.cpu().numpy(), b) <= 1e-12
+
+
+@pytest.mark.parametrize("N", [257, 1024])
+def test_refinement_on_ill_conditioned_block_laplacian(N):
+    """D_i = 2I + small SPD perturbation, B_i = -I: kappa ~ 4 (N+1)^2 / pi^2 (4e5 at N=1024)."""
+    n = 16
+    rng = np.random.default_rng(N)
+    M = rng.standard_normal((N, n, n)) * 0.05
+    D = 2.0 * np.eye(n)[None] + M @ np.swapaxes(M, 1, 2) / n
+    B = np.tile(-np.eye(n), (N - 1, 1, 1))
+    b = gen.rhs(N, n, 1, seed=N)
+    for dt in (btc.F64, btc.MIXED_F32):
+        p, Dd, Bd = factor_on_gpu(D, B, dt)
+        bd = dev(b, torch.float64)
+        xd = torch.zeros_like(bd)
+        it, rel, rc = btc.btc_solve_refined(p, bd, xd, 1, tol=1e-10, maxit=50)
+        assert rc == btc.OK and rel <= 1e-10
+        assert oracle.relres(D, B, xd.cpu().numpy(), b) <= 1e-10
