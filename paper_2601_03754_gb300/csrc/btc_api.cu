@@ -36,7 +36,7 @@ int fail(int code, const char *fmt, ...) {
 
 
 // ------------------------------------------------------------ kernel table
-static constexpr int kMaxSets = 8;
+static constexpr int kMaxSets = 10;
 static KernelSet g_sets[3][kMaxSets];
 static int g_nsets[3] = {0, 0, 0};
 static std::once_flag g_once;
@@ -349,9 +349,11 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   // allow the large dynamic shared memory the kernels use
   if ((rc = set_smem(ks.fac_first, ks.fac_smem)) || (rc = set_smem(ks.fac_rest, ks.fac_smem)) ||
       (rc = set_smem(ks.root_first, ks.root_smem)) || (rc = set_smem(ks.root_rest, ks.root_smem)) ||
-      (rc = set_smem(ks.fwd, ks.fwd_smem(kMaxCols))) || (rc = set_smem(ks.bwd, ks.bwd_smem(kMaxCols))) ||
+      (rc = set_smem(ks.fwd, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
+      (rc = set_smem(ks.bwd, ks.bwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.resid, residual_smem_bytes(n, kMaxCols))) ||
-      (rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.solve_flow, ks.fwd_smem(kMaxCols))))
+      (rc = set_smem(ks.fac_flow, ks.fac_smem)) ||
+      (rc = set_smem(ks.solve_flow, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))))
     return cleanup(rc);
   {
     int dev = 0, sms = 0, bf = 0, bs_ = 0;
@@ -359,8 +361,8 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, ks.fac_flow, ks.fac_threads, ks.fac_smem)) !=
             cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs_, ks.solve_flow, kSolveThreads,
-                                                           ks.fwd_smem(kMaxCols))) != cudaSuccess)
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs_, ks.solve_flow, kSolveThreads, ks.fwd_smem(1))) !=
+            cudaSuccess)
       return cleanup(fail(BTC_ERR_CUDA, "btc_plan: occupancy: %s", cudaGetErrorString(e)));
     p->fac_grid = std::max(1, bf * sms);
     p->solve_grid = std::max(1, bs_ * sms);
@@ -448,8 +450,9 @@ int btc_solve(btc_plan_t p, void *rhs, int nrhs) {
   if (!p || !rhs || nrhs < 1) return fail(BTC_ERR_ARG, "btc_solve: invalid arguments");
   if (!p->factored) return fail(BTC_ERR_NOT_FACTORED, "btc_solve: no factorization");
   const KernelSet &k = *p->ks;
-  for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
-    const int m = std::min(kMaxCols, nrhs - c0);
+  const int mc = std::min(kMaxCols, k.max_cols);
+  for (int c0 = 0; c0 < nrhs; c0 += mc) {
+    const int m = std::min(mc, nrhs - c0);
     int64_t base = 0;
     int rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)rhs,
                       p->N, p->n, p->np, m, nrhs, c0, base);
@@ -467,7 +470,8 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
                       double *relres) {
   if (!p || !b || !x || nrhs < 1 || maxit < 0) return fail(BTC_ERR_ARG, "btc_solve_refined: invalid arguments");
   if (p->dtype == BTC_F32) return fail(BTC_ERR_ARG, "btc_solve_refined needs an FP64 or mixed plan");
-  if (nrhs > kMaxCols) return fail(BTC_ERR_UNSUPPORTED, "btc_solve_refined: at most %d right-hand sides", kMaxCols);
+  const int mc = std::min(kMaxCols, p->ks->max_cols);
+  if (nrhs > mc) return fail(BTC_ERR_UNSUPPORTED, "btc_solve_refined: at most %d right-hand sides for this plan", mc);
   if (!p->factored) return fail(BTC_ERR_NOT_FACTORED, "btc_solve_refined: no factorization");
   const KernelSet &k = *p->ks;
   int blk, col;
@@ -484,8 +488,8 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
   int worst_it = 0;
   double worst_rel = 0.0;
   bool all_ok = true;
-  for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
-    const int m = std::min(kMaxCols, nrhs - c0);
+  for (int c0 = 0; c0 < nrhs; c0 += mc) {
+    const int m = std::min(mc, nrhs - c0);
     int64_t base = 0;
     // x_0 = solve(b)
     if ((rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)b, p->N,

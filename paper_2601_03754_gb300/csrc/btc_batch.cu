@@ -64,8 +64,9 @@ __global__ void k_batch_unpack(const T *y, const BatchNode *nodes, const InstDes
 template <typename T>
 __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const BatchNode *nodes, const InstDesc *inst,
                                                                 const BatchVec *vec, int np, double *norms) {
-  __shared__ double xs[3 * 64];
-  __shared__ double ps[kResParts * 64];
+  constexpr int NMAX = 96;  // largest compiled block size
+  __shared__ double xs[3 * NMAX];
+  __shared__ double ps[kResParts * NMAX];
   const BatchNode nd = nodes[blockIdx.x];
   const InstDesc in = inst[nd.inst];
   const int n = in.n, N = in.N, i = nd.row;
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const Batc
   const double *b = reinterpret_cast<const double *>(vec[nd.inst].b);
   for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {
     const int which = q / n, off = q % n, row = i - 1 + which;
-    xs[which * 64 + off] = (row >= 0 && row < N) ? x[(size_t)row * n + off] : 0.0;
+    xs[which * NMAX + off] = (row >= 0 && row < N) ? x[(size_t)row * n + off] : 0.0;
   }
   __syncthreads();
   const size_t bs = (size_t)n * n;
@@ -87,12 +88,12 @@ __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const Batc
     const int part = idx / n, r = idx % n;
     const int c0 = part * chunk, c1 = min(n, c0 + chunk);
     double v = 0.0;
-    for (int c = c0; c < c1; ++c) v = fma(r >= c ? Di[r * n + c] : Di[c * n + r], xs[64 + c], v);
+    for (int c = c0; c < c1; ++c) v = fma(r >= c ? Di[r * n + c] : Di[c * n + r], xs[NMAX + c], v);
     if (Bl)
       for (int c = c0; c < c1; ++c) v = fma(Bl[r * n + c], xs[c], v);
     if (Br)
-      for (int c = c0; c < c1; ++c) v = fma(Br[c * n + r], xs[128 + c], v);
-    ps[part * 64 + r] = v;
+      for (int c = c0; c < c1; ++c) v = fma(Br[c * n + r], xs[2 * NMAX + c], v);
+    ps[part * NMAX + r] = v;
   }
   __syncthreads();
   double rmax = 0.0, xmax = 0.0;
@@ -100,11 +101,11 @@ __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const Batc
     if (r < n) {
       double ax = 0.0;
 #pragma unroll
-      for (int k = 0; k < kResParts; ++k) ax += ps[k * 64 + r];
+      for (int k = 0; k < kResParts; ++k) ax += ps[k * NMAX + r];
       const double v = b[(size_t)i * n + r] - ax;
       y[(size_t)blockIdx.x * np + r] = (T)v;
       rmax = fmax(rmax, fabs(v));
-      xmax = fmax(xmax, fabs(xs[64 + r]));
+      xmax = fmax(xmax, fabs(xs[NMAX + r]));
     } else {
       y[(size_t)blockIdx.x * np + r] = T(0);
     }

@@ -37,20 +37,25 @@ struct FactorArgs {
 template <typename T, int NP, int R>
 constexpr size_t factor_smem_bytes() {
   using C = TileCfg<T, NP, R>;
-  return sizeof(T) * (4 * (size_t)C::BLK + NP);
+  return sizeof(T) * (3 * (size_t)C::BLK + NP);
 }
 
 // T: arithmetic type; P: element type of the pools; S: element type of the
 // caller's D and B (read at level 1 only). The FP64 top-separator Cholesky of
 // the mixed-precision path is the instantiation T = double, P = float.
+//
+// Three shared-memory blocks: sS holds S_e -> U_e; sA and sB first hold the
+// deferred blocks P_a, P_b (both deferred updates are applied before the
+// Cholesky, the one onto S_{e+s} in registers), then receive S(e,e-s) and
+// S(e,e+s) by asynchronous copies that overlap the Cholesky, and finally hold
+// U(e,e-s), U(e,e+s) for the syrk and the fill.
 template <typename T, typename P, typename S, int NP, int R, bool FIRST>
 __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorArgs &args, const InstDesc &single,
                                             unsigned char *smem_raw) {
   using C = TileCfg<T, NP, R>;
   T *sS = reinterpret_cast<T *>(smem_raw);  // S_e -> U_e
-  T *sP = sS + C::BLK;                      // P_a, later P_b
-  T *sA = sP + C::BLK;                      // S(e,e-s) -> U(e,e-s)
-  T *sB = sA + C::BLK;                      // S(e,e+s) -> U(e,e+s)
+  T *sA = sS + C::BLK;                      // P_a, then S(e,e-s) -> U(e,e-s)
+  T *sB = sA + C::BLK;                      // P_b, then S(e,e+s) -> U(e,e+s)
   T *dinv = sB + C::BLK;                    // 1 / U_kk
 
   P *dpool = reinterpret_cast<P *>(args.dpool);
@@ -65,67 +70,67 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
   const S *uD = reinterpret_cast<const S *>(ins.D);
   const S *uB = reinterpret_cast<const S *>(ins.B);
   const size_t ubs = (size_t)ins.n * ins.n;
-  const bool has_up = it.r_up >= 0, has_dn = it.r_down >= 0;
+  const bool has_up = it.r_up >= 0, has_dn = it.r_down >= 0, has_next = it.d_next >= 0;
+  constexpr bool ASYNC = sizeof(T) == sizeof(P);
+  T d[R][R];  // the tile of S_{e+s} owned by this thread (upper tiles only)
 
-  // ---- stage the node's blocks
   if constexpr (FIRST) {
-    user_to_smem<C>(sS, uD + e * ubs, ins.n, true, T(1));                 // S[i][j] = D_e[j][i]
+    // level 1: the caller's blocks, converted and padded on the way in
+    user_to_smem<C>(sS, uD + e * ubs, ins.n, true, T(1));                     // S[i][j] = D_e[j][i]
     if (has_up) user_to_smem<C>(sA, uB + (e - 1) * ubs, ins.n, false, T(0));  // S(e, e-1) = B_{e-1}
     if (has_dn) user_to_smem<C>(sB, uB + e * ubs, ins.n, true, T(0));         // S(e, e+1) = B_e^T
-  } else if constexpr (sizeof(T) == sizeof(P)) {
-    block_to_smem_async<C>(sS, dpool + it.d_self);
-    if (it.p_a >= 0) block_to_smem_async<C>(sP, epool + it.p_a);
-    if (has_up) block_to_smem_async<C>(sA, epool + it.r_up);
-    if (has_dn) block_to_smem_async<C>(sB, epool + it.r_down);
-    cp_async_commit_wait_all();
+    if (has_next && upper_tile) tile_from_user<C>(d, uD + (e + 1) * ubs, ins.n, r0, c0, true, T(1));
+    __syncthreads();
   } else {
-    block_to_smem<C>(sS, dpool + it.d_self);
-    if (it.p_a >= 0) block_to_smem<C>(sP, epool + it.p_a);
-    if (has_up) block_to_smem<C>(sA, epool + it.r_up);
-    if (has_dn) block_to_smem<C>(sB, epool + it.r_down);
-  }
-  __syncthreads();
-
-  // ---- deferred update of level l-1 onto S_e
-  if (!FIRST && it.p_a >= 0) {
-    if (upper_tile) {
-      T a[R][R];
-      tile_from_smem<C>(a, sS, r0, c0);
-      tile_sub_xty<C, NP>(a, sP, sP, r0, c0);
-      tile_to_smem<C>(sS, a, r0, c0);
+    const bool pa = it.p_a >= 0, pb = it.p_b >= 0;
+    if constexpr (ASYNC) {
+      block_to_smem_async<C>(sS, dpool + it.d_self);
+      if (pa) block_to_smem_async<C>(sA, epool + it.p_a);
+      if (pb) block_to_smem_async<C>(sB, epool + it.p_b);
+    }
+    if (has_next && upper_tile) tile_from_pool<C>(d, dpool + it.d_next, r0, c0);
+    if constexpr (ASYNC) {
+      cp_async_commit_wait_all();
+    } else {
+      block_to_smem<C>(sS, dpool + it.d_self);
+      if (pa) block_to_smem<C>(sA, epool + it.p_a);
+      if (pb) block_to_smem<C>(sB, epool + it.p_b);
     }
     __syncthreads();
+    // deferred updates of level l-1: S_e -= P_a^T P_a, S_{e+s} -= P_b^T P_b
+    if (upper_tile) {
+      if (pa) {
+        T a[R][R];
+        tile_from_smem<C>(a, sS, r0, c0);
+        tile_sub_xty<C, NP>(a, sA, sA, r0, c0);
+        tile_to_smem<C>(sS, a, r0, c0);
+      }
+      if (pb && has_next) tile_sub_xty<C, NP>(d, sB, sB, r0, c0);
+    }
+    __syncthreads();
+    // the off-diagonal operands arrive while the Cholesky runs
+    if constexpr (ASYNC) {
+      if (has_up) block_to_smem_async<C>(sA, epool + it.r_up);
+      if (has_dn) block_to_smem_async<C>(sB, epool + it.r_down);
+    } else {
+      if (has_up) block_to_smem<C>(sA, epool + it.r_up);
+      if (has_dn) block_to_smem<C>(sB, epool + it.r_down);
+    }
   }
 
   // ---- potrf, then the two trsm of the same node
   block_potrf_upper<C>(sS, dinv, info, e, r0, c0);
   smem_to_block<C>(dpool + it.d_self, sS, true);
+  if constexpr (!FIRST && ASYNC) cp_async_commit_wait_all();
+  if constexpr (!FIRST) __syncthreads();
   block_trsm_ut<C>(has_up ? sA : nullptr, has_dn ? sB : nullptr, sS, dinv, r0, c0);
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
 
-  // ---- S_{e+s} -= P_b^T P_b + U_dn^T U_dn
-  if (it.d_next >= 0) {
-    const bool pb = !FIRST && it.p_b >= 0;
-    if (pb) {
-      if constexpr (sizeof(T) == sizeof(P)) {
-        block_to_smem_async<C>(sP, epool + it.p_b);
-        cp_async_commit_wait_all();
-      } else {
-        block_to_smem<C>(sP, epool + it.p_b);
-      }
-    }
-    T d[R][R];
-    if (upper_tile) {
-      if constexpr (FIRST) tile_from_user<C>(d, uD + (e + 1) * ubs, ins.n, r0, c0, true, T(1));
-      else tile_from_pool<C>(d, dpool + it.d_next, r0, c0);
-    }
-    if (pb) __syncthreads();
-    if (upper_tile) {
-      if (pb) tile_sub_xty<C, NP>(d, sP, sP, r0, c0);
-      tile_sub_xty<C, NP>(d, sB, sB, r0, c0);
-      tile_to_pool<C>(dpool + it.d_next, d, r0, c0);
-    }
+  // ---- S_{e+s} -= U_dn^T U_dn
+  if (has_next && upper_tile) {
+    tile_sub_xty<C, NP>(d, sB, sB, r0, c0);
+    tile_to_pool<C>(dpool + it.d_next, d, r0, c0);
   }
   // ---- fill block for level l+1
   if (it.fill >= 0) {
@@ -152,10 +157,11 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT) k_factor_level(FactorAr
 template <typename T, int NP, int R>
 struct FlowMinBlocks {  // resident CTAs per SM the shared memory allows (caps registers accordingly)
   static constexpr size_t smem = factor_smem_bytes<T, NP, R>();
-  static constexpr int by_smem = (int)((220 * 1024) / smem);
+  static constexpr int by_smem = (int)((226 * 1024) / smem);
   static constexpr int by_threads = 2048 / TileCfg<T, NP, R>::NT;
-  static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads) > 4 ? 4
-                                                : (by_smem < by_threads ? by_smem : by_threads);
+  static constexpr int fit = by_smem < by_threads ? by_smem : by_threads;
+  // large CTAs (np = 96: 576 threads) keep their registers rather than a second resident CTA
+  static constexpr int value = TileCfg<T, NP, R>::NT >= 512 ? 1 : fit < 1 ? 1 : fit > 3 ? 3 : fit;
 };
 
 template <typename T, typename P, typename S, int NP, int R>

@@ -9,6 +9,7 @@ void register_f64(KernelSet *t, int *count) {
   t[c++] = make_set<double, double, 32, false>();
   t[c++] = make_set<double, double, 48, false>();
   t[c++] = make_set<double, double, 64, false>();
+  t[c++] = make_set<double, double, 96, false>();
   *count = c;
 }
 }  // namespace btc

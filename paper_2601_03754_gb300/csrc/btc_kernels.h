@@ -25,6 +25,7 @@ struct KernelSet {
   // solve
   const void *fwd = nullptr, *bwd = nullptr;
   size_t (*fwd_smem)(int m) = nullptr;
+  int max_cols = 16;  // right-hand sides per solve launch that fit in shared memory
   size_t (*bwd_smem)(int m) = nullptr;
   const void *pack = nullptr, *unpack = nullptr, *resid = nullptr;
 };

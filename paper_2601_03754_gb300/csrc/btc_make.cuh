@@ -9,7 +9,7 @@ namespace btc {
 // Register tile edge per padded block size: (np/R)^2 threads per CTA.
 template <int NP>
 struct TileEdge {
-  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : 4;
+  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : 4;  // 96 -> 576 threads
 };
 
 template <typename T, int NP>
@@ -40,6 +40,8 @@ KernelSet make_set() {
   k.fwd = (const void *)&k_fwd_level<T, NP>;
   k.bwd = (const void *)&k_bwd_level<T, NP>;
   k.fwd_smem = &fwd_smem_fn<T, NP>;
+  k.max_cols = 16;
+  while (k.max_cols > 1 && fwd_smem_bytes<T, NP>(k.max_cols) > 232448 - 64) --k.max_cols;
   k.bwd_smem = &bwd_smem_fn<T, NP>;
   k.pack = (const void *)&k_pack_rhs<T, S>;
   k.unpack = (const void *)&k_unpack<T, S>;

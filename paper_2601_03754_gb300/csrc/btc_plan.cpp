@@ -10,7 +10,7 @@
 
 namespace btc {
 
-static const int kSizes[] = {8, 16, 32, 48, 64};
+static const int kSizes[] = {8, 16, 32, 48, 64, 96};
 
 int padded_size(int n, int dtype) {
   (void)dtype;

@@ -72,7 +72,11 @@ __device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *
     }
 #pragma unroll 4
     for (int j = 0; j < NP; ++j) {
-      const T zj = warp_bcast((RPL == 1 || j < 32) ? v[0] : v[RPL - 1], j & 31) * dinv[j];
+      T src = v[0];  // the lane slot holding row j
+#pragma unroll
+      for (int t = 1; t < RPL; ++t)
+        if ((j >> 5) == t) src = v[t];
+      const T zj = warp_bcast(src, j & 31) * dinv[j];
 #pragma unroll
       for (int s = 0; s < RPL; ++s) {
         const int i = lane + 32 * s;
@@ -103,7 +107,11 @@ __device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *d
     }
 #pragma unroll 4
     for (int j = NP - 1; j >= 0; --j) {
-      const T xj = warp_bcast((RPL == 1 || j < 32) ? v[0] : v[RPL - 1], j & 31) * dinv[j];
+      T src = v[0];  // the lane slot holding row j
+#pragma unroll
+      for (int t = 1; t < RPL; ++t)
+        if ((j >> 5) == t) src = v[t];
+      const T xj = warp_bcast(src, j & 31) * dinv[j];
 #pragma unroll
       for (int s = 0; s < RPL; ++s) {
         const int i = lane + 32 * s;

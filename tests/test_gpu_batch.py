@@ -11,7 +11,7 @@ from gpu_helpers import dev, need_gpu, tdtype, torch
 pytestmark = pytest.mark.gpu
 
 SIZES = [(1, 8), (2, 3), (5, 12), (17, 16), (33, 24), (64, 33), (100, 48), (129, 64), (40, 8), (7, 64), (200, 16),
-         (3, 48), (90, 5)]
+         (3, 48), (90, 5), (30, 96), (11, 70)]
 
 
 @pytest.fixture(scope="module", autouse=True)

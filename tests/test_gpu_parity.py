@@ -17,7 +17,7 @@ from gpu_helpers import compare_factor_with_oracle, dev, factor_on_gpu, need_gpu
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(1, 1), (1, 16), (2, 3), (3, 8), (5, 12), (7, 16), (16, 5), (20, 24), (33, 32), (64, 16), (100, 48),
-          (129, 64), (257, 8)]
+          (129, 64), (257, 8), (9, 96), (40, 80), (3, 65)]
 FACT_TOL = {btc.F64: 1e-11, btc.F32: 5e-5, btc.MIXED_F32: 5e-5}
 REC_TOL = {btc.F64: 1e-12, btc.F32: 1e-5, btc.MIXED_F32: 1e-5}
 RES_TOL = {btc.F64: 1e-12, btc.F32: 1e-5}
@@ -44,7 +44,7 @@ def test_factor_blocks_match_oracle(N, n, dt):
 
 @pytest.mark.parametrize("dt", [btc.F64, btc.F32], ids=["f64", "f32"])
 @pytest.mark.parametrize("N,n,m", [(1, 4, 1), (3, 8, 2), (64, 16, 1), (100, 12, 3), (129, 64, 1), (65, 33, 16),
-                                   (40, 7, 17)])
+                                   (40, 7, 17), (33, 96, 3), (20, 72, 1)])
 def test_solve_residual_and_solution(N, n, m, dt):
     D, B = gen.bt_random(N, n, delta=1.0, seed=7 + N + n)
     b = gen.rhs(N, n, m, seed=N)

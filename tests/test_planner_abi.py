@@ -37,8 +37,9 @@ def test_version_and_last_error():
 
 
 def test_describe_rejects_oversized_blocks():
+    assert btc.btc_describe(16, 96, btc.F32)["np"] == 96
     with pytest.raises(btc.BtcError) as ei:
-        btc.btc_describe(16, 65, btc.F32)
+        btc.btc_describe(16, 97, btc.F32)
     assert ei.value.code == btc.ERR_UNSUPPORTED
 
 
@@ -140,4 +141,5 @@ def test_padding_rule():
     assert btc.btc_describe(10, 24)["np"] == 32
     assert btc.btc_describe(10, 48)["np"] == 48
     assert btc.btc_describe(10, 64)["np"] == 64
+    assert btc.btc_describe(10, 65)["np"] == 96
     assert btc.btc_describe(10, 1)["np"] == 8
