@@ -249,6 +249,31 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
     return out
 
 
+def serving_measure(btc, torch, rates=(1000.0, 4000.0), count=300):
+    """Config: Poisson stream of factor+solve requests, n uniform in {12,24,48,96}, N log-uniform
+    in [50, 5000], MPC-like generator, 30% re-solves of a cached factor, HBM-footprint admission;
+    mixed FP32+FP64-refinement server vs plain FP64 server; p50/p99 latency and sustained solves/s."""
+    from paper_2601_03754_gb300 import serve
+    pool = serve.make_pool(count=24, seed=0)
+    out = {"pool": len(pool), "requests_per_rate": count, "slots": 8, "hbm_budget_gb": 16}
+    for name, dt in (("mixed", btc.MIXED_F32), ("plain_f64", btc.F64)):
+        res = {}
+        for rate in rates:
+            srv = btc.btc_server_start(dt, slots=8, hbm_budget_bytes=16 << 30, cache_factors=True)
+            serve.run_stream(srv, pool, rate, 40, seed=1)  # warm-up: plans allocated, kernels loaded
+            srv.stop()
+            srv = btc.btc_server_start(dt, slots=8, hbm_budget_bytes=16 << 30, cache_factors=True)
+            results, wall, _, _, _ = serve.run_stream(srv, pool, rate, count, seed=2)
+            st = btc.btc_server_stats(srv)
+            srv.stop()
+            ok = sum(1 for r in results if r["status"] == btc.OK)
+            res[str(int(rate))] = {"p50_us": st["p50_us"], "p99_us": st["p99_us"], "mean_us": st["mean_us"],
+                                   "solves_per_s": st["solves_per_s"], "completed": ok,
+                                   "cache_hits": st["cache_hits"], "max_relres": max(r["relres"] for r in results)}
+        out[name] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,6 +282,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--profile", choices=["mixed", "f64", "both"], default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
@@ -373,6 +399,7 @@ def main():
     d2h = b.nbytes
 
     batched = batched_measure(btc, gen, torch, max(3, args.steps // 5), stream, flush) if not args.no_batch else None
+    serving = serving_measure(btc, torch) if not args.no_serve else None
 
     peaks, pk_kind = _peaks()
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -411,6 +438,7 @@ def main():
         "clocks": clk,
         "peaks_source": pk_kind,
         "batched": batched,
+        "serving": serving,
         "wall_s_timed": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:

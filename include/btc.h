@@ -113,6 +113,10 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream);
 enum btc_schedule_mode { BTC_SCHED_LEVELS = 0, BTC_SCHED_FLOW = 1 };
 int btc_plan_set_schedule(btc_plan_t p, int mode);
 
+/* Rebind the plan's work to another CUDA stream (NULL = legacy default
+ * stream). Work already enqueued on the old stream is not waited for. */
+int btc_plan_set_stream(btc_plan_t p, void *stream);
+
 /* Copy the plan's static description into *info. */
 int btc_plan_query(btc_plan_t p, btc_plan_info *info);
 
@@ -269,6 +273,60 @@ const char *btc_last_error(void);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int btc_version(void);
+
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching request server (no paper counterpart beyond the
+ * real-time setting of Sec. 1). Requests enter a FIFO queue; `slots` worker
+ * threads, each with its own CUDA stream, take the oldest request that is
+ * admissible (a slot is free and its HBM footprint fits the budget together
+ * with the work in flight and the cached factors; least-recently-used cached
+ * factors are evicted to make room), so requests arriving while others run
+ * are admitted as slots and memory free up and their kernels overlap. Each
+ * request is factor + refined solve (one RHS) or, with factor_id >= 0, a
+ * refined re-solve with the cached factor of an earlier request.
+ */
+typedef struct btc_server_s *btc_server_t;
+
+typedef struct btc_request {
+  int N, n;           /* system size                                                           */
+  const double *D;    /* device FP64 [N][n][n] (lower triangles), alive until completion, and
+                         for a factor that may be cached, until the server stops                */
+  const double *B;    /* device FP64 [N-1][n][n]                                                */
+  const double *b;    /* device FP64 [N*n] right-hand side                                      */
+  double *x;          /* device FP64 [N*n] solution (written)                                   */
+  int64_t factor_id;  /* -1: new factor (cached under this request's ticket when caching is on);
+                         >= 0: ticket of an earlier factor request whose factor is reused (the
+                         request is factored anew if that factor is no longer cached)            */
+  double tol;         /* relative residual target, e.g. 1e-10                                   */
+  int maxit;          /* refinement step limit                                                  */
+} btc_request;
+
+typedef struct btc_server_stats_s {
+  int64_t completed, failed, queued, evictions, cache_hits, cache_misses;
+  double p50_us, p99_us, mean_us; /* latency = completion - submission                         */
+  double solves_per_s;            /* completed / (last completion - first submission)          */
+  int64_t device_bytes;           /* plans in flight, cached and idle                          */
+} btc_server_stats_t;
+
+/* Start a server. dtype: BTC_MIXED_F32 or BTC_F64. slots: 1..64 concurrent
+ * requests. hbm_budget_bytes: device memory the server may hold in plans.
+ * cache_factors: keep factors for re-solve requests. */
+int btc_server_start(btc_server_t *out, int dtype, int slots, int64_t hbm_budget_bytes, int cache_factors);
+
+/* Enqueue a request (returns at once); *ticket identifies it. Errors:
+ * BTC_ERR_ARG, BTC_ERR_UNSUPPORTED, BTC_ERR_OOM (larger than the budget). */
+int btc_server_submit(btc_server_t s, const btc_request *req, int64_t *ticket);
+
+/* Result of a request: returns 1 while it is queued or running (wait = 0),
+ * BTC_OK once done (wait = 1 blocks until then); *status is the request's own
+ * status (BTC_OK, BTC_ERR_NOT_SPD, BTC_ERR_NOT_CONVERGED, ...). */
+int btc_server_poll(btc_server_t s, int64_t ticket, int wait, int *status, int *iters, double *relres,
+                    double *latency_us);
+
+int btc_server_stats(btc_server_t s, btc_server_stats_t *st);
+
+/* Finish every queued request, release all plans and streams. */
+int btc_server_stop(btc_server_t s);
 
 #ifdef __cplusplus
 }

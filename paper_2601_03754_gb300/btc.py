@@ -61,6 +61,12 @@ _SIGS = {
     "btc_residual": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
     "btc_residual_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
     "btc_free": [_vp],
+    "btc_plan_set_stream": [_vp, _vp],
+    "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
+    "btc_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_int64)],
+    "btc_server_poll": [_vp, ctypes.c_int64, ctypes.c_int, _ip, _ip, _dp, _dp],
+    "btc_server_stats": [_vp, _vp],
+    "btc_server_stop": [_vp],
     "btc_batch_plan": [ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, ctypes.c_int, _vp],
     "btc_batch_query": [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)],
     "btc_batch_factor": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
@@ -316,4 +322,79 @@ def btc_batch_info(batch):
 
 def btc_batch_free(batch):
     batch.free()
+    return OK
+
+
+def btc_plan_set_stream(plan, stream):
+    return _check(load().btc_plan_set_stream(plan.h, _stream(stream)))
+
+
+class btc_request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("n", ctypes.c_int), ("D", _vp), ("B", _vp), ("b", _vp), ("x", _vp),
+                ("factor_id", ctypes.c_int64), ("tol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
+class btc_server_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("cache_hits", ctypes.c_int64), ("cache_misses", ctypes.c_int64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Server:
+    """Owning handle of a btc_server_t (stopped by stop() or garbage collection)."""
+
+    def __init__(self, dtype=MIXED_F32, slots=4, hbm_budget_bytes=8 << 30, cache_factors=True):
+        h = _vp()
+        _check(load().btc_server_start(ctypes.byref(h), dtype, slots, int(hbm_budget_bytes), int(cache_factors)))
+        self.h = h
+
+    def stop(self):
+        if getattr(self, "h", None):
+            load().btc_server_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+
+def btc_server_start(dtype=MIXED_F32, slots=4, hbm_budget_bytes=8 << 30, cache_factors=True):
+    return Server(dtype, slots, hbm_budget_bytes, cache_factors)
+
+
+def btc_server_submit(server, N, n, D, B, b, x, factor_id=-1, tol=1e-10, maxit=30):
+    req = btc_request(N, n, _ptr(D), _ptr(B), _ptr(b), _ptr(x), factor_id, tol, maxit)
+    t = ctypes.c_int64(0)
+    _check(load().btc_server_submit(server.h, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def btc_server_poll(server, ticket, wait=True):
+    """None while queued/running (wait=False); else dict(status, iters, relres, latency_us)."""
+    st = ctypes.c_int(0)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0)
+    lat = ctypes.c_double(0)
+    rc = load().btc_server_poll(server.h, ticket, int(wait), ctypes.byref(st), ctypes.byref(it), ctypes.byref(rel),
+                                ctypes.byref(lat))
+    if rc == 1:
+        return None
+    _check(rc)
+    return {"status": st.value, "iters": it.value, "relres": rel.value, "latency_us": lat.value}
+
+
+def btc_server_stats(server):
+    s = btc_server_stats_t()
+    _check(load().btc_server_stats(server.h, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def btc_server_stop(server):
+    server.stop()
     return OK

@@ -371,6 +371,12 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   return BTC_OK;
 }
 
+int btc_plan_set_stream(btc_plan_t p, void *stream) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_stream: NULL plan");
+  p->stream = (cudaStream_t)stream;
+  return BTC_OK;
+}
+
 int btc_plan_set_schedule(btc_plan_t p, int mode) {
   if (!p || (mode != BTC_SCHED_LEVELS && mode != BTC_SCHED_FLOW))
     return fail(BTC_ERR_ARG, "btc_plan_set_schedule: invalid arguments");

@@ -89,6 +89,27 @@ def bt_random_torch(N: int, n: int, delta: float = 1.0, seed: int = 0, device="c
     return D.contiguous(), B.contiguous()
 
 
+def mpc_torch(N: int, n: int, seed: int = 0, device="cuda"):
+    """MPC-like reduced KKT Hessian drawn on `device` for large serving pools.
+    Same structure as mpc(); the stable dynamics are A_k = 0.95 Q_k with Q_k a
+    random orthogonal matrix (QR of a Gaussian), so every eigenvalue of A_k has
+    modulus 0.95 without a per-block eigenvalue solve."""
+    import torch
+    if n % 2:
+        raise ValueError("mpc generator needs an even block size (inputs of size n/2)")
+    g_ = torch.Generator(device=device)
+    g_.manual_seed(seed)
+    G = torch.randn((N, n, n), generator=g_, device=device, dtype=torch.float64)
+    Q, Rr = torch.linalg.qr(G)
+    Q = Q * torch.sign(torch.diagonal(Rr, dim1=1, dim2=2))[:, None, :]
+    A = 0.95 * Q
+    Bu = torch.randn((N, n, n // 2), generator=g_, device=device, dtype=torch.float64) / math.sqrt(n)
+    D = torch.eye(n, device=device, dtype=torch.float64)[None] + Bu @ Bu.transpose(1, 2)
+    D[1:] += A[1:] @ A[1:].transpose(1, 2)
+    B = -A[1:].clone()
+    return D.contiguous(), B.contiguous()
+
+
 def _stable_dynamics(rng, count, n, radius=0.95):
     A = rng.standard_normal((count, n, n))
     if count == 0:

@@ -411,3 +411,12 @@ def test_planted_mistake_is_caught(tag, old, new, which, golden_dir):
     with oracle.use_variant(src.replace(old, new), tag):
         with pytest.raises((AssertionError, oracle.NotSPD, ZeroDivisionError, ValueError, IndexError)):
             _run_pins(which, golden_dir)
+
+
+def test_mpc_torch_generator_is_spd_with_radius_095():
+    torch = pytest.importorskip("torch")
+    D, B = gen.mpc_torch(9, 6, seed=3, device="cpu")
+    A = -B.numpy()
+    assert np.allclose(np.abs(np.linalg.eigvals(A)), 0.95)
+    w = np.linalg.eigvalsh(oracle.assemble(D.numpy(), B.numpy()))
+    assert w.min() > 0
