@@ -160,7 +160,7 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline_sample(budget_s=12.0, max_reps=8):
+def cpu_baseline_sample(budget_s=12.0, max_reps=200):
     import oracle
     from paper_2601_03754_gb300 import gen
     oracle.build()
@@ -427,7 +427,7 @@ def main():
                       "p99_us": 1000 * float(np.percentile(np.asarray(ts64), 99))},
         "speedup_vs_plain_f64": ms64 / ms,
         "phases_ms": {"factor_mixed": t_fact, "one_solve_mixed": t_solve},
-        "roofline": {"kernel": "k_factor_level (all levels of one factorization)", "bound": "alu",
+        "roofline": {"kernel": "k_factor_flow + FP64 root (one factorization, btc_factor)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic,
                      "peak_kind": f"FP32 FFMA: {SMS} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (derived)",
