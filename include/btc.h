@@ -113,6 +113,21 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream);
 enum btc_schedule_mode { BTC_SCHED_LEVELS = 0, BTC_SCHED_FLOW = 1 };
 int btc_plan_set_schedule(btc_plan_t p, int mode);
 
+/*
+ * Factorization variant (default BTC_VARIANT_HYBRID).
+ * BTC_VARIANT_HYBRID: Alg. 5 — hybrid left/right-looking; the update of the
+ *   upper neighbour is deferred to the next level, every block has one writer
+ *   per level, results are deterministic.
+ * BTC_VARIANT_RIGHT_LOOKING: Alg. 6 — fully right-looking; after an explicit
+ *   packing pass (its first parallel loop), each node updates both neighbours'
+ *   diagonal blocks at once with floating-point atomics (at most two writers
+ *   per block), shortening the per-level chain by the deferred syrk; the
+ *   summation order of the two updates is not fixed, so results may differ
+ *   from run to run by rounding.
+ */
+enum btc_variant { BTC_VARIANT_HYBRID = 0, BTC_VARIANT_RIGHT_LOOKING = 1 };
+int btc_plan_set_variant(btc_plan_t p, int variant);
+
 /* Rebind the plan's work to another CUDA stream (NULL = legacy default
  * stream). Work already enqueued on the old stream is not waited for. */
 int btc_plan_set_stream(btc_plan_t p, void *stream);

@@ -62,6 +62,7 @@ _SIGS = {
     "btc_residual_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _dp, _vp],
     "btc_free": [_vp],
     "btc_plan_set_stream": [_vp, _vp],
+    "btc_plan_set_variant": [_vp, ctypes.c_int],
     "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
     "btc_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_int64)],
     "btc_server_poll": [_vp, ctypes.c_int64, ctypes.c_int, _ip, _ip, _dp, _dp],
@@ -323,6 +324,13 @@ def btc_batch_info(batch):
 def btc_batch_free(batch):
     batch.free()
     return OK
+
+
+VARIANT_HYBRID, VARIANT_RIGHT_LOOKING = 0, 1
+
+
+def btc_plan_set_variant(plan, variant):
+    return _check(load().btc_plan_set_variant(plan.h, variant))
 
 
 def btc_plan_set_stream(plan, stream):

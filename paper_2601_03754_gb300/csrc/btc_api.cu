@@ -125,7 +125,8 @@ struct btc_plan_s {
   void *d_y = nullptr;        // work vector [N][np][kMaxCols]
   // persistent dataflow launches
   int sched = BTC_SCHED_FLOW;
-  int32_t *d_fac_deps = nullptr;
+  int variant = BTC_VARIANT_HYBRID;
+  int32_t *d_fac_deps = nullptr, *d_fac_deps_rl = nullptr;
   SolveFlowItem *d_solve_flow = nullptr;
   int n_fac = 0, n_solve = 0;
   int *d_flow = nullptr;  // [0] factor ticket, [1] solve ticket, [2] status, then done flags
@@ -337,10 +338,13 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   p->n_solve = (int)p->hp.solve_flow.size();
   const size_t nflags = kFlowHeader + (size_t)std::max(p->n_fac, p->n_solve);
   if ((e = cudaMalloc(&p->d_fac_deps, p->hp.fac_deps.size() * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_fac_deps_rl, p->hp.fac_deps_rl.size() * sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_solve_flow, p->hp.solve_flow.size() * sizeof(SolveFlowItem))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_flow, nflags * sizeof(int))) != cudaSuccess)
     return cleanup(fail(BTC_ERR_OOM, "btc_plan: flow allocation: %s", cudaGetErrorString(e)));
   if ((e = cudaMemcpy(p->d_fac_deps, p->hp.fac_deps.data(), p->hp.fac_deps.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_fac_deps_rl, p->hp.fac_deps_rl.data(), p->hp.fac_deps_rl.size() * sizeof(int32_t),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_solve_flow, p->hp.solve_flow.data(), p->hp.solve_flow.size() * sizeof(SolveFlowItem),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -352,7 +356,8 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
       (rc = set_smem(ks.fwd, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.bwd, ks.bwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.resid, residual_smem_bytes(n, kMaxCols))) ||
-      (rc = set_smem(ks.fac_flow, ks.fac_smem)) ||
+      (rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.fac_flow_rl, ks.fac_smem)) ||
+      (rc = set_smem(ks.fac_rl, ks.fac_smem)) || (rc = set_smem(ks.root_rl, ks.root_smem)) ||
       (rc = set_smem(ks.solve_flow, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))))
     return cleanup(rc);
   {
@@ -368,6 +373,13 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
     p->solve_grid = std::max(1, bs_ * sms);
   }
   *out = p;
+  return BTC_OK;
+}
+
+int btc_plan_set_variant(btc_plan_t p, int variant) {
+  if (!p || (variant != BTC_VARIANT_HYBRID && variant != BTC_VARIANT_RIGHT_LOOKING))
+    return fail(BTC_ERR_ARG, "btc_plan_set_variant: invalid arguments");
+  p->variant = variant;
   return BTC_OK;
 }
 
@@ -402,6 +414,44 @@ int btc_factor(btc_plan_t p, const void *D, const void *B) {
   a.info = p->d_info;
   a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
   const bool mixed_root = p->dtype == BTC_MIXED_F32;
+  if (p->variant == BTC_VARIANT_RIGHT_LOOKING) {
+    // Alg. 6: packing pass, then every level from the pools with immediate (atomic) updates
+    InstDesc d{D, B, p->N, p->n};
+    int rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n);
+    if (rc) return rc;
+    BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
+    const int last = p->hp.levels - 1;
+    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
+    if (p->sched == BTC_SCHED_FLOW) {
+      if (nflow > 0) {
+        BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+        BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
+        a.items = p->d_fac;
+        a.count = nflow;
+        const int32_t *deps = p->d_fac_deps_rl;
+        int zero = 0;
+        if ((rc = launch_n(k.fac_flow_rl, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d,
+                           deps, zero, flow_sync(p, 0))))
+          return rc;
+      }
+    } else {
+      for (int l = 0; l < p->hp.levels - (mixed_root ? 1 : 0); ++l) {
+        a.items = p->d_fac + p->fac_off[l];
+        a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
+        if ((rc = launch_n(k.fac_rl, a.count, k.fac_threads, k.fac_smem, p->stream, a, d))) return rc;
+      }
+    }
+    if (mixed_root) {
+      a.items = p->d_fac + p->fac_off[last];
+      a.count = 1;
+      if ((rc = launch_n(k.root_rl, 1, k.root_threads, k.root_smem, p->stream, a, d))) return rc;
+    }
+    p->D = D;
+    p->B = B;
+    p->factored = true;
+    p->anorm_valid = false;
+    return BTC_OK;
+  }
   if (p->sched == BTC_SCHED_FLOW) {
     // all levels but the FP64 root (mixed path) in one persistent launch
     const int last = p->hp.levels - 1;
@@ -665,9 +715,9 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
 int btc_free(btc_plan_t p) {
   if (!p) return BTC_OK;
   if (p->stream || p->dpool) cudaStreamSynchronize(p->stream);
-  void *dev[] = {p->dpool, p->epool, p->d_fac, p->d_fwd,        p->d_bwd,      p->d_info,
-                 p->d_norms, p->d_y,   p->s_D,   p->d_fac_deps, p->d_solve_flow, p->d_flow,
-                 p->s_B,     p->s_b,   p->s_x};
+  void *dev[] = {p->dpool, p->epool, p->d_fac, p->d_fwd,        p->d_bwd,          p->d_info,
+                 p->d_norms, p->d_y,   p->s_D,   p->d_fac_deps, p->d_solve_flow,     p->d_flow,
+                 p->s_B,     p->s_b,   p->s_x,   p->d_fac_deps_rl};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_norms) cudaFreeHost(p->h_norms);

@@ -49,9 +49,27 @@ constexpr size_t factor_smem_bytes() {
 // Cholesky, the one onto S_{e+s} in registers), then receive S(e,e-s) and
 // S(e,e+s) by asynchronous copies that overlap the Cholesky, and finally hold
 // U(e,e-s), U(e,e+s) for the syrk and the fill.
-template <typename T, typename P, typename S, int NP, int R, bool FIRST>
+// Atomic a -= X^T Y into a pool block (Alg. 6: two nodes of one level may
+// update the same diagonal block; floating-point atomics, contention <= 2).
+template <class C, typename T, typename P>
+__device__ __forceinline__ void tile_atomic_sub_xty(P *g, const T *X, const T *Y, int r0, int c0) {
+  T a[C::R][C::R];
+  tile_zero<C>(a);
+  tile_sub_xty<C, C::NP>(a, X, Y, r0, c0);
+#pragma unroll
+  for (int r = 0; r < C::R; ++r)
+#pragma unroll
+    for (int c = 0; c < C::R; ++c) atomicAdd(g + (size_t)(r0 + r) * C::NP + c0 + c, (P)a[r][c]);
+}
+
+// RL = true: the fully right-looking form of Alg. 6 — no deferred updates;
+// after its trsm the node subtracts U(e,e-s)^T U(e,e-s) from Dhat_{e-s} and
+// U(e,e+s)^T U(e,e+s) from Dhat_{e+s} with atomics. Every level reads the
+// pools, which a packing pass has initialized (FIRST must be false).
+template <typename T, typename P, typename S, int NP, int R, bool FIRST, bool RL = false>
 __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorArgs &args, const InstDesc &single,
                                             unsigned char *smem_raw) {
+  static_assert(!(FIRST && RL), "the right-looking form reads packed pools at every level");
   using C = TileCfg<T, NP, R>;
   T *sS = reinterpret_cast<T *>(smem_raw);  // S_e -> U_e
   T *sA = sS + C::BLK;                      // P_a, then S(e,e-s) -> U(e,e-s)
@@ -82,13 +100,13 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
     if (has_next && upper_tile) tile_from_user<C>(d, uD + (e + 1) * ubs, ins.n, r0, c0, true, T(1));
     __syncthreads();
   } else {
-    const bool pa = it.p_a >= 0, pb = it.p_b >= 0;
+    const bool pa = !RL && it.p_a >= 0, pb = !RL && it.p_b >= 0;
     if constexpr (ASYNC) {
       block_to_smem_async<C>(sS, dpool + it.d_self);
       if (pa) block_to_smem_async<C>(sA, epool + it.p_a);
       if (pb) block_to_smem_async<C>(sB, epool + it.p_b);
     }
-    if (has_next && upper_tile) tile_from_pool<C>(d, dpool + it.d_next, r0, c0);
+    if (!RL && has_next && upper_tile) tile_from_pool<C>(d, dpool + it.d_next, r0, c0);
     if constexpr (ASYNC) {
       cp_async_commit_wait_all();
     } else {
@@ -127,8 +145,13 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
 
-  // ---- S_{e+s} -= U_dn^T U_dn
-  if (has_next && upper_tile) {
+  // ---- S_{e+s} -= U_dn^T U_dn (and, right-looking, S_{e-s} -= U_up^T U_up)
+  if constexpr (RL) {
+    if (upper_tile) {
+      if (has_next) tile_atomic_sub_xty<C>(dpool + it.d_next, sB, sB, r0, c0);
+      if (it.d_prev >= 0) tile_atomic_sub_xty<C>(dpool + it.d_prev, sA, sA, r0, c0);
+    }
+  } else if (has_next && upper_tile) {
     tile_sub_xty<C, NP>(d, sB, sB, r0, c0);
     tile_to_pool<C>(dpool + it.d_next, d, r0, c0);
   }
@@ -143,11 +166,11 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
 }
 
 // One launch per dissection level: CTA b eliminates item b of the level.
-template <typename T, typename P, typename S, int NP, int R, bool FIRST>
+template <typename T, typename P, typename S, int NP, int R, bool FIRST, bool RL = false>
 __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT) k_factor_level(FactorArgs args, InstDesc single) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FactorItem it = args.items[blockIdx.x];
-  factor_node<T, P, S, NP, R, FIRST>(it, args, single, smem_raw);
+  factor_node<T, P, S, NP, R, FIRST, RL>(it, args, single, smem_raw);
 }
 
 // Persistent dataflow form: all levels in one launch. CTAs claim items in
@@ -178,6 +201,49 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R
       else factor_node<T, P, S, NP, R, false>(it, args, single, smem_raw);
     }
     flow_publish(fs, t);
+  }
+}
+
+// Persistent dataflow form of Alg. 6 (right-looking, atomics): every level
+// reads the packed pools; each item waits for the two nodes of the previous
+// level that last update its diagonal block and write its two fill blocks.
+template <typename T, typename P, typename S, int NP, int R>
+__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R>::value))
+    k_factor_flow_rl(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_slot, s_ok;
+  (void)nfirst;
+  for (;;) {
+    const int t = flow_claim(fs, args.count, &s_slot);
+    if (t < 0) break;
+    const FactorItem it = args.items[t];
+    if (flow_wait(fs, deps + 3 * t, 3, &s_ok)) factor_node<T, P, S, NP, R, false, true>(it, args, single, smem_raw);
+    flow_publish(fs, t);
+  }
+}
+
+// Packing pass of Alg. 6 (its first parallel loop): Dhat_v <- D_v for every
+// node (upper-form copy of the caller's lower triangle, identity padding) and
+// the level-1 slot of B_v in the orientation level 1 eliminates: slot k
+// (1-based, pair k, k+1) holds S(k, k+1) = B_k^T when k is odd, else
+// S(k+1, k) = B_k. One CTA per node.
+template <typename P, typename S, int NP>
+__global__ void k_pack_matrix(P *dpool, P *epool, const S *D, const S *B, int N, int n) {
+  const int v = blockIdx.x;  // 0-based node
+  const size_t ubs = (size_t)n * n, bs = (size_t)NP * NP;
+  for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) {
+    const int i = q / NP, j = q % NP;
+    P val;
+    if (i < n && j < n) val = (P)(i <= j ? D[v * ubs + (size_t)j * n + i] : D[v * ubs + (size_t)i * n + j]);
+    else val = (i == j) ? P(1) : P(0);
+    dpool[v * bs + q] = val;
+    if (v + 1 < N) {
+      const bool odd = ((v + 1) & 1) != 0;  // 1-based slot index k = v + 1
+      P b;
+      if (i < n && j < n) b = (P)(odd ? B[v * ubs + (size_t)j * n + i] : B[v * ubs + (size_t)i * n + j]);
+      else b = P(0);
+      epool[v * bs + q] = b;
+    }
   }
 }
 

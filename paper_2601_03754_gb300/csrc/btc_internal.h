@@ -35,6 +35,7 @@ struct FactorItem {
   int64_t p_a;     // deferred block onto Dhat_e:     U(e+s/2, e)        (level > 1)
   int64_t p_b;     // deferred block onto Dhat_{e+s}: U(e+3s/2, e+s)     (level > 1)
   int64_t fill;    // new slot at level l+1 for the pair (e-s, e+s)
+  int64_t d_prev;  // Dhat_{e-s} (Alg. 6 updates it immediately; Alg. 5 defers the update)
   int32_t node;    // e, 0-based, within its instance
   int32_t flags;
   int32_t inst;    // instance index (batched plans)
@@ -84,6 +85,7 @@ struct HostPlan {
   // dataflow form: factor items in level order with the (<= 3) items of the
   // previous level that produce their inputs, and the fused solve list
   std::vector<int32_t> fac_deps;           // 3 per factor item (flat level order), -1: none
+  std::vector<int32_t> fac_deps_rl;        // the same for the right-looking variant (Alg. 6)
   std::vector<SolveFlowItem> solve_flow;
   int64_t offdiag = 0, fill = 0;
   std::vector<int64_t> level_slot_off;  // first U slot of each level (in blocks)

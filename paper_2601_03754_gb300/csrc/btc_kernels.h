@@ -22,6 +22,8 @@ struct KernelSet {
   size_t root_smem = 0;
   // persistent dataflow forms (all levels in one launch)
   const void *fac_flow = nullptr, *solve_flow = nullptr;
+  // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, FP64 root
+  const void *pack_matrix = nullptr, *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
   // solve
   const void *fwd = nullptr, *bwd = nullptr;
   size_t (*fwd_smem)(int m) = nullptr;

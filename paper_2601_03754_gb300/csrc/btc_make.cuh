@@ -32,10 +32,14 @@ KernelSet make_set() {
   if constexpr (MIXED) {
     k.root_first = (const void *)&k_factor_level<double, T, S, NP, R, true>;
     k.root_rest = (const void *)&k_factor_level<double, T, S, NP, R, false>;
+    k.root_rl = (const void *)&k_factor_level<double, T, S, NP, R, false, true>;
     k.root_threads = TileCfg<double, NP, R>::NT;
     k.root_smem = factor_smem_bytes<double, NP, R>();
   }
   k.fac_flow = (const void *)&k_factor_flow<T, T, S, NP, R>;
+  k.pack_matrix = (const void *)&k_pack_matrix<T, S, NP>;
+  k.fac_rl = (const void *)&k_factor_level<T, T, S, NP, R, false, true>;
+  k.fac_flow_rl = (const void *)&k_factor_flow_rl<T, T, S, NP, R>;
   k.solve_flow = (const void *)&k_solve_flow<T, NP>;
   k.fwd = (const void *)&k_fwd_level<T, NP>;
   k.bwd = (const void *)&k_bwd_level<T, NP>;

@@ -71,6 +71,7 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
       it.p_a = (l > 1 && e + h <= N) ? eOff(l - 1, 2 * e / s) : -1;
       it.p_b = (l > 1 && e + s + h <= N) ? eOff(l - 1, 2 * e / s + 2) : -1;
       it.fill = (e > s && e + s <= N) ? eOff(l + 1, (e - s) / (2 * s)) : -1;
+      it.d_prev = (e > s) ? dOff(e - s) : -1;
       it.flags = 0;
       if (it.fill >= 0 && (((e - s) / (2 * s)) & 1)) it.flags |= FI_FILL_UPFIRST;
       if (l == levels) it.flags |= FI_ROOT;
@@ -131,6 +132,7 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
     for (int l = 1; l <= levels; ++l)
       for (const FactorItem &it : P->lv[l - 1].fac) fac_index[it.node + 1] = idx++;
     P->fac_deps.assign(3 * (size_t)idx, -1);
+    P->fac_deps_rl.assign(3 * (size_t)idx, -1);
     idx = 0;
     for (int l = 1; l <= levels; ++l) {
       const int64_t s = int64_t(1) << (l - 1), h = s / 2;
@@ -140,6 +142,10 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
           const int64_t cand[3] = {e - h, e + h, e + 3 * h};
           for (int k = 0; k < 3; ++k)
             if (cand[k] >= 1 && cand[k] <= N) P->fac_deps[3 * (size_t)idx + k] = fac_index[cand[k]];
+          // Alg. 6: Dhat_e receives its last (atomic) updates at level l-1 from e-h and e+h,
+          // which also write the two fill blocks e reads; nothing is deferred.
+          for (int k = 0; k < 2; ++k)
+            if (cand[k] >= 1 && cand[k] <= N) P->fac_deps_rl[3 * (size_t)idx + k] = fac_index[cand[k]];
         }
         ++idx;
       }
