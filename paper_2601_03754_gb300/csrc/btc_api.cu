@@ -36,7 +36,7 @@ int fail(int code, const char *fmt, ...) {
 
 
 // ------------------------------------------------------------ kernel table
-static constexpr int kMaxSets = 10;
+static constexpr int kMaxSets = 12;
 static KernelSet g_sets[3][kMaxSets];
 static int g_nsets[3] = {0, 0, 0};
 static std::once_flag g_once;

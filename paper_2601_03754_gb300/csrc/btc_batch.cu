@@ -64,7 +64,7 @@ __global__ void k_batch_unpack(const T *y, const BatchNode *nodes, const InstDes
 template <typename T>
 __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const BatchNode *nodes, const InstDesc *inst,
                                                                 const BatchVec *vec, int np, double *norms) {
-  constexpr int NMAX = 96;  // largest compiled block size
+  constexpr int NMAX = 128;  // largest compiled block size
   __shared__ double xs[3 * NMAX];
   __shared__ double ps[kResParts * NMAX];
   const BatchNode nd = nodes[blockIdx.x];

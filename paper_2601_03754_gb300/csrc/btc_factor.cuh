@@ -222,6 +222,63 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R
   }
 }
 
+// a -= X^T Y with X, Y read from a pool block in global memory (type P),
+// over k = 0..np-1.
+template <class C, typename T, typename P>
+__device__ __forceinline__ void tile_sub_xty_gmem(T (&a)[C::R][C::R], const P *X, const P *Y, int r0, int c0) {
+#pragma unroll 2
+  for (int k = 0; k < C::NP; ++k) {
+    P xv[C::R], yv[C::R];
+    vload_cg<P, C::R>(X + (size_t)k * C::NP + r0, xv);
+    vload_cg<P, C::R>(Y + (size_t)k * C::NP + c0, yv);
+#pragma unroll
+    for (int r = 0; r < C::R; ++r)
+#pragma unroll
+      for (int c = 0; c < C::R; ++c) a[r][c] = fma(-(T)xv[r], (T)yv[c], a[r][c]);
+  }
+}
+
+// FP64 top-separator Cholesky for block sizes whose three FP64 shared blocks
+// do not fit in shared memory (np >= 128): one shared block holds S; the
+// deferred block P_a (Alg. 5) is read from the FP32 pool directly.
+template <typename P, typename S, int NP, int R, bool FIRST, bool RL>
+__global__ void __launch_bounds__(TileCfg<double, NP, R>::NT) k_root_large(FactorArgs args, InstDesc single) {
+  using C = TileCfg<double, NP, R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *sS = reinterpret_cast<double *>(smem_raw);
+  double *dinv = sS + C::BLK;
+  const FactorItem it = args.items[blockIdx.x];
+  P *dpool = reinterpret_cast<P *>(args.dpool);
+  const P *epool = reinterpret_cast<const P *>(args.epool);
+  const int ty = threadIdx.x / C::TXN, tx = threadIdx.x % C::TXN;
+  const int r0 = ty * R, c0 = tx * R;
+  const InstDesc ins = args.inst ? args.inst[it.inst] : single;
+  unsigned long long *info = args.info + it.inst;
+  if constexpr (FIRST) {
+    const S *uD = reinterpret_cast<const S *>(ins.D);
+    user_to_smem<C>(sS, uD + (size_t)it.node * ins.n * ins.n, ins.n, true, 1.0);
+  } else {
+    block_to_smem<C>(sS, dpool + it.d_self);
+  }
+  __syncthreads();
+  if (!FIRST && !RL && it.p_a >= 0) {
+    if (c0 >= r0) {
+      double a[R][R];
+      tile_from_smem<C>(a, sS, r0, c0);
+      tile_sub_xty_gmem<C>(a, epool + it.p_a, epool + it.p_a, r0, c0);
+      tile_to_smem<C>(sS, a, r0, c0);
+    }
+    __syncthreads();
+  }
+  block_potrf_upper<C>(sS, dinv, info, it.node, r0, c0);
+  smem_to_block<C>(dpool + it.d_self, sS, true);
+}
+
+template <int NP, int R>
+constexpr size_t root_large_smem_bytes() {
+  return sizeof(double) * ((size_t)TileCfg<double, NP, R>::BLK + NP);
+}
+
 // Packing pass of Alg. 6 (its first parallel loop): Dhat_v <- D_v for every
 // node (upper-form copy of the caller's lower triangle, identity padding) and
 // the level-1 slot of B_v in the orientation level 1 eliminates: slot k

@@ -10,6 +10,7 @@ void register_f32(KernelSet *t, int *count) {
   t[c++] = make_set<float, float, 48, false>();
   t[c++] = make_set<float, float, 64, false>();
   t[c++] = make_set<float, float, 96, false>();
+  t[c++] = make_set<float, float, 128, false>();
   *count = c;
 }
 }  // namespace btc

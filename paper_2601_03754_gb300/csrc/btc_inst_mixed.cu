@@ -11,6 +11,7 @@ void register_mixed(KernelSet *t, int *count) {
   t[c++] = make_set<float, double, 48, true>();
   t[c++] = make_set<float, double, 64, true>();
   t[c++] = make_set<float, double, 96, true>();
+  t[c++] = make_set<float, double, 128, true>();
   *count = c;
 }
 }  // namespace btc

@@ -9,7 +9,7 @@ namespace btc {
 // Register tile edge per padded block size: (np/R)^2 threads per CTA.
 template <int NP>
 struct TileEdge {
-  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : 4;  // 96 -> 576 threads
+  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : NP == 128 ? 8 : 4;  // 96 -> 576 threads
 };
 
 template <typename T, int NP>
@@ -29,7 +29,13 @@ KernelSet make_set() {
   k.fac_rest = (const void *)&k_factor_level<T, T, S, NP, R, false>;
   k.fac_threads = TileCfg<T, NP, R>::NT;
   k.fac_smem = factor_smem_bytes<T, NP, R>();
-  if constexpr (MIXED) {
+  if constexpr (MIXED && NP >= 128) {
+    k.root_first = (const void *)&k_root_large<T, S, NP, R, true, false>;
+    k.root_rest = (const void *)&k_root_large<T, S, NP, R, false, false>;
+    k.root_rl = (const void *)&k_root_large<T, S, NP, R, false, true>;
+    k.root_threads = TileCfg<double, NP, R>::NT;
+    k.root_smem = root_large_smem_bytes<NP, R>();
+  } else if constexpr (MIXED) {
     k.root_first = (const void *)&k_factor_level<double, T, S, NP, R, true>;
     k.root_rest = (const void *)&k_factor_level<double, T, S, NP, R, false>;
     k.root_rl = (const void *)&k_factor_level<double, T, S, NP, R, false, true>;

@@ -10,12 +10,15 @@
 
 namespace btc {
 
-static const int kSizes[] = {8, 16, 32, 48, 64, 96};
+static const int kSizes[] = {8, 16, 32, 48, 64, 96, 128};
 
+// Smallest compiled block size >= n. FP64 stops at 96: three 128 x 128 FP64
+// blocks do not fit in one SM's shared memory.
 int padded_size(int n, int dtype) {
-  (void)dtype;
-  for (int s : kSizes)
+  for (int s : kSizes) {
+    if (dtype == 0 && s > 96) break;
     if (n <= s) return s;
+  }
   return 0;
 }
 

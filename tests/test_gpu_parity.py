@@ -215,3 +215,29 @@ def test_refinement_on_ill_conditioned_block_laplacian(N):
         it, rel, rc = btc.btc_solve_refined(p, bd, xd, 1, tol=1e-10, maxit=50)
         assert rc == btc.OK and rel <= 1e-10
         assert oracle.relres(D, B, xd.cpu().numpy(), b) <= 1e-10
+
+
+@pytest.mark.parametrize("dt", [btc.F32, btc.MIXED_F32], ids=["f32", "mixed"])
+@pytest.mark.parametrize("N,n", [(1, 128), (5, 128), (37, 100), (130, 128)])
+def test_block_size_128(N, n, dt):
+    D, B = gen.bt_random(N, n, delta=1.0, seed=N + n)
+    p, Dd, Bd = factor_on_gpu(D, B, dt)
+    assert btc.btc_info(p)[0] == btc.OK
+    err, rec = compare_factor_with_oracle(p, D, B, FACT_TOL[dt])
+    assert err <= FACT_TOL[dt] and rec <= REC_TOL[dt], (err, rec)
+    b = gen.rhs(N, n, 2, seed=N)
+    if dt == btc.MIXED_F32:
+        bd = dev(b, torch.float64)
+        xd = torch.zeros_like(bd)
+        it, rel, rc = btc.btc_solve_refined(p, bd, xd, 2, tol=1e-10, maxit=30)
+        assert rc == btc.OK and oracle.relres(D, B, xd.cpu().numpy(), b) <= 1e-10
+    else:
+        x = dev(b, torch.float32)
+        btc.btc_solve(p, x, 2)
+        assert oracle.relres(D, B, x.cpu().numpy().astype(np.float64), b) <= 1e-5
+
+
+def test_f64_plans_stop_at_96():
+    with pytest.raises(btc.BtcError) as ei:
+        btc.btc_plan(4, 128, btc.F64)
+    assert ei.value.code == btc.ERR_UNSUPPORTED

@@ -37,10 +37,12 @@ def test_version_and_last_error():
 
 
 def test_describe_rejects_oversized_blocks():
-    assert btc.btc_describe(16, 96, btc.F32)["np"] == 96
-    with pytest.raises(btc.BtcError) as ei:
-        btc.btc_describe(16, 97, btc.F32)
-    assert ei.value.code == btc.ERR_UNSUPPORTED
+    assert btc.btc_describe(16, 96, btc.F64)["np"] == 96
+    assert btc.btc_describe(16, 128, btc.F32)["np"] == 128
+    for n, dt in ((97, btc.F64), (129, btc.F32), (129, btc.MIXED_F32)):
+        with pytest.raises(btc.BtcError) as ei:
+            btc.btc_describe(16, n, dt)
+        assert ei.value.code == btc.ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("N", list(range(1, 130)) + [255, 256, 257, 1000, 1024, 4096])
