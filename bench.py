@@ -249,6 +249,40 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
     return out
 
 
+def large_block_measure(btc, gen, torch, stream, flush, steps=5):
+    """Config: N=4096, n=128 (delta in {1, 1e-3, 1e-6}): FP32 factor on CUDA cores + FP64 root,
+    residual and refinement to 1e-10; error against the FP64 solution reported per delta."""
+    out = {"N": 4096, "n": 128, "form": "mixed_f32 (FFMA register tiles)"}
+    for delta in (1.0, 1e-3, 1e-6):
+        D, B = gen.bt_random_torch(4096, 128, delta=delta, seed=7)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(11)
+        b = torch.randn((4096 * 128, 1), generator=g, device="cuda", dtype=torch.float64)
+        x = torch.zeros_like(b)
+        p = btc.btc_plan(4096, 128, btc.MIXED_F32, stream)
+        info = btc.btc_plan_query(p)
+        ts, tf = [], []
+        with torch.cuda.stream(stream):
+            for rep in range(steps + 1):
+                flush.fill_(1.0)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                btc.btc_factor(p, D, B)
+                e1.record(stream)
+                it, rel, rc = btc.btc_solve_refined(p, b, x, 1, tol=TOL, maxit=40)
+                e2.record(stream)
+                e2.synchronize()
+                if rep:
+                    ts.append(e0.elapsed_time(e2))
+                    tf.append(e0.elapsed_time(e1))
+        out[str(delta)] = {"ms_factor_solve": statistics.mean(ts), "ms_factor": statistics.mean(tf),
+                           "factor_tflops": info["factor_flops"] / (statistics.mean(tf) * 1e-3) / 1e12,
+                           "refine_iters": it, "relres": rel}
+        p.free()
+        del D, B
+    return out
+
+
 def serving_measure(btc, torch, rates=(1000.0, 4000.0), count=300):
     """Config: Poisson stream of factor+solve requests, n uniform in {12,24,48,96}, N log-uniform
     in [50, 5000], MPC-like generator, 30% re-solves of a cached factor, HBM-footprint admission;
@@ -283,6 +317,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-server measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the N=4096, n=128 measurement")
     ap.add_argument("--profile", choices=["mixed", "f64", "both"], default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
@@ -400,6 +435,7 @@ def main():
 
     batched = batched_measure(btc, gen, torch, max(3, args.steps // 5), stream, flush) if not args.no_batch else None
     serving = serving_measure(btc, torch) if not args.no_serve else None
+    large = large_block_measure(btc, gen, torch, stream, flush) if not args.no_large else None
 
     peaks, pk_kind = _peaks()
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -439,6 +475,7 @@ def main():
         "peaks_source": pk_kind,
         "batched": batched,
         "serving": serving,
+        "large_blocks": large,
         "wall_s_timed": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -128,6 +128,17 @@ int btc_plan_set_schedule(btc_plan_t p, int mode);
 enum btc_variant { BTC_VARIANT_HYBRID = 0, BTC_VARIANT_RIGHT_LOOKING = 1 };
 int btc_plan_set_variant(btc_plan_t p, int variant);
 
+/*
+ * Device-side trace of the persistent launches (for profiling; off by
+ * default). factor_trace / solve_trace: caller-owned device buffers of
+ * 4 * (number of work items) uint64 each (factor items = N; solve items =
+ * forward items of all levels + N backward items), or NULL to disable. Every
+ * item records the global timer (ns) when it was claimed, when its inputs were
+ * ready and when it finished, and the SM it ran on. Items that do not run
+ * (the FP64 root of the mixed path, launched separately) stay untouched.
+ */
+int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
+
 /* Rebind the plan's work to another CUDA stream (NULL = legacy default
  * stream). Work already enqueued on the old stream is not waited for. */
 int btc_plan_set_stream(btc_plan_t p, void *stream);

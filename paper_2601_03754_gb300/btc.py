@@ -63,6 +63,7 @@ _SIGS = {
     "btc_free": [_vp],
     "btc_plan_set_stream": [_vp, _vp],
     "btc_plan_set_variant": [_vp, ctypes.c_int],
+    "btc_plan_set_trace": [_vp, _vp, _vp],
     "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
     "btc_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_int64)],
     "btc_server_poll": [_vp, ctypes.c_int64, ctypes.c_int, _ip, _ip, _dp, _dp],
@@ -324,6 +325,10 @@ def btc_batch_info(batch):
 def btc_batch_free(batch):
     batch.free()
     return OK
+
+
+def btc_plan_set_trace(plan, factor_trace, solve_trace):
+    return _check(load().btc_plan_set_trace(plan.h, _ptr(factor_trace), _ptr(solve_trace)))
 
 
 VARIANT_HYBRID, VARIANT_RIGHT_LOOKING = 0, 1

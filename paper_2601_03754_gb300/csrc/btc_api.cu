@@ -131,6 +131,7 @@ struct btc_plan_s {
   int n_fac = 0, n_solve = 0;
   int *d_flow = nullptr;  // [0] factor ticket, [1] solve ticket, [2] status, then done flags
   int fac_grid = 0, solve_grid = 0;
+  unsigned long long *trace_fac = nullptr, *trace_solve = nullptr;  // caller-owned trace buffers
   // host staging for readbacks
   double *h_norms = nullptr;
   unsigned long long *h_info = nullptr;
@@ -186,6 +187,7 @@ static FlowSync flow_sync(btc_plan_s *p, int which) {
   fs.ticket = p->d_flow + which;
   fs.status = p->d_flow + 2;
   fs.done = p->d_flow + kFlowHeader;
+  fs.trace = which == 0 ? p->trace_fac : p->trace_solve;
   return fs;
 }
 
@@ -373,6 +375,13 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
     p->solve_grid = std::max(1, bs_ * sms);
   }
   *out = p;
+  return BTC_OK;
+}
+
+int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_trace: NULL plan");
+  p->trace_fac = (unsigned long long *)factor_trace;
+  p->trace_solve = (unsigned long long *)solve_trace;
   return BTC_OK;
 }
 

@@ -346,6 +346,7 @@ static FlowSync group_sync(BatchGroup &g, int which) {
   fs.ticket = g.d_flow + which;
   fs.status = g.d_flow + 2;
   fs.done = g.d_flow + kFlowHeader;
+  fs.trace = nullptr;
   return fs;
 }
 

@@ -196,10 +196,14 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R
     const int t = flow_claim(fs, args.count, &s_slot);
     if (t < 0) break;
     const FactorItem it = args.items[t];
+    flow_trace(fs, t, 0);
     if (flow_wait(fs, deps + 3 * t, 3, &s_ok)) {
+      flow_trace(fs, t, 1);
       if (t < nfirst) factor_node<T, P, S, NP, R, true>(it, args, single, smem_raw);
       else factor_node<T, P, S, NP, R, false>(it, args, single, smem_raw);
     }
+    __syncthreads();
+    flow_trace(fs, t, 2);
     flow_publish(fs, t);
   }
 }
@@ -222,61 +226,148 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R
   }
 }
 
-// a -= X^T Y with X, Y read from a pool block in global memory (type P),
-// over k = 0..np-1.
-template <class C, typename T, typename P>
-__device__ __forceinline__ void tile_sub_xty_gmem(T (&a)[C::R][C::R], const P *X, const P *Y, int r0, int c0) {
-#pragma unroll 2
-  for (int k = 0; k < C::NP; ++k) {
-    P xv[C::R], yv[C::R];
-    vload_cg<P, C::R>(X + (size_t)k * C::NP + r0, xv);
-    vload_cg<P, C::R>(Y + (size_t)k * C::NP + c0, yv);
-#pragma unroll
-    for (int r = 0; r < C::R; ++r)
-#pragma unroll
-      for (int c = 0; c < C::R; ++c) a[r][c] = fma(-(T)xv[r], (T)yv[c], a[r][c]);
-  }
+// ------------------------------------------------ FP64 top-separator Cholesky
+// Mixed path: the top separator's Schur complement S (FP32 pool, upper
+// triangle valid) is factored in FP64 by one CTA and the factor is rounded to
+// the FP32 pool. The deferred update S -= P_a^T P_a (Alg. 5, level L-1 block)
+// is applied first in FP32 register tiles, like every other Schur update of
+// this path.
+//
+// The FP64 pipe of this GPU issues about two lanes per clock per SM and a
+// masked lane costs as much as an active one, so the factorization avoids
+// both single-warp panels and tile masks: it is the unblocked right-looking
+// form over a dense list of the upper-triangle elements. At step k every
+// element (i, j) with k+2 <= i <= j is updated, S_ij -= U_ki U_kj, by the
+// threads of warps 1.., in list order (row-major, so the elements still
+// active form a suffix); warp 0 meanwhile updates row k+1 and factors it
+// (pivot, 1/sqrt, row scaling), so that one barrier per column suffices.
+template <int NP>
+struct RootCfg {
+  static constexpr int LD = NP + 1;                // FP64 leading dimension
+  static constexpr int NE = NP * (NP + 1) / 2;     // upper-triangle elements
+  __host__ __device__ static constexpr int row_off(int i) { return i * NP - i * (i - 1) / 2; }
+};
+
+template <int NP, int R>
+constexpr size_t root_smem_bytes() {
+  using C = TileCfg<float, NP, R>;
+  constexpr size_t dbl = sizeof(double) * ((size_t)NP * RootCfg<NP>::LD + NP);
+  constexpr size_t tab = sizeof(unsigned short) * (size_t)RootCfg<NP>::NE;
+  constexpr size_t stage = sizeof(float) * (size_t)C::BLK;  // P_a, before the element list is built
+  return dbl + (tab > stage ? tab : stage);
 }
 
-// FP64 top-separator Cholesky for block sizes whose three FP64 shared blocks
-// do not fit in shared memory (np >= 128): one shared block holds S; the
-// deferred block P_a (Alg. 5) is read from the FP32 pool directly.
 template <typename P, typename S, int NP, int R, bool FIRST, bool RL>
-__global__ void __launch_bounds__(TileCfg<double, NP, R>::NT) k_root_large(FactorArgs args, InstDesc single) {
-  using C = TileCfg<double, NP, R>;
+__global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorArgs args, InstDesc single) {
+  static_assert(sizeof(P) == 4, "the FP64 top-separator kernel serves FP32 pools");
+  using C = TileCfg<float, NP, R>;
+  using RC = RootCfg<NP>;
+  constexpr int NT = C::NT, LD = RC::LD, NE = RC::NE;
+  static_assert(NT >= 64, "a full look-ahead warp and at least one update warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *sS = reinterpret_cast<double *>(smem_raw);
-  double *dinv = sS + C::BLK;
+  double *Sd = reinterpret_cast<double *>(smem_raw);  // NP x LD, upper triangle used
+  double *dinv = Sd + NP * LD;                         // 1 / U_kk
+  unsigned short *tab = reinterpret_cast<unsigned short *>(dinv + NP);  // element list (i | j << 7)
+  float *sA = reinterpret_cast<float *>(dinv + NP);                     // P_a (aliases the list)
+
   const FactorItem it = args.items[blockIdx.x];
   P *dpool = reinterpret_cast<P *>(args.dpool);
   const P *epool = reinterpret_cast<const P *>(args.epool);
-  const int ty = threadIdx.x / C::TXN, tx = threadIdx.x % C::TXN;
-  const int r0 = ty * R, c0 = tx * R;
   const InstDesc ins = args.inst ? args.inst[it.inst] : single;
   unsigned long long *info = args.info + it.inst;
-  if constexpr (FIRST) {
-    const S *uD = reinterpret_cast<const S *>(ins.D);
-    user_to_smem<C>(sS, uD + (size_t)it.node * ins.n * ins.n, ins.n, true, 1.0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // ---- S in FP64
+  if constexpr (FIRST) {  // a single-node problem: the caller's D_1 (lower triangle valid)
+    const S *uD = reinterpret_cast<const S *>(ins.D) + (size_t)it.node * ins.n * ins.n;
+    for (int q = tid; q < NP * NP; q += NT) {
+      const int i = q / NP, j = q % NP;
+      if (i > j) continue;
+      Sd[i * LD + j] = (j < ins.n) ? (double)uD[(size_t)j * ins.n + i] : (i == j ? 1.0 : 0.0);
+    }
+  } else if (!RL && it.p_a >= 0) {
+    block_to_smem_async<C>(sA, epool + it.p_a);
+    const int r0 = (tid / C::TXN) * R, c0 = (tid % C::TXN) * R;
+    float a[R][R];
+    if (c0 >= r0) tile_from_pool<C>(a, dpool + it.d_self, r0, c0);
+    cp_async_commit_wait_all();
+    __syncthreads();
+    if (c0 >= r0) {
+      tile_sub_xty<C, NP>(a, sA, sA, r0, c0);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < R; ++c) Sd[(r0 + r) * LD + c0 + c] = f32_to_f64(a[r][c]);
+    }
   } else {
-    block_to_smem<C>(sS, dpool + it.d_self);
+    const P *g = dpool + it.d_self;
+    for (int q = tid; q < NP * NP; q += NT) {
+      const int i = q / NP, j = q % NP;
+      if (i <= j) Sd[i * LD + j] = f32_to_f64(__ldcg(g + q));
+    }
+  }
+  __syncthreads();  // sA is dead from here on
+  for (int q = tid; q < NP * NP; q += NT) {
+    const int i = q / NP, j = q % NP;
+    if (i <= j) tab[RC::row_off(i) + j - i] = (unsigned short)(i | (j << 7));
+  }
+
+  // ---- row 0
+  if (warp == 0) {
+    double d = Sd[0];
+    if (!(d > 0.0)) {
+      if (lane == 0 && info) atomicMin(info, pack_info(it.node, 0));
+      d = 1.0;
+    }
+    const double rs = rsqrt(d);
+    __syncwarp();
+    for (int j = 1 + lane; j < NP; j += 32) Sd[j] *= rs;
+    if (lane == 0) {
+      Sd[0] = d * rs;
+      dinv[0] = rs;
+    }
   }
   __syncthreads();
-  if (!FIRST && !RL && it.p_a >= 0) {
-    if (c0 >= r0) {
-      double a[R][R];
-      tile_from_smem<C>(a, sS, r0, c0);
-      tile_sub_xty_gmem<C>(a, epool + it.p_a, epool + it.p_a, r0, c0);
-      tile_to_smem<C>(sS, a, r0, c0);
+
+  // ---- steps k = 0 .. NP-2: row k is final at the start of step k
+#pragma unroll 1
+  for (int k = 0; k + 1 < NP; ++k) {
+    const double *Uk = Sd + k * LD;
+    if (warp == 0) {
+      double *row = Sd + (k + 1) * LD;
+      const double ukk1 = Uk[k + 1];
+      for (int j = k + 1 + lane; j < NP; j += 32) row[j] = fma(-ukk1, Uk[j], row[j]);
+      __syncwarp();
+      double d = row[k + 1];
+      if (!(d > 0.0)) {
+        if (lane == 0 && info) atomicMin(info, pack_info(it.node, k + 1));
+        d = 1.0;
+      }
+      const double rs = rsqrt(d);
+      __syncwarp();
+      for (int j = k + 2 + lane; j < NP; j += 32) row[j] *= rs;
+      if (lane == 0) {
+        row[k + 1] = d * rs;
+        dinv[k + 1] = rs;
+      }
+    } else {
+      const int base = RC::row_off(k + 2);
+#pragma unroll 4
+      for (int q = base + tid - 32; q < NE; q += NT - 32) {
+        const unsigned e = tab[q];
+        const int i = e & 127, j = e >> 7;
+        Sd[i * LD + j] = fma(-Uk[i], Uk[j], Sd[i * LD + j]);
+      }
     }
     __syncthreads();
   }
-  block_potrf_upper<C>(sS, dinv, info, it.node, r0, c0);
-  smem_to_block<C>(dpool + it.d_self, sS, true);
-}
 
-template <int NP, int R>
-constexpr size_t root_large_smem_bytes() {
-  return sizeof(double) * ((size_t)TileCfg<double, NP, R>::BLK + NP);
+  // ---- U (zeros below the diagonal) -> FP32 pool
+  P *g = dpool + it.d_self;
+  for (int q = tid; q < NP * NP; q += NT) {
+    const int i = q / NP, j = q % NP;
+    g[q] = i <= j ? f64_to_f32_rn(Sd[i * LD + j]) : P(0);
+  }
 }
 
 // Packing pass of Alg. 6 (its first parallel loop): Dhat_v <- D_v for every
@@ -291,13 +382,13 @@ __global__ void k_pack_matrix(P *dpool, P *epool, const S *D, const S *B, int N,
   for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) {
     const int i = q / NP, j = q % NP;
     P val;
-    if (i < n && j < n) val = (P)(i <= j ? D[v * ubs + (size_t)j * n + i] : D[v * ubs + (size_t)i * n + j]);
+    if (i < n && j < n) val = convert_in<P, S>(i <= j ? D[v * ubs + (size_t)j * n + i] : D[v * ubs + (size_t)i * n + j]);
     else val = (i == j) ? P(1) : P(0);
     dpool[v * bs + q] = val;
     if (v + 1 < N) {
       const bool odd = ((v + 1) & 1) != 0;  // 1-based slot index k = v + 1
       P b;
-      if (i < n && j < n) b = (P)(odd ? B[v * ubs + (size_t)j * n + i] : B[v * ubs + (size_t)i * n + j]);
+      if (i < n && j < n) b = convert_in<P, S>(odd ? B[v * ubs + (size_t)j * n + i] : B[v * ubs + (size_t)i * n + j]);
       else b = P(0);
       epool[v * bs + q] = b;
     }

@@ -29,18 +29,12 @@ KernelSet make_set() {
   k.fac_rest = (const void *)&k_factor_level<T, T, S, NP, R, false>;
   k.fac_threads = TileCfg<T, NP, R>::NT;
   k.fac_smem = factor_smem_bytes<T, NP, R>();
-  if constexpr (MIXED && NP >= 128) {
-    k.root_first = (const void *)&k_root_large<T, S, NP, R, true, false>;
-    k.root_rest = (const void *)&k_root_large<T, S, NP, R, false, false>;
-    k.root_rl = (const void *)&k_root_large<T, S, NP, R, false, true>;
-    k.root_threads = TileCfg<double, NP, R>::NT;
-    k.root_smem = root_large_smem_bytes<NP, R>();
-  } else if constexpr (MIXED) {
-    k.root_first = (const void *)&k_factor_level<double, T, S, NP, R, true>;
-    k.root_rest = (const void *)&k_factor_level<double, T, S, NP, R, false>;
-    k.root_rl = (const void *)&k_factor_level<double, T, S, NP, R, false, true>;
-    k.root_threads = TileCfg<double, NP, R>::NT;
-    k.root_smem = factor_smem_bytes<double, NP, R>();
+  if constexpr (MIXED) {
+    k.root_first = (const void *)&k_root_chol<T, S, NP, R, true, false>;
+    k.root_rest = (const void *)&k_root_chol<T, S, NP, R, false, false>;
+    k.root_rl = (const void *)&k_root_chol<T, S, NP, R, false, true>;
+    k.root_threads = TileCfg<float, NP, R>::NT;
+    k.root_smem = root_smem_bytes<NP, R>();
   }
   k.fac_flow = (const void *)&k_factor_flow<T, T, S, NP, R>;
   k.pack_matrix = (const void *)&k_pack_matrix<T, S, NP>;

@@ -136,29 +136,53 @@ struct SolveArgs {
   int m;
 };
 
+// Shared-memory layout of one solve item: three np x np blocks (the node's
+// own factor block, then the two coupling blocks), the reciprocal diagonal,
+// and three np x m vectors.
+template <typename T, int NP>
+struct SolveSmem {
+  T *U0, *U1, *U2, *dinv, *y0, *y1, *y2;
+  __device__ __forceinline__ explicit SolveSmem(unsigned char *raw, int m) {
+    constexpr int LDL = SolveCfg<T, NP>::LDL;
+    U0 = reinterpret_cast<T *>(raw);
+    U1 = U0 + NP * LDL;
+    U2 = U1 + NP * LDL;
+    dinv = U2 + NP * LDL;
+    y0 = dinv + NP;
+    y1 = y0 + NP * m;
+    y2 = y1 + NP * m;
+  }
+};
+
+// Issue the copies of an item's factor blocks (they do not depend on other
+// items of the solve, so a persistent CTA starts them before it waits for
+// the item's inputs). d0: dpool offset or -1; e1/e2: epool offsets, used when
+// the matching vector index v1/v2 is >= 0.
+template <typename T, int NP>
+__device__ __forceinline__ void stage_item_blocks(const SolveSmem<T, NP> &sm, const SolveArgs &a, int64_t d0,
+                                                  int64_t v1, int64_t e1, int64_t v2, int64_t e2) {
+  const T *dpool = reinterpret_cast<const T *>(a.dpool);
+  const T *epool = reinterpret_cast<const T *>(a.epool);
+  if (d0 >= 0) stage_block<T, NP>(sm.U0, dpool + d0);
+  if (v1 >= 0) stage_block<T, NP>(sm.U1, epool + e1);
+  if (v2 >= 0) stage_block<T, NP>(sm.U2, epool + e2);
+}
+
 // Forward step for one surviving node j (pull form, Alg. 7 forward sweep):
 //   y_j -= U(j-h, j)^T y_{j-h} + U(j+h, j)^T y_{j+h}   (contributions of level l-1)
 //   y_j <- U_j^{-T} y_j                                 (if j is eliminated at this level)
-template <typename T, int NP>
+// STAGED: the factor blocks were already issued by stage_item_blocks.
+template <typename T, int NP, bool STAGED = false>
 __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_l, int64_t y_r, int64_t e_r,
                                          int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
   constexpr int LDL = SolveCfg<T, NP>::LDL;
   const int m = a.m;
-  T *Us = reinterpret_cast<T *>(smem_raw);  // U_j
-  T *Ul = Us + NP * LDL;                    // U(j-h, j)
-  T *Ur = Ul + NP * LDL;                    // U(j+h, j)
-  T *dinv = Ur + NP * LDL;                  // NP
-  T *ys = dinv + NP;                        // NP*m
-  T *yl = ys + NP * m;
-  T *yr = yl + NP * m;
+  const SolveSmem<T, NP> sm(smem_raw, m);
+  T *Us = sm.U0, *Ul = sm.U1, *Ur = sm.U2, *dinv = sm.dinv, *ys = sm.y0, *yl = sm.y1, *yr = sm.y2;
   T *y = reinterpret_cast<T *>(a.y);
-  const T *dpool = reinterpret_cast<const T *>(a.dpool);
-  const T *epool = reinterpret_cast<const T *>(a.epool);
   const int nm = NP * m;
   T *yself = y + y_self * nm;
-  if (d_self >= 0) stage_block<T, NP>(Us, dpool + d_self);
-  if (y_l >= 0) stage_block<T, NP>(Ul, epool + e_l);
-  if (y_r >= 0) stage_block<T, NP>(Ur, epool + e_r);
+  if (!STAGED) stage_item_blocks<T, NP>(sm, a, d_self, y_l, e_l, y_r, e_r);
   stage_vec<T>(ys, yself, nm);
   if (y_l >= 0) stage_vec<T>(yl, y + y_l * nm, nm);
   if (y_r >= 0) stage_vec<T>(yr, y + y_r * nm, nm);
@@ -196,26 +220,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
 
 // Backward step for one eliminated node e (Alg. 7 backward sweep):
 //   x_e <- U_e^{-1} (y_e - U(e, e+s) x_{e+s} - U(e, e-s) x_{e-s})
-template <typename T, int NP>
+template <typename T, int NP, bool STAGED = false>
 __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e_dn, int64_t x_up, int64_t e_up,
                                          int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
   constexpr int LDL = SolveCfg<T, NP>::LDL;
   const int m = a.m;
-  T *Us = reinterpret_cast<T *>(smem_raw);  // U_e
-  T *Ud = Us + NP * LDL;                    // U(e, e+s)
-  T *Uu = Ud + NP * LDL;                    // U(e, e-s)
-  T *dinv = Uu + NP * LDL;                  // NP
-  T *ys = dinv + NP;                        // NP*m
-  T *xd = ys + NP * m;
-  T *xu = xd + NP * m;
+  const SolveSmem<T, NP> sm(smem_raw, m);
+  T *Us = sm.U0, *Ud = sm.U1, *Uu = sm.U2, *dinv = sm.dinv, *ys = sm.y0, *xd = sm.y1, *xu = sm.y2;
   T *y = reinterpret_cast<T *>(a.y);
-  const T *dpool = reinterpret_cast<const T *>(a.dpool);
-  const T *epool = reinterpret_cast<const T *>(a.epool);
   const int nm = NP * m;
   T *yself = y + x_self * nm;
-  stage_block<T, NP>(Us, dpool + d_self);
-  if (x_dn >= 0) stage_block<T, NP>(Ud, epool + e_dn);
-  if (x_up >= 0) stage_block<T, NP>(Uu, epool + e_up);
+  if (!STAGED) stage_item_blocks<T, NP>(sm, a, d_self, x_dn, e_dn, x_up, e_up);
   stage_vec<T>(ys, yself, nm);
   if (x_dn >= 0) stage_vec<T>(xd, y + x_dn * nm, nm);
   if (x_up >= 0) stage_vec<T>(xu, y + x_up * nm, nm);
@@ -261,10 +276,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowS
     const int t = flow_claim(fs, a.count, &s_slot);
     if (t < 0) break;
     const SolveFlowItem it = items[t];
+    flow_trace(fs, t, 0);
+    // the factor blocks load while the item waits for its inputs
+    stage_item_blocks<T, NP>(SolveSmem<T, NP>(smem_raw, a.m), a, it.d_self, it.y_a, it.e_a, it.y_b, it.e_b);
     if (flow_wait(fs, it.dep, 3, &s_ok)) {
-      if (it.kind == 0) fwd_node<T, NP>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
-      else bwd_node<T, NP>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
+      flow_trace(fs, t, 1);
+      if (it.kind == 0) fwd_node<T, NP, true>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
+      else bwd_node<T, NP, true>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
+    } else {
+      cp_async_wait_all_s();  // no copy may still target shared memory when the CTA moves on
     }
+    __syncthreads();
+    flow_trace(fs, t, 2);
     flow_publish(fs, t);
   }
 }
@@ -287,7 +310,7 @@ __global__ void k_pack_rhs(T *y, const S *b, int N, int n, int np, int m, int ld
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / ((int64_t)np * m);
     const int r = (int)((q / m) % np), c = (int)(q % m);
-    y[node_base * np * m + q] = r < n ? (T)b[(i * n + r) * ldb + col0 + c] : T(0);
+    y[node_base * np * m + q] = r < n ? convert_in<T, S>(b[(i * n + r) * ldb + col0 + c]) : T(0);
   }
 }
 
@@ -394,7 +417,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
     for (int k = 0; k < kResParts; ++k) ax += ps[k * nm + q];
     const int r = q / m, col = q % m;
     const double v = b[(size_t)i * nm + q] - ax;
-    if (y) y[(node_base + i) * np * m + r * m + col] = (T)v;
+    if (y) y[(node_base + i) * np * m + r * m + col] = convert_in<T, double>(v);
     rmax = fmax(rmax, fabs(v));
     xmax = fmax(xmax, fabs(xs[nm + q]));
   }

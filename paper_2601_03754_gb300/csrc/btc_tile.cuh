@@ -94,6 +94,49 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[R]) {
   }
 }
 
+// ------------------------------------------------------------ conversions
+// FP64 -> FP32 with round-to-nearest-even using integer operations only: on
+// this GPU the conversion instruction runs on the FP64 pipe, which is 1/64 of
+// the FP32 rate. Exact (IEEE) for results in the FP32 normal range, for
+// zeros, infinities and NaNs; results below the normal range fall back to the
+// hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double a) {
+  const unsigned hi = (unsigned)__double2hiint(a), lo = (unsigned)__double2loint(a);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+  if (e == 0) return __uint_as_float(sign);  // zero / FP64 subnormal -> signed zero
+  const int ef = e - 1023 + 127;
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+  if (ef <= 0) return (float)a;
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 of the 52 fraction bits
+  const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;   // the 29 dropped bits
+  unsigned bits = ((unsigned)ef << 23) | mant;
+  if (rem > half || (rem == half && (mant & 1u))) bits += 1u;  // a carry moves to the next binade
+  return __uint_as_float(sign | bits);
+}
+
+// FP32 -> FP64 (exact) with integer operations; subnormal, infinite and NaN
+// inputs use the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)sign);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0 || e == 0xffu) return (double)f;
+  const unsigned long long bits = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// Element conversion between the caller's, the pools' and the arithmetic
+// types (identity when they agree).
+template <typename T, typename S>
+__device__ __forceinline__ T convert_in(S v) {
+  if constexpr (sizeof(T) == 4 && sizeof(S) == 8) return f64_to_f32_rn(v);
+  else if constexpr (sizeof(T) == 8 && sizeof(S) == 4) return f32_to_f64(v);
+  else return (T)v;
+}
+
 // ------------------------------------------------------------ async copies
 // 16-byte global -> shared copy that bypasses registers (cp.async, L2 only).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -146,7 +189,7 @@ __device__ __forceinline__ void block_to_smem(T *s, const P *g) {
         *reinterpret_cast<float4 *>(s + row * C::LD + col) = raw[it];
       } else {
 #pragma unroll
-        for (int i = 0; i < V; ++i) s[row * C::LD + col + i] = (T)src[i];
+        for (int i = 0; i < V; ++i) s[row * C::LD + col + i] = convert_in<T, P>(src[i]);
       }
     }
   }
@@ -164,43 +207,65 @@ __device__ __forceinline__ void smem_to_block(P *g, const T *s, bool lower_zero)
     float4 raw;
     P *dst = reinterpret_cast<P *>(&raw);
 #pragma unroll
-    for (int i = 0; i < V; ++i) dst[i] = (lower_zero && col + i < row) ? P(0) : (P)s[row * C::LD + col + i];
+    for (int i = 0; i < V; ++i) dst[i] = (lower_zero && col + i < row) ? P(0) : convert_in<P, T>(s[row * C::LD + col + i]);
     *reinterpret_cast<float4 *>(g + (size_t)row * C::NP + col) = raw;
   }
 }
 
+
 // Caller's block (n x n row-major, type S) -> padded shared memory (type T).
 // trans: element (i, k) of the result is src(k, i). Padding: `diag` on the
-// padded diagonal, 0 elsewhere.
+// padded diagonal, 0 elsewhere. Each thread issues a chunk of loads before
+// converting any of them, so their latencies overlap.
 template <class C, typename T, typename S>
 __device__ __forceinline__ void user_to_smem(T *s, const S *src, int n, bool trans, T diag) {
   constexpr int TOTAL = C::NP * C::NP;
-  for (int q = threadIdx.x; q < TOTAL; q += C::NT) {
-    // consecutive threads read consecutive source elements
-    const int a = q / C::NP, b = q % C::NP;  // source row a, column b
-    T v;
-    if (a < n && b < n) v = (T)__ldg(src + (size_t)a * n + b);
-    else v = (a == b) ? diag : T(0);
-    if (trans) s[b * C::LD + a] = v;
-    else s[a * C::LD + b] = v;
+  constexpr int ITER = (TOTAL + C::NT - 1) / C::NT;
+  constexpr int CHMAX = 32 / (int)sizeof(S);  // 32 bytes of loads in flight per thread
+  constexpr int CH = ITER < CHMAX ? ITER : CHMAX;
+#pragma unroll 1
+  for (int i0 = 0; i0 < ITER; i0 += CH) {
+    S v[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      // consecutive threads read consecutive source elements
+      const int q = threadIdx.x + (i0 + u) * C::NT;
+      const int a = q / C::NP, b = q % C::NP;  // source row a, column b
+      v[u] = (q < TOTAL && a < n && b < n) ? __ldg(src + (size_t)a * n + b) : S(0);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int q = threadIdx.x + (i0 + u) * C::NT;
+      if (q >= TOTAL) continue;
+      const int a = q / C::NP, b = q % C::NP;
+      const T x = (a < n && b < n) ? convert_in<T, S>(v[u]) : (a == b ? diag : T(0));
+      if (trans) s[b * C::LD + a] = x;
+      else s[a * C::LD + b] = x;
+    }
   }
 }
 
 // Caller's block (n x n row-major, type S) -> one register tile, padded like
-// user_to_smem. trans: element (i, k) is src(k, i).
+// user_to_smem. trans: element (i, k) is src(k, i). Each tile row's loads
+// precede its conversions.
 template <class C, typename T, typename S>
 __device__ __forceinline__ void tile_from_user(T (&a)[C::R][C::R], const S *src, int n, int r0, int c0, bool trans,
                                                T diag) {
 #pragma unroll
-  for (int r = 0; r < C::R; ++r)
+  for (int r = 0; r < C::R; ++r) {
+    S v[C::R];
+    const int i = r0 + r;
 #pragma unroll
     for (int c = 0; c < C::R; ++c) {
-      const int i = r0 + r, k = c0 + c;
-      T v;
-      if (i < n && k < n) v = (T)(trans ? __ldg(src + (size_t)k * n + i) : __ldg(src + (size_t)i * n + k));
-      else v = (i == k) ? diag : T(0);
-      a[r][c] = v;
+      const int k = c0 + c;
+      v[c] = (i < n && k < n) ? (trans ? __ldg(src + (size_t)k * n + i) : __ldg(src + (size_t)i * n + k)) : S(0);
     }
+#pragma unroll
+    for (int c = 0; c < C::R; ++c) {
+      const int k = c0 + c;
+      a[r][c] = (i < n && k < n) ? convert_in<T, S>(v[c]) : ((i == k) ? diag : T(0));
+    }
+  }
 }
 
 // ------------------------------------------------------------ tile algebra
@@ -261,7 +326,7 @@ __device__ __forceinline__ void tile_from_pool(T (&a)[C::R][C::R], const P *g, i
     P v[C::R];
     vload_cg<P, C::R>(g + (size_t)(r0 + r) * C::NP + c0, v);
 #pragma unroll
-    for (int c = 0; c < C::R; ++c) a[r][c] = (T)v[c];
+    for (int c = 0; c < C::R; ++c) a[r][c] = convert_in<T, P>(v[c]);
   }
 }
 
@@ -271,7 +336,7 @@ __device__ __forceinline__ void tile_to_pool(P *g, const T (&a)[C::R][C::R], int
   for (int r = 0; r < C::R; ++r) {
     P v[C::R];
 #pragma unroll
-    for (int c = 0; c < C::R; ++c) v[c] = (P)a[r][c];
+    for (int c = 0; c < C::R; ++c) v[c] = convert_in<P, T>(a[r][c]);
     vstore<P, C::R>(g + (size_t)(r0 + r) * C::NP + c0, v);
   }
 }
@@ -312,10 +377,30 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v) {
 }
 
 struct FlowSync {
-  int *ticket;  // next item to claim
-  int *done;    // one flag per item
-  int *status;  // 0 = ok; kFlowTimeout when a wait gave up
+  int *ticket;                // next item to claim
+  int *done;                  // one flag per item
+  int *status;                // 0 = ok; kFlowTimeout when a wait gave up
+  unsigned long long *trace;  // optional: 4 words per item (claim, ready, done ns; SM id), or null
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned s;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+  return s;
+}
+
+// Trace hooks (thread 0 only; no-ops when tracing is off).
+__device__ __forceinline__ void flow_trace(const FlowSync &fs, int t, int slot) {
+  if (fs.trace && threadIdx.x == 0) {
+    fs.trace[4 * (size_t)t + slot] = global_ns();
+    if (slot == 0) fs.trace[4 * (size_t)t + 3] = sm_id();
+  }
+}
 
 // Claim the next item (ticket order = dependency order). Returns the item
 // index, or -1 when all `total` items are taken. All threads of the CTA call it.
