@@ -3,11 +3,12 @@ residual <= 1e-10 on GB300, through the libbtc C ABI.
 
 Workload (default): N = 1024 blocks of n = 64, one right-hand side, seeded
 synthetic inputs (B_i ~ N(0, 1/n), D_i = M M^T/n + (||B_{i-1}||+||B_i||+1) I).
-A step = btc_factor (all dissection levels of Alg. 5) + btc_solve_refined
-(Alg. 7 solves with FP64 residuals until ||r|| <= 1e-10 ||A|| ||x||), in the
-chosen form: FP32 factor and correction solves, FP64 root Cholesky, residual
-and update. The plain FP64 GPU path (same kernels in FP64, no refinement
-needed) is timed beside it.
+A step = btc_factor_solve_refined: the factorization of Alg. 5 with the
+forward substitution of Alg. 7 interlaced in the same persistent launch, the
+backward substitution, then FP64 residuals and correction solves until
+||r|| <= 1e-10 ||A|| ||x||, in the chosen form: FP32 factor and correction
+solves, FP64 root Cholesky, residual and update. The plain FP64 GPU path
+(same kernels in FP64, no refinement needed) is timed beside it.
 
 Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
 (sequential Alg. 1 factor + block substitution) on the host cores instead.
@@ -106,22 +107,23 @@ class ClockSampler:
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("btc_factor.cuh", "btc_tile.cuh"):
+    for f in ("btc_factor.cuh", "btc_tile.cuh", "btc_solve.cuh", "btc_fused.cuh"):
         with open(os.path.join(ROOT, "paper_2601_03754_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def _traffic_from_profile():
-    """DRAM bytes per factor call from the committed ncu summary, if it matches the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "factor_level_traffic.json")
+    """DRAM bytes per launch of the interlaced factor + forward kernel from the committed ncu summary, if it
+    matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "factor_forward_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         t = json.load(f)
     if t.get("kernel_sha") != _kernel_hash():
         return None
-    return t.get("dram_bytes_per_factor")
+    return t.get("dram_bytes_per_launch")
 
 
 def run_reference(args):
@@ -195,8 +197,7 @@ def run_profile(which):
     for dt in dts:
         p = btc.btc_plan(N, n, dt)
         for _ in range(2):
-            btc.btc_factor(p, Dd, Bd)
-            it, rel, rc = btc.btc_solve_refined(p, bd, xd, m, tol=TOL, maxit=30)
+            it, rel, rc = btc.btc_factor_solve_refined(p, Dd, Bd, bd, xd, m, tol=TOL, maxit=30)
         print(f"profile dtype={dt} iters={it} relres={rel:.3e}")
         p.free()
     torch.cuda.synchronize()
@@ -371,8 +372,7 @@ def main():
     info = btc.btc_plan_query(pm)
 
     def mixed_step():
-        btc.btc_factor(pm, Dd, Bd)
-        return btc.btc_solve_refined(pm, bd, xd, m, tol=TOL, maxit=30)
+        return btc.btc_factor_solve_refined(pm, Dd, Bd, bd, xd, m, tol=TOL, maxit=30)
 
     timed_steps(pm, args.warmup, mixed_step)
     if world > 1:
@@ -395,20 +395,24 @@ def main():
     value = world * 1000.0 / ms
     assert rel <= TOL, rel
 
-    # ---- phase split of the chosen form (same stream, same L2 flush), for the roofline
-    fact_ts, _ = timed_steps(pm, max(10, args.steps // 2), lambda: btc.btc_factor(pm, Dd, Bd))
-    t_fact = statistics.median(fact_ts)
-    # solve-only (one FP32 correction solve of an FP64 vector)
-    xs = bd.clone()
-    solve_ts, _ = timed_steps(pm, max(10, args.steps // 2), lambda: btc.btc_solve(pm, xs, m))
-    t_solve = statistics.median(solve_ts)
+    # ---- per-kernel device times of the same step (library events on the plan's stream, L2 flushed),
+    # for the phase split and the roofline of the dominant kernel
+    n_phase = max(10, args.steps // 2)
+    btc.btc_plan_set_timing(pm, True)
+    timed_steps(pm, n_phase, mixed_step)
+    k_ms, k_n = btc.btc_plan_timing(pm)
+    btc.btc_plan_set_timing(pm, False)
+    phase = {name: (k_ms[c] / k_n[c] if k_n[c] else None) for name, c in
+             (("factor_forward_interlaced", btc.TIME_FACTOR_FORWARD), ("root_fp64", btc.TIME_ROOT),
+              ("solve_tail", btc.TIME_SOLVE_TAIL), ("correction_solve", btc.TIME_SOLVE),
+              ("residual", btc.TIME_RESIDUAL))}
+    t_fused = phase["factor_forward_interlaced"]
 
     # ---- the plain FP64 GPU path on the same workload
     p64 = btc.btc_plan(N, n, btc.F64, stream)
 
     def f64_step():
-        btc.btc_factor(p64, Dd, Bd)
-        return btc.btc_solve_refined(p64, bd, xd, m, tol=TOL, maxit=30)
+        return btc.btc_factor_solve_refined(p64, Dd, Bd, bd, xd, m, tol=TOL, maxit=30)
 
     timed_steps(p64, 3, f64_step)
     ts64, (it64, rel64, _) = timed_steps(p64, max(5, args.steps // 5), f64_step)
@@ -440,12 +444,17 @@ def main():
     peaks, pk_kind = _peaks()
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_PEAK_PER_SM_CLK * sm_max * 1e6 / 1e12
-    achieved = info["factor_flops"] / (t_fact * 1e-3) / 1e12
+    # algorithmic work of the interlaced launch: Table 1 factor costs without the top separator's
+    # potrf (its own FP64 kernel), plus the forward sweep (Alg. 7: n^2 m per eliminated node, 2 n^2 m
+    # per off-diagonal block)
+    root_flops = n ** 3 / 3.0
+    fwd_flops = m * (N * n * n + 2.0 * info["offdiag_blocks"] * n * n)
+    fused_flops = info["factor_flops"] - root_flops + fwd_flops
+    achieved = fused_flops / (t_fused * 1e-3) / 1e12
     traffic = _traffic_from_profile()
-    L = info["levels"]
-    # factor levels + ||A|| + first solve (pack, 2L levels, unpack) + per refinement step
-    # (2L levels + update) + one residual per check
-    launches = L + 1 + (2 * L + 2) + iters * (2 * L + 1) + (iters + 1)
+    # pack, interlaced factor + forward, FP64 root, solve tail, unpack, residual; per refinement
+    # step: solve, update, residual
+    launches = 6 + 3 * iters
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -462,12 +471,14 @@ def main():
         "plain_f64": {"ms_per_step": ms64, "solves_per_s": 1000.0 / ms64, "refine_iters": it64, "relres": rel64,
                       "p99_us": 1000 * float(np.percentile(np.asarray(ts64), 99))},
         "speedup_vs_plain_f64": ms64 / ms,
-        "phases_ms": {"factor_mixed": t_fact, "one_solve_mixed": t_solve},
-        "roofline": {"kernel": "k_factor_flow + FP64 root (one factorization, btc_factor)", "bound": "alu",
+        "phases_ms": phase,
+        "roofline": {"kernel": "k_factor_fwd_flow (interlaced factor + forward sweep, one launch per step)",
+                     "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic,
                      "peak_kind": f"FP32 FFMA: {SMS} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (derived)",
-                     "algorithmic": f"{info['factor_flops']:.4g} flop per factorization (Alg. 5, Table 1 costs)"},
+                     "algorithmic": f"{fused_flops:.4g} flop per launch (Alg. 5 Table 1 costs without the top "
+                                    f"separator + Alg. 7 forward sweep)"},
         "e2e": {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "entry_point": "btc_factor_solve_host (pinned host buffers)"},
         "gpu_launches": launches * args.steps,

@@ -92,6 +92,21 @@ int btc_describe(int N, int n, int dtype, btc_plan_info *info);
 int btc_schedule(int N, int *order_out, int *levels_out);
 
 /*
+ * Host-only: the launch order of the interlaced factorization + forward
+ * substitution (btc_factor_solve) for an N-block plan, for inspection and
+ * tests. root_separate != 0: the mixed-precision form, whose top-separator
+ * factor and forward item run outside the interlaced launch. On input *count
+ * is the capacity of the arrays (all four may be NULL to query the length);
+ * on output it is the number of entries. Entry t: kind[t] 0 = factor item,
+ * 1 = forward item; node[t] 1-based node; level[t] dissection level;
+ * deps[6t .. 6t+5] earlier entries it waits for (-1: none). *tail_count (may
+ * be NULL): items of the second launch (top-separator forward item when
+ * root_separate, then every backward item).
+ */
+int btc_schedule_interlaced(int N, int root_separate, int *kind, int *node, int *level, int *deps, int *count,
+                            int *tail_count);
+
+/*
  * Create a plan for one N-block, n x n system: plans the dissection levels on
  * the host, allocates the device pools (padded n_p x n_p blocks, level-major),
  * and binds `stream` (a cudaStream_t, NULL for the legacy default stream).
@@ -182,6 +197,49 @@ int btc_solve(btc_plan_t p, void *rhs, int nrhs);
  */
 int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
                       double *relres);
+
+/*
+ * Optional event timing of a plan's kernels, by class. While enabled, every
+ * launch of the classes below is bracketed by CUDA events recorded on the
+ * plan's stream (a few microseconds of host work per launch; leave disabled in
+ * production). btc_plan_timing synchronizes the stream, returns per class the
+ * summed device time in ms[c] and the launch count in launches[c] (host
+ * arrays of BTC_TIMING_CLASSES entries) since the last call, and resets them.
+ * Enabling or disabling discards what is pending.
+ */
+enum btc_timing_class {
+  BTC_TIME_FACTOR = 0,          /* persistent factorization launch (or its level launches)        */
+  BTC_TIME_FACTOR_FORWARD = 1,  /* interlaced factorization + forward substitution launch         */
+  BTC_TIME_ROOT = 2,            /* FP64 top-separator Cholesky (mixed path)                        */
+  BTC_TIME_SOLVE = 3,           /* full solve launch (forward + backward)                          */
+  BTC_TIME_SOLVE_TAIL = 4,      /* solve tail after an interlaced factorization                    */
+  BTC_TIME_RESIDUAL = 5,        /* FP64 residual and norms of the refinement                       */
+  BTC_TIMING_CLASSES = 6
+};
+int btc_plan_set_timing(btc_plan_t p, int enable);
+int btc_plan_timing(btc_plan_t p, double *ms, int *launches);
+
+/*
+ * Factorization with the forward substitution interlaced (the paper's fused
+ * factor + forward variant, Sec. 5: the forward sweep of level l runs as soon
+ * as the blocks it reads are factored), then the backward substitution:
+ * RHS <- Psi^{-1} RHS. D, B as for btc_factor; rhs as for btc_solve, in
+ * place. The factor stays valid for later btc_solve / btc_solve_refined
+ * calls. The interlaced form applies with the hybrid variant, the persistent
+ * schedule and nrhs <= the plan's columns per pass; otherwise this is
+ * btc_factor followed by btc_solve (same results). Asynchronous. Errors as
+ * for btc_factor and btc_solve.
+ */
+int btc_factor_solve(btc_plan_t p, const void *D, const void *B, void *rhs, int nrhs);
+
+/*
+ * btc_factor_solve followed by the FP64 refinement of btc_solve_refined: the
+ * first solve is the interlaced one; b, x, tol, maxit, iters, relres and the
+ * return codes as for btc_solve_refined (plans of dtype BTC_F64 or
+ * BTC_MIXED_F32; nrhs up to the plan's columns per pass). Synchronous.
+ */
+int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const double *b, double *x, int nrhs,
+                             double tol, int maxit, int *iters, double *relres);
 
 /*
  * End-to-end call on HOST buffers: copies D, B (element type as for

@@ -55,6 +55,11 @@ _SIGS = {
     "btc_factor": [_vp, _vp, _vp],
     "btc_solve": [_vp, _vp, ctypes.c_int],
     "btc_solve_refined": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
+    "btc_factor_solve": [_vp, _vp, _vp, _vp, ctypes.c_int],
+    "btc_plan_set_timing": [_vp, ctypes.c_int],
+    "btc_plan_timing": [_vp, _dp, _ip],
+    "btc_schedule_interlaced": [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip, _ip, _ip, _ip],
+    "btc_factor_solve_refined": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
     "btc_factor_solve_host": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
     "btc_info": [_vp, _ip, _ip],
     "btc_get_factor": [_vp, _vp, _vp, _ip],
@@ -204,6 +209,52 @@ def btc_solve_refined(plan, b, x, nrhs, tol=1e-10, maxit=20, allow_not_converged
     allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
     rc = _check(load().btc_solve_refined(plan.h, _ptr(b), _ptr(x), nrhs, tol, maxit, ctypes.byref(it),
                                          ctypes.byref(rel)), allow)
+    return it.value, rel.value, rc
+
+
+TIME_FACTOR, TIME_FACTOR_FORWARD, TIME_ROOT, TIME_SOLVE, TIME_SOLVE_TAIL, TIME_RESIDUAL = range(6)
+TIMING_CLASSES = 6
+
+
+def btc_plan_set_timing(plan, enable=True):
+    return _check(load().btc_plan_set_timing(plan.h, int(bool(enable))))
+
+
+def btc_plan_timing(plan):
+    """Per kernel class: (summed device ms, launches) since the last call (synchronizes)."""
+    ms = (ctypes.c_double * TIMING_CLASSES)()
+    n = (ctypes.c_int * TIMING_CLASSES)()
+    _check(load().btc_plan_timing(plan.h, ms, n))
+    return [float(v) for v in ms], [int(v) for v in n]
+
+
+def btc_schedule_interlaced(N, root_separate):
+    """Entries of the interlaced factor + forward launch: (kind, node, level, deps[count, 6]), tail length."""
+    import numpy as np
+    lib = load()
+    count = ctypes.c_int(0)
+    _check(lib.btc_schedule_interlaced(N, int(root_separate), None, None, None, None, ctypes.byref(count), None))
+    c = count.value
+    kind, node, level = (np.zeros(max(c, 1), dtype=np.int32) for _ in range(3))
+    deps = np.zeros(max(c, 1) * 6, dtype=np.int32)
+    tail = ctypes.c_int(0)
+    ip = lambda a: a.ctypes.data_as(_ip)
+    _check(lib.btc_schedule_interlaced(N, int(root_separate), ip(kind), ip(node), ip(level), ip(deps),
+                                       ctypes.byref(count), ctypes.byref(tail)))
+    return kind[:c], node[:c], level[:c], deps[:6 * c].reshape(c, 6), tail.value
+
+
+def btc_factor_solve(plan, D, B, rhs, nrhs):
+    """Factor with the forward sweep interlaced, then the backward sweep; rhs is overwritten by x."""
+    return _check(load().btc_factor_solve(plan.h, _ptr(D), _ptr(B), _ptr(rhs), nrhs))
+
+
+def btc_factor_solve_refined(plan, D, B, b, x, nrhs, tol=1e-10, maxit=20, allow_not_converged=False):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    rc = _check(load().btc_factor_solve_refined(plan.h, _ptr(D), _ptr(B), _ptr(b), _ptr(x), nrhs, tol, maxit,
+                                                ctypes.byref(it), ctypes.byref(rel)), allow)
     return it.value, rel.value, rc
 
 

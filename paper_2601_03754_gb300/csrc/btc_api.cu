@@ -76,33 +76,6 @@ __global__ void k_anorm(const double *D, const double *B, int N, int n, double *
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, best);
 }
 
-// Lower bound of ||Psi||_inf (into norms[2]) for the stopping test of the
-// refinement: each |a_ij| is rounded toward zero to FP32 and the row sums
-// accumulate with round-toward-zero additions, so the result never exceeds the
-// exact norm and the test ||r|| <= tol ||Psi|| ||x|| is never met early.
-// One CTA per block row, one thread per row; entries read from global memory.
-__global__ void k_anorm_lb(const double *D, const double *B, int N, int n, double *norms) {
-  const int i = blockIdx.x;
-  const size_t bs = (size_t)n * n;
-  const double *Di = D + i * bs;
-  float best = 0.0f;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    float s = 0.0f;
-    for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(r >= c ? Di[r * n + c] : Di[c * n + r]));
-    if (i > 0) {
-      const double *Bl = B + (i - 1) * bs;
-      for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(Bl[r * n + c]));
-    }
-    if (i + 1 < N) {
-      const double *Br = B + i * bs;
-      for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(Br[c * n + r]));
-    }
-    best = fmaxf(best, s);
-  }
-  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, (double)best);
-}
-
 bool dtype_ok(int dtype) { return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32; }
 
 }  // namespace btc
@@ -120,19 +93,36 @@ struct btc_plan_s {
   FwdItem *d_fwd = nullptr;
   BwdItem *d_bwd = nullptr;
   std::vector<int64_t> fac_off, fwd_off, bwd_off;  // per level start index
-  unsigned long long *d_info = nullptr;
-  double *d_norms = nullptr;  // [0] max|r|, [1] max|x|, [2] ||Psi||_inf
-  void *d_y = nullptr;        // work vector [N][np][kMaxCols]
+  // one readback block: the norms, the pivot report and the flow status come
+  // back to the host in a single copy
+  struct Readback {
+    double norms[4];  // [0] max|r|, [1] max|x|, [2] ||Psi||_inf (lower bound)
+    unsigned long long info;
+    int status;
+    int pad;
+  };
+  Readback *d_rb = nullptr, *h_rb = nullptr;
+  unsigned long long *d_info = nullptr;  // &d_rb->info
+  double *d_norms = nullptr;             // d_rb->norms
+  int *d_status = nullptr;               // &d_rb->status
+  void *d_y = nullptr;                   // work vector [N][np][kMaxCols]
   // persistent dataflow launches
   int sched = BTC_SCHED_FLOW;
   int variant = BTC_VARIANT_HYBRID;
   int32_t *d_fac_deps = nullptr, *d_fac_deps_rl = nullptr;
   SolveFlowItem *d_solve_flow = nullptr;
   int n_fac = 0, n_solve = 0;
-  int *d_flow = nullptr;  // [0] factor ticket, [1] solve ticket, [2] status, then done flags
+  int *d_flow = nullptr;  // [0] factor ticket, [1] solve ticket, then done flags
   int fac_grid = 0, solve_grid = 0;
+  // interlaced factorization + forward sweep, and the rest of the solve
+  int32_t *d_inter_code = nullptr, *d_inter_deps = nullptr;
+  SolveFlowItem *d_tail = nullptr;
+  int n_inter = 0, n_tail = 0, inter_grid = 0;
   unsigned long long *trace_fac = nullptr, *trace_solve = nullptr;  // caller-owned trace buffers
-  // host staging for readbacks
+  // optional per-kernel-class event timing (btc_plan_set_timing)
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing_pending[BTC_TIMING_CLASSES];
+  // host views of the readback block
   double *h_norms = nullptr;
   unsigned long long *h_info = nullptr;
   int *h_status = nullptr;
@@ -146,6 +136,26 @@ struct btc_plan_s {
 };
 
 namespace btc {
+
+// Brackets the launches of one kernel class with CUDA events on the plan's
+// stream when timing is enabled (resolved by btc_plan_timing).
+struct KernelTimer {
+  btc_plan_s *p;
+  int cls;
+  cudaEvent_t e0 = nullptr;
+  KernelTimer(btc_plan_s *plan, int c) : p(plan), cls(c) {
+    if (p->timing && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, p->stream);
+  }
+  ~KernelTimer() {
+    cudaEvent_t e1 = nullptr;
+    if (e0 && cudaEventCreate(&e1) == cudaSuccess) {
+      cudaEventRecord(e1, p->stream);
+      p->timing_pending[cls].push_back({e0, e1});
+    } else if (e0) {
+      cudaEventDestroy(e0);
+    }
+  }
+};
 
 static void fill_info(const HostPlan &hp, int dtype, btc_plan_info *info) {
   memset(info, 0, sizeof(*info));
@@ -185,7 +195,7 @@ int set_smem(const void *fn, size_t bytes) {
 static FlowSync flow_sync(btc_plan_s *p, int which) {
   FlowSync fs;
   fs.ticket = p->d_flow + which;
-  fs.status = p->d_flow + 2;
+  fs.status = p->d_status;
   fs.done = p->d_flow + kFlowHeader;
   fs.trace = which == 0 ? p->trace_fac : p->trace_solve;
   return fs;
@@ -199,6 +209,7 @@ static int run_solve(btc_plan_s *p, int m) {
   a.epool = p->epool;
   a.y = p->d_y;
   a.m = m;
+  KernelTimer timer(p, BTC_TIME_SOLVE);
   if (p->sched == BTC_SCHED_FLOW) {
     BTC_CUDA(cudaMemsetAsync(p->d_flow + 1, 0, sizeof(int), p->stream));
     BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_solve, p->stream));
@@ -222,10 +233,17 @@ static int run_solve(btc_plan_s *p, int m) {
   return BTC_OK;
 }
 
+static int decode_info(btc_plan_s *p, int *block, int *col);
+
 static int read_info(btc_plan_s *p, int *block, int *col) {
-  BTC_CUDA(cudaMemcpyAsync(p->h_info, p->d_info, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->stream));
-  BTC_CUDA(cudaMemcpyAsync(p->h_status, p->d_flow + 2, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  BTC_CUDA(cudaMemcpyAsync(p->h_info, p->d_info, sizeof(unsigned long long) + sizeof(int), cudaMemcpyDeviceToHost,
+                           p->stream));
   BTC_CUDA(cudaStreamSynchronize(p->stream));
+  return decode_info(p, block, col);
+}
+
+// Pivot report and flow status as last copied to the host.
+static int decode_info(btc_plan_s *p, int *block, int *col) {
   if (*p->h_status != 0) return BTC_ERR_TIMEOUT;
   unsigned long long v = *p->h_info;
   if (v == ~0ull) {
@@ -238,6 +256,227 @@ static int read_info(btc_plan_s *p, int *block, int *col) {
   return BTC_ERR_NOT_SPD;
 }
 
+// Factorization (Alg. 5, or Alg. 6 with the right-looking variant). m_inter > 0:
+// the forward sweep over the first m_inter columns of the work vector (packed
+// by the caller) is interlaced with the factorization in the same persistent
+// launch; the caller then runs only the tail of the solve (run_solve_tail).
+static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter) {
+  if (!p || !D || (p->N > 1 && !B)) return fail(BTC_ERR_ARG, "btc_factor: NULL argument");
+  if (((uintptr_t)D | (uintptr_t)B) & 15) return fail(BTC_ERR_ARG, "btc_factor: D and B must be 16-byte aligned");
+  const KernelSet &k = *p->ks;
+  BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
+  FactorArgs a;
+  a.dpool = p->dpool;
+  a.epool = p->epool;
+  a.info = p->d_info;
+  a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
+  const bool mixed_root = p->dtype == BTC_MIXED_F32;
+  if (p->variant == BTC_VARIANT_RIGHT_LOOKING) {
+    // Alg. 6: packing pass, then every level from the pools with immediate (atomic) updates
+    InstDesc d{D, B, p->N, p->n};
+    int rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n);
+    if (rc) return rc;
+    BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+    const int last = p->hp.levels - 1;
+    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
+    if (p->sched == BTC_SCHED_FLOW) {
+      if (nflow > 0) {
+        BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+        BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
+        a.items = p->d_fac;
+        a.count = nflow;
+        const int32_t *deps = p->d_fac_deps_rl;
+        int zero = 0;
+        if ((rc = launch_n(k.fac_flow_rl, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d,
+                           deps, zero, flow_sync(p, 0))))
+          return rc;
+      }
+    } else {
+      for (int l = 0; l < p->hp.levels - (mixed_root ? 1 : 0); ++l) {
+        a.items = p->d_fac + p->fac_off[l];
+        a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
+        if ((rc = launch_n(k.fac_rl, a.count, k.fac_threads, k.fac_smem, p->stream, a, d))) return rc;
+      }
+    }
+    if (mixed_root) {
+      a.items = p->d_fac + p->fac_off[last];
+      a.count = 1;
+      if ((rc = launch_n(k.root_rl, 1, k.root_threads, k.root_smem, p->stream, a, d))) return rc;
+    }
+    p->D = D;
+    p->B = B;
+    p->factored = true;
+    p->anorm_valid = false;
+    return BTC_OK;
+  }
+  if (p->sched == BTC_SCHED_FLOW) {
+    // all levels but the FP64 root (mixed path) in one persistent launch
+    const int last = p->hp.levels - 1;
+    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
+    const int nfirst = (int)p->fac_off[1];
+    InstDesc d{D, B, p->N, p->n};
+    if (m_inter > 0 && p->n_inter > 0) {
+      BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+      BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+      BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_inter, p->stream));
+      a.items = p->d_fac;
+      a.count = p->n_inter;
+      SolveArgs sa;
+      sa.items = p->d_solve_flow;
+      sa.count = p->hp.n_fwd;
+      sa.dpool = p->dpool;
+      sa.epool = p->epool;
+      sa.y = p->d_y;
+      sa.m = m_inter;
+      const int32_t *code = p->d_inter_code, *deps = p->d_inter_deps;
+      KernelTimer timer(p, BTC_TIME_FACTOR_FORWARD);
+      int rc = launch_n(k.fac_fwd_flow, std::min(p->inter_grid, p->n_inter), k.fac_threads, k.fused_smem(m_inter),
+                        p->stream, a, d, sa, code, deps, nfirst, p->n_inter, flow_sync(p, 0));
+      if (rc) return rc;
+    } else if (nflow > 0) {
+      BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+      BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+      BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
+      a.items = p->d_fac;
+      a.count = nflow;
+      const int32_t *deps = p->d_fac_deps;
+      KernelTimer timer(p, BTC_TIME_FACTOR);
+      int rc = launch_n(k.fac_flow, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps,
+                        nfirst, flow_sync(p, 0));
+      if (rc) return rc;
+    } else {
+      BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+    }
+    if (mixed_root) {
+      a.items = p->d_fac + p->fac_off[last];
+      a.count = 1;
+      KernelTimer timer(p, BTC_TIME_ROOT);
+      int rc = launch_n(last == 0 ? k.root_first : k.root_rest, 1, k.root_threads, k.root_smem, p->stream, a, d);
+      if (rc) return rc;
+    }
+    p->D = D;
+    p->B = B;
+    p->factored = true;
+    p->anorm_valid = false;
+    return BTC_OK;
+  }
+  BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  for (int l = 0; l < p->hp.levels; ++l) {
+    a.items = p->d_fac + p->fac_off[l];
+    a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
+    const bool root = (l == p->hp.levels - 1) && p->dtype == BTC_MIXED_F32;
+    const void *fn = root ? (l == 0 ? k.root_first : k.root_rest) : (l == 0 ? k.fac_first : k.fac_rest);
+    const int threads = root ? k.root_threads : k.fac_threads;
+    const size_t smem = root ? k.root_smem : k.fac_smem;
+    InstDesc d{D, B, p->N, p->n};
+    int rc = launch_n(fn, a.count, threads, smem, p->stream, a, d);
+    if (rc) return rc;
+  }
+  p->D = D;
+  p->B = B;
+  p->factored = true;
+  p->anorm_valid = false;
+  return BTC_OK;
+}
+
+// The rest of the solve after an interlaced factorization: the top
+// separator's forward item (mixed path) and the whole backward sweep, in one
+// persistent launch.
+static int run_solve_tail(btc_plan_s *p, int m) {
+  const KernelSet &k = *p->ks;
+  SolveArgs a;
+  a.dpool = p->dpool;
+  a.epool = p->epool;
+  a.y = p->d_y;
+  a.m = m;
+  a.items = p->d_tail;
+  a.count = p->n_tail;
+  KernelTimer timer(p, BTC_TIME_SOLVE_TAIL);
+  BTC_CUDA(cudaMemsetAsync(p->d_flow + 1, 0, sizeof(int), p->stream));
+  BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_tail, p->stream));
+  return launch_n(k.solve_flow, std::min(p->solve_grid, p->n_tail), kSolveThreads, k.fwd_smem(m), p->stream, a,
+                  flow_sync(p, 1));
+}
+
+// The interlaced form needs the hybrid variant, the persistent schedule and
+// right-hand sides that fit in one pass.
+static bool can_interlace(const btc_plan_s *p, int m) {
+  return p->variant == BTC_VARIANT_HYBRID && p->sched == BTC_SCHED_FLOW && p->ks->fac_fwd_flow && m >= 1 &&
+         m <= std::min(kMaxCols, p->ks->max_cols);
+}
+
+
+// FP64 iterative refinement, chunk by chunk of at most max_cols columns:
+// x = solve(b), then while ||b - Psi x|| > tol ||Psi|| ||x||: x += solve(r).
+// first_done: the first chunk of x already holds its first solve (interlaced
+// factorization). The first residual also forms the ||Psi|| bound when the
+// factorization is new, and the norms, the pivot report and the flow status
+// come back to the host in one copy per iteration.
+static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
+                        double *relres, bool first_done) {
+  const KernelSet &k = *p->ks;
+  const int mc = std::min(kMaxCols, k.max_cols);
+  int worst_it = 0, rc = BTC_OK;
+  double worst_rel = 0.0;
+  bool all_ok = true, info_checked = false;
+  for (int c0 = 0; c0 < nrhs; c0 += mc) {
+    const int m = std::min(mc, nrhs - c0);
+    int64_t base = 0;
+    int assign = 0, accumulate = 1;
+    if (!(first_done && c0 == 0)) {
+      if ((rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)b,
+                         p->N, p->n, p->np, m, nrhs, c0, base)) ||
+          (rc = run_solve(p, m)) ||
+          (rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
+                         (const void *)p->d_y, p->N, p->n, p->np, m, nrhs, c0, base, assign)))
+        return rc;
+    }
+    int it = 0;
+    double rel = 0.0;
+    bool ok = false;
+    for (;;) {
+      const int with_anorm = p->anorm_valid ? 0 : 1;
+      BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, (2 + with_anorm) * sizeof(double), p->stream));
+      {
+        KernelTimer timer(p, BTC_TIME_RESIDUAL);
+        if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
+                           (const double *)p->D, (const double *)p->B, (const double *)x, b, p->N, p->n, p->np, m,
+                           base, p->d_norms, with_anorm)))
+          return rc;
+      }
+      BTC_CUDA(cudaMemcpyAsync(p->h_rb, p->d_rb, sizeof(btc_plan_s::Readback), cudaMemcpyDeviceToHost, p->stream));
+      BTC_CUDA(cudaStreamSynchronize(p->stream));
+      p->anorm_valid = true;
+      if (!info_checked) {
+        int blk, col;
+        rc = decode_info(p, &blk, &col);
+        if (rc == BTC_ERR_TIMEOUT) return fail(rc, "factorization failed: a bounded device-side wait gave up");
+        if (rc) return fail(rc, "factorization failed: pivot of block %d, column %d not positive", blk, col);
+        info_checked = true;
+      }
+      const double rn = p->h_norms[0], xn = p->h_norms[1], an = p->h_norms[2];
+      rel = (an * xn > 0) ? rn / (an * xn) : rn;
+      if (!(rel == rel)) break;  // NaN: give up
+      if (rel <= tol) {
+        ok = true;
+        break;
+      }
+      if (it >= maxit) break;
+      if ((rc = run_solve(p, m))) return rc;
+      if ((rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
+                         (const void *)p->d_y, p->N, p->n, p->np, m, nrhs, c0, base, accumulate)))
+        return rc;
+      ++it;
+    }
+    worst_it = std::max(worst_it, it);
+    worst_rel = std::max(worst_rel, rel);
+    all_ok = all_ok && ok;
+  }
+  if (iters) *iters = worst_it;
+  if (relres) *relres = worst_rel;
+  if (!all_ok) return fail(BTC_ERR_NOT_CONVERGED, "refinement stopped at relative residual %.3e", worst_rel);
+  return BTC_OK;
+}
 }  // namespace btc
 
 extern "C" {
@@ -274,6 +513,34 @@ int btc_schedule(int N, int *order_out, int *levels_out) {
   return t == N ? BTC_OK : fail(BTC_ERR_ARG, "schedule covers %d of %d nodes", t, N);
 }
 
+int btc_schedule_interlaced(int N, int root_separate, int *kind, int *node, int *level, int *deps, int *count,
+                            int *tail_count) {
+  if (N < 1 || !count) return fail(BTC_ERR_ARG, "btc_schedule_interlaced: invalid arguments");
+  HostPlan hp;
+  build_host_plan(N, 1, 8, 0, 0, 0, 0, &hp);
+  std::vector<int32_t> code, dp;
+  std::vector<SolveFlowItem> tail;
+  build_interlaced(hp, root_separate != 0, &code, &dp, &tail);
+  std::vector<int32_t> fnode, flevel;
+  for (int l = 1; l <= hp.levels; ++l)
+    for (const FactorItem &it : hp.lv[l - 1].fac) {
+      fnode.push_back(it.node + 1);
+      flevel.push_back(l);
+    }
+  const int c = (int)code.size();
+  if (kind && node && level && deps)
+    for (int t = 0; t < std::min(c, *count); ++t) {
+      const int32_t q = code[t];
+      kind[t] = q >= 0 ? 0 : 1;
+      node[t] = q >= 0 ? fnode[q] : hp.fwd_node[-1 - q];
+      level[t] = q >= 0 ? flevel[q] : hp.fwd_level[-1 - q];
+      for (int k = 0; k < kInterDeps; ++k) deps[kInterDeps * t + k] = dp[(size_t)kInterDeps * t + k];
+    }
+  *count = c;
+  if (tail_count) *tail_count = (int)tail.size();
+  return BTC_OK;
+}
+
 int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   if (!out || N < 1 || n < 1) return fail(BTC_ERR_ARG, "btc_plan: invalid arguments (N=%d, n=%d)", N, n);
   *out = nullptr;
@@ -301,13 +568,18 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   if ((e = cudaMalloc(&p->dpool, dbytes)) != cudaSuccess ||
       (e = cudaMalloc(&p->epool, ebytes)) != cudaSuccess ||
       (e = cudaMalloc(&p->d_y, (size_t)N * np * kMaxCols * ks.elem)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_info, sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_norms, 4 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&p->h_norms, 4 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&p->h_info, sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMallocHost(&p->h_status, sizeof(int))) != cudaSuccess)
+      (e = cudaMalloc(&p->d_rb, sizeof(btc_plan_s::Readback))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_rb, sizeof(btc_plan_s::Readback))) != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
                         cudaGetErrorString(e)));
+  p->d_norms = p->d_rb->norms;
+  p->d_info = &p->d_rb->info;
+  p->d_status = &p->d_rb->status;
+  p->h_norms = p->h_rb->norms;
+  p->h_info = &p->h_rb->info;
+  p->h_status = &p->h_rb->status;
+  if ((e = cudaMemset(p->d_rb, 0, sizeof(btc_plan_s::Readback))) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_CUDA, "btc_plan: %s", cudaGetErrorString(e)));
   p->device_bytes = (int64_t)(dbytes + ebytes + (size_t)N * np * kMaxCols * ks.elem);
   // flatten the per-level schedules and upload them
   std::vector<FactorItem> fac;
@@ -338,7 +610,24 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   // dataflow form
   p->n_fac = (int)fac.size();
   p->n_solve = (int)p->hp.solve_flow.size();
-  const size_t nflags = kFlowHeader + (size_t)std::max(p->n_fac, p->n_solve);
+  std::vector<int32_t> icode, ideps;
+  std::vector<SolveFlowItem> tail;
+  build_interlaced(p->hp, dtype == BTC_MIXED_F32, &icode, &ideps, &tail);
+  p->n_inter = (int)icode.size();
+  p->n_tail = (int)tail.size();
+  if ((e = cudaMalloc(&p->d_inter_code, std::max<size_t>(icode.size(), 1) * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_inter_deps, std::max<size_t>(ideps.size(), 1) * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_tail, std::max<size_t>(tail.size(), 1) * sizeof(SolveFlowItem))) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_OOM, "btc_plan: interlaced schedule allocation: %s", cudaGetErrorString(e)));
+  if ((!icode.empty() && (e = cudaMemcpy(p->d_inter_code, icode.data(), icode.size() * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!ideps.empty() && (e = cudaMemcpy(p->d_inter_deps, ideps.data(), ideps.size() * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!tail.empty() && (e = cudaMemcpy(p->d_tail, tail.data(), tail.size() * sizeof(SolveFlowItem),
+                                        cudaMemcpyHostToDevice)) != cudaSuccess))
+    return cleanup(fail(BTC_ERR_CUDA, "btc_plan: interlaced schedule upload: %s", cudaGetErrorString(e)));
+  p->device_bytes += (int64_t)((icode.size() + ideps.size()) * sizeof(int32_t) + tail.size() * sizeof(SolveFlowItem));
+  const size_t nflags = kFlowHeader + (size_t)std::max(std::max(p->n_fac, p->n_solve), std::max(p->n_inter, p->n_tail));
   if ((e = cudaMalloc(&p->d_fac_deps, p->hp.fac_deps.size() * sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_fac_deps_rl, p->hp.fac_deps_rl.size() * sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_solve_flow, p->hp.solve_flow.size() * sizeof(SolveFlowItem))) != cudaSuccess ||
@@ -360,19 +649,23 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
       (rc = set_smem(ks.resid, residual_smem_bytes(n, kMaxCols))) ||
       (rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.fac_flow_rl, ks.fac_smem)) ||
       (rc = set_smem(ks.fac_rl, ks.fac_smem)) || (rc = set_smem(ks.root_rl, ks.root_smem)) ||
-      (rc = set_smem(ks.solve_flow, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))))
+      (rc = set_smem(ks.solve_flow, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
+      (rc = set_smem(ks.fac_fwd_flow, ks.fused_smem(std::min(kMaxCols, ks.max_cols)))))
     return cleanup(rc);
   {
-    int dev = 0, sms = 0, bf = 0, bs_ = 0;
+    int dev = 0, sms = 0, bf = 0, bs_ = 0, bi = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, ks.fac_flow, ks.fac_threads, ks.fac_smem)) !=
             cudaSuccess ||
         (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs_, ks.solve_flow, kSolveThreads, ks.fwd_smem(1))) !=
+            cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, ks.fac_fwd_flow, ks.fac_threads, ks.fused_smem(1))) !=
             cudaSuccess)
       return cleanup(fail(BTC_ERR_CUDA, "btc_plan: occupancy: %s", cudaGetErrorString(e)));
     p->fac_grid = std::max(1, bf * sms);
     p->solve_grid = std::max(1, bs_ * sms);
+    p->inter_grid = std::max(1, bi * sms);
   }
   *out = p;
   return BTC_OK;
@@ -412,104 +705,7 @@ int btc_plan_query(btc_plan_t p, btc_plan_info *info) {
   return BTC_OK;
 }
 
-int btc_factor(btc_plan_t p, const void *D, const void *B) {
-  if (!p || !D || (p->N > 1 && !B)) return fail(BTC_ERR_ARG, "btc_factor: NULL argument");
-  if (((uintptr_t)D | (uintptr_t)B) & 15) return fail(BTC_ERR_ARG, "btc_factor: D and B must be 16-byte aligned");
-  const KernelSet &k = *p->ks;
-  BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
-  FactorArgs a;
-  a.dpool = p->dpool;
-  a.epool = p->epool;
-  a.info = p->d_info;
-  a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
-  const bool mixed_root = p->dtype == BTC_MIXED_F32;
-  if (p->variant == BTC_VARIANT_RIGHT_LOOKING) {
-    // Alg. 6: packing pass, then every level from the pools with immediate (atomic) updates
-    InstDesc d{D, B, p->N, p->n};
-    int rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n);
-    if (rc) return rc;
-    BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
-    const int last = p->hp.levels - 1;
-    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
-    if (p->sched == BTC_SCHED_FLOW) {
-      if (nflow > 0) {
-        BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
-        BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
-        a.items = p->d_fac;
-        a.count = nflow;
-        const int32_t *deps = p->d_fac_deps_rl;
-        int zero = 0;
-        if ((rc = launch_n(k.fac_flow_rl, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d,
-                           deps, zero, flow_sync(p, 0))))
-          return rc;
-      }
-    } else {
-      for (int l = 0; l < p->hp.levels - (mixed_root ? 1 : 0); ++l) {
-        a.items = p->d_fac + p->fac_off[l];
-        a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
-        if ((rc = launch_n(k.fac_rl, a.count, k.fac_threads, k.fac_smem, p->stream, a, d))) return rc;
-      }
-    }
-    if (mixed_root) {
-      a.items = p->d_fac + p->fac_off[last];
-      a.count = 1;
-      if ((rc = launch_n(k.root_rl, 1, k.root_threads, k.root_smem, p->stream, a, d))) return rc;
-    }
-    p->D = D;
-    p->B = B;
-    p->factored = true;
-    p->anorm_valid = false;
-    return BTC_OK;
-  }
-  if (p->sched == BTC_SCHED_FLOW) {
-    // all levels but the FP64 root (mixed path) in one persistent launch
-    const int last = p->hp.levels - 1;
-    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
-    const int nfirst = (int)p->fac_off[1];
-    InstDesc d{D, B, p->N, p->n};
-    if (nflow > 0) {
-      BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
-      BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
-      BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
-      a.items = p->d_fac;
-      a.count = nflow;
-      const int32_t *deps = p->d_fac_deps;
-      int rc = launch_n(k.fac_flow, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps,
-                        nfirst, flow_sync(p, 0));
-      if (rc) return rc;
-    } else {
-      BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
-    }
-    if (mixed_root) {
-      a.items = p->d_fac + p->fac_off[last];
-      a.count = 1;
-      int rc = launch_n(last == 0 ? k.root_first : k.root_rest, 1, k.root_threads, k.root_smem, p->stream, a, d);
-      if (rc) return rc;
-    }
-    p->D = D;
-    p->B = B;
-    p->factored = true;
-    p->anorm_valid = false;
-    return BTC_OK;
-  }
-  BTC_CUDA(cudaMemsetAsync(p->d_flow + 2, 0, sizeof(int), p->stream));
-  for (int l = 0; l < p->hp.levels; ++l) {
-    a.items = p->d_fac + p->fac_off[l];
-    a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
-    const bool root = (l == p->hp.levels - 1) && p->dtype == BTC_MIXED_F32;
-    const void *fn = root ? (l == 0 ? k.root_first : k.root_rest) : (l == 0 ? k.fac_first : k.fac_rest);
-    const int threads = root ? k.root_threads : k.fac_threads;
-    const size_t smem = root ? k.root_smem : k.fac_smem;
-    InstDesc d{D, B, p->N, p->n};
-    int rc = launch_n(fn, a.count, threads, smem, p->stream, a, d);
-    if (rc) return rc;
-  }
-  p->D = D;
-  p->B = B;
-  p->factored = true;
-  p->anorm_valid = false;
-  return BTC_OK;
-}
+int btc_factor(btc_plan_t p, const void *D, const void *B) { return factor_impl(p, D, B, 0); }
 
 int btc_solve(btc_plan_t p, void *rhs, int nrhs) {
   if (!p || !rhs || nrhs < 1) return fail(BTC_ERR_ARG, "btc_solve: invalid arguments");
@@ -538,66 +734,46 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
   const int mc = std::min(kMaxCols, p->ks->max_cols);
   if (nrhs > mc) return fail(BTC_ERR_UNSUPPORTED, "btc_solve_refined: at most %d right-hand sides for this plan", mc);
   if (!p->factored) return fail(BTC_ERR_NOT_FACTORED, "btc_solve_refined: no factorization");
+  return refined_impl(p, b, x, nrhs, tol, maxit, iters, relres, false);
+}
+
+int btc_factor_solve(btc_plan_t p, const void *D, const void *B, void *rhs, int nrhs) {
+  if (!p || !rhs || nrhs < 1) return fail(BTC_ERR_ARG, "btc_factor_solve: invalid arguments");
+  if (!can_interlace(p, nrhs)) {
+    int rc = btc_factor(p, D, B);
+    return rc ? rc : btc_solve(p, rhs, nrhs);
+  }
   const KernelSet &k = *p->ks;
-  int blk, col;
-  int rc = read_info(p, &blk, &col);
-  if (rc == BTC_ERR_TIMEOUT) return fail(rc, "factorization failed: a bounded device-side wait gave up");
-  if (rc) return fail(rc, "factorization failed: pivot of block %d, column %d not positive", blk, col);
-  if (!p->anorm_valid) {
-    BTC_CUDA(cudaMemsetAsync(p->d_norms + 2, 0, sizeof(double), p->stream));
-    if ((rc = launch_n((const void *)&k_anorm_lb, p->N, 64, 0, p->stream, (const double *)p->D,
-                       (const double *)p->B, p->N, p->n, p->d_norms)))
-      return rc;
-    p->anorm_valid = true;
+  int64_t base = 0;
+  int c0 = 0, assign = 0;
+  int rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * nrhs), 256, 0, p->stream, p->d_y, (const void *)rhs,
+                    p->N, p->n, p->np, nrhs, nrhs, c0, base);
+  if (rc || (rc = factor_impl(p, D, B, nrhs)) || (rc = run_solve_tail(p, nrhs))) return rc;
+  return launch_n(k.unpack, grid_for((int64_t)p->N * p->n * nrhs), 256, 0, p->stream, rhs, (const void *)p->d_y,
+                  p->N, p->n, p->np, nrhs, nrhs, c0, base, assign);
+}
+
+int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const double *b, double *x, int nrhs,
+                             double tol, int maxit, int *iters, double *relres) {
+  if (!p || !b || !x || nrhs < 1 || maxit < 0) return fail(BTC_ERR_ARG, "btc_factor_solve_refined: invalid arguments");
+  if (p->dtype == BTC_F32) return fail(BTC_ERR_ARG, "btc_factor_solve_refined needs an FP64 or mixed plan");
+  const int mc = std::min(kMaxCols, p->ks->max_cols);
+  if (nrhs > mc)
+    return fail(BTC_ERR_UNSUPPORTED, "btc_factor_solve_refined: at most %d right-hand sides for this plan", mc);
+  if (!can_interlace(p, nrhs)) {
+    int rc = btc_factor(p, D, B);
+    return rc ? rc : btc_solve_refined(p, b, x, nrhs, tol, maxit, iters, relres);
   }
-  int worst_it = 0;
-  double worst_rel = 0.0;
-  bool all_ok = true;
-  for (int c0 = 0; c0 < nrhs; c0 += mc) {
-    const int m = std::min(mc, nrhs - c0);
-    int64_t base = 0;
-    // x_0 = solve(b)
-    if ((rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)b, p->N,
-                       p->n, p->np, m, nrhs, c0, base)))
-      return rc;
-    if ((rc = run_solve(p, m))) return rc;
-    int assign = 0, accumulate = 1;
-    if ((rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
-                       (const void *)p->d_y, p->N, p->n, p->np, m, nrhs, c0, base, assign)))
-      return rc;
-    int it = 0;
-    double rel = 0.0;
-    bool ok = false;
-    for (;;) {
-      BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, 2 * sizeof(double), p->stream));
-      if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
-                         (const double *)p->D, (const double *)p->B, (const double *)x, b, p->N, p->n, p->np, m, base,
-                         p->d_norms)))
-        return rc;
-      BTC_CUDA(cudaMemcpyAsync(p->h_norms, p->d_norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-      BTC_CUDA(cudaStreamSynchronize(p->stream));
-      const double rn = p->h_norms[0], xn = p->h_norms[1], an = p->h_norms[2];
-      rel = (an * xn > 0) ? rn / (an * xn) : rn;
-      if (!(rel == rel)) break;  // NaN: give up
-      if (rel <= tol) {
-        ok = true;
-        break;
-      }
-      if (it >= maxit) break;
-      if ((rc = run_solve(p, m))) return rc;
-      if ((rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
-                         (const void *)p->d_y, p->N, p->n, p->np, m, nrhs, c0, base, accumulate)))
-        return rc;
-      ++it;
-    }
-    worst_it = std::max(worst_it, it);
-    worst_rel = std::max(worst_rel, rel);
-    all_ok = all_ok && ok;
-  }
-  if (iters) *iters = worst_it;
-  if (relres) *relres = worst_rel;
-  if (!all_ok) return fail(BTC_ERR_NOT_CONVERGED, "refinement stopped at relative residual %.3e", worst_rel);
-  return BTC_OK;
+  const KernelSet &k = *p->ks;
+  int64_t base = 0;
+  int c0 = 0, assign = 0;
+  int rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np * nrhs), 256, 0, p->stream, p->d_y, (const void *)b, p->N,
+                    p->n, p->np, nrhs, nrhs, c0, base);
+  if (rc || (rc = factor_impl(p, D, B, nrhs)) || (rc = run_solve_tail(p, nrhs))) return rc;
+  if ((rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * nrhs), 256, 0, p->stream, (void *)x,
+                     (const void *)p->d_y, p->N, p->n, p->np, nrhs, nrhs, c0, base, assign)))
+    return rc;
+  return refined_impl(p, b, x, nrhs, tol, maxit, iters, relres, true);
 }
 
 int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void *b, void *x, int nrhs, double tol,
@@ -621,17 +797,17 @@ int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void
   BTC_CUDA(cudaMemcpyAsync(p->s_D, D, nb * p->N, cudaMemcpyHostToDevice, p->stream));
   if (p->N > 1) BTC_CUDA(cudaMemcpyAsync(p->s_B, B, nb * (p->N - 1), cudaMemcpyHostToDevice, p->stream));
   BTC_CUDA(cudaMemcpyAsync(p->s_b, b, rbytes, cudaMemcpyHostToDevice, p->stream));
-  int rc = btc_factor(p, p->s_D, p->s_B);
-  if (rc) return rc;
+  int rc = BTC_OK;
   if (p->dtype == BTC_F32) {
     BTC_CUDA(cudaMemcpyAsync(p->s_x, p->s_b, rbytes, cudaMemcpyDeviceToDevice, p->stream));
-    if ((rc = btc_solve(p, p->s_x, nrhs))) return rc;
+    if ((rc = btc_factor_solve(p, p->s_D, p->s_B, p->s_x, nrhs))) return rc;
     int blk, col;
     if ((rc = read_info(p, &blk, &col))) return fail(rc, "pivot of block %d, column %d not positive", blk, col);
     if (iters) *iters = 0;
     if (relres) *relres = -1.0;
   } else {
-    rc = btc_solve_refined(p, (const double *)p->s_b, (double *)p->s_x, nrhs, tol, maxit, iters, relres);
+    rc = btc_factor_solve_refined(p, p->s_D, p->s_B, (const double *)p->s_b, (double *)p->s_x, nrhs, tol, maxit, iters,
+                                  relres);
     if (rc && rc != BTC_ERR_NOT_CONVERGED) return rc;
     if (rc) {
       std::string keep = g_err;
@@ -706,7 +882,8 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
     double *ynull = nullptr;
     int np = n;
     int64_t base = 0;
-    if (!rc) rc = launch_n(rk, N, kResThreads, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d);
+    int no_bound = 0;
+    if (!rc) rc = launch_n(rk, N, kResThreads, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d, no_bound);
   }
   double h[3] = {0, 0, 0};
   if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -721,17 +898,49 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
   return BTC_OK;
 }
 
+int btc_plan_set_timing(btc_plan_t p, int enable) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_timing: NULL plan");
+  double ms[BTC_TIMING_CLASSES];
+  int n[BTC_TIMING_CLASSES];
+  int rc = btc_plan_timing(p, ms, n);  // drop what is pending
+  p->timing = enable != 0;
+  return rc;
+}
+
+int btc_plan_timing(btc_plan_t p, double *ms, int *launches) {
+  if (!p || !ms || !launches) return fail(BTC_ERR_ARG, "btc_plan_timing: NULL argument");
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  for (int c = 0; c < BTC_TIMING_CLASSES; ++c) {
+    ms[c] = 0.0;
+    launches[c] = 0;
+    for (auto &ev : p->timing_pending[c]) {
+      float t = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev.first, ev.second);
+      ms[c] += t;
+      ++launches[c];
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+    p->timing_pending[c].clear();
+  }
+  if (e != cudaSuccess) return fail(BTC_ERR_CUDA, "btc_plan_timing: %s", cudaGetErrorString(e));
+  return BTC_OK;
+}
+
 int btc_free(btc_plan_t p) {
   if (!p) return BTC_OK;
   if (p->stream || p->dpool) cudaStreamSynchronize(p->stream);
-  void *dev[] = {p->dpool, p->epool, p->d_fac, p->d_fwd,        p->d_bwd,          p->d_info,
-                 p->d_norms, p->d_y,   p->s_D,   p->d_fac_deps, p->d_solve_flow,     p->d_flow,
-                 p->s_B,     p->s_b,   p->s_x,   p->d_fac_deps_rl};
+  for (auto &v : p->timing_pending)
+    for (auto &ev : v) {
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+  void *dev[] = {p->dpool,        p->epool,        p->d_fac,    p->d_fwd,  p->d_bwd,     p->d_rb,
+                 p->d_y,          p->s_D,          p->d_fac_deps, p->d_solve_flow, p->d_flow, p->s_B,
+                 p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail};
   for (void *q : dev)
     if (q) cudaFree(q);
-  if (p->h_norms) cudaFreeHost(p->h_norms);
-  if (p->h_info) cudaFreeHost(p->h_info);
-  if (p->h_status) cudaFreeHost(p->h_status);
+  if (p->h_rb) cudaFreeHost(p->h_rb);
   delete p;
   return BTC_OK;
 }

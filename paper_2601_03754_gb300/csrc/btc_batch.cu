@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const Batc
   }
 }
 
-// Lower bound of ||Psi||_inf per instance into norms[3*inst + 2] (see k_anorm_lb).
+// Lower bound of ||Psi||_inf per instance into norms[3*inst + 2] for the
+// refinement's stopping test: each |a_ij| rounded toward zero to FP32, row
+// sums with round-toward-zero additions, so the bound never exceeds the norm.
 __global__ void k_batch_anorm_lb(const BatchNode *nodes, const InstDesc *inst, double *norms) {
   const BatchNode nd = nodes[blockIdx.x];
   const InstDesc in = inst[nd.inst];

@@ -93,7 +93,25 @@ struct HostPlan {
   std::vector<int> slot_e, slot_o;      // per U slot: eliminated node and partner (0-based)
   double factor_flops = 0, seq_factor_flops = 0, crit_flops = 0, crit_formula = 0;
   double solve_flops_per_rhs = 0;
+  // forward items of solve_flow (the first n_fwd entries): node (1-based) and level
+  int32_t n_fwd = 0;
+  std::vector<int32_t> fwd_node, fwd_level;
 };
+
+// Interlaced factorization and forward substitution in one persistent launch
+// (the forward sweep of level l runs as soon as the blocks it reads are
+// factored). Entry t of `code` is a factor item (code >= 0, flat level-order
+// index) or a forward item (code < 0: solve_flow index -code-1); its
+// dependencies are kInterDeps earlier entries (-1: none). Order: factor items
+// of level 1, forward items of level 1, factor items of level 2, ...
+// root_separate (mixed path): the top separator's factor and forward items
+// are left out; its FP64 factor runs between the two launches. `tail` is the
+// rest of the solve for a second persistent launch: the top separator's
+// forward item (root_separate only, first), then every backward item, with
+// dependencies renumbered within the tail.
+constexpr int kInterDeps = 6;
+void build_interlaced(const HostPlan &P, bool root_separate, std::vector<int32_t> *code, std::vector<int32_t> *deps,
+                      std::vector<SolveFlowItem> *tail);
 
 // Build the schedule. Offsets are relative to the given bases (in blocks for
 // the pools, in nodes for the work vector) so that batched plans can

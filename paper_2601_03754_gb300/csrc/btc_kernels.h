@@ -22,6 +22,9 @@ struct KernelSet {
   size_t root_smem = 0;
   // persistent dataflow forms (all levels in one launch)
   const void *fac_flow = nullptr, *solve_flow = nullptr;
+  // interlaced factorization + forward substitution (same CTA shape as fac_flow)
+  const void *fac_fwd_flow = nullptr;
+  size_t (*fused_smem)(int m) = nullptr;
   // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, FP64 root
   const void *pack_matrix = nullptr, *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
   // solve

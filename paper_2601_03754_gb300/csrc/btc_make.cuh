@@ -1,6 +1,7 @@
 // Builds the KernelSet of one (arithmetic, pool, source, np) instantiation.
 #pragma once
 #include "btc_factor.cuh"
+#include "btc_fused.cuh"
 #include "btc_kernels.h"
 #include "btc_solve.cuh"
 
@@ -16,6 +17,8 @@ template <typename T, int NP>
 size_t fwd_smem_fn(int m) { return fwd_smem_bytes<T, NP>(m); }
 template <typename T, int NP>
 size_t bwd_smem_fn(int m) { return bwd_smem_bytes<T, NP>(m); }
+template <typename T, int NP, int R>
+size_t fused_smem_fn(int m) { return fused_smem_bytes<T, NP, R>(m); }
 
 template <typename T, typename S, int NP, bool MIXED>
 KernelSet make_set() {
@@ -37,6 +40,8 @@ KernelSet make_set() {
     k.root_smem = root_smem_bytes<NP, R>();
   }
   k.fac_flow = (const void *)&k_factor_flow<T, T, S, NP, R>;
+  k.fac_fwd_flow = (const void *)&k_factor_fwd_flow<T, T, S, NP, R>;
+  k.fused_smem = &fused_smem_fn<T, NP, R>;
   k.pack_matrix = (const void *)&k_pack_matrix<T, S, NP>;
   k.fac_rl = (const void *)&k_factor_level<T, T, S, NP, R, false, true>;
   k.fac_flow_rl = (const void *)&k_factor_flow_rl<T, T, S, NP, R>;

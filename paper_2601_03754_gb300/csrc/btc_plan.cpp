@@ -122,6 +122,7 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
         }
       }
       f.d_self = ((j / s) & 1) ? dOff(j) : -1;
+      if (f.y_l < 0 && f.y_r < 0 && f.d_self < 0) continue;  // a level-1 survivor: nothing to do
       L.fwd.push_back(f);
     }
   }
@@ -160,6 +161,8 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
     std::vector<std::vector<int32_t>> fwd_index(levels + 1);
     std::vector<int32_t> fwd_final(N + 1, -1), bwd_index(N + 1, -1);
     P->solve_flow.clear();
+    P->fwd_node.clear();
+    P->fwd_level.clear();
     for (int l = 1; l <= levels; ++l) {
       const int64_t s = int64_t(1) << (l - 1), h = s / 2;
       fwd_index[l].assign(N + 1, -1);
@@ -182,8 +185,11 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
         fwd_index[l][j] = (int32_t)P->solve_flow.size();
         if (f.d_self >= 0) fwd_final[j] = (int32_t)P->solve_flow.size();
         P->solve_flow.push_back(q);
+        P->fwd_node.push_back((int32_t)j);
+        P->fwd_level.push_back(l);
       }
     }
+    P->n_fwd = (int32_t)P->solve_flow.size();
     for (int l = levels; l >= 1; --l) {
       for (const BwdItem &b : P->lv[l - 1].bwd) {
         const int64_t e = b.x_self - y_base + 1;
@@ -214,6 +220,65 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
   int lg = levels - 1;
   P->crit_formula = N >= 2 ? (16.0 / 3.0 + 22.0 / 3.0 * (lg - 1) + 4.0 / 3.0) * n3 : n3 / 3.0;
   P->solve_flops_per_rhs = sol;
+}
+
+void build_interlaced(const HostPlan &P, bool root_separate, std::vector<int32_t> *code, std::vector<int32_t> *deps,
+                      std::vector<SolveFlowItem> *tail) {
+  const int N = P.N, levels = P.levels;
+  code->clear();
+  deps->clear();
+  tail->clear();
+  // flat factor index of the node eliminated at each level
+  std::vector<int32_t> fac_start(levels + 1, 0), fac_of_node(N + 1, -1);
+  for (int l = 1; l <= levels; ++l) {
+    fac_start[l] = fac_start[l - 1] + (int32_t)P.lv[l - 1].fac.size();
+    for (size_t q = 0; q < P.lv[l - 1].fac.size(); ++q) fac_of_node[P.lv[l - 1].fac[q].node + 1] = fac_start[l - 1] + (int32_t)q;
+  }
+  std::vector<int32_t> fac_ticket(fac_start[levels], -1), fwd_ticket(P.n_fwd, -1);
+  auto push = [&](int32_t c, const int32_t (&d)[kInterDeps]) {
+    code->push_back(c);
+    deps->insert(deps->end(), d, d + kInterDeps);
+    return (int32_t)code->size() - 1;
+  };
+  int32_t w = 0;  // next forward item
+  for (int l = 1; l <= levels; ++l) {
+    if (root_separate && l == levels) break;  // the top separator: factored by its own kernel
+    const int64_t h = (int64_t(1) << (l - 1)) / 2;
+    for (int32_t f = fac_start[l - 1]; f < fac_start[l]; ++f) {
+      int32_t d[kInterDeps] = {-1, -1, -1, -1, -1, -1};
+      for (int k = 0; k < 3; ++k) {
+        const int32_t src = P.fac_deps[3 * (size_t)f + k];
+        d[k] = src >= 0 ? fac_ticket[src] : -1;
+      }
+      fac_ticket[f] = push(f, d);
+    }
+    for (; w < P.n_fwd && P.fwd_level[w] == l; ++w) {
+      const SolveFlowItem &it = P.solve_flow[w];
+      const int64_t j = P.fwd_node[w];
+      int32_t d[kInterDeps] = {-1, -1, -1, -1, -1, -1};
+      for (int k = 0; k < 3; ++k) d[k] = it.dep[k] >= 0 ? fwd_ticket[it.dep[k]] : -1;
+      // the factor items that write U_j (level l), U(j-h, j) and U(j+h, j) (level l-1)
+      if (it.d_self >= 0) d[3] = fac_ticket[fac_of_node[j]];
+      if (it.y_a >= 0) d[4] = fac_ticket[fac_of_node[j - h]];
+      if (it.y_b >= 0) d[5] = fac_ticket[fac_of_node[j + h]];
+      fwd_ticket[w] = push(-1 - w, d);
+    }
+  }
+  // the tail: [top-separator forward item] + backward items
+  int32_t root_fwd = -1;
+  if (root_separate) {
+    root_fwd = P.n_fwd - 1;  // the single forward item of the top level
+    SolveFlowItem r = P.solve_flow[root_fwd];
+    r.dep[0] = r.dep[1] = r.dep[2] = -1;  // its inputs are complete before the tail starts
+    tail->push_back(r);
+  }
+  const int32_t off = root_separate ? 1 : 0;
+  for (size_t b = (size_t)P.n_fwd; b < P.solve_flow.size(); ++b) {
+    SolveFlowItem q = P.solve_flow[b];
+    for (int k = 0; k < 2; ++k) q.dep[k] = q.dep[k] >= 0 ? q.dep[k] - P.n_fwd + off : -1;
+    q.dep[2] = (root_fwd >= 0 && q.dep[2] == root_fwd) ? 0 : -1;
+    tail->push_back(q);
+  }
 }
 
 }  // namespace btc

@@ -40,7 +40,4 @@ inline int grid_for(int64_t total) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
 }
 
-// Lower bound of the infinity norm per block row (refinement stopping test).
-__global__ void k_anorm_lb(const double *D, const double *B, int N, int n, double *norms);
-
 }  // namespace btc

@@ -170,8 +170,10 @@ void worker(btc_server_s *s, int slot) {
     if (rc == BTC_OK) rc = btc_plan_set_stream(plan, stream);  // plans move between slots
     int iters = 0;
     double rel = 0.0;
-    if (rc == BTC_OK && !resolve) rc = btc_factor(plan, job.req.D, job.req.B);
-    if (rc == BTC_OK)
+    if (rc == BTC_OK && !resolve)  // factor with the forward sweep interlaced, then refine
+      rc = btc_factor_solve_refined(plan, job.req.D, job.req.B, job.req.b, job.req.x, 1, job.req.tol, job.req.maxit,
+                                    &iters, &rel);
+    else if (rc == BTC_OK)
       rc = btc_solve_refined(plan, job.req.b, job.req.x, 1, job.req.tol, job.req.maxit, &iters, &rel);
     cudaStreamSynchronize(stream);
     const auto t_done = Clock::now();

@@ -42,7 +42,7 @@ __device__ __forceinline__ void stage_block(T *dst, const T *g) {
   constexpr int CPR = NP / V;
   constexpr int CHUNKS = NP * CPR;
 #pragma unroll 4
-  for (int q = threadIdx.x; q < CHUNKS; q += kSolveThreads) {
+  for (int q = threadIdx.x; q < CHUNKS; q += blockDim.x) {
     const int row = q / CPR, col = (q % CPR) * V;
     cp_async16_s(dst + row * LDL + col, g + (size_t)row * NP + col);
   }
@@ -62,8 +62,8 @@ template <typename T, int NP>
 __device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *dinv) {
   constexpr int LDL = SolveCfg<T, NP>::LDL;
   constexpr int RPL = (NP + 31) / 32;  // rows per lane
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = warp; q < m; q += nw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
+  for (int q = warp; q < m && warp < nw; q += nw) {
     T v[RPL];
 #pragma unroll
     for (int s = 0; s < RPL; ++s) {
@@ -97,8 +97,8 @@ template <typename T, int NP>
 __device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *dinv) {
   constexpr int LDL = SolveCfg<T, NP>::LDL;
   constexpr int RPL = (NP + 31) / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = warp; q < m; q += nw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
+  for (int q = warp; q < m && warp < nw; q += nw) {
     T v[RPL];
 #pragma unroll
     for (int s = 0; s < RPL; ++s) {
@@ -367,26 +367,42 @@ __device__ __forceinline__ void stage_f64(double *dst, const double *src, int n)
   }
 }
 
+// |a| rounded toward zero to FP32 with integer operations only (the FP64 ->
+// FP32 conversion instruction runs on the slow FP64 pipe of this GPU): keep
+// the exponent and the top 23 mantissa bits. Magnitudes below the FP32
+// normal range give 0 and above it FLT_MAX, both lower bounds of |a|.
+__device__ __forceinline__ float abs_lower_f32(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+  const int e = (int)(u >> 52) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return 3.402823466e38f;
+  return __int_as_float((e << 23) | (int)((u >> 29) & 0x7fffff));
+}
+
 // r = b - Psi x in FP64 for one block row per CTA; writes r (converted to T)
 // into the padded work vector y when y != nullptr, and max|r|, max|x| into
 // norms[0], norms[1]. D: lower triangles read. Each output's 3n-term dot
 // product is split into kResParts contiguous partial sums, added in a fixed
 // order (deterministic). Matrix entries are read straight from global memory
 // (each block's rows stay in L1 across the partial sums); x_{i-1}, x_i,
-// x_{i+1} are staged in shared memory. Dynamic shared memory:
-// (3 + kResParts) * n * m doubles.
+// x_{i+1} are staged in shared memory. with_anorm != 0: the same pass also
+// forms a lower bound of ||Psi||_inf into norms[2] (each |a_ij| rounded toward
+// zero to FP32, row sums with round-toward-zero additions, so the stopping
+// test ||r|| <= tol ||Psi|| ||x|| is never met early). Dynamic shared memory:
+// residual_smem_bytes(n, m).
 constexpr int kResParts = 4;
 constexpr int kResThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D, const double *B, const double *x,
                                                           const double *b, int N, int n, int np, int m,
-                                                          int64_t node_base, double *norms) {
+                                                          int64_t node_base, double *norms, int with_anorm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i = blockIdx.x;
   const int nm = n * m;
   double *xs = reinterpret_cast<double *>(smem_raw);  // [3][n*m]: x_{i-1}, x_i, x_{i+1}
   double *ps = xs + 3 * nm;                            // [kResParts][n*m]
+  float *as = reinterpret_cast<float *>(ps + kResParts * nm);  // [kResParts][n] row-sum parts
   const size_t bs = (size_t)n * n;
   for (int q = threadIdx.x; q < 3 * nm; q += blockDim.x) {
     const int which = q / nm, off = q % nm, row = i - 1 + which;
@@ -401,16 +417,32 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
     const int part = idx / nm, q = idx % nm;
     const int r = q / m, col = q % m;
     const int c0 = part * chunk, c1 = min(n, c0 + chunk);
+    const bool lb = with_anorm && col == 0;
     double v = 0.0;
-    for (int c = c0; c < c1; ++c) v = fma(r >= c ? Di[r * n + c] : Di[c * n + r], xs[nm + c * m + col], v);
+    float s = 0.0f;
+    for (int c = c0; c < c1; ++c) {
+      const double a = r >= c ? Di[r * n + c] : Di[c * n + r];
+      v = fma(a, xs[nm + c * m + col], v);
+      if (lb) s = __fadd_rz(s, abs_lower_f32(a));
+    }
     if (Bl)
-      for (int c = c0; c < c1; ++c) v = fma(Bl[r * n + c], xs[c * m + col], v);
+      for (int c = c0; c < c1; ++c) {
+        const double a = Bl[r * n + c];
+        v = fma(a, xs[c * m + col], v);
+        if (lb) s = __fadd_rz(s, abs_lower_f32(a));
+      }
     if (Br)
-      for (int c = c0; c < c1; ++c) v = fma(Br[c * n + r], xs[2 * nm + c * m + col], v);
+      for (int c = c0; c < c1; ++c) {
+        const double a = Br[c * n + r];
+        v = fma(a, xs[2 * nm + c * m + col], v);
+        if (lb) s = __fadd_rz(s, abs_lower_f32(a));
+      }
     ps[part * nm + q] = v;
+    if (lb) as[part * n + r] = s;
   }
   __syncthreads();
   double rmax = 0.0, xmax = 0.0;
+  float amax = 0.0f;
   for (int q = threadIdx.x; q < nm; q += blockDim.x) {
     double ax = 0.0;
 #pragma unroll
@@ -420,6 +452,12 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
     if (y) y[(node_base + i) * np * m + r * m + col] = convert_in<T, double>(v);
     rmax = fmax(rmax, fabs(v));
     xmax = fmax(xmax, fabs(xs[nm + q]));
+    if (with_anorm && col == 0) {
+      float rs = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kResParts; ++k) rs = __fadd_rz(rs, as[k * n + r]);
+      amax = fmaxf(amax, rs);
+    }
   }
   if (y) {
     for (int q = threadIdx.x; q < (np - n) * m; q += blockDim.x) y[(node_base + i) * np * m + n * m + q] = T(0);
@@ -427,25 +465,18 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
   for (int o = 16; o > 0; o >>= 1) {
     rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   }
   if ((threadIdx.x & 31) == 0) {
     atomic_max_nonneg(norms + 0, rmax);
     atomic_max_nonneg(norms + 1, xmax);
+    if (with_anorm) atomic_max_nonneg(norms + 2, (double)amax);
   }
 }
 
-inline size_t residual_smem_bytes(int n, int m) { return sizeof(double) * (size_t)(3 + kResParts) * n * m; }
-
-// |a| rounded toward zero to FP32 with integer operations only (the FP64 ->
-// FP32 conversion instruction runs on the slow FP64 pipe of this GPU): keep
-// the exponent and the top 23 mantissa bits. Magnitudes below the FP32
-// normal range give 0 and above it FLT_MAX, both lower bounds of |a|.
-__device__ __forceinline__ float abs_lower_f32(double a) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
-  const int e = (int)(u >> 52) - 1023 + 127;
-  if (e <= 0) return 0.0f;
-  if (e >= 255) return 3.402823466e38f;
-  return __int_as_float((e << 23) | (int)((u >> 29) & 0x7fffff));
+inline size_t residual_smem_bytes(int n, int m) {
+  return sizeof(double) * (size_t)(3 + kResParts) * n * m + sizeof(float) * (size_t)kResParts * n;
 }
+
 
 }  // namespace btc
