@@ -472,6 +472,7 @@ def main():
                       "p99_us": 1000 * float(np.percentile(np.asarray(ts64), 99))},
         "speedup_vs_plain_f64": ms64 / ms,
         "phases_ms": phase,
+        "flow_config": dict(zip(("resident_cap", "ctas_per_sm", "tuned"), btc.btc_plan_tuning(pm))),
         "roofline": {"kernel": "k_factor_fwd_flow (interlaced factor + forward sweep, one launch per step)",
                      "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,

@@ -199,6 +199,33 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
                       double *relres);
 
 /*
+ * Autotuning of the persistent factorization (on by default). The library
+ * compiles the persistent factor kernels for several register budgets (one per
+ * cap of 1-4 resident CTAs per SM; 1, 2, 4, 8 for 64-thread CTAs). On the first
+ * persistent factorization of a plan shape (dtype, padded n, N, variant) it
+ * times every compiled cap at every CTAs-per-SM count that fits, three runs
+ * each on the caller's D and B, keeps the fastest median and remembers it for
+ * the process; the factor itself is the same in every configuration (only the
+ * schedule changes). enable = 0: no tuning, the default configuration.
+ * btc_plan_tuning reports the configuration in use (host pointers, each may be
+ * NULL): the register-budget cap, the CTAs per SM of the launch, and whether it
+ * was tuned.
+ */
+int btc_plan_set_autotune(btc_plan_t p, int enable);
+int btc_plan_tuning(btc_plan_t p, int *resident_cap, int *ctas_per_sm, int *tuned);
+
+/*
+ * Pin the persistent factorization's configuration (turns autotuning off):
+ * the compiled register-budget cap and the CTAs per SM of the launch
+ * (0: as many as fit). Errors: BTC_ERR_UNSUPPORTED when no variant has that
+ * cap, BTC_ERR_ARG when the CTAs do not fit. btc_plan_flow_configs lists the
+ * compiled caps and the CTAs per SM each allows (host arrays; on input *count
+ * is their capacity, on output the number of variants).
+ */
+int btc_plan_set_flow_config(btc_plan_t p, int resident_cap, int ctas_per_sm);
+int btc_plan_flow_configs(btc_plan_t p, int *caps, int *max_ctas, int *count);
+
+/*
  * Optional event timing of a plan's kernels, by class. While enabled, every
  * launch of the classes below is bracketed by CUDA events recorded on the
  * plan's stream (a few microseconds of host work per launch; leave disabled in

@@ -57,6 +57,10 @@ _SIGS = {
     "btc_solve_refined": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
     "btc_factor_solve": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "btc_plan_set_timing": [_vp, ctypes.c_int],
+    "btc_plan_set_autotune": [_vp, ctypes.c_int],
+    "btc_plan_tuning": [_vp, _ip, _ip, _ip],
+    "btc_plan_set_flow_config": [_vp, ctypes.c_int, ctypes.c_int],
+    "btc_plan_flow_configs": [_vp, _ip, _ip, _ip],
     "btc_plan_timing": [_vp, _dp, _ip],
     "btc_schedule_interlaced": [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip, _ip, _ip, _ip],
     "btc_factor_solve_refined": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
@@ -214,6 +218,30 @@ def btc_solve_refined(plan, b, x, nrhs, tol=1e-10, maxit=20, allow_not_converged
 
 TIME_FACTOR, TIME_FACTOR_FORWARD, TIME_ROOT, TIME_SOLVE, TIME_SOLVE_TAIL, TIME_RESIDUAL = range(6)
 TIMING_CLASSES = 6
+
+
+def btc_plan_set_autotune(plan, enable=True):
+    return _check(load().btc_plan_set_autotune(plan.h, int(bool(enable))))
+
+
+def btc_plan_tuning(plan):
+    """(register-budget cap, CTAs per SM, tuned) of the plan's persistent factorization."""
+    a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().btc_plan_tuning(plan.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, bool(c.value)
+
+
+def btc_plan_set_flow_config(plan, resident_cap, ctas_per_sm=0):
+    return _check(load().btc_plan_set_flow_config(plan.h, resident_cap, ctas_per_sm))
+
+
+def btc_plan_flow_configs(plan):
+    """[(register-budget cap, max CTAs per SM)] of the compiled persistent factor kernels."""
+    caps = (ctypes.c_int * 8)()
+    mx = (ctypes.c_int * 8)()
+    n = ctypes.c_int(8)
+    _check(load().btc_plan_flow_configs(plan.h, caps, mx, ctypes.byref(n)))
+    return [(caps[i], mx[i]) for i in range(min(n.value, 8))]
 
 
 def btc_plan_set_timing(plan, enable=True):

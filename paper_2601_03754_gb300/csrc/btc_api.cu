@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -43,9 +45,10 @@ static std::once_flag g_once;
 
 static void init_tables() {
   std::call_once(g_once, [] {
-    register_f64(g_sets[BTC_F64], &g_nsets[BTC_F64]);
-    register_f32(g_sets[BTC_F32], &g_nsets[BTC_F32]);
-    register_mixed(g_sets[BTC_MIXED_F32], &g_nsets[BTC_MIXED_F32]);
+    const int code_f64 = BTC_F64, code_f32 = BTC_F32, code_mixed = BTC_MIXED_F32;
+#define BTC_ADD_SET(dt, np) g_sets[code_##dt][g_nsets[code_##dt]++] = make_set_##dt##_##np();
+    BTC_FOR_EACH_SET(BTC_ADD_SET)
+#undef BTC_ADD_SET
   });
 }
 
@@ -118,6 +121,11 @@ struct btc_plan_s {
   int32_t *d_inter_code = nullptr, *d_inter_deps = nullptr;
   SolveFlowItem *d_tail = nullptr;
   int n_inter = 0, n_tail = 0, inter_grid = 0;
+  // persistent-kernel configuration: residency variant and CTAs per SM (autotuned)
+  int sms = 0;
+  int flow_var = 0, ctas_per_sm = 0;
+  int occ_fac[kFlowVariants] = {}, occ_fused[kFlowVariants] = {}, occ_rl[kFlowVariants] = {};
+  bool autotune = true, tuned[2] = {false, false};  // per algorithm variant (hybrid, right-looking)
   unsigned long long *trace_fac = nullptr, *trace_solve = nullptr;  // caller-owned trace buffers
   // optional per-kernel-class event timing (btc_plan_set_timing)
   bool timing = false;
@@ -256,66 +264,136 @@ static int decode_info(btc_plan_s *p, int *block, int *col) {
   return BTC_ERR_NOT_SPD;
 }
 
-// Factorization (Alg. 5, or Alg. 6 with the right-looking variant). m_inter > 0:
-// the forward sweep over the first m_inter columns of the work vector (packed
-// by the caller) is interlaced with the factorization in the same persistent
-// launch; the caller then runs only the tail of the solve (run_solve_tail).
-static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter) {
-  if (!p || !D || (p->N > 1 && !B)) return fail(BTC_ERR_ARG, "btc_factor: NULL argument");
-  if (((uintptr_t)D | (uintptr_t)B) & 15) return fail(BTC_ERR_ARG, "btc_factor: D and B must be 16-byte aligned");
+// Persistent factor kernels of variant v with c CTAs per SM (0: as many as fit).
+static void apply_flow_config(btc_plan_s *p, int v, int c) {
+  const int occ = std::max(1, p->occ_fac[v]);
+  c = (c <= 0 || c > occ) ? occ : c;
+  p->flow_var = v;
+  p->ctas_per_sm = c;
+  p->fac_grid = c * p->sms;
+  p->inter_grid = std::max(1, std::min(c, std::max(1, p->occ_fused[v]))) * p->sms;
+}
+
+// Process-wide memory of tuned configurations: (dtype, np, N, algorithm
+// variant) -> (residency variant, CTAs per SM).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;
+
+static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B);
+
+// Autotuner of the persistent factorization: times every compiled residency
+// variant at every CTAs-per-SM count that fits on the caller's own D and B (the
+// arithmetic does not depend on the configuration, only the schedule does) and
+// keeps the fastest median of three; remembered per shape for the process.
+static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
+  const int alg = p->variant == BTC_VARIANT_RIGHT_LOOKING ? 1 : 0;
+  const auto key = std::make_tuple(p->dtype, p->np, p->N, alg);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      apply_flow_config(p, it->second.first, it->second.second);
+      p->tuned[alg] = true;
+      return BTC_OK;
+    }
+  }
   const KernelSet &k = *p->ks;
-  BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
+  cudaEvent_t e0, e1;
+  BTC_CUDA(cudaEventCreate(&e0));
+  BTC_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_v = k.flow_default, best_c = 0, rc = BTC_OK;
+  for (int v = 0; v < k.n_flow_v && rc == BTC_OK; ++v) {
+    const int occ = alg ? p->occ_rl[v] : p->occ_fac[v];
+    for (int c = 1; c <= occ && rc == BTC_OK; ++c) {
+      apply_flow_config(p, v, c);
+      float t[3];
+      for (int r = 0; r < 3 && rc == BTC_OK; ++r) {
+        cudaEventRecord(e0, p->stream);
+        rc = launch_factor_flow(p, D, B);
+        cudaEventRecord(e1, p->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(BTC_ERR_CUDA, "autotune: synchronize failed");
+        cudaEventElapsedTime(&t[r], e0, e1);
+      }
+      if (rc) break;
+      std::sort(t, t + 3);
+      if (t[1] < best) {
+        best = t[1];
+        best_v = v;
+        best_c = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  apply_flow_config(p, best_v, best_c);
+  p->tuned[alg] = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = {best_v, best_c};
+  return BTC_OK;
+}
+
+// Persistent factorization launch of every level except the FP64 top
+// separator of the mixed path (hybrid Alg. 5, or Alg. 6 after its packing
+// pass), with the plan's configuration.
+static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
+  const KernelSet &k = *p->ks;
+  const FlowVariant &fv = k.flow_v[p->flow_var];
+  const bool mixed_root = p->dtype == BTC_MIXED_F32;
+  const int last = p->hp.levels - 1;
+  const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
   FactorArgs a;
   a.dpool = p->dpool;
   a.epool = p->epool;
   a.info = p->d_info;
   a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
-  const bool mixed_root = p->dtype == BTC_MIXED_F32;
-  if (p->variant == BTC_VARIANT_RIGHT_LOOKING) {
-    // Alg. 6: packing pass, then every level from the pools with immediate (atomic) updates
-    InstDesc d{D, B, p->N, p->n};
-    int rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n);
-    if (rc) return rc;
-    BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
-    const int last = p->hp.levels - 1;
-    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
-    if (p->sched == BTC_SCHED_FLOW) {
-      if (nflow > 0) {
-        BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
-        BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
-        a.items = p->d_fac;
-        a.count = nflow;
-        const int32_t *deps = p->d_fac_deps_rl;
-        int zero = 0;
-        if ((rc = launch_n(k.fac_flow_rl, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d,
-                           deps, zero, flow_sync(p, 0))))
-          return rc;
-      }
-    } else {
-      for (int l = 0; l < p->hp.levels - (mixed_root ? 1 : 0); ++l) {
-        a.items = p->d_fac + p->fac_off[l];
-        a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
-        if ((rc = launch_n(k.fac_rl, a.count, k.fac_threads, k.fac_smem, p->stream, a, d))) return rc;
-      }
-    }
-    if (mixed_root) {
-      a.items = p->d_fac + p->fac_off[last];
-      a.count = 1;
-      if ((rc = launch_n(k.root_rl, 1, k.root_threads, k.root_smem, p->stream, a, d))) return rc;
-    }
-    p->D = D;
-    p->B = B;
-    p->factored = true;
-    p->anorm_valid = false;
-    return BTC_OK;
+  a.items = p->d_fac;
+  a.count = nflow;
+  InstDesc d{D, B, p->N, p->n};
+  int rc = BTC_OK;
+  const bool rl = p->variant == BTC_VARIANT_RIGHT_LOOKING;
+  if (rl && (rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n))) return rc;
+  BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  if (nflow == 0) return BTC_OK;
+  BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+  BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
+  KernelTimer timer(p, BTC_TIME_FACTOR);
+  if (rl) {
+    int zero = 0;
+    const int32_t *deps = p->d_fac_deps_rl;
+    return launch_n(fv.fac_rl, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps, zero,
+                    flow_sync(p, 0));
   }
+  const int nfirst = (int)p->fac_off[1];
+  const int32_t *deps = p->d_fac_deps;
+  return launch_n(fv.fac, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps, nfirst,
+                  flow_sync(p, 0));
+}
+
+// Factorization (Alg. 5, or Alg. 6 with the right-looking variant). m_inter > 0:
+// the forward sweep over the first m_inter columns of the work vector (packed
+// by the caller) is interlaced with the factorization in the same persistent
+// launch (hybrid variant, persistent schedule); the caller then runs only the
+// tail of the solve (run_solve_tail).
+static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter) {
+  if (!p || !D || (p->N > 1 && !B)) return fail(BTC_ERR_ARG, "btc_factor: NULL argument");
+  if (((uintptr_t)D | (uintptr_t)B) & 15) return fail(BTC_ERR_ARG, "btc_factor: D and B must be 16-byte aligned");
+  const KernelSet &k = *p->ks;
+  const bool rl = p->variant == BTC_VARIANT_RIGHT_LOOKING;
+  int rc = BTC_OK;
+  if (p->sched == BTC_SCHED_FLOW && p->autotune && !p->tuned[rl ? 1 : 0] && (rc = autotune_flow(p, D, B))) return rc;
+  BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
+  FactorArgs a;
+  a.dpool = p->dpool;
+  a.epool = p->epool;
+  a.info = p->d_info;
+  a.inst = nullptr;
+  InstDesc d{D, B, p->N, p->n};
+  const bool mixed_root = p->dtype == BTC_MIXED_F32;
+  const int last = p->hp.levels - 1;
   if (p->sched == BTC_SCHED_FLOW) {
-    // all levels but the FP64 root (mixed path) in one persistent launch
-    const int last = p->hp.levels - 1;
-    const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
-    const int nfirst = (int)p->fac_off[1];
-    InstDesc d{D, B, p->N, p->n};
-    if (m_inter > 0 && p->n_inter > 0) {
+    if (!rl && m_inter > 0 && p->n_inter > 0) {
       BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
       BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
       BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_inter, p->stream));
@@ -329,48 +407,32 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
       sa.y = p->d_y;
       sa.m = m_inter;
       const int32_t *code = p->d_inter_code, *deps = p->d_inter_deps;
+      const int nfirst = (int)p->fac_off[1];
       KernelTimer timer(p, BTC_TIME_FACTOR_FORWARD);
-      int rc = launch_n(k.fac_fwd_flow, std::min(p->inter_grid, p->n_inter), k.fac_threads, k.fused_smem(m_inter),
-                        p->stream, a, d, sa, code, deps, nfirst, p->n_inter, flow_sync(p, 0));
-      if (rc) return rc;
-    } else if (nflow > 0) {
-      BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
-      BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
-      BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
-      a.items = p->d_fac;
-      a.count = nflow;
-      const int32_t *deps = p->d_fac_deps;
-      KernelTimer timer(p, BTC_TIME_FACTOR);
-      int rc = launch_n(k.fac_flow, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps,
-                        nfirst, flow_sync(p, 0));
-      if (rc) return rc;
+      rc = launch_n(k.flow_v[p->flow_var].fac_fwd, std::min(p->inter_grid, p->n_inter), k.fac_threads,
+                    k.fused_smem(m_inter), p->stream, a, d, sa, code, deps, nfirst, p->n_inter, flow_sync(p, 0));
     } else {
-      BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+      rc = launch_factor_flow(p, D, B);
     }
-    if (mixed_root) {
-      a.items = p->d_fac + p->fac_off[last];
-      a.count = 1;
-      KernelTimer timer(p, BTC_TIME_ROOT);
-      int rc = launch_n(last == 0 ? k.root_first : k.root_rest, 1, k.root_threads, k.root_smem, p->stream, a, d);
-      if (rc) return rc;
-    }
-    p->D = D;
-    p->B = B;
-    p->factored = true;
-    p->anorm_valid = false;
-    return BTC_OK;
-  }
-  BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
-  for (int l = 0; l < p->hp.levels; ++l) {
-    a.items = p->d_fac + p->fac_off[l];
-    a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
-    const bool root = (l == p->hp.levels - 1) && p->dtype == BTC_MIXED_F32;
-    const void *fn = root ? (l == 0 ? k.root_first : k.root_rest) : (l == 0 ? k.fac_first : k.fac_rest);
-    const int threads = root ? k.root_threads : k.fac_threads;
-    const size_t smem = root ? k.root_smem : k.fac_smem;
-    InstDesc d{D, B, p->N, p->n};
-    int rc = launch_n(fn, a.count, threads, smem, p->stream, a, d);
     if (rc) return rc;
+  } else {
+    // one launch per level (Alg. 5 or Alg. 6 level loops)
+    BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+    if (rl && (rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n))) return rc;
+    KernelTimer timer(p, BTC_TIME_FACTOR);
+    for (int l = 0; l < p->hp.levels - (mixed_root ? 1 : 0); ++l) {
+      a.items = p->d_fac + p->fac_off[l];
+      a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
+      const void *fn = rl ? k.fac_rl : (l == 0 ? k.fac_first : k.fac_rest);
+      if ((rc = launch_n(fn, a.count, k.fac_threads, k.fac_smem, p->stream, a, d))) return rc;
+    }
+  }
+  if (mixed_root) {
+    a.items = p->d_fac + p->fac_off[last];
+    a.count = 1;
+    const void *fn = rl ? k.root_rl : (last == 0 ? k.root_first : k.root_rest);
+    KernelTimer timer(p, BTC_TIME_ROOT);
+    if ((rc = launch_n(fn, 1, k.root_threads, k.root_smem, p->stream, a, d))) return rc;
   }
   p->D = D;
   p->B = B;
@@ -653,19 +715,28 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
       (rc = set_smem(ks.fac_fwd_flow, ks.fused_smem(std::min(kMaxCols, ks.max_cols)))))
     return cleanup(rc);
   {
-    int dev = 0, sms = 0, bf = 0, bs_ = 0, bi = 0;
+    int dev = 0, sms = 0, bs_ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, ks.fac_flow, ks.fac_threads, ks.fac_smem)) !=
-            cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs_, ks.solve_flow, kSolveThreads, ks.fwd_smem(1))) !=
-            cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, ks.fac_fwd_flow, ks.fac_threads, ks.fused_smem(1))) !=
-            cudaSuccess)
+    p->sms = std::max(1, sms);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs_, ks.solve_flow, kSolveThreads, ks.fwd_smem(1))) !=
+        cudaSuccess)
       return cleanup(fail(BTC_ERR_CUDA, "btc_plan: occupancy: %s", cudaGetErrorString(e)));
-    p->fac_grid = std::max(1, bf * sms);
+    for (int v = 0; v < ks.n_flow_v; ++v) {
+      const FlowVariant &fv = ks.flow_v[v];
+      if ((rc = set_smem(fv.fac, ks.fac_smem)) || (rc = set_smem(fv.fac_rl, ks.fac_smem)) ||
+          (rc = set_smem(fv.fac_fwd, ks.fused_smem(std::min(kMaxCols, ks.max_cols)))))
+        return cleanup(rc);
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_fac[v], fv.fac, ks.fac_threads, ks.fac_smem)) !=
+              cudaSuccess ||
+          (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_fused[v], fv.fac_fwd, ks.fac_threads,
+                                                             ks.fused_smem(1))) != cudaSuccess ||
+          (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_rl[v], fv.fac_rl, ks.fac_threads, ks.fac_smem)) !=
+              cudaSuccess)
+        return cleanup(fail(BTC_ERR_CUDA, "btc_plan: occupancy: %s", cudaGetErrorString(e)));
+    }
     p->solve_grid = std::max(1, bs_ * sms);
-    p->inter_grid = std::max(1, bi * sms);
+    apply_flow_config(p, ks.flow_default, 0);
   }
   *out = p;
   return BTC_OK;
@@ -895,6 +966,50 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
   out3[0] = h[0];
   out3[1] = h[2];
   out3[2] = h[1];
+  return BTC_OK;
+}
+
+int btc_plan_set_autotune(btc_plan_t p, int enable) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_autotune: NULL plan");
+  p->autotune = enable != 0;
+  if (!p->autotune) {
+    apply_flow_config(p, p->ks->flow_default, 0);
+    p->tuned[0] = p->tuned[1] = false;
+  }
+  return BTC_OK;
+}
+
+int btc_plan_set_flow_config(btc_plan_t p, int resident_cap, int ctas_per_sm) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_flow_config: NULL plan");
+  for (int v = 0; v < p->ks->n_flow_v; ++v)
+    if (p->ks->flow_v[v].minb == resident_cap) {
+      if (ctas_per_sm < 0 || ctas_per_sm > p->occ_fac[v])
+        return fail(BTC_ERR_ARG, "btc_plan_set_flow_config: %d CTAs per SM do not fit (at most %d)", ctas_per_sm,
+                    p->occ_fac[v]);
+      p->autotune = false;
+      p->tuned[0] = p->tuned[1] = false;
+      apply_flow_config(p, v, ctas_per_sm);
+      return BTC_OK;
+    }
+  return fail(BTC_ERR_UNSUPPORTED, "btc_plan_set_flow_config: no variant compiled for a cap of %d", resident_cap);
+}
+
+int btc_plan_flow_configs(btc_plan_t p, int *caps, int *max_ctas, int *count) {
+  if (!p || !count) return fail(BTC_ERR_ARG, "btc_plan_flow_configs: NULL argument");
+  const int n = std::min(*count, p->ks->n_flow_v);
+  for (int v = 0; v < n; ++v) {
+    if (caps) caps[v] = p->ks->flow_v[v].minb;
+    if (max_ctas) max_ctas[v] = p->occ_fac[v];
+  }
+  *count = p->ks->n_flow_v;
+  return BTC_OK;
+}
+
+int btc_plan_tuning(btc_plan_t p, int *resident_cap, int *ctas_per_sm, int *tuned) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_tuning: NULL plan");
+  if (resident_cap) *resident_cap = p->ks->flow_v[p->flow_var].minb;
+  if (ctas_per_sm) *ctas_per_sm = p->ctas_per_sm;
+  if (tuned) *tuned = p->tuned[p->variant == BTC_VARIANT_RIGHT_LOOKING ? 1 : 0] ? 1 : 0;
   return BTC_OK;
 }
 

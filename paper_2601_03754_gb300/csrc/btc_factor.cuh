@@ -176,19 +176,18 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT) k_factor_level(FactorAr
 // Persistent dataflow form: all levels in one launch. CTAs claim items in
 // level order and wait only for the (<= 3) items of the previous level that
 // produce their inputs (deps, 3 per item). The first `nfirst` items are
-// level 1 and read the caller's arrays.
+// level 1 and read the caller's arrays. MINB: resident CTAs per SM the
+// register budget is set for (one compiled variant per value).
 template <typename T, int NP, int R>
-struct FlowMinBlocks {  // resident CTAs per SM the shared memory allows (caps registers accordingly)
+struct FlowFit {  // resident CTAs per SM that shared memory and threads allow
   static constexpr size_t smem = factor_smem_bytes<T, NP, R>();
   static constexpr int by_smem = (int)((226 * 1024) / smem);
   static constexpr int by_threads = 2048 / TileCfg<T, NP, R>::NT;
-  static constexpr int fit = by_smem < by_threads ? by_smem : by_threads;
-  // large CTAs (np = 96: 576 threads) keep their registers rather than a second resident CTA
-  static constexpr int value = TileCfg<T, NP, R>::NT >= 512 ? 1 : fit < 1 ? 1 : fit > 3 ? 3 : fit;
+  static constexpr int value = by_smem < by_threads ? (by_smem < 1 ? 1 : by_smem) : by_threads;
 };
 
-template <typename T, typename P, typename S, int NP, int R>
-__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R>::value))
+template <typename T, typename P, typename S, int NP, int R, int MINB>
+__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     k_factor_flow(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
@@ -211,8 +210,8 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R
 // Persistent dataflow form of Alg. 6 (right-looking, atomics): every level
 // reads the packed pools; each item waits for the two nodes of the previous
 // level that last update its diagonal block and write its two fill blocks.
-template <typename T, typename P, typename S, int NP, int R>
-__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R>::value))
+template <typename T, typename P, typename S, int NP, int R, int MINB>
+__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     k_factor_flow_rl(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;

@@ -20,8 +20,8 @@ size_t fused_smem_bytes(int m) {
 // code[t] >= 0: factor item code[t] of fa.items (level 1 when < nfirst);
 // code[t] < 0: forward item -code[t]-1 of sa.items. kInterDeps dependencies
 // per entry.
-template <typename T, typename P, typename S, int NP, int R>
-__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, (FlowMinBlocks<T, NP, R>::value))
+template <typename T, typename P, typename S, int NP, int R, int MINB>
+__global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     k_factor_fwd_flow(FactorArgs fa, InstDesc single, SolveArgs sa, const int32_t *code, const int32_t *deps,
                       int nfirst, int count, FlowSync fs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

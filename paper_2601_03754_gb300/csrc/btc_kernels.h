@@ -7,6 +7,16 @@
 
 namespace btc {
 
+// One compiled form of the persistent factorization kernels: the register
+// budget is set for `minb` resident CTAs per SM (launch bounds), so the
+// variants trade registers per thread against CTAs per SM. The autotuner of a
+// plan picks the variant and the grid (btc_plan_set_autotune).
+struct FlowVariant {
+  int minb = 0;  // 0: absent
+  const void *fac = nullptr, *fac_fwd = nullptr, *fac_rl = nullptr;
+};
+constexpr int kFlowVariants = 4;
+
 struct KernelSet {
   bool valid = false;
   int np = 0;
@@ -25,6 +35,10 @@ struct KernelSet {
   // interlaced factorization + forward substitution (same CTA shape as fac_flow)
   const void *fac_fwd_flow = nullptr;
   size_t (*fused_smem)(int m) = nullptr;
+  // all compiled residency variants of the three persistent factor kernels;
+  // fac_flow, fac_fwd_flow and fac_flow_rl above are those of flow_v[flow_default]
+  FlowVariant flow_v[kFlowVariants];
+  int n_flow_v = 0, flow_default = 0;
   // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, FP64 root
   const void *pack_matrix = nullptr, *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
   // solve
@@ -37,8 +51,16 @@ struct KernelSet {
 
 // dtype codes as in btc.h
 const KernelSet &kernels_for(int dtype, int np);
-void register_f64(KernelSet *table, int *count);
-void register_f32(KernelSet *table, int *count);
-void register_mixed(KernelSet *table, int *count);
+
+// Every compiled (dtype, padded block size) pair; each has its own translation
+// unit btc_set_<dtype>_<np>.cu so that the build compiles them in parallel.
+// FP64 stops at 96 (three 128 x 128 FP64 blocks exceed one SM's shared memory).
+#define BTC_FOR_EACH_SET(X)                                                                              \
+  X(f64, 8) X(f64, 16) X(f64, 32) X(f64, 48) X(f64, 64) X(f64, 96)                                        \
+  X(f32, 8) X(f32, 16) X(f32, 32) X(f32, 48) X(f32, 64) X(f32, 96) X(f32, 128)                            \
+  X(mixed, 8) X(mixed, 16) X(mixed, 32) X(mixed, 48) X(mixed, 64) X(mixed, 96) X(mixed, 128)
+#define BTC_DECLARE_SET(dt, np) KernelSet make_set_##dt##_##np();
+BTC_FOR_EACH_SET(BTC_DECLARE_SET)
+#undef BTC_DECLARE_SET
 
 }  // namespace btc

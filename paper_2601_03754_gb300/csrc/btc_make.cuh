@@ -20,6 +20,19 @@ size_t bwd_smem_fn(int m) { return bwd_smem_bytes<T, NP>(m); }
 template <typename T, int NP, int R>
 size_t fused_smem_fn(int m) { return fused_smem_bytes<T, NP, R>(m); }
 
+// Residency variants of the persistent factor kernels: caps 1, 2, 3, 4 CTAs per
+// SM (1, 2, 4, 8 for 64-thread CTAs), those that shared memory and threads allow.
+template <typename T, typename S, int NP, int R, int MINB>
+void add_flow_variant(KernelSet &k) {
+  if constexpr (MINB == 1 || MINB <= FlowFit<T, NP, R>::value) {
+    FlowVariant &v = k.flow_v[k.n_flow_v++];
+    v.minb = MINB;
+    v.fac = (const void *)&k_factor_flow<T, T, S, NP, R, MINB>;
+    v.fac_fwd = (const void *)&k_factor_fwd_flow<T, T, S, NP, R, MINB>;
+    v.fac_rl = (const void *)&k_factor_flow_rl<T, T, S, NP, R, MINB>;
+  }
+}
+
 template <typename T, typename S, int NP, bool MIXED>
 KernelSet make_set() {
   constexpr int R = TileEdge<NP>::R;
@@ -39,12 +52,20 @@ KernelSet make_set() {
     k.root_threads = TileCfg<float, NP, R>::NT;
     k.root_smem = root_smem_bytes<NP, R>();
   }
-  k.fac_flow = (const void *)&k_factor_flow<T, T, S, NP, R>;
-  k.fac_fwd_flow = (const void *)&k_factor_fwd_flow<T, T, S, NP, R>;
+  constexpr bool small = TileCfg<T, NP, R>::NT <= 64;
+  add_flow_variant<T, S, NP, R, 1>(k);
+  add_flow_variant<T, S, NP, R, 2>(k);
+  add_flow_variant<T, S, NP, R, small ? 4 : 3>(k);
+  add_flow_variant<T, S, NP, R, small ? 8 : 4>(k);
+  // default without tuning: two resident CTAs where they fit (more registers per
+  // thread than the maximum residency; measured best at N = 1024, n = 64)
+  k.flow_default = k.n_flow_v > 1 ? 1 : 0;
+  k.fac_flow = k.flow_v[k.flow_default].fac;
+  k.fac_fwd_flow = k.flow_v[k.flow_default].fac_fwd;
+  k.fac_flow_rl = k.flow_v[k.flow_default].fac_rl;
   k.fused_smem = &fused_smem_fn<T, NP, R>;
   k.pack_matrix = (const void *)&k_pack_matrix<T, S, NP>;
   k.fac_rl = (const void *)&k_factor_level<T, T, S, NP, R, false, true>;
-  k.fac_flow_rl = (const void *)&k_factor_flow_rl<T, T, S, NP, R>;
   k.solve_flow = (const void *)&k_solve_flow<T, NP>;
   k.fwd = (const void *)&k_fwd_level<T, NP>;
   k.bwd = (const void *)&k_bwd_level<T, NP>;

@@ -1,0 +1,6 @@
+// Kernel set: FP64 inputs, FP32 factor and correction solves, FP64 top-separator Cholesky, padded block size 64.
+#include "btc_make.cuh"
+
+namespace btc {
+KernelSet make_set_mixed_64() { return make_set<float, double, 64, true>(); }
+}  // namespace btc

@@ -1,0 +1,6 @@
+// Kernel set: FP64 inputs, FP32 factor and correction solves, FP64 top-separator Cholesky, padded block size 8.
+#include "btc_make.cuh"
+
+namespace btc {
+KernelSet make_set_mixed_8() { return make_set<float, double, 8, true>(); }
+}  // namespace btc
