@@ -452,9 +452,9 @@ def main():
     fused_flops = info["factor_flops"] - root_flops + fwd_flops
     achieved = fused_flops / (t_fused * 1e-3) / 1e12
     traffic = _traffic_from_profile()
-    # pack, interlaced factor + forward, FP64 root, solve tail, unpack, residual; per refinement
-    # step: solve, update, residual
-    launches = 6 + 3 * iters
+    # graph of one step: pack, interlaced factor + forward, FP64 root, solve tail, unpack, residual,
+    # stopping test; per refinement step: solve, update, residual, stopping test
+    launches = 7 + 4 * iters
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

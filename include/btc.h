@@ -226,6 +226,20 @@ int btc_plan_set_flow_config(btc_plan_t p, int resident_cap, int ctas_per_sm);
 int btc_plan_flow_configs(btc_plan_t p, int *caps, int *max_ctas, int *count);
 
 /*
+ * CUDA graphs for btc_factor_solve_refined (on by default). With the
+ * interlaced form, one column pass and a settled persistent configuration,
+ * the whole refined factor + solve is captured once as an executable graph
+ * (pack, interlaced factorization + forward sweep, FP64 root, solve tail,
+ * unpack, FP64 residual, stopping test, and a device-side while loop of
+ * correction solves that runs until the stopping test says stop) and replayed
+ * on later calls with the same pointers, sizes and configuration (re-captured
+ * otherwise): one graph launch and one host synchronization per call. The
+ * graph runs on a plan-owned stream ordered after the plan's stream. Results
+ * are identical to the path without graphs. enable = 0: plain launches.
+ */
+int btc_plan_set_graphs(btc_plan_t p, int enable);
+
+/*
  * Optional event timing of a plan's kernels, by class. While enabled, every
  * launch of the classes below is bracketed by CUDA events recorded on the
  * plan's stream (a few microseconds of host work per launch; leave disabled in

@@ -58,6 +58,7 @@ _SIGS = {
     "btc_factor_solve": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "btc_plan_set_timing": [_vp, ctypes.c_int],
     "btc_plan_set_autotune": [_vp, ctypes.c_int],
+    "btc_plan_set_graphs": [_vp, ctypes.c_int],
     "btc_plan_tuning": [_vp, _ip, _ip, _ip],
     "btc_plan_set_flow_config": [_vp, ctypes.c_int, ctypes.c_int],
     "btc_plan_flow_configs": [_vp, _ip, _ip, _ip],
@@ -218,6 +219,10 @@ def btc_solve_refined(plan, b, x, nrhs, tol=1e-10, maxit=20, allow_not_converged
 
 TIME_FACTOR, TIME_FACTOR_FORWARD, TIME_ROOT, TIME_SOLVE, TIME_SOLVE_TAIL, TIME_RESIDUAL = range(6)
 TIMING_CLASSES = 6
+
+
+def btc_plan_set_graphs(plan, enable=True):
+    return _check(load().btc_plan_set_graphs(plan.h, int(bool(enable))))
 
 
 def btc_plan_set_autotune(plan, enable=True):

@@ -79,6 +79,30 @@ __global__ void k_anorm(const double *D, const double *B, int N, int n, double *
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, best);
 }
 
+// One readback block: the norms, the pivot report, the flow status and the
+// outcome of a graph-resident refinement come back to the host in one copy.
+struct Readback {
+  double norms[4];  // [0] max|r|, [1] max|x|, [2] ||Psi||_inf (lower bound)
+  unsigned long long info;
+  int status;
+  int iters;   // refinement steps taken (graph-resident loop)
+  double rel;  // last relative residual (graph-resident loop)
+};
+
+// Stopping test of the graph-resident refinement (one thread): relative
+// residual from the norms of the residual kernel; continue while it is above
+// tol, finite, and fewer than maxit steps were taken; the decision drives the
+// graph's while node.
+__global__ void k_refine_decide(Readback *rb, double tol, int maxit, int first, cudaGraphConditionalHandle h) {
+  const double rn = rb->norms[0], xn = rb->norms[1], an = rb->norms[2];
+  const double rel = (an * xn > 0) ? rn / (an * xn) : rn;
+  if (first) rb->iters = 0;
+  const bool more = !(rel <= tol) && rel == rel && rb->iters < maxit;
+  if (more) rb->iters += 1;
+  rb->rel = rel;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 bool dtype_ok(int dtype) { return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32; }
 
 }  // namespace btc
@@ -96,14 +120,6 @@ struct btc_plan_s {
   FwdItem *d_fwd = nullptr;
   BwdItem *d_bwd = nullptr;
   std::vector<int64_t> fac_off, fwd_off, bwd_off;  // per level start index
-  // one readback block: the norms, the pivot report and the flow status come
-  // back to the host in a single copy
-  struct Readback {
-    double norms[4];  // [0] max|r|, [1] max|x|, [2] ||Psi||_inf (lower bound)
-    unsigned long long info;
-    int status;
-    int pad;
-  };
   Readback *d_rb = nullptr, *h_rb = nullptr;
   unsigned long long *d_info = nullptr;  // &d_rb->info
   double *d_norms = nullptr;             // d_rb->norms
@@ -126,6 +142,13 @@ struct btc_plan_s {
   int flow_var = 0, ctas_per_sm = 0;
   int occ_fac[kFlowVariants] = {}, occ_fused[kFlowVariants] = {}, occ_rl[kFlowVariants] = {};
   bool autotune = true, tuned[2] = {false, false};  // per algorithm variant (hybrid, right-looking)
+  // executable graph of one refined factor + solve (btc_factor_solve_refined), for the pointers,
+  // sizes and configuration it was captured with
+  bool graphs = true;
+  cudaStream_t gstream = nullptr, gstream2 = nullptr;
+  cudaEvent_t gevent = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double> gkey;
   unsigned long long *trace_fac = nullptr, *trace_solve = nullptr;  // caller-owned trace buffers
   // optional per-kernel-class event timing (btc_plan_set_timing)
   bool timing = false;
@@ -506,7 +529,7 @@ static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, dou
                            base, p->d_norms, with_anorm)))
           return rc;
       }
-      BTC_CUDA(cudaMemcpyAsync(p->h_rb, p->d_rb, sizeof(btc_plan_s::Readback), cudaMemcpyDeviceToHost, p->stream));
+      BTC_CUDA(cudaMemcpyAsync(p->h_rb, p->d_rb, sizeof(Readback), cudaMemcpyDeviceToHost, p->stream));
       BTC_CUDA(cudaStreamSynchronize(p->stream));
       p->anorm_valid = true;
       if (!info_checked) {
@@ -537,6 +560,143 @@ static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, dou
   if (iters) *iters = worst_it;
   if (relres) *relres = worst_rel;
   if (!all_ok) return fail(BTC_ERR_NOT_CONVERGED, "refinement stopped at relative residual %.3e", worst_rel);
+  return BTC_OK;
+}
+
+// Key of a captured refinement graph: everything baked into it.
+static std::vector<double> refine_graph_key(const btc_plan_s *p, const void *D, const void *B, const double *b,
+                                            const double *x, int m, double tol, int maxit) {
+  return {(double)(uintptr_t)D, (double)(uintptr_t)B, (double)(uintptr_t)b, (double)(uintptr_t)x, (double)m, tol,
+          (double)maxit,        (double)p->flow_var,  (double)p->ctas_per_sm, (double)(uintptr_t)p->trace_fac,
+          (double)(uintptr_t)p->trace_solve};
+}
+
+// Capture one refined factor + solve of m <= max_cols columns as an executable
+// graph: pack, interlaced factorization + forward sweep, FP64 root, solve
+// tail, unpack, FP64 residual with the norm bound, stopping test; then a while
+// node whose body is one correction (solve, update, residual, stopping test),
+// repeated on the device until the test says stop; then one copy of the
+// readback block to the host. The host synchronizes once per call.
+static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const double *b, double *x, int m,
+                              double tol, int maxit) {
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  if (!p->gstream) {
+    BTC_CUDA(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+    BTC_CUDA(cudaStreamCreateWithFlags(&p->gstream2, cudaStreamNonBlocking));
+    BTC_CUDA(cudaEventCreateWithFlags(&p->gevent, cudaEventDisableTiming));
+  }
+  const KernelSet &k = *p->ks;
+  cudaStream_t user = p->stream;
+  cudaGraph_t g = nullptr;
+  int rc = BTC_OK;
+  int64_t base = 0;
+  int c0 = 0, assign = 0, accumulate = 1, one = 1, zero = 0;
+  cudaGraphConditionalHandle h = 0;
+  cudaError_t e = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(BTC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  p->stream = p->gstream;
+  auto body_cuda = [&]() -> int {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    BTC_CUDA(cudaStreamGetCaptureInfo(p->gstream, &st, nullptr, &cg, nullptr, nullptr, nullptr));
+    BTC_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
+    int r;
+    if ((r = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)b, p->N,
+                      p->n, p->np, m, m, c0, base)) ||
+        (r = factor_impl(p, D, B, m)) || (r = run_solve_tail(p, m)) ||
+        (r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
+                      (const void *)p->d_y, p->N, p->n, p->np, m, m, c0, base, assign)))
+      return r;
+    BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, 3 * sizeof(double), p->stream));
+    if ((r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
+                      (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base,
+                      p->d_norms, one)) ||
+        (r = launch_n((const void *)&k_refine_decide, 1, 1, 0, p->stream, p->d_rb, tol, maxit, one, h)))
+      return r;
+    // the correction loop as a while node
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t ndeps = 0;
+    BTC_CUDA(cudaStreamGetCaptureInfo(p->gstream, &st, nullptr, &cg, &deps, &edata, &ndeps));
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};  // zeroed, no constructor
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    BTC_CUDA(cudaGraphAddNode(&wnode, cg, deps, edata, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    BTC_CUDA(cudaStreamUpdateCaptureDependencies(p->gstream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    BTC_CUDA(cudaStreamBeginCaptureToGraph(p->gstream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    p->stream = p->gstream2;
+    r = run_solve(p, m);
+    if (!r)
+      r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x, (const void *)p->d_y,
+                   p->N, p->n, p->np, m, m, c0, base, accumulate);
+    if (!r && cudaMemsetAsync(p->d_norms, 0, 2 * sizeof(double), p->stream) != cudaSuccess)
+      r = fail(BTC_ERR_CUDA, "graph capture: memset");
+    if (!r)
+      r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y, (const double *)D,
+                   (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base, p->d_norms, zero);
+    if (!r) r = launch_n((const void *)&k_refine_decide, 1, 1, 0, p->stream, p->d_rb, tol, maxit, zero, h);
+    cudaGraph_t body_out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(p->gstream2, &body_out);
+    p->stream = p->gstream;
+    if (r) return r;
+    if (e2 != cudaSuccess) return fail(BTC_ERR_CUDA, "graph capture (loop body): %s", cudaGetErrorString(e2));
+    BTC_CUDA(cudaMemcpyAsync(p->h_rb, p->d_rb, sizeof(Readback), cudaMemcpyDeviceToHost, p->stream));
+    return BTC_OK;
+  };
+  rc = body_cuda();
+  e = cudaStreamEndCapture(p->gstream, &g);
+  p->stream = user;
+  if (rc == BTC_OK && e != cudaSuccess) rc = fail(BTC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  if (rc == BTC_OK && (e = cudaGraphInstantiate(&p->gexec, g, 0)) != cudaSuccess)
+    rc = fail(BTC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  if (g) cudaGraphDestroy(g);
+  if (rc) {
+    p->gexec = nullptr;
+    cudaGetLastError();
+    return rc;
+  }
+  p->gkey = refine_graph_key(p, D, B, b, x, m, tol, maxit);
+  return BTC_OK;
+}
+
+// The graph form applies to one column chunk with the interlaced form, once
+// the persistent configuration is settled, and without per-kernel timing.
+static bool can_graph(const btc_plan_s *p, int m) {
+  return p->graphs && !p->timing && can_interlace(p, m) && (!p->autotune || p->tuned[0]);
+}
+
+// One refined factor + solve through the captured graph (re-captured when a
+// pointer, size or configuration differs). Synchronous.
+static int refine_graph_run(btc_plan_s *p, const void *D, const void *B, const double *b, double *x, int m,
+                            double tol, int maxit, int *iters, double *relres) {
+  if (!p->gexec || p->gkey != refine_graph_key(p, D, B, b, x, m, tol, maxit)) {
+    int rc = build_refine_graph(p, D, B, b, x, m, tol, maxit);
+    if (rc) return rc;
+  }
+  BTC_CUDA(cudaEventRecord(p->gevent, p->stream));
+  BTC_CUDA(cudaStreamWaitEvent(p->gstream, p->gevent, 0));
+  BTC_CUDA(cudaGraphLaunch(p->gexec, p->gstream));
+  BTC_CUDA(cudaStreamSynchronize(p->gstream));
+  p->D = D;
+  p->B = B;
+  p->factored = true;
+  p->anorm_valid = true;
+  int blk, col;
+  int rc = decode_info(p, &blk, &col);
+  if (rc == BTC_ERR_TIMEOUT) return fail(rc, "factorization failed: a bounded device-side wait gave up");
+  if (rc) return fail(rc, "factorization failed: pivot of block %d, column %d not positive", blk, col);
+  if (iters) *iters = p->h_rb->iters;
+  if (relres) *relres = p->h_rb->rel;
+  if (!(p->h_rb->rel <= tol))
+    return fail(BTC_ERR_NOT_CONVERGED, "refinement stopped at relative residual %.3e", p->h_rb->rel);
   return BTC_OK;
 }
 }  // namespace btc
@@ -630,8 +790,8 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   if ((e = cudaMalloc(&p->dpool, dbytes)) != cudaSuccess ||
       (e = cudaMalloc(&p->epool, ebytes)) != cudaSuccess ||
       (e = cudaMalloc(&p->d_y, (size_t)N * np * kMaxCols * ks.elem)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_rb, sizeof(btc_plan_s::Readback))) != cudaSuccess ||
-      (e = cudaMallocHost(&p->h_rb, sizeof(btc_plan_s::Readback))) != cudaSuccess)
+      (e = cudaMalloc(&p->d_rb, sizeof(Readback))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_rb, sizeof(Readback))) != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
                         cudaGetErrorString(e)));
   p->d_norms = p->d_rb->norms;
@@ -640,7 +800,7 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   p->h_norms = p->h_rb->norms;
   p->h_info = &p->h_rb->info;
   p->h_status = &p->h_rb->status;
-  if ((e = cudaMemset(p->d_rb, 0, sizeof(btc_plan_s::Readback))) != cudaSuccess)
+  if ((e = cudaMemset(p->d_rb, 0, sizeof(Readback))) != cudaSuccess)
     return cleanup(fail(BTC_ERR_CUDA, "btc_plan: %s", cudaGetErrorString(e)));
   p->device_bytes = (int64_t)(dbytes + ebytes + (size_t)N * np * kMaxCols * ks.elem);
   // flatten the per-level schedules and upload them
@@ -835,6 +995,13 @@ int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const d
     int rc = btc_factor(p, D, B);
     return rc ? rc : btc_solve_refined(p, b, x, nrhs, tol, maxit, iters, relres);
   }
+  if (!D || (p->N > 1 && !B)) return fail(BTC_ERR_ARG, "btc_factor_solve_refined: NULL argument");
+  if (can_graph(p, nrhs)) {
+    int rc = refine_graph_run(p, D, B, b, x, nrhs, tol, maxit, iters, relres);
+    if (rc != BTC_ERR_CUDA) return rc;
+    p->graphs = false;  // capture or launch refused: continue without graphs for this plan
+    cudaGetLastError();
+  }
   const KernelSet &k = *p->ks;
   int64_t base = 0;
   int c0 = 0, assign = 0;
@@ -1013,6 +1180,16 @@ int btc_plan_tuning(btc_plan_t p, int *resident_cap, int *ctas_per_sm, int *tune
   return BTC_OK;
 }
 
+int btc_plan_set_graphs(btc_plan_t p, int enable) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_graphs: NULL plan");
+  p->graphs = enable != 0;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return BTC_OK;
+}
+
 int btc_plan_set_timing(btc_plan_t p, int enable) {
   if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_timing: NULL plan");
   double ms[BTC_TIMING_CLASSES];
@@ -1050,6 +1227,13 @@ int btc_free(btc_plan_t p) {
       cudaEventDestroy(ev.first);
       cudaEventDestroy(ev.second);
     }
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->gstream) {
+    cudaStreamSynchronize(p->gstream);
+    cudaStreamDestroy(p->gstream);
+    cudaStreamDestroy(p->gstream2);
+    cudaEventDestroy(p->gevent);
+  }
   void *dev[] = {p->dpool,        p->epool,        p->d_fac,    p->d_fwd,  p->d_bwd,     p->d_rb,
                  p->d_y,          p->s_D,          p->d_fac_deps, p->d_solve_flow, p->d_flow, p->s_B,
                  p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail};
