@@ -35,14 +35,21 @@ extern "C" {
 
 typedef struct btc_plan_s *btc_plan_t;
 
-/* Arithmetic of a plan. Input element type: FP64 for BTC_F64 and BTC_MIXED_F32,
- * FP32 for BTC_F32. */
+/* Arithmetic of a plan. Input element type: FP64 for BTC_F64, BTC_MIXED_F32 and
+ * BTC_MIXED_TF32, FP32 for BTC_F32. */
 enum btc_dtype {
-  BTC_F64 = 0,       /* factor and solve in FP64 (the plain FP64 path)                          */
-  BTC_F32 = 1,       /* factor and solve in FP32                                                 */
-  BTC_MIXED_F32 = 2, /* FP64 inputs; factor and correction solves in FP32 except the root
-                        (top-separator) Cholesky, which runs in FP64; FP64 residual and update
-                        in btc_solve_refined                                                     */
+  BTC_F64 = 0,        /* factor and solve in FP64 (the plain FP64 path)                         */
+  BTC_F32 = 1,        /* factor and solve in FP32                                                */
+  BTC_MIXED_F32 = 2,  /* FP64 inputs; factor and correction solves in FP32 except the root
+                         (top-separator) Cholesky, which runs in FP64; FP64 residual and update
+                         in btc_solve_refined                                                    */
+  BTC_MIXED_TF32 = 3, /* as BTC_MIXED_F32, with the four n^3 products of every node (the two
+                         deferred syrk, the immediate syrk and the fill gemm of Alg. 5) on the
+                         tcgen05 tensor cores with TF32 operands and FP32 accumulation, for
+                         padded block size 128 (97 <= n <= 128); smaller blocks run the
+                         BTC_MIXED_F32 kernels. Its factor is less accurate than FP32 (TF32 has
+                         a 10-bit mantissa); the FP64 refinement of btc_solve_refined recovers
+                         the solution's accuracy in a few more steps                            */
 };
 
 enum btc_status {

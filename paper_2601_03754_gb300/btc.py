@@ -14,7 +14,7 @@ import threading
 
 import numpy as np
 
-F64, F32, MIXED_F32 = 0, 1, 2
+F64, F32, MIXED_F32, MIXED_TF32 = 0, 1, 2, 3
 DTYPES = {"f64": F64, "f32": F32, "mixed_f32": MIXED_F32}
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_SPD, ERR_TIMEOUT, ERR_NOT_FACTORED, ERR_UNSUPPORTED, ERR_NOT_CONVERGED = (

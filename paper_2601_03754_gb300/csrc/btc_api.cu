@@ -39,23 +39,26 @@ int fail(int code, const char *fmt, ...) {
 
 // ------------------------------------------------------------ kernel table
 static constexpr int kMaxSets = 12;
-static KernelSet g_sets[3][kMaxSets];
-static int g_nsets[3] = {0, 0, 0};
+static KernelSet g_sets[4][kMaxSets];
+static int g_nsets[4] = {0, 0, 0, 0};
 static std::once_flag g_once;
 
 static void init_tables() {
   std::call_once(g_once, [] {
-    const int code_f64 = BTC_F64, code_f32 = BTC_F32, code_mixed = BTC_MIXED_F32;
+    const int code_f64 = BTC_F64, code_f32 = BTC_F32, code_mixed = BTC_MIXED_F32, code_tf32 = BTC_MIXED_TF32;
 #define BTC_ADD_SET(dt, np) g_sets[code_##dt][g_nsets[code_##dt]++] = make_set_##dt##_##np();
     BTC_FOR_EACH_SET(BTC_ADD_SET)
 #undef BTC_ADD_SET
+    // below the tensor-core block size the TF32 dtype runs the mixed FP32 sets
+    for (int i = 0; i < g_nsets[code_mixed]; ++i)
+      if (g_sets[code_mixed][i].np < 128) g_sets[code_tf32][g_nsets[code_tf32]++] = g_sets[code_mixed][i];
   });
 }
 
 const KernelSet &kernels_for(int dtype, int np) {
   static KernelSet none;
   init_tables();
-  if (dtype < 0 || dtype > 2) return none;
+  if (dtype < 0 || dtype > 3) return none;
   for (int i = 0; i < g_nsets[dtype]; ++i)
     if (g_sets[dtype][i].np == np) return g_sets[dtype][i];
   return none;
@@ -103,7 +106,10 @@ __global__ void k_refine_decide(Readback *rb, double tol, int maxit, int first, 
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
-bool dtype_ok(int dtype) { return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32; }
+bool dtype_ok(int dtype) {
+  return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32 || dtype == BTC_MIXED_TF32;
+}
+bool dtype_mixed(int dtype) { return dtype == BTC_MIXED_F32 || dtype == BTC_MIXED_TF32; }
 
 }  // namespace btc
 
@@ -363,13 +369,14 @@ static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
 static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
   const KernelSet &k = *p->ks;
   const FlowVariant &fv = k.flow_v[p->flow_var];
-  const bool mixed_root = p->dtype == BTC_MIXED_F32;
+  const bool mixed_root = dtype_mixed(p->dtype);
   const int last = p->hp.levels - 1;
   const int nflow = mixed_root ? (int)p->fac_off[last] : p->n_fac;
   FactorArgs a;
   a.dpool = p->dpool;
   a.epool = p->epool;
   a.info = p->d_info;
+  a.status = p->d_status;
   a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
   a.items = p->d_fac;
   a.count = nflow;
@@ -411,9 +418,10 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   a.dpool = p->dpool;
   a.epool = p->epool;
   a.info = p->d_info;
+  a.status = p->d_status;
   a.inst = nullptr;
   InstDesc d{D, B, p->N, p->n};
-  const bool mixed_root = p->dtype == BTC_MIXED_F32;
+  const bool mixed_root = dtype_mixed(p->dtype);
   const int last = p->hp.levels - 1;
   if (p->sched == BTC_SCHED_FLOW) {
     if (!rl && m_inter > 0 && p->n_inter > 0) {
@@ -834,7 +842,7 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   p->n_solve = (int)p->hp.solve_flow.size();
   std::vector<int32_t> icode, ideps;
   std::vector<SolveFlowItem> tail;
-  build_interlaced(p->hp, dtype == BTC_MIXED_F32, &icode, &ideps, &tail);
+  build_interlaced(p->hp, dtype_mixed(dtype), &icode, &ideps, &tail);
   p->n_inter = (int)icode.size();
   p->n_tail = (int)tail.size();
   if ((e = cudaMalloc(&p->d_inter_code, std::max<size_t>(icode.size(), 1) * sizeof(int32_t))) != cudaSuccess ||

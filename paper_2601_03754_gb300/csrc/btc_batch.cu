@@ -215,7 +215,7 @@ static int upload(V **dst, const std::vector<V> &src, int64_t *acc) {
 
 // Build the merged schedules of one group.
 static int build_group(btc_batch_s *bt, BatchGroup &g) {
-  const bool mixed = bt->dtype == BTC_MIXED_F32;
+  const bool mixed = dtype_mixed(bt->dtype);
   const KernelSet &ks = *g.ks;
   const int64_t bs = (int64_t)g.np * g.np;
   int64_t d_base = 0, e_base = 0, y_base = 0;
@@ -456,6 +456,7 @@ int btc_batch_factor(btc_batch_t bt, const void *const *D, const void *const *B)
     a.epool = g.epool;
     a.inst = bt->d_inst;
     a.info = bt->d_info;
+    a.status = g.d_flow + 2;
     InstDesc none{nullptr, nullptr, 0, 0};
     BTC_CUDA(cudaMemsetAsync(g.d_flow, 0, 3 * sizeof(int), bt->stream));
     if (g.n_fac > 0) {

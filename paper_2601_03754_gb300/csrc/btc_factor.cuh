@@ -32,6 +32,7 @@ struct FactorArgs {
   void *epool;
   const InstDesc *inst;      // per-instance descriptors (batched); NULL: use the by-value one
   unsigned long long *info;  // one word per instance
+  int *status = nullptr;     // launch status word (a bounded wait that gives up sets kFlowTimeout)
 };
 
 template <typename T, int NP, int R>

@@ -39,6 +39,7 @@ struct KernelSet {
   // fac_flow, fac_fwd_flow and fac_flow_rl above are those of flow_v[flow_default]
   FlowVariant flow_v[kFlowVariants];
   int n_flow_v = 0, flow_default = 0;
+  bool tensor_cores = false;  // level elimination products on tcgen05 (TF32)
   // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, FP64 root
   const void *pack_matrix = nullptr, *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
   // solve
@@ -54,11 +55,14 @@ const KernelSet &kernels_for(int dtype, int np);
 
 // Every compiled (dtype, padded block size) pair; each has its own translation
 // unit btc_set_<dtype>_<np>.cu so that the build compiles them in parallel.
-// FP64 stops at 96 (three 128 x 128 FP64 blocks exceed one SM's shared memory).
+// FP64 stops at 96 (three 128 x 128 FP64 blocks exceed one SM's shared memory);
+// the TF32 tensor-core dtype has its own set at 128 and shares the mixed FP32
+// sets below it.
 #define BTC_FOR_EACH_SET(X)                                                                              \
   X(f64, 8) X(f64, 16) X(f64, 32) X(f64, 48) X(f64, 64) X(f64, 96)                                        \
   X(f32, 8) X(f32, 16) X(f32, 32) X(f32, 48) X(f32, 64) X(f32, 96) X(f32, 128)                            \
-  X(mixed, 8) X(mixed, 16) X(mixed, 32) X(mixed, 48) X(mixed, 64) X(mixed, 96) X(mixed, 128)
+  X(mixed, 8) X(mixed, 16) X(mixed, 32) X(mixed, 48) X(mixed, 64) X(mixed, 96) X(mixed, 128)                \
+  X(tf32, 128)
 #define BTC_DECLARE_SET(dt, np) KernelSet make_set_##dt##_##np();
 BTC_FOR_EACH_SET(BTC_DECLARE_SET)
 #undef BTC_DECLARE_SET

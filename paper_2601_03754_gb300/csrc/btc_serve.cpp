@@ -27,6 +27,7 @@
 
 namespace btc {
 int fail(int code, const char *fmt, ...);
+bool dtype_mixed(int dtype);
 }
 
 namespace {
@@ -231,8 +232,8 @@ extern "C" {
 int btc_server_start(btc_server_t *out, int dtype, int slots, int64_t hbm_budget_bytes, int cache_factors) {
   if (!out || slots < 1 || slots > 64 || hbm_budget_bytes <= 0)
     return btc::fail(BTC_ERR_ARG, "btc_server_start: invalid arguments");
-  if (dtype != BTC_F64 && dtype != BTC_MIXED_F32)
-    return btc::fail(BTC_ERR_ARG, "btc_server_start: dtype must be BTC_F64 or BTC_MIXED_F32");
+  if (dtype != BTC_F64 && !btc::dtype_mixed(dtype))
+    return btc::fail(BTC_ERR_ARG, "btc_server_start: dtype must be BTC_F64, BTC_MIXED_F32 or BTC_MIXED_TF32");
   btc_server_s *s = new btc_server_s();
   s->dtype = dtype;
   s->slots = slots;

@@ -1,0 +1,417 @@
+// Tensor-core (tcgen05, TF32) form of the level elimination for 128 x 128
+// blocks: the four n^3 products of a node (Alg. 5: the two deferred syrk, the
+// immediate syrk onto the next diagonal block and the fill gemm) run as
+// tcgen05.mma with operands in shared memory and FP32 accumulators in TMEM;
+// the Cholesky and the two triangular solves stay on the FP32 FMA pipes
+// (btc_tile.cuh). The accuracy lost to TF32 operands is won back by the FP64
+// refinement of the mixed-precision solve.
+//
+// Operand layout (tcgen05 shared-memory descriptor, no swizzle, K-major): an
+// M x K operand is stored as 8-row x 16-byte core matrices; element (m, k) at
+// byte (m/8)*SBO + (k/4)*LBO + (m%8)*16 + (k%4)*4 with LBO = 128 (core
+// matrices adjacent along K) and SBO = 32 K (adjacent 8-row groups). A product
+// C[i][j] = sum_k X[k][i] Y[k][j] takes A(m=i, k) = X[k][i] and B(n=j, k) =
+// Y[k][j], i.e. both pool blocks in the same "transposed" operand layout.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "btc_factor.cuh"
+#include "btc_solve.cuh"
+#include "btc_tile.cuh"
+
+namespace btc {
+
+constexpr int kTcNP = 128;               // block size of the tensor-core path
+constexpr int kTcCols = 256;             // TMEM columns per CTA: two 128-column FP32 accumulators
+constexpr long long kTcMaxPolls = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (m, k) of a K-major operand with K = 128 (4-byte elements)
+__device__ __forceinline__ uint32_t op_off(int m, int k) {
+  return (uint32_t)((m >> 3) * (kTcNP * 32) + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t op_desc(uint32_t saddr) {
+  constexpr uint32_t lbo = 128, sbo = kTcNP * 32;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// D (TMEM, 128 lanes x 128 columns at tmem) (+)= A^T-form product over K = 128:
+// 16 MMAs of K = 8. Issued by one thread.
+__device__ __forceinline__ void tc_product(uint32_t tmem, const void *opA, const void *opB, bool accumulate) {
+  const uint32_t a0 = smem_addr(opA), b0 = smem_addr(opB);
+#pragma unroll
+  for (int kk = 0; kk < kTcNP / 8; ++kk) {
+    const uint64_t ad = op_desc(a0 + kk * 256), bd = op_desc(b0 + kk * 256);
+    const uint32_t acc = (accumulate || kk > 0) ? 1u : 0u;
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar)));
+}
+
+// Bounded wait for the MMAs of the given phase parity; false after kTcMaxPolls.
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long polls = 0; !done && polls < kTcMaxPolls; ++polls) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return done != 0;
+}
+
+// Make the CTA's shared-memory stores visible to the tensor core, then barrier.
+__device__ __forceinline__ void tc_publish_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+#define BTC_TMEM_LD32(r, taddr)                                                                                 \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                       \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),       \
+                 "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),      \
+                 "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),      \
+                 "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                          \
+               : "r"(taddr))
+
+// Accumulator rows of this thread: warp w reads TMEM lanes 32 (w % 4) .. + 31
+// (row i = 32 (w % 4) + lane) and the column half 64 (w / 4) .. + 63 (8 warps).
+// f(i, j0, v[32]) receives 32 consecutive columns j0 .. j0+31 of row i.
+template <class F>
+__device__ __forceinline__ void tc_read_rows(uint32_t tmem_acc, F &&f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, h = warp >> 2;
+  const int i = 32 * q + lane;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int j0 = 64 * h + 32 * c;
+    uint32_t r[32];
+    BTC_TMEM_LD32(r, tmem_acc + ((uint32_t)(32 * q) << 16) + (uint32_t)j0);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    float v[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+    f(i, j0, v);
+  }
+}
+
+// Pool block (row-major 128 x 128 FP32, X[k][m]) -> K-major TF32 operand
+// (A(m, k) = X[k][m]). Each warp writes whole 128-byte core matrices: lane ->
+// (m = m0 + lane/4, k = k0 + lane%4).
+template <int NT>
+__device__ __forceinline__ void stage_operand_from_pool(unsigned char *op, const float *g) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = NT / 32, NCM = (kTcNP / 8) * (kTcNP / 4);  // 512 core matrices
+  const int dm = lane >> 2, dk = lane & 3;
+#pragma unroll 4
+  for (int cm = warp; cm < NCM; cm += NW) {
+    const int m0 = (cm / (kTcNP / 4)) * 8, k0 = (cm % (kTcNP / 4)) * 4;
+    const float x = __ldcg(g + (size_t)(k0 + dk) * kTcNP + m0 + dm);
+    *reinterpret_cast<uint32_t *>(op + op_off(m0 + dm, k0 + dk)) = to_tf32(x);
+  }
+}
+
+// Padded row-major shared block (X[k][m], leading dimension LD) -> K-major TF32
+// operand in the same buffer: every thread first reads its 64 elements, then
+// all write after a barrier.
+template <int NT, int LD>
+__device__ __forceinline__ void convert_operand_in_place(float *buf) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = NT / 32, NCM = (kTcNP / 8) * (kTcNP / 4);
+  constexpr int PER = NCM / NW;  // core matrices per warp
+  const int dm = lane >> 2, dk = lane & 3;
+  uint32_t v[PER];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int cm = warp + t * NW;
+    const int m0 = (cm / (kTcNP / 4)) * 8, k0 = (cm % (kTcNP / 4)) * 4;
+    v[t] = to_tf32(buf[(k0 + dk) * LD + m0 + dm]);
+  }
+  __syncthreads();
+  unsigned char *op = reinterpret_cast<unsigned char *>(buf);
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int cm = warp + t * NW;
+    const int m0 = (cm / (kTcNP / 4)) * 8, k0 = (cm % (kTcNP / 4)) * 4;
+    *reinterpret_cast<uint32_t *>(op + op_off(m0 + dm, k0 + dk)) = v[t];
+  }
+}
+
+// Per-CTA tensor-core state of the node kernel: TMEM base (two accumulators at
+// columns 0 and 128), the MMA completion barrier and its phase.
+struct TcState {
+  uint32_t tmem;
+  uint64_t *mbar;
+  uint32_t phase;
+  int *status;  // set to kFlowTimeout when an MMA wait gives up
+};
+
+// Allocation by warp 0 (all lanes), barrier init by thread 0; call with all threads.
+__device__ __forceinline__ void tc_begin(TcState &st, uint32_t *tmem_slot, uint64_t *mbar, int *status) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  st.tmem = *tmem_slot;
+  st.mbar = mbar;
+  st.phase = 0;
+  st.status = status;
+}
+
+__device__ __forceinline__ void tc_end(TcState &st) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(kTcCols));
+}
+
+// Wait for the MMAs committed in the current phase; records a timeout.
+__device__ __forceinline__ void tc_sync(TcState &st) {
+  const bool ok = tc_wait(st.mbar, st.phase);
+  st.phase ^= 1u;
+  if (!ok && threadIdx.x == 0 && st.status) atomicExch(st.status, kFlowTimeout);
+}
+
+// One node of Alg. 5 with block size 128 (T = P = float, S = caller's type).
+// Same inputs, outputs and pool conventions as factor_node (btc_factor.cuh).
+template <typename S, bool FIRST>
+__device__ __forceinline__ void factor_node_tc(const FactorItem &it, const FactorArgs &args, const InstDesc &single,
+                                               unsigned char *smem_raw, TcState &st) {
+  using C = TileCfg<float, kTcNP, 8>;
+  constexpr int NT = C::NT, LD = C::LD;
+  float *sS = reinterpret_cast<float *>(smem_raw);  // S_e -> U_e (row-major, padded)
+  float *sA = sS + C::BLK;                          // P_a operand, then S(e,e-s) -> U(e,e-s) -> operand
+  float *sB = sA + C::BLK;                          // P_b operand, then S(e,e+s) -> U(e,e+s) -> operand
+  float *dinv = sB + C::BLK;
+  float *dpool = reinterpret_cast<float *>(args.dpool);
+  float *epool = reinterpret_cast<float *>(args.epool);
+  const int tid = threadIdx.x;
+  const int r0 = (tid / C::TXN) * C::R, c0 = (tid % C::TXN) * C::R;
+  unsigned long long *info = args.info + it.inst;
+  const InstDesc ins = args.inst ? args.inst[it.inst] : single;
+  const int e = it.node;
+  const S *uD = reinterpret_cast<const S *>(ins.D);
+  const S *uB = reinterpret_cast<const S *>(ins.B);
+  const size_t ubs = (size_t)ins.n * ins.n;
+  const bool has_up = it.r_up >= 0, has_dn = it.r_down >= 0, has_next = it.d_next >= 0;
+  const uint32_t acc_fill = st.tmem, acc_next = st.tmem + 128;
+  bool next_started = false;  // acc_next holds P_b^T P_b
+
+  if constexpr (FIRST) {
+    user_to_smem<C>(sS, uD + e * ubs, ins.n, true, 1.0f);                      // S[i][j] = D_e[j][i]
+    if (has_up) user_to_smem<C>(sA, uB + (e - 1) * ubs, ins.n, false, 0.0f);  // S(e, e-1) = B_{e-1}
+    if (has_dn) user_to_smem<C>(sB, uB + e * ubs, ins.n, true, 0.0f);         // S(e, e+1) = B_e^T
+    __syncthreads();
+  } else {
+    const bool pa = it.p_a >= 0, pb = it.p_b >= 0 && has_next;
+    block_to_smem_async<C>(sS, dpool + it.d_self);
+    if (pa) stage_operand_from_pool<NT>(reinterpret_cast<unsigned char *>(sA), epool + it.p_a);
+    if (pb) stage_operand_from_pool<NT>(reinterpret_cast<unsigned char *>(sB), epool + it.p_b);
+    cp_async_commit_wait_all();
+    tc_publish_smem();
+    if (pa || pb) {
+      if (tid == 0) {
+        if (pa) tc_product(acc_fill, sA, sA, false);  // P_a^T P_a
+        if (pb) tc_product(acc_next, sB, sB, false);  // P_b^T P_b, kept for S_{e+s}
+        tc_commit(st.mbar);
+      }
+      tc_sync(st);
+      next_started = pb;
+      if (pa)  // S_e -= P_a^T P_a (rows of this thread, 64 columns)
+        tc_read_rows(acc_fill, [&](int i, int j0, const float (&v)[32]) {
+#pragma unroll
+          for (int t = 0; t < 32; t += 4) {
+            float4 s = *reinterpret_cast<float4 *>(sS + i * LD + j0 + t);
+            s.x -= v[t];
+            s.y -= v[t + 1];
+            s.z -= v[t + 2];
+            s.w -= v[t + 3];
+            *reinterpret_cast<float4 *>(sS + i * LD + j0 + t) = s;
+          }
+        });
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+    // the off-diagonal operands arrive while the Cholesky runs
+    if (has_up) block_to_smem_async<C>(sA, epool + it.r_up);
+    if (has_dn) block_to_smem_async<C>(sB, epool + it.r_down);
+  }
+
+  // ---- potrf, then the two trsm (FP32 FMA)
+  block_potrf_upper<C>(sS, dinv, info, e, r0, c0);
+  smem_to_block<C>(dpool + it.d_self, sS, true);
+  if constexpr (!FIRST) cp_async_commit_wait_all();
+  __syncthreads();
+  block_trsm_ut<C>(has_up ? sA : nullptr, has_dn ? sB : nullptr, sS, dinv, r0, c0);
+  if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
+  if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
+
+  // ---- S_{e+s} -= U_dn^T U_dn and the fill, on the tensor cores
+  const bool fill = it.fill >= 0;
+  if (!(has_next || fill)) return;
+  __syncthreads();
+  if (has_dn) convert_operand_in_place<NT, LD>(sB);
+  if (fill) convert_operand_in_place<NT, LD>(sA);
+  tc_publish_smem();
+  if (tid == 0) {
+    if (has_next) tc_product(acc_next, sB, sB, next_started);
+    if (fill) {
+      if (it.flags & FI_FILL_UPFIRST) tc_product(acc_fill, sA, sB, false);  // S'(e-s, e+s) = -U_up^T U_dn
+      else tc_product(acc_fill, sB, sA, false);                             // S'(e+s, e-s) = -U_dn^T U_up
+    }
+    tc_commit(st.mbar);
+  }
+  tc_sync(st);
+  if (has_next) {
+    float *g = dpool + it.d_next;
+    tc_read_rows(acc_next, [&](int i, int j0, const float (&v)[32]) {
+#pragma unroll
+      for (int t = 0; t < 32; t += 4) {
+        const int j = j0 + t;
+        float4 s;
+        if constexpr (FIRST) {  // S_{e+1} = D_{e+1} (upper form of the caller's lower triangle), padded
+          const S *Dn = uD + (e + 1) * ubs;
+          float w[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int jj = j + u;
+            w[u] = (i < ins.n && jj < ins.n) ? convert_in<float, S>(i <= jj ? Dn[(size_t)jj * ins.n + i]
+                                                                           : Dn[(size_t)i * ins.n + jj])
+                                             : (i == jj ? 1.0f : 0.0f);
+          }
+          s = make_float4(w[0], w[1], w[2], w[3]);
+        } else {
+          s = __ldcg(reinterpret_cast<const float4 *>(g + (size_t)i * kTcNP + j));
+        }
+        s.x -= v[t];
+        s.y -= v[t + 1];
+        s.z -= v[t + 2];
+        s.w -= v[t + 3];
+        *reinterpret_cast<float4 *>(g + (size_t)i * kTcNP + j) = s;
+      }
+    });
+  }
+  if (fill) {
+    float *g = epool + it.fill;
+    tc_read_rows(acc_fill, [&](int i, int j0, const float (&v)[32]) {
+#pragma unroll
+      for (int t = 0; t < 32; t += 4)
+        *reinterpret_cast<float4 *>(g + (size_t)i * kTcNP + j0 + t) =
+            make_float4(-v[t], -v[t + 1], -v[t + 2], -v[t + 3]);
+    });
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- kernels
+// The tensor-core counterparts of k_factor_level, k_factor_flow and
+// k_factor_fwd_flow (same arguments and schedules); each CTA holds its TMEM
+// accumulators for its whole lifetime (one CTA per SM: the three 128 x 128
+// FP32 shared blocks take 198 KB).
+constexpr int kTcThreads = TileCfg<float, kTcNP, 8>::NT;
+
+template <typename S, bool FIRST>
+__global__ void __launch_bounds__(kTcThreads, 1) k_factor_level_tc(FactorArgs args, InstDesc single) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  TcState st;
+  tc_begin(st, &s_tmem, &s_mbar, args.status);
+  const FactorItem it = args.items[blockIdx.x];
+  factor_node_tc<S, FIRST>(it, args, single, smem_raw, st);
+  tc_end(st);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_factor_flow_tc(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_slot, s_ok;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  TcState st;
+  tc_begin(st, &s_tmem, &s_mbar, fs.status);
+  for (;;) {
+    const int t = flow_claim(fs, args.count, &s_slot);
+    if (t < 0) break;
+    const FactorItem it = args.items[t];
+    flow_trace(fs, t, 0);
+    if (flow_wait(fs, deps + 3 * t, 3, &s_ok)) {
+      flow_trace(fs, t, 1);
+      if (t < nfirst) factor_node_tc<S, true>(it, args, single, smem_raw, st);
+      else factor_node_tc<S, false>(it, args, single, smem_raw, st);
+    }
+    __syncthreads();
+    flow_trace(fs, t, 2);
+    flow_publish(fs, t);
+  }
+  tc_end(st);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_factor_fwd_flow_tc(FactorArgs fa, InstDesc single, SolveArgs sa, const int32_t *code, const int32_t *deps,
+                         int nfirst, int count, FlowSync fs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_slot, s_ok;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  TcState st;
+  tc_begin(st, &s_tmem, &s_mbar, fs.status);
+  const SolveFlowItem *fwd = reinterpret_cast<const SolveFlowItem *>(sa.items);
+  for (;;) {
+    const int t = flow_claim(fs, count, &s_slot);
+    if (t < 0) break;
+    const int c = code[t];
+    flow_trace(fs, t, 0);
+    if (flow_wait(fs, deps + (size_t)kInterDeps * t, kInterDeps, &s_ok)) {
+      flow_trace(fs, t, 1);
+      if (c >= 0) {
+        const FactorItem it = fa.items[c];
+        if (c < nfirst) factor_node_tc<S, true>(it, fa, single, smem_raw, st);
+        else factor_node_tc<S, false>(it, fa, single, smem_raw, st);
+      } else {
+        const SolveFlowItem it = fwd[-1 - c];
+        fwd_node<float, kTcNP>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, sa, smem_raw);
+      }
+    }
+    __syncthreads();
+    flow_trace(fs, t, 2);
+    flow_publish(fs, t);
+  }
+  tc_end(st);
+}
+
+}  // namespace btc
