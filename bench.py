@@ -189,13 +189,17 @@ def run_profile(which):
     btc.load()
     W = WORKLOAD
     N, n, m = W["N"], W["n"], W["nrhs"]
+    if which == "tf32":  # the tensor-core path on a smaller large-block case (inputs 134 MB > L2)
+        N, n = 512, 128
     D, B = gen.bt_random(N, n, delta=W["delta"], seed=W["seed"])
     b = gen.rhs(N, n, m, seed=W["seed"])
     Dd, Bd, bd = (torch.from_numpy(a).cuda() for a in (D, B, b))
     xd = torch.zeros_like(bd)
-    dts = {"mixed": [btc.MIXED_F32], "f64": [btc.F64], "both": [btc.MIXED_F32, btc.F64]}[which]
+    dts = {"mixed": [btc.MIXED_F32], "f64": [btc.F64], "both": [btc.MIXED_F32, btc.F64],
+           "tf32": [btc.MIXED_TF32]}[which]
     for dt in dts:
         p = btc.btc_plan(N, n, dt)
+        btc.btc_plan_set_graphs(p, False)  # ncu does not profile kernels inside graphs with conditional nodes
         for _ in range(2):
             it, rel, rc = btc.btc_factor_solve_refined(p, Dd, Bd, bd, xd, m, tol=TOL, maxit=30)
         print(f"profile dtype={dt} iters={it} relres={rel:.3e}")
@@ -251,35 +255,51 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
 
 
 def large_block_measure(btc, gen, torch, stream, flush, steps=5):
-    """Config: N=4096, n=128 (delta in {1, 1e-3, 1e-6}): FP32 factor on CUDA cores + FP64 root,
-    residual and refinement to 1e-10; error against the FP64 solution reported per delta."""
-    out = {"N": 4096, "n": 128, "form": "mixed_f32 (FFMA register tiles)"}
+    """Config: N=4096, n=128, delta in {1, 1e-3, 1e-6}: the FP32 factor on CUDA cores (BTC_MIXED_F32)
+    and with the level-elimination products on tcgen05 tensor cores (BTC_MIXED_TF32), both with the FP64
+    root, residual and refinement to 1e-10 (the relative residual reached is the stated error)."""
+    out = {"N": 4096, "n": 128}
+    forms = (("mixed_f32_ffma", btc.MIXED_F32), ("mixed_tf32_tcgen05", btc.MIXED_TF32))
     for delta in (1.0, 1e-3, 1e-6):
         D, B = gen.bt_random_torch(4096, 128, delta=delta, seed=7)
         g = torch.Generator(device="cuda")
         g.manual_seed(11)
         b = torch.randn((4096 * 128, 1), generator=g, device="cuda", dtype=torch.float64)
         x = torch.zeros_like(b)
-        p = btc.btc_plan(4096, 128, btc.MIXED_F32, stream)
-        info = btc.btc_plan_query(p)
-        ts, tf = [], []
-        with torch.cuda.stream(stream):
-            for rep in range(steps + 1):
-                flush.fill_(1.0)
-                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-                e0.record(stream)
+        res = {}
+        for name, dt in forms:
+            p = btc.btc_plan(4096, 128, dt, stream)
+            info = btc.btc_plan_query(p)
+            ts, tf = [], []
+            with torch.cuda.stream(stream):
+                for rep in range(steps + 2):
+                    flush.fill_(1.0)
+                    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                    e0.record(stream)
+                    btc.btc_factor(p, D, B)
+                    e1.record(stream)
+                    e1.synchronize()
+                    flush.fill_(1.0)
+                    e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                    e2.record(stream)
+                    it, rel, rc = btc.btc_factor_solve_refined(p, D, B, b, x, 1, tol=TOL, maxit=60,
+                                                               allow_not_converged=True)
+                    e3.record(stream)
+                    e3.synchronize()
+                    if rep >= 2:
+                        tf.append(e0.elapsed_time(e1))
+                        ts.append(e2.elapsed_time(e3))
+            btc.btc_plan_set_timing(p, True)
+            with torch.cuda.stream(stream):
                 btc.btc_factor(p, D, B)
-                e1.record(stream)
-                it, rel, rc = btc.btc_solve_refined(p, b, x, 1, tol=TOL, maxit=40)
-                e2.record(stream)
-                e2.synchronize()
-                if rep:
-                    ts.append(e0.elapsed_time(e2))
-                    tf.append(e0.elapsed_time(e1))
-        out[str(delta)] = {"ms_factor_solve": statistics.mean(ts), "ms_factor": statistics.mean(tf),
-                           "factor_tflops": info["factor_flops"] / (statistics.mean(tf) * 1e-3) / 1e12,
-                           "refine_iters": it, "relres": rel}
-        p.free()
+            k_ms, k_n = btc.btc_plan_timing(p)
+            btc.btc_plan_set_timing(p, False)
+            res[name] = {"ms_factor_solve_refined": statistics.mean(ts), "ms_factor": statistics.mean(tf),
+                         "factor_tflops": info["factor_flops"] / (statistics.mean(tf) * 1e-3) / 1e12,
+                         "ms_factor_kernel": k_ms[btc.TIME_FACTOR], "ms_root_fp64": k_ms[btc.TIME_ROOT],
+                         "refine_iters": it, "relres": rel, "converged": rc == btc.OK}
+            p.free()
+        out[str(delta)] = res
         del D, B
     return out
 
@@ -319,7 +339,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the N=4096, n=128 measurement")
-    ap.add_argument("--profile", choices=["mixed", "f64", "both"], default=None,
+    ap.add_argument("--profile", choices=["mixed", "f64", "both", "tf32"], default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
     if args.profile:
