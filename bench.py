@@ -200,6 +200,7 @@ def run_profile(which):
     for dt in dts:
         p = btc.btc_plan(N, n, dt)
         btc.btc_plan_set_graphs(p, False)  # ncu does not profile kernels inside graphs with conditional nodes
+        btc.btc_plan_set_autotune(p, False)  # the default configuration, without the tuner's timing runs
         for _ in range(2):
             it, rel, rc = btc.btc_factor_solve_refined(p, Dd, Bd, bd, xd, m, tol=TOL, maxit=30)
         print(f"profile dtype={dt} iters={it} relres={rel:.3e}")
