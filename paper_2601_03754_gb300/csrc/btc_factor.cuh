@@ -137,12 +137,9 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
     }
   }
 
-  // ---- potrf, then the two trsm of the same node
-  block_potrf_upper<C>(sS, dinv, info, e, r0, c0);
+  // ---- potrf with the two trsm of the same node, pipelined by panels
+  block_potrf_trsm<C>(sS, dinv, has_up ? sA : nullptr, has_dn ? sB : nullptr, info, e, !FIRST && ASYNC);
   smem_to_block<C>(dpool + it.d_self, sS, true);
-  if constexpr (!FIRST && ASYNC) cp_async_commit_wait_all();
-  if constexpr (!FIRST) __syncthreads();
-  block_trsm_ut<C>(has_up ? sA : nullptr, has_dn ? sB : nullptr, sS, dinv, r0, c0);
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
 

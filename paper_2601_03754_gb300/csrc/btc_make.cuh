@@ -4,7 +4,6 @@
 #include "btc_fused.cuh"
 #include "btc_kernels.h"
 #include "btc_solve.cuh"
-#include "btc_tc.cuh"
 
 namespace btc {
 
@@ -77,26 +76,6 @@ KernelSet make_set() {
   k.pack = (const void *)&k_pack_rhs<T, S>;
   k.unpack = (const void *)&k_unpack<T, S>;
   k.resid = (const void *)&k_residual<T>;
-  return k;
-}
-
-// Mixed TF32 set for block size 128: the mixed FP32 set with the level
-// elimination (per-level, persistent and interlaced forms) replaced by its
-// tcgen05 form; the right-looking variant keeps the FP32 FMA kernels.
-inline KernelSet make_set_tc128() {
-  KernelSet k = make_set<float, double, kTcNP, true>();
-  k.fac_first = (const void *)&k_factor_level_tc<double, true>;
-  k.fac_rest = (const void *)&k_factor_level_tc<double, false>;
-  k.n_flow_v = 1;
-  k.flow_default = 0;
-  FlowVariant &v = k.flow_v[0];
-  v.minb = 1;
-  v.fac = (const void *)&k_factor_flow_tc<double>;
-  v.fac_fwd = (const void *)&k_factor_fwd_flow_tc<double>;
-  k.fac_flow = v.fac;
-  k.fac_fwd_flow = v.fac_fwd;
-  k.fac_flow_rl = v.fac_rl;
-  k.tensor_cores = true;
   return k;
 }
 

@@ -2,7 +2,27 @@
 // tcgen05 (TF32), FP32 correction solves, FP64 top-separator Cholesky; padded
 // block size 128.
 #include "btc_make.cuh"
+#include "btc_tc.cuh"
 
 namespace btc {
-KernelSet make_set_tf32_128() { return make_set_tc128(); }
+// Mixed TF32 set for block size 128: the mixed FP32 set with the level
+// elimination (per-level, persistent and interlaced forms) replaced by its
+// tcgen05 form; the right-looking variant keeps the FP32 FMA kernels.
+KernelSet make_set_tf32_128() {
+  KernelSet k = make_set<float, double, kTcNP, true>();
+  k.fac_first = (const void *)&k_factor_level_tc<double, true>;
+  k.fac_rest = (const void *)&k_factor_level_tc<double, false>;
+  k.n_flow_v = 1;
+  k.flow_default = 0;
+  FlowVariant &v = k.flow_v[0];
+  v.minb = 1;
+  v.fac = (const void *)&k_factor_flow_tc<double>;
+  v.fac_fwd = (const void *)&k_factor_fwd_flow_tc<double>;
+  k.fac_flow = v.fac;
+  k.fac_fwd_flow = v.fac_fwd;
+  k.fac_flow_rl = v.fac_rl;
+  k.tensor_cores = true;
+  return k;
+}
+
 }  // namespace btc

@@ -218,7 +218,6 @@ __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const Facto
   float *dpool = reinterpret_cast<float *>(args.dpool);
   float *epool = reinterpret_cast<float *>(args.epool);
   const int tid = threadIdx.x;
-  const int r0 = (tid / C::TXN) * C::R, c0 = (tid % C::TXN) * C::R;
   unsigned long long *info = args.info + it.inst;
   const InstDesc ins = args.inst ? args.inst[it.inst] : single;
   const int e = it.node;
@@ -269,12 +268,9 @@ __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const Facto
     if (has_dn) block_to_smem_async<C>(sB, epool + it.r_down);
   }
 
-  // ---- potrf, then the two trsm (FP32 FMA)
-  block_potrf_upper<C>(sS, dinv, info, e, r0, c0);
+  // ---- potrf with the two trsm, pipelined by panels (FP32 FMA)
+  block_potrf_trsm<C>(sS, dinv, has_up ? sA : nullptr, has_dn ? sB : nullptr, info, e, !FIRST);
   smem_to_block<C>(dpool + it.d_self, sS, true);
-  if constexpr (!FIRST) cp_async_commit_wait_all();
-  __syncthreads();
-  block_trsm_ut<C>(has_up ? sA : nullptr, has_dn ? sB : nullptr, sS, dinv, r0, c0);
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
 

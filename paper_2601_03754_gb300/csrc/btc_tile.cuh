@@ -598,6 +598,86 @@ __device__ __forceinline__ void block_potrf_upper(T *S, T *dinv, unsigned long l
   }
 }
 
+// Blocked upper Cholesky S = U^T U fused with Z <- U^{-T} Z for up to two
+// right-hand-side blocks (either may be null), pipelined by panels: while
+// warp 0 factors panel p, the other warps apply panel p-1 to the rows of S
+// below panel p and Z_{p-1} to the rows of Z from p on; then all threads solve
+// panel p of Z (column substitution) and update the next panel's rows of S
+// with panel p. Every element receives the same updates in the same order as
+// block_potrf_upper followed by block_trsm_ut, so the results are identical;
+// the pipelining only overlaps the single-warp panel factorization with the
+// trailing updates. wait_operands: Z0/Z1 arrive by cp.async issued before the
+// call (waited for after the first panel).
+template <class C, typename T>
+__device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, unsigned long long *info, int node,
+                                                 bool wait_operands) {
+  constexpr int PB = C::PB, NP = C::NP, R = C::R, TXN = C::TXN, NT = C::NT;
+  const int tid = threadIdx.x;
+  const bool solve = Z0 || Z1;
+#pragma unroll 1
+  for (int p = 0; p < C::NPAN; ++p) {
+    const int p0 = p * PB;
+    if (tid < 32) {
+      warp_panel_potrf<C>(S, p0, dinv, info, node);
+    } else if (p > 0) {
+      const int q0 = p0 - PB;                     // panel p-1
+      const int tb = (NP - p0 - PB) / R;          // tile rows of S below panel p
+      const int nb = tb * (tb + 1) / 2;           // their upper tiles
+      const int zr = (NP - p0) / R;               // tile rows of Z from p0 on
+      const int nz = solve ? 2 * zr * TXN : 0;
+      for (int u = tid - 32; u < nb + nz; u += NT - 32) {
+        if (u < nb) {
+          int tr = 0, rem = u;
+          while (rem >= tb - tr) {
+            rem -= tb - tr;
+            ++tr;
+          }
+          const int r0 = p0 + PB + tr * R, c0 = r0 + rem * R;
+          T a[R][R];
+          tile_from_smem<C>(a, S, r0, c0);
+          tile_sub_xty<C, PB>(a, S, S, r0, c0, q0);
+          tile_to_smem<C>(S, a, r0, c0);
+        } else {
+          const int v = u - nb, w = v % (zr * TXN);
+          T *Z = v < zr * TXN ? Z0 : Z1;
+          if (Z) {
+            const int r0 = p0 + (w / TXN) * R, c0 = (w % TXN) * R;
+            T a[R][R];
+            tile_from_smem<C>(a, Z, r0, c0);
+            tile_sub_xty<C, PB>(a, S, Z, r0, c0, q0);  // Z[i][j] -= sum_k U[k][i] Z[k][j], k in panel p-1
+            tile_to_smem<C>(Z, a, r0, c0);
+          }
+        }
+      }
+    }
+    if (p == 0 && wait_operands) cp_async_commit_wait_all();
+    __syncthreads();
+    if (solve)
+      for (int q = tid; q < 2 * NP; q += NT) {
+        T *Z = q < NP ? Z0 : Z1;
+        if (Z) col_subst_ut<C>(Z, q % NP, S, dinv, p0);
+      }
+    if (p + 1 < C::NPAN) {  // the next panel's rows of S with panel p
+      constexpr int ta = PB / R;
+      const int tcols = (NP - p0 - PB) / R;
+      const int na = ta * tcols - ta * (ta - 1) / 2;
+      for (int u = tid; u < na; u += NT) {
+        int i = 0, rem = u;
+        while (rem >= tcols - i) {
+          rem -= tcols - i;
+          ++i;
+        }
+        const int r0 = p0 + PB + i * R, c0 = r0 + rem * R;
+        T a[R][R];
+        tile_from_smem<C>(a, S, r0, c0);
+        tile_sub_xty<C, PB>(a, S, S, r0, c0, p0);
+        tile_to_smem<C>(S, a, r0, c0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Z <- U^{-T} Z for up to two right-hand-side blocks Z0, Z1 (either may be
 // null), blocked by panels: column substitution with U_pp, then the trailing
 // rows are updated with X^T Y products.
