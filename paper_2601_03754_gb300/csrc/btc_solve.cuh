@@ -18,6 +18,10 @@ template <typename T, int NP>
 struct SolveCfg {
   // padded leading dimension; rows stay 16-byte aligned for cp.async
   static constexpr int LDL = NP + 16 / (int)sizeof(T);
+  // large blocks: only the diagonal factor is staged in shared memory; the two
+  // coupling blocks are read once from global memory inside the products
+  // (three staged 128 x 128 blocks would leave one CTA per SM)
+  static constexpr bool STREAM = NP >= 96;
 };
 
 __device__ __forceinline__ void cp_async16_s(void *smem, const void *gmem) {
@@ -55,74 +59,87 @@ __device__ __forceinline__ void stage_vec(T *dst, const T *g, int count) {
   for (int q = threadIdx.x; q < count / V; q += blockDim.x) cp_async16_s(dst + q * V, g + q * V);
 }
 
+// Warp triangular solves, in chunks of CH rows (one row per lane): a chunk's
+// CH-step substitution chain keeps one value per lane in a register, then the
+// rows outside the chunk receive its contribution as a plain product.
+template <typename T, int NP>
+struct TrsvCfg {
+  static constexpr int CH = NP % 32 == 0 ? 32 : (NP % 16 == 0 ? 16 : NP);
+  static constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte load
+};
+
 // Y <- U^{-T} Y (forward, with the upper factor U) for the m columns of Y
-// (np x m in shared memory), by warps: warp w takes columns w, w + nwarps, ...;
-// lane t holds rows t and t + 32. Row j of U is read (U[j][i], i > j).
+// (np x m in shared memory), by warps: warp w takes columns w, w + nwarps, ...
+// Row j of U is read (U[j][i], i > j), contiguous across lanes.
 template <typename T, int NP>
 __device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *dinv) {
-  constexpr int LDL = SolveCfg<T, NP>::LDL;
-  constexpr int RPL = (NP + 31) / 32;  // rows per lane
+  constexpr int LDL = SolveCfg<T, NP>::LDL, CH = TrsvCfg<T, NP>::CH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
   for (int q = warp; q < m && warp < nw; q += nw) {
-    T v[RPL];
+#pragma unroll 1
+    for (int base = 0; base < NP; base += CH) {
+      T v = lane < CH ? Y[(base + lane) * m + q] : T(0);
 #pragma unroll
-    for (int s = 0; s < RPL; ++s) {
-      const int i = lane + 32 * s;
-      v[s] = i < NP ? Y[i * m + q] : T(0);
-    }
-#pragma unroll 4
-    for (int j = 0; j < NP; ++j) {
-      T src = v[0];  // the lane slot holding row j
-#pragma unroll
-      for (int t = 1; t < RPL; ++t)
-        if ((j >> 5) == t) src = v[t];
-      const T zj = warp_bcast(src, j & 31) * dinv[j];
-#pragma unroll
-      for (int s = 0; s < RPL; ++s) {
-        const int i = lane + 32 * s;
-        if (i > j && i < NP) v[s] = fma(-Us[j * LDL + i], zj, v[s]);
-        if (i == j) v[s] = zj;
+      for (int j = 0; j < CH; ++j) {
+        const T zj = warp_bcast(v, j) * dinv[base + j];
+        if (lane > j && lane < CH) v = fma(-Us[(base + j) * LDL + base + lane], zj, v);
+        if (lane == j) v = zj;
       }
-    }
-#pragma unroll
-    for (int s = 0; s < RPL; ++s) {
-      const int i = lane + 32 * s;
-      if (i < NP) Y[i * m + q] = v[s];
+      if (lane < CH) Y[(base + lane) * m + q] = v;
+      __syncwarp();
+      for (int i = base + CH + lane; i < NP; i += 32) {  // rows below the chunk
+        T acc = Y[i * m + q];
+#pragma unroll 8
+        for (int j = 0; j < CH; ++j) acc = fma(-Us[(base + j) * LDL + i], Y[(base + j) * m + q], acc);
+        Y[i * m + q] = acc;
+      }
+      __syncwarp();
     }
   }
 }
 
-// Y <- U^{-1} Y (backward substitution with the upper factor; column j of U read).
+// Y <- U^{-1} Y (backward substitution with the upper factor), chunks from the
+// bottom. A lane's row of the chunk's diagonal block is loaded into registers
+// with 16-byte loads (conflict-free at the padded leading dimension), so the
+// substitution chain reads no shared memory.
 template <typename T, int NP>
 __device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *dinv) {
-  constexpr int LDL = SolveCfg<T, NP>::LDL;
-  constexpr int RPL = (NP + 31) / 32;
+  constexpr int LDL = SolveCfg<T, NP>::LDL, CH = TrsvCfg<T, NP>::CH, V = TrsvCfg<T, NP>::V;
+  static_assert(CH % V == 0, "chunk rows must hold whole 16-byte loads");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
   for (int q = warp; q < m && warp < nw; q += nw) {
-    T v[RPL];
+#pragma unroll 1
+    for (int base = NP - CH; base >= 0; base -= CH) {
+      T u[CH];
+      const int row = base + (lane < CH ? lane : 0);
 #pragma unroll
-    for (int s = 0; s < RPL; ++s) {
-      const int i = lane + 32 * s;
-      v[s] = i < NP ? Y[i * m + q] : T(0);
-    }
-#pragma unroll 4
-    for (int j = NP - 1; j >= 0; --j) {
-      T src = v[0];  // the lane slot holding row j
+      for (int j = 0; j < CH; j += V) {
+        T w[V];
+        vload<T, V>(Us + row * LDL + base + j, w);
 #pragma unroll
-      for (int t = 1; t < RPL; ++t)
-        if ((j >> 5) == t) src = v[t];
-      const T xj = warp_bcast(src, j & 31) * dinv[j];
-#pragma unroll
-      for (int s = 0; s < RPL; ++s) {
-        const int i = lane + 32 * s;
-        if (i < j) v[s] = fma(-Us[i * LDL + j], xj, v[s]);
-        if (i == j) v[s] = xj;
+        for (int t = 0; t < V; ++t) u[j + t] = w[t];
       }
-    }
+      T v = lane < CH ? Y[(base + lane) * m + q] : T(0);
 #pragma unroll
-    for (int s = 0; s < RPL; ++s) {
-      const int i = lane + 32 * s;
-      if (i < NP) Y[i * m + q] = v[s];
+      for (int j = CH - 1; j >= 0; --j) {
+        const T xj = warp_bcast(v, j) * dinv[base + j];
+        if (lane < j) v = fma(-u[j], xj, v);
+        if (lane == j) v = xj;
+      }
+      if (lane < CH) Y[(base + lane) * m + q] = v;
+      __syncwarp();
+      for (int i = lane; i < base; i += 32) {  // rows above the chunk
+        T acc = Y[i * m + q];
+#pragma unroll
+        for (int j = 0; j < CH; j += V) {
+          T w[V];
+          vload<T, V>(Us + i * LDL + base + j, w);
+#pragma unroll
+          for (int t = 0; t < V; ++t) acc = fma(-w[t], Y[(base + j + t) * m + q], acc);
+        }
+        Y[i * m + q] = acc;
+      }
+      __syncwarp();
     }
   }
 }
@@ -136,18 +153,19 @@ struct SolveArgs {
   int m;
 };
 
-// Shared-memory layout of one solve item: three np x np blocks (the node's
-// own factor block, then the two coupling blocks), the reciprocal diagonal,
+// Shared-memory layout of one solve item: the node's own factor block and
+// (unless SolveCfg::STREAM) the two coupling blocks, the reciprocal diagonal,
 // and three np x m vectors.
 template <typename T, int NP>
 struct SolveSmem {
   T *U0, *U1, *U2, *dinv, *y0, *y1, *y2;
   __device__ __forceinline__ explicit SolveSmem(unsigned char *raw, int m) {
     constexpr int LDL = SolveCfg<T, NP>::LDL;
+    constexpr int NB = SolveCfg<T, NP>::STREAM ? 1 : 3;
     U0 = reinterpret_cast<T *>(raw);
-    U1 = U0 + NP * LDL;
-    U2 = U1 + NP * LDL;
-    dinv = U2 + NP * LDL;
+    U1 = NB == 3 ? U0 + NP * LDL : nullptr;
+    U2 = NB == 3 ? U1 + NP * LDL : nullptr;
+    dinv = U0 + NB * NP * LDL;
     y0 = dinv + NP;
     y1 = y0 + NP * m;
     y2 = y1 + NP * m;
@@ -164,8 +182,10 @@ __device__ __forceinline__ void stage_item_blocks(const SolveSmem<T, NP> &sm, co
   const T *dpool = reinterpret_cast<const T *>(a.dpool);
   const T *epool = reinterpret_cast<const T *>(a.epool);
   if (d0 >= 0) stage_block<T, NP>(sm.U0, dpool + d0);
-  if (v1 >= 0) stage_block<T, NP>(sm.U1, epool + e1);
-  if (v2 >= 0) stage_block<T, NP>(sm.U2, epool + e2);
+  if constexpr (!SolveCfg<T, NP>::STREAM) {
+    if (v1 >= 0) stage_block<T, NP>(sm.U1, epool + e1);
+    if (v2 >= 0) stage_block<T, NP>(sm.U2, epool + e2);
+  }
 }
 
 // Forward step for one surviving node j (pull form, Alg. 7 forward sweep):
@@ -192,15 +212,30 @@ __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_
     for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
   if (y_l >= 0) {
     const bool right = y_r >= 0;
-    for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-      const int c = q / m, col = q % m;
-      T acc = ys[q];
+    if constexpr (SolveCfg<T, NP>::STREAM) {  // coupling blocks from global memory, coalesced over c
+      const T *gl = reinterpret_cast<const T *>(a.epool) + e_l;
+      const T *gr = right ? reinterpret_cast<const T *>(a.epool) + e_r : gl;
+      for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+        const int c = q / m, col = q % m;
+        T acc = ys[q];
+#pragma unroll 32
+        for (int r = 0; r < NP; ++r) acc = fma(-__ldcg(gl + r * NP + c), yl[r * m + col], acc);
+        if (right)
+#pragma unroll 32
+          for (int r = 0; r < NP; ++r) acc = fma(-__ldcg(gr + r * NP + c), yr[r * m + col], acc);
+        ys[q] = acc;
+      }
+    } else {
+      for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+        const int c = q / m, col = q % m;
+        T acc = ys[q];
 #pragma unroll 8
-      for (int r = 0; r < NP; ++r) acc = fma(-Ul[r * LDL + c], yl[r * m + col], acc);
-      if (right)
+        for (int r = 0; r < NP; ++r) acc = fma(-Ul[r * LDL + c], yl[r * m + col], acc);
+        if (right)
 #pragma unroll 8
-        for (int r = 0; r < NP; ++r) acc = fma(-Ur[r * LDL + c], yr[r * m + col], acc);
-      ys[q] = acc;
+          for (int r = 0; r < NP; ++r) acc = fma(-Ur[r * LDL + c], yr[r * m + col], acc);
+        ys[q] = acc;
+      }
     }
   }
   __syncthreads();
@@ -239,16 +274,36 @@ __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e
   for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
   if (x_dn >= 0 || x_up >= 0) {
     const bool dn = x_dn >= 0, up = x_up >= 0;
-    for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-      const int r = q / m, col = q % m;
-      T acc = ys[q];
-      if (dn)
+    if constexpr (SolveCfg<T, NP>::STREAM) {
+      // coupling blocks from global memory: one warp per output (row r, column col), lanes
+      // split the row (coalesced loads), a shuffle reduction sums the parts
+      const T *gd = reinterpret_cast<const T *>(a.epool) + (dn ? e_dn : 0);
+      const T *gu = reinterpret_cast<const T *>(a.epool) + (up ? e_up : 0);
+      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int q = threadIdx.x >> 5; q < nm && (threadIdx.x >> 5) < nw; q += nw) {
+        const int r = q / m, col = q % m;
+        T part = T(0);
+#pragma unroll
+        for (int c = lane; c < NP; c += 32) {
+          if (dn) part = fma(__ldcg(gd + r * NP + c), xd[c * m + col], part);
+          if (up) part = fma(__ldcg(gu + r * NP + c), xu[c * m + col], part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) ys[q] -= part;
+      }
+    } else {
+      for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+        const int r = q / m, col = q % m;
+        T acc = ys[q];
+        if (dn)
 #pragma unroll 8
-        for (int c = 0; c < NP; ++c) acc = fma(-Ud[r * LDL + c], xd[c * m + col], acc);
-      if (up)
+          for (int c = 0; c < NP; ++c) acc = fma(-Ud[r * LDL + c], xd[c * m + col], acc);
+        if (up)
 #pragma unroll 8
-        for (int c = 0; c < NP; ++c) acc = fma(-Uu[r * LDL + c], xu[c * m + col], acc);
-      ys[q] = acc;
+          for (int c = 0; c < NP; ++c) acc = fma(-Uu[r * LDL + c], xu[c * m + col], acc);
+        ys[q] = acc;
+      }
     }
   }
   __syncthreads();
@@ -294,11 +349,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowS
 
 template <typename T, int NP>
 constexpr size_t fwd_smem_bytes(int m) {
-  return sizeof(T) * (3 * (size_t)NP * SolveCfg<T, NP>::LDL + NP + 3 * (size_t)NP * m);
+  constexpr size_t nb = SolveCfg<T, NP>::STREAM ? 1 : 3;
+  return sizeof(T) * (nb * NP * SolveCfg<T, NP>::LDL + NP + 3 * (size_t)NP * m);
 }
 template <typename T, int NP>
 constexpr size_t bwd_smem_bytes(int m) {
-  return sizeof(T) * (3 * (size_t)NP * SolveCfg<T, NP>::LDL + NP + 3 * (size_t)NP * m);
+  return fwd_smem_bytes<T, NP>(m);
 }
 
 // ---------------------------------------------------------------- vectors
