@@ -305,6 +305,38 @@ def large_block_measure(btc, gen, torch, stream, flush, steps=5):
     return out
 
 
+def small_case_measure(btc, gen, torch, stream, flush, steps=200):
+    """Config C1: N=64, n=16, one RHS: factor + solve latency (p50/p99) of the plain FP64 path and the
+    mixed path (both to 1e-10), against a critical-path model: the planner's critical-path flops
+    (largest node cost per level, Sec. 4.3 with p = infinity) at one SM's FP64 rate (2 DFMA/clock)."""
+    N, n = 64, 16
+    D, B = gen.bt_random(N, n, delta=1.0, seed=0)
+    b = gen.rhs(N, n, 1, seed=0)
+    Dd, Bd, bd = (torch.from_numpy(a).cuda() for a in (D, B, b))
+    out = {"N": N, "n": n}
+    for name, dt in (("plain_f64", btc.F64), ("mixed_f32", btc.MIXED_F32)):
+        p = btc.btc_plan(N, n, dt, stream)
+        info = btc.btc_plan_query(p)
+        x = torch.zeros_like(bd)
+        ts = []
+        with torch.cuda.stream(stream):
+            for rep in range(steps + 5):
+                e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                e0.record(stream)
+                it, rel, _ = btc.btc_factor_solve_refined(p, Dd, Bd, bd, x, 1, tol=TOL, maxit=30)
+                e1.record(stream)
+                e1.synchronize()
+                if rep >= 5:
+                    ts.append(1000.0 * e0.elapsed_time(e1))
+        model_us = info["critical_path_flops"] / (FP64_PEAK_PER_SM_CLK * 2070e6) * 1e6
+        out[name] = {"p50_us": statistics.median(ts), "p99_us": float(np.percentile(np.asarray(ts), 99)),
+                     "refine_iters": it, "relres": rel, "levels": info["levels"],
+                     "critical_path_model_us": model_us,
+                     "critical_path_model": "critical-path flops at one SM's FP64 rate (2 DFMA/clock, 2070 MHz)"}
+        p.free()
+    return out
+
+
 def serving_measure(btc, torch, rates=(1000.0, 4000.0), count=300):
     """Config: Poisson stream of factor+solve requests, n uniform in {12,24,48,96}, N log-uniform
     in [50, 5000], MPC-like generator, 30% re-solves of a cached factor, HBM-footprint admission;
@@ -461,8 +493,17 @@ def main():
     batched = batched_measure(btc, gen, torch, max(3, args.steps // 5), stream, flush) if not args.no_batch else None
     serving = serving_measure(btc, torch) if not args.no_serve else None
     large = large_block_measure(btc, gen, torch, stream, flush) if not args.no_large else None
+    small = small_case_measure(btc, gen, torch, stream, flush)
+    # solve roofline: each factor block read once per direction (the compulsory bytes of Alg. 7, m = 1)
+    solve_bytes = 2.0 * (N + info["offdiag_blocks"]) * n * n * 4
+    t_solve = phase["correction_solve"]
+    solve_roof = {"kernel": "k_solve_flow (one correction solve, forward + backward)", "bound": "hbm",
+                  "achieved": solve_bytes / (t_solve * 1e-3) / 1e9, "peak": None, "unit": "GB/s",
+                  "algorithmic_bytes": solve_bytes, "note": "blocks L2-resident between factor and solve"}
 
     peaks, pk_kind = _peaks()
+    solve_roof["peak"] = peaks.get("hbm_gbs")
+    solve_roof["frac"] = solve_roof["achieved"] / solve_roof["peak"] if solve_roof["peak"] else None
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_PEAK_PER_SM_CLK * sm_max * 1e6 / 1e12
     # algorithmic work of the interlaced launch: Table 1 factor costs without the top separator's
@@ -509,6 +550,8 @@ def main():
         "batched": batched,
         "serving": serving,
         "large_blocks": large,
+        "small_case": small,
+        "solve_roofline": solve_roof,
         "wall_s_timed": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:

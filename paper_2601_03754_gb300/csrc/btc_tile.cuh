@@ -422,12 +422,13 @@ __device__ __forceinline__ bool flow_wait(const FlowSync &fs, const int32_t *dep
       if (d < 0) continue;
       long long polls = 0;
       while (ld_acquire_gpu(fs.done + d) == 0) {
-        if (++polls > kMaxPolls || *((volatile int *)fs.status) != 0) {
+        // the status word is checked every 64 polls; the first polls spin without sleeping
+        if ((++polls & 63) == 0 && (polls > kMaxPolls || *((volatile int *)fs.status) != 0)) {
           atomicOr(fs.status, kFlowTimeout);
           ok = 0;
           break;
         }
-        __nanosleep(128);
+        if (polls > 32) __nanosleep(64);
       }
     }
     *s_ok = ok;

@@ -35,20 +35,26 @@ def test_graph_matches_plain_launches(N, n, m, delta, dt):
     s = torch.cuda.Stream()
     pg, pp = _plans(N, n, dt, s)
     xp = torch.zeros_like(bd)
+    torch.cuda.synchronize()
     ref = btc.btc_factor_solve_refined(pp, Dd, Bd, bd, xp, m, tol=1e-11)
     for rep in range(3):  # first call tunes, then capture, then replays
         xg = torch.zeros_like(bd)
+        torch.cuda.synchronize()
         got = btc.btc_factor_solve_refined(pg, Dd, Bd, bd, xg, m, tol=1e-11)
         assert torch.equal(xg, xp) and got[:2] == ref[:2], rep
     # new output pointer: re-captured
     xg2 = torch.full_like(bd, 7.0)
+    torch.cuda.synchronize()
     got = btc.btc_factor_solve_refined(pg, Dd, Bd, bd, xg2, m, tol=1e-11)
     assert torch.equal(xg2, xp) and got[:2] == ref[:2]
-    # the factor left behind serves later solves
+    # the factor left behind serves later solves (the copies are made on torch's stream; the plans
+    # run on s, so wait for them first)
     xs = bd.clone()
-    btc.btc_solve(pg, xs, m)
     xs2 = bd.clone()
+    torch.cuda.synchronize()
+    btc.btc_solve(pg, xs, m)
     btc.btc_solve(pp, xs2, m)
+    s.synchronize()
     assert torch.equal(xs, xs2)
 
 
