@@ -337,6 +337,38 @@ def small_case_measure(btc, gen, torch, stream, flush, steps=200):
     return out
 
 
+def interlace_measure(btc, gen, torch, stream, flush, steps=30):
+    """The paper's interlaced factor + forward substitution (Sec. 5, n=64, N=128 in its traces):
+    btc_factor_solve against btc_factor followed by btc_solve, one RHS, mixed path, no refinement."""
+    out = {}
+    for N, n in ((128, 64), (1024, 64)):
+        D, B = gen.bt_random(N, n, delta=1.0, seed=0)
+        b = gen.rhs(N, n, 1, seed=0)
+        Dd, Bd, bd = (torch.from_numpy(a).cuda() for a in (D, B, b))
+        p = btc.btc_plan(N, n, btc.MIXED_F32, stream)
+        x = bd.clone()
+        res = {}
+        for name, body in (("sequential", lambda: (btc.btc_factor(p, Dd, Bd), btc.btc_solve(p, x, 1))),
+                           ("interlaced", lambda: btc.btc_factor_solve(p, Dd, Bd, x, 1))):
+            ts = []
+            with torch.cuda.stream(stream):
+                for rep in range(steps + 3):
+                    flush.fill_(1.0)
+                    x.copy_(bd)
+                    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                    e0.record(stream)
+                    body()
+                    e1.record(stream)
+                    e1.synchronize()
+                    if rep >= 3:
+                        ts.append(1000.0 * e0.elapsed_time(e1))
+            res[name + "_us"] = statistics.median(ts)
+        res["time_saved"] = 1.0 - res["interlaced_us"] / res["sequential_us"]
+        out[f"N{N}_n{n}"] = res
+        p.free()
+    return out
+
+
 def serving_measure(btc, torch, rates=(1000.0, 4000.0), count=300):
     """Config: Poisson stream of factor+solve requests, n uniform in {12,24,48,96}, N log-uniform
     in [50, 5000], MPC-like generator, 30% re-solves of a cached factor, HBM-footprint admission;
@@ -494,6 +526,7 @@ def main():
     serving = serving_measure(btc, torch) if not args.no_serve else None
     large = large_block_measure(btc, gen, torch, stream, flush) if not args.no_large else None
     small = small_case_measure(btc, gen, torch, stream, flush)
+    interlace = interlace_measure(btc, gen, torch, stream, flush)
     # solve roofline: each factor block read once per direction (the compulsory bytes of Alg. 7, m = 1)
     solve_bytes = 2.0 * (N + info["offdiag_blocks"]) * n * n * 4
     t_solve = phase["correction_solve"]
@@ -551,6 +584,7 @@ def main():
         "serving": serving,
         "large_blocks": large,
         "small_case": small,
+        "interlaced_vs_sequential": interlace,
         "solve_roofline": solve_roof,
         "wall_s_timed": t_wall,
     }
