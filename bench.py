@@ -126,6 +126,20 @@ def _traffic_from_profile():
     return t.get("dram_bytes_per_launch")
 
 
+def replica_throughput(ms_local, world):
+    """Replicas (one independent workload per rank): the job's step time is the slowest rank's mean
+    step time (max over ranks), its throughput the units of all ranks over that time (solves/s)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * 1000.0 / ms
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores: a bounded sample of the same workload."""
     rank, world, _ = _env_rank()
@@ -472,12 +486,7 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = statistics.mean(ts)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+    ms, value = replica_throughput(statistics.mean(ts), world)
     assert rel <= TOL, rel
 
     # ---- per-kernel device times of the same step (library events on the plan's stream, L2 flushed),
