@@ -138,7 +138,9 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
   }
 
   // ---- potrf with the two trsm of the same node, pipelined by panels
-  block_potrf_trsm<C>(sS, dinv, has_up ? sA : nullptr, has_dn ? sB : nullptr, info, e, !FIRST && ASYNC);
+  block_potrf_trsm<C>(sS, dinv, has_up ? sA : nullptr, has_dn ? sB : nullptr, info, e, [] {
+    if constexpr (!FIRST && ASYNC) cp_async_commit_wait_all();
+  });
   smem_to_block<C>(dpool + it.d_self, sS, true);
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);

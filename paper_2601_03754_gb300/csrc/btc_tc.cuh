@@ -162,18 +162,22 @@ __device__ __forceinline__ void convert_operand_in_place(float *buf) {
 }
 
 // Per-CTA tensor-core state of the node kernel: TMEM base (two accumulators at
-// columns 0 and 128), the MMA completion barrier and its phase.
+// columns 0 and 128), the MMA completion barrier and its phase, and the
+// barrier that counts the bytes of the bulk (TMA) block copies.
 struct TcState {
   uint32_t tmem;
   uint64_t *mbar;
   uint32_t phase;
-  int *status;  // set to kFlowTimeout when an MMA wait gives up
+  uint64_t *tma_mbar;
+  uint32_t tma_phase;
+  int *status;  // set to kFlowTimeout when a wait gives up
 };
 
 // Allocation by warp 0 (all lanes), barrier init by thread 0; call with all threads.
 __device__ __forceinline__ void tc_begin(TcState &st, uint32_t *tmem_slot, uint64_t *mbar, int *status) {
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if ((threadIdx.x >> 5) == 0) {
@@ -187,7 +191,57 @@ __device__ __forceinline__ void tc_begin(TcState &st, uint32_t *tmem_slot, uint6
   st.tmem = *tmem_slot;
   st.mbar = mbar;
   st.phase = 0;
+  st.tma_mbar = mbar + 1;
+  st.tma_phase = 0;
   st.status = status;
+}
+
+// Bulk-async (TMA engine) copies of up to three 128 x 128 FP32 pool blocks
+// into padded shared rows (one 512-byte copy per row, issued by the CTA's last
+// warp, so that warp 0 can start the Cholesky panel at once); the
+// bytes complete on st.tma_mbar. Call with all threads; complete with
+// tc_bulk_wait. The proxy fences order the copies after this CTA's earlier
+// shared-memory accesses and after the acquire of the blocks' producers.
+__device__ __forceinline__ void tc_bulk_load(TcState &st, float *d0, const float *g0, float *d1, const float *g1,
+                                             float *d2, const float *g2) {
+  constexpr int LD = TileCfg<float, kTcNP, 8>::LD;
+  constexpr uint32_t row_bytes = kTcNP * sizeof(float);
+  if ((threadIdx.x >> 5) != (blockDim.x >> 5) - 1) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nblk = (d0 ? 1u : 0u) + (d1 ? 1u : 0u) + (d2 ? 1u : 0u);
+  if (lane == 0) {
+    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(st.tma_mbar)),
+                 "r"(nblk * row_bytes * kTcNP)
+                 : "memory");
+  }
+  __syncwarp();
+  float *dst[3] = {d0, d1, d2};
+  const float *src[3] = {g0, g1, g2};
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (!dst[b]) continue;
+    for (int r = lane; r < kTcNP; r += 32)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_addr(dst[b] + r * LD)),
+          "l"(src[b] + (size_t)r * kTcNP), "r"(row_bytes), "r"(smem_addr(st.tma_mbar))
+          : "memory");
+  }
+}
+
+// Bounded wait (all threads) for the bulk copies of the current phase.
+__device__ __forceinline__ void tc_bulk_wait(TcState &st) {
+  uint32_t done = 0;
+  for (long long polls = 0; !done && polls < kTcMaxPolls; ++polls) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(st.tma_mbar)), "r"(st.tma_phase)
+        : "memory");
+  }
+  st.tma_phase ^= 1u;
+  if (!done && threadIdx.x == 0 && st.status) atomicExch(st.status, kFlowTimeout);
 }
 
 __device__ __forceinline__ void tc_end(TcState &st) {
@@ -235,10 +289,10 @@ __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const Facto
     __syncthreads();
   } else {
     const bool pa = it.p_a >= 0, pb = it.p_b >= 0 && has_next;
-    block_to_smem_async<C>(sS, dpool + it.d_self);
+    tc_bulk_load(st, sS, dpool + it.d_self, nullptr, nullptr, nullptr, nullptr);
     if (pa) stage_operand_from_pool<NT>(reinterpret_cast<unsigned char *>(sA), epool + it.p_a);
     if (pb) stage_operand_from_pool<NT>(reinterpret_cast<unsigned char *>(sB), epool + it.p_b);
-    cp_async_commit_wait_all();
+    tc_bulk_wait(st);
     tc_publish_smem();
     if (pa || pb) {
       if (tid == 0) {
@@ -263,13 +317,17 @@ __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const Facto
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
     }
-    // the off-diagonal operands arrive while the Cholesky runs
-    if (has_up) block_to_smem_async<C>(sA, epool + it.r_up);
-    if (has_dn) block_to_smem_async<C>(sB, epool + it.r_down);
+    // the off-diagonal operands arrive (bulk copies) while the Cholesky runs
+    if (has_up || has_dn)
+      tc_bulk_load(st, has_up ? sA : nullptr, has_up ? epool + it.r_up : nullptr, has_dn ? sB : nullptr,
+                   has_dn ? epool + it.r_down : nullptr, nullptr, nullptr);
   }
 
   // ---- potrf with the two trsm, pipelined by panels (FP32 FMA)
-  block_potrf_trsm<C>(sS, dinv, has_up ? sA : nullptr, has_dn ? sB : nullptr, info, e, !FIRST);
+  const bool bulk = !FIRST && (has_up || has_dn);
+  block_potrf_trsm<C>(sS, dinv, has_up ? sA : nullptr, has_dn ? sB : nullptr, info, e, [&] {
+    if (bulk) tc_bulk_wait(st);
+  });
   smem_to_block<C>(dpool + it.d_self, sS, true);
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
@@ -342,9 +400,9 @@ template <typename S, bool FIRST>
 __global__ void __launch_bounds__(kTcThreads, 1) k_factor_level_tc(FactorArgs args, InstDesc single) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ __align__(8) uint64_t s_mbar[2];
   TcState st;
-  tc_begin(st, &s_tmem, &s_mbar, args.status);
+  tc_begin(st, &s_tmem, s_mbar, args.status);
   const FactorItem it = args.items[blockIdx.x];
   factor_node_tc<S, FIRST>(it, args, single, smem_raw, st);
   tc_end(st);
@@ -356,9 +414,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ __align__(8) uint64_t s_mbar[2];
   TcState st;
-  tc_begin(st, &s_tmem, &s_mbar, fs.status);
+  tc_begin(st, &s_tmem, s_mbar, fs.status);
   for (;;) {
     const int t = flow_claim(fs, args.count, &s_slot);
     if (t < 0) break;
@@ -383,9 +441,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ __align__(8) uint64_t s_mbar[2];
   TcState st;
-  tc_begin(st, &s_tmem, &s_mbar, fs.status);
+  tc_begin(st, &s_tmem, s_mbar, fs.status);
   const SolveFlowItem *fwd = reinterpret_cast<const SolveFlowItem *>(sa.items);
   for (;;) {
     const int t = flow_claim(fs, count, &s_slot);

@@ -607,11 +607,12 @@ __device__ __forceinline__ void block_potrf_upper(T *S, T *dinv, unsigned long l
 // with panel p. Every element receives the same updates in the same order as
 // block_potrf_upper followed by block_trsm_ut, so the results are identical;
 // the pipelining only overlaps the single-warp panel factorization with the
-// trailing updates. wait_operands: Z0/Z1 arrive by cp.async issued before the
-// call (waited for after the first panel).
-template <class C, typename T>
+// trailing updates. wait_operands(): called by every thread after the first
+// panel, before Z0/Z1 are first read (their asynchronous copies were issued
+// before the call).
+template <class C, typename T, class WaitOperands>
 __device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, unsigned long long *info, int node,
-                                                 bool wait_operands) {
+                                                 WaitOperands &&wait_operands) {
   constexpr int PB = C::PB, NP = C::NP, R = C::R, TXN = C::TXN, NT = C::NT;
   const int tid = threadIdx.x;
   const bool solve = Z0 || Z1;
@@ -651,7 +652,7 @@ __device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, un
         }
       }
     }
-    if (p == 0 && wait_operands) cp_async_commit_wait_all();
+    if (p == 0) wait_operands();
     __syncthreads();
     if (solve)
       for (int q = tid; q < 2 * NP; q += NT) {
