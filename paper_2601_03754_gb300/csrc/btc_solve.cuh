@@ -390,39 +390,6 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// Leading dimension of a staged n x n FP64 block: rows 16-byte aligned when n is even.
-__host__ __device__ constexpr int f64_ld(int n) { return (n % 2 == 0) ? n + 2 : n + 1; }
-
-// Copy an n x n FP64 block (row-major, contiguous) into shared memory with
-// leading dimension f64_ld(n): cp.async of 16-byte chunks when n is even (the
-// block and its rows are then 16-byte aligned), batched scalar loads otherwise.
-// Completes at cp_async_wait_all_s() + __syncthreads().
-__device__ __forceinline__ void stage_f64(double *dst, const double *src, int n) {
-  const int ld = f64_ld(n);
-  if (n % 2 == 0) {
-    const int cpr = n / 2, total = n * cpr;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int row = q / cpr, col = (q % cpr) * 2;
-      cp_async16_s(dst + row * ld + col, src + (size_t)row * n + col);
-    }
-    return;
-  }
-  const int total = n * n;
-  for (int base = threadIdx.x; base < total; base += 8 * blockDim.x) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int q = base + u * blockDim.x;
-      v[u] = q < total ? __ldg(src + q) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int q = base + u * blockDim.x;
-      if (q < total) dst[(q / n) * ld + q % n] = v[u];
-    }
-  }
-}
-
 // |a| rounded toward zero to FP32 with integer operations only (the FP64 ->
 // FP32 conversion instruction runs on the slow FP64 pipe of this GPU): keep
 // the exponent and the top 23 mantissa bits. Magnitudes below the FP32

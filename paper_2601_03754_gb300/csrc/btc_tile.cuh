@@ -452,62 +452,6 @@ __device__ __forceinline__ unsigned long long pack_info(int node, int col) {
 }
 
 // ----------------------------------------------------- blocked factorization
-// Unblocked upper Cholesky of the PB x PB diagonal block at (p0, p0) of S, by
-// one warp (shared memory + __syncwarp). Right-looking with unscaled rows:
-// step k applies S[t][j] -= S[k][t] S[k][j] / d_k for k < t <= j, and the rows
-// are scaled by 1/sqrt(d_k) at the end. Writes dinv[p0+k] = 1/U_kk. A pivot
-// that is not positive (or NaN) is reported and replaced by 1 so that the
-// remaining arithmetic stays finite. Must be called by all lanes of one warp.
-template <class C, typename T>
-__device__ __forceinline__ void warp_chol_diag(T *S, int p0, T *dinv, unsigned long long *info, int node) {
-  constexpr int PB = C::PB;
-  constexpr int LD = C::LD;
-  constexpr int MAXE = PB * (PB + 1) / 2;  // upper-triangle elements of the diagonal block
-  constexpr int NE = (MAXE + 31) / 32;     // per lane
-  const int lane = threadIdx.x & 31;
-  T *B = S + p0 * LD + p0;
-  // this lane's elements (t, j), t <= j, of the upper triangle
-  int tt[NE], jj[NE];
-#pragma unroll
-  for (int i = 0; i < NE; ++i) {
-    int q = lane + 32 * i, t = 0;
-    if (q >= MAXE) {
-      tt[i] = -1;
-      jj[i] = 0;
-      continue;
-    }
-    while (q >= PB - t) {
-      q -= PB - t;
-      ++t;
-    }
-    tt[i] = t;
-    jj[i] = t + q;
-  }
-  for (int k = 0; k < PB; ++k) {
-    T d = B[k * LD + k];
-    if (!(d > T(0))) {  // uniform across the warp
-      if (lane == 0 && info) atomicMin(info, pack_info(node, p0 + k));
-      d = T(1);
-      __syncwarp();
-      if (lane == 0) B[k * LD + k] = T(1);
-    }
-    const T inv = T(1) / d;
-#pragma unroll
-    for (int i = 0; i < NE; ++i)
-      if (tt[i] > k) B[tt[i] * LD + jj[i]] = fma(-B[k * LD + tt[i]] * inv, B[k * LD + jj[i]], B[tt[i] * LD + jj[i]]);
-    __syncwarp();
-  }
-  // scale rows: U_kj = S_kj / sqrt(d_k), U_kk = sqrt(d_k)
-  for (int k = lane; k < PB; k += 32) dinv[p0 + k] = T(1) / sqrt(B[k * LD + k]);
-  __syncwarp();
-#pragma unroll
-  for (int i = 0; i < NE; ++i) {
-    const int t = tt[i], j = jj[i];
-    if (t >= 0) B[t * LD + j] = (t == j) ? sqrt(B[t * LD + t]) : B[t * LD + j] * dinv[p0 + t];
-  }
-  __syncwarp();
-}
-
 // Column-wise forward substitution with the transposed diagonal block:
 // X[p0 .. p0+PB)[col] <- U_pp^{-T} X[p0 .. p0+PB)[col] for one column of a
 // shared-memory block X (U_pp read from S, reciprocal diagonal from dinv).
@@ -576,38 +520,15 @@ __device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned
   }
 }
 
-// Blocked upper Cholesky S = U^T U in place (upper triangle of S read; U
-// written to the upper triangle; entries below the diagonal are left stale).
-template <class C, typename T>
-__device__ __forceinline__ void block_potrf_upper(T *S, T *dinv, unsigned long long *info, int node, int r0, int c0) {
-  constexpr int PB = C::PB;
-#pragma unroll 1
-  for (int p = 0; p < C::NPAN; ++p) {
-    const int p0 = p * PB;
-    if (threadIdx.x < 32) warp_panel_potrf<C>(S, p0, dinv, info, node);
-    __syncthreads();
-    // trailing update of the upper tiles right/below the panel
-    if (p + 1 < C::NPAN) {
-      if (r0 >= p0 + PB && c0 >= r0) {
-        T a[C::R][C::R];
-        tile_from_smem<C>(a, S, r0, c0);
-        tile_sub_xty<C, PB>(a, S, S, r0, c0, p0);
-        tile_to_smem<C>(S, a, r0, c0);
-      }
-      __syncthreads();
-    }
-  }
-}
-
 // Blocked upper Cholesky S = U^T U fused with Z <- U^{-T} Z for up to two
 // right-hand-side blocks (either may be null), pipelined by panels: while
 // warp 0 factors panel p, the other warps apply panel p-1 to the rows of S
 // below panel p and Z_{p-1} to the rows of Z from p on; then all threads solve
 // panel p of Z (column substitution) and update the next panel's rows of S
 // with panel p. Every element receives the same updates in the same order as
-// block_potrf_upper followed by block_trsm_ut, so the results are identical;
-// the pipelining only overlaps the single-warp panel factorization with the
-// trailing updates. wait_operands(): called by every thread after the first
+// the unpipelined blocked Cholesky followed by the blocked triangular solve
+// (right-looking by panels), so the results are identical; the pipelining only
+// overlaps the single-warp panel factorization with the trailing updates. wait_operands(): called by every thread after the first
 // panel, before Z0/Z1 are first read (their asynchronous copies were issued
 // before the call).
 template <class C, typename T, class WaitOperands>
@@ -674,40 +595,6 @@ __device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, un
         tile_from_smem<C>(a, S, r0, c0);
         tile_sub_xty<C, PB>(a, S, S, r0, c0, p0);
         tile_to_smem<C>(S, a, r0, c0);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Z <- U^{-T} Z for up to two right-hand-side blocks Z0, Z1 (either may be
-// null), blocked by panels: column substitution with U_pp, then the trailing
-// rows are updated with X^T Y products.
-template <class C, typename T>
-__device__ __forceinline__ void block_trsm_ut(T *Z0, T *Z1, const T *S, const T *dinv, int r0, int c0) {
-  constexpr int PB = C::PB;
-  const int nz = (Z0 ? 1 : 0) + (Z1 ? 1 : 0);
-  if (nz == 0) return;
-#pragma unroll 1
-  for (int p = 0; p < C::NPAN; ++p) {
-    const int p0 = p * PB;
-    for (int q = threadIdx.x; q < 2 * C::NP; q += C::NT) {
-      T *Z = q < C::NP ? Z0 : Z1;
-      if (Z) col_subst_ut<C>(Z, q % C::NP, S, dinv, p0);
-    }
-    __syncthreads();
-    if (p + 1 < C::NPAN && r0 >= p0 + PB) {
-      if (Z0) {
-        T a[C::R][C::R];
-        tile_from_smem<C>(a, Z0, r0, c0);
-        tile_sub_xty<C, PB>(a, S, Z0, r0, c0, p0);  // Z[i][j] -= sum_k U[k][i] Z[k][j], k in panel p
-        tile_to_smem<C>(Z0, a, r0, c0);
-      }
-      if (Z1) {
-        T a[C::R][C::R];
-        tile_from_smem<C>(a, Z1, r0, c0);
-        tile_sub_xty<C, PB>(a, S, Z1, r0, c0, p0);
-        tile_to_smem<C>(Z1, a, r0, c0);
       }
     }
     __syncthreads();
