@@ -64,16 +64,23 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, ValueError):
             self.proc = None
+            return
+        # the timed region starts only once the sampler is producing samples
+        t0 = time.perf_counter()
+        while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.01)
+        self.first = len(self.lines)
 
     def _read(self):
         for ln in self.proc.stdout:
@@ -89,7 +96,9 @@ class ClockSampler:
             self.proc.kill()
         sms, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # samples taken while the timed region ran (the last pre-region sample when it was shorter than the
+        # sampling period)
+        for ln in self.lines[max(self.first - 1, 0):]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -411,7 +420,7 @@ def serving_measure(btc, torch, rates=(1000.0, 4000.0), count=300):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -491,7 +500,7 @@ def main():
 
     # ---- per-kernel device times of the same step (library events on the plan's stream, L2 flushed),
     # for the phase split and the roofline of the dominant kernel
-    n_phase = max(10, args.steps // 2)
+    n_phase = max(10, min(200, args.steps // 2))
     btc.btc_plan_set_timing(pm, True)
     timed_steps(pm, n_phase, mixed_step)
     k_ms, k_n = btc.btc_plan_timing(pm)
@@ -509,7 +518,7 @@ def main():
         return btc.btc_factor_solve_refined(p64, Dd, Bd, bd, xd, m, tol=TOL, maxit=30)
 
     timed_steps(p64, 3, f64_step)
-    ts64, (it64, rel64, _) = timed_steps(p64, max(5, args.steps // 5), f64_step)
+    ts64, (it64, rel64, _) = timed_steps(p64, max(5, min(50, args.steps // 5)), f64_step)
     ms64 = statistics.mean(ts64)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
@@ -521,7 +530,7 @@ def main():
     for _ in range(2):
         btc.btc_factor_solve_host(pe, Dh, Bh, bh, xh, m, TOL, 30)
     e2e_ts = []
-    for _ in range(max(5, args.steps // 5)):
+    for _ in range(max(5, min(100, args.steps // 4))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -531,7 +540,8 @@ def main():
     h2d = D.nbytes + B.nbytes + b.nbytes
     d2h = b.nbytes
 
-    batched = batched_measure(btc, gen, torch, max(3, args.steps // 5), stream, flush) if not args.no_batch else None
+    batched = (batched_measure(btc, gen, torch, max(3, min(10, args.steps // 5)), stream, flush)
+               if not args.no_batch else None)
     serving = serving_measure(btc, torch) if not args.no_serve else None
     large = large_block_measure(btc, gen, torch, stream, flush) if not args.no_large else None
     small = small_case_measure(btc, gen, torch, stream, flush)
