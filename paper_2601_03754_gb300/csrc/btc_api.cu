@@ -532,9 +532,9 @@ static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, dou
       BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, (2 + with_anorm) * sizeof(double), p->stream));
       {
         KernelTimer timer(p, BTC_TIME_RESIDUAL);
-        if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
-                           (const double *)p->D, (const double *)p->B, (const double *)x, b, p->N, p->n, p->np, m,
-                           base, p->d_norms, with_anorm)))
+        if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream,
+                           p->d_y, (const double *)p->D, (const double *)p->B, (const double *)x, b, p->N, p->n,
+                           p->np, m, base, p->d_norms, with_anorm)))
           return rc;
       }
       BTC_CUDA(cudaMemcpyAsync(p->h_rb, p->d_rb, sizeof(Readback), cudaMemcpyDeviceToHost, p->stream));
@@ -648,8 +648,9 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
     if (!r && cudaMemsetAsync(p->d_norms, 0, 2 * sizeof(double), p->stream) != cudaSuccess)
       r = fail(BTC_ERR_CUDA, "graph capture: memset");
     if (!r)
-      r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y, (const double *)D,
-                   (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base, p->d_norms, zero);
+      r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
+                   (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base, p->d_norms,
+                   zero);
     if (!r) r = launch_n((const void *)&k_refine_decide, 1, 1, 0, p->stream, p->d_rb, tol, maxit, zero, h);
     cudaGraph_t body_out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(p->gstream2, &body_out);
@@ -1129,7 +1130,8 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
     int np = n;
     int64_t base = 0;
     int no_bound = 0;
-    if (!rc) rc = launch_n(rk, N, kResThreads, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d, no_bound);
+    if (!rc)
+      rc = launch_n(rk, N, kResThreads, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d, no_bound);
   }
   double h[3] = {0, 0, 0};
   if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);

@@ -390,28 +390,31 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// |a| rounded toward zero to FP32 with integer operations only (the FP64 ->
-// FP32 conversion instruction runs on the slow FP64 pipe of this GPU): keep
-// the exponent and the top 23 mantissa bits. Magnitudes below the FP32
-// normal range give 0 and above it FLT_MAX, both lower bounds of |a|.
+// |a| rounded toward zero to FP32 from the high word of the double with 32-bit
+// integer operations only (FP64 conversions, and a sign-bit clear on the
+// 64-bit value, run on the slow FP64 pipe of this GPU): keep the exponent and
+// the top 20 mantissa bits. Magnitudes below the FP32 normal range give 0 and
+// above it FLT_MAX, both lower bounds of |a|.
 __device__ __forceinline__ float abs_lower_f32(double a) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
-  const int e = (int)(u >> 52) - 1023 + 127;
+  const int hi = __double2hiint(a) & 0x7fffffff;
+  const int e = (hi >> 20) - 1023 + 127;
   if (e <= 0) return 0.0f;
   if (e >= 255) return 3.402823466e38f;
-  return __int_as_float((e << 23) | (int)((u >> 29) & 0x7fffff));
+  return __int_as_float((e << 23) | ((hi & 0xfffff) << 3));
 }
 
 // r = b - Psi x in FP64 for one block row per CTA; writes r (converted to T)
 // into the padded work vector y when y != nullptr, and max|r|, max|x| into
 // norms[0], norms[1]. D: lower triangles read. Each output's 3n-term dot
-// product is split into kResParts contiguous partial sums, added in a fixed
-// order (deterministic). Matrix entries are read straight from global memory
-// (each block's rows stay in L1 across the partial sums); x_{i-1}, x_i,
-// x_{i+1} are staged in shared memory. with_anorm != 0: the same pass also
-// forms a lower bound of ||Psi||_inf into norms[2] (each |a_ij| rounded toward
-// zero to FP32, row sums with round-toward-zero additions, so the stopping
-// test ||r|| <= tol ||Psi|| ||x|| is never met early). Dynamic shared memory:
+// product is split into kResParts contiguous column ranges, each with one
+// FP64 chain per block (D_i, B_{i-1}, B_i^T terms, interleaved so three
+// multiply-adds are in flight per thread), added in a fixed order
+// (deterministic). Matrix entries are read straight from global memory (each
+// block's rows stay in L1 across the partial sums); x_{i-1}, x_i, x_{i+1} are
+// staged in shared memory. with_anorm != 0: the same pass also forms a lower
+// bound of ||Psi||_inf into norms[2] (each |a_ij| truncated to FP32, row sums
+// with round-toward-zero additions, so the stopping test
+// ||r|| <= tol ||Psi|| ||x|| is never met early). Dynamic shared memory:
 // residual_smem_bytes(n, m).
 constexpr int kResParts = 4;
 constexpr int kResThreads = 256;
@@ -433,34 +436,29 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
   }
   __syncthreads();
   const double *Di = D + i * bs;
-  const double *Bl = i > 0 ? B + (i - 1) * bs : nullptr;
-  const double *Br = i + 1 < N ? B + i * bs : nullptr;
+  const double *Bl = i > 0 ? B + (i - 1) * bs : D;  // a valid address when the block is absent
+  const double *Br = i + 1 < N ? B + i * bs : D;
+  const bool has_l = i > 0, has_u = i + 1 < N;
   const int chunk = (n + kResParts - 1) / kResParts;
+  const double *x0 = xs, *x1 = xs + nm, *x2 = xs + 2 * nm;
   for (int idx = threadIdx.x; idx < kResParts * nm; idx += blockDim.x) {
     const int part = idx / nm, q = idx % nm;
     const int r = q / m, col = q % m;
     const int c0 = part * chunk, c1 = min(n, c0 + chunk);
     const bool lb = with_anorm && col == 0;
-    double v = 0.0;
+    double vd = 0.0, vl = 0.0, vu = 0.0;
     float s = 0.0f;
+#pragma unroll 4
     for (int c = c0; c < c1; ++c) {
-      const double a = r >= c ? Di[r * n + c] : Di[c * n + r];
-      v = fma(a, xs[nm + c * m + col], v);
-      if (lb) s = __fadd_rz(s, abs_lower_f32(a));
+      const double ad = __ldg(r >= c ? Di + r * n + c : Di + c * n + r);
+      const double al = has_l ? __ldg(Bl + r * n + c) : 0.0;
+      const double au = has_u ? __ldg(Br + c * n + r) : 0.0;
+      vd = fma(ad, x1[c * m + col], vd);
+      vl = fma(al, x0[c * m + col], vl);
+      vu = fma(au, x2[c * m + col], vu);
+      if (lb) s = __fadd_rz(__fadd_rz(__fadd_rz(s, abs_lower_f32(ad)), abs_lower_f32(al)), abs_lower_f32(au));
     }
-    if (Bl)
-      for (int c = c0; c < c1; ++c) {
-        const double a = Bl[r * n + c];
-        v = fma(a, xs[c * m + col], v);
-        if (lb) s = __fadd_rz(s, abs_lower_f32(a));
-      }
-    if (Br)
-      for (int c = c0; c < c1; ++c) {
-        const double a = Br[c * n + r];
-        v = fma(a, xs[2 * nm + c * m + col], v);
-        if (lb) s = __fadd_rz(s, abs_lower_f32(a));
-      }
-    ps[part * nm + q] = v;
+    ps[part * nm + q] = (vd + vl) + vu;
     if (lb) as[part * n + r] = s;
   }
   __syncthreads();
