@@ -492,9 +492,12 @@ __device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned
 #pragma unroll
     for (int t = 0; t < PB; ++t) v[s][t] = j < NP ? S[(p0 + t) * LD + j] : T(0);
   }
+  // next pivot candidate: lane k+1 forms S[k+1][k+1] - U[k][k+1]^2 from its own entry, so the pivot chain
+  // is shuffle, rsqrt, scale, fma per step (the same operation the update loop applies to that entry)
+  T piv = v[0][0];
 #pragma unroll
   for (int k = 0; k < PB; ++k) {
-    T d = __shfl_sync(0xffffffffu, v[0][k], k);
+    T d = __shfl_sync(0xffffffffu, piv, k);
     if (!(d > T(0))) {  // uniform across the warp
       if (lane == 0 && info) atomicMin(info, pack_info(node, p0 + k));
       d = T(1);
@@ -504,6 +507,7 @@ __device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned
     if (lane == 0) dinv[p0 + k] = rs;
 #pragma unroll
     for (int s = 0; s < CPL; ++s) v[s][k] *= rs;  // row k of U (the pivot becomes sqrt(d))
+    if (k + 1 < PB) piv = fma(-v[0][k], v[0][k], v[0][k + 1 < PB ? k + 1 : k]);
 #pragma unroll
     for (int t = k + 1; t < PB; ++t) {
       const T ukt = __shfl_sync(0xffffffffu, v[0][k], t);  // U[k][p0 + t]
