@@ -232,6 +232,50 @@ def run_profile(which):
     return 0
 
 
+def run_phases():
+    """Per-level means of the per-node phase stamps (btc_plan_set_phase_trace) of the interlaced factor +
+    forward launch on the benchmark workload (mixed path, default tuned configuration, graphs off); one
+    JSON line. The stamps add one CTA barrier per phase, so node times are slightly above the untraced ones."""
+    import numpy as np
+    import torch
+    from paper_2601_03754_gb300 import btc, build, gen
+    build.build()
+    btc.load()
+    W = WORKLOAD
+    N, n, m = W["N"], W["n"], W["nrhs"]
+    D, B = gen.bt_random(N, n, delta=W["delta"], seed=W["seed"])
+    b = gen.rhs(N, n, m, seed=W["seed"])
+    Dd, Bd, bd = (torch.from_numpy(a).cuda() for a in (D, B, b))
+    p = btc.btc_plan(N, n, btc.MIXED_F32)
+    btc.btc_plan_set_graphs(p, False)
+    ph = torch.zeros(8 * N, dtype=torch.int64, device="cuda")
+    x = bd.clone()
+    btc.btc_factor_solve(p, Dd, Bd, x, m)  # tuning pass, unstamped
+    btc.btc_plan_set_phase_trace(p, ph)
+    for _ in range(3):
+        ph.zero_()
+        x.copy_(bd)
+        btc.btc_factor_solve(p, Dd, Bd, x, m)
+        torch.cuda.synchronize()
+    P = ph.view(N, 8).cpu().numpy().astype(np.float64)
+    ok = P[:, 5] > 0
+    t0 = P[ok, 0].min()
+    lev = np.array([((i + 1) & -(i + 1)).bit_length() for i in range(N)])
+    names = ["operands", "potrf_trsm", "store", "next_diag", "fill"]
+    levels = {}
+    for lv in sorted(set(lev[ok].tolist())):
+        idx = np.where(ok & (lev == lv))[0]
+        d = np.diff(P[idx, :6], axis=1) / 1e3
+        levels[str(lv)] = {"nodes": int(len(idx)), "start_us": round(float((P[idx, 0].min() - t0) / 1e3), 2),
+                           "end_us": round(float((P[idx, 5].max() - t0) / 1e3), 2),
+                           "node_us": round(float(d.sum(1).mean()), 2),
+                           **{k + "_us": round(float(d[:, j].mean()), 2) for j, k in enumerate(names)}}
+    print(json.dumps({"workload": f"bt_random N={N} n={n} mixed, btc_factor_solve (interlaced)",
+                      "flow_config": dict(zip(["resident_cap", "ctas_per_sm", "tuned"], btc.btc_plan_tuning(p))),
+                      "levels": levels}), flush=True)
+    return 0
+
+
 def batched_measure(btc, gen, torch, steps, stream, flush):
     """Config: 512 instances, n uniform in {8,16,32,64}, N log-uniform in [32, 2048], one RHS each,
     delta = 1e-2; mixed FP32 factor + FP64 refinement to 1e-10, beside the plain FP64 batch."""
@@ -427,11 +471,14 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the N=4096, n=128 measurement")
+    ap.add_argument("--phases", action="store_true", help="per-level node phase times of the factor launch")
     ap.add_argument("--profile", choices=["mixed", "f64", "both", "tf32"], default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args.profile)
+    if args.phases:
+        return run_phases()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -161,6 +161,19 @@ int btc_plan_set_variant(btc_plan_t p, int variant);
  */
 int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
 
+/*
+ * Per-node phase stamps of the factorization (for profiling; off by default).
+ * phase: caller-owned device buffer of 8 * N uint64, or NULL to disable. Each
+ * node e (0-based) eliminated by the FP32 or FP64 node kernels (Alg. 5 and
+ * Alg. 6 items; not the FP64 top separator of the mixed path, not the TF32
+ * tensor-core kernels) writes the global timer (ns) at phase[8e + k] for
+ * k = 0 entry, 1 operands and deferred updates in place, 2 Cholesky and both
+ * triangular solves done, 3 factor blocks stored, 4 next diagonal block
+ * updated, 5 end (fill block stored), and its SM id at phase[8e + 6]. Each
+ * stamp adds one CTA barrier; the results are unchanged.
+ */
+int btc_plan_set_phase_trace(btc_plan_t p, void *phase);
+
 /* Rebind the plan's work to another CUDA stream (NULL = legacy default
  * stream). Work already enqueued on the old stream is not waited for. */
 int btc_plan_set_stream(btc_plan_t p, void *stream);

@@ -74,6 +74,7 @@ _SIGS = {
     "btc_plan_set_stream": [_vp, _vp],
     "btc_plan_set_variant": [_vp, ctypes.c_int],
     "btc_plan_set_trace": [_vp, _vp, _vp],
+    "btc_plan_set_phase_trace": [_vp, _vp],
     "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
     "btc_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_int64)],
     "btc_server_poll": [_vp, ctypes.c_int64, ctypes.c_int, _ip, _ip, _dp, _dp],
@@ -413,6 +414,11 @@ def btc_batch_free(batch):
 
 def btc_plan_set_trace(plan, factor_trace, solve_trace):
     return _check(load().btc_plan_set_trace(plan.h, _ptr(factor_trace), _ptr(solve_trace)))
+
+
+def btc_plan_set_phase_trace(plan, phase):
+    """phase: device int64 tensor of 8 * N words (per-node phase stamps), or None to disable."""
+    return _check(load().btc_plan_set_phase_trace(plan.h, _ptr(phase)))
 
 
 VARIANT_HYBRID, VARIANT_RIGHT_LOOKING = 0, 1

@@ -156,6 +156,7 @@ struct btc_plan_s {
   cudaGraphExec_t gexec = nullptr;
   std::vector<double> gkey;
   unsigned long long *trace_fac = nullptr, *trace_solve = nullptr;  // caller-owned trace buffers
+  unsigned long long *phase = nullptr;                               // caller-owned per-node phase stamps
   // optional per-kernel-class event timing (btc_plan_set_timing)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing_pending[BTC_TIMING_CLASSES];
@@ -377,6 +378,7 @@ static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
   a.epool = p->epool;
   a.info = p->d_info;
   a.status = p->d_status;
+  a.phase = p->phase;
   a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
   a.items = p->d_fac;
   a.count = nflow;
@@ -419,6 +421,7 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   a.epool = p->epool;
   a.info = p->d_info;
   a.status = p->d_status;
+  a.phase = p->phase;
   a.inst = nullptr;
   InstDesc d{D, B, p->N, p->n};
   const bool mixed_root = dtype_mixed(p->dtype);
@@ -576,7 +579,7 @@ static std::vector<double> refine_graph_key(const btc_plan_s *p, const void *D, 
                                             const double *x, int m, double tol, int maxit) {
   return {(double)(uintptr_t)D, (double)(uintptr_t)B, (double)(uintptr_t)b, (double)(uintptr_t)x, (double)m, tol,
           (double)maxit,        (double)p->flow_var,  (double)p->ctas_per_sm, (double)(uintptr_t)p->trace_fac,
-          (double)(uintptr_t)p->trace_solve};
+          (double)(uintptr_t)p->trace_solve, (double)(uintptr_t)p->phase};
 }
 
 // Capture one refined factor + solve of m <= max_cols columns as an executable
@@ -915,6 +918,12 @@ int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace) {
   if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_trace: NULL plan");
   p->trace_fac = (unsigned long long *)factor_trace;
   p->trace_solve = (unsigned long long *)solve_trace;
+  return BTC_OK;
+}
+
+int btc_plan_set_phase_trace(btc_plan_t p, void *phase) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_phase_trace: NULL plan");
+  p->phase = (unsigned long long *)phase;
   return BTC_OK;
 }
 

@@ -33,7 +33,23 @@ struct FactorArgs {
   const InstDesc *inst;      // per-instance descriptors (batched); NULL: use the by-value one
   unsigned long long *info;  // one word per instance
   int *status = nullptr;     // launch status word (a bounded wait that gives up sets kFlowTimeout)
+  unsigned long long *phase = nullptr;  // optional per-node phase stamps (phase_stamp), or null
 };
+
+// Optional phase stamps of one node e (8 words per node): the global timer
+// (ns) at entry (0), when its operands and deferred updates are in place (1),
+// after the Cholesky and its two triangular solves (2), after U_e, U(e,e-s),
+// U(e,e+s) are stored (3), after the update of the next diagonal block (4)
+// and at the end, after the fill block (5); word 6 = SM id. Each stamp
+// follows a CTA barrier; ph is uniform across the CTA.
+__device__ __forceinline__ void phase_stamp(unsigned long long *ph, int e, int k) {
+  if (!ph) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ph[(size_t)e * 8 + k] = global_ns();
+    if (k == 0) ph[(size_t)e * 8 + 6] = sm_id();
+  }
+}
 
 template <typename T, int NP, int R>
 constexpr size_t factor_smem_bytes() {
@@ -92,6 +108,7 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
   const bool has_up = it.r_up >= 0, has_dn = it.r_down >= 0, has_next = it.d_next >= 0;
   constexpr bool ASYNC = sizeof(T) == sizeof(P);
   T d[R][R];  // the tile of S_{e+s} owned by this thread (upper tiles only)
+  phase_stamp(args.phase, e, 0);
 
   if constexpr (FIRST) {
     // level 1: the caller's blocks, converted and padded on the way in
@@ -137,14 +154,17 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
     }
   }
 
+  phase_stamp(args.phase, e, 1);
   // ---- potrf with the two trsm of the same node, pipelined by panels
   block_potrf_trsm<C>(sS, dinv, has_up ? sA : nullptr, has_dn ? sB : nullptr, info, e, [] {
     if constexpr (!FIRST && ASYNC) cp_async_commit_wait_all();
   });
+  phase_stamp(args.phase, e, 2);
   smem_to_block<C>(dpool + it.d_self, sS, true);
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
 
+  phase_stamp(args.phase, e, 3);
   // ---- S_{e+s} -= U_dn^T U_dn (and, right-looking, S_{e-s} -= U_up^T U_up)
   if constexpr (RL) {
     if (upper_tile) {
@@ -155,6 +175,7 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
     tile_sub_xty<C, NP>(d, sB, sB, r0, c0);
     tile_to_pool<C>(dpool + it.d_next, d, r0, c0);
   }
+  phase_stamp(args.phase, e, 4);
   // ---- fill block for level l+1
   if (it.fill >= 0) {
     T f[R][R];
@@ -163,6 +184,7 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
     else tile_sub_xty<C, NP>(f, sB, sA, r0, c0);                             // S'(e+s, e-s) = -U_dn^T U_up
     tile_to_pool<C>(epool + it.fill, f, r0, c0);
   }
+  phase_stamp(args.phase, e, 5);
 }
 
 // One launch per dissection level: CTA b eliminates item b of the level.

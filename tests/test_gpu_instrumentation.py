@@ -1,5 +1,6 @@
-"""Per-kernel event timing (btc_plan_set_timing / btc_plan_timing) and the
-device-side item trace (btc_plan_set_trace) of the persistent launches.
+"""Per-kernel event timing (btc_plan_set_timing / btc_plan_timing), the
+device-side item trace (btc_plan_set_trace) of the persistent launches and the
+per-node phase stamps of the factorization (btc_plan_set_phase_trace).
 
 The trace doubles as an on-device check of the interlaced schedule: every item
 may start only after each of the items it depends on has finished (times from
@@ -78,3 +79,44 @@ def test_trace_shows_every_interlaced_item_after_its_dependencies(N, n):
     y = bd.clone()
     btc.btc_factor_solve(q, Dd, Bd, y, 1)
     assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("dt,variant", [(btc.MIXED_F32, btc.VARIANT_HYBRID), (btc.F64, btc.VARIANT_HYBRID),
+                                        (btc.MIXED_F32, btc.VARIANT_RIGHT_LOOKING)], ids=["mixed", "f64", "mixed-rl"])
+def test_phase_stamps_are_ordered_and_leave_results_unchanged(dt, variant):
+    N, n = 300, 32
+    Dd, Bd, bd = _inputs(N, n, seed=7)
+    ph = torch.zeros(8 * N, dtype=torch.int64, device="cuda")
+    out = []
+    for stamps in (ph, None):
+        p = btc.btc_plan(N, n, dt)
+        btc.btc_plan_set_variant(p, variant)
+        btc.btc_plan_set_phase_trace(p, stamps)
+        x = bd.clone()
+        if variant == btc.VARIANT_HYBRID:
+            btc.btc_factor_solve(p, Dd, Bd, x, 1)
+        else:
+            btc.btc_factor(p, Dd, Bd)
+            btc.btc_solve(p, x, 1)
+        assert btc.btc_info(p)[0] == btc.OK
+        out.append(x)
+    if variant == btc.VARIANT_HYBRID:
+        assert torch.equal(out[0], out[1]), "stamping does not change the result"
+    else:  # the right-looking updates are floating-point atomics in no fixed order
+        assert torch.allclose(out[0], out[1], rtol=1e-4, atol=1e-6)
+    P = ph.view(N, 8).cpu().numpy()
+    stamped = P[:, 5] > 0
+    expect = np.ones(N, dtype=bool)
+    if dt == btc.MIXED_F32:  # the top separator is factored by the FP64 root kernel
+        expect[(1 << (N.bit_length() - 1)) - 1] = False
+    assert np.array_equal(stamped, expect)
+    assert np.all(np.diff(P[stamped, :6], axis=1) >= 0), "phases in order"
+    assert np.all(P[stamped, 6] < 1024)
+    # a node starts only after the nodes of the previous level that write its operands have finished:
+    # node e at level l (stride s = 2^(l-1)) depends on e - s/2 and e + s/2
+    lev = np.array([((i + 1) & -(i + 1)).bit_length() for i in range(N)])
+    for e in np.where(stamped & (lev > 1))[0]:
+        h = 1 << (lev[e] - 2)
+        for q in (e - h, e + h):
+            if 0 <= q < N and stamped[q]:
+                assert P[e, 0] >= P[q, 5], (int(e), int(q))
