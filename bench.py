@@ -271,7 +271,8 @@ def run_phases():
                            "node_us": round(float(d.sum(1).mean()), 2),
                            **{k + "_us": round(float(d[:, j].mean()), 2) for j, k in enumerate(names)}}
     print(json.dumps({"workload": f"bt_random N={N} n={n} mixed, btc_factor_solve (interlaced)",
-                      "flow_config": dict(zip(["resident_cap", "ctas_per_sm", "tuned"], btc.btc_plan_tuning(p))),
+                      "flow_config": dict(zip(["resident_cap", "ctas_per_sm", "tuned"],
+                                              btc.btc_plan_tuning_interlaced(p))),
                       "levels": levels}), flush=True)
     return 0
 
@@ -633,7 +634,7 @@ def main():
                       "p99_us": 1000 * float(np.percentile(np.asarray(ts64), 99))},
         "speedup_vs_plain_f64": ms64 / ms,
         "phases_ms": phase,
-        "flow_config": dict(zip(("resident_cap", "ctas_per_sm", "tuned"), btc.btc_plan_tuning(pm))),
+        "flow_config": dict(zip(("resident_cap", "ctas_per_sm", "tuned"), btc.btc_plan_tuning_interlaced(pm))),
         "roofline": {"kernel": "k_factor_fwd_flow (interlaced factor + forward sweep, one launch per step)",
                      "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,

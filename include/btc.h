@@ -226,18 +226,25 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
  * times every compiled cap at every CTAs-per-SM count that fits, three runs
  * each on the caller's D and B, keeps the fastest median and remembers it for
  * the process; the factor itself is the same in every configuration (only the
- * schedule changes). enable = 0: no tuning, the default configuration.
- * btc_plan_tuning reports the configuration in use (host pointers, each may be
- * NULL): the register-budget cap, the CTAs per SM of the launch, and whether it
- * was tuned.
+ * schedule changes). The interlaced factor + forward launch (btc_factor_solve
+ * and the refined calls) is tuned the same way on its own, on the first
+ * interlaced call of a plan shape: its kernel has other register and shared
+ * memory needs, and its best residency differs; the packed right-hand side is
+ * saved and restored around its trial runs. enable = 0: no tuning, the default
+ * configuration for both launches. btc_plan_tuning and
+ * btc_plan_tuning_interlaced report the configuration in use for the plain and
+ * the interlaced launch (host pointers, each may be NULL): the register-budget
+ * cap, the CTAs per SM of the launch, and whether it was tuned.
  */
 int btc_plan_set_autotune(btc_plan_t p, int enable);
 int btc_plan_tuning(btc_plan_t p, int *resident_cap, int *ctas_per_sm, int *tuned);
+int btc_plan_tuning_interlaced(btc_plan_t p, int *resident_cap, int *ctas_per_sm, int *tuned);
 
 /*
  * Pin the persistent factorization's configuration (turns autotuning off):
  * the compiled register-budget cap and the CTAs per SM of the launch
- * (0: as many as fit). Errors: BTC_ERR_UNSUPPORTED when no variant has that
+ * (0: as many as fit); the interlaced launch takes the same cap and as many of
+ * those CTAs per SM as fit for it. Errors: BTC_ERR_UNSUPPORTED when no variant has that
  * cap, BTC_ERR_ARG when the CTAs do not fit. btc_plan_flow_configs lists the
  * compiled caps and the CTAs per SM each allows (host arrays; on input *count
  * is their capacity, on output the number of variants).
@@ -266,7 +273,8 @@ int btc_plan_set_graphs(btc_plan_t p, int enable);
  * production). btc_plan_timing synchronizes the stream, returns per class the
  * summed device time in ms[c] and the launch count in launches[c] (host
  * arrays of BTC_TIMING_CLASSES entries) since the last call, and resets them.
- * Enabling or disabling discards what is pending.
+ * Enabling or disabling discards what is pending. The autotuner's trial
+ * launches are not recorded.
  */
 enum btc_timing_class {
   BTC_TIME_FACTOR = 0,          /* persistent factorization launch (or its level launches)        */

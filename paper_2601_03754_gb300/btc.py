@@ -60,6 +60,7 @@ _SIGS = {
     "btc_plan_set_autotune": [_vp, ctypes.c_int],
     "btc_plan_set_graphs": [_vp, ctypes.c_int],
     "btc_plan_tuning": [_vp, _ip, _ip, _ip],
+    "btc_plan_tuning_interlaced": [_vp, _ip, _ip, _ip],
     "btc_plan_set_flow_config": [_vp, ctypes.c_int, ctypes.c_int],
     "btc_plan_flow_configs": [_vp, _ip, _ip, _ip],
     "btc_plan_timing": [_vp, _dp, _ip],
@@ -234,6 +235,13 @@ def btc_plan_tuning(plan):
     """(register-budget cap, CTAs per SM, tuned) of the plan's persistent factorization."""
     a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     _check(load().btc_plan_tuning(plan.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, bool(c.value)
+
+
+def btc_plan_tuning_interlaced(plan):
+    """(register-budget cap, CTAs per SM, tuned) of the plan's interlaced factor + forward launch."""
+    a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().btc_plan_tuning_interlaced(plan.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, bool(c.value)
 
 

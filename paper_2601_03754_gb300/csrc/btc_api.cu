@@ -146,8 +146,9 @@ struct btc_plan_s {
   // persistent-kernel configuration: residency variant and CTAs per SM (autotuned)
   int sms = 0;
   int flow_var = 0, ctas_per_sm = 0;
+  int inter_var = 0, inter_ctas = 0;  // the interlaced launch's own configuration
   int occ_fac[kFlowVariants] = {}, occ_fused[kFlowVariants] = {}, occ_rl[kFlowVariants] = {};
-  bool autotune = true, tuned[2] = {false, false};  // per algorithm variant (hybrid, right-looking)
+  bool autotune = true, tuned[3] = {false, false, false};  // hybrid, right-looking, interlaced launch
   // executable graph of one refined factor + solve (btc_factor_solve_refined), for the pointers,
   // sizes and configuration it was captured with
   bool graphs = true;
@@ -295,14 +296,35 @@ static int decode_info(btc_plan_s *p, int *block, int *col) {
 }
 
 // Persistent factor kernels of variant v with c CTAs per SM (0: as many as fit).
+// Configuration of the interlaced factor + forward launch: residency variant v,
+// c CTAs per SM (0 or too many: as many as fit).
+static void apply_inter_config(btc_plan_s *p, int v, int c) {
+  const int occ = std::max(1, p->occ_fused[v]);
+  c = (c <= 0 || c > occ) ? occ : c;
+  p->inter_var = v;
+  p->inter_ctas = c;
+  p->inter_grid = c * p->sms;
+}
+
+// Configuration of the persistent factorization; the interlaced launch follows
+// it until it is tuned on its own.
 static void apply_flow_config(btc_plan_s *p, int v, int c) {
   const int occ = std::max(1, p->occ_fac[v]);
   c = (c <= 0 || c > occ) ? occ : c;
   p->flow_var = v;
   p->ctas_per_sm = c;
   p->fac_grid = c * p->sms;
-  p->inter_grid = std::max(1, std::min(c, std::max(1, p->occ_fused[v]))) * p->sms;
+  apply_inter_config(p, v, c);
 }
+
+// Suspends the plan's per-kernel event timing for its lifetime: tuning trial
+// launches are not part of the caller's timing statistics.
+struct TimingPause {
+  btc_plan_s *p;
+  bool was;
+  explicit TimingPause(btc_plan_s *q) : p(q), was(q->timing) { q->timing = false; }
+  ~TimingPause() { p->timing = was; }
+};
 
 // Process-wide memory of tuned configurations: (dtype, np, N, algorithm
 // variant) -> (residency variant, CTAs per SM).
@@ -328,6 +350,7 @@ static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
     }
   }
   const KernelSet &k = *p->ks;
+  TimingPause pause(p);
   cudaEvent_t e0, e1;
   BTC_CUDA(cudaEventCreate(&e0));
   BTC_CUDA(cudaEventCreate(&e1));
@@ -403,6 +426,103 @@ static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
                   flow_sync(p, 0));
 }
 
+// The interlaced factor + forward launch over the first m columns of the packed
+// work vector, with the plan's interlaced configuration.
+static int launch_interlaced(btc_plan_s *p, const void *D, const void *B, int m) {
+  const KernelSet &k = *p->ks;
+  FactorArgs a;
+  a.dpool = p->dpool;
+  a.epool = p->epool;
+  a.info = p->d_info;
+  a.status = p->d_status;
+  a.phase = p->phase;
+  a.inst = nullptr;
+  a.items = p->d_fac;
+  a.count = p->n_inter;
+  InstDesc d{D, B, p->N, p->n};
+  BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+  BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_inter, p->stream));
+  SolveArgs sa;
+  sa.items = p->d_solve_flow;
+  sa.count = p->hp.n_fwd;
+  sa.dpool = p->dpool;
+  sa.epool = p->epool;
+  sa.y = p->d_y;
+  sa.m = m;
+  const int32_t *code = p->d_inter_code, *deps = p->d_inter_deps;
+  const int nfirst = (int)p->fac_off[1];
+  KernelTimer timer(p, BTC_TIME_FACTOR_FORWARD);
+  return launch_n(k.flow_v[p->inter_var].fac_fwd, std::min(p->inter_grid, p->n_inter), k.fac_threads,
+                  k.fused_smem(m), p->stream, a, d, sa, code, deps, nfirst, p->n_inter, flow_sync(p, 0));
+}
+
+// Autotuner of the interlaced launch, like autotune_flow but timing the fused
+// kernel itself (its registers, shared memory and item mix differ from the
+// plain factorization's, and so does its best residency). The launch runs the
+// forward sweep in place, so the packed work vector is saved first and put back
+// before every trial and at the end. Remembered per shape for the process.
+static int autotune_inter(btc_plan_s *p, const void *D, const void *B, int m) {
+  const auto key = std::make_tuple(p->dtype, p->np, p->N, 2);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      apply_inter_config(p, it->second.first, it->second.second);
+      p->tuned[2] = true;
+      return BTC_OK;
+    }
+  }
+  const KernelSet &k = *p->ks;
+  TimingPause pause(p);
+  const size_t ybytes = (size_t)p->N * p->np * m * k.elem;
+  void *ysave = nullptr;
+  BTC_CUDA(cudaMallocAsync(&ysave, ybytes, p->stream));
+  int rc = BTC_OK;
+  if (cudaMemcpyAsync(ysave, p->d_y, ybytes, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess)
+    rc = fail(BTC_ERR_CUDA, "autotune: work vector copy failed");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(BTC_ERR_CUDA, "autotune: event creation failed");
+  float best = 1e30f;
+  int best_v = p->inter_var, best_c = p->inter_ctas;
+  for (int v = 0; v < k.n_flow_v && rc == BTC_OK; ++v) {
+    for (int c = 1; c <= p->occ_fused[v] && rc == BTC_OK; ++c) {
+      apply_inter_config(p, v, c);
+      float t[3];
+      for (int r = 0; r < 3 && rc == BTC_OK; ++r) {
+        if (cudaMemcpyAsync(p->d_y, ysave, ybytes, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess) {
+          rc = fail(BTC_ERR_CUDA, "autotune: work vector copy failed");
+          break;
+        }
+        cudaEventRecord(e0, p->stream);
+        rc = launch_interlaced(p, D, B, m);
+        cudaEventRecord(e1, p->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(BTC_ERR_CUDA, "autotune: synchronize failed");
+        cudaEventElapsedTime(&t[r], e0, e1);
+      }
+      if (rc) break;
+      std::sort(t, t + 3);
+      if (t[1] < best) {
+        best = t[1];
+        best_v = v;
+        best_c = c;
+      }
+    }
+  }
+  if (cudaMemcpyAsync(p->d_y, ysave, ybytes, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess && !rc)
+    rc = fail(BTC_ERR_CUDA, "autotune: work vector copy failed");
+  cudaFreeAsync(ysave, p->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) return rc;
+  apply_inter_config(p, best_v, best_c);
+  p->tuned[2] = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = {best_v, best_c};
+  return BTC_OK;
+}
+
 // Factorization (Alg. 5, or Alg. 6 with the right-looking variant). m_inter > 0:
 // the forward sweep over the first m_inter columns of the work vector (packed
 // by the caller) is interlaced with the factorization in the same persistent
@@ -414,7 +534,11 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   const KernelSet &k = *p->ks;
   const bool rl = p->variant == BTC_VARIANT_RIGHT_LOOKING;
   int rc = BTC_OK;
-  if (p->sched == BTC_SCHED_FLOW && p->autotune && !p->tuned[rl ? 1 : 0] && (rc = autotune_flow(p, D, B))) return rc;
+  const bool inter = p->sched == BTC_SCHED_FLOW && !rl && m_inter > 0 && p->n_inter > 0;
+  if (p->sched == BTC_SCHED_FLOW && p->autotune) {
+    if (inter && !p->tuned[2] && (rc = autotune_inter(p, D, B, m_inter))) return rc;
+    if (!inter && !p->tuned[rl ? 1 : 0] && (rc = autotune_flow(p, D, B))) return rc;
+  }
   BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
   FactorArgs a;
   a.dpool = p->dpool;
@@ -427,24 +551,8 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   const bool mixed_root = dtype_mixed(p->dtype);
   const int last = p->hp.levels - 1;
   if (p->sched == BTC_SCHED_FLOW) {
-    if (!rl && m_inter > 0 && p->n_inter > 0) {
-      BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
-      BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
-      BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_inter, p->stream));
-      a.items = p->d_fac;
-      a.count = p->n_inter;
-      SolveArgs sa;
-      sa.items = p->d_solve_flow;
-      sa.count = p->hp.n_fwd;
-      sa.dpool = p->dpool;
-      sa.epool = p->epool;
-      sa.y = p->d_y;
-      sa.m = m_inter;
-      const int32_t *code = p->d_inter_code, *deps = p->d_inter_deps;
-      const int nfirst = (int)p->fac_off[1];
-      KernelTimer timer(p, BTC_TIME_FACTOR_FORWARD);
-      rc = launch_n(k.flow_v[p->flow_var].fac_fwd, std::min(p->inter_grid, p->n_inter), k.fac_threads,
-                    k.fused_smem(m_inter), p->stream, a, d, sa, code, deps, nfirst, p->n_inter, flow_sync(p, 0));
+    if (inter) {
+      rc = launch_interlaced(p, D, B, m_inter);
     } else {
       rc = launch_factor_flow(p, D, B);
     }
@@ -579,7 +687,8 @@ static std::vector<double> refine_graph_key(const btc_plan_s *p, const void *D, 
                                             const double *x, int m, double tol, int maxit) {
   return {(double)(uintptr_t)D, (double)(uintptr_t)B, (double)(uintptr_t)b, (double)(uintptr_t)x, (double)m, tol,
           (double)maxit,        (double)p->flow_var,  (double)p->ctas_per_sm, (double)(uintptr_t)p->trace_fac,
-          (double)(uintptr_t)p->trace_solve, (double)(uintptr_t)p->phase};
+          (double)(uintptr_t)p->trace_solve, (double)(uintptr_t)p->phase, (double)p->inter_var,
+          (double)p->inter_ctas};
 }
 
 // Capture one refined factor + solve of m <= max_cols columns as an executable
@@ -682,7 +791,7 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
 // The graph form applies to one column chunk with the interlaced form, once
 // the persistent configuration is settled, and without per-kernel timing.
 static bool can_graph(const btc_plan_s *p, int m) {
-  return p->graphs && !p->timing && can_interlace(p, m) && (!p->autotune || p->tuned[0]);
+  return p->graphs && !p->timing && can_interlace(p, m) && (!p->autotune || p->tuned[2]);
 }
 
 // One refined factor + solve through the captured graph (re-captured when a
@@ -1160,7 +1269,7 @@ int btc_plan_set_autotune(btc_plan_t p, int enable) {
   p->autotune = enable != 0;
   if (!p->autotune) {
     apply_flow_config(p, p->ks->flow_default, 0);
-    p->tuned[0] = p->tuned[1] = false;
+    p->tuned[0] = p->tuned[1] = p->tuned[2] = false;
   }
   return BTC_OK;
 }
@@ -1173,7 +1282,7 @@ int btc_plan_set_flow_config(btc_plan_t p, int resident_cap, int ctas_per_sm) {
         return fail(BTC_ERR_ARG, "btc_plan_set_flow_config: %d CTAs per SM do not fit (at most %d)", ctas_per_sm,
                     p->occ_fac[v]);
       p->autotune = false;
-      p->tuned[0] = p->tuned[1] = false;
+      p->tuned[0] = p->tuned[1] = p->tuned[2] = false;
       apply_flow_config(p, v, ctas_per_sm);
       return BTC_OK;
     }
@@ -1196,6 +1305,14 @@ int btc_plan_tuning(btc_plan_t p, int *resident_cap, int *ctas_per_sm, int *tune
   if (resident_cap) *resident_cap = p->ks->flow_v[p->flow_var].minb;
   if (ctas_per_sm) *ctas_per_sm = p->ctas_per_sm;
   if (tuned) *tuned = p->tuned[p->variant == BTC_VARIANT_RIGHT_LOOKING ? 1 : 0] ? 1 : 0;
+  return BTC_OK;
+}
+
+int btc_plan_tuning_interlaced(btc_plan_t p, int *resident_cap, int *ctas_per_sm, int *tuned) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_tuning_interlaced: NULL plan");
+  if (resident_cap) *resident_cap = p->ks->flow_v[p->inter_var].minb;
+  if (ctas_per_sm) *ctas_per_sm = p->inter_ctas;
+  if (tuned) *tuned = p->tuned[2] ? 1 : 0;
   return BTC_OK;
 }
 

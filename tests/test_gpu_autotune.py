@@ -64,16 +64,25 @@ def test_autotuner_picks_a_compiled_configuration_and_remembers_it():
     Dd, Bd = dev(D, torch.float64), dev(B, torch.float64)
     p0 = btc.btc_plan(N, n, dt)
     btc.btc_plan_set_autotune(p0, False)
-    _, x_ref = _run(p0, Dd, Bd, b, dt)
+    f_ref, x_ref = _run(p0, Dd, Bd, b, dt)
+    caps = dict(btc.btc_plan_flow_configs(p0))
     p = btc.btc_plan(N, n, dt)
-    assert btc.btc_plan_tuning(p)[2] is False
+    assert btc.btc_plan_tuning(p)[2] is False and btc.btc_plan_tuning_interlaced(p)[2] is False
+    # the interlaced call tunes its own launch; its trial runs do not disturb the right-hand side
     _, x = _run(p, Dd, Bd, b, dt)
-    cap, ctas, tuned = btc.btc_plan_tuning(p)
+    cap, ctas, tuned = btc.btc_plan_tuning_interlaced(p)
     assert tuned and np.array_equal(x, x_ref)
-    assert (cap, ) in [(c, ) for c, m in btc.btc_plan_flow_configs(p)]
-    assert 1 <= ctas <= dict(btc.btc_plan_flow_configs(p))[cap]
-    q = btc.btc_plan(N, n, dt)  # same shape: the remembered configuration, no new timing runs
+    assert cap in caps and ctas >= 1
+    assert btc.btc_plan_tuning(p)[2] is False, "the plain launch is tuned on its first use"
+    btc.btc_factor(p, Dd, Bd)
+    pcap, pctas, ptuned = btc.btc_plan_tuning(p)
+    assert ptuned and pcap in caps and 1 <= pctas <= caps[pcap]
+    f = btc.btc_get_factor(p)
+    assert np.array_equal(f[0], f_ref[0]) and np.array_equal(f[1], f_ref[1])
+    q = btc.btc_plan(N, n, dt)  # same shape: the remembered configurations, no new timing runs
     _run(q, Dd, Bd, b, dt)
-    assert btc.btc_plan_tuning(q) == (cap, ctas, True)
+    assert btc.btc_plan_tuning_interlaced(q) == (cap, ctas, True)
+    btc.btc_factor(q, Dd, Bd)
+    assert btc.btc_plan_tuning(q) == (pcap, pctas, True)
     with pytest.raises(btc.BtcError):
         btc.btc_plan_set_flow_config(q, 5, 1)
