@@ -7,7 +7,7 @@ A step = btc_factor_solve_refined: the factorization of Alg. 5 with the
 forward substitution of Alg. 7 interlaced in the same persistent launch, the
 backward substitution, then FP64 residuals and correction solves until
 ||r|| <= 1e-10 ||A|| ||x||, in the chosen form: FP32 factor and correction
-solves, FP64 root Cholesky, residual and update. The plain FP64 GPU path
+solves, double-FP32 root Cholesky, residual and update. The plain FP64 GPU path
 (same kernels in FP64, no refinement needed) is timed beside it.
 
 Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
@@ -365,7 +365,7 @@ def large_block_measure(btc, gen, torch, stream, flush, steps=5):
             btc.btc_plan_set_timing(p, False)
             res[name] = {"ms_factor_solve_refined": statistics.mean(ts), "ms_factor": statistics.mean(tf),
                          "factor_tflops": info["factor_flops"] / (statistics.mean(tf) * 1e-3) / 1e12,
-                         "ms_factor_kernel": k_ms[btc.TIME_FACTOR], "ms_root_fp64": k_ms[btc.TIME_ROOT],
+                         "ms_factor_kernel": k_ms[btc.TIME_FACTOR], "ms_root": k_ms[btc.TIME_ROOT],
                          "refine_iters": it, "relres": rel, "converged": rc == btc.OK}
             p.free()
         out[str(delta)] = res
@@ -554,7 +554,7 @@ def main():
     k_ms, k_n = btc.btc_plan_timing(pm)
     btc.btc_plan_set_timing(pm, False)
     phase = {name: (k_ms[c] / k_n[c] if k_n[c] else None) for name, c in
-             (("factor_forward_interlaced", btc.TIME_FACTOR_FORWARD), ("root_fp64", btc.TIME_ROOT),
+             (("factor_forward_interlaced", btc.TIME_FACTOR_FORWARD), ("root_chol", btc.TIME_ROOT),
               ("solve_tail", btc.TIME_SOLVE_TAIL), ("correction_solve", btc.TIME_SOLVE),
               ("residual", btc.TIME_RESIDUAL))}
     t_fused = phase["factor_forward_interlaced"]
@@ -614,7 +614,7 @@ def main():
     fused_flops = info["factor_flops"] - root_flops + fwd_flops
     achieved = fused_flops / (t_fused * 1e-3) / 1e12
     traffic = _traffic_from_profile()
-    # graph of one step: pack, interlaced factor + forward, FP64 root, solve tail, unpack, residual,
+    # graph of one step: pack, interlaced factor + forward, double-FP32 root, solve tail, unpack, residual,
     # stopping test; per refinement step: solve, update, residual, stopping test
     launches = 7 + 4 * iters
 

@@ -41,7 +41,7 @@ enum btc_dtype {
   BTC_F64 = 0,        /* factor and solve in FP64 (the plain FP64 path)                         */
   BTC_F32 = 1,        /* factor and solve in FP32                                                */
   BTC_MIXED_F32 = 2,  /* FP64 inputs; factor and correction solves in FP32 except the root
-                         (top-separator) Cholesky, which runs in FP64; FP64 residual and update
+                         (top-separator) Cholesky, which runs in double-FP32 (pairs of FP32, about 48 bits); FP64 residual and update
                          in btc_solve_refined                                                    */
   BTC_MIXED_TF32 = 3, /* as BTC_MIXED_F32, with the four n^3 products of every node (the two
                          deferred syrk, the immediate syrk and the fill gemm of Alg. 5) on the
@@ -157,7 +157,7 @@ int btc_plan_set_variant(btc_plan_t p, int variant);
  * forward items of all levels + N backward items), or NULL to disable. Every
  * item records the global timer (ns) when it was claimed, when its inputs were
  * ready and when it finished, and the SM it ran on. Items that do not run
- * (the FP64 root of the mixed path, launched separately) stay untouched.
+ * (the double-FP32 root of the mixed path, launched separately) stay untouched.
  */
 int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
 
@@ -165,7 +165,7 @@ int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
  * Per-node phase stamps of the factorization (for profiling; off by default).
  * phase: caller-owned device buffer of 8 * N uint64, or NULL to disable. Each
  * node e (0-based) eliminated by the FP32 or FP64 node kernels (Alg. 5 and
- * Alg. 6 items; not the FP64 top separator of the mixed path, not the TF32
+ * Alg. 6 items; not the double-FP32 top separator of the mixed path, not the TF32
  * tensor-core kernels) writes the global timer (ns) at phase[8e + k] for
  * k = 0 entry, 1 operands and deferred updates in place, 2 Cholesky and both
  * triangular solves done, 3 factor blocks stored, 4 next diagonal block
@@ -256,7 +256,7 @@ int btc_plan_flow_configs(btc_plan_t p, int *caps, int *max_ctas, int *count);
  * CUDA graphs for btc_factor_solve_refined (on by default). With the
  * interlaced form, one column pass and a settled persistent configuration,
  * the whole refined factor + solve is captured once as an executable graph
- * (pack, interlaced factorization + forward sweep, FP64 root, solve tail,
+ * (pack, interlaced factorization + forward sweep, double-FP32 root, solve tail,
  * unpack, FP64 residual, stopping test, and a device-side while loop of
  * correction solves that runs until the stopping test says stop) and replayed
  * on later calls with the same pointers, sizes and configuration (re-captured
@@ -279,7 +279,7 @@ int btc_plan_set_graphs(btc_plan_t p, int enable);
 enum btc_timing_class {
   BTC_TIME_FACTOR = 0,          /* persistent factorization launch (or its level launches)        */
   BTC_TIME_FACTOR_FORWARD = 1,  /* interlaced factorization + forward substitution launch         */
-  BTC_TIME_ROOT = 2,            /* FP64 top-separator Cholesky (mixed path)                        */
+  BTC_TIME_ROOT = 2,            /* double-FP32 top-separator Cholesky (mixed path)                        */
   BTC_TIME_SOLVE = 3,           /* full solve launch (forward + backward)                          */
   BTC_TIME_SOLVE_TAIL = 4,      /* solve tail after an interlaced factorization                    */
   BTC_TIME_RESIDUAL = 5,        /* FP64 residual and norms of the refinement                       */

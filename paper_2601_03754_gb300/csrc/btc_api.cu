@@ -387,7 +387,7 @@ static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
   return BTC_OK;
 }
 
-// Persistent factorization launch of every level except the FP64 top
+// Persistent factorization launch of every level except the double-FP32 top
 // separator of the mixed path (hybrid Alg. 5, or Alg. 6 after its packing
 // pass), with the plan's configuration.
 static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
@@ -692,7 +692,7 @@ static std::vector<double> refine_graph_key(const btc_plan_s *p, const void *D, 
 }
 
 // Capture one refined factor + solve of m <= max_cols columns as an executable
-// graph: pack, interlaced factorization + forward sweep, FP64 root, solve
+// graph: pack, interlaced factorization + forward sweep, double-FP32 root, solve
 // tail, unpack, FP64 residual with the norm bound, stopping test; then a while
 // node whose body is one correction (solve, update, residual, stopping test),
 // repeated on the device until the test says stop; then one copy of the

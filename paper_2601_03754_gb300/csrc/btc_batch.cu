@@ -160,7 +160,7 @@ struct BatchGroup {
   FactorItem *d_fac = nullptr;
   int32_t *d_fac_deps = nullptr;
   int n_fac = 0, n_first = 0;
-  FactorItem *d_roots = nullptr;  // FP64 roots (mixed path): [level-1 roots | other roots]
+  FactorItem *d_roots = nullptr;  // double-FP32 roots (mixed path): [level-1 roots | other roots]
   int n_roots_first = 0, n_roots_rest = 0;
   SolveFlowItem *d_solve = nullptr;
   int n_solve = 0;

@@ -58,7 +58,7 @@ constexpr size_t factor_smem_bytes() {
 }
 
 // T: arithmetic type; P: element type of the pools; S: element type of the
-// caller's D and B (read at level 1 only). The FP64 top-separator Cholesky of
+// caller's D and B (read at level 1 only). The double-FP32 top-separator Cholesky of
 // the mixed-precision path is the instantiation T = double, P = float.
 //
 // Three shared-memory blocks: sS holds S_e -> U_e; sA and sB first hold the
@@ -247,24 +247,71 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
   }
 }
 
-// ------------------------------------------------ FP64 top-separator Cholesky
+// ------------------------------------------ double-FP32 top-separator Cholesky
+// Double-FP32 numbers: unevaluated pairs hi + lo of FP32 values with
+// |lo| <= ulp(hi) / 2 (about 48 significant bits), built from the error-free
+// transformations of the double-double literature (Knuth's two-sum, the
+// FMA-based exact product; Hida, Li and Bailey 2001). The rounded intrinsics
+// keep the compiler from contracting the steps into FMAs, which would break
+// their exactness.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// u * v; the lo * lo term is below the format's precision
+__device__ __forceinline__ F2 f2_mul(F2 u, F2 v) {
+  const float p = __fmul_rn(u.hi, v.hi);
+  float e = fmaf(u.hi, v.hi, -p);  // exact error of p
+  e = fmaf(u.hi, v.lo, e);
+  e = fmaf(u.lo, v.hi, e);
+  return f2_fast_two_sum(p, e);
+}
+// a - u * v
+__device__ __forceinline__ F2 f2_sub_mul(F2 a, F2 u, F2 v) {
+  const float p = __fmul_rn(u.hi, v.hi);
+  float e = fmaf(u.hi, v.hi, -p);
+  e = fmaf(u.hi, v.lo, e);
+  e = fmaf(u.lo, v.hi, e);
+  const F2 t = f2_two_sum(a.hi, -p);
+  return f2_fast_two_sum(t.hi, __fadd_rn(t.lo, __fsub_rn(a.lo, e)));
+}
+// 1 / sqrt(d), d > 0: the FP32 estimate x and one Newton step x + x (1 - d x^2) / 2, with 1 - d x^2
+// formed from the exact square of x and the double-FP32 product (the difference from 1 is exact there)
+__device__ __forceinline__ F2 f2_rsqrt(F2 d) {
+  const float x = rsqrtf(d.hi);
+  const float x2 = __fmul_rn(x, x);
+  const F2 dx2 = f2_mul(d, F2{x2, fmaf(x, x, -x2)});
+  const float r = __fsub_rn(__fsub_rn(1.0f, dx2.hi), dx2.lo);
+  return f2_fast_two_sum(x, __fmul_rn(x, __fmul_rn(0.5f, r)));
+}
+
 // Mixed path: the top separator's Schur complement S (FP32 pool, upper
-// triangle valid) is factored in FP64 by one CTA and the factor is rounded to
-// the FP32 pool. The deferred update S -= P_a^T P_a (Alg. 5, level L-1 block)
-// is applied first in FP32 register tiles, like every other Schur update of
-// this path.
+// triangle valid) is factored in double-FP32 arithmetic by one CTA and the
+// factor is rounded to the FP32 pool, so the Cholesky adds no FP32 rounding of
+// its own (the pool value is the rounded double-FP32 result, as an FP64
+// factorization rounded to FP32 would give up to ties). The deferred update
+// S -= P_a^T P_a (Alg. 5, level L-1 block) is applied first in FP32 register
+// tiles, like every other Schur update of this path. Everything runs on the
+// FP32 pipe: the FP64 pipe of this GPU issues two lanes per clock per SM and
+// its square root is a software sequence, which made an FP64 form of this
+// kernel (same structure) about four times slower.
 //
-// The FP64 pipe of this GPU issues about two lanes per clock per SM and a
-// masked lane costs as much as an active one, so the factorization avoids
-// both single-warp panels and tile masks: it is the unblocked right-looking
-// form over a dense list of the upper-triangle elements. At step k every
-// element (i, j) with k+2 <= i <= j is updated, S_ij -= U_ki U_kj, by the
-// threads of warps 1.., in list order (row-major, so the elements still
-// active form a suffix); warp 0 meanwhile updates row k+1 and factors it
-// (pivot, 1/sqrt, row scaling), so that one barrier per column suffices.
+// The factorization is the unblocked right-looking form over a dense list of
+// the upper-triangle elements (no masked lanes): at step k every element
+// (i, j) with k+2 <= i <= j is updated, S_ij -= U_ki U_kj, by the threads of
+// warps 1.., in list order (row-major, so the elements still active form a
+// suffix); warp 0 meanwhile updates row k+1 and factors it (pivot, 1/sqrt,
+// row scaling), so that one barrier per column suffices.
 template <int NP>
 struct RootCfg {
-  static constexpr int LD = NP + 1;                // FP64 leading dimension
+  static constexpr int LD = NP + 1;                // leading dimension of the (hi, lo) array
   static constexpr int NE = NP * (NP + 1) / 2;     // upper-triangle elements
   __host__ __device__ static constexpr int row_off(int i) { return i * NP - i * (i - 1) / 2; }
 };
@@ -272,24 +319,29 @@ struct RootCfg {
 template <int NP, int R>
 constexpr size_t root_smem_bytes() {
   using C = TileCfg<float, NP, R>;
-  constexpr size_t dbl = sizeof(double) * ((size_t)NP * RootCfg<NP>::LD + NP);
+  constexpr size_t f2 = 2 * sizeof(float) * ((size_t)NP * RootCfg<NP>::LD + NP);
   constexpr size_t tab = sizeof(unsigned short) * (size_t)RootCfg<NP>::NE;
   constexpr size_t stage = sizeof(float) * (size_t)C::BLK;  // P_a, before the element list is built
-  return dbl + (tab > stage ? tab : stage);
+  return f2 + (tab > stage ? tab : stage);
 }
 
 template <typename P, typename S, int NP, int R, bool FIRST, bool RL>
 __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorArgs args, InstDesc single) {
-  static_assert(sizeof(P) == 4, "the FP64 top-separator kernel serves FP32 pools");
+  static_assert(sizeof(P) == 4, "the double-FP32 top-separator kernel serves FP32 pools");
   using C = TileCfg<float, NP, R>;
   using RC = RootCfg<NP>;
   constexpr int NT = C::NT, LD = RC::LD, NE = RC::NE;
   static_assert(NT >= 64, "a full look-ahead warp and at least one update warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *Sd = reinterpret_cast<double *>(smem_raw);  // NP x LD, upper triangle used
-  double *dinv = Sd + NP * LD;                         // 1 / U_kk
+  float2 *S2 = reinterpret_cast<float2 *>(smem_raw);  // NP x LD (hi, lo) pairs, upper triangle used
+  float2 *dinv = S2 + NP * LD;                         // 1 / U_kk
   unsigned short *tab = reinterpret_cast<unsigned short *>(dinv + NP);  // element list (i | j << 7)
-  float *sA = reinterpret_cast<float *>(dinv + NP);                     // P_a (aliases the list)
+  float *sA = reinterpret_cast<float *>(dinv + NP);                      // P_a (aliases the list)
+  auto ld = [&](int q) {
+    const float2 v = S2[q];
+    return F2{v.x, v.y};
+  };
+  auto st = [&](int q, F2 v) { S2[q] = make_float2(v.hi, v.lo); };
 
   const FactorItem it = args.items[blockIdx.x];
   P *dpool = reinterpret_cast<P *>(args.dpool);
@@ -298,13 +350,21 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorA
   unsigned long long *info = args.info + it.inst;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // ---- S in FP64
+  // ---- S in double-FP32
   if constexpr (FIRST) {  // a single-node problem: the caller's D_1 (lower triangle valid)
     const S *uD = reinterpret_cast<const S *>(ins.D) + (size_t)it.node * ins.n * ins.n;
     for (int q = tid; q < NP * NP; q += NT) {
       const int i = q / NP, j = q % NP;
       if (i > j) continue;
-      Sd[i * LD + j] = (j < ins.n) ? (double)uD[(size_t)j * ins.n + i] : (i == j ? 1.0 : 0.0);
+      if (j < ins.n) {
+        const S v = uD[(size_t)j * ins.n + i];
+        const float h = convert_in<float, S>(v);
+        float l = 0.0f;
+        if constexpr (sizeof(S) == 8) l = f64_to_f32_rn(v - f32_to_f64(h));
+        st(i * LD + j, F2{h, l});
+      } else {
+        st(i * LD + j, F2{i == j ? 1.0f : 0.0f, 0.0f});
+      }
     }
   } else if (!RL && it.p_a >= 0) {
     block_to_smem_async<C>(sA, epool + it.p_a);
@@ -318,13 +378,13 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorA
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < R; ++c) Sd[(r0 + r) * LD + c0 + c] = f32_to_f64(a[r][c]);
+        for (int c = 0; c < R; ++c) st((r0 + r) * LD + c0 + c, F2{a[r][c], 0.0f});
     }
   } else {
     const P *g = dpool + it.d_self;
     for (int q = tid; q < NP * NP; q += NT) {
       const int i = q / NP, j = q % NP;
-      if (i <= j) Sd[i * LD + j] = f32_to_f64(__ldcg(g + q));
+      if (i <= j) st(i * LD + j, F2{__ldcg(g + q), 0.0f});
     }
   }
   __syncthreads();  // sA is dead from here on
@@ -333,51 +393,43 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorA
     if (i <= j) tab[RC::row_off(i) + j - i] = (unsigned short)(i | (j << 7));
   }
 
-  // ---- row 0
-  if (warp == 0) {
-    double d = Sd[0];
-    if (!(d > 0.0)) {
-      if (lane == 0 && info) atomicMin(info, pack_info(it.node, 0));
-      d = 1.0;
+  // pivot of row r (already updated by every earlier row): U_rr = sqrt(d), row r scaled by 1/sqrt(d)
+  auto factor_row = [&](int r) {
+    F2 d = ld(r * LD + r);
+    if (!(d.hi > 0.0f)) {
+      if (lane == 0 && info) atomicMin(info, pack_info(it.node, r));
+      d = F2{1.0f, 0.0f};
     }
-    const double rs = rsqrt(d);
+    const F2 rs = f2_rsqrt(d);
     __syncwarp();
-    for (int j = 1 + lane; j < NP; j += 32) Sd[j] *= rs;
+    for (int j = r + 1 + lane; j < NP; j += 32) st(r * LD + j, f2_mul(ld(r * LD + j), rs));
     if (lane == 0) {
-      Sd[0] = d * rs;
-      dinv[0] = rs;
+      st(r * LD + r, f2_mul(d, rs));
+      dinv[r] = make_float2(rs.hi, rs.lo);
     }
-  }
+  };
+
+  // ---- row 0
+  if (warp == 0) factor_row(0);
   __syncthreads();
 
   // ---- steps k = 0 .. NP-2: row k is final at the start of step k
 #pragma unroll 1
   for (int k = 0; k + 1 < NP; ++k) {
-    const double *Uk = Sd + k * LD;
+    const int uk = k * LD;
     if (warp == 0) {
-      double *row = Sd + (k + 1) * LD;
-      const double ukk1 = Uk[k + 1];
-      for (int j = k + 1 + lane; j < NP; j += 32) row[j] = fma(-ukk1, Uk[j], row[j]);
+      const int r1 = (k + 1) * LD;
+      const F2 ukk1 = ld(uk + k + 1);
+      for (int j = k + 1 + lane; j < NP; j += 32) st(r1 + j, f2_sub_mul(ld(r1 + j), ukk1, ld(uk + j)));
       __syncwarp();
-      double d = row[k + 1];
-      if (!(d > 0.0)) {
-        if (lane == 0 && info) atomicMin(info, pack_info(it.node, k + 1));
-        d = 1.0;
-      }
-      const double rs = rsqrt(d);
-      __syncwarp();
-      for (int j = k + 2 + lane; j < NP; j += 32) row[j] *= rs;
-      if (lane == 0) {
-        row[k + 1] = d * rs;
-        dinv[k + 1] = rs;
-      }
+      factor_row(k + 1);
     } else {
       const int base = RC::row_off(k + 2);
 #pragma unroll 4
       for (int q = base + tid - 32; q < NE; q += NT - 32) {
         const unsigned e = tab[q];
         const int i = e & 127, j = e >> 7;
-        Sd[i * LD + j] = fma(-Uk[i], Uk[j], Sd[i * LD + j]);
+        st(i * LD + j, f2_sub_mul(ld(i * LD + j), ld(uk + i), ld(uk + j)));
       }
     }
     __syncthreads();
@@ -387,7 +439,8 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorA
   P *g = dpool + it.d_self;
   for (int q = tid; q < NP * NP; q += NT) {
     const int i = q / NP, j = q % NP;
-    g[q] = i <= j ? f64_to_f32_rn(Sd[i * LD + j]) : P(0);
+    const float2 v = S2[i * LD + j];
+    g[q] = i <= j ? __fadd_rn(v.x, v.y) : P(0);
   }
 }
 

@@ -26,7 +26,7 @@ struct KernelSet {
   const void *fac_first = nullptr, *fac_rest = nullptr;
   int fac_threads = 0;
   size_t fac_smem = 0;
-  // FP64 top-separator Cholesky for the mixed path (T = double, pools FP32)
+  // double-FP32 top-separator Cholesky for the mixed path (T = double, pools FP32)
   const void *root_first = nullptr, *root_rest = nullptr;
   int root_threads = 0;
   size_t root_smem = 0;
@@ -40,7 +40,7 @@ struct KernelSet {
   FlowVariant flow_v[kFlowVariants];
   int n_flow_v = 0, flow_default = 0;
   bool tensor_cores = false;  // level elimination products on tcgen05 (TF32)
-  // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, FP64 root
+  // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, double-FP32 root
   const void *pack_matrix = nullptr, *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
   // solve
   const void *fwd = nullptr, *bwd = nullptr;

@@ -1,5 +1,5 @@
 // Kernel set: FP64 inputs, FP32 factor with the level-elimination products on
-// tcgen05 (TF32), FP32 correction solves, FP64 top-separator Cholesky; padded
+// tcgen05 (TF32), FP32 correction solves, double-FP32 top-separator Cholesky; padded
 // block size 128.
 #include "btc_make.cuh"
 #include "btc_tc.cuh"
