@@ -585,7 +585,11 @@ def main():
         btc.btc_factor_solve_host(pe, Dh, Bh, bh, xh, m, TOL, 30)
         e2e_ts.append(time.perf_counter() - t0)
     e2e_v = 1.0 / statistics.mean(e2e_ts)
-    h2d = D.nbytes + B.nbytes + b.nbytes
+    # the level-1 loads read D's lower triangles (and, in the diagonal 4x4 tiles of the blocks they read as
+    # a tile of D_(e+1), the few entries above the diagonal there) and all of B from the pinned buffers;
+    # b is copied
+    R = 4
+    h2d = (N * n * (n + 1) // 2 + (N // 2) * (n // R) * (R * (R - 1) // 2)) * D.itemsize + B.nbytes + b.nbytes
     d2h = b.nbytes
 
     batched = (batched_measure(btc, gen, torch, max(3, min(10, args.steps // 5)), stream, flush)
@@ -643,7 +647,8 @@ def main():
                      "algorithmic": f"{fused_flops:.4g} flop per launch (Alg. 5 Table 1 costs without the top "
                                     f"separator + Alg. 7 forward sweep)"},
         "e2e": {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "entry_point": "btc_factor_solve_host (pinned host buffers)"},
+                "entry_point": "btc_factor_solve_host (pinned host buffers; the level-1 eliminations read D, B "
+                               "over the CPU-GPU link while level 1 runs)"},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
         "peaks_source": pk_kind,

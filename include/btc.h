@@ -311,11 +311,19 @@ int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const d
                              double tol, int maxit, int *iters, double *relres);
 
 /*
- * End-to-end call on HOST buffers: copies D, B (element type as for
+ * End-to-end call on HOST buffers: brings D, B (element type as for
  * btc_factor) and b (FP64 for BTC_F64 / BTC_MIXED_F32, FP32 for BTC_F32)
- * to plan-owned device buffers, factors, solves (refined to tol for BTC_F64
+ * into plan-owned device buffers, factors, solves (refined to tol for BTC_F64
  * and BTC_MIXED_F32; one solve for BTC_F32) and copies the solution to x.
- * b, x: [N*n][nrhs]. Synchronous. Pinned host memory gives the fastest copies.
+ * b, x: [N*n][nrhs]. Synchronous. When D and B are page-locked host memory
+ * (cudaHostAlloc, cudaHostRegister, a pinned tensor) and N >= 2 on the FP64
+ * or FP32-factor mixed path (hybrid variant, persistent schedule, no tensor
+ * cores), they are not copied up front: the level-1 eliminations read them
+ * over the CPU-GPU link (of each D_i only its lower triangle) while the rest
+ * of level 1 runs, and write the device copies the FP64 residuals use; the
+ * factor and solution are the same as with device inputs. Otherwise (pageable
+ * memory, other paths) D and B are copied first. D and B must stay unchanged
+ * during the call.
  */
 int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void *b, void *x, int nrhs, double tol,
                           int maxit, int *iters, double *relres);

@@ -158,6 +158,9 @@ struct btc_plan_s {
   std::vector<double> gkey;
   unsigned long long *trace_fac = nullptr, *trace_solve = nullptr;  // caller-owned trace buffers
   unsigned long long *phase = nullptr;                               // caller-owned per-node phase stamps
+  // btc_factor_solve_host with host-resident D and B: the level-1 loads read them over the CPU-GPU link
+  // and fill the staging copies s_D, s_B (which the factorization is given) for the residuals
+  const void *ingD = nullptr, *ingB = nullptr;
   // optional per-kernel-class event timing (btc_plan_set_timing)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing_pending[BTC_TIMING_CLASSES];
@@ -296,6 +299,20 @@ static int decode_info(btc_plan_s *p, int *block, int *col) {
 }
 
 // Persistent factor kernels of variant v with c CTAs per SM (0: as many as fit).
+// Instance descriptor of a factorization of (D, B); while btc_factor_solve_host
+// ingests host-resident inputs, the staging copies stand for them and the
+// level-1 loads read the host arrays and fill the copies.
+static InstDesc inst_desc(const btc_plan_s *p, const void *D, const void *B) {
+  InstDesc d{D, B, p->N, p->n};
+  if (p->ingD && D == p->s_D && B == p->s_B) {
+    d.D = p->ingD;
+    d.B = p->ingB;
+    d.Dm = p->s_D;
+    d.Bm = p->s_B;
+  }
+  return d;
+}
+
 // Configuration of the interlaced factor + forward launch: residency variant v,
 // c CTAs per SM (0 or too many: as many as fit).
 static void apply_inter_config(btc_plan_s *p, int v, int c) {
@@ -405,7 +422,7 @@ static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
   a.inst = nullptr;  // single instance: the descriptor travels by value in the kernel parameters
   a.items = p->d_fac;
   a.count = nflow;
-  InstDesc d{D, B, p->N, p->n};
+  const InstDesc d = inst_desc(p, D, B);
   int rc = BTC_OK;
   const bool rl = p->variant == BTC_VARIANT_RIGHT_LOOKING;
   if (rl && (rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n))) return rc;
@@ -439,7 +456,7 @@ static int launch_interlaced(btc_plan_s *p, const void *D, const void *B, int m)
   a.inst = nullptr;
   a.items = p->d_fac;
   a.count = p->n_inter;
-  InstDesc d{D, B, p->N, p->n};
+  const InstDesc d = inst_desc(p, D, B);
   BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
   BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_inter, p->stream));
@@ -547,7 +564,7 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   a.status = p->d_status;
   a.phase = p->phase;
   a.inst = nullptr;
-  InstDesc d{D, B, p->N, p->n};
+  const InstDesc d = inst_desc(p, D, B);
   const bool mixed_root = dtype_mixed(p->dtype);
   const int last = p->hp.levels - 1;
   if (p->sched == BTC_SCHED_FLOW) {
@@ -688,7 +705,7 @@ static std::vector<double> refine_graph_key(const btc_plan_s *p, const void *D, 
   return {(double)(uintptr_t)D, (double)(uintptr_t)B, (double)(uintptr_t)b, (double)(uintptr_t)x, (double)m, tol,
           (double)maxit,        (double)p->flow_var,  (double)p->ctas_per_sm, (double)(uintptr_t)p->trace_fac,
           (double)(uintptr_t)p->trace_solve, (double)(uintptr_t)p->phase, (double)p->inter_var,
-          (double)p->inter_ctas};
+          (double)p->inter_ctas, (double)(uintptr_t)p->ingD, (double)(uintptr_t)p->ingB};
 }
 
 // Capture one refined factor + solve of m <= max_cols columns as an executable
@@ -1141,6 +1158,17 @@ int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const d
   return refined_impl(p, b, x, nrhs, tol, maxit, iters, relres, true);
 }
 
+// Device address of page-locked host memory (registered or allocated through CUDA), or null.
+static const void *device_view_of_host(const void *h) {
+  if (!h) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void *b, void *x, int nrhs, double tol,
                           int maxit, int *iters, double *relres) {
   if (!p || !D || (p->N > 1 && !B) || !b || !x || nrhs < 1) return fail(BTC_ERR_ARG, "btc_factor_solve_host: args");
@@ -1159,8 +1187,23 @@ int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void
     BTC_CUDA(cudaMalloc(&p->s_x, rbytes));
     p->s_rhs_bytes = rbytes;
   }
-  BTC_CUDA(cudaMemcpyAsync(p->s_D, D, nb * p->N, cudaMemcpyHostToDevice, p->stream));
-  if (p->N > 1) BTC_CUDA(cudaMemcpyAsync(p->s_B, B, nb * (p->N - 1), cudaMemcpyHostToDevice, p->stream));
+  // D and B in page-locked host memory that the GPU addresses: the level-1 loads read them over the
+  // CPU-GPU link (D's lower triangles only) while the factorization runs, and fill s_D, s_B for the
+  // residuals; otherwise both are copied first
+  const void *hD = device_view_of_host(D), *hB = p->N > 1 ? device_view_of_host(B) : nullptr;
+  const bool ingest = p->dtype != BTC_F32 && p->N > 1 && hD && hB && !((((uintptr_t)hD) | ((uintptr_t)hB)) & 7) &&
+                      p->variant == BTC_VARIANT_HYBRID && p->sched == BTC_SCHED_FLOW && !p->ks->tensor_cores;
+  struct IngestGuard {
+    btc_plan_s *p;
+    ~IngestGuard() { p->ingD = p->ingB = nullptr; }
+  } guard{p};
+  if (ingest) {
+    p->ingD = hD;
+    p->ingB = hB;
+  } else {
+    BTC_CUDA(cudaMemcpyAsync(p->s_D, D, nb * p->N, cudaMemcpyHostToDevice, p->stream));
+    if (p->N > 1) BTC_CUDA(cudaMemcpyAsync(p->s_B, B, nb * (p->N - 1), cudaMemcpyHostToDevice, p->stream));
+  }
   BTC_CUDA(cudaMemcpyAsync(p->s_b, b, rbytes, cudaMemcpyHostToDevice, p->stream));
   int rc = BTC_OK;
   if (p->dtype == BTC_F32) {

@@ -23,6 +23,10 @@ struct InstDesc {
   const void *D;  // user D [N][n][n] (source type)
   const void *B;  // user B [N-1][n][n]
   int N, n;
+  // optional: device copies that the level-1 loads fill with what they read (the lower triangles of
+  // D, all of B), when D and B are host memory read over the CPU-GPU link
+  void *Dm = nullptr;
+  void *Bm = nullptr;
 };
 
 struct FactorArgs {
@@ -111,11 +115,16 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
   phase_stamp(args.phase, e, 0);
 
   if constexpr (FIRST) {
-    // level 1: the caller's blocks, converted and padded on the way in
-    user_to_smem<C>(sS, uD + e * ubs, ins.n, true, T(1));                     // S[i][j] = D_e[j][i]
-    if (has_up) user_to_smem<C>(sA, uB + (e - 1) * ubs, ins.n, false, T(0));  // S(e, e-1) = B_{e-1}
-    if (has_dn) user_to_smem<C>(sB, uB + e * ubs, ins.n, true, T(0));         // S(e, e+1) = B_e^T
-    if (has_next && upper_tile) tile_from_user<C>(d, uD + (e + 1) * ubs, ins.n, r0, c0, true, T(1));
+    // level 1: the caller's blocks, converted and padded on the way in (of D_e only its lower
+    // triangle, the upper triangle of S)
+    S *mD = reinterpret_cast<S *>(ins.Dm), *mB = reinterpret_cast<S *>(ins.Bm);
+    user_to_smem<C>(sS, uD + e * ubs, ins.n, true, T(1), true, mD ? mD + e * ubs : nullptr);  // S[i][j] = D_e[j][i]
+    if (has_up)  // S(e, e-1) = B_{e-1}
+      user_to_smem<C>(sA, uB + (e - 1) * ubs, ins.n, false, T(0), false, mB ? mB + (e - 1) * ubs : nullptr);
+    if (has_dn)  // S(e, e+1) = B_e^T
+      user_to_smem<C>(sB, uB + e * ubs, ins.n, true, T(0), false, mB ? mB + e * ubs : nullptr);
+    if (has_next && upper_tile)
+      tile_from_user<C>(d, uD + (e + 1) * ubs, ins.n, r0, c0, true, T(1), mD ? mD + (e + 1) * ubs : nullptr);
     __syncthreads();
   } else {
     const bool pa = !RL && it.p_a >= 0, pb = !RL && it.p_b >= 0;

@@ -215,10 +215,13 @@ __device__ __forceinline__ void smem_to_block(P *g, const T *s, bool lower_zero)
 
 // Caller's block (n x n row-major, type S) -> padded shared memory (type T).
 // trans: element (i, k) of the result is src(k, i). Padding: `diag` on the
-// padded diagonal, 0 elsewhere. Each thread issues a chunk of loads before
-// converting any of them, so their latencies overlap.
+// padded diagonal, 0 elsewhere. lower: read only the source's lower triangle
+// (row >= column; the rest of the result is 0). mirror (optional): every
+// element read is also stored there at its source offset. Each thread issues
+// a chunk of loads before converting any of them, so their latencies overlap.
 template <class C, typename T, typename S>
-__device__ __forceinline__ void user_to_smem(T *s, const S *src, int n, bool trans, T diag) {
+__device__ __forceinline__ void user_to_smem(T *s, const S *src, int n, bool trans, T diag, bool lower = false,
+                                             S *mirror = nullptr) {
   constexpr int TOTAL = C::NP * C::NP;
   constexpr int ITER = (TOTAL + C::NT - 1) / C::NT;
   constexpr int CHMAX = 32 / (int)sizeof(S);  // 32 bytes of loads in flight per thread
@@ -231,14 +234,16 @@ __device__ __forceinline__ void user_to_smem(T *s, const S *src, int n, bool tra
       // consecutive threads read consecutive source elements
       const int q = threadIdx.x + (i0 + u) * C::NT;
       const int a = q / C::NP, b = q % C::NP;  // source row a, column b
-      v[u] = (q < TOTAL && a < n && b < n) ? __ldg(src + (size_t)a * n + b) : S(0);
+      v[u] = (q < TOTAL && a < n && b < n && (!lower || a >= b)) ? __ldg(src + (size_t)a * n + b) : S(0);
     }
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
       const int q = threadIdx.x + (i0 + u) * C::NT;
       if (q >= TOTAL) continue;
       const int a = q / C::NP, b = q % C::NP;
-      const T x = (a < n && b < n) ? convert_in<T, S>(v[u]) : (a == b ? diag : T(0));
+      const bool in = a < n && b < n;
+      if (mirror && in && (!lower || a >= b)) mirror[(size_t)a * n + b] = v[u];
+      const T x = in ? convert_in<T, S>(v[u]) : (a == b ? diag : T(0));
       if (trans) s[b * C::LD + a] = x;
       else s[a * C::LD + b] = x;
     }
@@ -246,11 +251,12 @@ __device__ __forceinline__ void user_to_smem(T *s, const S *src, int n, bool tra
 }
 
 // Caller's block (n x n row-major, type S) -> one register tile, padded like
-// user_to_smem. trans: element (i, k) is src(k, i). Each tile row's loads
-// precede its conversions.
+// user_to_smem. trans: element (i, k) is src(k, i). mirror (optional): every
+// element read is also stored there at its source offset. Each tile row's
+// loads precede its conversions.
 template <class C, typename T, typename S>
 __device__ __forceinline__ void tile_from_user(T (&a)[C::R][C::R], const S *src, int n, int r0, int c0, bool trans,
-                                               T diag) {
+                                               T diag, S *mirror = nullptr) {
 #pragma unroll
   for (int r = 0; r < C::R; ++r) {
     S v[C::R];
@@ -263,6 +269,7 @@ __device__ __forceinline__ void tile_from_user(T (&a)[C::R][C::R], const S *src,
 #pragma unroll
     for (int c = 0; c < C::R; ++c) {
       const int k = c0 + c;
+      if (mirror && i < n && k < n) mirror[trans ? (size_t)k * n + i : (size_t)i * n + k] = v[c];
       a[r][c] = (i < n && k < n) ? convert_in<T, S>(v[c]) : ((i == k) ? diag : T(0));
     }
   }
