@@ -7,7 +7,7 @@ A step = btc_factor_solve_refined: the factorization of Alg. 5 with the
 forward substitution of Alg. 7 interlaced in the same persistent launch, the
 backward substitution, then FP64 residuals and correction solves until
 ||r|| <= 1e-10 ||A|| ||x||, in the chosen form: FP32 factor and correction
-solves, double-FP32 root Cholesky, residual and update. The plain FP64 GPU path
+solves, double-FP32 root Cholesky, FP64 residual and update. The plain FP64 GPU path
 (same kernels in FP64, no refinement needed) is timed beside it.
 
 Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
