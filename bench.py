@@ -325,10 +325,13 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
 
 def large_block_measure(btc, gen, torch, stream, flush, steps=5):
     """Config: N=4096, n=128, delta in {1, 1e-3, 1e-6}: the FP32 factor on CUDA cores (BTC_MIXED_F32)
-    and with the level-elimination products on tcgen05 tensor cores (BTC_MIXED_TF32), both with the FP64
-    root, residual and refinement to 1e-10 (the relative residual reached is the stated error)."""
+    and with the level-elimination products on tcgen05 tensor cores (BTC_MIXED_TF32), both with the
+    double-FP32 root (and the TF32 form also with the FP64 root), FP64 residual and refinement to 1e-10
+    (the relative residual reached is the stated error)."""
     out = {"N": 4096, "n": 128}
-    forms = (("mixed_f32_ffma", btc.MIXED_F32), ("mixed_tf32_tcgen05", btc.MIXED_TF32))
+    forms = (("mixed_f32_ffma", btc.MIXED_F32, btc.ROOT_DOUBLE_FP32),
+             ("mixed_tf32_tcgen05", btc.MIXED_TF32, btc.ROOT_DOUBLE_FP32),
+             ("mixed_tf32_tcgen05_root_fp64", btc.MIXED_TF32, btc.ROOT_FP64))
     for delta in (1.0, 1e-3, 1e-6):
         D, B = gen.bt_random_torch(4096, 128, delta=delta, seed=7)
         g = torch.Generator(device="cuda")
@@ -336,8 +339,9 @@ def large_block_measure(btc, gen, torch, stream, flush, steps=5):
         b = torch.randn((4096 * 128, 1), generator=g, device="cuda", dtype=torch.float64)
         x = torch.zeros_like(b)
         res = {}
-        for name, dt in forms:
+        for name, dt, root in forms:
             p = btc.btc_plan(4096, 128, dt, stream)
+            btc.btc_plan_set_root_precision(p, root)
             info = btc.btc_plan_query(p)
             ts, tf = [], []
             with torch.cuda.stream(stream):
@@ -546,6 +550,18 @@ def main():
     ms, value = replica_throughput(statistics.mean(ts), world)
     assert rel <= TOL, rel
 
+    # ---- the same step with the FP64 top-separator Cholesky (the option beside the double-FP32 default)
+    pr = btc.btc_plan(N, n, btc.MIXED_F32, stream)
+    btc.btc_plan_set_root_precision(pr, btc.ROOT_FP64)
+
+    def root64_step():
+        return btc.btc_factor_solve_refined(pr, Dd, Bd, bd, xd, m, tol=TOL, maxit=30)
+
+    timed_steps(pr, 3, root64_step)
+    ts64r, (it64r, rel64r, _) = timed_steps(pr, max(10, min(100, args.steps // 4)), root64_step)
+    root_fp64_option = {"ms_per_step": statistics.mean(ts64r), "refine_iters": it64r, "relres": rel64r}
+    pr.free()
+
     # ---- per-kernel device times of the same step (library events on the plan's stream, L2 flushed),
     # for the phase split and the roofline of the dominant kernel
     n_phase = max(10, min(200, args.steps // 2))
@@ -639,6 +655,7 @@ def main():
         "speedup_vs_plain_f64": ms64 / ms,
         "phases_ms": phase,
         "flow_config": dict(zip(("resident_cap", "ctas_per_sm", "tuned"), btc.btc_plan_tuning_interlaced(pm))),
+        "root_fp64_option": root_fp64_option,
         "roofline": {"kernel": "k_factor_fwd_flow (interlaced factor + forward sweep, one launch per step)",
                      "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,

@@ -151,6 +151,19 @@ enum btc_variant { BTC_VARIANT_HYBRID = 0, BTC_VARIANT_RIGHT_LOOKING = 1 };
 int btc_plan_set_variant(btc_plan_t p, int variant);
 
 /*
+ * Precision of the top-separator Cholesky of the mixed paths (BTC_MIXED_F32,
+ * BTC_MIXED_TF32; other dtypes ignore it). BTC_ROOT_DOUBLE_FP32 (default):
+ * double-FP32 arithmetic (pairs of FP32, about 48 significant bits) on the
+ * FP32 pipe; BTC_ROOT_FP64: FP64 arithmetic. Either way the Schur complement
+ * comes from the FP32 pool and the factor is rounded back to it, so the two
+ * agree up to rounding ties of that last step; the FP64 form is slower on
+ * this GPU (its FP64 pipe issues two lanes per clock per SM). Takes effect at
+ * the next factorization. Batched plans use the default.
+ */
+enum btc_root_precision { BTC_ROOT_DOUBLE_FP32 = 0, BTC_ROOT_FP64 = 1 };
+int btc_plan_set_root_precision(btc_plan_t p, int precision);
+
+/*
  * Device-side trace of the persistent launches (for profiling; off by
  * default). factor_trace / solve_trace: caller-owned device buffers of
  * 4 * (number of work items) uint64 each (factor items = N; solve items =

@@ -75,6 +75,7 @@ _SIGS = {
     "btc_plan_set_stream": [_vp, _vp],
     "btc_plan_set_variant": [_vp, ctypes.c_int],
     "btc_plan_set_trace": [_vp, _vp, _vp],
+    "btc_plan_set_root_precision": [_vp, ctypes.c_int],
     "btc_plan_set_phase_trace": [_vp, _vp],
     "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
     "btc_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_int64)],
@@ -430,6 +431,12 @@ def btc_plan_set_phase_trace(plan, phase):
 
 
 VARIANT_HYBRID, VARIANT_RIGHT_LOOKING = 0, 1
+ROOT_DOUBLE_FP32, ROOT_FP64 = 0, 1
+
+
+def btc_plan_set_root_precision(plan, precision):
+    """Top-separator Cholesky of the mixed paths in double-FP32 (ROOT_DOUBLE_FP32, default) or FP64."""
+    return _check(load().btc_plan_set_root_precision(plan.h, precision))
 
 
 def btc_plan_set_variant(plan, variant):

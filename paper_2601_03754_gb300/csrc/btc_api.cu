@@ -161,6 +161,7 @@ struct btc_plan_s {
   // btc_factor_solve_host with host-resident D and B: the level-1 loads read them over the CPU-GPU link
   // and fill the staging copies s_D, s_B (which the factorization is given) for the residuals
   const void *ingD = nullptr, *ingB = nullptr;
+  int root_prec = BTC_ROOT_DOUBLE_FP32;  // top-separator Cholesky of the mixed path
   // optional per-kernel-class event timing (btc_plan_set_timing)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing_pending[BTC_TIMING_CLASSES];
@@ -589,7 +590,9 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   if (mixed_root) {
     a.items = p->d_fac + p->fac_off[last];
     a.count = 1;
-    const void *fn = rl ? k.root_rl : (last == 0 ? k.root_first : k.root_rest);
+    const bool f64 = p->root_prec == BTC_ROOT_FP64;
+    const void *fn = rl ? (f64 ? k.root64_rl : k.root_rl)
+                        : (last == 0 ? (f64 ? k.root64_first : k.root_first) : (f64 ? k.root64_rest : k.root_rest));
     KernelTimer timer(p, BTC_TIME_ROOT);
     if ((rc = launch_n(fn, 1, k.root_threads, k.root_smem, p->stream, a, d))) return rc;
   }
@@ -705,7 +708,8 @@ static std::vector<double> refine_graph_key(const btc_plan_s *p, const void *D, 
   return {(double)(uintptr_t)D, (double)(uintptr_t)B, (double)(uintptr_t)b, (double)(uintptr_t)x, (double)m, tol,
           (double)maxit,        (double)p->flow_var,  (double)p->ctas_per_sm, (double)(uintptr_t)p->trace_fac,
           (double)(uintptr_t)p->trace_solve, (double)(uintptr_t)p->phase, (double)p->inter_var,
-          (double)p->inter_ctas, (double)(uintptr_t)p->ingD, (double)(uintptr_t)p->ingB};
+          (double)p->inter_ctas, (double)(uintptr_t)p->ingD, (double)(uintptr_t)p->ingB,
+          (double)p->root_prec};
 }
 
 // Capture one refined factor + solve of m <= max_cols columns as an executable
@@ -1004,6 +1008,8 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   // allow the large dynamic shared memory the kernels use
   if ((rc = set_smem(ks.fac_first, ks.fac_smem)) || (rc = set_smem(ks.fac_rest, ks.fac_smem)) ||
       (rc = set_smem(ks.root_first, ks.root_smem)) || (rc = set_smem(ks.root_rest, ks.root_smem)) ||
+      (rc = set_smem(ks.root64_first, ks.root_smem)) || (rc = set_smem(ks.root64_rest, ks.root_smem)) ||
+      (rc = set_smem(ks.root64_rl, ks.root_smem)) ||
       (rc = set_smem(ks.fwd, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.bwd, ks.bwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.resid, residual_smem_bytes(n, kMaxCols))) ||
@@ -1050,6 +1056,13 @@ int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace) {
 int btc_plan_set_phase_trace(btc_plan_t p, void *phase) {
   if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_phase_trace: NULL plan");
   p->phase = (unsigned long long *)phase;
+  return BTC_OK;
+}
+
+int btc_plan_set_root_precision(btc_plan_t p, int precision) {
+  if (!p || (precision != BTC_ROOT_DOUBLE_FP32 && precision != BTC_ROOT_FP64))
+    return fail(BTC_ERR_ARG, "btc_plan_set_root_precision: invalid arguments");
+  p->root_prec = precision;
   return BTC_OK;
 }
 

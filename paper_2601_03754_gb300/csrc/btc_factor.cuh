@@ -453,6 +453,126 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorA
   }
 }
 
+// The same top-separator factorization in FP64 (btc_plan_set_root_precision):
+// S from the FP32 pool (or the caller's FP64 block when the problem is one
+// node) in FP64 shared memory, the same dense-list right-looking Cholesky with
+// a look-ahead warp, FP64 square roots, the result rounded to the FP32 pool.
+// On this GPU the FP64 pipe issues two lanes per clock per SM and a masked
+// lane costs as much as an active one, which is why the list form avoids
+// single-warp panels and tile masks here too.
+template <typename P, typename S, int NP, int R, bool FIRST, bool RL>
+__global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol_f64(FactorArgs args, InstDesc single) {
+  static_assert(sizeof(P) == 4, "the FP64 top-separator kernel serves FP32 pools");
+  using C = TileCfg<float, NP, R>;
+  using RC = RootCfg<NP>;
+  constexpr int NT = C::NT, LD = RC::LD, NE = RC::NE;
+  static_assert(NT >= 64, "a full look-ahead warp and at least one update warp");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *Sd = reinterpret_cast<double *>(smem_raw);  // NP x LD, upper triangle used
+  double *dinv = Sd + NP * LD;                         // 1 / U_kk
+  unsigned short *tab = reinterpret_cast<unsigned short *>(dinv + NP);  // element list (i | j << 7)
+  float *sA = reinterpret_cast<float *>(dinv + NP);                     // P_a (aliases the list)
+
+  const FactorItem it = args.items[blockIdx.x];
+  P *dpool = reinterpret_cast<P *>(args.dpool);
+  const P *epool = reinterpret_cast<const P *>(args.epool);
+  const InstDesc ins = args.inst ? args.inst[it.inst] : single;
+  unsigned long long *info = args.info + it.inst;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // ---- S in FP64
+  if constexpr (FIRST) {  // a single-node problem: the caller's D_1 (lower triangle valid)
+    const S *uD = reinterpret_cast<const S *>(ins.D) + (size_t)it.node * ins.n * ins.n;
+    for (int q = tid; q < NP * NP; q += NT) {
+      const int i = q / NP, j = q % NP;
+      if (i > j) continue;
+      Sd[i * LD + j] = (j < ins.n) ? (double)uD[(size_t)j * ins.n + i] : (i == j ? 1.0 : 0.0);
+    }
+  } else if (!RL && it.p_a >= 0) {
+    block_to_smem_async<C>(sA, epool + it.p_a);
+    const int r0 = (tid / C::TXN) * R, c0 = (tid % C::TXN) * R;
+    float a[R][R];
+    if (c0 >= r0) tile_from_pool<C>(a, dpool + it.d_self, r0, c0);
+    cp_async_commit_wait_all();
+    __syncthreads();
+    if (c0 >= r0) {
+      tile_sub_xty<C, NP>(a, sA, sA, r0, c0);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < R; ++c) Sd[(r0 + r) * LD + c0 + c] = f32_to_f64(a[r][c]);
+    }
+  } else {
+    const P *g = dpool + it.d_self;
+    for (int q = tid; q < NP * NP; q += NT) {
+      const int i = q / NP, j = q % NP;
+      if (i <= j) Sd[i * LD + j] = f32_to_f64(__ldcg(g + q));
+    }
+  }
+  __syncthreads();  // sA is dead from here on
+  for (int q = tid; q < NP * NP; q += NT) {
+    const int i = q / NP, j = q % NP;
+    if (i <= j) tab[RC::row_off(i) + j - i] = (unsigned short)(i | (j << 7));
+  }
+
+  // ---- row 0
+  if (warp == 0) {
+    double d = Sd[0];
+    if (!(d > 0.0)) {
+      if (lane == 0 && info) atomicMin(info, pack_info(it.node, 0));
+      d = 1.0;
+    }
+    const double rs = rsqrt(d);
+    __syncwarp();
+    for (int j = 1 + lane; j < NP; j += 32) Sd[j] *= rs;
+    if (lane == 0) {
+      Sd[0] = d * rs;
+      dinv[0] = rs;
+    }
+  }
+  __syncthreads();
+
+  // ---- steps k = 0 .. NP-2: row k is final at the start of step k
+#pragma unroll 1
+  for (int k = 0; k + 1 < NP; ++k) {
+    const double *Uk = Sd + k * LD;
+    if (warp == 0) {
+      double *row = Sd + (k + 1) * LD;
+      const double ukk1 = Uk[k + 1];
+      for (int j = k + 1 + lane; j < NP; j += 32) row[j] = fma(-ukk1, Uk[j], row[j]);
+      __syncwarp();
+      double d = row[k + 1];
+      if (!(d > 0.0)) {
+        if (lane == 0 && info) atomicMin(info, pack_info(it.node, k + 1));
+        d = 1.0;
+      }
+      const double rs = rsqrt(d);
+      __syncwarp();
+      for (int j = k + 2 + lane; j < NP; j += 32) row[j] *= rs;
+      if (lane == 0) {
+        row[k + 1] = d * rs;
+        dinv[k + 1] = rs;
+      }
+    } else {
+      const int base = RC::row_off(k + 2);
+#pragma unroll 4
+      for (int q = base + tid - 32; q < NE; q += NT - 32) {
+        const unsigned e = tab[q];
+        const int i = e & 127, j = e >> 7;
+        Sd[i * LD + j] = fma(-Uk[i], Uk[j], Sd[i * LD + j]);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- U (zeros below the diagonal) -> FP32 pool
+  P *g = dpool + it.d_self;
+  for (int q = tid; q < NP * NP; q += NT) {
+    const int i = q / NP, j = q % NP;
+    g[q] = i <= j ? f64_to_f32_rn(Sd[i * LD + j]) : P(0);
+  }
+}
+
 // Packing pass of Alg. 6 (its first parallel loop): Dhat_v <- D_v for every
 // node (upper-form copy of the caller's lower triangle, identity padding) and
 // the level-1 slot of B_v in the orientation level 1 eliminates: slot k

@@ -26,8 +26,9 @@ struct KernelSet {
   const void *fac_first = nullptr, *fac_rest = nullptr;
   int fac_threads = 0;
   size_t fac_smem = 0;
-  // double-FP32 top-separator Cholesky for the mixed path (T = double, pools FP32)
+  // double-FP32 top-separator Cholesky for the mixed path (FP32 pools)
   const void *root_first = nullptr, *root_rest = nullptr;
+  const void *root64_first = nullptr, *root64_rest = nullptr, *root64_rl = nullptr;  // FP64 form (option)
   int root_threads = 0;
   size_t root_smem = 0;
   // persistent dataflow forms (all levels in one launch)

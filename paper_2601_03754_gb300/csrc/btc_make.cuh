@@ -49,6 +49,9 @@ KernelSet make_set() {
     k.root_first = (const void *)&k_root_chol<T, S, NP, R, true, false>;
     k.root_rest = (const void *)&k_root_chol<T, S, NP, R, false, false>;
     k.root_rl = (const void *)&k_root_chol<T, S, NP, R, false, true>;
+    k.root64_first = (const void *)&k_root_chol_f64<T, S, NP, R, true, false>;
+    k.root64_rest = (const void *)&k_root_chol_f64<T, S, NP, R, false, false>;
+    k.root64_rl = (const void *)&k_root_chol_f64<T, S, NP, R, false, true>;
     k.root_threads = TileCfg<float, NP, R>::NT;
     k.root_smem = root_smem_bytes<NP, R>();
   }
