@@ -324,6 +324,27 @@ int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const d
                              double tol, int maxit, int *iters, double *relres);
 
 /*
+ * GMRES-based iterative refinement (GMRES-IR; Carson and Higham 2018) on the
+ * current factorization, for one right-hand side: x0 = M^{-1} b, then per
+ * outer step r = b - Psi x in FP64 and, until ||r||_inf <= tol ||Psi||_inf
+ * ||x||_inf, the correction equation Psi d = r solved by GMRES on
+ * M^{-1} Psi d = M^{-1} r (M = the plan's FP32 or TF32 factor applied by the
+ * solve kernels, Psi applied in FP64; at most `restart` Arnoldi steps, stopped
+ * when the preconditioned residual falls by inner_tol), x += d. Unlike
+ * btc_solve_refined it converges when the factor is too inaccurate for
+ * classical refinement (condition number times the factor's error near or
+ * above 1, e.g. a TF32 factor of an ill-conditioned matrix). b, x: device
+ * FP64 [N*n]; needs an FP64 or mixed plan, factored (D, B kept as for
+ * btc_solve_refined). *outer: outer steps taken, *inner: Arnoldi steps in
+ * all, *relres: final relative residual (each may be NULL). Synchronous.
+ * Errors: BTC_ERR_ARG (restart outside 1..200, inner_tol outside (0, 1)),
+ * BTC_ERR_NOT_FACTORED, BTC_ERR_NOT_SPD, BTC_ERR_NOT_CONVERGED (x holds the
+ * last iterate).
+ */
+int btc_solve_gmres_ir(btc_plan_t p, const double *b, double *x, double tol, int max_outer, int restart,
+                       double inner_tol, int *outer, int *inner, double *relres);
+
+/*
  * End-to-end call on HOST buffers: brings D, B (element type as for
  * btc_factor) and b (FP64 for BTC_F64 / BTC_MIXED_F32, FP32 for BTC_F32)
  * into plan-owned device buffers, factors, solves (refined to tol for BTC_F64

@@ -75,6 +75,8 @@ _SIGS = {
     "btc_plan_set_stream": [_vp, _vp],
     "btc_plan_set_variant": [_vp, ctypes.c_int],
     "btc_plan_set_trace": [_vp, _vp, _vp],
+    "btc_solve_gmres_ir": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip, _ip,
+                           _dp],
     "btc_plan_set_root_precision": [_vp, ctypes.c_int],
     "btc_plan_set_phase_trace": [_vp, _vp],
     "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
@@ -307,6 +309,16 @@ def btc_factor_solve_host(plan, D, B, b, x, nrhs, tol=1e-10, maxit=20):
     rc = _check(load().btc_factor_solve_host(plan.h, _ptr(D), _ptr(B), _ptr(b), _ptr(x), nrhs, tol, maxit,
                                              ctypes.byref(it), ctypes.byref(rel)), (ERR_NOT_CONVERGED,))
     return it.value, rel.value, rc
+
+
+def btc_solve_gmres_ir(plan, b, x, tol=1e-10, max_outer=20, restart=30, inner_tol=1e-6, allow_not_converged=False):
+    """GMRES-IR on the plan's factor (one right-hand side): returns (outer steps, Arnoldi steps, relres, rc)."""
+    o, i = ctypes.c_int(0), ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    rc = _check(load().btc_solve_gmres_ir(plan.h, _ptr(b), _ptr(x), tol, max_outer, restart, inner_tol,
+                                          ctypes.byref(o), ctypes.byref(i), ctypes.byref(rel)), allow)
+    return o.value, i.value, rel.value, rc
 
 
 def btc_info(plan):

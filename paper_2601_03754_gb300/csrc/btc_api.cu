@@ -17,6 +17,7 @@
 #include "btc_factor.cuh"
 #include "btc_internal.h"
 #include "btc_kernels.h"
+#include "btc_krylov.cuh"
 #include "btc_solve.cuh"
 #include "btc_runtime.h"
 
@@ -162,6 +163,8 @@ struct btc_plan_s {
   // and fill the staging copies s_D, s_B (which the factorization is given) for the residuals
   const void *ingD = nullptr, *ingB = nullptr;
   int root_prec = BTC_ROOT_DOUBLE_FP32;  // top-separator Cholesky of the mixed path
+  double *kry = nullptr;  // GMRES-IR workspace: basis, work and zero vectors, device scalars
+  size_t kry_cap = 0;     // its size in doubles
   // optional per-kernel-class event timing (btc_plan_set_timing)
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing_pending[BTC_TIMING_CLASSES];
@@ -600,6 +603,160 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   p->B = B;
   p->factored = true;
   p->anorm_valid = false;
+  return BTC_OK;
+}
+
+// GMRES-based iterative refinement (Carson and Higham, SIAM J. Sci. Comput.
+// 2018): the correction equation Psi d = r is solved by GMRES (no restart
+// within an outer step) on the left-preconditioned system M^{-1} Psi d = M^{-1} r, M = the plan's
+// low-precision factor, with Psi applied in FP64 (the residual kernel with
+// b = 0) and M^{-1} applied by the solve kernels in the factor's precision;
+// classical Gram-Schmidt with one reorthogonalization, Givens rotations on the
+// small Hessenberg matrix on the host. One right-hand side. Each outer step:
+// r = b - Psi x in FP64, stop at ||r|| <= tol ||Psi|| ||x||, then at most
+// `restart` Arnoldi steps until the preconditioned residual falls by
+// `inner_tol`, x += V y.
+static int gmres_ir_impl(btc_plan_s *p, const double *b, double *x, double tol, int max_outer, int restart,
+                         double inner_tol, int *outer, int *inner, double *relres) {
+  const KernelSet &k = *p->ks;
+  const int64_t L = (int64_t)p->N * p->n;
+  const size_t need = (size_t)(restart + 3) * L + 4 * (size_t)(restart + 2);
+  if (p->kry_cap < need) {
+    if (p->kry) cudaFree(p->kry);
+    p->kry = nullptr;
+    p->kry_cap = 0;
+    BTC_CUDA(cudaMalloc(&p->kry, need * sizeof(double)));
+    p->kry_cap = need;
+  }
+  double *V = p->kry;                        // restart + 1 basis vectors
+  double *w = V + (int64_t)(restart + 1) * L;  // work vector
+  double *zero = w + L;                       // b = 0 for products with Psi
+  double *dh1 = zero + L, *dh2 = dh1 + (restart + 2), *dnrm = dh2 + (restart + 2), *dy = dnrm + (restart + 2);
+  BTC_CUDA(cudaMemsetAsync(zero, 0, L * sizeof(double), p->stream));
+  int64_t base = 0;
+  int one = 1, c0 = 0, assign = 0, no_bound = 0;
+  const int gv = grid_for(L);
+  auto apply_precond = [&](const double *rhs_b, const double *xv, double *out, int with_anorm) -> int {
+    // y = rhs_b - Psi xv (FP64, rounded to the factor precision), y <- M^{-1} y, out = y (FP64)
+    int rc;
+    if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, 1), p->stream, p->d_y, (const double *)p->D,
+                       (const double *)p->B, xv, rhs_b, p->N, p->n, p->np, one, base, p->d_norms, with_anorm)) ||
+        (rc = run_solve(p, 1)) ||
+        (rc = launch_n(k.unpack, grid_for(L), 256, 0, p->stream, (void *)out, (const void *)p->d_y, p->N, p->n, p->np,
+                       one, one, c0, base, assign)))
+      return rc;
+    return BTC_OK;
+  };
+  // x0 = M^{-1} b
+  int rc;
+  if ((rc = launch_n(k.pack, grid_for((int64_t)p->N * p->np), 256, 0, p->stream, p->d_y, (const void *)b, p->N, p->n,
+                     p->np, one, one, c0, base)) ||
+      (rc = run_solve(p, 1)) ||
+      (rc = launch_n(k.unpack, grid_for(L), 256, 0, p->stream, (void *)x, (const void *)p->d_y, p->N, p->n, p->np, one,
+                     one, c0, base, assign)))
+    return rc;
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart);
+  std::vector<double> hbuf(2 * (restart + 2) + 1);
+  int it = 0, tot_inner = 0;
+  double rel = 0.0;
+  bool ok = false, info_checked = false;
+  for (;;) {
+    // r = b - Psi x (FP64) and z = M^{-1} r in V_0
+    const int with_anorm = p->anorm_valid ? 0 : 1;
+    BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, (2 + with_anorm) * sizeof(double), p->stream));
+    if ((rc = apply_precond(b, x, V, with_anorm))) return rc;
+    if ((rc = launch_n((const void *)&k_mdot, 1, kKryThreads, 0, p->stream, (const double *)V, L, (const double *)V, L,
+                       dnrm)))
+      return rc;
+    BTC_CUDA(cudaMemcpyAsync(p->h_rb, p->d_rb, sizeof(Readback), cudaMemcpyDeviceToHost, p->stream));
+    BTC_CUDA(cudaMemcpyAsync(hbuf.data(), dnrm, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    BTC_CUDA(cudaStreamSynchronize(p->stream));
+    p->anorm_valid = true;
+    if (!info_checked) {
+      int blk, col;
+      rc = decode_info(p, &blk, &col);
+      if (rc == BTC_ERR_TIMEOUT) return fail(rc, "factorization failed: a bounded device-side wait gave up");
+      if (rc) return fail(rc, "factorization failed: pivot of block %d, column %d not positive", blk, col);
+      info_checked = true;
+    }
+    const double rn = p->h_norms[0], xn = p->h_norms[1], an = p->h_norms[2];
+    rel = (an * xn > 0) ? rn / (an * xn) : rn;
+    if (!(rel == rel)) break;
+    if (rel <= tol) {
+      ok = true;
+      break;
+    }
+    if (it >= max_outer) break;
+    const double beta = std::sqrt(hbuf[0]);
+    if (!(beta > 0.0)) break;
+    if ((rc = launch_n((const void *)&k_vscale, gv, 256, 0, p->stream, V, (const double *)V, 1.0 / beta,
+                       (const double *)nullptr, L)))
+      return rc;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kdim = 0;
+    for (int j = 0; j < restart; ++j) {
+      double *Vj = V + (int64_t)j * L, *Vn = V + (int64_t)(j + 1) * L;
+      // w = M^{-1} Psi V_j: the residual kernel with b = 0 gives -Psi V_j
+      if ((rc = apply_precond(zero, Vj, w, no_bound)) ||
+          (rc = launch_n((const void *)&k_vscale, gv, 256, 0, p->stream, w, (const double *)w, -1.0,
+                         (const double *)nullptr, L)))
+        return rc;
+      // classical Gram-Schmidt, twice
+      const double *Vc = V;
+      if ((rc = launch_n((const void *)&k_mdot, j + 1, kKryThreads, 0, p->stream, Vc, L, (const double *)w, L, dh1)) ||
+          (rc = launch_n((const void *)&k_mupdate, gv, 256, 0, p->stream, w, Vc, L, (const double *)dh1, j + 1, L,
+                         -1.0)) ||
+          (rc = launch_n((const void *)&k_mdot, j + 1, kKryThreads, 0, p->stream, Vc, L, (const double *)w, L, dh2)) ||
+          (rc = launch_n((const void *)&k_mupdate, gv, 256, 0, p->stream, w, Vc, L, (const double *)dh2, j + 1, L,
+                         -1.0)) ||
+          (rc = launch_n((const void *)&k_mdot, 1, kKryThreads, 0, p->stream, (const double *)w, L, (const double *)w,
+                         L, dnrm)) ||
+          (rc = launch_n((const void *)&k_vscale, gv, 256, 0, p->stream, Vn, (const double *)w, 0.0,
+                         (const double *)dnrm, L)))
+        return rc;
+      BTC_CUDA(cudaMemcpyAsync(hbuf.data(), dh1, (2 * (restart + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                               p->stream));
+      BTC_CUDA(cudaStreamSynchronize(p->stream));
+      const double *h1 = hbuf.data(), *h2 = h1 + (restart + 2);
+      double *Hj = H.data() + (size_t)j * (restart + 1);  // column j
+      for (int i = 0; i <= j; ++i) Hj[i] = h1[i] + h2[i];
+      Hj[j + 1] = std::sqrt(std::max(h2[restart + 2], 0.0));
+      // earlier rotations, then a new one that zeroes H[j+1][j]
+      for (int i = 0; i < j; ++i) {
+        const double a = Hj[i], c = Hj[i + 1];
+        Hj[i] = cs[i] * a + sn[i] * c;
+        Hj[i + 1] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = Hj[j], c = Hj[j + 1], r = std::hypot(a, c);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? c / r : 0.0;
+      Hj[j] = r;
+      Hj[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++tot_inner;
+      kdim = j + 1;
+      if (std::fabs(g[j + 1]) <= inner_tol * beta || !(c > 0.0)) break;
+    }
+    // y = R^{-1} g (upper triangular kdim x kdim), x += V y
+    for (int i = kdim - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int q = i + 1; q < kdim; ++q) t -= H[(size_t)q * (restart + 1) + i] * y[q];
+      const double d = H[(size_t)i * (restart + 1) + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+    BTC_CUDA(cudaMemcpyAsync(dy, y.data(), kdim * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    if ((rc = launch_n((const void *)&k_mupdate, gv, 256, 0, p->stream, x, (const double *)V, L, (const double *)dy,
+                       kdim, L, 1.0)))
+      return rc;
+    BTC_CUDA(cudaStreamSynchronize(p->stream));  // y lives on the host stack frame
+    ++it;
+  }
+  if (outer) *outer = it;
+  if (inner) *inner = tot_inner;
+  if (relres) *relres = rel;
+  if (!ok) return fail(BTC_ERR_NOT_CONVERGED, "GMRES-IR stopped at relative residual %.3e", rel);
   return BTC_OK;
 }
 
@@ -1125,6 +1282,15 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
   return refined_impl(p, b, x, nrhs, tol, maxit, iters, relres, false);
 }
 
+int btc_solve_gmres_ir(btc_plan_t p, const double *b, double *x, double tol, int max_outer, int restart,
+                       double inner_tol, int *outer, int *inner, double *relres) {
+  if (!p || !b || !x || max_outer < 0 || restart < 1 || restart > 200 || !(inner_tol > 0.0) || !(inner_tol < 1.0))
+    return fail(BTC_ERR_ARG, "btc_solve_gmres_ir: invalid arguments");
+  if (p->dtype == BTC_F32) return fail(BTC_ERR_ARG, "btc_solve_gmres_ir needs an FP64 or mixed plan");
+  if (!p->factored) return fail(BTC_ERR_NOT_FACTORED, "btc_solve_gmres_ir: no factorization");
+  return gmres_ir_impl(p, b, x, tol, max_outer, restart, inner_tol, outer, inner, relres);
+}
+
 int btc_factor_solve(btc_plan_t p, const void *D, const void *B, void *rhs, int nrhs) {
   if (!p || !rhs || nrhs < 1) return fail(BTC_ERR_ARG, "btc_factor_solve: invalid arguments");
   if (!can_interlace(p, nrhs)) {
@@ -1428,7 +1594,8 @@ int btc_free(btc_plan_t p) {
   }
   void *dev[] = {p->dpool,        p->epool,        p->d_fac,    p->d_fwd,  p->d_bwd,     p->d_rb,
                  p->d_y,          p->s_D,          p->d_fac_deps, p->d_solve_flow, p->d_flow, p->s_B,
-                 p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail};
+                 p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail,
+                 p->kry};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_rb) cudaFreeHost(p->h_rb);

@@ -1,0 +1,87 @@
+"""GMRES-based iterative refinement (btc_solve_gmres_ir) on the plan's low-precision factor: it
+reaches the FP64 bar where classical refinement does (against the oracle), and also where
+classical refinement cannot, a TF32 factor of an ill-conditioned block Laplacian."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_03754_gb300 import btc, build, gen
+from gpu_helpers import dev, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    need_gpu()
+    build.build()
+    btc.load()
+
+
+def _laplacian(N, n, seed):
+    """D_i = 2I + a small SPD perturbation, B_i = -I: kappa ~ 4 (N+1)^2 / pi^2."""
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((N, n, n)) * 0.05
+    D = 2.0 * np.eye(n)[None] + M @ np.swapaxes(M, 1, 2) / n
+    B = np.tile(-np.eye(n), (N - 1, 1, 1))
+    return D, B
+
+
+@pytest.mark.parametrize("dt,N,n,delta", [(btc.MIXED_F32, 300, 32, 1e-2), (btc.MIXED_F32, 1024, 64, 1.0),
+                                          (btc.F64, 100, 16, 1.0), (btc.MIXED_TF32, 65, 128, 1.0)])
+def test_gmres_ir_reaches_the_fp64_bar(dt, N, n, delta):
+    D, B = gen.bt_random(N, n, delta=delta, seed=N)
+    b = gen.rhs(N, n, 1, seed=N)
+    Dd, Bd, bd = dev(D, torch.float64), dev(B, torch.float64), dev(b, torch.float64)
+    p = btc.btc_plan(N, n, dt)
+    btc.btc_factor(p, Dd, Bd)
+    xs = []
+    for _ in range(2):
+        x = torch.zeros_like(bd)
+        outer, inner, rel, rc = btc.btc_solve_gmres_ir(p, bd, x, tol=1e-11)
+        assert rc == btc.OK and rel <= 1e-11, (outer, inner, rel)
+        xs.append(x)
+    assert torch.equal(xs[0], xs[1]), "reproducible"
+    if N <= 300:
+        xo = oracle.solve(D, B, b)
+        assert np.abs(xs[0].cpu().numpy() - xo).max() <= 1e-8 * np.abs(xo).max()
+
+
+@pytest.mark.parametrize("N", [129, 257])
+def test_gmres_ir_converges_where_classical_refinement_does_not(N):
+    n = 128
+    D, B = _laplacian(N, n, seed=N)
+    b = gen.rhs(N, n, 1, seed=N)
+    Dd, Bd, bd = dev(D, torch.float64), dev(B, torch.float64), dev(b, torch.float64)
+    p = btc.btc_plan(N, n, btc.MIXED_TF32)
+    btc.btc_factor(p, Dd, Bd)
+    xc = torch.zeros_like(bd)
+    it_c, rel_c, rc_c = btc.btc_solve_refined(p, bd, xc, 1, tol=1e-10, maxit=20, allow_not_converged=True)
+    xg = torch.zeros_like(bd)
+    outer, inner, rel_g, rc_g = btc.btc_solve_gmres_ir(p, bd, xg, tol=1e-10, max_outer=20, restart=40)
+    assert rc_g == btc.OK and rel_g <= 1e-10, (outer, inner, rel_g)
+    assert rc_c != btc.OK or it_c > outer, (it_c, rel_c, outer, inner)
+    xo = oracle.solve(D, B, b)
+    assert np.abs(xg.cpu().numpy() - xo).max() <= 1e-6 * np.abs(xo).max()
+    assert oracle.relres(D, B, xg.cpu().numpy(), b) <= 1e-10
+
+
+def test_gmres_ir_arguments():
+    N, n = 20, 16
+    D, B = gen.bt_random(N, n, seed=1)
+    b = gen.rhs(N, n, 1, seed=1)
+    Dd, Bd, bd = dev(D, torch.float64), dev(B, torch.float64), dev(b, torch.float64)
+    p = btc.btc_plan(N, n, btc.MIXED_F32)
+    x = torch.zeros_like(bd)
+    with pytest.raises(btc.BtcError) as ei:
+        btc.btc_solve_gmres_ir(p, bd, x)
+    assert ei.value.code == btc.ERR_NOT_FACTORED
+    btc.btc_factor(p, Dd, Bd)
+    for kw in ({"restart": 0}, {"inner_tol": 1.5}):
+        with pytest.raises(btc.BtcError) as ei:
+            btc.btc_solve_gmres_ir(p, bd, x, **kw)
+        assert ei.value.code == btc.ERR_ARG
+    q = btc.btc_plan(N, n, btc.F32)
+    btc.btc_factor(q, Dd.float(), Bd.float())
+    with pytest.raises(btc.BtcError):
+        btc.btc_solve_gmres_ir(q, bd, x)
