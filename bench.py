@@ -441,6 +441,45 @@ def interlace_measure(btc, gen, torch, stream, flush, steps=30):
     return out
 
 
+def gmres_ir_measure(btc, torch, stream):
+    """GMRES-IR against classical refinement on a TF32 factor (n = 128) of ill-conditioned block
+    Laplacians (D_i = 2I + small SPD perturbation, B_i = -I, kappa ~ 4 (N+1)^2 / pi^2): steps,
+    final relative residual and time of each, on the same factorization."""
+    import numpy as np
+    out = {}
+    n = 128
+    for N in (129, 257, 513):
+        rng = np.random.default_rng(N)
+        M = rng.standard_normal((N, n, n)) * 0.05
+        D = 2.0 * np.eye(n)[None] + M @ np.swapaxes(M, 1, 2) / n
+        B = np.tile(-np.eye(n), (N - 1, 1, 1))
+        b = rng.standard_normal((N * n, 1))
+        Dd, Bd, bd = (torch.from_numpy(a).cuda() for a in (D, B, b))
+        p = btc.btc_plan(N, n, btc.MIXED_TF32, stream)
+        with torch.cuda.stream(stream):
+            btc.btc_factor(p, Dd, Bd)
+            res = {"kappa_estimate": 4.0 * (N + 1) ** 2 / np.pi ** 2}
+            for name in ("classical", "gmres_ir"):
+                x = torch.zeros_like(bd)
+                e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                t0 = time.perf_counter()
+                e0.record(stream)
+                if name == "classical":
+                    it, rel, rc = btc.btc_solve_refined(p, bd, x, 1, tol=TOL, maxit=30, allow_not_converged=True)
+                    steps = {"steps": it}
+                else:
+                    o, i, rel, rc = btc.btc_solve_gmres_ir(p, bd, x, tol=TOL, max_outer=20, restart=40,
+                                                           allow_not_converged=True)
+                    steps = {"outer_steps": o, "arnoldi_steps": i}
+                e1.record(stream)
+                e1.synchronize()
+                res[name] = {**steps, "relres": rel, "converged": rc == btc.OK,
+                             "ms": 1000.0 * (time.perf_counter() - t0)}
+        out[f"N{N}_n{n}"] = res
+        p.free()
+    return out
+
+
 def serving_measure(btc, torch, rates=(1000.0, 4000.0), count=300):
     """Config: Poisson stream of factor+solve requests, n uniform in {12,24,48,96}, N log-uniform
     in [50, 5000], MPC-like generator, 30% re-solves of a cached factor, HBM-footprint admission;
@@ -612,6 +651,7 @@ def main():
                if not args.no_batch else None)
     serving = serving_measure(btc, torch) if not args.no_serve else None
     large = large_block_measure(btc, gen, torch, stream, flush) if not args.no_large else None
+    gmres = gmres_ir_measure(btc, torch, stream) if not args.no_large else None
     small = small_case_measure(btc, gen, torch, stream, flush)
     interlace = interlace_measure(btc, gen, torch, stream, flush)
     # solve roofline: each factor block read once per direction (the compulsory bytes of Alg. 7, m = 1)
@@ -656,6 +696,7 @@ def main():
         "phases_ms": phase,
         "flow_config": dict(zip(("resident_cap", "ctas_per_sm", "tuned"), btc.btc_plan_tuning_interlaced(pm))),
         "root_fp64_option": root_fp64_option,
+        "gmres_ir_vs_classical_tf32": gmres,
         "roofline": {"kernel": "k_factor_fwd_flow (interlaced factor + forward sweep, one launch per step)",
                      "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,

@@ -330,10 +330,11 @@ int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const d
  * ||x||_inf, the correction equation Psi d = r solved by GMRES on
  * M^{-1} Psi d = M^{-1} r (M = the plan's FP32 or TF32 factor applied by the
  * solve kernels, Psi applied in FP64; at most `restart` Arnoldi steps, stopped
- * when the preconditioned residual falls by inner_tol), x += d. Unlike
- * btc_solve_refined it converges when the factor is too inaccurate for
- * classical refinement (condition number times the factor's error near or
- * above 1, e.g. a TF32 factor of an ill-conditioned matrix). b, x: device
+ * when the preconditioned residual falls by inner_tol), x += d. Its analysis
+ * (Carson and Higham) covers factors too inaccurate for classical refinement
+ * (condition number times the factor's relative error near or above 1); on
+ * the ill-conditioned TF32 cases measured with this library both converge,
+ * GMRES-IR in fewer outer steps and to a smaller residual. b, x: device
  * FP64 [N*n]; needs an FP64 or mixed plan, factored (D, B kept as for
  * btc_solve_refined). *outer: outer steps taken, *inner: Arnoldi steps in
  * all, *relres: final relative residual (each may be NULL). Synchronous.
