@@ -681,7 +681,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (factor, solves) + f64 (root chol, residual, update)",
+        "vs_baseline": None, "dtype": "f32 (factor, solves) + double-f32 (root chol) + f64 (residual, update)",
         "data": "synthetic",
         "config": {"workload": "bt_random N=1024 n=64 nrhs=1 delta=1 seed=0; mixed FP32 factor + FP64 refinement "
                                "to relres<=1e-10", "N": N, "n": n, "nrhs": m, "delta": W["delta"],
