@@ -222,6 +222,45 @@ __device__ __forceinline__ void smem_to_block(P *g, const T *s, bool lower_zero)
 template <class C, typename T, typename S>
 __device__ __forceinline__ void user_to_smem(T *s, const S *src, int n, bool trans, T diag, bool lower = false,
                                              S *mirror = nullptr) {
+  if constexpr (sizeof(S) == 8) {
+    // FP64 rows of even length from a 16-byte aligned block: pairs of elements per 16-byte load, so a
+    // thread's 32 bytes in flight take half as many load requests
+    if ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+      constexpr int HP = C::NP / 2;  // pairs per padded row
+      constexpr int TOT2 = C::NP * HP;
+      constexpr int IT2 = (TOT2 + C::NT - 1) / C::NT;
+      constexpr int CH2 = IT2 < 2 ? IT2 : 2;
+#pragma unroll 1
+      for (int i0 = 0; i0 < IT2; i0 += CH2) {
+        double2 v[CH2];
+#pragma unroll
+        for (int u = 0; u < CH2; ++u) {
+          const int q = threadIdx.x + (i0 + u) * C::NT;
+          const int a = q / HP, b = 2 * (q % HP);  // source row a, columns b, b + 1 (b + 1 < n: n is even)
+          v[u] = (q < TOT2 && a < n && b < n && (!lower || a >= b))
+                     ? __ldg(reinterpret_cast<const double2 *>(src + (size_t)a * n + b))
+                     : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < CH2; ++u) {
+          const int q = threadIdx.x + (i0 + u) * C::NT;
+          if (q >= TOT2) continue;
+          const int a = q / HP, b0 = 2 * (q % HP);
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int b = b0 + t;
+            const bool in = a < n && b < n, use = in && (!lower || a >= b);
+            const double val = t ? v[u].y : v[u].x;
+            if (mirror && use) mirror[(size_t)a * n + b] = val;
+            const T x = use ? convert_in<T, double>(val) : (in ? T(0) : (a == b ? diag : T(0)));
+            if (trans) s[b * C::LD + a] = x;
+            else s[a * C::LD + b] = x;
+          }
+        }
+      }
+      return;
+    }
+  }
   constexpr int TOTAL = C::NP * C::NP;
   constexpr int ITER = (TOTAL + C::NT - 1) / C::NT;
   constexpr int CHMAX = 32 / (int)sizeof(S);  // 32 bytes of loads in flight per thread
