@@ -28,7 +28,8 @@ def _laplacian(N, n, seed):
 
 
 @pytest.mark.parametrize("dt,N,n,delta", [(btc.MIXED_F32, 300, 32, 1e-2), (btc.MIXED_F32, 1024, 64, 1.0),
-                                          (btc.F64, 100, 16, 1.0), (btc.MIXED_TF32, 65, 128, 1.0)])
+                                          (btc.F64, 100, 16, 1.0), (btc.MIXED_TF32, 65, 128, 1.0),
+                                          (btc.MIXED_TF32, 50, 100, 1e-3), (btc.MIXED_F32, 77, 13, 1.0)])
 def test_gmres_ir_reaches_the_fp64_bar(dt, N, n, delta):
     D, B = gen.bt_random(N, n, delta=delta, seed=N)
     b = gen.rhs(N, n, 1, seed=N)

@@ -32,7 +32,7 @@ def _device_reference(N, n, m, D, B, b, dt):
 
 @pytest.mark.parametrize("dt", [btc.MIXED_F32, btc.F64], ids=["mixed", "f64"])
 @pytest.mark.parametrize("N,n,m,delta", [(2, 16, 1, 1.0), (257, 16, 2, 1e-3), (300, 32, 1, 1.0), (129, 48, 1, 1e-2),
-                                         (1024, 64, 1, 1.0), (65, 96, 1, 1.0)])
+                                         (1024, 64, 1, 1.0), (65, 96, 1, 1.0), (97, 33, 1, 1.0), (40, 7, 2, 1e-2)])
 def test_pinned_inputs_give_the_device_result(N, n, m, delta, dt):
     if dt == btc.F64 and n > 96:
         pytest.skip("FP64 blocks up to 96")
