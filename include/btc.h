@@ -151,8 +151,9 @@ enum btc_variant { BTC_VARIANT_HYBRID = 0, BTC_VARIANT_RIGHT_LOOKING = 1 };
 int btc_plan_set_variant(btc_plan_t p, int variant);
 
 /*
- * Precision of the top-separator Cholesky of the mixed paths (BTC_MIXED_F32,
- * BTC_MIXED_TF32; other dtypes ignore it). BTC_ROOT_DOUBLE_FP32 (default):
+ * Precision of the top-separator Cholesky of the mixed paths (the potrf of
+ * Alg. 5's last iteration; BTC_MIXED_F32, BTC_MIXED_TF32; other dtypes ignore
+ * it). BTC_ROOT_DOUBLE_FP32 (default):
  * double-FP32 arithmetic (pairs of FP32, about 48 significant bits) on the
  * FP32 pipe; BTC_ROOT_FP64: FP64 arithmetic. Either way the Schur complement
  * comes from the FP32 pool and the factor is rounded back to it, so the two
@@ -175,7 +176,8 @@ int btc_plan_set_root_precision(btc_plan_t p, int precision);
 int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
 
 /*
- * Per-node phase stamps of the factorization (for profiling; off by default).
+ * Per-node phase stamps of the factorization (the steps of one Alg. 5 node;
+ * for profiling; off by default).
  * phase: caller-owned device buffer of 8 * N uint64, or NULL to disable. Each
  * node e (0-based) eliminated by the FP32 or FP64 node kernels (Alg. 5 and
  * Alg. 6 items; not the double-FP32 top separator of the mixed path, not the TF32
@@ -325,7 +327,9 @@ int btc_factor_solve_refined(btc_plan_t p, const void *D, const void *B, const d
 
 /*
  * GMRES-based iterative refinement (GMRES-IR; Carson and Higham 2018) on the
- * current factorization, for one right-hand side: x0 = M^{-1} b, then per
+ * current factorization (Alg. 5 as the preconditioner, applied by the solves
+ * of Alg. 7; the paper names mixed precision as future work, Sec. 7), for one
+ * right-hand side: x0 = M^{-1} b, then per
  * outer step r = b - Psi x in FP64 and, until ||r||_inf <= tol ||Psi||_inf
  * ||x||_inf, the correction equation Psi d = r solved by GMRES on
  * M^{-1} Psi d = M^{-1} r (M = the plan's FP32 or TF32 factor applied by the
