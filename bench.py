@@ -659,7 +659,8 @@ def main():
     t_solve = phase["correction_solve"]
     solve_roof = {"kernel": "k_solve_flow (one correction solve, forward + backward)", "bound": "hbm",
                   "achieved": solve_bytes / (t_solve * 1e-3) / 1e9, "peak": None, "unit": "GB/s",
-                  "algorithmic_bytes": solve_bytes, "note": "bound by 22 dependent levels; part of the factor is still in L2 from the factorization"}
+                  "algorithmic_bytes": solve_bytes,
+                  "note": "bound by 22 dependent levels; part of the factor is still in L2 from the factorization"}
 
     peaks, pk_kind = _peaks()
     solve_roof["peak"] = peaks.get("hbm_gbs")
