@@ -120,6 +120,16 @@ __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const Batc
   }
 }
 
+// Clears the residual and solution norm slots (norms[3k], norms[3k+1]) of every
+// instance in one launch; the matrix-norm slot norms[3k+2] is kept.
+__global__ void k_batch_clear_norms(double *norms, int count) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) {
+    norms[3 * k] = 0.0;
+    norms[3 * k + 1] = 0.0;
+  }
+}
+
 // Lower bound of ||Psi||_inf per instance into norms[3*inst + 2] for the
 // refinement's stopping test: each |a_ij| rounded toward zero to FP32, row
 // sums with round-toward-zero additions, so the bound never exceeds the norm.
@@ -170,6 +180,8 @@ struct BatchGroup {
   int n_nodes = 0;
   const void *pack = nullptr, *unpack = nullptr, *resid = nullptr;
   double flops = 0;
+  cudaStream_t s = nullptr;  // the group's own stream: groups run concurrently
+  cudaEvent_t ev = nullptr;  // its join point
 };
 
 }  // namespace btc
@@ -192,6 +204,7 @@ struct btc_batch_s {
   std::vector<InstDesc> inst_host;
   double flops = 0;
   int64_t device_bytes = 0;
+  cudaEvent_t fork_ev = nullptr;  // work queued on the batch stream before the groups start
 };
 
 namespace btc {
@@ -352,10 +365,28 @@ static FlowSync group_sync(BatchGroup &g, int which) {
   return fs;
 }
 
+// The block-size groups are independent (own pools, work vector, flags and
+// persistent launches; each launch waits only on its own items), so they run
+// concurrently, each on its own stream: fork after the work queued on the
+// batch stream, join before the batch stream continues.
+static int batch_fork(btc_batch_s *bt) {
+  BTC_CUDA(cudaEventRecord(bt->fork_ev, bt->stream));
+  for (BatchGroup &g : bt->groups) BTC_CUDA(cudaStreamWaitEvent(g.s, bt->fork_ev, 0));
+  return BTC_OK;
+}
+static int batch_join(btc_batch_s *bt) {
+  for (BatchGroup &g : bt->groups) {
+    BTC_CUDA(cudaEventRecord(g.ev, g.s));
+    BTC_CUDA(cudaStreamWaitEvent(bt->stream, g.ev, 0));
+  }
+  return BTC_OK;
+}
+
 static int group_solve(btc_batch_s *bt, BatchGroup &g) {
   const KernelSet &k = *g.ks;
-  BTC_CUDA(cudaMemsetAsync(g.d_flow + 1, 0, sizeof(int), bt->stream));
-  BTC_CUDA(cudaMemsetAsync(g.d_flow + kFlowHeader, 0, sizeof(int) * (size_t)g.n_solve, bt->stream));
+  (void)bt;
+  BTC_CUDA(cudaMemsetAsync(g.d_flow + 1, 0, sizeof(int), g.s));
+  BTC_CUDA(cudaMemsetAsync(g.d_flow + kFlowHeader, 0, sizeof(int) * (size_t)g.n_solve, g.s));
   SolveArgs a;
   a.items = g.d_solve;
   a.count = g.n_solve;
@@ -363,7 +394,7 @@ static int group_solve(btc_batch_s *bt, BatchGroup &g) {
   a.epool = g.epool;
   a.y = g.y;
   a.m = 1;
-  return launch_n(k.solve_flow, std::min(g.solve_grid, g.n_solve), kSolveThreads, k.fwd_smem(1), bt->stream, a,
+  return launch_n(k.solve_flow, std::min(g.solve_grid, g.n_solve), kSolveThreads, k.fwd_smem(1), g.s, a,
                   group_sync(g, 1));
 }
 
@@ -420,6 +451,12 @@ int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int 
       (rc = batch_alloc((void **)&bt->d_info, count * sizeof(unsigned long long), acc)) ||
       (rc = batch_alloc((void **)&bt->d_norms, 3 * count * sizeof(double), acc)))
     return cleanup(rc);
+  if (cudaEventCreateWithFlags(&bt->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_CUDA, "btc_batch_plan: event creation failed"));
+  for (BatchGroup &g : bt->groups)
+    if (cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming) != cudaSuccess)
+      return cleanup(fail(BTC_ERR_CUDA, "btc_batch_plan: stream creation failed"));
   cudaError_t e;
   if ((e = cudaMallocHost(&bt->h_norms, 3 * count * sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost(&bt->h_info, count * sizeof(unsigned long long))) != cudaSuccess ||
@@ -449,7 +486,9 @@ int btc_batch_factor(btc_batch_t bt, const void *const *D, const void *const *B)
   BTC_CUDA(cudaMemcpyAsync(bt->d_inst, bt->inst_host.data(), bt->count * sizeof(InstDesc), cudaMemcpyHostToDevice,
                            bt->stream));
   BTC_CUDA(cudaMemsetAsync(bt->d_info, 0xFF, bt->count * sizeof(unsigned long long), bt->stream));
+  int rc = batch_fork(bt);
   for (BatchGroup &g : bt->groups) {
+    if (rc) break;
     const KernelSet &k = *g.ks;
     FactorArgs a;
     a.dpool = g.dpool;
@@ -458,29 +497,35 @@ int btc_batch_factor(btc_batch_t bt, const void *const *D, const void *const *B)
     a.info = bt->d_info;
     a.status = g.d_flow + 2;
     InstDesc none{nullptr, nullptr, 0, 0};
-    BTC_CUDA(cudaMemsetAsync(g.d_flow, 0, 3 * sizeof(int), bt->stream));
+    if (cudaMemsetAsync(g.d_flow, 0, 3 * sizeof(int), g.s) != cudaSuccess) {
+      rc = fail(BTC_ERR_CUDA, "btc_batch_factor: memset");
+      break;
+    }
     if (g.n_fac > 0) {
-      BTC_CUDA(cudaMemsetAsync(g.d_flow + kFlowHeader, 0, sizeof(int) * (size_t)g.n_fac, bt->stream));
+      if (cudaMemsetAsync(g.d_flow + kFlowHeader, 0, sizeof(int) * (size_t)g.n_fac, g.s) != cudaSuccess) {
+        rc = fail(BTC_ERR_CUDA, "btc_batch_factor: memset");
+        break;
+      }
       a.items = g.d_fac;
       a.count = g.n_fac;
       const int32_t *deps = g.d_fac_deps;
-      int rc = launch_n(k.fac_flow, std::min(g.fac_grid, g.n_fac), k.fac_threads, k.fac_smem, bt->stream, a, none,
-                        deps, g.n_first, group_sync(g, 0));
-      if (rc) return rc;
+      if ((rc = launch_n(k.fac_flow, std::min(g.fac_grid, g.n_fac), k.fac_threads, k.fac_smem, g.s, a, none, deps,
+                         g.n_first, group_sync(g, 0))))
+        break;
     }
     if (g.n_roots_first > 0) {
       a.items = g.d_roots;
       a.count = g.n_roots_first;
-      int rc = launch_n(k.root_first, g.n_roots_first, k.root_threads, k.root_smem, bt->stream, a, none);
-      if (rc) return rc;
+      if ((rc = launch_n(k.root_first, g.n_roots_first, k.root_threads, k.root_smem, g.s, a, none))) break;
     }
     if (g.n_roots_rest > 0) {
       a.items = g.d_roots + g.n_roots_first;
       a.count = g.n_roots_rest;
-      int rc = launch_n(k.root_rest, g.n_roots_rest, k.root_threads, k.root_smem, bt->stream, a, none);
-      if (rc) return rc;
+      if ((rc = launch_n(k.root_rest, g.n_roots_rest, k.root_threads, k.root_smem, g.s, a, none))) break;
     }
   }
+  const int rj = batch_join(bt);
+  if (rc || (rc = rj)) return rc;
   bt->factored = true;
   bt->anorm_valid = false;
   return BTC_OK;
@@ -521,18 +566,18 @@ int btc_batch_solve(btc_batch_t bt, const void *const *b, void *const *x) {
   if (!bt || !b || !x) return fail(BTC_ERR_ARG, "btc_batch_solve: NULL argument");
   if (!bt->factored) return fail(BTC_ERR_NOT_FACTORED, "btc_batch_solve: no factorization");
   int rc = batch_set_vec(bt, b, x);
-  if (rc) return rc;
+  if (rc || (rc = batch_fork(bt))) return rc;
   for (BatchGroup &g : bt->groups) {
-    if ((rc = launch_n(g.pack, g.n_nodes, 64, 0, bt->stream, g.y, (const BatchNode *)g.d_nodes,
-                       (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np)))
-      return rc;
-    if ((rc = group_solve(bt, g))) return rc;
     int assign = 0;
-    if ((rc = launch_n(g.unpack, g.n_nodes, 64, 0, bt->stream, (const void *)g.y, (const BatchNode *)g.d_nodes,
+    if ((rc = launch_n(g.pack, g.n_nodes, 64, 0, g.s, g.y, (const BatchNode *)g.d_nodes, (const InstDesc *)bt->d_inst,
+                       (const BatchVec *)bt->d_vec, g.np)) ||
+        (rc = group_solve(bt, g)) ||
+        (rc = launch_n(g.unpack, g.n_nodes, 64, 0, g.s, (const void *)g.y, (const BatchNode *)g.d_nodes,
                        (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, assign)))
-      return rc;
+      break;
   }
-  return BTC_OK;
+  const int rj = batch_join(bt);
+  return rc ? rc : rj;
 }
 
 int btc_batch_solve_refined(btc_batch_t bt, const double *const *b, double *const *x, double tol, int maxit,
@@ -544,25 +589,29 @@ int btc_batch_solve_refined(btc_batch_t bt, const double *const *b, double *cons
   if (rc) return rc;
   if ((rc = btc_batch_solve(bt, (const void *const *)b, (void *const *)x))) return rc;
   if (!bt->anorm_valid) {
-    for (int k = 0; k < bt->count; ++k) {
-      // only the norm slot of each instance is cleared here
-      BTC_CUDA(cudaMemsetAsync(bt->d_norms + 3 * k + 2, 0, sizeof(double), bt->stream));
-    }
+    BTC_CUDA(cudaMemsetAsync(bt->d_norms, 0, 3 * (size_t)bt->count * sizeof(double), bt->stream));
+    if ((rc = batch_fork(bt))) return rc;
     for (BatchGroup &g : bt->groups)
-      if ((rc = launch_n((const void *)&k_batch_anorm_lb, g.n_nodes, 64, 0, bt->stream, (const BatchNode *)g.d_nodes,
+      if ((rc = launch_n((const void *)&k_batch_anorm_lb, g.n_nodes, 64, 0, g.s, (const BatchNode *)g.d_nodes,
                          (const InstDesc *)bt->d_inst, bt->d_norms)))
-        return rc;
+        break;
+    const int rj = batch_join(bt);
+    if (rc || (rc = rj)) return rc;
     bt->anorm_valid = true;
   }
   int it = 0;
   double worst = 0.0;
   for (;;) {
-    for (int k = 0; k < bt->count; ++k)
-      BTC_CUDA(cudaMemsetAsync(bt->d_norms + 3 * k, 0, 2 * sizeof(double), bt->stream));
+    if ((rc = launch_n((const void *)&k_batch_clear_norms, (bt->count + 255) / 256, 256, 0, bt->stream, bt->d_norms,
+                       bt->count)))
+      return rc;
+    if ((rc = batch_fork(bt))) return rc;
     for (BatchGroup &g : bt->groups)
-      if ((rc = launch_n(g.resid, g.n_nodes, kResThreads, 0, bt->stream, g.y, (const BatchNode *)g.d_nodes,
+      if ((rc = launch_n(g.resid, g.n_nodes, kResThreads, 0, g.s, g.y, (const BatchNode *)g.d_nodes,
                          (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, bt->d_norms)))
-        return rc;
+        break;
+    const int rj = batch_join(bt);
+    if (rc || (rc = rj)) return rc;
     BTC_CUDA(cudaMemcpyAsync(bt->h_norms, bt->d_norms, 3 * bt->count * sizeof(double), cudaMemcpyDeviceToHost,
                              bt->stream));
     BTC_CUDA(cudaStreamSynchronize(bt->stream));
@@ -575,13 +624,16 @@ int btc_batch_solve_refined(btc_batch_t bt, const double *const *b, double *cons
       worst = std::max(worst, rel);
     }
     if (nan || worst <= tol || it >= maxit) break;
+    if ((rc = batch_fork(bt))) return rc;
     for (BatchGroup &g : bt->groups) {
-      if ((rc = group_solve(bt, g))) return rc;
       int accumulate = 1;
-      if ((rc = launch_n(g.unpack, g.n_nodes, 64, 0, bt->stream, (const void *)g.y, (const BatchNode *)g.d_nodes,
+      if ((rc = group_solve(bt, g)) ||
+          (rc = launch_n(g.unpack, g.n_nodes, 64, 0, g.s, (const void *)g.y, (const BatchNode *)g.d_nodes,
                          (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, accumulate)))
-        return rc;
+        break;
     }
+    const int rj2 = batch_join(bt);
+    if (rc || (rc = rj2)) return rc;
     ++it;
   }
   if (iters) *iters = it;
@@ -595,6 +647,11 @@ int btc_batch_free(btc_batch_t bt) {
   if (!bt) return BTC_OK;
   cudaStreamSynchronize(bt->stream);
   for (BatchGroup &g : bt->groups) {
+    if (g.s) {
+      cudaStreamSynchronize(g.s);
+      cudaStreamDestroy(g.s);
+    }
+    if (g.ev) cudaEventDestroy(g.ev);
     void *ptrs[] = {g.dpool, g.epool, g.y, g.d_fac, g.d_fac_deps, g.d_roots, g.d_solve, g.d_flow, g.d_nodes};
     for (void *q : ptrs)
       if (q) cudaFree(q);
@@ -605,6 +662,7 @@ int btc_batch_free(btc_batch_t bt) {
   if (bt->h_norms) cudaFreeHost(bt->h_norms);
   if (bt->h_info) cudaFreeHost(bt->h_info);
   if (bt->h_status) cudaFreeHost(bt->h_status);
+  if (bt->fork_ev) cudaEventDestroy(bt->fork_ev);
   delete bt;
   return BTC_OK;
 }
