@@ -35,14 +35,15 @@ extern "C" {
 
 typedef struct btc_plan_s *btc_plan_t;
 
-/* Arithmetic of a plan. Input element type: FP64 for BTC_F64, BTC_MIXED_F32 and
- * BTC_MIXED_TF32, FP32 for BTC_F32. */
+/* Arithmetic of a plan. Input element type: FP64 for BTC_F64 and the three
+ * BTC_MIXED_* dtypes, FP32 for BTC_F32. */
 enum btc_dtype {
   BTC_F64 = 0,        /* factor and solve in FP64 (the plain FP64 path)                         */
   BTC_F32 = 1,        /* factor and solve in FP32                                                */
   BTC_MIXED_F32 = 2,  /* FP64 inputs; factor and correction solves in FP32 except the root
-                         (top-separator) Cholesky, which runs in double-FP32 (pairs of FP32, about 48 bits); FP64 residual and update
-                         in btc_solve_refined                                                    */
+                         (top-separator) Cholesky, which runs in FP64 (or, as an option, in
+                         double-FP32: btc_plan_set_root_precision); FP64 residual and update in
+                         btc_solve_refined                                                       */
   BTC_MIXED_TF32 = 3, /* as BTC_MIXED_F32, with the four n^3 products of every node (the two
                          deferred syrk, the immediate syrk and the fill gemm of Alg. 5) on the
                          tcgen05 tensor cores with TF32 operands and FP32 accumulation, for
@@ -50,6 +51,11 @@ enum btc_dtype {
                          BTC_MIXED_F32 kernels. Its factor is less accurate than FP32 (TF32 has
                          a 10-bit mantissa); the FP64 refinement of btc_solve_refined recovers
                          the solution's accuracy in a few more steps                            */
+  BTC_MIXED_BF16 = 4, /* as BTC_MIXED_TF32 with BF16 operands (8-bit mantissa; kind::f16 MMAs,
+                         FP32 accumulation) for the four n^3 products: twice the tensor rate and
+                         half the operand bytes of TF32, a factor about 8 times less accurate, so
+                         refinement needs more steps, and for ill-conditioned matrices classical
+                         refinement can stall where btc_solve_gmres_ir still converges          */
 };
 
 enum btc_status {
@@ -152,14 +158,15 @@ int btc_plan_set_variant(btc_plan_t p, int variant);
 
 /*
  * Precision of the top-separator Cholesky of the mixed paths (the potrf of
- * Alg. 5's last iteration; BTC_MIXED_F32, BTC_MIXED_TF32; other dtypes ignore
- * it). BTC_ROOT_DOUBLE_FP32 (default):
+ * Alg. 5's last iteration; the BTC_MIXED_* dtypes; other dtypes ignore
+ * it). BTC_ROOT_FP64 (default): FP64 arithmetic; the pivots of this step
+ * decide the factorization's stability. BTC_ROOT_DOUBLE_FP32 (option):
  * double-FP32 arithmetic (pairs of FP32, about 48 significant bits) on the
- * FP32 pipe; BTC_ROOT_FP64: FP64 arithmetic. Either way the Schur complement
- * comes from the FP32 pool and the factor is rounded back to it, so the two
- * agree up to rounding ties of that last step; the FP64 form is slower on
- * this GPU (its FP64 pipe issues two lanes per clock per SM). Takes effect at
- * the next factorization. Batched plans use the default.
+ * FP32 pipe, somewhat faster on this GPU, whose FP64 pipe issues two lanes per
+ * clock per SM. Either way the Schur complement comes from the FP32 pool and
+ * the factor is rounded back to it, so the two agree up to rounding ties of
+ * that last step. Takes effect at the next factorization. Batched plans and
+ * servers use the FP64 default.
  */
 enum btc_root_precision { BTC_ROOT_DOUBLE_FP32 = 0, BTC_ROOT_FP64 = 1 };
 int btc_plan_set_root_precision(btc_plan_t p, int precision);
@@ -171,7 +178,7 @@ int btc_plan_set_root_precision(btc_plan_t p, int precision);
  * forward items of all levels + N backward items), or NULL to disable. Every
  * item records the global timer (ns) when it was claimed, when its inputs were
  * ready and when it finished, and the SM it ran on. Items that do not run
- * (the double-FP32 root of the mixed path, launched separately) stay untouched.
+ * (the top-separator root of the mixed path, launched separately) stay untouched.
  */
 int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
 
@@ -180,7 +187,7 @@ int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
  * for profiling; off by default).
  * phase: caller-owned device buffer of 8 * N uint64, or NULL to disable. Each
  * node e (0-based) eliminated by the FP32 or FP64 node kernels (Alg. 5 and
- * Alg. 6 items; not the double-FP32 top separator of the mixed path, not the TF32
+ * Alg. 6 items; not the top separator of the mixed path, not the TF32
  * tensor-core kernels) writes the global timer (ns) at phase[8e + k] for
  * k = 0 entry, 1 operands and deferred updates in place, 2 Cholesky and both
  * triangular solves done, 3 factor blocks stored, 4 next diagonal block
@@ -188,6 +195,24 @@ int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace);
  * stamp adds one CTA barrier; the results are unchanged.
  */
 int btc_plan_set_phase_trace(btc_plan_t p, void *phase);
+
+/*
+ * Test hook for the failure detection of the persistent launches (no paper
+ * counterpart; the bounded waits are this library's own). Makes factor item
+ * `item` (0-based, in the order of btc_schedule: level by level) of the next
+ * persistent factorizations, plain and interlaced, wait for a completion flag
+ * that no item ever sets, and lowers the poll limit of every wait of the
+ * plan's persistent launches to max_polls (>= 64; the default is 2^23 polls,
+ * about a second). That wait runs out after max_polls polls: the CTA records
+ * the timeout in the launch's status word and moves on, every later wait of
+ * the launch gives up at once, the launch drains, and btc_info and the solve
+ * calls report BTC_ERR_TIMEOUT (results are then undefined). No kernel traps
+ * or faults; the CUDA context stays usable. item = -1 restores the planner's
+ * dependencies and the default limit. On the mixed paths the top separator
+ * (run by its own kernel, without waits) cannot be chosen. Synchronizes the
+ * plan's stream. Errors: BTC_ERR_ARG.
+ */
+int btc_plan_inject_stall(btc_plan_t p, int item, int64_t max_polls);
 
 /* Rebind the plan's work to another CUDA stream (NULL = legacy default
  * stream). Work already enqueued on the old stream is not waited for. */
@@ -228,7 +253,8 @@ int btc_solve(btc_plan_t p, void *rhs, int nrhs);
  * *iters (may be NULL): refinement steps taken (0 when the first solve
  * already meets tol); *relres (may be NULL): final relative residual.
  * Returns BTC_ERR_NOT_CONVERGED if maxit steps did not reach tol (x then
- * holds the last iterate), BTC_ERR_NOT_SPD if the factor failed.
+ * holds the last iterate) or a residual norm is NaN (a NaN in b; *relres is
+ * then NaN), BTC_ERR_NOT_SPD if the factor failed.
  */
 int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double tol, int maxit, int *iters,
                       double *relres);
@@ -271,7 +297,7 @@ int btc_plan_flow_configs(btc_plan_t p, int *caps, int *max_ctas, int *count);
  * CUDA graphs for btc_factor_solve_refined (on by default). With the
  * interlaced form, one column pass and a settled persistent configuration,
  * the whole refined factor + solve is captured once as an executable graph
- * (pack, interlaced factorization + forward sweep, double-FP32 root, solve tail,
+ * (pack, interlaced factorization + forward sweep, top-separator root, solve tail,
  * unpack, FP64 residual, stopping test, and a device-side while loop of
  * correction solves that runs until the stopping test says stop) and replayed
  * on later calls with the same pointers, sizes and configuration (re-captured
@@ -294,7 +320,7 @@ int btc_plan_set_graphs(btc_plan_t p, int enable);
 enum btc_timing_class {
   BTC_TIME_FACTOR = 0,          /* persistent factorization launch (or its level launches)        */
   BTC_TIME_FACTOR_FORWARD = 1,  /* interlaced factorization + forward substitution launch         */
-  BTC_TIME_ROOT = 2,            /* double-FP32 top-separator Cholesky (mixed path)                        */
+  BTC_TIME_ROOT = 2,            /* top-separator Cholesky of the mixed path (FP64 or double-FP32)  */
   BTC_TIME_SOLVE = 3,           /* full solve launch (forward + backward)                          */
   BTC_TIME_SOLVE_TAIL = 4,      /* solve tail after an interlaced factorization                    */
   BTC_TIME_RESIDUAL = 5,        /* FP64 residual and norms of the refinement                       */
@@ -390,8 +416,9 @@ int btc_get_factor(btc_plan_t p, void *Dhat, void *U, int *pairs);
  * ||b - Psi x||_inf, ||Psi||_inf and ||x||_inf (max over right-hand sides),
  * computed on the device in FP64 for FP64 device arrays D [N][n][n] (lower
  * triangles read), B [N-1][n][n], x and b [N*n][nrhs]; the three numbers are
- * written to out3 (host pointer) after a synchronization of `stream`. Uses a
- * small scratch buffer allocated and freed inside the call.
+ * written to out3 (host pointer) after a synchronization of `stream`. A NaN
+ * anywhere in the inputs comes back as a NaN norm. Uses a small scratch
+ * buffer allocated and freed inside the call.
  */
 int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const double *x, const double *b,
                  double *out3, void *stream);
@@ -399,8 +426,9 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
 /*
  * btc_residual without any device allocation (the paper has no counterpart;
  * this is a deployment convenience). Computes the same three numbers as
- * btc_residual, with the same FP64 arithmetic, into out3 (host pointer), and
- * synchronizes `stream` before returning.
+ * btc_residual, with the same FP64 arithmetic, into out3 (host pointer): each
+ * call copies them to the host and synchronizes `stream` before it returns.
+ * A NaN anywhere in b, x or the matrix comes back as a NaN norm.
  *
  * For callers that cannot allocate device memory: real-time control loops
  * that forbid allocation after start-up, processes whose memory is entirely
@@ -416,9 +444,10 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
  *  - all calls share that one array: calls that overlap on the GPU (on two
  *    streams, or from two host threads) race and may return wrong norms;
  *    serialize them;
- *  - the first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture begins.
+ *  - the first call on each device does a one-time set-up: it looks up the
+ *    array's device address (cudaGetSymbolAddress) with that device current.
+ *    A caller that captures CUDA graphs on that device should make this first
+ *    call before any stream capture begins.
  * D, B, x, b: device pointers as for btc_residual. Errors: BTC_ERR_ARG,
  * BTC_ERR_UNSUPPORTED, BTC_ERR_CUDA (message in btc_last_error()).
  */
@@ -483,7 +512,9 @@ int btc_version(void);
  * factors are evicted to make room), so requests arriving while others run
  * are admitted as slots and memory free up and their kernels overlap. Each
  * request is factor + refined solve (one RHS) or, with factor_id >= 0, a
- * refined re-solve with the cached factor of an earlier request.
+ * refined re-solve with the cached factor of an earlier request. Re-solves of
+ * one cached factor run one at a time (they share that factor's plan and its
+ * work vectors); requests queued behind such a re-solve may start before it.
  */
 typedef struct btc_server_s *btc_server_t;
 
@@ -508,7 +539,7 @@ typedef struct btc_server_stats_s {
   int64_t device_bytes;           /* plans in flight, cached and idle                          */
 } btc_server_stats_t;
 
-/* Start a server. dtype: BTC_MIXED_F32 or BTC_F64. slots: 1..64 concurrent
+/* Start a server. dtype: BTC_F64 or a BTC_MIXED_* dtype. slots: 1..64 concurrent
  * requests. hbm_budget_bytes: device memory the server may hold in plans.
  * cache_factors: keep factors for re-solve requests. */
 int btc_server_start(btc_server_t *out, int dtype, int slots, int64_t hbm_budget_bytes, int cache_factors);

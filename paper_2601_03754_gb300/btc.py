@@ -14,7 +14,7 @@ import threading
 
 import numpy as np
 
-F64, F32, MIXED_F32, MIXED_TF32 = 0, 1, 2, 3
+F64, F32, MIXED_F32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3, 4
 DTYPES = {"f64": F64, "f32": F32, "mixed_f32": MIXED_F32}
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_SPD, ERR_TIMEOUT, ERR_NOT_FACTORED, ERR_UNSUPPORTED, ERR_NOT_CONVERGED = (
@@ -78,6 +78,7 @@ _SIGS = {
     "btc_solve_gmres_ir": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip, _ip,
                            _dp],
     "btc_plan_set_root_precision": [_vp, ctypes.c_int],
+    "btc_plan_inject_stall": [_vp, ctypes.c_int, ctypes.c_int64],
     "btc_plan_set_phase_trace": [_vp, _vp],
     "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
     "btc_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_int64)],
@@ -447,8 +448,14 @@ ROOT_DOUBLE_FP32, ROOT_FP64 = 0, 1
 
 
 def btc_plan_set_root_precision(plan, precision):
-    """Top-separator Cholesky of the mixed paths in double-FP32 (ROOT_DOUBLE_FP32, default) or FP64."""
+    """Top-separator Cholesky of the mixed paths in FP64 (ROOT_FP64, default) or double-FP32 (ROOT_DOUBLE_FP32)."""
     return _check(load().btc_plan_set_root_precision(plan.h, precision))
+
+
+def btc_plan_inject_stall(plan, item, max_polls=4096):
+    """Test hook: factor item `item` waits on a flag nothing sets, every wait gives up after max_polls
+    polls (item=-1 restores the plan)."""
+    return _check(load().btc_plan_inject_stall(plan.h, item, max_polls))
 
 
 def btc_plan_set_variant(plan, variant):

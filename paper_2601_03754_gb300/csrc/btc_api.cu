@@ -40,26 +40,29 @@ int fail(int code, const char *fmt, ...) {
 
 // ------------------------------------------------------------ kernel table
 static constexpr int kMaxSets = 12;
-static KernelSet g_sets[4][kMaxSets];
-static int g_nsets[4] = {0, 0, 0, 0};
+static constexpr int kDtypes = 5;
+static KernelSet g_sets[kDtypes][kMaxSets];
+static int g_nsets[kDtypes] = {0, 0, 0, 0, 0};
 static std::once_flag g_once;
 
 static void init_tables() {
   std::call_once(g_once, [] {
-    const int code_f64 = BTC_F64, code_f32 = BTC_F32, code_mixed = BTC_MIXED_F32, code_tf32 = BTC_MIXED_TF32;
+    const int code_f64 = BTC_F64, code_f32 = BTC_F32, code_mixed = BTC_MIXED_F32, code_tf32 = BTC_MIXED_TF32,
+              code_bf16 = BTC_MIXED_BF16;
 #define BTC_ADD_SET(dt, np) g_sets[code_##dt][g_nsets[code_##dt]++] = make_set_##dt##_##np();
     BTC_FOR_EACH_SET(BTC_ADD_SET)
 #undef BTC_ADD_SET
-    // below the tensor-core block size the TF32 dtype runs the mixed FP32 sets
-    for (int i = 0; i < g_nsets[code_mixed]; ++i)
-      if (g_sets[code_mixed][i].np < 128) g_sets[code_tf32][g_nsets[code_tf32]++] = g_sets[code_mixed][i];
+    // below the tensor-core block size the TF32 and BF16 dtypes run the mixed FP32 sets
+    for (int code : {code_tf32, code_bf16})
+      for (int i = 0; i < g_nsets[code_mixed]; ++i)
+        if (g_sets[code_mixed][i].np < 128) g_sets[code][g_nsets[code]++] = g_sets[code_mixed][i];
   });
 }
 
 const KernelSet &kernels_for(int dtype, int np) {
   static KernelSet none;
   init_tables();
-  if (dtype < 0 || dtype > 3) return none;
+  if (dtype < 0 || dtype >= kDtypes) return none;
   for (int i = 0; i < g_nsets[dtype]; ++i)
     if (g_sets[dtype][i].np == np) return g_sets[dtype][i];
   return none;
@@ -77,9 +80,9 @@ __global__ void k_anorm(const double *D, const double *B, int N, int n, double *
       for (int c = 0; c < n; ++c) s += fabs(B[(i - 1) * bs + r * n + c]);
     if (i + 1 < N)
       for (int c = 0; c < n; ++c) s += fabs(B[i * bs + c * n + r]);
-    best = fmax(best, s);
+    best = nan_max(best, s);
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  for (int o = 16; o > 0; o >>= 1) best = nan_max(best, __shfl_xor_sync(0xffffffffu, best, o));
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 2, best);
 }
 
@@ -108,9 +111,9 @@ __global__ void k_refine_decide(Readback *rb, double tol, int maxit, int first, 
 }
 
 bool dtype_ok(int dtype) {
-  return dtype == BTC_F64 || dtype == BTC_F32 || dtype == BTC_MIXED_F32 || dtype == BTC_MIXED_TF32;
+  return dtype == BTC_F64 || dtype == BTC_F32 || dtype_mixed(dtype);
 }
-bool dtype_mixed(int dtype) { return dtype == BTC_MIXED_F32 || dtype == BTC_MIXED_TF32; }
+bool dtype_mixed(int dtype) { return dtype == BTC_MIXED_F32 || dtype == BTC_MIXED_TF32 || dtype == BTC_MIXED_BF16; }
 
 }  // namespace btc
 
@@ -162,7 +165,17 @@ struct btc_plan_s {
   // btc_factor_solve_host with host-resident D and B: the level-1 loads read them over the CPU-GPU link
   // and fill the staging copies s_D, s_B (which the factorization is given) for the residuals
   const void *ingD = nullptr, *ingB = nullptr;
-  int root_prec = BTC_ROOT_DOUBLE_FP32;  // top-separator Cholesky of the mixed path
+  int root_prec = BTC_ROOT_FP64;  // top-separator Cholesky of the mixed path
+  // failure-detection test hook (btc_plan_inject_stall): poll limit of the persistent launches' waits,
+  // the factor item made to wait on a flag that no item sets (-1: none), that flag's index, and host
+  // copies of the dependency lists to restore
+  long long wait_limit = kMaxPolls;
+  int stall_item = -1, stall_flag = 0;
+  std::vector<int32_t> inter_code_h, inter_deps_h;
+  // blocked nodes (padded n = 256): tile tasks in launch order and one completion counter per node
+  TileTask *d_tiles = nullptr;
+  int *d_tile_cnt = nullptr;
+  int n_tiles = 0, tile_grid = 0;
   double *kry = nullptr;  // GMRES-IR workspace: basis, work and zero vectors, device scalars
   size_t kry_cap = 0;     // its size in doubles
   // optional per-kernel-class event timing (btc_plan_set_timing)
@@ -244,6 +257,7 @@ static FlowSync flow_sync(btc_plan_s *p, int which) {
   fs.status = p->d_status;
   fs.done = p->d_flow + kFlowHeader;
   fs.trace = which == 0 ? p->trace_fac : p->trace_solve;
+  fs.max_polls = p->wait_limit;
   return fs;
 }
 
@@ -408,7 +422,7 @@ static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
   return BTC_OK;
 }
 
-// Persistent factorization launch of every level except the double-FP32 top
+// Persistent factorization launch of every level except the FP64 (or double-FP32) top
 // separator of the mixed path (hybrid Alg. 5, or Alg. 6 after its packing
 // pass), with the plan's configuration.
 static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
@@ -549,10 +563,45 @@ static int autotune_inter(btc_plan_s *p, const void *D, const void *B, int m) {
 // by the caller) is interlaced with the factorization in the same persistent
 // launch (hybrid variant, persistent schedule); the caller then runs only the
 // tail of the solve (run_solve_tail).
+// Factorization of a plan with blocked 256 x 256 nodes: the packing pass
+// (the caller's D and B, converted, into the pools in the orientation level 1
+// eliminates), then one persistent launch of every node's tile tasks,
+// including the top separator's.
+static int tiled_factor(btc_plan_s *p, const void *D, const void *B) {
+  const KernelSet &k = *p->ks;
+  int rc;
+  BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
+  BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
+  BTC_CUDA(cudaMemsetAsync(p->d_tile_cnt, 0, sizeof(int) * (size_t)p->n_fac, p->stream));
+  if ((rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n))) return rc;
+  TileArgs a;
+  a.tasks = p->d_tiles;
+  a.count = p->n_tiles;
+  a.dpool = reinterpret_cast<float *>(p->dpool);
+  a.epool = reinterpret_cast<float *>(p->epool);
+  a.counters = p->d_tile_cnt;
+  a.info = p->d_info;
+  FlowSync fs = flow_sync(p, 0);
+  fs.trace = nullptr;  // the trace buffers are sized for node items, not tile tasks
+  {
+    KernelTimer timer(p, BTC_TIME_FACTOR);
+    if ((rc = launch_n(k.tile_flow, std::min(p->tile_grid, p->n_tiles), kTileThreads, k.tile_smem, p->stream, a,
+                       fs)))
+      return rc;
+  }
+  p->D = D;
+  p->B = B;
+  p->factored = true;
+  p->anorm_valid = false;
+  return BTC_OK;
+}
+
 static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter) {
   if (!p || !D || (p->N > 1 && !B)) return fail(BTC_ERR_ARG, "btc_factor: NULL argument");
   if (((uintptr_t)D | (uintptr_t)B) & 15) return fail(BTC_ERR_ARG, "btc_factor: D and B must be 16-byte aligned");
   const KernelSet &k = *p->ks;
+  if (k.tiled) return tiled_factor(p, D, B);
   const bool rl = p->variant == BTC_VARIANT_RIGHT_LOOKING;
   int rc = BTC_OK;
   const bool inter = p->sched == BTC_SCHED_FLOW && !rl && m_inter > 0 && p->n_inter > 0;
@@ -837,7 +886,7 @@ static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, dou
       }
       const double rn = p->h_norms[0], xn = p->h_norms[1], an = p->h_norms[2];
       rel = (an * xn > 0) ? rn / (an * xn) : rn;
-      if (!(rel == rel)) break;  // NaN: give up
+      if (!(rel == rel)) break;  // NaN (in b, x or the factor): give up, not converged
       if (rel <= tol) {
         ok = true;
         break;
@@ -850,7 +899,7 @@ static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, dou
       ++it;
     }
     worst_it = std::max(worst_it, it);
-    worst_rel = std::max(worst_rel, rel);
+    worst_rel = (rel == rel && worst_rel == worst_rel) ? std::max(worst_rel, rel) : NAN;
     all_ok = all_ok && ok;
   }
   if (iters) *iters = worst_it;
@@ -866,11 +915,11 @@ static std::vector<double> refine_graph_key(const btc_plan_s *p, const void *D, 
           (double)maxit,        (double)p->flow_var,  (double)p->ctas_per_sm, (double)(uintptr_t)p->trace_fac,
           (double)(uintptr_t)p->trace_solve, (double)(uintptr_t)p->phase, (double)p->inter_var,
           (double)p->inter_ctas, (double)(uintptr_t)p->ingD, (double)(uintptr_t)p->ingB,
-          (double)p->root_prec};
+          (double)p->root_prec, (double)p->wait_limit};
 }
 
 // Capture one refined factor + solve of m <= max_cols columns as an executable
-// graph: pack, interlaced factorization + forward sweep, double-FP32 root, solve
+// graph: pack, interlaced factorization + forward sweep, top-separator root, solve
 // tail, unpack, FP64 residual with the norm bound, stopping test; then a while
 // node whose body is one correction (solve, update, residual, stopping test),
 // repeated on the device until the test says stop; then one copy of the
@@ -1148,7 +1197,35 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
                                         cudaMemcpyHostToDevice)) != cudaSuccess))
     return cleanup(fail(BTC_ERR_CUDA, "btc_plan: interlaced schedule upload: %s", cudaGetErrorString(e)));
   p->device_bytes += (int64_t)((icode.size() + ideps.size()) * sizeof(int32_t) + tail.size() * sizeof(SolveFlowItem));
-  const size_t nflags = kFlowHeader + (size_t)std::max(std::max(p->n_fac, p->n_solve), std::max(p->n_inter, p->n_tail));
+  if (ks.tiled) {
+    std::vector<TileTask> tiles;
+    std::vector<int32_t> totals;
+    build_tile_tasks(p->hp, &tiles, &totals);
+    p->n_tiles = (int)tiles.size();
+    if ((e = cudaMalloc(&p->d_tiles, tiles.size() * sizeof(TileTask))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_tile_cnt, std::max<size_t>(totals.size(), 1) * sizeof(int))) != cudaSuccess)
+      return cleanup(fail(BTC_ERR_OOM, "btc_plan: tile task allocation: %s", cudaGetErrorString(e)));
+    if ((e = cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileTask), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return cleanup(fail(BTC_ERR_CUDA, "btc_plan: tile task upload: %s", cudaGetErrorString(e)));
+    p->device_bytes += (int64_t)(tiles.size() * sizeof(TileTask) + totals.size() * sizeof(int));
+    int occ = 0;
+    if ((rc = set_smem(ks.tile_flow, ks.tile_smem)) ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.tile_flow, kTileThreads, ks.tile_smem)) !=
+            cudaSuccess)
+      return cleanup(rc ? rc : fail(BTC_ERR_CUDA, "btc_plan: tile occupancy: %s", cudaGetErrorString(e)));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    p->tile_grid = std::max(1, occ) * std::max(1, sms);
+  }
+  // one flag per item of the largest launch, and one more that no item ever sets (the target of
+  // btc_plan_inject_stall)
+  const size_t nflags =
+      kFlowHeader + (size_t)std::max(std::max(p->n_fac, p->n_solve), std::max(p->n_inter, p->n_tail)) + 1;
+  p->stall_flag = (int)(nflags - 1 - kFlowHeader);
+  p->inter_code_h = icode;
+  p->inter_deps_h = ideps;
   if ((e = cudaMalloc(&p->d_fac_deps, p->hp.fac_deps.size() * sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_fac_deps_rl, p->hp.fac_deps_rl.size() * sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_solve_flow, p->hp.solve_flow.size() * sizeof(SolveFlowItem))) != cudaSuccess ||
@@ -1169,7 +1246,7 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
       (rc = set_smem(ks.root64_rl, ks.root_smem)) ||
       (rc = set_smem(ks.fwd, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.bwd, ks.bwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
-      (rc = set_smem(ks.resid, residual_smem_bytes(n, kMaxCols))) ||
+      (rc = set_smem(ks.resid, residual_smem_bytes(n, std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.fac_flow_rl, ks.fac_smem)) ||
       (rc = set_smem(ks.fac_rl, ks.fac_smem)) || (rc = set_smem(ks.root_rl, ks.root_smem)) ||
       (rc = set_smem(ks.solve_flow, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
@@ -1213,6 +1290,43 @@ int btc_plan_set_trace(btc_plan_t p, void *factor_trace, void *solve_trace) {
 int btc_plan_set_phase_trace(btc_plan_t p, void *phase) {
   if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_phase_trace: NULL plan");
   p->phase = (unsigned long long *)phase;
+  return BTC_OK;
+}
+
+int btc_plan_inject_stall(btc_plan_t p, int item, int64_t max_polls) {
+  if (!p) return fail(BTC_ERR_ARG, "btc_plan_inject_stall: NULL plan");
+  if (p->ks->tiled) return fail(BTC_ERR_UNSUPPORTED, "btc_plan_inject_stall: not for plans of blocked 256 nodes");
+  const int nflow = dtype_mixed(p->dtype) ? (int)p->fac_off[p->hp.levels - 1] : p->n_fac;
+  if (item >= nflow || (item >= 0 && max_polls < 64))
+    return fail(BTC_ERR_ARG, "btc_plan_inject_stall: item %d outside 0..%d or poll limit below 64", item, nflow - 1);
+  BTC_CUDA(cudaStreamSynchronize(p->stream));
+  // first dependency slot of `it` in the plain and in the interlaced lists (or -1)
+  auto inter_slot = [&](int it) {
+    for (size_t t = 0; t < p->inter_code_h.size(); ++t)
+      if (p->inter_code_h[t] == it) return (int64_t)t * kInterDeps;
+    return (int64_t)-1;
+  };
+  auto put = [&](int32_t *dst, int64_t off, int32_t v) -> int {
+    if (off < 0) return BTC_OK;
+    BTC_CUDA(cudaMemcpy(dst + off, &v, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return BTC_OK;
+  };
+  int rc;
+  if (p->stall_item >= 0) {  // restore the planner's dependency lists
+    const int it = p->stall_item;
+    const int64_t si = inter_slot(it);
+    if ((rc = put(p->d_fac_deps, 3 * (int64_t)it, p->hp.fac_deps[3 * (size_t)it])) ||
+        (rc = put(p->d_inter_deps, si, si >= 0 ? p->inter_deps_h[si] : -1)))
+      return rc;
+    p->stall_item = -1;
+  }
+  p->wait_limit = kMaxPolls;
+  if (item < 0) return BTC_OK;
+  if ((rc = put(p->d_fac_deps, 3 * (int64_t)item, p->stall_flag)) ||
+      (rc = put(p->d_inter_deps, inter_slot(item), p->stall_flag)))
+    return rc;
+  p->stall_item = item;
+  p->wait_limit = max_polls;
   return BTC_OK;
 }
 
@@ -1595,7 +1709,7 @@ int btc_free(btc_plan_t p) {
   void *dev[] = {p->dpool,        p->epool,        p->d_fac,    p->d_fwd,  p->d_bwd,     p->d_rb,
                  p->d_y,          p->s_D,          p->d_fac_deps, p->d_solve_flow, p->d_flow, p->s_B,
                  p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail,
-                 p->kry};
+                 p->kry,          p->d_tiles,      p->d_tile_cnt};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_rb) cudaFreeHost(p->h_rb);

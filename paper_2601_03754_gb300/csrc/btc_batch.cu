@@ -104,15 +104,15 @@ __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const Batc
       for (int k = 0; k < kResParts; ++k) ax += ps[k * NMAX + r];
       const double v = b[(size_t)i * n + r] - ax;
       y[(size_t)blockIdx.x * np + r] = (T)v;
-      rmax = fmax(rmax, fabs(v));
-      xmax = fmax(xmax, fabs(xs[NMAX + r]));
+      rmax = nan_max(rmax, fabs(v));
+      xmax = nan_max(xmax, fabs(xs[NMAX + r]));
     } else {
       y[(size_t)blockIdx.x * np + r] = T(0);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    rmax = nan_max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    xmax = nan_max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
   }
   if ((threadIdx.x & 31) == 0) {
     atomic_max_nonneg(norms + 3 * nd.inst + 0, rmax);
@@ -170,7 +170,7 @@ struct BatchGroup {
   FactorItem *d_fac = nullptr;
   int32_t *d_fac_deps = nullptr;
   int n_fac = 0, n_first = 0;
-  FactorItem *d_roots = nullptr;  // double-FP32 roots (mixed path): [level-1 roots | other roots]
+  FactorItem *d_roots = nullptr;  // top-separator roots (mixed path, FP64 Cholesky): [level-1 roots | other roots]
   int n_roots_first = 0, n_roots_rest = 0;
   SolveFlowItem *d_solve = nullptr;
   int n_solve = 0;
@@ -331,7 +331,7 @@ static int build_group(btc_batch_s *bt, BatchGroup &g) {
   if ((rc = batch_alloc((void **)&g.d_flow, nflags * sizeof(int), acc))) return rc;
   BTC_CUDA(cudaMemset(g.d_flow, 0, nflags * sizeof(int)));
   if ((rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.solve_flow, ks.fwd_smem(1))) ||
-      (rc = set_smem(ks.root_first, ks.root_smem)) || (rc = set_smem(ks.root_rest, ks.root_smem)))
+      (rc = set_smem(ks.root64_first, ks.root_smem)) || (rc = set_smem(ks.root64_rest, ks.root_smem)))
     return rc;
   int dev = 0, sms = 0, bf = 0, bsl = 0;
   cudaGetDevice(&dev);
@@ -430,6 +430,8 @@ int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int 
     if (N[k] < 1 || n[k] < 1) return cleanup(fail(BTC_ERR_ARG, "instance %d: invalid sizes", k));
     const int np = padded_size(n[k], dtype);
     if (!np) return cleanup(fail(BTC_ERR_UNSUPPORTED, "instance %d: block size %d not compiled", k, n[k]));
+    if (np > 128)
+      return cleanup(fail(BTC_ERR_UNSUPPORTED, "instance %d: batches take block sizes up to 128 (n = %d)", k, n[k]));
     by_np[np].push_back(k);
   }
   int rc;
@@ -516,12 +518,12 @@ int btc_batch_factor(btc_batch_t bt, const void *const *D, const void *const *B)
     if (g.n_roots_first > 0) {
       a.items = g.d_roots;
       a.count = g.n_roots_first;
-      if ((rc = launch_n(k.root_first, g.n_roots_first, k.root_threads, k.root_smem, g.s, a, none))) break;
+      if ((rc = launch_n(k.root64_first, g.n_roots_first, k.root_threads, k.root_smem, g.s, a, none))) break;
     }
     if (g.n_roots_rest > 0) {
       a.items = g.d_roots + g.n_roots_first;
       a.count = g.n_roots_rest;
-      if ((rc = launch_n(k.root_rest, g.n_roots_rest, k.root_threads, k.root_smem, g.s, a, none))) break;
+      if ((rc = launch_n(k.root64_rest, g.n_roots_rest, k.root_threads, k.root_smem, g.s, a, none))) break;
     }
   }
   const int rj = batch_join(bt);
@@ -623,6 +625,7 @@ int btc_batch_solve_refined(btc_batch_t bt, const double *const *b, double *cons
       if (!(rel == rel)) nan = true;
       worst = std::max(worst, rel);
     }
+    if (nan) worst = NAN;  // reported as such: a NaN residual never counts as converged
     if (nan || worst <= tol || it >= maxit) break;
     if ((rc = batch_fork(bt))) return rc;
     for (BatchGroup &g : bt->groups) {

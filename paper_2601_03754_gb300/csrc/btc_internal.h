@@ -73,6 +73,49 @@ struct SolveFlowItem {
   int32_t dep[3];    // indices of the items this one waits for (-1: none), all smaller
 };
 
+// Blocked node elimination for blocks larger than one CTA's shared memory
+// (padded n = 256): every node of Alg. 5 becomes a few tasks on 128 x 128
+// tiles (kTileT) of its 256 x 256 blocks (row stride kTileNP), run by one
+// persistent launch. Per node, in phase order:
+//   A  deferred syrk: S_e(i,j) -= sum_k P_a(k,i)^T P_a(k,j), upper tiles   (TK_GEMM x3)
+//   P  blocked potrf of S_e: U00, U01 = U00^-T S01, S11 -= U01^T U01, U11 (TK_POTRF)
+//   T  trsm of S(e,e-s) and S(e,e+s), one task per column tile j:
+//      Z0j = U00^-T R0j, R1j -= U01^T Z0j, Z1j = U11^-T R1j            (TK_TRSM x2 per block)
+//   G  S_{e+s}(i,j) -= P_b^T P_b + U_dn^T U_dn, upper tiles              (TK_GEMM x3)
+//      fill(i,j) = -U_up^T U_dn or -U_dn^T U_up, all four tiles          (TK_GEMM x4)
+// A node's tasks wait for its earlier phases (node counter >= wait_self) and
+// for the nodes of the previous level that produce its blocks (the producers
+// of Alg. 5's dataflow, each counter >= its task total).
+constexpr int kTileT = 128, kTileNP = 256;
+enum : int32_t { TK_GEMM = 0, TK_POTRF = 1, TK_TRSM = 2 };
+enum : int32_t {
+  TG_NEG_STORE = 1,  // gemm: C = -(sum) (a fill block); else C -= sum
+  TG_C_EPOOL = 2,    // gemm: C lives in the off-diagonal pool; else in the diagonal pool
+};
+struct TileTask {
+  int64_t c;       // GEMM: C block; POTRF: S_e block; TRSM: U_e block (element offsets)
+  int64_t x0, y0;  // GEMM: first operand pair (blocks of the off-diagonal pool); TRSM: x0 = R block
+  int64_t x1, y1;  // GEMM: second operand pair, or -1
+  int32_t kind, flags;
+  int32_t ti, tj;       // GEMM: output tile; TRSM: tj = column tile
+  int32_t counter;      // this node's completion counter
+  int32_t wait_self;    // tasks of this node in earlier phases
+  int32_t dep[3];       // producer counters (-1: none)
+  int32_t dep_n[3];     // ... and their task totals
+  int32_t node, inst;   // node (0-based, for pivot reports) and instance
+};
+
+constexpr int kTileThreads = 256;  // threads of a tile-task CTA (a 16 x 16 grid of 8 x 8 register tiles)
+
+// Arguments of the persistent tile-task launch.
+struct TileArgs {
+  const TileTask *tasks;
+  int count;
+  float *dpool, *epool;
+  int *counters;             // one per node (flat factor index): its tasks finished
+  unsigned long long *info;  // pivot report per instance
+};
+
 struct LevelSchedule {
   int s;  // stride 2^(l-1)
   std::vector<FactorItem> fac;
@@ -118,6 +161,10 @@ void build_interlaced(const HostPlan &P, bool root_separate, std::vector<int32_t
 // concatenate instances.
 void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64_t y_base, int inst,
                      HostPlan *out);
+
+// Tile tasks of a plan in launch order (level by level, phase by phase within
+// a level) and the task total of every node (indexed like the flat factor list).
+void build_tile_tasks(const HostPlan &P, std::vector<TileTask> *tasks, std::vector<int32_t> *node_total);
 
 int padded_size(int n, int dtype);       // np for a block size (0 if unsupported)
 int64_t count_offdiag(int N);            // sum over levels of floor(N/s) - 1

@@ -26,9 +26,9 @@ struct KernelSet {
   const void *fac_first = nullptr, *fac_rest = nullptr;
   int fac_threads = 0;
   size_t fac_smem = 0;
-  // double-FP32 top-separator Cholesky for the mixed path (FP32 pools)
+  // top-separator Cholesky of the mixed path (FP32 pools): double-FP32 and FP64 forms
   const void *root_first = nullptr, *root_rest = nullptr;
-  const void *root64_first = nullptr, *root64_rest = nullptr, *root64_rl = nullptr;  // FP64 form (option)
+  const void *root64_first = nullptr, *root64_rest = nullptr, *root64_rl = nullptr;  // FP64 form (default)
   int root_threads = 0;
   size_t root_smem = 0;
   // persistent dataflow forms (all levels in one launch)
@@ -40,8 +40,13 @@ struct KernelSet {
   // fac_flow, fac_fwd_flow and fac_flow_rl above are those of flow_v[flow_default]
   FlowVariant flow_v[kFlowVariants];
   int n_flow_v = 0, flow_default = 0;
-  bool tensor_cores = false;  // level elimination products on tcgen05 (TF32)
-  // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, double-FP32 root
+  bool tensor_cores = false;  // level elimination products on tcgen05 (TF32 or BF16 operands)
+  // blocked nodes of tile tasks (padded n = 256): a packing pass (pack_matrix) and one persistent
+  // launch of tile tasks replace the node kernels; the top separator is one more node of that launch
+  bool tiled = false;
+  const void *tile_flow = nullptr;
+  size_t tile_smem = 0;
+  // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, double-FP32 root (its FP64 form is root64_rl)
   const void *pack_matrix = nullptr, *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
   // solve
   const void *fwd = nullptr, *bwd = nullptr;
@@ -57,13 +62,13 @@ const KernelSet &kernels_for(int dtype, int np);
 // Every compiled (dtype, padded block size) pair; each has its own translation
 // unit btc_set_<dtype>_<np>.cu so that the build compiles them in parallel.
 // FP64 stops at 96 (three 128 x 128 FP64 blocks exceed one SM's shared memory);
-// the TF32 tensor-core dtype has its own set at 128 and shares the mixed FP32
-// sets below it.
+// the TF32 and BF16 tensor-core dtypes have their own sets at 128 and 256 (the
+// blocked node of tile tasks) and share the mixed FP32 sets below 128.
 #define BTC_FOR_EACH_SET(X)                                                                              \
   X(f64, 8) X(f64, 16) X(f64, 32) X(f64, 48) X(f64, 64) X(f64, 96)                                        \
   X(f32, 8) X(f32, 16) X(f32, 32) X(f32, 48) X(f32, 64) X(f32, 96) X(f32, 128)                            \
   X(mixed, 8) X(mixed, 16) X(mixed, 32) X(mixed, 48) X(mixed, 64) X(mixed, 96) X(mixed, 128)                \
-  X(tf32, 128)
+  X(tf32, 128) X(bf16, 128) X(tf32, 256) X(bf16, 256)
 #define BTC_DECLARE_SET(dt, np) KernelSet make_set_##dt##_##np();
 BTC_FOR_EACH_SET(BTC_DECLARE_SET)
 #undef BTC_DECLARE_SET

@@ -19,6 +19,7 @@ template <typename T, int NP>
 size_t bwd_smem_fn(int m) { return bwd_smem_bytes<T, NP>(m); }
 template <typename T, int NP, int R>
 size_t fused_smem_fn(int m) { return fused_smem_bytes<T, NP, R>(m); }
+inline size_t zero_smem_fn(int) { return 0; }
 
 // Residency variants of the persistent factor kernels: caps 1, 2, 3, 4 CTAs per
 // SM (1, 2, 4, 8 for 64-thread CTAs), those that shared memory and threads allow.

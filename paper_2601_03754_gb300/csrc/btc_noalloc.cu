@@ -19,6 +19,10 @@ constexpr int kMaxDevices = 64;
 // Partial maxima of block row i at [3*i .. 3*i+2]; the reduced result at the end.
 static __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMaxBlocks + 3];
 
+// max(a, b) that propagates NaN (fmax drops it), so that a NaN in b, x or the
+// matrix shows in the returned norms.
+__device__ __forceinline__ double max_keep_nan(double a, double b) { return (b > a || b != b) ? b : a; }
+
 // Host-side device addresses of g_noalloc_scratch, one per device (the array's
 // name in host code is only a stand-in, never a device address).
 static double *g_scratch_ptr[kMaxDevices] = {nullptr};
@@ -52,7 +56,7 @@ __global__ void k_residual_rows(const double *D, const double *B, const double *
       for (int c = 0; c < n; ++c) s += fabs(Bl[r * ld + c]);
     if (i + 1 < N)
       for (int c = 0; c < n; ++c) s += fabs(Br[c * ld + r]);
-    amax = fmax(amax, s);
+    amax = max_keep_nan(amax, s);
   }
   for (int q = threadIdx.x; q < n * m; q += blockDim.x) {
     const int r = q / m, col = q % m;
@@ -66,13 +70,13 @@ __global__ void k_residual_rows(const double *D, const double *B, const double *
       const double *xn = x + (size_t)(i + 1) * n * m;
       for (int c = 0; c < n; ++c) v = fma(-Br[c * ld + r], xn[c * m + col], v);
     }
-    rmax = fmax(rmax, fabs(v));
-    xmax = fmax(xmax, fabs(xi[r * m + col]));
+    rmax = max_keep_nan(rmax, fabs(v));
+    xmax = max_keep_nan(xmax, fabs(xi[r * m + col]));
   }
   for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    rmax = max_keep_nan(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    amax = max_keep_nan(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    xmax = max_keep_nan(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
   }
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) {
@@ -83,7 +87,7 @@ __global__ void k_residual_rows(const double *D, const double *B, const double *
   __syncthreads();
   if (threadIdx.x < 3) {
     double v = 0.0;
-    for (int k = 0; k < nw; ++k) v = fmax(v, red[threadIdx.x][k]);
+    for (int k = 0; k < nw; ++k) v = max_keep_nan(v, red[threadIdx.x][k]);
     part[3 * i + threadIdx.x] = v;  // every slot of rows 0..N-1 is overwritten: nothing to clear
   }
 }
@@ -93,16 +97,16 @@ __global__ void k_reduce_rows(const double *part, int N, double *out) {
   __shared__ double red[3][32];
   double v[3] = {0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < N; i += blockDim.x)
-    for (int k = 0; k < 3; ++k) v[k] = fmax(v[k], part[3 * i + k]);
+    for (int k = 0; k < 3; ++k) v[k] = max_keep_nan(v[k], part[3 * i + k]);
   for (int k = 0; k < 3; ++k)
-    for (int o = 16; o > 0; o >>= 1) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    for (int o = 16; o > 0; o >>= 1) v[k] = max_keep_nan(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0)
     for (int k = 0; k < 3; ++k) red[k][w] = v[k];
   __syncthreads();
   if (threadIdx.x < 3) {
     double r = 0.0;
-    for (int k = 0; k < nw; ++k) r = fmax(r, red[threadIdx.x][k]);
+    for (int k = 0; k < nw; ++k) r = max_keep_nan(r, red[threadIdx.x][k]);
     out[threadIdx.x] = r;
   }
 }

@@ -10,13 +10,15 @@
 
 namespace btc {
 
-static const int kSizes[] = {8, 16, 32, 48, 64, 96, 128};
+static const int kSizes[] = {8, 16, 32, 48, 64, 96, 128, 256};
 
 // Smallest compiled block size >= n. FP64 stops at 96: three 128 x 128 FP64
-// blocks do not fit in one SM's shared memory.
+// blocks do not fit in one SM's shared memory. 256 (the blocked node of tile
+// tasks) exists for the tensor-core dtypes (3: TF32, 4: BF16) only.
 int padded_size(int n, int dtype) {
   for (int s : kSizes) {
     if (dtype == 0 && s > 96) break;
+    if (s > 128 && dtype != 3 && dtype != 4) break;
     if (n <= s) return s;
   }
   return 0;
@@ -279,6 +281,108 @@ void build_interlaced(const HostPlan &P, bool root_separate, std::vector<int32_t
     q.dep[2] = (root_fwd >= 0 && q.dep[2] == root_fwd) ? 0 : -1;
     tail->push_back(q);
   }
+}
+
+}  // namespace btc
+
+namespace btc {
+
+void build_tile_tasks(const HostPlan &P, std::vector<TileTask> *tasks, std::vector<int32_t> *node_total) {
+  constexpr int64_t T = kTileT, LDG = kTileNP;
+  tasks->clear();
+  int32_t nitems = 0;
+  for (const LevelSchedule &L : P.lv) nitems += (int32_t)L.fac.size();
+  node_total->assign(nitems, 0);
+  // per-node task counts by phase
+  auto count_phases = [](const FactorItem &it, int32_t c[4]) {
+    c[0] = it.p_a >= 0 ? 3 : 0;
+    c[1] = 1;
+    c[2] = (it.r_up >= 0 ? 2 : 0) + (it.r_down >= 0 ? 2 : 0);
+    c[3] = (it.d_next >= 0 ? 3 : 0) + (it.fill >= 0 ? 4 : 0);
+  };
+  int32_t base = 0;  // flat index of the level's first item
+  for (const LevelSchedule &L : P.lv) {
+    const int32_t nl = (int32_t)L.fac.size();
+    for (int32_t q = 0; q < nl; ++q) {
+      int32_t c[4];
+      count_phases(L.fac[q], c);
+      (*node_total)[base + q] = c[0] + c[1] + c[2] + c[3];
+    }
+    for (int phase = 0; phase < 4; ++phase)
+      for (int32_t q = 0; q < nl; ++q) {
+        const FactorItem &it = L.fac[q];
+        const int32_t f = base + q;
+        int32_t c[4];
+        count_phases(it, c);
+        int32_t before = 0;
+        for (int k = 0; k < phase; ++k) before += c[k];
+        TileTask t;
+        t.c = t.x0 = t.y0 = t.x1 = t.y1 = -1;
+        t.kind = TK_GEMM;
+        t.flags = 0;
+        t.ti = t.tj = 0;
+        t.counter = f;
+        t.wait_self = before;
+        for (int k = 0; k < 3; ++k) {
+          const int32_t d = P.fac_deps.empty() ? -1 : P.fac_deps[3 * (size_t)f + k];
+          t.dep[k] = d;
+          t.dep_n[k] = d >= 0 ? (*node_total)[d] : 0;
+        }
+        t.node = it.node;
+        t.inst = it.inst;
+        auto gemm = [&](int64_t c_blk, int flags, int64_t x0, int64_t y0, int64_t x1, int64_t y1, int i, int j) {
+          TileTask g = t;
+          g.kind = TK_GEMM;
+          g.flags = flags;
+          g.c = c_blk;
+          g.x0 = x0;
+          g.y0 = y0;
+          g.x1 = x1;
+          g.y1 = y1;
+          g.ti = i;
+          g.tj = j;
+          tasks->push_back(g);
+        };
+        static const int up3[3][2] = {{0, 0}, {0, 1}, {1, 1}};
+        if (phase == 0 && it.p_a >= 0)
+          for (auto &ij : up3) gemm(it.d_self, 0, it.p_a, it.p_a, -1, -1, ij[0], ij[1]);
+        if (phase == 1) {
+          TileTask pt = t;
+          pt.kind = TK_POTRF;
+          pt.c = it.d_self;
+          tasks->push_back(pt);
+        }
+        if (phase == 2)
+          for (int64_t r : {it.r_up, it.r_down}) {
+            if (r < 0) continue;
+            for (int j = 0; j < 2; ++j) {
+              TileTask tt = t;
+              tt.kind = TK_TRSM;
+              tt.c = it.d_self;
+              tt.x0 = r;
+              tt.tj = j;
+              tasks->push_back(tt);
+            }
+          }
+        if (phase == 3) {
+          if (it.d_next >= 0) {
+            const int64_t pb = it.p_b >= 0 ? it.p_b : -1;
+            for (auto &ij : up3)
+              if (pb >= 0) gemm(it.d_next, 0, pb, pb, it.r_down, it.r_down, ij[0], ij[1]);
+              else gemm(it.d_next, 0, it.r_down, it.r_down, -1, -1, ij[0], ij[1]);
+          }
+          if (it.fill >= 0) {
+            const bool upfirst = (it.flags & FI_FILL_UPFIRST) != 0;
+            const int64_t X = upfirst ? it.r_up : it.r_down, Y = upfirst ? it.r_down : it.r_up;
+            for (int i = 0; i < 2; ++i)
+              for (int j = 0; j < 2; ++j) gemm(it.fill, TG_NEG_STORE | TG_C_EPOOL, X, Y, -1, -1, i, j);
+          }
+        }
+      }
+    base += nl;
+  }
+  (void)T;
+  (void)LDG;
 }
 
 }  // namespace btc

@@ -15,7 +15,7 @@ namespace btc {
 int fail(int code, const char *fmt, ...);
 int set_smem(const void *fn, size_t bytes);
 bool dtype_ok(int dtype);
-bool dtype_mixed(int dtype);  // FP64 inputs, FP32 factor, double-FP32 root, FP64 refinement
+bool dtype_mixed(int dtype);  // FP64 inputs, FP32 factor, FP64 (or double-FP32) root, FP64 refinement
 
 constexpr int kMaxCols = 16;     // right-hand sides per solve launch
 constexpr int kFlowHeader = 4;   // ints before the done flags of a flow state array

@@ -114,11 +114,16 @@ void evict_for(btc_server_s *s, int64_t need) {
   }
 }
 
-// The oldest admissible job, or -1. Caller holds mu.
+// The oldest admissible job, or -1. Caller holds mu. A re-solve whose cached
+// factor is in use by a running re-solve waits (the plan's work vectors,
+// norms and stream are per plan, so two solves on one plan would overwrite
+// each other's state); the jobs behind it may pass it. Every other job keeps
+// FIFO order.
 long pick(btc_server_s *s) {
   for (size_t i = 0; i < s->queue.size(); ++i) {
     const Job &j = s->queue[i];
     const bool resolve = j.req.factor_id >= 0 && s->cached.count(j.req.factor_id);
+    if (resolve && s->pinned.count(j.req.factor_id)) continue;
     const int64_t need = resolve ? 0 : j.bytes;
     if (s->in_flight_bytes + s->cached_bytes + s->free_bytes + need <= s->budget) return (long)i;
     evict_for(s, need);
@@ -233,7 +238,7 @@ int btc_server_start(btc_server_t *out, int dtype, int slots, int64_t hbm_budget
   if (!out || slots < 1 || slots > 64 || hbm_budget_bytes <= 0)
     return btc::fail(BTC_ERR_ARG, "btc_server_start: invalid arguments");
   if (dtype != BTC_F64 && !btc::dtype_mixed(dtype))
-    return btc::fail(BTC_ERR_ARG, "btc_server_start: dtype must be BTC_F64, BTC_MIXED_F32 or BTC_MIXED_TF32");
+    return btc::fail(BTC_ERR_ARG, "btc_server_start: dtype must be BTC_F64 or one of the BTC_MIXED_* dtypes");
   btc_server_s *s = new btc_server_s();
   s->dtype = dtype;
   s->slots = slots;

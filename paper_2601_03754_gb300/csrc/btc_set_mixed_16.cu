@@ -1,4 +1,4 @@
-// Kernel set: FP64 inputs, FP32 factor and correction solves, double-FP32 top-separator Cholesky, padded block size 16.
+// Kernel set: FP64 inputs, FP32 factor and correction solves, FP64 (or double-FP32) top-separator Cholesky, padded block size 16.
 #include "btc_make.cuh"
 
 namespace btc {

@@ -1,5 +1,5 @@
 // Kernel set: FP64 inputs, FP32 factor with the level-elimination products on
-// tcgen05 (TF32), FP32 correction solves, double-FP32 top-separator Cholesky; padded
+// tcgen05 (TF32), FP32 correction solves, FP64 (or double-FP32) top-separator Cholesky; padded
 // block size 128.
 #include "btc_make.cuh"
 #include "btc_tc.cuh"
@@ -10,14 +10,14 @@ namespace btc {
 // tcgen05 form; the right-looking variant keeps the FP32 FMA kernels.
 KernelSet make_set_tf32_128() {
   KernelSet k = make_set<float, double, kTcNP, true>();
-  k.fac_first = (const void *)&k_factor_level_tc<double, true>;
-  k.fac_rest = (const void *)&k_factor_level_tc<double, false>;
+  k.fac_first = (const void *)&k_factor_level_tc<double, true, 4>;
+  k.fac_rest = (const void *)&k_factor_level_tc<double, false, 4>;
   k.n_flow_v = 1;
   k.flow_default = 0;
   FlowVariant &v = k.flow_v[0];
   v.minb = 1;
-  v.fac = (const void *)&k_factor_flow_tc<double>;
-  v.fac_fwd = (const void *)&k_factor_fwd_flow_tc<double>;
+  v.fac = (const void *)&k_factor_flow_tc<double, 4>;
+  v.fac_fwd = (const void *)&k_factor_fwd_flow_tc<double, 4>;
   k.fac_flow = v.fac;
   k.fac_fwd_flow = v.fac_fwd;
   k.fac_flow_rl = v.fac_rl;

@@ -22,6 +22,10 @@ struct SolveCfg {
   // coupling blocks are read once from global memory inside the products
   // (three staged 128 x 128 blocks would leave one CTA per SM)
   static constexpr bool STREAM = NP >= 96;
+  // blocks larger than 128 (256 KB in FP32): the diagonal factor is read from
+  // global memory too, row by row inside the triangular solves
+  static constexpr bool DIAG_GLOBAL = NP > 128;
+  static constexpr int LDU = DIAG_GLOBAL ? NP : LDL;  // leading dimension of the diagonal factor as read
 };
 
 __device__ __forceinline__ void cp_async16_s(void *smem, const void *gmem) {
@@ -70,10 +74,11 @@ struct TrsvCfg {
 
 // Y <- U^{-T} Y (forward, with the upper factor U) for the m columns of Y
 // (np x m in shared memory), by warps: warp w takes columns w, w + nwarps, ...
-// Row j of U is read (U[j][i], i > j), contiguous across lanes.
+// Row j of U is read (U[j][i], i > j), contiguous across lanes. U: shared
+// memory, or global memory for the blocks of SolveCfg::DIAG_GLOBAL.
 template <typename T, int NP>
 __device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *dinv) {
-  constexpr int LDL = SolveCfg<T, NP>::LDL, CH = TrsvCfg<T, NP>::CH;
+  constexpr int LDL = SolveCfg<T, NP>::LDU, CH = TrsvCfg<T, NP>::CH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
   for (int q = warp; q < m && warp < nw; q += nw) {
 #pragma unroll 1
@@ -104,7 +109,7 @@ __device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *
 // substitution chain reads no shared memory.
 template <typename T, int NP>
 __device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *dinv) {
-  constexpr int LDL = SolveCfg<T, NP>::LDL, CH = TrsvCfg<T, NP>::CH, V = TrsvCfg<T, NP>::V;
+  constexpr int LDL = SolveCfg<T, NP>::LDU, CH = TrsvCfg<T, NP>::CH, V = TrsvCfg<T, NP>::V;
   static_assert(CH % V == 0, "chunk rows must hold whole 16-byte loads");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
   for (int q = warp; q < m && warp < nw; q += nw) {
@@ -161,7 +166,7 @@ struct SolveSmem {
   T *U0, *U1, *U2, *dinv, *y0, *y1, *y2;
   __device__ __forceinline__ explicit SolveSmem(unsigned char *raw, int m) {
     constexpr int LDL = SolveCfg<T, NP>::LDL;
-    constexpr int NB = SolveCfg<T, NP>::STREAM ? 1 : 3;
+    constexpr int NB = SolveCfg<T, NP>::DIAG_GLOBAL ? 0 : SolveCfg<T, NP>::STREAM ? 1 : 3;
     U0 = reinterpret_cast<T *>(raw);
     U1 = NB == 3 ? U0 + NP * LDL : nullptr;
     U2 = NB == 3 ? U1 + NP * LDL : nullptr;
@@ -181,7 +186,7 @@ __device__ __forceinline__ void stage_item_blocks(const SolveSmem<T, NP> &sm, co
                                                   int64_t v1, int64_t e1, int64_t v2, int64_t e2) {
   const T *dpool = reinterpret_cast<const T *>(a.dpool);
   const T *epool = reinterpret_cast<const T *>(a.epool);
-  if (d0 >= 0) stage_block<T, NP>(sm.U0, dpool + d0);
+  if (!SolveCfg<T, NP>::DIAG_GLOBAL && d0 >= 0) stage_block<T, NP>(sm.U0, dpool + d0);
   if constexpr (!SolveCfg<T, NP>::STREAM) {
     if (v1 >= 0) stage_block<T, NP>(sm.U1, epool + e1);
     if (v2 >= 0) stage_block<T, NP>(sm.U2, epool + e2);
@@ -195,10 +200,12 @@ __device__ __forceinline__ void stage_item_blocks(const SolveSmem<T, NP> &sm, co
 template <typename T, int NP, bool STAGED = false>
 __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_l, int64_t y_r, int64_t e_r,
                                          int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
-  constexpr int LDL = SolveCfg<T, NP>::LDL;
+  constexpr int LDL = SolveCfg<T, NP>::LDL, LDU = SolveCfg<T, NP>::LDU;
   const int m = a.m;
   const SolveSmem<T, NP> sm(smem_raw, m);
-  T *Us = sm.U0, *Ul = sm.U1, *Ur = sm.U2, *dinv = sm.dinv, *ys = sm.y0, *yl = sm.y1, *yr = sm.y2;
+  const T *Us = SolveCfg<T, NP>::DIAG_GLOBAL ? reinterpret_cast<const T *>(a.dpool) + (d_self >= 0 ? d_self : 0)
+                                             : sm.U0;
+  T *Ul = sm.U1, *Ur = sm.U2, *dinv = sm.dinv, *ys = sm.y0, *yl = sm.y1, *yr = sm.y2;
   T *y = reinterpret_cast<T *>(a.y);
   const int nm = NP * m;
   T *yself = y + y_self * nm;
@@ -209,7 +216,7 @@ __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_
   cp_async_wait_all_s();
   __syncthreads();
   if (d_self >= 0)
-    for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
+    for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDU + j];
   if (y_l >= 0) {
     const bool right = y_r >= 0;
     if constexpr (SolveCfg<T, NP>::STREAM) {  // coupling blocks from global memory, coalesced over c
@@ -258,10 +265,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
 template <typename T, int NP, bool STAGED = false>
 __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e_dn, int64_t x_up, int64_t e_up,
                                          int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
-  constexpr int LDL = SolveCfg<T, NP>::LDL;
+  constexpr int LDL = SolveCfg<T, NP>::LDL, LDU = SolveCfg<T, NP>::LDU;
   const int m = a.m;
   const SolveSmem<T, NP> sm(smem_raw, m);
-  T *Us = sm.U0, *Ud = sm.U1, *Uu = sm.U2, *dinv = sm.dinv, *ys = sm.y0, *xd = sm.y1, *xu = sm.y2;
+  const T *Us = SolveCfg<T, NP>::DIAG_GLOBAL ? reinterpret_cast<const T *>(a.dpool) + d_self : sm.U0;
+  T *Ud = sm.U1, *Uu = sm.U2, *dinv = sm.dinv, *ys = sm.y0, *xd = sm.y1, *xu = sm.y2;
   T *y = reinterpret_cast<T *>(a.y);
   const int nm = NP * m;
   T *yself = y + x_self * nm;
@@ -271,7 +279,7 @@ __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e
   if (x_up >= 0) stage_vec<T>(xu, y + x_up * nm, nm);
   cp_async_wait_all_s();
   __syncthreads();
-  for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDL + j];
+  for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDU + j];
   if (x_dn >= 0 || x_up >= 0) {
     const bool dn = x_dn >= 0, up = x_up >= 0;
     if constexpr (SolveCfg<T, NP>::STREAM) {
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowS
 
 template <typename T, int NP>
 constexpr size_t fwd_smem_bytes(int m) {
-  constexpr size_t nb = SolveCfg<T, NP>::STREAM ? 1 : 3;
+  constexpr size_t nb = SolveCfg<T, NP>::DIAG_GLOBAL ? 0 : SolveCfg<T, NP>::STREAM ? 1 : 3;
   return sizeof(T) * (nb * NP * SolveCfg<T, NP>::LDL + NP + 3 * (size_t)NP * m);
 }
 template <typename T, int NP>
@@ -385,7 +393,14 @@ __global__ void k_unpack(S *x, const T *y, int N, int n, int np, int m, int ldx,
   }
 }
 
-// Non-negative doubles order like their bit patterns.
+// max(a, b) that propagates NaN (fmax drops it): a NaN entry of r or x must
+// reach the host, where it stops the refinement instead of vanishing from the
+// norms.
+__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
+__device__ __forceinline__ float nan_maxf(float a, float b) { return (b > a || b != b) ? b : a; }
+
+// Non-negative doubles order like their bit patterns; a NaN with the sign bit
+// clear (fabs of any NaN) orders above +inf, so it wins the maximum.
 __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
@@ -471,22 +486,22 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
     const int r = q / m, col = q % m;
     const double v = b[(size_t)i * nm + q] - ax;
     if (y) y[(node_base + i) * np * m + r * m + col] = convert_in<T, double>(v);
-    rmax = fmax(rmax, fabs(v));
-    xmax = fmax(xmax, fabs(xs[nm + q]));
+    rmax = nan_max(rmax, fabs(v));
+    xmax = nan_max(xmax, fabs(xs[nm + q]));
     if (with_anorm && col == 0) {
       float rs = 0.0f;
 #pragma unroll
       for (int k = 0; k < kResParts; ++k) rs = __fadd_rz(rs, as[k * n + r]);
-      amax = fmaxf(amax, rs);
+      amax = nan_maxf(amax, rs);
     }
   }
   if (y) {
     for (int q = threadIdx.x; q < (np - n) * m; q += blockDim.x) y[(node_base + i) * np * m + n * m + q] = T(0);
   }
   for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    rmax = nan_max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    xmax = nan_max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    amax = nan_maxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   }
   if ((threadIdx.x & 31) == 0) {
     atomic_max_nonneg(norms + 0, rmax);

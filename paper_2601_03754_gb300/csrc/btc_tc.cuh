@@ -1,18 +1,25 @@
-// Tensor-core (tcgen05, TF32) form of the level elimination for 128 x 128
-// blocks: the four n^3 products of a node (Alg. 5: the two deferred syrk, the
+// Tensor-core (tcgen05) form of the level elimination for 128 x 128 blocks:
+// the four n^3 products of a node (Alg. 5: the two deferred syrk, the
 // immediate syrk onto the next diagonal block and the fill gemm) run as
 // tcgen05.mma with operands in shared memory and FP32 accumulators in TMEM;
 // the Cholesky and the two triangular solves stay on the FP32 FMA pipes
-// (btc_tile.cuh). The accuracy lost to TF32 operands is won back by the FP64
-// refinement of the mixed-precision solve.
+// (btc_tile.cuh). Operands are TF32 (kind::tf32, 4-byte elements) or BF16
+// (kind::f16 with BF16 A and B, 2-byte elements), both accumulated in FP32.
+// The accuracy lost to the short operands is won back by the FP64 refinement
+// of the mixed-precision solve.
 //
 // Operand layout (tcgen05 shared-memory descriptor, no swizzle, K-major): an
-// M x K operand is stored as 8-row x 16-byte core matrices; element (m, k) at
-// byte (m/8)*SBO + (k/4)*LBO + (m%8)*16 + (k%4)*4 with LBO = 128 (core
-// matrices adjacent along K) and SBO = 32 K (adjacent 8-row groups). A product
-// C[i][j] = sum_k X[k][i] Y[k][j] takes A(m=i, k) = X[k][i] and B(n=j, k) =
-// Y[k][j], i.e. both pool blocks in the same "transposed" operand layout.
+// M x K operand is stored as core matrices of 8 rows x 16 bytes (4 TF32 or 8
+// BF16 elements along K); element (m, k) sits at byte
+// (m/8)*SBO + (k/CK)*LBO + (m%8)*16 + (k%CK)*OPB, with CK = 16/OPB elements
+// per core-matrix row, LBO = 128 (core matrices adjacent along K) and
+// SBO = 128 * OPB * 8 (adjacent 8-row groups; the whole K extent of 128 lies
+// between them). One MMA consumes 32 bytes of K (two core matrices): K = 8
+// for TF32, 16 for BF16. A product C[i][j] = sum_k X[k][i] Y[k][j] takes
+// A(m=i, k) = X[k][i] and B(n=j, k) = Y[k][j], i.e. both pool blocks in the
+// same "transposed" operand layout.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,19 +35,35 @@ constexpr long long kTcMaxPolls = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of element (m, k) of a K-major operand with K = 128 (4-byte elements)
+// Operand element format: OPB = bytes per element (4: TF32, 2: BF16).
+template <int OPB>
+struct TcOp {
+  static_assert(OPB == 4 || OPB == 2, "TF32 or BF16 operands");
+  static constexpr int CK = 16 / OPB;                  // K elements per core-matrix row
+  static constexpr uint32_t LBO = 128;                 // bytes between core matrices along K
+  static constexpr uint32_t SBO = kTcNP * OPB * 8;     // bytes between 8-row groups (K = 128)
+  static constexpr int KMMA = 32 / OPB;                // K per MMA instruction
+  static constexpr int NMMA = kTcNP / KMMA;            // MMAs per 128-deep product
+  static constexpr uint32_t BYTES = kTcNP * kTcNP * OPB;  // one 128 x 128 operand
+  // instruction descriptor: FP32 accumulator, A and B of the operand format (TF32 = 2 under
+  // kind::tf32, BF16 = 1 under kind::f16), both K-major, N = M = 128
+  static constexpr uint32_t FMT = OPB == 4 ? 2u : 1u;
+  static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+};
+
+// byte offset of element (m, k) of a K-major operand with K = 128
+template <int OPB>
 __device__ __forceinline__ uint32_t op_off(int m, int k) {
-  return (uint32_t)((m >> 3) * (kTcNP * 32) + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4);
+  using O = TcOp<OPB>;
+  return (uint32_t)((m >> 3) * O::SBO + (k / O::CK) * O::LBO + (m & 7) * 16 + (k % O::CK) * OPB);
 }
 
+template <int OPB>
 __device__ __forceinline__ uint64_t op_desc(uint32_t saddr) {
-  constexpr uint32_t lbo = 128, sbo = kTcNP * 32;
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+  using O = TcOp<OPB>;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((O::LBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((O::SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
-
-// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -48,18 +71,39 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-// D (TMEM, 128 lanes x 128 columns at tmem) (+)= A^T-form product over K = 128:
-// 16 MMAs of K = 8. Issued by one thread.
+// Two consecutive-K operand elements packed into the 32-bit word written at op_off(m, k) (k even for
+// BF16): TF32 takes one element (x0), BF16 two (x0 at k, x1 at k + 1), each rounded to nearest even.
+template <int OPB>
+__device__ __forceinline__ uint32_t pack_operand(float x0, float x1) {
+  if constexpr (OPB == 4) {
+    (void)x1;
+    return to_tf32(x0);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);  // .x = x0 (low half), .y = x1
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
+}
+
+// D (TMEM, 128 lanes x 128 columns at tmem) (+)= A^T-form product over K = 128,
+// issued by one thread: NMMA instructions of 32 bytes of K each.
+template <int OPB>
 __device__ __forceinline__ void tc_product(uint32_t tmem, const void *opA, const void *opB, bool accumulate) {
+  using O = TcOp<OPB>;
   const uint32_t a0 = smem_addr(opA), b0 = smem_addr(opB);
 #pragma unroll
-  for (int kk = 0; kk < kTcNP / 8; ++kk) {
-    const uint64_t ad = op_desc(a0 + kk * 256), bd = op_desc(b0 + kk * 256);
+  for (int kk = 0; kk < O::NMMA; ++kk) {
+    const uint64_t ad = op_desc<OPB>(a0 + kk * 2 * O::LBO), bd = op_desc<OPB>(b0 + kk * 2 * O::LBO);
     const uint32_t acc = (accumulate || kk > 0) ? 1u : 0u;
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+    if constexpr (OPB == 4)
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(O::IDESC), "r"(acc));
+    else
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(O::IDESC), "r"(acc));
   }
 }
 
@@ -119,45 +163,51 @@ __device__ __forceinline__ void tc_read_rows(uint32_t tmem_acc, F &&f) {
   }
 }
 
-// Pool block (row-major 128 x 128 FP32, X[k][m]) -> K-major TF32 operand
-// (A(m, k) = X[k][m]). Each warp writes whole 128-byte core matrices: lane ->
-// (m = m0 + lane/4, k = k0 + lane%4).
-template <int NT>
-__device__ __forceinline__ void stage_operand_from_pool(unsigned char *op, const float *g) {
+// Pool block (row-major 128 x 128 FP32 with row stride ldg, X[k][m]) -> K-major
+// operand (A(m, k) = X[k][m]). Each warp writes whole 128-byte core matrices:
+// lane -> (m = m0 + lane/4, k = k0 + (lane%4) * EPL), EPL = 4 / OPB elements
+// packed in one 32-bit word.
+template <int NT, int OPB>
+__device__ __forceinline__ void stage_operand_from_pool(unsigned char *op, const float *g, int ldg = kTcNP) {
+  using O = TcOp<OPB>;
+  constexpr int EPL = 4 / OPB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = NT / 32, NCM = (kTcNP / 8) * (kTcNP / 4);  // 512 core matrices
-  const int dm = lane >> 2, dk = lane & 3;
+  constexpr int NW = NT / 32, KCM = kTcNP / O::CK, NCM = (kTcNP / 8) * KCM;  // core matrices
+  const int dm = lane >> 2, dk = (lane & 3) * EPL;
 #pragma unroll 4
   for (int cm = warp; cm < NCM; cm += NW) {
-    const int m0 = (cm / (kTcNP / 4)) * 8, k0 = (cm % (kTcNP / 4)) * 4;
-    const float x = __ldcg(g + (size_t)(k0 + dk) * kTcNP + m0 + dm);
-    *reinterpret_cast<uint32_t *>(op + op_off(m0 + dm, k0 + dk)) = to_tf32(x);
+    const int m0 = (cm / KCM) * 8, k0 = (cm % KCM) * O::CK;
+    const float x0 = __ldcg(g + (size_t)(k0 + dk) * ldg + m0 + dm);
+    const float x1 = EPL == 2 ? __ldcg(g + (size_t)(k0 + dk + 1) * ldg + m0 + dm) : 0.0f;
+    *reinterpret_cast<uint32_t *>(op + op_off<OPB>(m0 + dm, k0 + dk)) = pack_operand<OPB>(x0, x1);
   }
 }
 
-// Padded row-major shared block (X[k][m], leading dimension LD) -> K-major TF32
-// operand in the same buffer: every thread first reads its 64 elements, then
-// all write after a barrier.
-template <int NT, int LD>
+// Padded row-major shared block (X[k][m], leading dimension LD) -> K-major
+// operand in the same buffer: every thread first reads its elements, then all
+// write after a barrier.
+template <int NT, int LD, int OPB>
 __device__ __forceinline__ void convert_operand_in_place(float *buf) {
+  using O = TcOp<OPB>;
+  constexpr int EPL = 4 / OPB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = NT / 32, NCM = (kTcNP / 8) * (kTcNP / 4);
+  constexpr int NW = NT / 32, KCM = kTcNP / O::CK, NCM = (kTcNP / 8) * KCM;
   constexpr int PER = NCM / NW;  // core matrices per warp
-  const int dm = lane >> 2, dk = lane & 3;
+  const int dm = lane >> 2, dk = (lane & 3) * EPL;
   uint32_t v[PER];
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int cm = warp + t * NW;
-    const int m0 = (cm / (kTcNP / 4)) * 8, k0 = (cm % (kTcNP / 4)) * 4;
-    v[t] = to_tf32(buf[(k0 + dk) * LD + m0 + dm]);
+    const int m0 = (cm / KCM) * 8, k0 = (cm % KCM) * O::CK;
+    v[t] = pack_operand<OPB>(buf[(k0 + dk) * LD + m0 + dm], EPL == 2 ? buf[(k0 + dk + 1) * LD + m0 + dm] : 0.0f);
   }
   __syncthreads();
   unsigned char *op = reinterpret_cast<unsigned char *>(buf);
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int cm = warp + t * NW;
-    const int m0 = (cm / (kTcNP / 4)) * 8, k0 = (cm % (kTcNP / 4)) * 4;
-    *reinterpret_cast<uint32_t *>(op + op_off(m0 + dm, k0 + dk)) = v[t];
+    const int m0 = (cm / KCM) * 8, k0 = (cm % KCM) * O::CK;
+    *reinterpret_cast<uint32_t *>(op + op_off<OPB>(m0 + dm, k0 + dk)) = v[t];
   }
 }
 
@@ -260,7 +310,7 @@ __device__ __forceinline__ void tc_sync(TcState &st) {
 
 // One node of Alg. 5 with block size 128 (T = P = float, S = caller's type).
 // Same inputs, outputs and pool conventions as factor_node (btc_factor.cuh).
-template <typename S, bool FIRST>
+template <typename S, bool FIRST, int OPB>
 __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const FactorArgs &args, const InstDesc &single,
                                                unsigned char *smem_raw, TcState &st) {
   using C = TileCfg<float, kTcNP, 8>;
@@ -290,14 +340,14 @@ __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const Facto
   } else {
     const bool pa = it.p_a >= 0, pb = it.p_b >= 0 && has_next;
     tc_bulk_load(st, sS, dpool + it.d_self, nullptr, nullptr, nullptr, nullptr);
-    if (pa) stage_operand_from_pool<NT>(reinterpret_cast<unsigned char *>(sA), epool + it.p_a);
-    if (pb) stage_operand_from_pool<NT>(reinterpret_cast<unsigned char *>(sB), epool + it.p_b);
+    if (pa) stage_operand_from_pool<NT, OPB>(reinterpret_cast<unsigned char *>(sA), epool + it.p_a);
+    if (pb) stage_operand_from_pool<NT, OPB>(reinterpret_cast<unsigned char *>(sB), epool + it.p_b);
     tc_bulk_wait(st);
     tc_publish_smem();
     if (pa || pb) {
       if (tid == 0) {
-        if (pa) tc_product(acc_fill, sA, sA, false);  // P_a^T P_a
-        if (pb) tc_product(acc_next, sB, sB, false);  // P_b^T P_b, kept for S_{e+s}
+        if (pa) tc_product<OPB>(acc_fill, sA, sA, false);  // P_a^T P_a
+        if (pb) tc_product<OPB>(acc_next, sB, sB, false);  // P_b^T P_b, kept for S_{e+s}
         tc_commit(st.mbar);
       }
       tc_sync(st);
@@ -336,14 +386,14 @@ __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const Facto
   const bool fill = it.fill >= 0;
   if (!(has_next || fill)) return;
   __syncthreads();
-  if (has_dn) convert_operand_in_place<NT, LD>(sB);
-  if (fill) convert_operand_in_place<NT, LD>(sA);
+  if (has_dn) convert_operand_in_place<NT, LD, OPB>(sB);
+  if (fill) convert_operand_in_place<NT, LD, OPB>(sA);
   tc_publish_smem();
   if (tid == 0) {
-    if (has_next) tc_product(acc_next, sB, sB, next_started);
+    if (has_next) tc_product<OPB>(acc_next, sB, sB, next_started);
     if (fill) {
-      if (it.flags & FI_FILL_UPFIRST) tc_product(acc_fill, sA, sB, false);  // S'(e-s, e+s) = -U_up^T U_dn
-      else tc_product(acc_fill, sB, sA, false);                             // S'(e+s, e-s) = -U_dn^T U_up
+      if (it.flags & FI_FILL_UPFIRST) tc_product<OPB>(acc_fill, sA, sB, false);  // S'(e-s, e+s) = -U_up^T U_dn
+      else tc_product<OPB>(acc_fill, sB, sA, false);                             // S'(e+s, e-s) = -U_dn^T U_up
     }
     tc_commit(st.mbar);
   }
@@ -396,7 +446,7 @@ __device__ __forceinline__ void factor_node_tc(const FactorItem &it, const Facto
 // FP32 shared blocks take 198 KB).
 constexpr int kTcThreads = TileCfg<float, kTcNP, 8>::NT;
 
-template <typename S, bool FIRST>
+template <typename S, bool FIRST, int OPB>
 __global__ void __launch_bounds__(kTcThreads, 1) k_factor_level_tc(FactorArgs args, InstDesc single) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
@@ -404,11 +454,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_factor_level_tc(FactorArgs ar
   TcState st;
   tc_begin(st, &s_tmem, s_mbar, args.status);
   const FactorItem it = args.items[blockIdx.x];
-  factor_node_tc<S, FIRST>(it, args, single, smem_raw, st);
+  factor_node_tc<S, FIRST, OPB>(it, args, single, smem_raw, st);
   tc_end(st);
 }
 
-template <typename S>
+template <typename S, int OPB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_factor_flow_tc(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -424,8 +474,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     flow_trace(fs, t, 0);
     if (flow_wait(fs, deps + 3 * t, 3, &s_ok)) {
       flow_trace(fs, t, 1);
-      if (t < nfirst) factor_node_tc<S, true>(it, args, single, smem_raw, st);
-      else factor_node_tc<S, false>(it, args, single, smem_raw, st);
+      if (t < nfirst) factor_node_tc<S, true, OPB>(it, args, single, smem_raw, st);
+      else factor_node_tc<S, false, OPB>(it, args, single, smem_raw, st);
     }
     __syncthreads();
     flow_trace(fs, t, 2);
@@ -434,7 +484,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_end(st);
 }
 
-template <typename S>
+template <typename S, int OPB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_factor_fwd_flow_tc(FactorArgs fa, InstDesc single, SolveArgs sa, const int32_t *code, const int32_t *deps,
                          int nfirst, int count, FlowSync fs) {
@@ -454,8 +504,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       flow_trace(fs, t, 1);
       if (c >= 0) {
         const FactorItem it = fa.items[c];
-        if (c < nfirst) factor_node_tc<S, true>(it, fa, single, smem_raw, st);
-        else factor_node_tc<S, false>(it, fa, single, smem_raw, st);
+        if (c < nfirst) factor_node_tc<S, true, OPB>(it, fa, single, smem_raw, st);
+        else factor_node_tc<S, false, OPB>(it, fa, single, smem_raw, st);
       } else {
         const SolveFlowItem it = fwd[-1 - c];
         fwd_node<float, kTcNP>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, sa, smem_raw);

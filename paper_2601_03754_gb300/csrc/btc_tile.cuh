@@ -148,17 +148,17 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 }
 
 // ------------------------------------------------------------ block transfer
-// Pool block (np x np, type T) -> padded shared memory (same type) with cp.async;
-// completes at cp_async_commit_wait_all() + __syncthreads().
+// Pool block (np x np, type T, row stride ldg) -> padded shared memory (same
+// type) with cp.async; completes at cp_async_commit_wait_all() + __syncthreads().
 template <class C, typename T>
-__device__ __forceinline__ void block_to_smem_async(T *s, const T *g) {
+__device__ __forceinline__ void block_to_smem_async(T *s, const T *g, int ldg = C::NP) {
   constexpr int V = 16 / sizeof(T);
   constexpr int CPR = C::NP / V;
   constexpr int TOTAL = C::NP * CPR;
 #pragma unroll
   for (int q = threadIdx.x; q < TOTAL; q += C::NT) {
     const int row = q / CPR, col = (q % CPR) * V;
-    cp_async16(s + row * C::LD + col, g + (size_t)row * C::NP + col);
+    cp_async16(s + row * C::LD + col, g + (size_t)row * ldg + col);
   }
 }
 
@@ -195,10 +195,10 @@ __device__ __forceinline__ void block_to_smem(T *s, const P *g) {
   }
 }
 
-// Padded shared memory (type T) -> pool block (type P), cooperative.
+// Padded shared memory (type T) -> pool block (type P, row stride ldg), cooperative.
 // lower_zero: write zeros below the diagonal (the final U factor).
 template <class C, typename T, typename P>
-__device__ __forceinline__ void smem_to_block(P *g, const T *s, bool lower_zero) {
+__device__ __forceinline__ void smem_to_block(P *g, const T *s, bool lower_zero, int ldg = C::NP) {
   constexpr int V = 16 / sizeof(P);
   constexpr int CPR = C::NP / V;
   constexpr int TOTAL = C::NP * CPR;
@@ -208,7 +208,7 @@ __device__ __forceinline__ void smem_to_block(P *g, const T *s, bool lower_zero)
     P *dst = reinterpret_cast<P *>(&raw);
 #pragma unroll
     for (int i = 0; i < V; ++i) dst[i] = (lower_zero && col + i < row) ? P(0) : convert_in<P, T>(s[row * C::LD + col + i]);
-    *reinterpret_cast<float4 *>(g + (size_t)row * C::NP + col) = raw;
+    *reinterpret_cast<float4 *>(g + (size_t)row * ldg + col) = raw;
   }
 }
 
@@ -427,6 +427,7 @@ struct FlowSync {
   int *done;                  // one flag per item
   int *status;                // 0 = ok; kFlowTimeout when a wait gave up
   unsigned long long *trace;  // optional: 4 words per item (claim, ready, done ns; SM id), or null
+  long long max_polls = kMaxPolls;  // poll limit of every wait (lowered only by the failure-detection tests)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -469,7 +470,7 @@ __device__ __forceinline__ bool flow_wait(const FlowSync &fs, const int32_t *dep
       long long polls = 0;
       while (ld_acquire_gpu(fs.done + d) == 0) {
         // the status word is checked every 64 polls; the first polls spin without sleeping
-        if ((++polls & 63) == 0 && (polls > kMaxPolls || *((volatile int *)fs.status) != 0)) {
+        if ((++polls & 63) == 0 && (polls > fs.max_polls || *((volatile int *)fs.status) != 0)) {
           atomicOr(fs.status, kFlowTimeout);
           ok = 0;
           break;
@@ -527,7 +528,8 @@ __device__ __forceinline__ void col_subst_ut(T *X, int col, const T *S, const T 
 // NaN) is reported and replaced by 1 so that the remaining arithmetic stays
 // finite. Writes 1/U_kk to dinv.
 template <class C, typename T>
-__device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned long long *info, int node) {
+__device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned long long *info, int node,
+                                                 int col_base = 0) {
   constexpr int PB = C::PB, NP = C::NP, LD = C::LD;
   constexpr int CPL = (NP + 31) / 32;  // column slots per lane
   const int lane = threadIdx.x & 31;
@@ -545,7 +547,7 @@ __device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned
   for (int k = 0; k < PB; ++k) {
     T d = __shfl_sync(0xffffffffu, piv, k);
     if (!(d > T(0))) {  // uniform across the warp
-      if (lane == 0 && info) atomicMin(info, pack_info(node, p0 + k));
+      if (lane == 0 && info) atomicMin(info, pack_info(node, col_base + p0 + k));
       d = T(1);
       if (lane == k) v[0][k] = T(1);
     }
@@ -580,10 +582,11 @@ __device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned
 // (right-looking by panels), so the results are identical; the pipelining only
 // overlaps the single-warp panel factorization with the trailing updates. wait_operands(): called by every thread after the first
 // panel, before Z0/Z1 are first read (their asynchronous copies were issued
-// before the call).
+// before the call). col_base: column of S's first row within the node's block,
+// for the pivot report (S is a diagonal tile of a larger block).
 template <class C, typename T, class WaitOperands>
 __device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, unsigned long long *info, int node,
-                                                 WaitOperands &&wait_operands) {
+                                                 WaitOperands &&wait_operands, int col_base = 0) {
   constexpr int PB = C::PB, NP = C::NP, R = C::R, TXN = C::TXN, NT = C::NT;
   const int tid = threadIdx.x;
   const bool solve = Z0 || Z1;
@@ -591,7 +594,7 @@ __device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, un
   for (int p = 0; p < C::NPAN; ++p) {
     const int p0 = p * PB;
     if (tid < 32) {
-      warp_panel_potrf<C>(S, p0, dinv, info, node);
+      warp_panel_potrf<C>(S, p0, dinv, info, node, col_base);
     } else if (p > 0) {
       const int q0 = p0 - PB;                     // panel p-1
       const int tb = (NP - p0 - PB) / R;          // tile rows of S below panel p
@@ -646,6 +649,31 @@ __device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, un
         tile_sub_xty<C, PB>(a, S, S, r0, c0, p0);
         tile_to_smem<C>(S, a, r0, c0);
       }
+    }
+    __syncthreads();
+  }
+}
+
+// Z <- U^{-T} Z with an upper factor U already in shared memory (dinv holds
+// 1 / U_kk), right-looking by panels: the column substitution of panel p on
+// every column of Z, then the rows below it receive the panel's contribution
+// (the same steps block_potrf_trsm applies to its right-hand sides).
+template <class C, typename T>
+__device__ __forceinline__ void block_trsm_ut(T *Z, const T *U, const T *dinv) {
+  constexpr int PB = C::PB, NP = C::NP, R = C::R, TXN = C::TXN, NT = C::NT;
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int p = 0; p < C::NPAN; ++p) {
+    const int p0 = p * PB;
+    for (int q = tid; q < NP; q += NT) col_subst_ut<C>(Z, q, U, dinv, p0);
+    __syncthreads();
+    const int tb = (NP - p0 - PB) / R;  // tile rows below the panel
+    for (int u = tid; u < tb * TXN; u += NT) {
+      const int r0 = p0 + PB + (u / TXN) * R, c0 = (u % TXN) * R;
+      T a[R][R];
+      tile_from_smem<C>(a, Z, r0, c0);
+      tile_sub_xty<C, PB>(a, U, Z, r0, c0, p0);
+      tile_to_smem<C>(Z, a, r0, c0);
     }
     __syncthreads();
   }

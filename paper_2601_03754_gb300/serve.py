@@ -61,3 +61,17 @@ def run_stream(server, pool, rate, count, seed=0, tol=1e-10, maxit=30):
     results = [btc.btc_server_poll(server, t, wait=True) for t in tickets]
     wall = time.perf_counter() - t0
     return results, wall, xs, which, rhs
+
+
+def check_results(pool, xs, which, rhs):
+    """Relative residual ||b - Psi x|| / (||Psi|| ||x||) of every returned x, recomputed by the library's
+    FP64 residual (btc_residual) on the request's own b, independently of what the server reported."""
+    worst = 0.0
+    for k, x in enumerate(xs):
+        p = pool[which[k]]
+        r, a, xn = btc.btc_residual(p["N"], p["n"], 1, p["D"], p["B"], x, rhs[k])
+        rel = r / (a * xn) if a * xn > 0 else float("inf")
+        if rel != rel:
+            rel = float("inf")
+        worst = max(worst, rel)
+    return {"checked": len(xs), "max_relres_recomputed": worst}

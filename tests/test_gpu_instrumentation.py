@@ -107,7 +107,7 @@ def test_phase_stamps_are_ordered_and_leave_results_unchanged(dt, variant):
     P = ph.view(N, 8).cpu().numpy()
     stamped = P[:, 5] > 0
     expect = np.ones(N, dtype=bool)
-    if dt == btc.MIXED_F32:  # the top separator is factored by the double-FP32 root kernel
+    if dt == btc.MIXED_F32:  # the top separator is factored by the separate root kernel
         expect[(1 << (N.bit_length() - 1)) - 1] = False
     assert np.array_equal(stamped, expect)
     assert np.all(np.diff(P[stamped, :6], axis=1) >= 0), "phases in order"

@@ -1,5 +1,5 @@
 """The top-separator Cholesky of the mixed paths in its two precisions (btc_plan_set_root_precision):
-double-FP32 (default) and FP64. Both factor the FP32 Schur complement and round the factor back to
+FP64 (default) and double-FP32. Both factor the FP32 Schur complement and round the factor back to
 FP32, so the top block agrees to FP32 rounding, every other block is untouched, and the refined
 solutions agree."""
 import numpy as np
@@ -56,6 +56,7 @@ def test_switching_precision_recaptures_the_graph():
     b = gen.rhs(N, n, m, seed=3)
     Dd, Bd, bd = dev(D, torch.float64), dev(B, torch.float64), dev(b, torch.float64)
     p = btc.btc_plan(N, n, btc.MIXED_F32)
+    btc.btc_plan_set_root_precision(p, btc.ROOT_DOUBLE_FP32)
     for _ in range(3):  # tuning, capture, replay
         _run(p, Dd, Bd, bd, m)
     btc.btc_plan_set_root_precision(p, btc.ROOT_FP64)

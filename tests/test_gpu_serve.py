@@ -97,6 +97,49 @@ def test_resolve_uses_the_cached_factor_and_eviction_recomputes():
     srv.stop()
 
 
+@pytest.mark.parametrize("dt", [btc.MIXED_F32, btc.F64], ids=["mixed", "f64"])
+def test_concurrent_resolves_of_one_cached_factor(dt):
+    """Many re-solves of the same cached factor submitted at once to a multi-slot server: they share
+    that factor's plan, so the server must run them one at a time; each x must equal the x of the same
+    re-solve run alone (bitwise) and meet the tolerance against the oracle."""
+    pool = _pool()
+    p = pool[5]
+    rhs = [dev(gen.rhs(p["N"], p["n"], 1, seed=500 + k)[:, 0], torch.float64) for k in range(12)]
+    # alone: each re-solve on its own after the factor request
+    srv = btc.btc_server_start(dt, slots=1, hbm_budget_bytes=4 << 30, cache_factors=True)
+    t0 = btc.btc_server_submit(srv, p["N"], p["n"], p["D"], p["B"], p["b"], torch.zeros_like(p["b"]))
+    assert btc.btc_server_poll(srv, t0)["status"] == btc.OK
+    alone = []
+    for b in rhs:
+        x = torch.zeros_like(b)
+        t = btc.btc_server_submit(srv, p["N"], p["n"], p["D"], p["B"], b, x, factor_id=t0)
+        assert btc.btc_server_poll(srv, t)["status"] == btc.OK
+        alone.append(x.cpu().numpy())
+    srv.stop()
+    # together: 6 slots, all re-solves of one factor submitted back to back, with other requests between
+    srv = btc.btc_server_start(dt, slots=6, hbm_budget_bytes=4 << 30, cache_factors=True)
+    t0 = btc.btc_server_submit(srv, p["N"], p["n"], p["D"], p["B"], p["b"], torch.zeros_like(p["b"]))
+    assert btc.btc_server_poll(srv, t0)["status"] == btc.OK
+    xs, tickets, others = [], [], []
+    for k, b in enumerate(rhs):
+        x = torch.zeros_like(b)
+        xs.append(x)
+        tickets.append(btc.btc_server_submit(srv, p["N"], p["n"], p["D"], p["B"], b, x, factor_id=t0))
+        if k % 4 == 0:
+            q = pool[k % len(pool)]
+            others.append(btc.btc_server_submit(srv, q["N"], q["n"], q["D"], q["B"], q["b"],
+                                                torch.zeros_like(q["b"])))
+    for t in tickets + others:
+        assert btc.btc_server_poll(srv, t)["status"] == btc.OK
+    st = btc.btc_server_stats(srv)
+    assert st["cache_hits"] == len(rhs) and st["failed"] == 0
+    srv.stop()
+    for k, x in enumerate(xs):
+        xh = x.cpu().numpy()
+        np.testing.assert_array_equal(xh, alone[k])
+        assert oracle.relres(p["Dh"], p["Bh"], xh, rhs[k].cpu().numpy()) <= 1e-10
+
+
 def test_oversized_request_is_rejected():
     srv = btc.btc_server_start(btc.MIXED_F32, slots=1, hbm_budget_bytes=1 << 20, cache_factors=False)
     D = torch.zeros((1000, 48, 48), dtype=torch.float64, device="cuda")

@@ -39,7 +39,12 @@ def test_version_and_last_error():
 def test_describe_rejects_oversized_blocks():
     assert btc.btc_describe(16, 96, btc.F64)["np"] == 96
     assert btc.btc_describe(16, 128, btc.F32)["np"] == 128
-    for n, dt in ((97, btc.F64), (129, btc.F32), (129, btc.MIXED_F32)):
+    # blocks above 128 run as blocked nodes of tile tasks, on the tensor-core dtypes only, up to 256
+    for dt in (btc.MIXED_TF32, btc.MIXED_BF16):
+        assert btc.btc_describe(16, 129, dt)["np"] == 256
+        assert btc.btc_describe(16, 256, dt)["np"] == 256
+    for n, dt in ((97, btc.F64), (129, btc.F32), (129, btc.MIXED_F32), (257, btc.MIXED_TF32),
+                  (257, btc.MIXED_BF16)):
         with pytest.raises(btc.BtcError) as ei:
             btc.btc_describe(16, n, dt)
         assert ei.value.code == btc.ERR_UNSUPPORTED
