@@ -338,7 +338,10 @@ def run_phases():
 
 def batched_measure(btc, gen, torch, steps, stream, flush):
     """Config: 512 instances, n uniform in {8,16,32,64}, N log-uniform in [32, 2048], one RHS each,
-    delta = 1e-2; mixed FP32 factor + FP64 refinement to 1e-10, beside the plain FP64 batch."""
+    delta = 1e-2; mixed FP32 factor + FP64 refinement to 1e-10, beside the plain FP64 batch. A step is
+    btc_batch_factor_solve_refined: after the first (tuning) call, one captured graph with the
+    refinement loop on the device. The tuned launch configuration of every block-size group is
+    reported."""
     specs = gen.batch_specs(512, seed=0)
     Ds, Bs, bs, xs = [], [], [], []
     for k, (N, n) in enumerate(specs):
@@ -357,12 +360,12 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
         q = btc.btc_batch_query(batch)
 
         def step():
-            btc.btc_batch_factor(batch, Ds, Bs)
-            return btc.btc_batch_solve_refined(batch, bs, xs, tol=TOL, maxit=30)
+            return btc.btc_batch_factor_solve_refined(batch, Ds, Bs, bs, xs, tol=TOL, maxit=30)
 
         reps = steps if dt == btc.MIXED_F32 else max(2, steps // 4)
         with torch.cuda.stream(stream):
-            step()
+            step()  # tuning of every group
+            step()  # graph capture
             ts = []
             for _ in range(reps):
                 flush.fill_(1.0)
@@ -374,9 +377,14 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
         ms = statistics.mean(ts)
+        tuning = []
+        for g in range(q["groups"]):
+            np_, cap, ctas, tuned, gms = btc.btc_batch_tuning(batch, g)
+            tuning.append({"np": np_, "resident_cap": cap, "ctas_per_sm": ctas, "tuned": tuned,
+                           "factor_ms_alone": round(gms, 3)})
         out[name] = {"ms_per_batch": ms, "solves_per_s": len(specs) * 1000.0 / ms, "refine_iters": it,
                      "max_relres": rel, "factor_tflops": q["factor_flops"] / (ms * 1e-3) / 1e12,
-                     "groups": q["groups"], "device_gb": q["device_bytes"] / 1e9}
+                     "groups": q["groups"], "group_tuning": tuning, "device_gb": q["device_bytes"] / 1e9}
         batch.free()
     out["speedup_vs_plain_f64"] = out["plain_f64"]["ms_per_batch"] / out["mixed"]["ms_per_batch"]
     return out
@@ -517,6 +525,58 @@ def gmres_ir_measure(btc, torch, stream):
     return out
 
 
+def c2_measure(btc, gen, torch, stream, flush, steps=8):
+    """Config C2 beyond the headline row: N=1024, n=64, m in {1, 16}; the bt_random generator at
+    delta in {1, 1e-2, 1e-4} and the MPC-like generator. Per input: the measured condition number, then
+    per form (mixed FP32 factor + FP64 refinement to 1e-10; plain FP64; plain FP32 factor + one solve,
+    no refinement) and m: factor + solve time (L2 flushed), refinement steps and relative residual."""
+    N, n = 1024, 64
+    out = {}
+    inputs = [(f"delta{d:g}", lambda d=d: gen.bt_random(N, n, delta=d, seed=3)) for d in (1.0, 1e-2, 1e-4)]
+    inputs.append(("mpc", lambda: gen.mpc(N, n, seed=3)))
+    for name, make in inputs:
+        D, B = make()
+        res = {}
+        for dt, form in ((btc.MIXED_F32, "mixed"), (btc.F64, "plain_f64"), (btc.F32, "plain_f32")):
+            tdt = torch.float32 if dt == btc.F32 else torch.float64
+            Dd, Bd = (torch.from_numpy(a).to("cuda", tdt) for a in (D, B))
+            p = btc.btc_plan(N, n, dt, stream)
+            if form == "mixed":
+                Dk, Bk = (torch.from_numpy(a).cuda() for a in (D, B))
+                btc.btc_factor(p, Dk, Bk)
+                res["kappa_estimate"] = kappa_estimate(btc, torch, Dk, Bk, p)
+            for m in (1, 16):
+                b = torch.from_numpy(gen.rhs(N, n, m, seed=4)).to("cuda", tdt)
+                x = torch.zeros_like(b)
+                ts = []
+                with torch.cuda.stream(stream):
+                    for rep in range(steps + 2):
+                        flush.fill_(1.0)
+                        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                        if dt == btc.F32:
+                            x.copy_(b)
+                            e0.record(stream)
+                            btc.btc_factor_solve(p, Dd, Bd, x, m)
+                            e1.record(stream)
+                            it, rel = 0, None
+                        else:
+                            e0.record(stream)
+                            it, rel, rc = btc.btc_factor_solve_refined(p, Dd, Bd, b, x, m, tol=TOL, maxit=30)
+                            e1.record(stream)
+                        e1.synchronize()
+                        if rep >= 2:
+                            ts.append(e0.elapsed_time(e1))
+                if dt == btc.F32:
+                    r, a, xn = btc.btc_residual(N, n, m, torch.from_numpy(D).cuda(), torch.from_numpy(B).cuda(),
+                                                x.double(), b.double())
+                    rel = r / (a * xn)
+                res[f"{form}_m{m}"] = {"ms": statistics.mean(ts), "solves_per_s": 1000.0 / statistics.mean(ts),
+                                      "refine_steps": it, "relres": rel}
+            p.free()
+        out[name] = res
+    return out
+
+
 def small_case_measure(btc, gen, torch, stream, flush, steps=200):
     """Config C1: N=64, n=16, one RHS: factor + solve latency (p50/p99) of the plain FP64 path and the
     mixed path (both to 1e-10), against a critical-path model: the planner's critical-path flops
@@ -581,28 +641,46 @@ def interlace_measure(btc, gen, torch, stream, flush, steps=30):
     return out
 
 
-def serving_measure(btc, torch, rates=(1000.0, 4000.0), count=300):
+def serving_measure(btc, torch, rates=(1000.0, 5000.0, 20000.0, 50000.0), count=5000, pool_size=128):
     """Config: Poisson stream of factor+solve requests, n uniform in {12,24,48,96}, N log-uniform
     in [50, 5000], MPC-like generator, 30% re-solves of a cached factor, HBM-footprint admission;
-    mixed FP32+FP64-refinement server vs plain FP64 server; p50/p99 latency and sustained solves/s."""
+    mixed FP32+FP64-refinement server (FP64 root) vs plain FP64 server; p50/p99 latency and sustained
+    solves/s per offered rate, and the knee (the first rate the server does not sustain within 10 %).
+    Both servers are prewarmed (plans of every size bucket built, tuned and captured before the
+    traffic), so no request pays plan construction. The pool holds `pool_size` distinct systems of
+    distinct sizes; every returned x is re-checked by the FP64 residual."""
     from paper_2601_03754_gb300 import serve
-    pool = serve.make_pool(count=24, seed=0)
-    out = {"pool": len(pool), "requests_per_rate": count, "slots": 8, "hbm_budget_gb": 16}
-    for name, dt in (("mixed", btc.MIXED_F32), ("plain_f64", btc.F64)):
-        res = {}
-        for rate in rates:
-            srv = btc.btc_server_start(dt, slots=8, hbm_budget_bytes=16 << 30, cache_factors=True)
-            serve.run_stream(srv, pool, rate, 40, seed=1)  # warm-up: plans allocated, kernels loaded
-            srv.stop()
-            srv = btc.btc_server_start(dt, slots=8, hbm_budget_bytes=16 << 30, cache_factors=True)
-            results, wall, xs, which, rhs = serve.run_stream(srv, pool, rate, count, seed=2)
+    t0 = time.perf_counter()
+    pool = serve.make_pool(count=pool_size, seed=0)
+    out = {"pool": len(pool), "distinct_shapes": len({(p["N"], p["n"]) for p in pool}), "requests_per_rate": count,
+           "slots": 8, "hbm_budget_gb": 64, "prewarm_copies": 2, "pool_build_s": round(time.perf_counter() - t0, 1)}
+    for name, dt, rr, cnt in (("mixed", btc.MIXED_F32, rates, count), ("plain_f64", btc.F64, rates[:2], count // 2)):
+        srv = btc.btc_server_start(dt, slots=8, hbm_budget_bytes=64 << 30, cache_factors=True)
+        t0 = time.perf_counter()
+        for n in (12, 24, 48, 96):
+            btc.btc_server_prewarm(srv, n, 5000, copies=2)
+        res = {"prewarm_s": round(time.perf_counter() - t0, 1)}
+        serve.run_stream(srv, pool, 2000.0, 200, seed=1)  # warm-up traffic
+        knee = None
+        for rate in rr:
+            st0 = btc.btc_server_stats(srv)
+            results, wall, xs, which, rhs, span = serve.run_stream(srv, pool, rate, cnt, seed=2)
             st = btc.btc_server_stats(srv)
-            srv.stop()
-            ok = sum(1 for r in results if r["status"] == btc.OK)
-            res[str(int(rate))] = {"p50_us": st["p50_us"], "p99_us": st["p99_us"], "mean_us": st["mean_us"],
-                                   "solves_per_s": st["solves_per_s"], "completed": ok,
-                                   "cache_hits": st["cache_hits"], "max_relres": max(r["relres"] for r in results),
-                                   **serve.check_results(pool, xs, which, rhs)}
+            lat = np.asarray([r["latency_us"] for r in results if r["status"] == btc.OK])
+            ok = int(lat.size)
+            sustained = ok / wall
+            row = {"offered_req_per_s": cnt / span if span > 0 else None,
+                   "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                   "mean_us": float(lat.mean()), "solves_per_s": sustained, "completed": ok,
+                   "cache_hits": st["cache_hits"] - st0["cache_hits"],
+                   "max_relres": max(r["relres"] for r in results),
+                   **serve.check_results(pool, xs, which, rhs)}
+            res[str(int(rate))] = row
+            if knee is None and sustained < 0.9 * rate:
+                knee = rate
+        res["knee_req_per_s"] = knee
+        res["device_gb"] = btc.btc_server_stats(srv)["device_bytes"] / 1e9
+        srv.stop()
         out[name] = res
     return out
 
@@ -616,7 +694,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-server measurement")
-    ap.add_argument("--no-large", action="store_true", help="skip the N=4096, n=128 measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the N=4096, n in {128, 256} measurement")
+    ap.add_argument("--no-c2", action="store_true", help="skip the N=1024 delta/MPC/16-RHS rows")
     ap.add_argument("--phases", action="store_true", help="per-level node phase times of the factor launch")
     ap.add_argument("--profile", choices=["mixed", "f64", "both", "tf32"], default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
@@ -759,6 +838,7 @@ def main():
     large = large_block_measure(btc, gen, torch, stream, flush) if not args.no_large else None
     gmres = gmres_ir_measure(btc, torch, stream) if not args.no_large else None
     small = small_case_measure(btc, gen, torch, stream, flush)
+    c2 = c2_measure(btc, gen, torch, stream, flush) if not args.no_c2 else None
     interlace = interlace_measure(btc, gen, torch, stream, flush)
     # solve roofline: each factor block read once per direction (the compulsory bytes of Alg. 7, m = 1)
     solve_bytes = 2.0 * (N + info["offdiag_blocks"]) * n * n * 4
@@ -821,6 +901,7 @@ def main():
         "serving": serving,
         "large_blocks": large,
         "small_case": small,
+        "c2_delta_mpc_m16": c2,
         "interlaced_vs_sequential": interlace,
         "solve_roofline": solve_roof,
         "wall_s_timed": t_wall,

@@ -262,7 +262,7 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
 /*
  * Autotuning of the persistent factorization (on by default). The library
  * compiles the persistent factor kernels for several register budgets (one per
- * cap of 1-4 resident CTAs per SM; 1, 2, 4, 8 for 64-thread CTAs). On the first
+ * cap of 1-4 resident CTAs per SM; 1, 2, 4, 8, 16 for 64-thread CTAs). On the first
  * persistent factorization of a plan shape (dtype, padded n, N, variant) it
  * times every compiled cap at every CTAs-per-SM count that fits, three runs
  * each on the caller's D and B, keeps the fastest median and remembers it for
@@ -272,7 +272,10 @@ int btc_solve_refined(btc_plan_t p, const double *b, double *x, int nrhs, double
  * interlaced call of a plan shape: its kernel has other register and shared
  * memory needs, and its best residency differs; the packed right-hand side is
  * saved and restored around its trial runs. enable = 0: no tuning, the default
- * configuration for both launches. btc_plan_tuning and
+ * configuration for both launches. enable = 2: a configuration remembered for
+ * the shape earlier in the process is used, but no trial launches are run
+ * (the default configuration otherwise; for latency-bound callers such as a
+ * request server). btc_plan_tuning and
  * btc_plan_tuning_interlaced report the configuration in use for the plain and
  * the interlaced launch (host pointers, each may be NULL): the register-budget
  * cap, the CTAs per SM of the launch, and whether it was tuned.
@@ -494,6 +497,39 @@ int btc_batch_solve_refined(btc_batch_t b, const double *const *rhs, double *con
  * BTC_ERR_TIMEOUT. */
 int btc_batch_info(btc_batch_t b, int *failed_instance, int *block, int *col);
 
+/*
+ * Factor every instance and solve with FP64 refinement in one call: the same
+ * results as btc_batch_factor followed by btc_batch_solve_refined (arguments
+ * and return codes as those two). Once the groups' launch configurations are
+ * settled (tuned on the first call, or tuning off), the whole sequence runs as
+ * one captured CUDA graph: every group's persistent factorization and top
+ * separators, the first solve, the FP64 residuals with the matrix-norm bounds,
+ * and a device-side while loop of correction solves and residuals that runs
+ * until the worst instance meets tol (or maxit steps); one graph launch and
+ * one host synchronization per call. The instances' pointers are read from
+ * device arrays at run time, so the graph is captured once per (tol, maxit)
+ * and replayed for new inputs. If capture is refused, plain launches are used.
+ * Synchronous.
+ */
+int btc_batch_factor_solve_refined(btc_batch_t b, const void *const *D, const void *const *B, const double *const *rhs,
+                                   double *const *x, double tol, int maxit, int *iters, double *max_relres);
+
+/* Autotuning of the groups' persistent factor launches (on by default): on the
+ * first factorization each group times every compiled register-budget variant
+ * at 1, 2, 4, ... CTAs per SM up to what fits (the number of nodes one SM holds
+ * at once), three runs each on the batch's own inputs, and keeps the fastest;
+ * the factor is the same in every configuration. */
+int btc_batch_set_autotune(btc_batch_t b, int enable);
+
+/* CUDA graphs for btc_batch_factor_solve_refined (on by default). */
+int btc_batch_set_graphs(btc_batch_t b, int enable);
+
+/* Launch configuration of group `group` (groups in launch order, largest work
+ * first): padded block size, register-budget cap, CTAs per SM, whether it was
+ * tuned and the tuned launch's median time in ms (host pointers, may be NULL). */
+int btc_batch_tuning(btc_batch_t b, int group, int *np, int *resident_cap, int *ctas_per_sm, int *tuned,
+                     double *factor_ms);
+
 /* Release the batch (synchronizes its stream). */
 int btc_batch_free(btc_batch_t b);
 
@@ -515,6 +551,13 @@ int btc_version(void);
  * refined re-solve with the cached factor of an earlier request. Re-solves of
  * one cached factor run one at a time (they share that factor's plan and its
  * work vectors); requests queued behind such a re-solve may start before it.
+ * Plans are made per block size and bucket of N (sizes growing by 2^(1/4));
+ * a request is copied into its plan's staging buffers and padded to the
+ * bucket size with identity diagonal blocks, zero coupling blocks and a zero
+ * right-hand side, which leaves its solution and residual unchanged (the
+ * stopping test's matrix norm is max(||Psi||_inf, 1)). Plans made on the
+ * request path run no tuning trials (btc_plan_set_autotune mode 2);
+ * btc_server_prewarm builds and tunes them ahead of the traffic.
  */
 typedef struct btc_server_s *btc_server_t;
 
@@ -555,6 +598,29 @@ int btc_server_poll(btc_server_t s, int64_t ticket, int wait, int *status, int *
                     double *latency_us);
 
 int btc_server_stats(btc_server_t s, btc_server_stats_t *st);
+
+/*
+ * Device bytes that a request of size (N, n) reserves in a server of this
+ * dtype: the plan of its size bucket (plans serve every N up to a bucket size,
+ * buckets growing by 2^(1/4)) and that plan's staging copy of the padded
+ * system. Host-only. Errors: BTC_ERR_ARG, BTC_ERR_UNSUPPORTED.
+ */
+int btc_server_footprint(int dtype, int N, int n, int64_t *bytes);
+
+/*
+ * Build, tune and capture ahead of the traffic `copies` plans of every size
+ * bucket up to N_max for block size n, so that requests never pay plan
+ * construction, tuning or graph capture: each plan factors and solves a
+ * placeholder system (identity blocks) three times and is kept idle for
+ * requests of its bucket. A factor request takes an idle plan of its bucket,
+ * else the plan of the bucket's least recently used cached factor (that
+ * factor is dropped; a later re-solve of it factors anew), and builds a plan
+ * only when the bucket has neither, so `copies` bounds how many factors of one
+ * bucket stay cached. Stops early (BTC_OK) when the HBM budget is full.
+ * Synchronous. Errors: BTC_ERR_ARG, BTC_ERR_UNSUPPORTED, BTC_ERR_OOM,
+ * BTC_ERR_CUDA.
+ */
+int btc_server_prewarm(btc_server_t s, int n, int N_max, int copies);
 
 /* Finish every queued request, release all plans and streams. */
 int btc_server_stop(btc_server_t s);

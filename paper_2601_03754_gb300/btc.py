@@ -85,6 +85,8 @@ _SIGS = {
     "btc_server_poll": [_vp, ctypes.c_int64, ctypes.c_int, _ip, _ip, _dp, _dp],
     "btc_server_stats": [_vp, _vp],
     "btc_server_stop": [_vp],
+    "btc_server_prewarm": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "btc_server_footprint": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "btc_batch_plan": [ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, ctypes.c_int, _vp],
     "btc_batch_query": [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)],
     "btc_batch_factor": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
@@ -93,6 +95,11 @@ _SIGS = {
                                 _dp],
     "btc_batch_info": [_vp, _ip, _ip, _ip],
     "btc_batch_free": [_vp],
+    "btc_batch_factor_solve_refined": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                       ctypes.POINTER(_vp), ctypes.c_double, ctypes.c_int, _ip, _dp],
+    "btc_batch_set_autotune": [_vp, ctypes.c_int],
+    "btc_batch_set_graphs": [_vp, ctypes.c_int],
+    "btc_batch_tuning": [_vp, ctypes.c_int, _ip, _ip, _ip, _ip, _dp],
     "btc_last_error": [],
     "btc_version": [],
 }
@@ -232,7 +239,8 @@ def btc_plan_set_graphs(plan, enable=True):
 
 
 def btc_plan_set_autotune(plan, enable=True):
-    return _check(load().btc_plan_set_autotune(plan.h, int(bool(enable))))
+    """enable: False/0 off, True/1 on, 2 = only a configuration remembered for the shape (no trials)."""
+    return _check(load().btc_plan_set_autotune(plan.h, int(enable)))
 
 
 def btc_plan_tuning(plan):
@@ -420,6 +428,32 @@ def btc_batch_solve_refined(batch, bs, xs, tol=1e-10, maxit=30):
     return it.value, rel.value, rc
 
 
+def btc_batch_factor_solve_refined(batch, Ds, Bs, bs, xs, tol=1e-10, maxit=30):
+    """Factor + FP64-refined solve of every instance (one captured graph once the tuning is settled)."""
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    rc = _check(load().btc_batch_factor_solve_refined(batch.h, _ptr_array(Ds), _ptr_array(Bs), _ptr_array(bs),
+                                                      _ptr_array(xs), tol, maxit, ctypes.byref(it),
+                                                      ctypes.byref(rel)), (ERR_NOT_CONVERGED,))
+    return it.value, rel.value, rc
+
+
+def btc_batch_set_autotune(batch, enable=True):
+    return _check(load().btc_batch_set_autotune(batch.h, int(bool(enable))))
+
+
+def btc_batch_set_graphs(batch, enable=True):
+    return _check(load().btc_batch_set_graphs(batch.h, int(bool(enable))))
+
+
+def btc_batch_tuning(batch, group):
+    """(np, register-budget cap, CTAs per SM, tuned, tuned factor ms) of a group (launch order)."""
+    v = [ctypes.c_int(0) for _ in range(4)]
+    ms = ctypes.c_double(0.0)
+    _check(load().btc_batch_tuning(batch.h, group, *[ctypes.byref(a) for a in v], ctypes.byref(ms)))
+    return v[0].value, v[1].value, v[2].value, bool(v[3].value), ms.value
+
+
 def btc_batch_info(batch):
     k = ctypes.c_int(0)
     blk = ctypes.c_int(0)
@@ -530,6 +564,18 @@ def btc_server_stats(server):
     s = btc_server_stats_t()
     _check(load().btc_server_stats(server.h, ctypes.byref(s)))
     return s.as_dict()
+
+
+def btc_server_prewarm(server, n, N_max, copies=1):
+    """Build, tune and capture `copies` plans of every size bucket up to N_max for block size n."""
+    return _check(load().btc_server_prewarm(server.h, n, N_max, copies))
+
+
+def btc_server_footprint(dtype, N, n):
+    """Device bytes a request of size (N, n) reserves in a server (its bucket plan and staging)."""
+    b = ctypes.c_int64(0)
+    _check(load().btc_server_footprint(dtype, N, n, ctypes.byref(b)))
+    return b.value
 
 
 def btc_server_stop(server):

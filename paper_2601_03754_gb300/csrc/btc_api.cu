@@ -110,6 +110,22 @@ __global__ void k_refine_decide(Readback *rb, double tol, int maxit, int first, 
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// Diagonal entries of nblocks consecutive n x n FP64 blocks set to 1 (the pad blocks of a server's
+// bucketed plans).
+__global__ void k_set_unit_diagonal(double *D, int64_t nblocks, int n) {
+  const int64_t total = nblocks * n;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = q / n, i = q % n;
+    D[(b * n + i) * n + i] = 1.0;
+  }
+}
+
+int set_unit_diagonal(double *D, int64_t nblocks, int n, void *stream) {
+  if (nblocks <= 0) return BTC_OK;
+  return launch_n((const void *)&k_set_unit_diagonal, grid_for(nblocks * n), 256, 0, (cudaStream_t)stream, D,
+                  nblocks, n);
+}
+
 bool dtype_ok(int dtype) {
   return dtype == BTC_F64 || dtype == BTC_F32 || dtype_mixed(dtype);
 }
@@ -153,6 +169,7 @@ struct btc_plan_s {
   int inter_var = 0, inter_ctas = 0;  // the interlaced launch's own configuration
   int occ_fac[kFlowVariants] = {}, occ_fused[kFlowVariants] = {}, occ_rl[kFlowVariants] = {};
   bool autotune = true, tuned[3] = {false, false, false};  // hybrid, right-looking, interlaced launch
+  bool tune_cached_only = false;  // autotune mode 2: a configuration remembered for the shape, no trials
   // executable graph of one refined factor + solve (btc_factor_solve_refined), for the pointers,
   // sizes and configuration it was captured with
   bool graphs = true;
@@ -385,6 +402,10 @@ static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
     }
   }
   const KernelSet &k = *p->ks;
+  if (p->tune_cached_only) {  // nothing remembered: the default configuration, no trial launches
+    p->tuned[alg] = true;
+    return BTC_OK;
+  }
   TimingPause pause(p);
   cudaEvent_t e0, e1;
   BTC_CUDA(cudaEventCreate(&e0));
@@ -393,7 +414,7 @@ static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
   int best_v = k.flow_default, best_c = 0, rc = BTC_OK;
   for (int v = 0; v < k.n_flow_v && rc == BTC_OK; ++v) {
     const int occ = alg ? p->occ_rl[v] : p->occ_fac[v];
-    for (int c = 1; c <= occ && rc == BTC_OK; ++c) {
+    for (int c = 1; c <= occ && rc == BTC_OK; c = next_ctas(c, occ)) {
       apply_flow_config(p, v, c);
       float t[3];
       for (int r = 0; r < 3 && rc == BTC_OK; ++r) {
@@ -509,6 +530,10 @@ static int autotune_inter(btc_plan_s *p, const void *D, const void *B, int m) {
     }
   }
   const KernelSet &k = *p->ks;
+  if (p->tune_cached_only) {
+    p->tuned[2] = true;
+    return BTC_OK;
+  }
   TimingPause pause(p);
   const size_t ybytes = (size_t)p->N * p->np * m * k.elem;
   void *ysave = nullptr;
@@ -522,7 +547,7 @@ static int autotune_inter(btc_plan_s *p, const void *D, const void *B, int m) {
   float best = 1e30f;
   int best_v = p->inter_var, best_c = p->inter_ctas;
   for (int v = 0; v < k.n_flow_v && rc == BTC_OK; ++v) {
-    for (int c = 1; c <= p->occ_fused[v] && rc == BTC_OK; ++c) {
+    for (int c = 1; c <= p->occ_fused[v] && rc == BTC_OK; c = next_ctas(c, p->occ_fused[v])) {
       apply_inter_config(p, v, c);
       float t[3];
       for (int r = 0; r < 3 && rc == BTC_OK; ++r) {
@@ -1601,8 +1626,10 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
 }
 
 int btc_plan_set_autotune(btc_plan_t p, int enable) {
-  if (!p) return fail(BTC_ERR_ARG, "btc_plan_set_autotune: NULL plan");
+  if (!p || enable < 0 || enable > 2) return fail(BTC_ERR_ARG, "btc_plan_set_autotune: invalid arguments");
   p->autotune = enable != 0;
+  p->tune_cached_only = enable == 2;
+  p->tuned[0] = p->tuned[1] = p->tuned[2] = false;
   if (!p->autotune) {
     apply_flow_config(p, p->ks->flow_default, 0);
     p->tuned[0] = p->tuned[1] = p->tuned[2] = false;

@@ -4,7 +4,11 @@
 // for the solve, whose work items are the (instance, node) eliminations of all
 // instances in level order. Each item waits only for the producer nodes of its
 // own instance (bounded waits), so short instances finish early and long ones
-// keep the SMs busy.
+// keep the SMs busy. Each group's factor launch is autotuned (register budget
+// x resident CTAs per SM, i.e. how many nodes one SM holds at once), the
+// groups are launched largest first on their own streams, and the whole
+// factor + refined solve can run as one captured graph with a device-side
+// refinement loop (btc_batch_factor_solve_refined).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,101 +62,142 @@ __global__ void k_batch_unpack(const T *y, const BatchNode *nodes, const InstDes
   }
 }
 
-// FP64 residual of one block row of one instance (one RHS): r -> y (type T),
-// max|r| and max|x| into norms[3*inst + 0/1]. Same arithmetic as the single-
-// instance residual kernel (fixed-order partial sums).
+// FP64 residual of block rows of the group (one RHS): r -> y (type T),
+// max|r| and max|x| into norms[3*inst + 0/1], and with with_anorm also the
+// lower bound of ||Psi_inst||_inf (each |a_ij| rounded toward zero to FP32,
+// row sums with round-toward-zero additions) into norms[3*inst + 2]. One CTA
+// covers NPC = max(1, kResThreads / (kResParts * np)) consecutive block rows
+// of the group, so small blocks keep the CTA's threads busy. Each output's
+// 3n-term dot product is split into kResParts column ranges, each with three
+// independent FP64 chains (the D_i, B_{i-1} and B_i^T terms) added in a fixed
+// order (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const BatchNode *nodes, const InstDesc *inst,
-                                                                const BatchVec *vec, int np, double *norms) {
-  constexpr int NMAX = 128;  // largest compiled block size
-  __shared__ double xs[3 * NMAX];
-  __shared__ double ps[kResParts * NMAX];
-  const BatchNode nd = nodes[blockIdx.x];
-  const InstDesc in = inst[nd.inst];
-  const int n = in.n, N = in.N, i = nd.row;
-  const double *D = reinterpret_cast<const double *>(in.D);
-  const double *B = reinterpret_cast<const double *>(in.B);
-  const double *x = reinterpret_cast<const double *>(vec[nd.inst].x);
-  const double *b = reinterpret_cast<const double *>(vec[nd.inst].b);
-  for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {
-    const int which = q / n, off = q % n, row = i - 1 + which;
-    xs[which * NMAX + off] = (row >= 0 && row < N) ? x[(size_t)row * n + off] : 0.0;
+__global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const BatchNode *nodes, int n_nodes,
+                                                                const InstDesc *inst, const BatchVec *vec, int np,
+                                                                double *norms, int with_anorm) {
+  constexpr int NMAX = 128;  // largest block size of a batch
+  __shared__ double xs[3 * NMAX * 2];
+  __shared__ double ps[kResParts * NMAX * 2];
+  __shared__ float as[kResParts * NMAX * 2];
+  __shared__ unsigned long long red[3 * 8];                 // per block row: max|r|, max|x|, norm bound
+  const int npc = max(1, kResThreads / (kResParts * np));  // block rows per CTA (<= 8: np >= 8)
+  const int slot_sz = np;                                   // per-row stride in the staging arrays
+  const int r0 = blockIdx.x * npc;
+  if (threadIdx.x < 3 * 8) red[threadIdx.x] = 0ull;  // +0.0
+  // stage x_{i-1}, x_i, x_{i+1} of each block row of this CTA
+  for (int q = threadIdx.x; q < npc * 3 * np; q += blockDim.x) {
+    const int w = q / (3 * np), rem = q % (3 * np), which = rem / np, off = rem % np;
+    if (r0 + w >= n_nodes) continue;
+    const BatchNode nd = nodes[r0 + w];
+    const InstDesc in = inst[nd.inst];
+    const int row = nd.row - 1 + which;
+    const double *x = reinterpret_cast<const double *>(vec[nd.inst].x);
+    xs[(w * 3 + which) * slot_sz + off] = (off < in.n && row >= 0 && row < in.N) ? x[(size_t)row * in.n + off] : 0.0;
   }
   __syncthreads();
-  const size_t bs = (size_t)n * n;
-  const double *Di = D + i * bs;
-  const double *Bl = i > 0 ? B + (i - 1) * bs : nullptr;
-  const double *Br = i + 1 < N ? B + i * bs : nullptr;
-  const int chunk = (n + kResParts - 1) / kResParts;
-  for (int idx = threadIdx.x; idx < kResParts * n; idx += blockDim.x) {
-    const int part = idx / n, r = idx % n;
+  for (int idx = threadIdx.x; idx < npc * kResParts * np; idx += blockDim.x) {
+    const int w = idx / (kResParts * np), rem = idx % (kResParts * np), part = rem / np, r = rem % np;
+    if (r0 + w >= n_nodes) continue;
+    const BatchNode nd = nodes[r0 + w];
+    const InstDesc in = inst[nd.inst];
+    const int n = in.n, N = in.N, i = nd.row;
+    if (r >= n) continue;
+    const size_t bs = (size_t)n * n;
+    const double *Di = reinterpret_cast<const double *>(in.D) + i * bs;
+    const double *B = reinterpret_cast<const double *>(in.B);
+    const bool has_l = i > 0, has_u = i + 1 < N;
+    const double *Bl = has_l ? B + (i - 1) * bs : Di;  // a valid address when the block is absent
+    const double *Br = has_u ? B + i * bs : Di;
+    const int chunk = (n + kResParts - 1) / kResParts;
     const int c0 = part * chunk, c1 = min(n, c0 + chunk);
-    double v = 0.0;
-    for (int c = c0; c < c1; ++c) v = fma(r >= c ? Di[r * n + c] : Di[c * n + r], xs[NMAX + c], v);
-    if (Bl)
-      for (int c = c0; c < c1; ++c) v = fma(Bl[r * n + c], xs[c], v);
-    if (Br)
-      for (int c = c0; c < c1; ++c) v = fma(Br[c * n + r], xs[2 * NMAX + c], v);
-    ps[part * NMAX + r] = v;
+    const double *x0 = xs + (w * 3 + 0) * slot_sz, *x1 = x0 + slot_sz, *x2 = x1 + slot_sz;
+    double vd = 0.0, vl = 0.0, vu = 0.0;
+    float sabs = 0.0f;
+    for (int c = c0; c < c1; ++c) {
+      const double ad = __ldg(r >= c ? Di + r * n + c : Di + c * n + r);
+      const double al = has_l ? __ldg(Bl + r * n + c) : 0.0;
+      const double au = has_u ? __ldg(Br + c * n + r) : 0.0;
+      vd = fma(ad, x1[c], vd);
+      vl = fma(al, x0[c], vl);
+      vu = fma(au, x2[c], vu);
+      if (with_anorm)
+        sabs = __fadd_rz(__fadd_rz(__fadd_rz(sabs, abs_lower_f32(ad)), abs_lower_f32(al)), abs_lower_f32(au));
+    }
+    ps[(w * kResParts + part) * slot_sz + r] = (vd + vl) + vu;
+    if (with_anorm) as[(w * kResParts + part) * slot_sz + r] = sabs;
   }
   __syncthreads();
-  double rmax = 0.0, xmax = 0.0;
-  for (int r = threadIdx.x; r < np; r += blockDim.x) {
-    if (r < n) {
-      double ax = 0.0;
-#pragma unroll
-      for (int k = 0; k < kResParts; ++k) ax += ps[k * NMAX + r];
-      const double v = b[(size_t)i * n + r] - ax;
-      y[(size_t)blockIdx.x * np + r] = (T)v;
-      rmax = nan_max(rmax, fabs(v));
-      xmax = nan_max(xmax, fabs(xs[NMAX + r]));
-    } else {
-      y[(size_t)blockIdx.x * np + r] = T(0);
+  for (int q = threadIdx.x; q < npc * np; q += blockDim.x) {
+    const int w = q / np, r = q % np;
+    if (r0 + w >= n_nodes) continue;
+    const BatchNode nd = nodes[r0 + w];
+    const InstDesc in = inst[nd.inst];
+    const int n = in.n;
+    T *yr = y + (size_t)(r0 + w) * np + r;
+    if (r >= n) {
+      *yr = T(0);
+      continue;
     }
+    double ax = 0.0;
+    float rs = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kResParts; ++k) {
+      ax += ps[(w * kResParts + k) * slot_sz + r];
+      if (with_anorm) rs = __fadd_rz(rs, as[(w * kResParts + k) * slot_sz + r]);
+    }
+    const double *b = reinterpret_cast<const double *>(vec[nd.inst].b);
+    const double v = b[(size_t)nd.row * n + r] - ax;
+    *yr = (T)v;
+    // maxima of the block row in shared memory first (non-negative doubles order like their bits; fabs of a
+    // NaN orders above +inf), then one global update per block row
+    atomicMax(&red[3 * w + 0], (unsigned long long)__double_as_longlong(fabs(v)));
+    atomicMax(&red[3 * w + 1], (unsigned long long)__double_as_longlong(fabs(xs[(w * 3 + 1) * slot_sz + r])));
+    if (with_anorm) atomicMax(&red[3 * w + 2], (unsigned long long)__double_as_longlong((double)rs));
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    rmax = nan_max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    xmax = nan_max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(norms + 3 * nd.inst + 0, rmax);
-    atomic_max_nonneg(norms + 3 * nd.inst + 1, xmax);
+  __syncthreads();
+  if (threadIdx.x < 3 * npc) {
+    const int w = threadIdx.x / 3, k = threadIdx.x % 3;
+    if (r0 + w < n_nodes && (k < 2 || with_anorm))
+      atomic_max_nonneg(norms + 3 * nodes[r0 + w].inst + k, __longlong_as_double((long long)red[threadIdx.x]));
   }
 }
 
 // Clears the residual and solution norm slots (norms[3k], norms[3k+1]) of every
-// instance in one launch; the matrix-norm slot norms[3k+2] is kept.
-__global__ void k_batch_clear_norms(double *norms, int count) {
+// instance in one launch; the matrix-norm slot norms[3k+2] too when the next
+// residual forms the matrix-norm bound.
+__global__ void k_batch_clear_norms(double *norms, int count, int with_anorm) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < count) {
     norms[3 * k] = 0.0;
     norms[3 * k + 1] = 0.0;
+    if (with_anorm) norms[3 * k + 2] = 0.0;
   }
 }
 
-// Lower bound of ||Psi||_inf per instance into norms[3*inst + 2] for the
-// refinement's stopping test: each |a_ij| rounded toward zero to FP32, row
-// sums with round-toward-zero additions, so the bound never exceeds the norm.
-__global__ void k_batch_anorm_lb(const BatchNode *nodes, const InstDesc *inst, double *norms) {
-  const BatchNode nd = nodes[blockIdx.x];
-  const InstDesc in = inst[nd.inst];
-  const int n = in.n, N = in.N, i = nd.row;
-  const double *D = reinterpret_cast<const double *>(in.D);
-  const double *B = reinterpret_cast<const double *>(in.B);
-  const size_t bs = (size_t)n * n;
-  const double *Di = D + i * bs;
-  float best = 0.0f;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    float s = 0.0f;
-    for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(r >= c ? Di[r * n + c] : Di[c * n + r]));
-    if (i > 0)
-      for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(B[(i - 1) * bs + r * n + c]));
-    if (i + 1 < N)
-      for (int c = 0; c < n; ++c) s = __fadd_rz(s, abs_lower_f32(B[i * bs + c * n + r]));
-    best = fmaxf(best, s);
+// Stopping test of the graph-resident batch refinement (one CTA): the worst
+// relative residual over the instances (NaN if any is NaN); continue while it
+// is above tol and fewer than maxit steps were taken.
+__global__ void k_batch_decide(const double *norms, int count, double tol, int maxit, int first, void *rb_,
+                               cudaGraphConditionalHandle h) {
+  __shared__ double red[32];
+  double worst = 0.0;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) {
+    const double rn = norms[3 * k], xn = norms[3 * k + 1], an = norms[3 * k + 2];
+    worst = nan_max(worst, (an * xn > 0) ? rn / (an * xn) : rn);
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norms + 3 * nd.inst + 2, (double)best);
+  for (int o = 16; o > 0; o >>= 1) worst = nan_max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) worst = nan_max(worst, red[w]);
+    int *iters = reinterpret_cast<int *>(reinterpret_cast<char *>(rb_) + sizeof(double));
+    double *wst = reinterpret_cast<double *>(rb_);
+    if (first) *iters = 0;
+    const bool more = !(worst <= tol) && worst == worst && *iters < maxit;
+    if (more) *iters += 1;
+    *wst = worst;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
 }
 
 template <typename T, typename S>
@@ -182,6 +227,19 @@ struct BatchGroup {
   double flops = 0;
   cudaStream_t s = nullptr;  // the group's own stream: groups run concurrently
   cudaEvent_t ev = nullptr;  // its join point
+  // persistent factor launch configuration: residency variant and CTAs per SM (autotuned)
+  int occ[kFlowVariants] = {};
+  int var = 0, ctas = 0, sms = 1;
+  bool tuned = false;
+  double tuned_ms = 0.0;
+};
+
+// One readback block of the batch's graph-resident refinement: worst relative residual over the
+// instances, refinement steps taken, and the launch status words of the groups.
+struct BatchReadback {
+  double worst;
+  int iters;
+  int status;
 };
 
 }  // namespace btc
@@ -190,6 +248,14 @@ using namespace btc;
 
 struct btc_batch_s {
   int count = 0, dtype = 0;
+  bool autotune = true, graphs = true;
+  // captured factor + refined solve (btc_batch_factor_solve_refined)
+  cudaStream_t gstream = nullptr, gstream2 = nullptr;
+  cudaEvent_t gevent = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double gtol = -1.0;
+  int gmaxit = -1;
+  BatchReadback *d_rb = nullptr, *h_rb = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<int> N, n;
   std::vector<BatchGroup> groups;
@@ -333,12 +399,18 @@ static int build_group(btc_batch_s *bt, BatchGroup &g) {
   if ((rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.solve_flow, ks.fwd_smem(1))) ||
       (rc = set_smem(ks.root64_first, ks.root_smem)) || (rc = set_smem(ks.root64_rest, ks.root_smem)))
     return rc;
-  int dev = 0, sms = 0, bf = 0, bsl = 0;
+  int dev = 0, sms = 0, bsl = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  BTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, ks.fac_flow, ks.fac_threads, ks.fac_smem));
+  g.sms = std::max(1, sms);
+  for (int v = 0; v < ks.n_flow_v; ++v) {
+    if ((rc = set_smem(ks.flow_v[v].fac, ks.fac_smem))) return rc;
+    BTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ[v], ks.flow_v[v].fac, ks.fac_threads, ks.fac_smem));
+  }
   BTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bsl, ks.solve_flow, kSolveThreads, ks.fwd_smem(1)));
-  g.fac_grid = std::max(1, bf * sms);
+  g.var = ks.flow_default;
+  g.ctas = std::max(1, g.occ[g.var]);
+  g.fac_grid = g.ctas * g.sms;
   g.solve_grid = std::max(1, bsl * sms);
   if (bt->dtype == BTC_F32) {
     g.pack = BatchVecKernels<float, float>::pack();
@@ -398,6 +470,100 @@ static int group_solve(btc_batch_s *bt, BatchGroup &g) {
                   group_sync(g, 1));
 }
 
+// The group's persistent factorization (every level except the mixed path's top separators) with its
+// configuration, then its top-separator roots (FP64 Cholesky) on the mixed path.
+static int group_factor(btc_batch_s *bt, BatchGroup &g, bool roots) {
+  const KernelSet &k = *g.ks;
+  FactorArgs a;
+  a.dpool = g.dpool;
+  a.epool = g.epool;
+  a.inst = bt->d_inst;
+  a.info = bt->d_info;
+  a.status = g.d_flow + 2;
+  InstDesc none{nullptr, nullptr, 0, 0};
+  int rc;
+  BTC_CUDA(cudaMemsetAsync(g.d_flow, 0, 3 * sizeof(int), g.s));
+  if (g.n_fac > 0) {
+    BTC_CUDA(cudaMemsetAsync(g.d_flow + kFlowHeader, 0, sizeof(int) * (size_t)g.n_fac, g.s));
+    a.items = g.d_fac;
+    a.count = g.n_fac;
+    const int32_t *deps = g.d_fac_deps;
+    if ((rc = launch_n(k.flow_v[g.var].fac, std::min(g.fac_grid, g.n_fac), k.fac_threads, k.fac_smem, g.s, a, none,
+                       deps, g.n_first, group_sync(g, 0))))
+      return rc;
+  }
+  if (roots && g.n_roots_first > 0) {
+    a.items = g.d_roots;
+    a.count = g.n_roots_first;
+    if ((rc = launch_n(k.root64_first, g.n_roots_first, k.root_threads, k.root_smem, g.s, a, none))) return rc;
+  }
+  if (roots && g.n_roots_rest > 0) {
+    a.items = g.d_roots + g.n_roots_first;
+    a.count = g.n_roots_rest;
+    if ((rc = launch_n(k.root64_rest, g.n_roots_rest, k.root_threads, k.root_smem, g.s, a, none))) return rc;
+  }
+  return BTC_OK;
+}
+
+// Autotuner of a group's persistent factorization: every compiled residency variant (register
+// budget) at 1, 2, 4, ... CTAs per SM up to what fits, three timed launches each on the batch's own
+// inputs, the fastest median kept. The factor is the same in every configuration (only the schedule
+// changes), so the last launch's result stands.
+static int tune_group(btc_batch_s *bt, BatchGroup &g) {
+  const KernelSet &k = *g.ks;
+  cudaEvent_t e0, e1;
+  BTC_CUDA(cudaEventCreate(&e0));
+  BTC_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_v = g.var, best_c = g.ctas, rc = BTC_OK;
+  for (int v = 0; v < k.n_flow_v && rc == BTC_OK; ++v)
+    for (int c = 1; c <= g.occ[v] && rc == BTC_OK; c = next_ctas(c, g.occ[v])) {
+      g.var = v;
+      g.ctas = c;
+      g.fac_grid = c * g.sms;
+      float t[3];
+      for (int r = 0; r < 3 && rc == BTC_OK; ++r) {
+        cudaEventRecord(e0, g.s);
+        rc = group_factor(bt, g, false);
+        cudaEventRecord(e1, g.s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(BTC_ERR_CUDA, "batch autotune: synchronize failed");
+        cudaEventElapsedTime(&t[r], e0, e1);
+      }
+      std::sort(t, t + 3);
+      if (rc == BTC_OK && t[1] < best) {
+        best = t[1];
+        best_v = v;
+        best_c = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.var = best_v;
+  g.ctas = best_c;
+  g.fac_grid = best_c * g.sms;
+  g.tuned = true;
+  g.tuned_ms = best;
+  return rc;
+}
+
+// Clear the norm slots and run every group's FP64 residual (forks onto the group streams and joins).
+static int batch_residuals(btc_batch_s *bt, int with_anorm) {
+  int rc;
+  if ((rc = launch_n((const void *)&k_batch_clear_norms, (bt->count + 255) / 256, 256, 0, bt->stream, bt->d_norms,
+                     bt->count, with_anorm)))
+    return rc;
+  if ((rc = batch_fork(bt))) return rc;
+  for (BatchGroup &g : bt->groups) {
+    const int npc = std::max(1, kResThreads / (kResParts * g.np));
+    if ((rc = launch_n(g.resid, (g.n_nodes + npc - 1) / npc, kResThreads, 0, g.s, g.y, (const BatchNode *)g.d_nodes,
+                       g.n_nodes, (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, bt->d_norms,
+                       with_anorm)))
+      break;
+  }
+  const int rj = batch_join(bt);
+  return rc ? rc : rj;
+}
+
 static int batch_read_status(btc_batch_s *bt) {
   for (BatchGroup &g : bt->groups) {
     BTC_CUDA(cudaMemcpyAsync(bt->h_status, g.d_flow + 2, sizeof(int), cudaMemcpyDeviceToHost, bt->stream));
@@ -445,6 +611,10 @@ int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int 
     if ((rc = build_group(bt, bt->groups.back()))) return cleanup(rc);
     bt->flops += bt->groups.back().flops;
   }
+  // launch order: the group with the most work first, so that its long tail of dependent upper
+  // levels overlaps the smaller groups' launches
+  std::stable_sort(bt->groups.begin(), bt->groups.end(),
+                   [](const BatchGroup &a, const BatchGroup &b) { return a.flops > b.flops; });
   int64_t *acc = &bt->device_bytes;
   bt->inst_host.assign(count, InstDesc{nullptr, nullptr, 0, 0});
   for (int k = 0; k < count; ++k) bt->inst_host[k] = InstDesc{nullptr, nullptr, N[k], n[k]};
@@ -460,7 +630,9 @@ int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int 
         cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming) != cudaSuccess)
       return cleanup(fail(BTC_ERR_CUDA, "btc_batch_plan: stream creation failed"));
   cudaError_t e;
-  if ((e = cudaMallocHost(&bt->h_norms, 3 * count * sizeof(double))) != cudaSuccess ||
+  if ((rc = batch_alloc((void **)&bt->d_rb, sizeof(BatchReadback), acc))) return cleanup(rc);
+  if ((e = cudaMallocHost(&bt->h_rb, sizeof(BatchReadback))) != cudaSuccess ||
+      (e = cudaMallocHost(&bt->h_norms, 3 * count * sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost(&bt->h_info, count * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMallocHost(&bt->h_status, sizeof(int))) != cudaSuccess)
     return cleanup(fail(BTC_ERR_OOM, "btc_batch_plan: host staging: %s", cudaGetErrorString(e)));
@@ -489,42 +661,10 @@ int btc_batch_factor(btc_batch_t bt, const void *const *D, const void *const *B)
                            bt->stream));
   BTC_CUDA(cudaMemsetAsync(bt->d_info, 0xFF, bt->count * sizeof(unsigned long long), bt->stream));
   int rc = batch_fork(bt);
-  for (BatchGroup &g : bt->groups) {
+  for (BatchGroup &g : bt->groups) {  // largest group first: the small ones fill its tail
     if (rc) break;
-    const KernelSet &k = *g.ks;
-    FactorArgs a;
-    a.dpool = g.dpool;
-    a.epool = g.epool;
-    a.inst = bt->d_inst;
-    a.info = bt->d_info;
-    a.status = g.d_flow + 2;
-    InstDesc none{nullptr, nullptr, 0, 0};
-    if (cudaMemsetAsync(g.d_flow, 0, 3 * sizeof(int), g.s) != cudaSuccess) {
-      rc = fail(BTC_ERR_CUDA, "btc_batch_factor: memset");
-      break;
-    }
-    if (g.n_fac > 0) {
-      if (cudaMemsetAsync(g.d_flow + kFlowHeader, 0, sizeof(int) * (size_t)g.n_fac, g.s) != cudaSuccess) {
-        rc = fail(BTC_ERR_CUDA, "btc_batch_factor: memset");
-        break;
-      }
-      a.items = g.d_fac;
-      a.count = g.n_fac;
-      const int32_t *deps = g.d_fac_deps;
-      if ((rc = launch_n(k.fac_flow, std::min(g.fac_grid, g.n_fac), k.fac_threads, k.fac_smem, g.s, a, none, deps,
-                         g.n_first, group_sync(g, 0))))
-        break;
-    }
-    if (g.n_roots_first > 0) {
-      a.items = g.d_roots;
-      a.count = g.n_roots_first;
-      if ((rc = launch_n(k.root64_first, g.n_roots_first, k.root_threads, k.root_smem, g.s, a, none))) break;
-    }
-    if (g.n_roots_rest > 0) {
-      a.items = g.d_roots + g.n_roots_first;
-      a.count = g.n_roots_rest;
-      if ((rc = launch_n(k.root64_rest, g.n_roots_rest, k.root_threads, k.root_smem, g.s, a, none))) break;
-    }
+    if (bt->autotune && !g.tuned && (rc = tune_group(bt, g))) break;
+    rc = group_factor(bt, g, true);
   }
   const int rj = batch_join(bt);
   if (rc || (rc = rj)) return rc;
@@ -590,30 +730,13 @@ int btc_batch_solve_refined(btc_batch_t bt, const double *const *b, double *cons
   int rc = btc_batch_info(bt, nullptr, nullptr, nullptr);
   if (rc) return rc;
   if ((rc = btc_batch_solve(bt, (const void *const *)b, (void *const *)x))) return rc;
-  if (!bt->anorm_valid) {
-    BTC_CUDA(cudaMemsetAsync(bt->d_norms, 0, 3 * (size_t)bt->count * sizeof(double), bt->stream));
-    if ((rc = batch_fork(bt))) return rc;
-    for (BatchGroup &g : bt->groups)
-      if ((rc = launch_n((const void *)&k_batch_anorm_lb, g.n_nodes, 64, 0, g.s, (const BatchNode *)g.d_nodes,
-                         (const InstDesc *)bt->d_inst, bt->d_norms)))
-        break;
-    const int rj = batch_join(bt);
-    if (rc || (rc = rj)) return rc;
-    bt->anorm_valid = true;
-  }
   int it = 0;
   double worst = 0.0;
   for (;;) {
-    if ((rc = launch_n((const void *)&k_batch_clear_norms, (bt->count + 255) / 256, 256, 0, bt->stream, bt->d_norms,
-                       bt->count)))
-      return rc;
-    if ((rc = batch_fork(bt))) return rc;
-    for (BatchGroup &g : bt->groups)
-      if ((rc = launch_n(g.resid, g.n_nodes, kResThreads, 0, g.s, g.y, (const BatchNode *)g.d_nodes,
-                         (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, bt->d_norms)))
-        break;
-    const int rj = batch_join(bt);
-    if (rc || (rc = rj)) return rc;
+    // the first residual after a factorization also forms the matrix-norm bounds
+    const int with_anorm = bt->anorm_valid ? 0 : 1;
+    if ((rc = batch_residuals(bt, with_anorm))) return rc;
+    bt->anorm_valid = true;
     BTC_CUDA(cudaMemcpyAsync(bt->h_norms, bt->d_norms, 3 * bt->count * sizeof(double), cudaMemcpyDeviceToHost,
                              bt->stream));
     BTC_CUDA(cudaStreamSynchronize(bt->stream));
@@ -646,9 +769,218 @@ int btc_batch_solve_refined(btc_batch_t bt, const double *const *b, double *cons
   return BTC_OK;
 }
 
+int btc_batch_set_autotune(btc_batch_t bt, int enable) {
+  if (!bt) return fail(BTC_ERR_ARG, "btc_batch_set_autotune: NULL batch");
+  bt->autotune = enable != 0;
+  return BTC_OK;
+}
+
+int btc_batch_set_graphs(btc_batch_t bt, int enable) {
+  if (!bt) return fail(BTC_ERR_ARG, "btc_batch_set_graphs: NULL batch");
+  bt->graphs = enable != 0;
+  if (bt->gexec) {
+    cudaGraphExecDestroy(bt->gexec);
+    bt->gexec = nullptr;
+  }
+  return BTC_OK;
+}
+
+int btc_batch_tuning(btc_batch_t bt, int group, int *np, int *resident_cap, int *ctas_per_sm, int *tuned,
+                     double *factor_ms) {
+  if (!bt || group < 0 || group >= (int)bt->groups.size()) return fail(BTC_ERR_ARG, "btc_batch_tuning: bad group");
+  const BatchGroup &g = bt->groups[group];
+  if (np) *np = g.np;
+  if (resident_cap) *resident_cap = g.ks->flow_v[g.var].minb;
+  if (ctas_per_sm) *ctas_per_sm = g.ctas;
+  if (tuned) *tuned = g.tuned ? 1 : 0;
+  if (factor_ms) *factor_ms = g.tuned ? g.tuned_ms : 0.0;
+  return BTC_OK;
+}
+
+}  // extern "C"
+
+namespace btc {
+
+// Capture the batch's factor + refined solve as one executable graph: every group's persistent
+// factorization and top-separator roots (forked onto the group streams), the packed first solve,
+// the FP64 residuals with the matrix-norm bounds, the device-side stopping test, then a while node
+// whose body (groups in turn on one stream) is one correction solve per group, the update, the
+// residuals and the stopping test; finally one copy of the readback block. The instances' pointers
+// are read from device arrays at run time, so the graph serves every call with the same tol and maxit.
+static int build_batch_graph(btc_batch_s *bt, double tol, int maxit) {
+  if (bt->gexec) {
+    cudaGraphExecDestroy(bt->gexec);
+    bt->gexec = nullptr;
+  }
+  if (!bt->gstream) {
+    BTC_CUDA(cudaStreamCreateWithFlags(&bt->gstream, cudaStreamNonBlocking));
+    BTC_CUDA(cudaStreamCreateWithFlags(&bt->gstream2, cudaStreamNonBlocking));
+    BTC_CUDA(cudaEventCreateWithFlags(&bt->gevent, cudaEventDisableTiming));
+  }
+  cudaStream_t user = bt->stream;
+  cudaGraph_t graph = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  cudaError_t e = cudaStreamBeginCapture(bt->gstream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(BTC_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  bt->stream = bt->gstream;
+  auto body = [&]() -> int {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    BTC_CUDA(cudaStreamGetCaptureInfo(bt->gstream, &st, nullptr, &cg, nullptr, nullptr, nullptr));
+    BTC_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
+    BTC_CUDA(cudaMemsetAsync(bt->d_info, 0xFF, bt->count * sizeof(unsigned long long), bt->stream));
+    int rc = batch_fork(bt);
+    for (BatchGroup &g : bt->groups)
+      if (!rc) rc = group_factor(bt, g, true);
+    const int rj = batch_join(bt);
+    if (rc || (rc = rj)) return rc;
+    if ((rc = batch_fork(bt))) return rc;
+    for (BatchGroup &g : bt->groups) {
+      int assign = 0;
+      if ((rc = launch_n(g.pack, g.n_nodes, 64, 0, g.s, g.y, (const BatchNode *)g.d_nodes, (const InstDesc *)bt->d_inst,
+                         (const BatchVec *)bt->d_vec, g.np)) ||
+          (rc = group_solve(bt, g)) ||
+          (rc = launch_n(g.unpack, g.n_nodes, 64, 0, g.s, (const void *)g.y, (const BatchNode *)g.d_nodes,
+                         (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, assign)))
+        break;
+    }
+    const int rj2 = batch_join(bt);
+    if (rc || (rc = rj2)) return rc;
+    int one = 1, zero = 0;
+    if ((rc = batch_residuals(bt, 1)) ||
+        (rc = launch_n((const void *)&k_batch_decide, 1, 256, 0, bt->stream, (const double *)bt->d_norms, bt->count,
+                       tol, maxit, one, (void *)bt->d_rb, h)))
+      return rc;
+    // the correction loop as a while node; its body runs the groups in turn on one stream
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t ndeps = 0;
+    BTC_CUDA(cudaStreamGetCaptureInfo(bt->gstream, &st, nullptr, &cg, &deps, &edata, &ndeps));
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    BTC_CUDA(cudaGraphAddNode(&wnode, cg, deps, edata, ndeps, &cp));
+    cudaGraph_t loop = cp.conditional.phGraph_out[0];
+    BTC_CUDA(cudaStreamUpdateCaptureDependencies(bt->gstream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    BTC_CUDA(cudaStreamBeginCaptureToGraph(bt->gstream2, loop, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    std::vector<cudaStream_t> saved;
+    for (BatchGroup &g : bt->groups) {
+      saved.push_back(g.s);
+      g.s = bt->gstream2;
+    }
+    bt->stream = bt->gstream2;
+    for (BatchGroup &g : bt->groups) {
+      int accumulate = 1;
+      if (!rc) rc = group_solve(bt, g);
+      if (!rc)
+        rc = launch_n(g.unpack, g.n_nodes, 64, 0, g.s, (const void *)g.y, (const BatchNode *)g.d_nodes,
+                      (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, accumulate);
+    }
+    if (!rc) {  // residuals of the groups in turn (no fork inside the loop body)
+      rc = launch_n((const void *)&k_batch_clear_norms, (bt->count + 255) / 256, 256, 0, bt->stream, bt->d_norms,
+                    bt->count, zero);
+      for (BatchGroup &g : bt->groups) {
+        const int npc = std::max(1, kResThreads / (kResParts * g.np));
+        if (!rc)
+          rc = launch_n(g.resid, (g.n_nodes + npc - 1) / npc, kResThreads, 0, g.s, g.y, (const BatchNode *)g.d_nodes,
+                        g.n_nodes, (const InstDesc *)bt->d_inst, (const BatchVec *)bt->d_vec, g.np, bt->d_norms,
+                        zero);
+      }
+    }
+    if (!rc)
+      rc = launch_n((const void *)&k_batch_decide, 1, 256, 0, bt->stream, (const double *)bt->d_norms, bt->count, tol,
+                    maxit, zero, (void *)bt->d_rb, h);
+    for (size_t q = 0; q < bt->groups.size(); ++q) bt->groups[q].s = saved[q];
+    cudaGraph_t loop_out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bt->gstream2, &loop_out);
+    bt->stream = bt->gstream;
+    if (rc) return rc;
+    if (e2 != cudaSuccess) return fail(BTC_ERR_CUDA, "batch graph capture (loop body): %s", cudaGetErrorString(e2));
+    BTC_CUDA(cudaMemcpyAsync(bt->h_rb, bt->d_rb, sizeof(BatchReadback), cudaMemcpyDeviceToHost, bt->stream));
+    return BTC_OK;
+  };
+  int rc = body();
+  e = cudaStreamEndCapture(bt->gstream, &graph);
+  bt->stream = user;
+  if (rc == BTC_OK && e != cudaSuccess) rc = fail(BTC_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  if (rc == BTC_OK && (e = cudaGraphInstantiate(&bt->gexec, graph, 0)) != cudaSuccess)
+    rc = fail(BTC_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+  if (graph) cudaGraphDestroy(graph);
+  if (rc) {
+    bt->gexec = nullptr;
+    cudaGetLastError();
+    return rc;
+  }
+  bt->gtol = tol;
+  bt->gmaxit = maxit;
+  return BTC_OK;
+}
+
+}  // namespace btc
+
+extern "C" {
+
+int btc_batch_factor_solve_refined(btc_batch_t bt, const void *const *D, const void *const *B, const double *const *b,
+                                   double *const *x, double tol, int maxit, int *iters, double *max_relres) {
+  if (!bt || !D || !B || !b || !x || maxit < 0)
+    return fail(BTC_ERR_ARG, "btc_batch_factor_solve_refined: invalid arguments");
+  if (bt->dtype == BTC_F32) return fail(BTC_ERR_ARG, "btc_batch_factor_solve_refined needs an FP64 or mixed batch");
+  bool settled = true;  // the groups' launch configurations are final (tuned, or tuning is off)
+  if (bt->autotune)
+    for (const BatchGroup &g : bt->groups) settled = settled && g.tuned;
+  if (!bt->graphs || !settled) {  // plain launches (and, the first time, the tuning)
+    int rc = btc_batch_factor(bt, D, B);
+    return rc ? rc : btc_batch_solve_refined(bt, b, x, tol, maxit, iters, max_relres);
+  }
+  for (int k = 0; k < bt->count; ++k) {
+    if (!D[k] || (bt->N[k] > 1 && !B[k])) return fail(BTC_ERR_ARG, "btc_batch_factor_solve_refined: instance %d", k);
+    if (((uintptr_t)D[k] | (uintptr_t)B[k]) & 15) return fail(BTC_ERR_ARG, "instance %d: 16-byte alignment", k);
+    bt->inst_host[k].D = D[k];
+    bt->inst_host[k].B = B[k];
+  }
+  BTC_CUDA(cudaMemcpyAsync(bt->d_inst, bt->inst_host.data(), bt->count * sizeof(InstDesc), cudaMemcpyHostToDevice,
+                           bt->stream));
+  int rc = batch_set_vec(bt, (const void *const *)b, (void *const *)x);
+  if (rc) return rc;
+  if (!bt->gexec || bt->gtol != tol || bt->gmaxit != maxit) {
+    if ((rc = build_batch_graph(bt, tol, maxit))) {
+      if (rc != BTC_ERR_CUDA) return rc;
+      bt->graphs = false;  // capture refused: plain launches from now on
+      cudaGetLastError();
+      rc = btc_batch_factor(bt, D, B);
+      return rc ? rc : btc_batch_solve_refined(bt, b, x, tol, maxit, iters, max_relres);
+    }
+  }
+  BTC_CUDA(cudaEventRecord(bt->gevent, bt->stream));
+  BTC_CUDA(cudaStreamWaitEvent(bt->gstream, bt->gevent, 0));
+  BTC_CUDA(cudaGraphLaunch(bt->gexec, bt->gstream));
+  BTC_CUDA(cudaStreamSynchronize(bt->gstream));
+  bt->factored = true;
+  bt->anorm_valid = true;
+  if ((rc = btc_batch_info(bt, nullptr, nullptr, nullptr))) return rc;
+  if (iters) *iters = bt->h_rb->iters;
+  if (max_relres) *max_relres = bt->h_rb->worst;
+  if (!(bt->h_rb->worst <= tol))
+    return fail(BTC_ERR_NOT_CONVERGED, "batch refinement stopped at %.3e", bt->h_rb->worst);
+  return BTC_OK;
+}
+
 int btc_batch_free(btc_batch_t bt) {
   if (!bt) return BTC_OK;
   cudaStreamSynchronize(bt->stream);
+  if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+  if (bt->gstream) {
+    cudaStreamSynchronize(bt->gstream);
+    cudaStreamDestroy(bt->gstream);
+    cudaStreamDestroy(bt->gstream2);
+    cudaEventDestroy(bt->gevent);
+  }
+  if (bt->d_rb) cudaFree(bt->d_rb);
+  if (bt->h_rb) cudaFreeHost(bt->h_rb);
   for (BatchGroup &g : bt->groups) {
     if (g.s) {
       cudaStreamSynchronize(g.s);

@@ -15,7 +15,7 @@ struct FlowVariant {
   int minb = 0;  // 0: absent
   const void *fac = nullptr, *fac_fwd = nullptr, *fac_rl = nullptr;
 };
-constexpr int kFlowVariants = 4;
+constexpr int kFlowVariants = 5;
 
 struct KernelSet {
   bool valid = false;

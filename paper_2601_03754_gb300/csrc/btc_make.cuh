@@ -22,7 +22,8 @@ size_t fused_smem_fn(int m) { return fused_smem_bytes<T, NP, R>(m); }
 inline size_t zero_smem_fn(int) { return 0; }
 
 // Residency variants of the persistent factor kernels: caps 1, 2, 3, 4 CTAs per
-// SM (1, 2, 4, 8 for 64-thread CTAs), those that shared memory and threads allow.
+// SM (1, 2, 4, 8, 16 for 64-thread CTAs: many small nodes resident on one SM),
+// those that shared memory and threads allow.
 template <typename T, typename S, int NP, int R, int MINB>
 void add_flow_variant(KernelSet &k) {
   if constexpr (MINB == 1 || MINB <= FlowFit<T, NP, R>::value) {
@@ -61,6 +62,7 @@ KernelSet make_set() {
   add_flow_variant<T, S, NP, R, 2>(k);
   add_flow_variant<T, S, NP, R, small ? 4 : 3>(k);
   add_flow_variant<T, S, NP, R, small ? 8 : 4>(k);
+  if constexpr (small) add_flow_variant<T, S, NP, R, 16>(k);
   // default without tuning: two resident CTAs where they fit (more registers per
   // thread than the maximum residency; measured best at N = 1024, n = 64)
   k.flow_default = k.n_flow_v > 1 ? 1 : 0;

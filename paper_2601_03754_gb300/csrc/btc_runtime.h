@@ -36,6 +36,9 @@ inline int launch_n(const void *fn, int grid, int block, size_t smem, cudaStream
   return BTC_OK;
 }
 
+// CTAs-per-SM counts a tuner tries: 1, 2, 4, ... and the largest that fits (occ); after occ: occ + 1 (stop).
+inline int next_ctas(int c, int occ) { return c >= occ ? occ + 1 : (2 * c <= occ ? 2 * c : occ); }
+
 inline int grid_for(int64_t total) {
   int64_t g = (total + 255) / 256;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));

@@ -33,7 +33,8 @@ def make_pool(count=24, seed=0, sizes=(12, 24, 48, 96), nmin=50, nmax=5000, devi
 
 def run_stream(server, pool, rate, count, seed=0, tol=1e-10, maxit=30):
     """Submit `count` requests at Poisson arrival times with mean `rate` per second.
-    Returns (results, wall seconds)."""
+    Returns (results, wall seconds, solutions, pool index of each request, right-hand sides, seconds
+    from the first to the last submission)."""
     import torch
     reqs = gen.request_stream(rate, count, seed=seed)
     rhs, xs, tickets, which = [], [], [], []
@@ -58,9 +59,10 @@ def run_stream(server, pool, rate, count, seed=0, tol=1e-10, maxit=30):
         tickets.append(t)
         if r["resolve_of"] < 0:
             factor_ticket[k] = t
+    submit_span = time.perf_counter() - t0
     results = [btc.btc_server_poll(server, t, wait=True) for t in tickets]
     wall = time.perf_counter() - t0
-    return results, wall, xs, which, rhs
+    return results, wall, xs, which, rhs, submit_span
 
 
 def check_results(pool, xs, which, rhs):

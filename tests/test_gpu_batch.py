@@ -1,6 +1,8 @@
 """Batched plans: many uneven instances in one persistent launch per block-size
 group, against single-instance plans (bitwise, same per-node arithmetic) and
-against the FP64 oracle."""
+against the FP64 oracle; the per-group autotuner (every configuration gives the
+same factor) and the captured factor + refined-solve graph (bitwise equal to the
+plain launches, replayed with new inputs)."""
 import numpy as np
 import pytest
 
@@ -82,3 +84,60 @@ def test_batch_reports_the_failing_instance():
     btc.btc_batch_factor(batch, [dev(D, torch.float64) for D in Ds], [dev(B, torch.float64) for B in Bs])
     rc, k, blk, col = btc.btc_batch_info(batch)
     assert rc == btc.ERR_NOT_SPD and k == 6 and blk == 0 and col == 0
+
+
+def _dev_inputs(Ds, Bs, bs):
+    return ([dev(D, torch.float64) for D in Ds], [dev(B, torch.float64) for B in Bs],
+            [dev(b, torch.float64) for b in bs])
+
+
+@pytest.mark.parametrize("dt", [btc.F64, btc.MIXED_F32], ids=["f64", "mixed"])
+def test_batch_tuned_configuration_gives_the_same_factor(dt):
+    Ds, Bs, bs = _inputs(dt, seed=13)
+    Dd, Bd, bd = _dev_inputs(Ds, Bs, bs)
+    out = []
+    for tune in (False, True):
+        batch = btc.btc_batch_plan([N for N, _ in SIZES], [n for _, n in SIZES], dt)
+        btc.btc_batch_set_autotune(batch, tune)
+        btc.btc_batch_factor(batch, Dd, Bd)
+        xd = [torch.zeros_like(b) for b in bd]
+        btc.btc_batch_solve(batch, bd, xd)
+        out.append([x.cpu().numpy() for x in xd])
+        groups = btc.btc_batch_query(batch)["groups"]
+        nps = []
+        for g in range(groups):
+            np_, cap, ctas, tuned, ms = btc.btc_batch_tuning(batch, g)
+            assert tuned == tune and cap >= 1 and ctas >= 1 and (ms > 0) == tune
+            nps.append(np_)
+        assert sorted(nps) == sorted({btc.btc_describe(N, n)["np"] for N, n in SIZES})
+        batch.free()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("dt", [btc.F64, btc.MIXED_F32], ids=["f64", "mixed"])
+def test_batch_graph_equals_plain_launches_and_replays_new_inputs(dt):
+    sets = [_inputs(dt, seed=s, delta=1e-2) for s in (21, 22)]
+    plain = []
+    for Ds, Bs, bs in sets:  # reference: plain launches
+        Dd, Bd, bd = _dev_inputs(Ds, Bs, bs)
+        batch = btc.btc_batch_plan([N for N, _ in SIZES], [n for _, n in SIZES], dt)
+        btc.btc_batch_set_graphs(batch, False)
+        xd = [torch.zeros_like(b) for b in bd]
+        it, rel, rc = btc.btc_batch_factor_solve_refined(batch, Dd, Bd, bd, xd, tol=1e-10, maxit=30)
+        assert rc == btc.OK and rel <= 1e-10
+        plain.append(([x.cpu().numpy() for x in xd], it, rel))
+        batch.free()
+    batch = btc.btc_batch_plan([N for N, _ in SIZES], [n for _, n in SIZES], dt)
+    for rep in range(4):  # tuning pass, capture, replay, replay with the other inputs
+        Ds, Bs, bs = sets[rep % 2] if rep >= 2 else sets[0]
+        Dd, Bd, bd = _dev_inputs(Ds, Bs, bs)
+        xd = [torch.zeros_like(b) for b in bd]
+        it, rel, rc = btc.btc_batch_factor_solve_refined(batch, Dd, Bd, bd, xd, tol=1e-10, maxit=30)
+        ref = plain[rep % 2] if rep >= 2 else plain[0]
+        assert rc == btc.OK and it == ref[1] and rel == ref[2], (rep, it, rel, ref[1:])
+        for a, b in zip(xd, ref[0]):
+            np.testing.assert_array_equal(a.cpu().numpy(), b)
+        for k, (N, n) in enumerate(SIZES):
+            assert oracle.relres(Ds[k], Bs[k][:max(N - 1, 0)], xd[k].cpu().numpy(), bs[k]) <= 1e-10
+    batch.free()

@@ -81,8 +81,8 @@ def test_resolve_uses_the_cached_factor_and_eviction_recomputes():
     srv.stop()
     # a budget that holds one plan: the cached factor is evicted by the next request,
     # and the re-solve falls back to a fresh factorization (a cache miss)
-    one = btc.btc_describe(pool[1]["N"], pool[1]["n"], btc.MIXED_F32)["device_bytes"]
-    other = btc.btc_describe(pool[4]["N"], pool[4]["n"], btc.MIXED_F32)["device_bytes"]
+    one = btc.btc_server_footprint(btc.MIXED_F32, pool[1]["N"], pool[1]["n"])
+    other = btc.btc_server_footprint(btc.MIXED_F32, pool[4]["N"], pool[4]["n"])
     srv = btc.btc_server_start(btc.MIXED_F32, slots=1, hbm_budget_bytes=max(one, other) + 1024, cache_factors=True)
     t0 = btc.btc_server_submit(srv, p["N"], p["n"], p["D"], p["B"], p["b"], torch.zeros_like(p["b"]))
     q = pool[4]
@@ -147,4 +147,39 @@ def test_oversized_request_is_rejected():
     with pytest.raises(btc.BtcError) as ei:
         btc.btc_server_submit(srv, 1000, 48, D, D, b, b)
     assert ei.value.code == btc.ERR_OOM
+    srv.stop()
+
+
+def test_bucketed_plans_serve_smaller_systems_and_prewarm():
+    """A plan of a size bucket serves every N up to the bucket, padded: the result equals the result of the
+    same request on an exact-size plan to the refinement tolerance, and meets it against the oracle; a
+    prewarmed server builds no plan on the request path (its device bytes do not grow)."""
+    srv = btc.btc_server_start(btc.MIXED_F32, slots=3, hbm_budget_bytes=8 << 30, cache_factors=True)
+    btc.btc_server_prewarm(srv, 24, 400, copies=2)
+    before = btc.btc_server_stats(srv)["device_bytes"]
+    assert before > 0
+    cases = []
+    for k, N in enumerate((17, 63, 100, 101, 333, 400)):
+        D, B = gen.mpc(N, 24, seed=300 + k)
+        b = gen.rhs(N, 24, 1, seed=400 + k)[:, 0]
+        cases.append((N, D, B, b))
+    outs = []
+    for N, D, B, b in cases:
+        x = torch.zeros(N * 24, dtype=torch.float64, device="cuda")
+        t = btc.btc_server_submit(srv, N, 24, dev(D, torch.float64), dev(B, torch.float64), dev(b, torch.float64), x)
+        r = btc.btc_server_poll(srv, t)
+        assert r["status"] == btc.OK and r["relres"] <= 1e-10
+        outs.append((t, x))
+    st = btc.btc_server_stats(srv)
+    assert st["device_bytes"] <= before + 1
+    # re-solves of the padded cached factors
+    for (N, D, B, b), (t, x) in zip(cases, outs):
+        xh = x.cpu().numpy()
+        assert oracle.relres(D, B, xh, b) <= 1e-10
+        b2 = gen.rhs(N, 24, 1, seed=N)[:, 0]
+        x2 = torch.zeros_like(x)
+        t2 = btc.btc_server_submit(srv, N, 24, dev(D, torch.float64), dev(B, torch.float64), dev(b2, torch.float64),
+                                   x2, factor_id=t)
+        assert btc.btc_server_poll(srv, t2)["status"] == btc.OK
+        assert oracle.relres(D, B, x2.cpu().numpy(), b2) <= 1e-10
     srv.stop()
