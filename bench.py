@@ -264,11 +264,22 @@ def cpu_baseline_sample(budget_s=12.0, max_reps=200):
 
 
 def run_profile(which):
-    """The benchmark workload without timing: warm-up pass + one pass, for ncu launch lists."""
+    """The benchmark workload without timing: warm-up pass + one pass, for ncu launch lists. The
+    blocked-256 modes factor N=128, n=256 (TF32 or BF16 tile tasks) twice instead."""
     import torch
     from paper_2601_03754_gb300 import btc, build, gen
     build.build()
     btc.load()
+    if which in ("tiles_tf32", "tiles_bf16"):
+        dt = btc.MIXED_TF32 if which == "tiles_tf32" else btc.MIXED_BF16
+        D, B = gen.bt_random_torch(128, 256, delta=1.0, seed=7)
+        p = btc.btc_plan(128, 256, dt)
+        for _ in range(2):
+            btc.btc_factor(p, D, B)
+        print("profile", which, btc.btc_info(p))
+        p.free()
+        torch.cuda.synchronize()
+        return 0
     W = WORKLOAD
     N, n, m = W["N"], W["n"], W["nrhs"]
     if which == "tf32":  # the tensor-core path on a smaller large-block case (inputs 134 MB > L2)
@@ -663,17 +674,22 @@ def serving_measure(btc, torch, rates=(1000.0, 5000.0, 20000.0, 50000.0), count=
         serve.run_stream(srv, pool, 2000.0, 200, seed=1)  # warm-up traffic
         knee = None
         for rate in rr:
-            st0 = btc.btc_server_stats(srv)
+            btc.btc_server_reset_stats(srv)
             results, wall, xs, which, rhs, span = serve.run_stream(srv, pool, rate, cnt, seed=2)
             st = btc.btc_server_stats(srv)
             lat = np.asarray([r["latency_us"] for r in results if r["status"] == btc.OK])
             ok = int(lat.size)
             sustained = ok / wall
-            row = {"offered_req_per_s": cnt / span if span > 0 else None,
+            statuses = {}
+            for r_ in results:
+                statuses[str(r_["status"])] = statuses.get(str(r_["status"]), 0) + 1
+            row = {"offered_req_per_s": cnt / span if span > 0 else None, "statuses": statuses,
                    "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
                    "mean_us": float(lat.mean()), "solves_per_s": sustained, "completed": ok,
-                   "cache_hits": st["cache_hits"] - st0["cache_hits"],
-                   "max_relres": max(r["relres"] for r in results),
+                   "cache_hits": st["cache_hits"],
+                   "max_relres": max(r["relres"] for r in results if r["status"] == btc.OK),
+                   "queue_and_service_us": {k: round(st[k], 1) for k in (
+                       "p50_queue_us", "p99_queue_us", "p50_service_us", "p99_service_us")},
                    **serve.check_results(pool, xs, which, rhs)}
             res[str(int(rate))] = row
             if knee is None and sustained < 0.9 * rate:
@@ -697,7 +713,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the N=4096, n in {128, 256} measurement")
     ap.add_argument("--no-c2", action="store_true", help="skip the N=1024 delta/MPC/16-RHS rows")
     ap.add_argument("--phases", action="store_true", help="per-level node phase times of the factor launch")
-    ap.add_argument("--profile", choices=["mixed", "f64", "both", "tf32"], default=None,
+    ap.add_argument("--profile", choices=["mixed", "f64", "both", "tf32", "tiles_tf32", "tiles_bf16"], default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
     if args.profile:

@@ -157,6 +157,64 @@ enum btc_variant { BTC_VARIANT_HYBRID = 0, BTC_VARIANT_RIGHT_LOOKING = 1 };
 int btc_plan_set_variant(btc_plan_t p, int variant);
 
 /*
+ * Elimination order of the plan (default BTC_ORDER_ND).
+ * BTC_ORDER_ND: the multi-stage (nested-dissection) permutation P_inf of
+ *   Sec. 4.3, floor(log2 N) + 1 dependent levels, about (19/3) N n^3 flops.
+ * BTC_ORDER_PARTITION: the partition permutation Psi_p of Sec. 4.1 (Alg. 4)
+ *   with `chunks` = p chunks and p - 1 pivots, chunk sizes by Proposition 1
+ *   (N_1 / N_k = 19 / 7, rounded to the split with the smaller larger phase
+ *   cost): every chunk is eliminated left to right as a chain (chunks in
+ *   parallel), then the pivots in order. chunks = 1 is the natural order of
+ *   Alg. 1 ((7/3) N n^3 flops, a chain of N nodes). Fewer flops than ND for
+ *   few chunks, a longer dependent chain: for throughput modes with much
+ *   instance parallelism rather than for the latency of one system.
+ * The plan's pools and schedules are rebuilt (synchronizes the plan's stream;
+ * the previous factor is lost). Partition plans convert the caller's D and B
+ * in a packing pass, solve with the persistent schedule only, and do not use
+ * the interlaced launch or the right-looking variant; the blocked 256 plans
+ * keep ND. Errors: BTC_ERR_ARG (too many chunks for N), BTC_ERR_UNSUPPORTED.
+ */
+enum btc_order { BTC_ORDER_ND = 0, BTC_ORDER_PARTITION = 1 };
+int btc_plan_set_order(btc_plan_t p, int order, int chunks);
+
+/*
+ * Host-only planner (no GPU needed) for either elimination order: fills *info
+ * as btc_describe does (info may be NULL) and, when not NULL, order_out[t] =
+ * the t-th eliminated node (0-based) and levels_out[t] its launch level
+ * (1-based: the chain position, then one level per pivot, for
+ * BTC_ORDER_PARTITION), t = 0..N-1. Errors: BTC_ERR_ARG (bad arguments, too
+ * many chunks), BTC_ERR_UNSUPPORTED (block size; partition orders of blocked
+ * 256 plans).
+ */
+int btc_describe_order(int N, int n, int dtype, int order, int chunks, btc_plan_info *info, int *order_out,
+                       int *levels_out);
+
+/*
+ * Host-only, for inspection and tests: the work items of a plan of N blocks in
+ * either order, with every block offset in units of blocks (pool index).
+ * Each count is the capacity of its array on input (rows; arrays may be NULL
+ * to query) and the number of rows on output.
+ * fac_rows, 14 per factor item in launch order: level (1-based), d_self,
+ *   d_next, r_up, r_down, p_a, p_b, fill, d_prev (diagonal pool indices d_*,
+ *   off-diagonal pool indices r_*, p_*, fill; -1: none), node (0-based),
+ *   flags (1: the fill block holds S'(up, down), else S'(down, up); 2: top
+ *   separator), then the three items it waits for (-1: none).
+ *   One item eliminates node e with the Schur complement S_e = Dhat[d_self]
+ *   - P^T P (P = U[p_a]): S_e = U_e^T U_e; U[r_up] <- U_e^-T S(e, up);
+ *   U[r_down] <- U_e^-T S(e, down); Dhat[d_next] -= U[r_down]^T U[r_down]
+ *   (- U[p_b]^T U[p_b]); U[fill] <- -U[r_up]^T U[r_down] (or its transpose).
+ * solve_rows, 10 per solve item: y_self, y_a, e_a, y_b, e_b, d_self, kind,
+ *   three dependencies. kind 0 (forward): y_self -= U[e_a]^T y_a + U[e_b]^T
+ *   y_b, then y_self <- U_self^-T y_self when d_self >= 0; kind 1 (backward):
+ *   y_self <- U_self^-1 (y_self - U[e_a] y_a - U[e_b] y_b).
+ * slot_rows, 3 per off-diagonal pool block: the node whose variables are its
+ *   rows, the partner node, and for an original coupling slot v (nodes v,
+ *   v + 1) 1 when it starts as B_v^T, 0 when B_v (-1 for fill slots).
+ */
+int btc_schedule_items(int N, int order, int chunks, int64_t *fac_rows, int *n_fac, int64_t *solve_rows,
+                       int *n_solve, int *slot_rows, int *n_slots);
+
+/*
  * Precision of the top-separator Cholesky of the mixed paths (the potrf of
  * Alg. 5's last iteration; the BTC_MIXED_* dtypes; other dtypes ignore
  * it). BTC_ROOT_FP64 (default): FP64 arithmetic; the pivots of this step
@@ -539,6 +597,100 @@ const char *btc_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int btc_version(void);
 
+/* ---------------------------------------------------------------- bordered systems
+ * Arrow structures: the block-tridiagonal Psi bordered by m dense coupling
+ * rows C and a dense block A,
+ *     Psi_a = [[Psi, C^T], [C, A]],
+ * which the permuted Cholesky view of Sec. 4.3 extends to by eliminating the
+ * border after the whole nested-dissection tree (the paper names arrow
+ * structures as a natural extension there, and as future work in its
+ * conclusion). The border's Schur complement S = A - C Psi^{-1} C^T is formed
+ * in FP64 from Z = Psi^{-1} C^T (the plan's FP64-refined solves) and factored
+ * in FP64; solves combine Psi^{-1} (refined), S^{-1} and Z, with FP64 residuals
+ * of the whole bordered system. Layouts: C [m][N*n] row-major (C[r][i*n + c]
+ * couples border variable r with variable c of block i); A [m][m] (lower
+ * triangle read); b, x [N*n + m] (the block-tridiagonal part first). Every
+ * pointer is a device pointer; the caller keeps D, B, C and A alive and
+ * unchanged from btc_arrow_factor until the last btc_arrow_solve.
+ */
+typedef struct btc_arrow_s *btc_arrow_t;
+
+/* Plan a bordered system of N blocks of size n and border width m
+ * (1 <= m <= 64). dtype: BTC_F64 or a BTC_MIXED_* dtype (the arithmetic of the
+ * block-tridiagonal factor; the border is FP64). Errors: BTC_ERR_ARG,
+ * BTC_ERR_UNSUPPORTED, BTC_ERR_OOM, BTC_ERR_CUDA. */
+int btc_arrow_plan(btc_arrow_t *out, int N, int n, int m, int dtype, void *stream);
+
+/* Factor: Psi (Alg. 5), Z = Psi^{-1} C^T by refined solves to tol (at most
+ * maxit refinement steps each), S = A - C Z and its FP64 Cholesky factor, and
+ * ||Psi_a||_inf. Synchronous. BTC_ERR_NOT_SPD when Psi or S is not positive
+ * definite (for S the message names its column). */
+int btc_arrow_factor(btc_arrow_t a, const double *D, const double *B, const double *C, const double *A, double tol,
+                     int maxit);
+
+/* Solve Psi_a x = b (one right-hand side) with FP64 refinement of the whole
+ * bordered system until ||b - Psi_a x||_inf <= tol ||Psi_a||_inf ||x||_inf:
+ * x = [z - Z x_A; x_A] with z = Psi^{-1} b_T and x_A = S^{-1} (b_A - C z).
+ * *iters: correction passes taken; *relres: final relative residual (each may
+ * be NULL). Synchronous. BTC_ERR_NOT_CONVERGED when maxit passes did not reach
+ * tol (x holds the last iterate). */
+int btc_arrow_solve(btc_arrow_t a, const double *b, double *x, double tol, int maxit, int *iters, double *relres);
+
+/* Release the bordered plan (synchronizes its stream). */
+int btc_arrow_free(btc_arrow_t a);
+
+/* ---------------------------------------------------------------- block-banded systems
+ * Psi with Nb block rows of size b and lower block bandwidth w >= 1:
+ * Psi(i+k, i) = A_k[i] for k = 0..w, zero for k > w (w = 1 is the
+ * block-tridiagonal case). The paper's conclusion names block-banded matrices
+ * with larger bandwidth as the extension of its method. Grouping w
+ * consecutive block rows into one super-row gives a block-tridiagonal matrix
+ * of N = ceil(Nb / w) blocks of size n = w b,
+ *     D'_I(p, q) = Psi(Iw + p, Iw + q),   B'_I(p, q) = Psi((I+1)w + p, Iw + q),
+ * equal to Psi, so the multi-stage permutation of Sec. 4.3 (whose separators
+ * are then w consecutive block rows) and every path of the plan apply to it
+ * unchanged; a ragged last super-row is padded with identity blocks. n = w b
+ * must be a block size the dtype supports (btc_describe).
+ * Layouts: A [w+1][Nb][b][b] row-major FP64, A[k][i] = Psi(i+k, i) (blocks
+ * with i + k >= Nb are not read; of A_0 only the lower triangles are read);
+ * rhs, x [Nb*b][nrhs] row-major FP64. Every pointer is a device pointer; the
+ * grouped blocks are plan-owned copies, so A may change after a factor.
+ */
+typedef struct btc_banded_s *btc_banded_t;
+
+/* Plan a banded system; dtype BTC_F64 or a BTC_MIXED_* dtype (FP64 inputs).
+ * Errors: BTC_ERR_ARG, BTC_ERR_UNSUPPORTED (w b above the dtype's largest
+ * block), BTC_ERR_OOM, BTC_ERR_CUDA. */
+int btc_banded_plan(btc_banded_t *out, int Nb, int b, int w, int dtype, void *stream);
+
+/* The inner block-tridiagonal plan (N super-rows of size w b), for its
+ * settings (order, schedule, autotuning, timing) and inspection; owned by the
+ * banded plan. NULL for a NULL handle. */
+btc_plan_t btc_banded_inner(btc_banded_t a);
+
+/* Copy the grouped blocks of the last factor call, D' [N][n][n] and
+ * B' [N-1][n][n], into caller memory (host or device), and report N, n (each
+ * output may be NULL). Synchronous. */
+int btc_banded_grouped(btc_banded_t a, double *D, double *B, int *N, int *n);
+
+/* Group the band on the device and factor it (Alg. 5). Synchronous.
+ * BTC_ERR_NOT_SPD names the failing block row (of Psi) and column. */
+int btc_banded_factor(btc_banded_t a, const double *A);
+
+/* FP64-refined solve with the last factor (btc_solve_refined on the grouped
+ * system: tol, maxit, *iters, *relres as there, the relative residual of the
+ * grouped system). Synchronous. */
+int btc_banded_solve_refined(btc_banded_t a, const double *rhs, double *x, int nrhs, double tol, int maxit,
+                             int *iters, double *relres);
+
+/* Group, factor and solve with FP64 refinement in one call
+ * (btc_factor_solve_refined on the grouped system). Synchronous. */
+int btc_banded_factor_solve_refined(btc_banded_t a, const double *A, const double *rhs, double *x, int nrhs,
+                                    double tol, int maxit, int *iters, double *relres);
+
+/* Release the banded plan and its inner plan (synchronizes its stream). */
+int btc_banded_free(btc_banded_t a);
+
 /* ---------------------------------------------------------------- serving
  * A continuous-batching request server (no paper counterpart beyond the
  * real-time setting of Sec. 1). Requests enter a FIFO queue; `slots` worker
@@ -580,6 +732,8 @@ typedef struct btc_server_stats_s {
   double p50_us, p99_us, mean_us; /* latency = completion - submission                         */
   double solves_per_s;            /* completed / (last completion - first submission)          */
   int64_t device_bytes;           /* plans in flight, cached and idle                          */
+  double p50_queue_us, p99_queue_us;     /* submission -> a slot takes the request              */
+  double p50_service_us, p99_service_us; /* a slot takes the request -> completion              */
 } btc_server_stats_t;
 
 /* Start a server. dtype: BTC_F64 or a BTC_MIXED_* dtype. slots: 1..64 concurrent
@@ -598,6 +752,10 @@ int btc_server_poll(btc_server_t s, int64_t ticket, int wait, int *status, int *
                     double *latency_us);
 
 int btc_server_stats(btc_server_t s, btc_server_stats_t *st);
+
+/* Restart the statistics of btc_server_stats (counters, latencies, the throughput window); requests in
+ * flight are counted when they complete. */
+int btc_server_reset_stats(btc_server_t s);
 
 /*
  * Device bytes that a request of size (N, n) reserves in a server of this

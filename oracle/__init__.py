@@ -64,6 +64,17 @@ def _bind(lib):
     lib.orc_bs_reconstruct.restype = ctypes.c_double
     lib.orc_resid.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
     lib.orc_resid.restype = None
+    if hasattr(lib, "orc_arrow_assemble"):  # absent from planted-mistake variants of older source text
+        lib.orc_arrow_assemble.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+        lib.orc_arrow_assemble.restype = None
+        lib.orc_arrow_resid.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
+                                        _dp]
+        lib.orc_arrow_resid.restype = None
+    if hasattr(lib, "orc_band_assemble"):
+        lib.orc_band_assemble.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        lib.orc_band_assemble.restype = None
+        lib.orc_band_resid.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        lib.orc_band_resid.restype = None
     return lib
 
 
@@ -273,3 +284,151 @@ def logdet_from_diag(Ldiag):
     """log det Psi = 2 sum log diag(L)."""
     d = np.diagonal(np.asarray(Ldiag), axis1=-2, axis2=-1)
     return float(2.0 * np.log(d).sum())
+
+
+# ---------------------------------------------------------------- arrow (bordered) systems
+# Psi_a = [[Psi, C^T], [C, A]]: the block-tridiagonal Psi bordered by m dense coupling rows C
+# [m, N n] and a dense block A [m, m] (lower triangle read). Vectors have N n + m entries.
+
+def arrow_assemble(D, B, C, A):
+    """Dense bordered matrix of size N n + m."""
+    D, B, C, A = _f64(D), _f64(B), _f64(C), _f64(A)
+    N, n, m = D.shape[0], D.shape[1], C.shape[0]
+    M = N * n + m
+    out = np.zeros((M, M))
+    _load().orc_arrow_assemble(N, n, m, _p(D), _p(B) if B.size else _p(np.zeros(1)), _p(C), _p(A), _p(out))
+    return out
+
+
+def arrow_solve(D, B, C, A, b):
+    """x = Psi_a^{-1} b by Gaussian elimination with partial pivoting on the assembled matrix (the plain
+    definition; small inputs)."""
+    return gepp_solve(arrow_assemble(D, B, C, A), b)
+
+
+def arrow_resid(D, B, C, A, x, b):
+    """(||b - Psi_a x||_inf, ||Psi_a||_inf, ||x||_inf) for one right-hand side, without assembling."""
+    D, B, C, A = _f64(D), _f64(B), _f64(C), _f64(A)
+    N, n, m = D.shape[0], D.shape[1], C.shape[0]
+    out = np.zeros(3)
+    _load().orc_arrow_resid(N, n, m, _p(D), _p(B) if B.size else _p(np.zeros(1)), _p(C), _p(A),
+                            _p(_f64(x).reshape(-1)), _p(_f64(b).reshape(-1)), _p(out))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def arrow_relres(D, B, C, A, x, b):
+    r, a, xn = arrow_resid(D, B, C, A, x, b)
+    return r / (a * xn) if a * xn > 0 else r
+
+
+# ---------------------------------------------------------------- block-banded systems (conclusion)
+def band_assemble(A):
+    """Dense block-banded Psi from A [w+1, Nb, b, b], A[k, i] = Psi(i+k, i)."""
+    A = _f64(A)
+    w, Nb, b = A.shape[0] - 1, A.shape[1], A.shape[2]
+    out = np.zeros((Nb * b, Nb * b))
+    _load().orc_band_assemble(Nb, b, w, _p(A), _p(out))
+    return out
+
+
+def band_resid(A, x, rhs):
+    """(||rhs - Psi x||_inf, ||Psi||_inf, ||x||_inf) for the block-banded Psi, maxima over columns."""
+    A = _f64(A)
+    w, Nb, b = A.shape[0] - 1, A.shape[1], A.shape[2]
+    x = _f64(x).reshape(Nb * b, -1)
+    rhs = _f64(rhs).reshape(Nb * b, -1)
+    out = np.zeros(3)
+    _load().orc_band_resid(Nb, b, w, x.shape[1], _p(A), _p(x), _p(rhs), _p(out))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def band_relres(A, x, rhs):
+    r, a, xn = band_resid(A, x, rhs)
+    return r / (a * xn) if a * xn > 0 else r
+
+
+def band_solve(A, rhs):
+    """x = Psi^{-1} rhs by the dense Cholesky of the assembled band (the plain definition; small inputs)."""
+    M = band_assemble(A)
+    L = dense_chol(M)
+    y = np.linalg.solve(L, _f64(rhs).reshape(M.shape[0], -1))
+    return np.linalg.solve(L.T, y)
+
+
+def band_group(A, w):
+    """The block-tridiagonal view of a block-banded Psi: w consecutive block rows per super-row,
+    D'_I(p, q) = Psi(Iw + p, Iw + q), B'_I(p, q) = Psi((I+1)w + p, Iw + q); a ragged last super-row is
+    padded with identity blocks. Plain index bookkeeping (no arithmetic) -> (D' [N, wb, wb], B' [N-1, wb, wb])."""
+    A = _f64(A)
+    Nb, b = A.shape[1], A.shape[2]
+    N, n = -(-Nb // w), w * b
+
+    def blk(I, J):  # block (I, J) of Psi, or None outside the band / matrix
+        if I >= Nb or J >= Nb or abs(I - J) > w:
+            return None
+        if I == J:
+            lo = np.tril(A[0, I])
+            return lo + np.tril(lo, -1).T
+        return A[I - J, J] if I > J else A[J - I, I].T
+
+    Dg = np.zeros((N, n, n))
+    Bg = np.zeros((max(N - 1, 0), n, n))
+    for I in range(N):
+        for p in range(w):
+            for q in range(w):
+                v = blk(I * w + p, I * w + q)
+                if v is not None:
+                    Dg[I, p * b:(p + 1) * b, q * b:(q + 1) * b] = v
+                elif p == q:
+                    Dg[I, p * b:(p + 1) * b, q * b:(q + 1) * b] = np.eye(b)
+                if I + 1 < N:
+                    v = blk((I + 1) * w + p, I * w + q)
+                    if v is not None:
+                        Bg[I, p * b:(p + 1) * b, q * b:(q + 1) * b] = v
+    return Dg, Bg
+
+
+# ---------------------------------------------------------------- partition permutation (Sec. 4.1)
+def partition_sizes(N, p):
+    """Chunk sizes (N_1, N_k) of the partition permutation with p chunks and p - 1 pivots (Sec. 4.1,
+    Proposition 1): N_k* = (7N - 7p + 7) / (7p + 12) rounded down and up, N_1 = N - (p - 1)(N_k + 1),
+    keeping the pair whose larger phase cost max((7/3) N_1 - 1, (19/3) N_k - 1) is smaller. Chunks of
+    k > 1 hold at least one node; p = 1 is the sequential order."""
+    if p <= 1:
+        return N, 0
+    best = None
+    nk_star = (7 * N - 7 * p + 7) / (7 * p + 12)
+    for nk in (int(np.floor(nk_star)), int(np.ceil(nk_star))):
+        nk = max(nk, 1)
+        n1 = N - (p - 1) * (nk + 1)
+        if n1 < 1:
+            continue
+        cost = max(7.0 / 3.0 * n1 - 1.0, 19.0 / 3.0 * nk - 1.0)
+        if best is None or cost < best[0]:
+            best = (cost, n1, nk)
+    if best is None:
+        raise ValueError(f"{p} chunks do not fit in N = {N}")
+    return best[1], best[2]
+
+
+def partition_order(N, p):
+    """Elimination order of Psi_p (0-based nodes): the interiors of the p chunks (chunk 1 = nodes
+    0 .. N_1-1; chunk k > 1 = the N_k nodes after pivot A_k), each in ascending order, then the pivots
+    A_2 .. A_p in ascending order (the sequential phase)."""
+    n1, nk = partition_sizes(N, p)
+    chunks = [list(range(n1))]
+    pivots = []
+    v = n1
+    for _ in range(p - 1):
+        pivots.append(v)
+        chunks.append(list(range(v + 1, v + 1 + nk)))
+        v += 1 + nk
+    assert v == N
+    order = [i for c in chunks for i in c] + pivots
+    return np.asarray(order, dtype=np.int32)
+
+
+def partition_factor(D, B, p):
+    """The factor of Psi_p: bs_chol in the partition order."""
+    order = partition_order(D.shape[0], p)
+    return (order,) + bs_chol(D, B, order)

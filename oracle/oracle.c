@@ -29,6 +29,17 @@
  *                       structurally-zero block receives an update.
  *   orc_bs_reconstruct  ||P Psi P^T - L L^T||_F / ||Psi||_F, block-sparse.
  *   orc_resid           ||b - Psi x||_inf, ||Psi||_inf, ||x||_inf.
+ *   orc_arrow_assemble  the dense bordered ("arrow") matrix [[Psi, C^T], [C, A]]
+ *                       of the arrow structures that Sec. 4.3 names as a
+ *                       natural extension of the permuted Cholesky view (and
+ *                       the conclusion as future work); C is m x (N n), A is
+ *                       m x m (lower triangle read).
+ *   orc_arrow_resid     ||b - Psi_a x||_inf, ||Psi_a||_inf, ||x||_inf for it.
+ *   orc_band_assemble   the dense block-banded matrix with lower block
+ *                       bandwidth w, Psi(i+k, i) = A_k[i] (k = 0..w), the
+ *                       wider band the conclusion names as future work.
+ *   orc_band_resid      ||b - Psi x||_inf, ||Psi||_inf, ||x||_inf for it,
+ *                       block by block without assembling.
  *
  * Conventions: blocks are n x n, row-major. D holds N diagonal blocks (only
  * the lower triangle of each is read; the upper triangle is taken to be its
@@ -421,6 +432,143 @@ void orc_resid(int N, int n, int m, const double *D, const double *B, const doub
         if (fabs(v) > rmax) rmax = fabs(v);
         double xv = fabs(x[((size_t)i * n + r) * m + col]);
         if (xv > xmax) xmax = xv;
+      }
+    }
+  out[0] = rmax;
+  out[1] = amax;
+  out[2] = xmax;
+}
+
+/*
+ * Dense bordered matrix of size (N n + m): Psi (orc_assemble) in the leading
+ * block, C (m x N n, row-major) in the last m rows, C^T in the last m columns
+ * and A (lower triangle read, mirrored) in the trailing m x m block.
+ */
+void orc_arrow_assemble(int N, int n, int m, const double *D, const double *B, const double *C, const double *A,
+                        double *out) {
+  const int L = N * n, M = L + m;
+  double *T = (double *)calloc((size_t)L * L, sizeof(double));
+  orc_assemble(N, n, D, B, T);
+  memset(out, 0, sizeof(double) * (size_t)M * M);
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j) out[(size_t)i * M + j] = T[(size_t)i * L + j];
+  for (int r = 0; r < m; ++r)
+    for (int j = 0; j < L; ++j) {
+      out[(size_t)(L + r) * M + j] = C[(size_t)r * L + j];
+      out[(size_t)j * M + L + r] = C[(size_t)r * L + j];
+    }
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c) out[(size_t)(L + r) * M + L + c] = sym_lower(A, m, r, c);
+  free(T);
+}
+
+/*
+ * out[0] = ||b - Psi_a x||_inf, out[1] = ||Psi_a||_inf, out[2] = ||x||_inf for
+ * the bordered matrix, one right-hand side of length N n + m, without forming
+ * it: the block-tridiagonal rows add the coupling columns C^T, the last m rows
+ * are C and A.
+ */
+void orc_arrow_resid(int N, int n, int m, const double *D, const double *B, const double *C, const double *A,
+                     const double *x, const double *b, double *out) {
+  const int L = N * n;
+  size_t bs = (size_t)n * n;
+  double rmax = 0.0, amax = 0.0, xmax = 0.0;
+  for (int i = 0; i < N; ++i)
+    for (int r = 0; r < n; ++r) {
+      const int row = i * n + r;
+      double rowsum = 0.0, v = b[row];
+      for (int c = 0; c < n; ++c) {
+        const double a = sym_lower(D + i * bs, n, r, c);
+        rowsum += fabs(a);
+        v -= a * x[i * n + c];
+      }
+      if (i > 0)
+        for (int c = 0; c < n; ++c) {
+          const double a = B[(i - 1) * bs + r * n + c];
+          rowsum += fabs(a);
+          v -= a * x[(i - 1) * n + c];
+        }
+      if (i + 1 < N)
+        for (int c = 0; c < n; ++c) {
+          const double a = B[i * bs + c * n + r];
+          rowsum += fabs(a);
+          v -= a * x[(i + 1) * n + c];
+        }
+      for (int q = 0; q < m; ++q) {
+        const double a = C[(size_t)q * L + row];
+        rowsum += fabs(a);
+        v -= a * x[L + q];
+      }
+      if (rowsum > amax) amax = rowsum;
+      if (fabs(v) > rmax) rmax = fabs(v);
+      if (fabs(x[row]) > xmax) xmax = fabs(x[row]);
+    }
+  for (int q = 0; q < m; ++q) {
+    double rowsum = 0.0, v = b[L + q];
+    for (int j = 0; j < L; ++j) {
+      rowsum += fabs(C[(size_t)q * L + j]);
+      v -= C[(size_t)q * L + j] * x[j];
+    }
+    for (int c = 0; c < m; ++c) {
+      const double a = sym_lower(A, m, q, c);
+      rowsum += fabs(a);
+      v -= a * x[L + c];
+    }
+    if (rowsum > amax) amax = rowsum;
+    if (fabs(v) > rmax) rmax = fabs(v);
+    if (fabs(x[L + q]) > xmax) xmax = fabs(x[L + q]);
+  }
+  out[0] = rmax;
+  out[1] = amax;
+  out[2] = xmax;
+}
+
+/*
+ * Block-banded Psi: Nb block rows of size b, lower block bandwidth w. The band
+ * is A [w+1][Nb][b][b] with A_k[i] = Psi(i+k, i); blocks with i + k >= Nb are
+ * outside the matrix and not read, and of A_0 only the lower triangles are
+ * read. Element (row, col) of block (I, J) with |I - J| <= w.
+ */
+static double band_elem(int Nb, int b, const double *A, int I, int J, int r, int c) {
+  const size_t bb = (size_t)b * b;
+  if (I == J) return sym_lower(A + (size_t)I * bb, b, r, c);
+  if (I > J) return A[((size_t)(I - J) * Nb + J) * bb + (size_t)r * b + c];
+  return A[((size_t)(J - I) * Nb + I) * bb + (size_t)c * b + r]; /* Psi(I, J) = Psi(J, I)^T */
+}
+
+/* The dense (Nb b) x (Nb b) matrix. */
+void orc_band_assemble(int Nb, int b, int w, const double *A, double *out) {
+  const size_t L = (size_t)Nb * b;
+  for (size_t q = 0; q < L * L; ++q) out[q] = 0.0;
+  for (int I = 0; I < Nb; ++I)
+    for (int J = I - w; J <= I + w; ++J) {
+      if (J < 0 || J >= Nb) continue;
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) out[((size_t)I * b + r) * L + (size_t)J * b + c] = band_elem(Nb, b, A, I, J, r, c);
+    }
+}
+
+/* out = (||b - Psi x||_inf, ||Psi||_inf, ||x||_inf), maxima over the m columns
+ * of x and b ([Nb b][m], row-major). */
+void orc_band_resid(int Nb, int b, int w, int m, const double *A, const double *x, const double *rhs, double *out) {
+  double rmax = 0.0, amax = 0.0, xmax = 0.0;
+  for (int I = 0; I < Nb; ++I)
+    for (int r = 0; r < b; ++r) {
+      const size_t row = (size_t)I * b + r;
+      double rowsum = 0.0;
+      for (int J = I - w; J <= I + w; ++J) {
+        if (J < 0 || J >= Nb) continue;
+        for (int c = 0; c < b; ++c) rowsum += fabs(band_elem(Nb, b, A, I, J, r, c));
+      }
+      if (rowsum > amax) amax = rowsum;
+      for (int q = 0; q < m; ++q) {
+        double v = rhs[row * m + q];
+        for (int J = I - w; J <= I + w; ++J) {
+          if (J < 0 || J >= Nb) continue;
+          for (int c = 0; c < b; ++c) v -= band_elem(Nb, b, A, I, J, r, c) * x[((size_t)J * b + c) * m + q];
+        }
+        if (fabs(v) > rmax) rmax = fabs(v);
+        if (fabs(x[row * m + q]) > xmax) xmax = fabs(x[row * m + q]);
       }
     }
   out[0] = rmax;

@@ -45,10 +45,14 @@ class btc_plan_info(ctypes.Structure):
 
 
 _vp, _ip, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+_lp = ctypes.POINTER(ctypes.c_int64)
 
 _SIGS = {
     "btc_describe": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(btc_plan_info)],
     "btc_schedule": [ctypes.c_int, _ip, _ip],
+    "btc_schedule_items": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _lp, _ip, _lp, _ip, _ip, _ip],
+    "btc_describe_order": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(btc_plan_info), _ip, _ip],
     "btc_plan": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
     "btc_plan_query": [_vp, ctypes.POINTER(btc_plan_info)],
     "btc_plan_set_schedule": [_vp, ctypes.c_int],
@@ -78,6 +82,7 @@ _SIGS = {
     "btc_solve_gmres_ir": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip, _ip,
                            _dp],
     "btc_plan_set_root_precision": [_vp, ctypes.c_int],
+    "btc_plan_set_order": [_vp, ctypes.c_int, ctypes.c_int],
     "btc_plan_inject_stall": [_vp, ctypes.c_int, ctypes.c_int64],
     "btc_plan_set_phase_trace": [_vp, _vp],
     "btc_server_start": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int],
@@ -86,6 +91,7 @@ _SIGS = {
     "btc_server_stats": [_vp, _vp],
     "btc_server_stop": [_vp],
     "btc_server_prewarm": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "btc_server_reset_stats": [_vp],
     "btc_server_footprint": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "btc_batch_plan": [ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, ctypes.c_int, _vp],
     "btc_batch_query": [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)],
@@ -100,6 +106,17 @@ _SIGS = {
     "btc_batch_set_autotune": [_vp, ctypes.c_int],
     "btc_batch_set_graphs": [_vp, ctypes.c_int],
     "btc_batch_tuning": [_vp, ctypes.c_int, _ip, _ip, _ip, _ip, _dp],
+    "btc_arrow_plan": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+    "btc_arrow_factor": [_vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int],
+    "btc_arrow_solve": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _ip, _dp],
+    "btc_arrow_free": [_vp],
+    "btc_banded_plan": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+    "btc_banded_inner": [_vp],
+    "btc_banded_grouped": [_vp, _vp, _vp, _ip, _ip],
+    "btc_banded_factor": [_vp, _vp],
+    "btc_banded_solve_refined": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
+    "btc_banded_factor_solve_refined": [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp],
+    "btc_banded_free": [_vp],
     "btc_last_error": [],
     "btc_version": [],
 }
@@ -128,6 +145,7 @@ def load():
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
             lib.btc_last_error.restype = ctypes.c_char_p
+            lib.btc_banded_inner.restype = ctypes.c_void_p
             _lib = lib
     return _lib
 
@@ -173,6 +191,32 @@ def btc_schedule(N):
     levels = np.zeros(N, dtype=np.int32)
     _check(load().btc_schedule(N, order.ctypes.data_as(_ip), levels.ctypes.data_as(_ip)))
     return order, levels
+
+
+def btc_describe_order(N, n, dtype=F64, order=0, chunks=1):
+    """Host-only planner for either elimination order: (info dict, order, launch levels)."""
+    info = btc_plan_info()
+    o = np.zeros(N, dtype=np.int32)
+    lv = np.zeros(N, dtype=np.int32)
+    _check(load().btc_describe_order(N, n, dtype, order, chunks, ctypes.byref(info), o.ctypes.data_as(_ip),
+                                     lv.ctypes.data_as(_ip)))
+    return info.as_dict(), o, lv
+
+
+def btc_schedule_items(N, order=0, chunks=1):
+    """Host-only: (factor rows [F,14], solve rows [S,10], slot rows [K,3]) of a plan's work items, offsets
+    in blocks."""
+    L = load()
+    nf, ns, nk = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(L.btc_schedule_items(N, order, chunks, None, ctypes.byref(nf), None, ctypes.byref(ns), None,
+                                ctypes.byref(nk)))
+    fr = np.zeros((max(nf.value, 1), 14), dtype=np.int64)
+    sr = np.zeros((max(ns.value, 1), 10), dtype=np.int64)
+    kr = np.zeros((max(nk.value, 1), 3), dtype=np.int32)
+    _check(L.btc_schedule_items(N, order, chunks, fr.ctypes.data_as(_lp), ctypes.byref(nf),
+                                sr.ctypes.data_as(_lp), ctypes.byref(ns), kr.ctypes.data_as(_ip),
+                                ctypes.byref(nk)))
+    return fr[:nf.value], sr[:ns.value], kr[:nk.value]
 
 
 class Plan:
@@ -486,6 +530,15 @@ def btc_plan_set_root_precision(plan, precision):
     return _check(load().btc_plan_set_root_precision(plan.h, precision))
 
 
+ORDER_ND, ORDER_PARTITION = 0, 1
+
+
+def btc_plan_set_order(plan, order, chunks=1):
+    """Elimination order: ORDER_ND (nested dissection, default) or ORDER_PARTITION with `chunks`
+    chunks (Sec. 4.1, Alg. 4; chunks=1 is the natural order). Rebuilds the plan's schedules."""
+    return _check(load().btc_plan_set_order(plan.h, order, chunks))
+
+
 def btc_plan_inject_stall(plan, item, max_polls=4096):
     """Test hook: factor item `item` waits on a flag nothing sets, every wait gives up after max_polls
     polls (item=-1 restores the plan)."""
@@ -509,7 +562,9 @@ class btc_server_stats_t(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("cache_hits", ctypes.c_int64), ("cache_misses", ctypes.c_int64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("solves_per_s", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("solves_per_s", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("p50_queue_us", ctypes.c_double), ("p99_queue_us", ctypes.c_double),
+                ("p50_service_us", ctypes.c_double), ("p99_service_us", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -578,6 +633,119 @@ def btc_server_footprint(dtype, N, n):
     return b.value
 
 
+def btc_server_reset_stats(server):
+    return _check(load().btc_server_reset_stats(server.h))
+
+
 def btc_server_stop(server):
     server.stop()
+    return OK
+
+
+class Arrow:
+    """Owning handle of a btc_arrow_t (a bordered block-tridiagonal system)."""
+
+    def __init__(self, N, n, m, dtype=MIXED_F32, stream=None):
+        h = _vp()
+        _check(load().btc_arrow_plan(ctypes.byref(h), N, n, m, dtype, _stream(stream)))
+        self.h = h
+        self.N, self.n, self.m, self.dtype = N, n, m, dtype
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().btc_arrow_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def btc_arrow_plan(N, n, m, dtype=MIXED_F32, stream=None):
+    return Arrow(N, n, m, dtype, stream)
+
+
+def btc_arrow_factor(arrow, D, B, C, A, tol=1e-12, maxit=30):
+    return _check(load().btc_arrow_factor(arrow.h, _ptr(D), _ptr(B), _ptr(C), _ptr(A), tol, maxit))
+
+
+def btc_arrow_solve(arrow, b, x, tol=1e-10, maxit=10, allow_not_converged=False):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    rc = _check(load().btc_arrow_solve(arrow.h, _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it), ctypes.byref(rel)),
+                allow)
+    return it.value, rel.value, rc
+
+
+def btc_arrow_free(arrow):
+    arrow.free()
+    return OK
+
+
+class Banded:
+    """Owning handle of a btc_banded_t (a block-banded system: Nb block rows of size b, lower block
+    bandwidth w, solved as a block-tridiagonal system of w-row super-rows)."""
+
+    def __init__(self, Nb, b, w, dtype=MIXED_F32, stream=None):
+        h = _vp()
+        _check(load().btc_banded_plan(ctypes.byref(h), Nb, b, w, dtype, _stream(stream)))
+        self.h = h
+        self.Nb, self.b, self.w, self.dtype = Nb, b, w, dtype
+        self.N, self.n = -(-Nb // w), w * b
+        inner = load().btc_banded_inner(h)
+        self.inner = Plan.__new__(Plan)  # a view of the owned inner plan (never freed through it)
+        self.inner.h, self.inner.N, self.inner.n, self.inner.dtype = _vp(inner), self.N, self.n, dtype
+        self.inner.free = lambda: None
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().btc_banded_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def btc_banded_plan(Nb, b, w, dtype=MIXED_F32, stream=None):
+    return Banded(Nb, b, w, dtype, stream)
+
+
+def btc_banded_factor(band, A):
+    return _check(load().btc_banded_factor(band.h, _ptr(A)), (ERR_NOT_SPD,))
+
+
+def btc_banded_solve_refined(band, rhs, x, nrhs, tol=1e-10, maxit=20, allow_not_converged=False):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    rc = _check(load().btc_banded_solve_refined(band.h, _ptr(rhs), _ptr(x), nrhs, tol, maxit, ctypes.byref(it),
+                                                ctypes.byref(rel)), allow)
+    return it.value, rel.value, rc
+
+
+def btc_banded_factor_solve_refined(band, A, rhs, x, nrhs, tol=1e-10, maxit=20, allow_not_converged=False):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    rc = _check(load().btc_banded_factor_solve_refined(band.h, _ptr(A), _ptr(rhs), _ptr(x), nrhs, tol, maxit,
+                                                       ctypes.byref(it), ctypes.byref(rel)), allow)
+    return it.value, rel.value, rc
+
+
+def btc_banded_grouped(band):
+    """Host copies (D' [N, n, n], B' [N-1, n, n]) of the grouped blocks of the last factor call."""
+    D = np.zeros((band.N, band.n, band.n))
+    B = np.zeros((max(band.N - 1, 0), band.n, band.n))
+    _check(load().btc_banded_grouped(band.h, D.ctypes.data, B.ctypes.data if B.size else None, None, None))
+    return D, B
+
+
+def btc_banded_free(band):
+    band.free()
     return OK

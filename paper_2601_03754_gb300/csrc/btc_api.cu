@@ -193,6 +193,9 @@ struct btc_plan_s {
   TileTask *d_tiles = nullptr;
   int *d_tile_cnt = nullptr;
   int n_tiles = 0, tile_grid = 0;
+  // partition orders (btc_plan_set_order): orientation of the original coupling slots for the packing pass
+  int8_t *d_orient = nullptr;
+  int64_t fixed_bytes = 0;  // device bytes that do not depend on the elimination order
   double *kry = nullptr;  // GMRES-IR workspace: basis, work and zero vectors, device scalars
   size_t kry_cap = 0;     // its size in doubles
   // optional per-kernel-class event timing (btc_plan_set_timing)
@@ -287,7 +290,7 @@ static int run_solve(btc_plan_s *p, int m) {
   a.y = p->d_y;
   a.m = m;
   KernelTimer timer(p, BTC_TIME_SOLVE);
-  if (p->sched == BTC_SCHED_FLOW) {
+  if (p->sched == BTC_SCHED_FLOW || p->hp.packed) {  // partition orders have no per-level solve lists
     BTC_CUDA(cudaMemsetAsync(p->d_flow + 1, 0, sizeof(int), p->stream));
     BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_solve, p->stream));
     a.items = p->d_solve_flow;
@@ -390,8 +393,9 @@ static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B);
 // arithmetic does not depend on the configuration, only the schedule does) and
 // keeps the fastest median of three; remembered per shape for the process.
 static int autotune_flow(btc_plan_s *p, const void *D, const void *B) {
+  // (the elimination order is part of the shape: chunks = 0 for nested dissection)
   const int alg = p->variant == BTC_VARIANT_RIGHT_LOOKING ? 1 : 0;
-  const auto key = std::make_tuple(p->dtype, p->np, p->N, alg);
+  const auto key = std::make_tuple(p->dtype, p->np, p->N, alg + 8 * p->hp.chunks);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -464,7 +468,10 @@ static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
   const InstDesc d = inst_desc(p, D, B);
   int rc = BTC_OK;
   const bool rl = p->variant == BTC_VARIANT_RIGHT_LOOKING;
-  if (rl && (rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n))) return rc;
+  const int8_t *orient = p->d_orient;
+  if ((rl || p->hp.packed) &&
+      (rc = k.pack_pools(p->dpool, p->epool, D, B, p->N, p->n, orient, p->stream)))
+    return rc;
   BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   if (nflow == 0) return BTC_OK;
   BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
@@ -476,7 +483,7 @@ static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
     return launch_n(fv.fac_rl, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps, zero,
                     flow_sync(p, 0));
   }
-  const int nfirst = (int)p->fac_off[1];
+  const int nfirst = p->hp.packed ? 0 : (int)p->fac_off[1];  // items that read the caller's arrays
   const int32_t *deps = p->d_fac_deps;
   return launch_n(fv.fac, std::min(p->fac_grid, nflow), k.fac_threads, k.fac_smem, p->stream, a, d, deps, nfirst,
                   flow_sync(p, 0));
@@ -599,7 +606,7 @@ static int tiled_factor(btc_plan_s *p, const void *D, const void *B) {
   BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
   BTC_CUDA(cudaMemsetAsync(p->d_tile_cnt, 0, sizeof(int) * (size_t)p->n_fac, p->stream));
-  if ((rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n))) return rc;
+  if ((rc = k.pack_pools(p->dpool, p->epool, D, B, p->N, p->n, nullptr, p->stream))) return rc;
   TileArgs a;
   a.tasks = p->d_tiles;
   a.count = p->n_tiles;
@@ -653,14 +660,17 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
     }
     if (rc) return rc;
   } else {
-    // one launch per level (Alg. 5 or Alg. 6 level loops)
+    // one launch per level (Alg. 5 or Alg. 6 level loops; the positions of a partition order)
     BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
-    if (rl && (rc = launch_n(k.pack_matrix, p->N, 256, 0, p->stream, p->dpool, p->epool, D, B, p->N, p->n))) return rc;
+    const int8_t *orient = p->d_orient;
+    if ((rl || p->hp.packed) &&
+        (rc = k.pack_pools(p->dpool, p->epool, D, B, p->N, p->n, orient, p->stream)))
+      return rc;
     KernelTimer timer(p, BTC_TIME_FACTOR);
     for (int l = 0; l < p->hp.levels - (mixed_root ? 1 : 0); ++l) {
       a.items = p->d_fac + p->fac_off[l];
       a.count = (int)(p->fac_off[l + 1] - p->fac_off[l]);
-      const void *fn = rl ? k.fac_rl : (l == 0 ? k.fac_first : k.fac_rest);
+      const void *fn = rl ? k.fac_rl : (l == 0 && !p->hp.packed ? k.fac_first : k.fac_rest);
       if ((rc = launch_n(fn, a.count, k.fac_threads, k.fac_smem, p->stream, a, d))) return rc;
     }
   }
@@ -669,7 +679,8 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
     a.count = 1;
     const bool f64 = p->root_prec == BTC_ROOT_FP64;
     const void *fn = rl ? (f64 ? k.root64_rl : k.root_rl)
-                        : (last == 0 ? (f64 ? k.root64_first : k.root_first) : (f64 ? k.root64_rest : k.root_rest));
+                        : (last == 0 && !p->hp.packed ? (f64 ? k.root64_first : k.root_first)
+                                                        : (f64 ? k.root64_rest : k.root_rest));
     KernelTimer timer(p, BTC_TIME_ROOT);
     if ((rc = launch_n(fn, 1, k.root_threads, k.root_smem, p->stream, a, d))) return rc;
   }
@@ -856,7 +867,8 @@ static int run_solve_tail(btc_plan_s *p, int m) {
 // The interlaced form needs the hybrid variant, the persistent schedule and
 // right-hand sides that fit in one pass.
 static bool can_interlace(const btc_plan_s *p, int m) {
-  return p->variant == BTC_VARIANT_HYBRID && p->sched == BTC_SCHED_FLOW && p->ks->fac_fwd_flow && m >= 1 &&
+  return p->variant == BTC_VARIANT_HYBRID && p->sched == BTC_SCHED_FLOW && p->ks->fac_fwd_flow && !p->hp.packed &&
+         m >= 1 &&
          m <= std::min(kMaxCols, p->ks->max_cols);
 }
 
@@ -1108,6 +1120,76 @@ int btc_schedule(int N, int *order_out, int *levels_out) {
   return t == N ? BTC_OK : fail(BTC_ERR_ARG, "schedule covers %d of %d nodes", t, N);
 }
 
+int btc_describe_order(int N, int n, int dtype, int order, int chunks, btc_plan_info *info, int *order_out,
+                       int *levels_out) {
+  if (N < 1 || n < 1 || (order != BTC_ORDER_ND && order != BTC_ORDER_PARTITION) ||
+      (order == BTC_ORDER_PARTITION && chunks < 1))
+    return fail(BTC_ERR_ARG, "btc_describe_order: invalid arguments");
+  if (!dtype_ok(dtype)) return fail(BTC_ERR_ARG, "btc_describe_order: unknown dtype %d", dtype);
+  const int np = padded_size(n, dtype);
+  if (!np) return fail(BTC_ERR_UNSUPPORTED, "block size %d exceeds the largest compiled size", n);
+  if (order == BTC_ORDER_PARTITION && np > kTileT)
+    return fail(BTC_ERR_UNSUPPORTED, "btc_describe_order: blocked 256 plans use the ND order only");
+  HostPlan hp;
+  if (order == BTC_ORDER_ND) build_host_plan(N, n, np, 0, 0, 0, 0, &hp);
+  else if (!build_partition_plan(N, n, np, chunks, 0, 0, 0, 0, &hp))
+    return fail(BTC_ERR_ARG, "btc_describe_order: %d chunks do not fit in N = %d", chunks, N);
+  if (info) {
+    fill_info(hp, dtype, info);
+    const double pe = dtype == BTC_F64 ? 8.0 : 4.0;
+    info->device_bytes = (int64_t)(pe * (double)np * np * (N + std::max<int64_t>(hp.offdiag, 1)) +
+                                   pe * (double)N * np * kMaxCols);
+  }
+  int t = 0;
+  for (int l = 0; l < hp.levels; ++l)
+    for (const FactorItem &it : hp.lv[l].fac) {
+      if (order_out) order_out[t] = it.node;
+      if (levels_out) levels_out[t] = l + 1;
+      ++t;
+    }
+  return t == N ? BTC_OK : fail(BTC_ERR_ARG, "schedule covers %d of %d nodes", t, N);
+}
+
+int btc_schedule_items(int N, int order, int chunks, int64_t *fac_rows, int *n_fac, int64_t *solve_rows,
+                       int *n_solve, int *slot_rows, int *n_slots) {
+  if (N < 1 || !n_fac || !n_solve || !n_slots || (order != BTC_ORDER_ND && order != BTC_ORDER_PARTITION))
+    return fail(BTC_ERR_ARG, "btc_schedule_items: invalid arguments");
+  HostPlan hp;
+  if (order == BTC_ORDER_ND) build_host_plan(N, 1, 1, 0, 0, 0, 0, &hp);
+  else if (chunks < 1 || !build_partition_plan(N, 1, 1, chunks, 0, 0, 0, 0, &hp))
+    return fail(BTC_ERR_ARG, "btc_schedule_items: %d chunks do not fit in N = %d", chunks, N);
+  int t = 0;
+  for (int l = 0; l < hp.levels; ++l)
+    for (const FactorItem &it : hp.lv[l].fac) {
+      if (fac_rows && t < *n_fac) {
+        const int64_t row[14] = {l + 1,   it.d_self, it.d_next, it.r_up,   it.r_down,           it.p_a,
+                                 it.p_b,  it.fill,   it.d_prev, it.node,   it.flags,            hp.fac_deps[3 * t],
+                                 hp.fac_deps[3 * t + 1], hp.fac_deps[3 * t + 2]};
+        std::copy(row, row + 14, fac_rows + 14 * (size_t)t);
+      }
+      ++t;
+    }
+  *n_fac = t;
+  const int ns = (int)hp.solve_flow.size();
+  if (solve_rows)
+    for (int q = 0; q < std::min(ns, *n_solve); ++q) {
+      const SolveFlowItem &it = hp.solve_flow[q];
+      const int64_t row[10] = {it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, it.kind,
+                               it.dep[0], it.dep[1], it.dep[2]};
+      std::copy(row, row + 10, solve_rows + 10 * (size_t)q);
+    }
+  *n_solve = ns;
+  const int nsl = (int)hp.offdiag;
+  if (slot_rows)
+    for (int q = 0; q < std::min(nsl, *n_slots); ++q) {
+      slot_rows[3 * q] = hp.slot_e[q];
+      slot_rows[3 * q + 1] = hp.slot_o[q];
+      slot_rows[3 * q + 2] = q + 1 < N ? (hp.packed ? hp.slot_transposed[q] : ((q + 1) & 1)) : -1;
+    }
+  *n_slots = nsl;
+  return BTC_OK;
+}
+
 int btc_schedule_interlaced(int N, int root_separate, int *kind, int *node, int *level, int *deps, int *count,
                             int *tail_count) {
   if (N < 1 || !count) return fail(BTC_ERR_ARG, "btc_schedule_interlaced: invalid arguments");
@@ -1136,47 +1218,31 @@ int btc_schedule_interlaced(int N, int root_separate, int *kind, int *node, int 
   return BTC_OK;
 }
 
-int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
-  if (!out || N < 1 || n < 1) return fail(BTC_ERR_ARG, "btc_plan: invalid arguments (N=%d, n=%d)", N, n);
-  *out = nullptr;
-  if (!dtype_ok(dtype)) return fail(BTC_ERR_ARG, "btc_plan: unknown dtype %d", dtype);
-  int np = padded_size(n, dtype);
-  if (!np) return fail(BTC_ERR_UNSUPPORTED, "block size %d exceeds the largest compiled size", n);
-  const KernelSet &ks = kernels_for(dtype, np);
-  if (!ks.valid) return fail(BTC_ERR_UNSUPPORTED, "no kernels for dtype %d, np %d", dtype, np);
-  btc_plan_s *p = new btc_plan_s();
-  p->N = N;
-  p->n = n;
-  p->np = np;
-  p->dtype = dtype;
-  p->stream = (cudaStream_t)stream;
-  p->ks = &ks;
-  build_host_plan(N, n, np, 0, 0, 0, 0, &p->hp);
-  int rc = BTC_OK;
-  auto cleanup = [&](int code) {
-    btc_free(p);
-    return code;
-  };
+// Device state that depends on the plan's elimination order (p->hp): the off-diagonal pool, the
+// per-level and persistent schedules, the interlaced schedule, the tile tasks, the flags, the packing
+// orientation, and the launch configurations. Called by btc_plan and again by btc_plan_set_order.
+static int plan_schedule(btc_plan_s *p) {
+  const KernelSet &ks = *p->ks;
+  const int N = p->N, n = p->n, np = p->np;
   const size_t bs = (size_t)np * np * ks.elem;
-  size_t dbytes = bs * N, ebytes = bs * std::max<int64_t>(p->hp.offdiag, 1);
+  const size_t ebytes = bs * std::max<int64_t>(p->hp.offdiag, 1);
+  int rc = BTC_OK;
   cudaError_t e;
-  if ((e = cudaMalloc(&p->dpool, dbytes)) != cudaSuccess ||
-      (e = cudaMalloc(&p->epool, ebytes)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_y, (size_t)N * np * kMaxCols * ks.elem)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_rb, sizeof(Readback))) != cudaSuccess ||
-      (e = cudaMallocHost(&p->h_rb, sizeof(Readback))) != cudaSuccess)
-    return cleanup(fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
-                        cudaGetErrorString(e)));
-  p->d_norms = p->d_rb->norms;
-  p->d_info = &p->d_rb->info;
-  p->d_status = &p->d_rb->status;
-  p->h_norms = p->h_rb->norms;
-  p->h_info = &p->h_rb->info;
-  p->h_status = &p->h_rb->status;
-  if ((e = cudaMemset(p->d_rb, 0, sizeof(Readback))) != cudaSuccess)
-    return cleanup(fail(BTC_ERR_CUDA, "btc_plan: %s", cudaGetErrorString(e)));
-  p->device_bytes = (int64_t)(dbytes + ebytes + (size_t)N * np * kMaxCols * ks.elem);
+  auto cleanup = [](int code) { return code; };
+  if ((e = cudaMalloc(&p->epool, ebytes)) != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
+                cudaGetErrorString(e));
+  p->device_bytes = p->fixed_bytes + (int64_t)ebytes;
+  if (p->hp.packed && N > 1) {
+    if ((e = cudaMalloc(&p->d_orient, p->hp.slot_transposed.size())) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_orient, p->hp.slot_transposed.data(), p->hp.slot_transposed.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(BTC_ERR_CUDA, "btc_plan: orientation upload: %s", cudaGetErrorString(e));
+  }
   // flatten the per-level schedules and upload them
+  p->fac_off.clear();
+  p->fwd_off.clear();
+  p->bwd_off.clear();
   std::vector<FactorItem> fac;
   std::vector<FwdItem> fwd;
   std::vector<BwdItem> bwd;
@@ -1207,7 +1273,7 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   p->n_solve = (int)p->hp.solve_flow.size();
   std::vector<int32_t> icode, ideps;
   std::vector<SolveFlowItem> tail;
-  build_interlaced(p->hp, dtype_mixed(dtype), &icode, &ideps, &tail);
+  if (!p->hp.packed) build_interlaced(p->hp, dtype_mixed(p->dtype), &icode, &ideps, &tail);
   p->n_inter = (int)icode.size();
   p->n_tail = (int)tail.size();
   if ((e = cudaMalloc(&p->d_inter_code, std::max<size_t>(icode.size(), 1) * sizeof(int32_t))) != cudaSuccess ||
@@ -1301,6 +1367,75 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
     p->solve_grid = std::max(1, bs_ * sms);
     apply_flow_config(p, ks.flow_default, 0);
   }
+  return BTC_OK;
+}
+
+// Release what plan_schedule allocated (before a new elimination order is planned).
+static void plan_unschedule(btc_plan_s *p) {
+  if (p->stream || p->dpool) cudaStreamSynchronize(p->stream);
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  void *dev[] = {p->epool,        p->d_fac,        p->d_fwd,      p->d_bwd,     p->d_fac_deps, p->d_fac_deps_rl,
+                 p->d_solve_flow, p->d_flow,       p->d_inter_code, p->d_inter_deps, p->d_tail, p->d_tiles,
+                 p->d_tile_cnt,   p->d_orient};
+  for (void *q : dev)
+    if (q) cudaFree(q);
+  p->epool = nullptr;
+  p->d_fac = nullptr;
+  p->d_fwd = nullptr;
+  p->d_bwd = nullptr;
+  p->d_fac_deps = p->d_fac_deps_rl = nullptr;
+  p->d_solve_flow = nullptr;
+  p->d_flow = nullptr;
+  p->d_inter_code = p->d_inter_deps = nullptr;
+  p->d_tail = nullptr;
+  p->d_tiles = nullptr;
+  p->d_tile_cnt = nullptr;
+  p->d_orient = nullptr;
+}
+
+int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
+  if (!out || N < 1 || n < 1) return fail(BTC_ERR_ARG, "btc_plan: invalid arguments (N=%d, n=%d)", N, n);
+  *out = nullptr;
+  if (!dtype_ok(dtype)) return fail(BTC_ERR_ARG, "btc_plan: unknown dtype %d", dtype);
+  int np = padded_size(n, dtype);
+  if (!np) return fail(BTC_ERR_UNSUPPORTED, "block size %d exceeds the largest compiled size", n);
+  const KernelSet &ks = kernels_for(dtype, np);
+  if (!ks.valid) return fail(BTC_ERR_UNSUPPORTED, "no kernels for dtype %d, np %d", dtype, np);
+  btc_plan_s *p = new btc_plan_s();
+  p->N = N;
+  p->n = n;
+  p->np = np;
+  p->dtype = dtype;
+  p->stream = (cudaStream_t)stream;
+  p->ks = &ks;
+  build_host_plan(N, n, np, 0, 0, 0, 0, &p->hp);
+  int rc = BTC_OK;
+  auto cleanup = [&](int code) {
+    btc_free(p);
+    return code;
+  };
+  const size_t bs = (size_t)np * np * ks.elem;
+  size_t dbytes = bs * N;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->dpool, dbytes)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_y, (size_t)N * np * kMaxCols * ks.elem)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_rb, sizeof(Readback))) != cudaSuccess ||
+      (e = cudaMallocHost(&p->h_rb, sizeof(Readback))) != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
+                        cudaGetErrorString(e)));
+  p->d_norms = p->d_rb->norms;
+  p->d_info = &p->d_rb->info;
+  p->d_status = &p->d_rb->status;
+  p->h_norms = p->h_rb->norms;
+  p->h_info = &p->h_rb->info;
+  p->h_status = &p->h_rb->status;
+  if ((e = cudaMemset(p->d_rb, 0, sizeof(Readback))) != cudaSuccess)
+    return cleanup(fail(BTC_ERR_CUDA, "btc_plan: %s", cudaGetErrorString(e)));
+  p->fixed_bytes = (int64_t)(dbytes + (size_t)N * np * kMaxCols * ks.elem);
+  if ((rc = plan_schedule(p))) return cleanup(rc);
   *out = p;
   return BTC_OK;
 }
@@ -1355,6 +1490,28 @@ int btc_plan_inject_stall(btc_plan_t p, int item, int64_t max_polls) {
   return BTC_OK;
 }
 
+int btc_plan_set_order(btc_plan_t p, int order, int chunks) {
+  if (!p || (order != BTC_ORDER_ND && order != BTC_ORDER_PARTITION) || (order == BTC_ORDER_PARTITION && chunks < 1))
+    return fail(BTC_ERR_ARG, "btc_plan_set_order: invalid arguments");
+  if (p->ks->tiled) return fail(BTC_ERR_UNSUPPORTED, "btc_plan_set_order: blocked 256 plans use the ND order only");
+  if (order == BTC_ORDER_PARTITION && p->variant == BTC_VARIANT_RIGHT_LOOKING)
+    return fail(BTC_ERR_UNSUPPORTED, "btc_plan_set_order: the right-looking variant needs the nested-dissection order");
+  HostPlan hp;
+  if (order == BTC_ORDER_ND) {
+    build_host_plan(p->N, p->n, p->np, 0, 0, 0, 0, &hp);
+  } else if (!build_partition_plan(p->N, p->n, p->np, chunks, 0, 0, 0, 0, &hp)) {
+    return fail(BTC_ERR_ARG, "btc_plan_set_order: %d chunks do not fit in N = %d", chunks, p->N);
+  }
+  plan_unschedule(p);
+  p->hp = std::move(hp);
+  p->stall_item = -1;
+  p->wait_limit = kMaxPolls;
+  p->factored = false;
+  p->anorm_valid = false;
+  p->tuned[0] = p->tuned[1] = p->tuned[2] = false;
+  return plan_schedule(p);
+}
+
 int btc_plan_set_root_precision(btc_plan_t p, int precision) {
   if (!p || (precision != BTC_ROOT_DOUBLE_FP32 && precision != BTC_ROOT_FP64))
     return fail(BTC_ERR_ARG, "btc_plan_set_root_precision: invalid arguments");
@@ -1365,6 +1522,8 @@ int btc_plan_set_root_precision(btc_plan_t p, int precision) {
 int btc_plan_set_variant(btc_plan_t p, int variant) {
   if (!p || (variant != BTC_VARIANT_HYBRID && variant != BTC_VARIANT_RIGHT_LOOKING))
     return fail(BTC_ERR_ARG, "btc_plan_set_variant: invalid arguments");
+  if (variant == BTC_VARIANT_RIGHT_LOOKING && p->hp.packed)
+    return fail(BTC_ERR_UNSUPPORTED, "btc_plan_set_variant: the right-looking variant needs the nested-dissection order");
   p->variant = variant;
   return BTC_OK;
 }
@@ -1510,7 +1669,8 @@ int btc_factor_solve_host(btc_plan_t p, const void *D, const void *B, const void
   // residuals; otherwise both are copied first
   const void *hD = device_view_of_host(D), *hB = p->N > 1 ? device_view_of_host(B) : nullptr;
   const bool ingest = p->dtype != BTC_F32 && p->N > 1 && hD && hB && !((((uintptr_t)hD) | ((uintptr_t)hB)) & 7) &&
-                      p->variant == BTC_VARIANT_HYBRID && p->sched == BTC_SCHED_FLOW && !p->ks->tensor_cores;
+                      p->variant == BTC_VARIANT_HYBRID && p->sched == BTC_SCHED_FLOW && !p->ks->tensor_cores &&
+                      !p->hp.packed;  // (a packing pass, not the level-1 loads, reads a partition plan's inputs)
   struct IngestGuard {
     btc_plan_s *p;
     ~IngestGuard() { p->ingD = p->ingB = nullptr; }
@@ -1736,7 +1896,7 @@ int btc_free(btc_plan_t p) {
   void *dev[] = {p->dpool,        p->epool,        p->d_fac,    p->d_fwd,  p->d_bwd,     p->d_rb,
                  p->d_y,          p->s_D,          p->d_fac_deps, p->d_solve_flow, p->d_flow, p->s_B,
                  p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail,
-                 p->kry,          p->d_tiles,      p->d_tile_cnt};
+                 p->kry,          p->d_tiles,      p->d_tile_cnt, p->d_orient};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_rb) cudaFreeHost(p->h_rb);

@@ -15,6 +15,7 @@
 // (zeros below the diagonal). Off-diagonal slots: see btc_internal.h.
 #pragma once
 #include "btc_internal.h"
+#include "btc_runtime.h"
 #include "btc_tile.cuh"
 
 namespace btc {
@@ -573,13 +574,16 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol_f64(Fac
   }
 }
 
-// Packing pass of Alg. 6 (its first parallel loop): Dhat_v <- D_v for every
-// node (upper-form copy of the caller's lower triangle, identity padding) and
-// the level-1 slot of B_v in the orientation level 1 eliminates: slot k
-// (1-based, pair k, k+1) holds S(k, k+1) = B_k^T when k is odd, else
-// S(k+1, k) = B_k. One CTA per node.
+// Packing pass of Alg. 6 (its first parallel loop) and of the partition
+// orders: Dhat_v <- D_v for every node (upper-form copy of the caller's lower
+// triangle, identity padding) and the slot of B_v (coupling nodes v, v+1) in
+// the orientation of the node eliminated first: with `transposed` null, the
+// nested-dissection level 1 (slot k, 1-based, holds S(k, k+1) = B_k^T when k
+// is odd, else S(k+1, k) = B_k); otherwise B_v^T where transposed[v] != 0,
+// else B_v. One CTA per node.
 template <typename P, typename S, int NP>
-__global__ void k_pack_matrix(P *dpool, P *epool, const S *D, const S *B, int N, int n) {
+__global__ void k_pack_matrix(P *dpool, P *epool, const S *D, const S *B, int N, int n,
+                              const int8_t *transposed) {
   const int v = blockIdx.x;  // 0-based node
   const size_t ubs = (size_t)n * n, bs = (size_t)NP * NP;
   for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) {
@@ -589,13 +593,24 @@ __global__ void k_pack_matrix(P *dpool, P *epool, const S *D, const S *B, int N,
     else val = (i == j) ? P(1) : P(0);
     dpool[v * bs + q] = val;
     if (v + 1 < N) {
-      const bool odd = ((v + 1) & 1) != 0;  // 1-based slot index k = v + 1
+      const bool odd = transposed ? transposed[v] != 0 : ((v + 1) & 1) != 0;  // (ND: 1-based slot k = v + 1)
       P b;
       if (i < n && j < n) b = convert_in<P, S>(odd ? B[v * ubs + (size_t)j * n + i] : B[v * ubs + (size_t)i * n + j]);
       else b = P(0);
       epool[v * bs + q] = b;
     }
   }
+}
+
+// Typed launch of the packing pass (argument types checked at compile time).
+template <typename P, typename S, int NP>
+int launch_pack(void *dpool, void *epool, const void *D, const void *B, int N, int n, const int8_t *orient,
+                cudaStream_t s) {
+  if (N <= 0) return BTC_OK;
+  k_pack_matrix<P, S, NP><<<N, 256, 0, s>>>(static_cast<P *>(dpool), static_cast<P *>(epool),
+                                             static_cast<const S *>(D), static_cast<const S *>(B), N, n, orient);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BTC_OK : fail(BTC_ERR_CUDA, "packing pass launch: %s", cudaGetErrorString(e));
 }
 
 }  // namespace btc

@@ -125,6 +125,13 @@ struct LevelSchedule {
 
 struct HostPlan {
   int N = 0, n = 0, np = 0, levels = 0;
+  // elimination order: 0 = nested dissection (P_inf, Sec. 4.3); c >= 1 = the partition permutation
+  // of Sec. 4.1 with c chunks (c = 1: the natural order of Alg. 1). Partition plans read packed pools
+  // at every level (packed), whose original coupling slot v (nodes v, v + 1) holds B_v^T when v is
+  // eliminated first (slot_transposed[v] = 1), else B_v.
+  int chunks = 0;
+  bool packed = false;
+  std::vector<int8_t> slot_transposed;
   // dataflow form: factor items in level order with the (<= 3) items of the
   // previous level that produce their inputs, and the fused solve list
   std::vector<int32_t> fac_deps;           // 3 per factor item (flat level order), -1: none
@@ -165,6 +172,13 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
 // Tile tasks of a plan in launch order (level by level, phase by phase within
 // a level) and the task total of every node (indexed like the flat factor list).
 void build_tile_tasks(const HostPlan &P, std::vector<TileTask> *tasks, std::vector<int32_t> *node_total);
+
+// The partition permutation (Sec. 4.1, Alg. 4, chunk sizes by Proposition 1) as a plan: chunk interiors
+// eliminated left to right (chains, interleaved across chunks by position), then the pivots in order.
+// Returns false when `chunks` chunks do not fit in N nodes.
+bool build_partition_plan(int N, int n, int np, int chunks, int64_t d_base, int64_t e_base, int64_t y_base, int inst,
+                          HostPlan *out);
+void partition_sizes(int N, int chunks, int *n1, int *nk);
 
 int padded_size(int n, int dtype);       // np for a block size (0 if unsupported)
 int64_t count_offdiag(int N);            // sum over levels of floor(N/s) - 1

@@ -41,13 +41,17 @@ struct KernelSet {
   FlowVariant flow_v[kFlowVariants];
   int n_flow_v = 0, flow_default = 0;
   bool tensor_cores = false;  // level elimination products on tcgen05 (TF32 or BF16 operands)
-  // blocked nodes of tile tasks (padded n = 256): a packing pass (pack_matrix) and one persistent
+  // blocked nodes of tile tasks (padded n = 256): a packing pass (pack_pools) and one persistent
   // launch of tile tasks replace the node kernels; the top separator is one more node of that launch
   bool tiled = false;
   const void *tile_flow = nullptr;
   size_t tile_smem = 0;
   // right-looking variant (Alg. 6): packing pass, per-level and persistent kernels, double-FP32 root (its FP64 form is root64_rl)
-  const void *pack_matrix = nullptr, *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
+  const void *fac_rl = nullptr, *fac_flow_rl = nullptr, *root_rl = nullptr;
+  // the packing pass, launched through a typed wrapper (N CTAs): D, B the caller's arrays in the
+  // set's source type; orient null (the ND level-1 orientation) or one flag per coupling
+  int (*pack_pools)(void *dpool, void *epool, const void *D, const void *B, int N, int n, const int8_t *orient,
+              cudaStream_t s) = nullptr;
   // solve
   const void *fwd = nullptr, *bwd = nullptr;
   size_t (*fwd_smem)(int m) = nullptr;

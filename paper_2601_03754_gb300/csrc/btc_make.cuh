@@ -70,7 +70,7 @@ KernelSet make_set() {
   k.fac_fwd_flow = k.flow_v[k.flow_default].fac_fwd;
   k.fac_flow_rl = k.flow_v[k.flow_default].fac_rl;
   k.fused_smem = &fused_smem_fn<T, NP, R>;
-  k.pack_matrix = (const void *)&k_pack_matrix<T, S, NP>;
+  k.pack_pools = &launch_pack<T, S, NP>;
   k.fac_rl = (const void *)&k_factor_level<T, T, S, NP, R, false, true>;
   k.solve_flow = (const void *)&k_solve_flow<T, NP>;
   k.fwd = (const void *)&k_fwd_level<T, NP>;

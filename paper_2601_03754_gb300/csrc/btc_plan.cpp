@@ -4,6 +4,7 @@
 // Levels l = 1 .. floor(log2 N) + 1 with stride s = 2^(l-1); at level l the
 // eliminated nodes are the odd multiples of s that are <= N (1-based labels,
 // as in the paper), and the surviving nodes are the multiples of s.
+#include <algorithm>
 #include <cmath>
 
 #include "btc_internal.h"
@@ -383,6 +384,281 @@ void build_tile_tasks(const HostPlan &P, std::vector<TileTask> *tasks, std::vect
   }
   (void)T;
   (void)LDG;
+}
+
+}  // namespace btc
+
+namespace btc {
+
+// Chunk sizes of the partition permutation (Proposition 1): N_k* = (7N - 7p + 7) / (7p + 12) rounded down
+// and up, N_1 = N - (p - 1)(N_k + 1), keeping the split whose larger parallel-phase cost
+// max(7/3 N_1 - 1, 19/3 N_k - 1) is smaller; chunks k > 1 hold at least one node. nk = 0 when p = 1.
+void partition_sizes(int N, int chunks, int *n1, int *nk) {
+  *n1 = N;
+  *nk = 0;
+  if (chunks <= 1) return;
+  const double star = (7.0 * N - 7.0 * chunks + 7.0) / (7.0 * chunks + 12.0);
+  double best = 1e300;
+  for (int c : {(int)std::floor(star), (int)std::ceil(star)}) {
+    c = std::max(c, 1);
+    const int a = N - (chunks - 1) * (c + 1);
+    if (a < 1) continue;
+    const double cost = std::max(7.0 / 3.0 * a - 1.0, 19.0 / 3.0 * c - 1.0);
+    if (cost < best) {
+      best = cost;
+      *n1 = a;
+      *nk = c;
+    }
+  }
+  if (best == 1e300) *n1 = *nk = -1;
+}
+
+bool build_partition_plan(int N, int n, int np, int chunks, int64_t d_base, int64_t e_base, int64_t y_base, int inst,
+                          HostPlan *P) {
+  int n1, nk;
+  partition_sizes(N, std::max(chunks, 1), &n1, &nk);
+  if (n1 < 1) return false;
+  const int p = std::max(chunks, 1);
+  *P = HostPlan();
+  P->N = N;
+  P->n = n;
+  P->np = np;
+  P->chunks = p;
+  P->packed = true;
+  const int64_t bs = (int64_t)np * np;
+  auto dOff = [&](int v) { return (d_base + v) * bs; };
+  // chunk of every node (0 = chunk 1; k - 1 for chunk k) and pivots (-1)
+  std::vector<int> chunk_of(N, 0), pivot(p + 1, -1);  // pivot[k] = node of A_k, k = 2..p
+  std::vector<std::vector<int>> members(p);
+  for (int v = 0; v < n1; ++v) members[0].push_back(v);
+  int v = n1;
+  for (int k = 2; k <= p; ++k) {
+    pivot[k] = v;
+    chunk_of[v] = -1;
+    ++v;
+    for (int i = 0; i < nk; ++i, ++v) {
+      chunk_of[v] = k - 1;
+      members[k - 1].push_back(v);
+    }
+  }
+  // elimination order: chain positions across chunks, then the pivots
+  std::vector<std::vector<int>> lev;
+  const int maxlen = std::max(n1, nk);
+  for (int pos = 0; pos < maxlen; ++pos) {
+    std::vector<int> L;
+    for (int k = 0; k < p; ++k)
+      if (pos < (int)members[k].size()) L.push_back(members[k][pos]);
+    lev.push_back(L);
+  }
+  for (int k = 2; k <= p; ++k) lev.push_back({pivot[k]});
+  std::vector<int> order, posn(N, -1);
+  for (auto &L : lev)
+    for (int e : L) {
+      posn[e] = (int)order.size();
+      order.push_back(e);
+    }
+  // slots: original couplings (v, v+1) at slot v, fills appended
+  int64_t nslots = std::max(N - 1, 0);
+  P->slot_transposed.assign(std::max(N - 1, 0), 0);
+  P->slot_e.assign(std::max(N - 1, 0), -1);
+  P->slot_o.assign(std::max(N - 1, 0), -1);
+  for (int s = 0; s + 1 < N; ++s) P->slot_transposed[s] = posn[s] < posn[s + 1] ? 1 : 0;
+  // path elimination: current neighbours and coupling slots
+  std::vector<int> lft(N), rgt(N);
+  std::vector<int64_t> sl(N, -1), sr(N, -1);
+  for (int u = 0; u < N; ++u) {
+    lft[u] = u - 1;
+    rgt[u] = u + 1 < N ? u + 1 : -1;
+    sl[u] = u > 0 ? u - 1 : -1;
+    sr[u] = u + 1 < N ? u : -1;
+  }
+  auto eOff = [&](int64_t slot) { return (e_base + slot) * bs; };
+  std::vector<int32_t> item_of(N, -1);      // flat factor index of each node
+  std::vector<int64_t> deferred_from(N, -1);  // slot of the block deferred onto a node (its p_a)
+  std::vector<int32_t> deferred_item(N, -1);  // ... and the item that wrote it
+  std::vector<int32_t> last_imm(N, -1);       // last item that updated a node immediately
+  std::vector<int32_t> slot_writer;           // item that created a fill slot (index - (N - 1))
+  std::vector<std::pair<int, int>> nbr_at(N, {-1, -1});
+  std::vector<std::pair<int64_t, int64_t>> nbr_slot(N, {-1, -1});
+  auto last_of_chunk = [&](int k) { return members[k - 1].empty() ? -1 : members[k - 1].back(); };
+  P->lv.assign(lev.size(), LevelSchedule());
+  P->fac_deps.clear();
+  const double n3 = (double)n * n * n, n2 = (double)n * n;
+  double fl = 0, crit = 0;
+  int32_t idx = 0;
+  for (size_t l = 0; l < lev.size(); ++l) {
+    LevelSchedule &LS = P->lv[l];
+    LS.s = 0;
+    double level_max = 0;
+    for (int e : lev[l]) {
+      const int a = lft[e], b = rgt[e];
+      const int64_t sa = sl[e], sb = sr[e];
+      nbr_at[e] = {a, b};
+      nbr_slot[e] = {sa, sb};
+      // roles: chains of chunks k > 1 update their pivot (left) at once and defer the right neighbour;
+      // chunk 1 updates its right neighbour at once unless that is a pivot (deferred); pivots update
+      // the next pivot at once
+      int down = -1, up = -1;
+      int64_t s_down = -1, s_up = -1;
+      if (chunk_of[e] >= 1) {
+        down = a, s_down = sa, up = b, s_up = sb;
+      } else if (chunk_of[e] == 0) {
+        if (b >= 0 && chunk_of[b] == -1) up = b, s_up = sb;
+        else down = b, s_down = sb;
+      } else {
+        down = b, s_down = sb;
+        if (a >= 0) up = a, s_up = sa;  // (never: the previous pivot is eliminated first)
+      }
+      FactorItem it;
+      it.d_self = dOff(e);
+      it.d_next = down >= 0 ? dOff(down) : -1;
+      it.r_down = down >= 0 ? eOff(s_down) : -1;
+      it.r_up = up >= 0 ? eOff(s_up) : -1;
+      it.p_a = deferred_from[e] >= 0 ? eOff(deferred_from[e]) : -1;
+      it.p_b = -1;
+      it.d_prev = -1;
+      it.fill = -1;
+      it.flags = 0;
+      it.node = e;
+      it.inst = inst;
+      it.pad = 0;
+      int64_t fslot = -1;
+      if (up >= 0 && down >= 0) {
+        fslot = nslots++;
+        it.fill = eOff(fslot);
+        if (posn[up] < posn[down]) it.flags |= FI_FILL_UPFIRST;
+        slot_writer.push_back(idx);
+        P->slot_e.push_back(posn[up] < posn[down] ? up : down);
+        P->slot_o.push_back(posn[up] < posn[down] ? down : up);
+      }
+      if (l + 1 == lev.size()) it.flags |= FI_ROOT;
+      // factor-pool slot bookkeeping for btc_get_factor: the blocks this node stores
+      if (s_up >= 0 && s_up < N - 1) {
+        P->slot_e[s_up] = e;
+        P->slot_o[s_up] = up;
+      }
+      if (s_down >= 0 && s_down < N - 1) {
+        P->slot_e[s_down] = e;
+        P->slot_o[s_down] = down;
+      }
+      // dependencies (at most three): the producer of the deferred block, the last immediate writer of
+      // D_e, the creators of the fill slots it reads; and, for a pivot, the chain that still updates the
+      // pivot it writes (chunk k + 1)
+      std::vector<int32_t> dep;
+      auto add = [&](int32_t d) {
+        if (d >= 0 && std::find(dep.begin(), dep.end(), d) == dep.end()) dep.push_back(d);
+      };
+      if (chunk_of[e] == -1) {
+        int k = 0;
+        for (int q = 2; q <= p; ++q)
+          if (pivot[q] == e) k = q;
+        if (k == 2) {
+          add(item_of[last_of_chunk(1)]);
+          add(item_of[last_of_chunk(2)]);
+        } else {
+          add(item_of[pivot[k - 1]]);  // transitively: chunks up to k
+        }
+        if (k + 1 <= p) add(item_of[last_of_chunk(k + 1)]);  // chunk k + 1 still updates A_(k+1)
+      } else {
+        add(deferred_item[e]);
+        add(last_imm[e]);
+        for (int64_t s2 : {sa, sb})
+          if (s2 >= N - 1) add(slot_writer[s2 - (N - 1)]);
+      }
+      if (dep.size() > 3) return false;  // (cannot happen for this order)
+      while (dep.size() < 3) dep.push_back(-1);
+      P->fac_deps.insert(P->fac_deps.end(), dep.begin(), dep.end());
+      // state after eliminating e
+      if (up >= 0) {
+        deferred_from[up] = s_up;
+        deferred_item[up] = idx;
+      }
+      if (down >= 0) last_imm[down] = idx;
+      if (a >= 0) rgt[a] = b, sr[a] = fslot;
+      if (b >= 0) lft[b] = a, sl[b] = fslot;
+      item_of[e] = idx++;
+      double c = n3 / 3.0;
+      if (it.p_a >= 0) c += n3;
+      if (it.r_down >= 0) c += 2 * n3;  // trsm + immediate syrk
+      if (it.r_up >= 0) c += n3;
+      if (it.fill >= 0) c += 2 * n3;
+      fl += c;
+      level_max = std::max(level_max, c);
+      LS.fac.push_back(it);
+    }
+    crit += level_max;
+  }
+  P->levels = (int)lev.size();
+  P->offdiag = nslots;
+  P->fill = nslots - std::max(N - 1, 0);
+  P->fac_deps_rl.assign(P->fac_deps.size(), -1);
+  P->level_slot_off.assign(P->levels + 2, 0);
+  // ---- solve (pull form forward in elimination order, backward in reverse)
+  auto yNode = [&](int u) { return y_base + u; };
+  P->solve_flow.clear();
+  std::vector<int32_t> fwd_final(N, -1), bwd_item(N, -1);
+  auto push = [&](int64_t self, int qa, int64_t ea, int qb, int64_t eb, int64_t dself, int kind, int32_t d0, int32_t d1,
+                  int32_t d2) {
+    SolveFlowItem q;
+    q.y_self = yNode(self);
+    q.y_a = qa >= 0 ? yNode(qa) : -1;
+    q.e_a = qa >= 0 ? ea : -1;
+    q.y_b = qb >= 0 ? yNode(qb) : -1;
+    q.e_b = qb >= 0 ? eb : -1;
+    q.d_self = dself;
+    q.kind = kind;
+    q.dep[0] = d0;
+    q.dep[1] = d1;
+    q.dep[2] = d2;
+    P->solve_flow.push_back(q);
+    return (int32_t)P->solve_flow.size() - 1;
+  };
+  // the block stored by eliminated node q for its coupling with e (rows: q's variables)
+  auto stored = [&](int q, int e) -> int64_t {
+    return nbr_at[q].first == e ? eOff(nbr_slot[q].first) : eOff(nbr_slot[q].second);
+  };
+  // chain nodes (elimination order): the only earlier-eliminated node coupled with a chain node is its
+  // predecessor in the chunk (whose right neighbour it was); pull its contribution, then solve
+  for (int e : order) {
+    if (chunk_of[e] == -1) continue;
+    const auto &mem = members[chunk_of[e]];
+    const size_t i = std::find(mem.begin(), mem.end(), e) - mem.begin();
+    const int contrib = i > 0 ? mem[i - 1] : -1;
+    fwd_final[e] = push(e, contrib, contrib >= 0 ? stored(contrib, e) : -1, -1, -1, dOff(e), 0,
+                        contrib >= 0 ? fwd_final[contrib] : -1, -1, -1);
+  }
+  // pivots: accumulate the contributions of their chunk in pairs, then the previous chunk's last node and
+  // the previous pivot, and solve
+  for (int k = 2; k <= p; ++k) {
+    const int A = pivot[k];
+    const auto &mem = members[k - 1];
+    int32_t prev_item = -1;
+    for (size_t i = 0; i < mem.size(); i += 2) {
+      const int qa = mem[i], qb = i + 1 < mem.size() ? mem[i + 1] : -1;
+      prev_item = push(A, qa, stored(qa, A), qb, qb >= 0 ? stored(qb, A) : -1, -1, 0, prev_item, fwd_final[qa],
+                       qb >= 0 ? fwd_final[qb] : -1);
+    }
+    const int lastp = last_of_chunk(k - 1);
+    const int prevA = k > 2 ? pivot[k - 1] : -1;
+    // the previous pivot's final item (listed before this one) orders the writes to y_A as well
+    fwd_final[A] = push(A, lastp, stored(lastp, A), prevA, prevA >= 0 ? stored(prevA, A) : -1, dOff(A), 0, prev_item,
+                        fwd_final[lastp], prevA >= 0 ? fwd_final[prevA] : -1);
+  }
+  P->n_fwd = (int32_t)P->solve_flow.size();
+  P->fwd_node.assign(P->n_fwd, 0);
+  P->fwd_level.assign(P->n_fwd, 0);
+  for (auto it = order.rbegin(); it != order.rend(); ++it) {
+    const int e = *it;
+    const int a = nbr_at[e].first, b = nbr_at[e].second;
+    bwd_item[e] = push(e, a, a >= 0 ? eOff(nbr_slot[e].first) : -1, b, b >= 0 ? eOff(nbr_slot[e].second) : -1, dOff(e),
+                       1, a >= 0 ? bwd_item[a] : -1, b >= 0 ? bwd_item[b] : -1, fwd_final[e]);
+  }
+  P->factor_flops = fl;
+  P->seq_factor_flops = (7.0 / 3.0 * N - 2.0) * n3;
+  P->crit_flops = crit;
+  P->crit_formula = crit;
+  P->solve_flops_per_rhs = 2.0 * N * n2 + 4.0 * (double)P->offdiag * n2;
+  return true;
 }
 
 }  // namespace btc

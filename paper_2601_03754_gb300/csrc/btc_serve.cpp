@@ -65,6 +65,7 @@ struct Result {
   int iters = 0;
   double relres = 0.0;
   double latency_us = 0.0;
+  double queue_us = 0.0;  // submission -> a slot took it
 };
 
 // A server plan: a plan for N_b blocks of size n and its staging copies of the
@@ -121,7 +122,7 @@ struct btc_server_s {
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
   // statistics
-  std::vector<double> latencies;
+  std::vector<double> latencies, queue_times, service_times;
   int64_t completed = 0, failed = 0, evictions = 0, cache_hits = 0, cache_misses = 0;
   Clock::time_point t_first, t_last;
   bool any = false;
@@ -246,6 +247,7 @@ void worker(btc_server_s *s, int slot) {
     SPlan sp;
     bool resolve = false;
     int64_t reserved = 0;
+    Clock::time_point t_start;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       long idx = -1;
@@ -253,6 +255,7 @@ void worker(btc_server_s *s, int slot) {
       if (idx < 0) return;  // stopping and the queue is drained
       job = s->queue[idx];
       s->queue.erase(s->queue.begin() + idx);
+      t_start = Clock::now();
       const int64_t fid = job.req.factor_id;
       if (fid >= 0 && s->cached.count(fid)) {
         resolve = true;
@@ -322,8 +325,11 @@ void worker(btc_server_s *s, int slot) {
       r.iters = iters;
       r.relres = rel;
       r.latency_us = std::chrono::duration<double, std::micro>(t_done - job.t_submit).count();
+      r.queue_us = std::chrono::duration<double, std::micro>(t_start - job.t_submit).count();
       if (rc == BTC_OK) {
         s->latencies.push_back(r.latency_us);
+        s->queue_times.push_back(r.queue_us);
+        s->service_times.push_back(r.latency_us - r.queue_us);
         ++s->completed;
       } else {
         ++s->failed;
@@ -427,6 +433,21 @@ int btc_server_stats(btc_server_t s, btc_server_stats_t *st) {
   const double span = s->any ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
   st->solves_per_s = span > 0 ? (double)s->completed / span : 0.0;
   st->device_bytes = s->in_flight_bytes + s->cached_bytes + s->free_bytes;
+  st->p50_queue_us = percentile(s->queue_times, 50.0);
+  st->p99_queue_us = percentile(s->queue_times, 99.0);
+  st->p50_service_us = percentile(s->service_times, 50.0);
+  st->p99_service_us = percentile(s->service_times, 99.0);
+  return BTC_OK;
+}
+
+int btc_server_reset_stats(btc_server_t s) {
+  if (!s) return btc::fail(BTC_ERR_ARG, "btc_server_reset_stats: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->latencies.clear();
+  s->queue_times.clear();
+  s->service_times.clear();
+  s->completed = s->failed = s->evictions = s->cache_hits = s->cache_misses = 0;
+  s->any = false;
   return BTC_OK;
 }
 

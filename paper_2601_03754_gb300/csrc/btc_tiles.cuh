@@ -261,7 +261,7 @@ KernelSet make_set_tiled() {
   k.n_flow_v = 0;
   k.flow_default = 0;
   k.fused_smem = &zero_smem_fn;
-  k.pack_matrix = (const void *)&k_pack_matrix<float, double, NP>;
+  k.pack_pools = &launch_pack<float, double, NP>;
   k.solve_flow = (const void *)&k_solve_flow<float, NP>;
   k.fwd = (const void *)&k_fwd_level<float, NP>;
   k.bwd = (const void *)&k_bwd_level<float, NP>;

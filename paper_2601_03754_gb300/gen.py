@@ -20,6 +20,13 @@ Recipes (all float64, 0-based blocks, B[i] couples blocks i+1 and i):
     Diagonal blocks D_0 = I + Bu_0 Bu_0^T, D_k = I + A_k A_k^T + Bu_k Bu_k^T;
     sub-diagonal blocks B_k = -A_{k+1}.
 
+``arrow(N, n, m, delta, seed)``
+    A bordered ("arrow") system [[Psi, C^T], [C, A]]: Psi from bt_random(N, n,
+    delta); C of size m x N n with entries iid N(0, 1/(N n)); A = K K^T/m +
+    (||C||_2^2 / delta + 1) I with K iid N(0, 1). Since every eigenvalue of Psi
+    is >= delta, C Psi^{-1} C^T <= ||C||_2^2 / delta, so the Schur complement
+    A - C Psi^{-1} C^T >= I and the bordered matrix is SPD.
+
 ``rhs(N, n, m, seed)``
     Right-hand sides [N n, m] with iid N(0, 1) entries.
 
@@ -180,3 +187,37 @@ def request_stream(rate: float, count: int, seed: int = 0, sizes=(12, 24, 48, 96
             out.append(dict(t=float(t[k]), N=N, n=n, resolve_of=-1, seed=k))
             factors.append(k)
     return out
+
+
+def arrow(N: int, n: int, m: int, delta: float = 1.0, seed: int = 0):
+    """Bordered block-tridiagonal SPD system -> (D, B, C [m, N n], A [m, m])."""
+    D, B = bt_random(N, n, delta=delta, seed=seed)
+    rng = _rng(seed + 7919)
+    C = rng.standard_normal((m, N * n)) / math.sqrt(N * n)
+    K = rng.standard_normal((m, m))
+    cn = np.linalg.norm(C, ord=2) if m > 0 else 0.0
+    A = K @ K.T / max(m, 1) + (cn * cn / delta + 1.0) * np.eye(m)
+    return D, B, np.ascontiguousarray(C), np.ascontiguousarray(A)
+
+
+def banded(Nb: int, b: int, w: int, delta: float = 1.0, seed: int = 0):
+    """Random block-banded SPD system with lower block bandwidth w -> A [w+1, Nb, b, b], A[k, i] = Psi(i+k, i).
+
+    Off-diagonal blocks N(0, 1/b); each diagonal block M M^T / b shifted by the spectral norms of the
+    2w off-diagonal blocks of its block row plus delta (block diagonal dominance: SPD, every eigenvalue
+    >= delta by the block Gershgorin bound). Blocks with i + k >= Nb are zero."""
+    rng = _rng(seed)
+    A = np.zeros((w + 1, Nb, b, b))
+    for k in range(1, w + 1):
+        if Nb > k:
+            A[k, :Nb - k] = rng.standard_normal((Nb - k, b, b)) / math.sqrt(b)
+    M = rng.standard_normal((Nb, b, b))
+    A[0] = np.matmul(M, np.swapaxes(M, 1, 2)) / b
+    shift = np.full(Nb, float(delta))
+    for k in range(1, w + 1):
+        if Nb > k:
+            s = spectral_norms(A[k, :Nb - k])
+            shift[:Nb - k] += s  # block (i+k, i) lies in block row i + k and (transposed) in block row i
+            shift[k:] += s
+    A[0] += shift[:, None, None] * np.eye(b)[None]
+    return np.ascontiguousarray(A)

@@ -66,7 +66,9 @@ def test_gmres_ir_converges_where_classical_refinement_fails_bf16(N):
     xg = torch.zeros_like(bd)
     outer, inner, rel_g, rc_g = btc.btc_solve_gmres_ir(p, bd, xg, tol=1e-10, max_outer=20, restart=60)
     assert rc_g == btc.OK and rel_g <= 1e-10, (outer, inner, rel_g)
-    assert 1 + outer + inner < 1 + it_c  # fewer preconditioned solves than the failed classical attempt
+    # classical refinement stops without converging (it diverges: the norms turn NaN, or maxit runs out);
+    # GMRES-IR needs a bounded number of preconditioned solves
+    assert 1 + outer + inner <= 60, (outer, inner)
     xh = xg.cpu().numpy()
     assert oracle.relres(D, B, xh, b) <= 1e-10
     xo = oracle.solve(D, B, b)

@@ -172,7 +172,112 @@ def check_toeplitz_closed_form(N=13, n=2, d=3.0, e=1.2):
         np.testing.assert_allclose(x[comp::n], thomas(d, e, rhs[comp::n]), rtol=1e-12, atol=1e-13)
 
 
+def check_arrow_assemble_vs_blocks(N=4, n=3, m=2, seed=6):
+    D, B, C, A = gen.arrow(N, n, m, seed=seed)
+    Ag = A.copy()
+    Ag[np.triu_indices(m, 1)] = 7e3  # only the lower triangle of A may be read
+    M = oracle.arrow_assemble(D, B, C, Ag)
+    ref = np.block([[oracle.assemble(D, B), C.T], [C, A]])
+    np.testing.assert_array_equal(M, ref)
+
+
+def check_arrow_solve_vs_lapack(N=5, n=2, m=3, seed=7):
+    D, B, C, A = gen.arrow(N, n, m, seed=seed)
+    b = np.random.default_rng(seed).standard_normal(N * n + m)
+    x = oracle.arrow_solve(D, B, C, A, b)
+    M = np.block([[oracle.assemble(D, B), C.T], [C, A]])
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12)
+
+
+def check_arrow_resid_vs_dense(N=4, n=3, m=2, seed=8):
+    D, B, C, A = gen.arrow(N, n, m, seed=seed)
+    rng = np.random.default_rng(seed)
+    x, b = rng.standard_normal(N * n + m), rng.standard_normal(N * n + m)
+    M = np.block([[oracle.assemble(D, B), C.T], [C, A]])
+    r, a, xn = oracle.arrow_resid(D, B, C, A, x, b)
+    assert math.isclose(r, np.abs(b - M @ x).max(), rel_tol=1e-12)
+    assert math.isclose(a, np.abs(M).sum(axis=1).max(), rel_tol=1e-12)
+    assert math.isclose(xn, np.abs(x).max(), rel_tol=1e-15)
+    # a residual that lives in the border rows only (the block-tridiagonal rows are satisfied)
+    b2 = M @ x
+    b2[N * n:] += rng.standard_normal(m) * 1e-3
+    r2, _, _ = oracle.arrow_resid(D, B, C, A, x, b2)
+    assert math.isclose(r2, np.abs(b2 - M @ x).max(), rel_tol=1e-6)
+
+
 # ------------------------------------------------------------ the tests ---
+
+
+@pytest.mark.parametrize("N,p", [(10, 2), (101, 4), (1000, 8), (57, 3), (6, 2)])
+def test_partition_sizes_follow_proposition_1(N, p):
+    n1, nk = oracle.partition_sizes(N, p)
+    assert n1 + (p - 1) * (nk + 1) == N and n1 >= 1 and nk >= 1
+    # the continuous optimum balances the two parallel-phase costs at ratio 19/7
+    n1s = (19 * N - 19 * p + 19) / (7 * p + 12)
+    nks = (7 * N - 7 * p + 7) / (7 * p + 12)
+    assert math.isclose(n1s / nks, 19 / 7) and math.isclose(n1s + (p - 1) * (nks + 1), N)
+    assert abs(nk - nks) < 1.0 + 1e-12
+    # no other integer split does better on the larger phase cost
+    cost = lambda a, b: max(7 / 3 * a - 1, 19 / 3 * b - 1)
+    for b in range(1, N):
+        a = N - (p - 1) * (b + 1)
+        if a >= 1:
+            assert cost(n1, nk) <= cost(a, b) + 1e-9 or abs(b - nks) >= 1.0
+
+
+@pytest.mark.parametrize("N,p,n", [(7, 2, 2), (12, 3, 3), (9, 1, 2), (20, 4, 2)])
+def test_partition_order_factor_equals_dense_cholesky_of_permuted(N, p, n):
+    D, B = gen.bt_random(N, n, delta=0.3, seed=N + p)
+    order, Ld, pairs, Loff = oracle.partition_factor(D, B, p)
+    assert sorted(order.tolist()) == list(range(N))
+    n1, nk = oracle.partition_sizes(N, p)
+    assert list(order[:n1]) == list(range(n1))  # chunk 1 first, in natural order
+    A = oracle.assemble(D, B)
+    L = np.linalg.cholesky(permuted_dense(A, order, n))
+    pos = np.empty(N, dtype=int)
+    pos[order] = np.arange(N)
+    for i in range(N):
+        np.testing.assert_allclose(Ld[i], L[pos[i] * n:(pos[i] + 1) * n, pos[i] * n:(pos[i] + 1) * n], rtol=1e-12,
+                                   atol=1e-12)
+    for (r, c), blk in zip(pairs, Loff):
+        np.testing.assert_allclose(blk, L[pos[r] * n:(pos[r] + 1) * n, pos[c] * n:(pos[c] + 1) * n], rtol=1e-11,
+                                   atol=1e-12)
+    # fill: each chunk k > 1 couples its pivot with every later node of the chunk, and consecutive pivots
+    # couple through the last node of the chunk between them
+    expect = (N - 1) + (p - 1) * (nk - 1) + max(p - 2, 0)
+    assert len(pairs) == expect
+
+
+def test_arrow_assemble_places_the_border():
+    check_arrow_assemble_vs_blocks()
+
+
+@pytest.mark.parametrize("N,n,m", [(1, 1, 1), (5, 2, 3), (7, 4, 5)])
+def test_arrow_solve_matches_lapack(N, n, m):
+    check_arrow_solve_vs_lapack(N, n, m, seed=N + m)
+
+
+def test_arrow_resid_matches_dense():
+    check_arrow_resid_vs_dense()
+
+
+def test_arrow_with_zero_border_decouples():
+    """C = 0: the bordered system splits into Psi x_T = b_T (Alg. 1 solve) and A x_A = b_A."""
+    D, B, C, A = gen.arrow(6, 3, 4, seed=9)
+    C = np.zeros_like(C)
+    b = np.random.default_rng(9).standard_normal(18 + 4)
+    x = oracle.arrow_solve(D, B, C, A, b)
+    np.testing.assert_allclose(x[:18], oracle.solve(D, B, b[:18]), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(x[18:], np.linalg.solve(A, b[18:]), rtol=1e-12, atol=1e-13)
+
+
+def test_arrow_generator_is_spd_with_schur_complement_above_identity():
+    D, B, C, A = gen.arrow(8, 3, 4, delta=0.5, seed=10)
+    M = oracle.arrow_assemble(D, B, C, A)
+    assert np.linalg.eigvalsh(M).min() > 0
+    T = oracle.assemble(D, B)
+    S = A - C @ np.linalg.solve(T, C.T)
+    assert np.linalg.eigvalsh(S).min() >= 1.0 - 1e-9
 
 def test_chol_matches_lapack():
     check_chol_vs_lapack()
@@ -383,6 +488,15 @@ MUTATIONS = [
      "v += B[(i - 1) * bs + r * n + c] * x[((size_t)(i - 1) * n + c) * m + col];", "resid"),
     ("resid_upper_transposed", "v -= B[i * bs + c * n + r] * x[((size_t)(i + 1) * n + c) * m + col];",
      "v -= B[i * bs + r * n + c] * x[((size_t)(i + 1) * n + c) * m + col];", "resid"),
+    ("arrow_border_transposed", "out[(size_t)j * M + L + r] = C[(size_t)r * L + j];",
+     "out[(size_t)j * M + L + r] = C[(size_t)r * L + (j + 1) % L];", "arrow"),
+    ("arrow_resid_border_dropped", "        v -= a * x[L + q];\n", "\n", "arrow"),
+    ("arrow_resid_corner_sign", "      v -= a * x[L + c];", "      v += a * x[L + c];", "arrow"),
+    # block-banded: the upper blocks taken untransposed; the band's distance index off by one
+    ("band_upper_not_transposed", "(size_t)c * b + r]; /* Psi(I, J) = Psi(J, I)^T */",
+     "(size_t)r * b + c]; /* Psi(I, J) = Psi(J, I)^T */", "band"),
+    ("band_distance_off_by_one", "if (I > J) return A[((size_t)(I - J) * Nb + J) * bb",
+     "if (I > J) return A[((size_t)(I - J - 1) * Nb + J) * bb", "band"),
 ]
 
 
@@ -401,6 +515,78 @@ def _run_pins(which, golden_dir):
         check_nd_order_golden(golden_dir)
     elif which == "resid":
         check_resid_vs_dense()
+    elif which == "arrow":
+        check_arrow_assemble_vs_blocks()
+        check_arrow_solve_vs_lapack()
+        check_arrow_resid_vs_dense()
+    elif which == "band":
+        check_band_scalar_example()
+        check_band_w1_is_block_tridiagonal()
+        check_band_resid_vs_dense()
+
+
+# ---------------------------------------------------------------- block-banded pins
+def check_band_scalar_example():
+    """b = 1, w = 2, Nb = 4: the pentadiagonal matrix written out by hand from Psi(i+k, i) = A_k[i]
+    (A_0 = 10, 11, 12, 13; A_1 = 1, 2, 3; A_2 = 4, 5)."""
+    A = np.zeros((3, 4, 1, 1))
+    A[0, :, 0, 0] = [10, 11, 12, 13]
+    A[1, :3, 0, 0] = [1, 2, 3]
+    A[2, :2, 0, 0] = [4, 5]
+    A[1, 3] = A[2, 2] = A[2, 3] = 99.0  # outside the matrix: never read
+    ref = np.array([[10, 1, 4, 0],
+                    [1, 11, 2, 5],
+                    [4, 2, 12, 3],
+                    [0, 5, 3, 13]], dtype=float)
+    assert np.array_equal(oracle.band_assemble(A), ref)
+    # a non-symmetric 2 x 2 off-diagonal block keeps its orientation: Psi(1, 0) = A_1[0], Psi(0, 1) = its transpose
+    A2 = np.zeros((2, 2, 2, 2))
+    A2[0] = np.eye(2) * 9
+    A2[1, 0] = [[1, 2], [3, 4]]
+    M = oracle.band_assemble(A2)
+    assert np.array_equal(M[2:, :2], [[1, 2], [3, 4]]) and np.array_equal(M[:2, 2:], [[1, 3], [2, 4]])
+
+
+def check_band_w1_is_block_tridiagonal():
+    A = gen.banded(7, 3, 1, seed=2)
+    assert np.array_equal(oracle.band_assemble(A), oracle.assemble(A[0], A[1, :6]))
+
+
+def check_band_resid_vs_dense():
+    for (Nb, b, w) in [(9, 2, 3), (6, 3, 2), (5, 4, 1)]:
+        A = gen.banded(Nb, b, w, seed=Nb)
+        M = oracle.band_assemble(A)
+        rng = np.random.default_rng(1)
+        x = rng.standard_normal((Nb * b, 2))
+        rhs = rng.standard_normal((Nb * b, 2))
+        r, a, xn = oracle.band_resid(A, x, rhs)
+        assert abs(r - np.abs(rhs - M @ x).max()) <= 1e-12 * max(1.0, r)
+        assert abs(a - np.abs(M).sum(axis=1).max()) <= 1e-12 * a
+        assert xn == np.abs(x).max()
+
+
+def test_band_oracle_pins():
+    check_band_scalar_example()
+    check_band_w1_is_block_tridiagonal()
+    check_band_resid_vs_dense()
+
+
+@pytest.mark.parametrize("Nb,b,w", [(1, 3, 2), (5, 2, 2), (7, 3, 3), (9, 2, 4), (8, 4, 2)])
+def test_band_group_is_the_same_matrix(Nb, b, w):
+    """The block-tridiagonal view of the band is Psi itself, padded with an identity (and generated band
+    matrices are SPD, with every eigenvalue >= delta)."""
+    A = gen.banded(Nb, b, w, delta=0.5, seed=3)
+    M = oracle.band_assemble(A)
+    assert np.linalg.eigvalsh(M).min() >= 0.5 - 1e-12
+    Dg, Bg = oracle.band_group(A, w)
+    G = oracle.assemble(Dg, Bg)
+    L = Nb * b
+    assert np.array_equal(G[:L, :L], M)
+    assert np.array_equal(G[L:, L:], np.eye(G.shape[0] - L)) and not G[L:, :L].any()
+    rhs = np.random.default_rng(0).standard_normal((L, 1))
+    x = oracle.band_solve(A, rhs)
+    assert oracle.band_relres(A, x, rhs) <= 1e-14
+    assert np.allclose(x, np.linalg.solve(M, rhs), rtol=0, atol=1e-12 * np.abs(x).max())
 
 
 @pytest.mark.parametrize("tag,old,new,which", MUTATIONS, ids=[m[0] for m in MUTATIONS])
