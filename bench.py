@@ -347,57 +347,90 @@ def run_phases():
     return 0
 
 
+def _batch_run(btc, torch, specs, dt, chunks, steps, stream, flush, seed0):
+    """One batch workload: factor + FP64-refined solve of every instance per step (graph after the first
+    two calls); mean ms per batch over `steps` L2-flushed steps, the batch's tuning and its orders."""
+    Ds, Bs, bs, xs = [], [], [], []
+    for k, (N, n) in enumerate(specs):
+        D, B = gen_bt(N, n, seed0 + k)
+        Ds.append(D)
+        Bs.append(B if B.numel() else torch.zeros((1, n, n), dtype=torch.float64, device="cuda"))
+        g = torch.Generator(device="cuda")
+        g.manual_seed(4000 + seed0 + k)
+        bs.append(torch.randn((N * n, 1), generator=g, device="cuda", dtype=torch.float64))
+        xs.append(torch.zeros_like(bs[-1]))
+    Ns = [N for N, _ in specs]
+    ns = [n for _, n in specs]
+    batch = btc.btc_batch_plan(Ns, ns, dt, stream, chunks=chunks)
+    q = btc.btc_batch_query(batch)
+
+    def step():
+        return btc.btc_batch_factor_solve_refined(batch, Ds, Bs, bs, xs, tol=TOL, maxit=30)
+
+    with torch.cuda.stream(stream):
+        step()  # tuning of every group
+        step()  # graph capture
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, rel, rc = step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.mean(ts)
+    tuning = []
+    for g in range(q["groups"]):
+        np_, cap, ctas, tuned, gms = btc.btc_batch_tuning(batch, g)
+        tuning.append({"np": np_, "resident_cap": cap, "ctas_per_sm": ctas, "tuned": tuned,
+                       "factor_ms_alone": round(gms, 3)})
+    out = {"ms_per_batch": ms, "solves_per_s": len(specs) * 1000.0 / ms, "refine_iters": it, "max_relres": rel,
+           "factor_gflop": q["factor_flops"] / 1e9, "factor_tflops": q["factor_flops"] / (ms * 1e-3) / 1e12,
+           "groups": q["groups"], "group_tuning": tuning, "device_gb": q["device_bytes"] / 1e9}
+    if chunks is not None:
+        ch = np.asarray(chunks)
+        out["orders"] = {"nested_dissection": int((ch == 0).sum()),
+                         "partition_by_chunks": {str(c): int((ch == c).sum()) for c in sorted(set(ch.tolist())) if c}}
+    batch.free()
+    return out
+
+
+def gen_bt(N, n, seed):
+    from paper_2601_03754_gb300 import gen
+    return gen.bt_random_torch(N, n, delta=1e-2, seed=seed)
+
+
 def batched_measure(btc, gen, torch, steps, stream, flush):
     """Config: 512 instances, n uniform in {8,16,32,64}, N log-uniform in [32, 2048], one RHS each,
     delta = 1e-2; mixed FP32 factor + FP64 refinement to 1e-10, beside the plain FP64 batch. A step is
     btc_batch_factor_solve_refined: after the first (tuning) call, one captured graph with the
     refinement loop on the device. The tuned launch configuration of every block-size group is
-    reported."""
+    reported. Method dispatch (btc_dispatch_orders) is measured against nested dissection on this mix
+    and on a throughput mix of 600 short systems (n in {16, 32}, N log-uniform in [32, 128]), and a
+    forced partition order on the benchmark mix's n <= 16 systems shows what the model avoids."""
     specs = gen.batch_specs(512, seed=0)
-    Ds, Bs, bs, xs = [], [], [], []
-    for k, (N, n) in enumerate(specs):
-        D, B = gen.bt_random_torch(N, n, delta=1e-2, seed=1000 + k)
-        Ds.append(D)
-        Bs.append(B if B.numel() else torch.zeros((1, n, n), dtype=torch.float64, device="cuda"))
-        g = torch.Generator(device="cuda")
-        g.manual_seed(5000 + k)
-        bs.append(torch.randn((N * n, 1), generator=g, device="cuda", dtype=torch.float64))
-        xs.append(torch.zeros_like(bs[-1]))
     Ns = [N for N, _ in specs]
     ns = [n for _, n in specs]
     out = {"instances": len(specs), "nodes": int(sum(Ns)), "n_mix": sorted(set(ns))}
-    for name, dt in (("mixed", btc.MIXED_F32), ("plain_f64", btc.F64)):
-        batch = btc.btc_batch_plan(Ns, ns, dt, stream)
-        q = btc.btc_batch_query(batch)
-
-        def step():
-            return btc.btc_batch_factor_solve_refined(batch, Ds, Bs, bs, xs, tol=TOL, maxit=30)
-
-        reps = steps if dt == btc.MIXED_F32 else max(2, steps // 4)
-        with torch.cuda.stream(stream):
-            step()  # tuning of every group
-            step()  # graph capture
-            ts = []
-            for _ in range(reps):
-                flush.fill_(1.0)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                it, rel, rc = step()
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-        ms = statistics.mean(ts)
-        tuning = []
-        for g in range(q["groups"]):
-            np_, cap, ctas, tuned, gms = btc.btc_batch_tuning(batch, g)
-            tuning.append({"np": np_, "resident_cap": cap, "ctas_per_sm": ctas, "tuned": tuned,
-                           "factor_ms_alone": round(gms, 3)})
-        out[name] = {"ms_per_batch": ms, "solves_per_s": len(specs) * 1000.0 / ms, "refine_iters": it,
-                     "max_relres": rel, "factor_tflops": q["factor_flops"] / (ms * 1e-3) / 1e12,
-                     "groups": q["groups"], "group_tuning": tuning, "device_gb": q["device_bytes"] / 1e9}
-        batch.free()
+    dispatch = btc.btc_dispatch_orders(Ns, ns, btc.MIXED_F32)
+    forced = np.asarray([0 if n > 16 or N > 1000 else max(1, min(48, N // 4)) for N, n in specs], dtype=np.int32)
+    out["mixed"] = _batch_run(btc, torch, specs, btc.MIXED_F32, None, steps, stream, flush, 1000)
+    out["mixed_dispatch"] = _batch_run(btc, torch, specs, btc.MIXED_F32, dispatch, steps, stream, flush, 1000)
+    out["mixed_forced_partition_n_le_16"] = _batch_run(btc, torch, specs, btc.MIXED_F32, forced, steps, stream,
+                                                       flush, 1000)
+    out["plain_f64"] = _batch_run(btc, torch, specs, btc.F64, None, max(2, steps // 4), stream, flush, 1000)
     out["speedup_vs_plain_f64"] = out["plain_f64"]["ms_per_batch"] / out["mixed"]["ms_per_batch"]
+    out["dispatch_speedup"] = out["mixed"]["ms_per_batch"] / out["mixed_dispatch"]["ms_per_batch"]
+    short = gen.batch_specs(600, seed=4, sizes=(16, 32), nmin=32, nmax=128)
+    sd = btc.btc_dispatch_orders([N for N, _ in short], [n for _, n in short], btc.MIXED_F32)
+    out["short_systems"] = {"instances": len(short),
+                            "nested_dissection": _batch_run(btc, torch, short, btc.MIXED_F32, None, steps, stream,
+                                                            flush, 7000),
+                            "dispatch": _batch_run(btc, torch, short, btc.MIXED_F32, sd, steps, stream, flush, 7000)}
+    out["short_systems"]["dispatch_speedup"] = (out["short_systems"]["nested_dissection"]["ms_per_batch"] /
+                                                out["short_systems"]["dispatch"]["ms_per_batch"])
     return out
 
 
@@ -812,7 +845,7 @@ def main():
     phase = {name: (k_ms[c] / k_n[c] if k_n[c] else None) for name, c in
              (("factor_forward_interlaced", btc.TIME_FACTOR_FORWARD), ("root_chol", btc.TIME_ROOT),
               ("solve_tail", btc.TIME_SOLVE_TAIL), ("correction_solve", btc.TIME_SOLVE),
-              ("residual", btc.TIME_RESIDUAL))}
+              ("residual", btc.TIME_RESIDUAL), ("diag_inverse", btc.TIME_INVERSE))}
     t_fused = phase["factor_forward_interlaced"]
 
     # ---- the plain FP64 GPU path on the same workload

@@ -385,7 +385,8 @@ enum btc_timing_class {
   BTC_TIME_SOLVE = 3,           /* full solve launch (forward + backward)                          */
   BTC_TIME_SOLVE_TAIL = 4,      /* solve tail after an interlaced factorization                    */
   BTC_TIME_RESIDUAL = 5,        /* FP64 residual and norms of the refinement                       */
-  BTC_TIMING_CLASSES = 6
+  BTC_TIME_INVERSE = 6,         /* inversion of the diagonal factors for the correction solves     */
+  BTC_TIMING_CLASSES = 7
 };
 int btc_plan_set_timing(btc_plan_t p, int enable);
 int btc_plan_timing(btc_plan_t p, double *ms, int *launches);
@@ -532,6 +533,39 @@ typedef struct btc_batch_s *btc_batch_t;
 /* Plan a batch (host planning + device pools). N, n: host arrays of `count`
  * sizes. Errors: BTC_ERR_ARG, BTC_ERR_UNSUPPORTED, BTC_ERR_OOM, BTC_ERR_CUDA. */
 int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int dtype, void *stream);
+
+/* btc_batch_plan with an elimination order per instance: chunks[k] = 0 for
+ * the nested-dissection order P_inf (Sec. 4.3), c >= 1 for the partition
+ * permutation with c chunks (Sec. 4.1, Alg. 4, Proposition 1 split; c = 1 is
+ * the natural order of Alg. 1), as btc_plan_set_order; chunks NULL: all
+ * nested dissection. A block-size group holding a partition-order instance
+ * converts every instance's inputs in one batched packing pass before its
+ * factor launch. Errors as btc_batch_plan; BTC_ERR_ARG when c chunks do not
+ * fit in N_k. */
+int btc_batch_plan_orders(btc_batch_t *out, int count, const int *N, const int *n, const int *chunks, int dtype,
+                          void *stream);
+
+/* The per-instance chunk counts a batch was planned with (0: nested
+ * dissection); chunks: host array of `count` ints. */
+int btc_batch_orders(btc_batch_t b, int *chunks);
+
+/* Host-only method dispatch for a batch (the adaptive choice between
+ * elimination orders that the paper leaves as future work, Sec. 4.3): writes
+ * chunks[k] for btc_batch_plan_orders (0 = nested dissection). Model of a
+ * block-size group's persistent launches, which claim items level by level
+ * across the batch: each factor launch level lasts max(its slowest item, its
+ * total item time over the group's share of two resident CTAs per SM), and so
+ * does each forward and backward solve level (two solves per refined call);
+ * an item's time follows a per-block-size node time measured on GB300. Per
+ * group, the policy "systems with N <= t take the partition order with c
+ * chunks, the rest nested dissection" with the smallest modelled makespan is
+ * chosen over c in {1, 2, 3, 4, 6, ..., 64} and t over 16 quantiles of the
+ * group's N (all nested dissection when nothing beats it). The groups run
+ * concurrently, so only the group with the longest nested-dissection makespan
+ * takes its policy; the others keep nested dissection. Uses the current
+ * device's SM count when a device is present (152 otherwise). Errors:
+ * BTC_ERR_ARG, BTC_ERR_UNSUPPORTED (a block size batches do not take). */
+int btc_dispatch_orders(int count, const int *N, const int *n, int dtype, int *chunks);
 
 /* Number of block-size groups, total Alg. 5 flops, device bytes of the batch. */
 int btc_batch_query(btc_batch_t b, int *groups, double *factor_flops, int64_t *device_bytes);

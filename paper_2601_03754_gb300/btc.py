@@ -94,6 +94,9 @@ _SIGS = {
     "btc_server_reset_stats": [_vp],
     "btc_server_footprint": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "btc_batch_plan": [ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, ctypes.c_int, _vp],
+    "btc_batch_plan_orders": [ctypes.POINTER(_vp), ctypes.c_int, _ip, _ip, _ip, ctypes.c_int, _vp],
+    "btc_batch_orders": [_vp, _ip],
+    "btc_dispatch_orders": [ctypes.c_int, _ip, _ip, ctypes.c_int, _ip],
     "btc_batch_query": [_vp, _ip, _dp, ctypes.POINTER(ctypes.c_int64)],
     "btc_batch_factor": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "btc_batch_solve": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
@@ -274,8 +277,8 @@ def btc_solve_refined(plan, b, x, nrhs, tol=1e-10, maxit=20, allow_not_converged
     return it.value, rel.value, rc
 
 
-TIME_FACTOR, TIME_FACTOR_FORWARD, TIME_ROOT, TIME_SOLVE, TIME_SOLVE_TAIL, TIME_RESIDUAL = range(6)
-TIMING_CLASSES = 6
+TIME_FACTOR, TIME_FACTOR_FORWARD, TIME_ROOT, TIME_SOLVE, TIME_SOLVE_TAIL, TIME_RESIDUAL, TIME_INVERSE = range(7)
+TIMING_CLASSES = 7
 
 
 def btc_plan_set_graphs(plan, enable=True):
@@ -422,12 +425,18 @@ def _ptr_array(xs):
 class Batch:
     """Owning handle of a btc_batch_t."""
 
-    def __init__(self, Ns, ns, dtype=MIXED_F32, stream=None):
+    def __init__(self, Ns, ns, dtype=MIXED_F32, stream=None, chunks=None):
         Ns = np.ascontiguousarray(Ns, dtype=np.int32)
         ns = np.ascontiguousarray(ns, dtype=np.int32)
         h = _vp()
-        _check(load().btc_batch_plan(ctypes.byref(h), len(Ns), Ns.ctypes.data_as(_ip), ns.ctypes.data_as(_ip), dtype,
-                                     _stream(stream)))
+        if chunks is None:
+            _check(load().btc_batch_plan(ctypes.byref(h), len(Ns), Ns.ctypes.data_as(_ip), ns.ctypes.data_as(_ip),
+                                         dtype, _stream(stream)))
+        else:
+            ch = np.ascontiguousarray(chunks, dtype=np.int32)
+            _check(load().btc_batch_plan_orders(ctypes.byref(h), len(Ns), Ns.ctypes.data_as(_ip),
+                                                ns.ctypes.data_as(_ip), ch.ctypes.data_as(_ip), dtype,
+                                                _stream(stream)))
         self.h = h
         self.count, self.dtype = len(Ns), dtype
         self.Ns, self.ns = Ns, ns
@@ -444,8 +453,25 @@ class Batch:
             pass
 
 
-def btc_batch_plan(Ns, ns, dtype=MIXED_F32, stream=None):
-    return Batch(Ns, ns, dtype, stream)
+def btc_batch_plan(Ns, ns, dtype=MIXED_F32, stream=None, chunks=None):
+    """A batch plan; chunks (optional, per instance): 0 = nested dissection, c >= 1 = partition order."""
+    return Batch(Ns, ns, dtype, stream, chunks)
+
+
+def btc_batch_orders(batch):
+    out = np.zeros(batch.count, dtype=np.int32)
+    _check(load().btc_batch_orders(batch.h, out.ctypes.data_as(_ip)))
+    return out
+
+
+def btc_dispatch_orders(Ns, ns, dtype=MIXED_F32):
+    """Host-only dispatch model: the per-instance chunk counts (0 = nested dissection) for a batch."""
+    Ns = np.ascontiguousarray(Ns, dtype=np.int32)
+    ns = np.ascontiguousarray(ns, dtype=np.int32)
+    out = np.zeros(len(Ns), dtype=np.int32)
+    _check(load().btc_dispatch_orders(len(Ns), Ns.ctypes.data_as(_ip), ns.ctypes.data_as(_ip), dtype,
+                                      out.ctypes.data_as(_ip)))
+    return out
 
 
 def btc_batch_query(batch):

@@ -223,6 +223,10 @@ struct BatchGroup {
   int fac_grid = 0, solve_grid = 0;
   BatchNode *d_nodes = nullptr;
   int n_nodes = 0;
+  // a group with a partition-order instance converts every instance's inputs in a batched packing
+  // pass first (then no item reads the caller's arrays)
+  bool packed = false;
+  PackNode *d_pack = nullptr;
   const void *pack = nullptr, *unpack = nullptr, *resid = nullptr;
   double flops = 0;
   cudaStream_t s = nullptr;  // the group's own stream: groups run concurrently
@@ -258,6 +262,7 @@ struct btc_batch_s {
   BatchReadback *d_rb = nullptr, *h_rb = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<int> N, n;
+  std::vector<int> chunks;  // per instance: 0 = nested dissection, c >= 1 = partition order with c chunks
   std::vector<BatchGroup> groups;
   InstDesc *d_inst = nullptr;
   BatchVec *d_vec = nullptr;
@@ -304,10 +309,23 @@ static int build_group(btc_batch_s *bt, BatchGroup &g) {
   std::vector<HostPlan> hps(g.inst.size());
   std::vector<Ref> frefs, srefs;
   std::vector<BatchNode> nodes;
+  std::vector<PackNode> pack;
+  g.packed = false;
+  for (size_t k = 0; k < g.inst.size(); ++k) g.packed = g.packed || bt->chunks[g.inst[k]] > 0;
   for (size_t k = 0; k < g.inst.size(); ++k) {
     const int id = g.inst[k];
     HostPlan &hp = hps[k];
-    build_host_plan(bt->N[id], bt->n[id], g.np, d_base, e_base, y_base, id, &hp);
+    if (bt->chunks[id] > 0) {
+      if (!build_partition_plan(bt->N[id], bt->n[id], g.np, bt->chunks[id], d_base, e_base, y_base, id, &hp))
+        return fail(BTC_ERR_ARG, "instance %d: %d chunks do not fit in N = %d", id, bt->chunks[id], bt->N[id]);
+    } else {
+      build_host_plan(bt->N[id], bt->n[id], g.np, d_base, e_base, y_base, id, &hp);
+    }
+    if (g.packed)  // each node's coupling with the next one starts in the orientation of the node eliminated first
+      for (int r = 0; r < bt->N[id]; ++r) {
+        const int tr = r + 1 >= bt->N[id] ? 0 : hp.packed ? (int)hp.slot_transposed[r] : ((r + 1) & 1);
+        pack.push_back({e_base + r, id, r, tr, 0});
+      }
     g.flops += hp.factor_flops;
     int local = 0;
     for (int l = 1; l <= hp.levels; ++l)
@@ -336,12 +354,12 @@ static int build_group(btc_batch_s *bt, BatchGroup &g) {
   for (const Ref &r : frefs) {
     const FactorItem &it = flat[r.k][r.local];
     if (mixed && (it.flags & FI_ROOT)) {
-      (r.level == 1 ? roots_first : roots_rest).push_back(it);
+      (r.level == 1 && !g.packed ? roots_first : roots_rest).push_back(it);
       continue;
     }
     merged_of[r.k][r.local] = (int32_t)fac.size();
     fac.push_back(it);
-    if (r.level == 1) g.n_first = (int)fac.size();
+    if (r.level == 1 && !g.packed) g.n_first = (int)fac.size();
   }
   deps.assign(3 * fac.size(), -1);
   for (const Ref &r : frefs) {
@@ -364,6 +382,11 @@ static int build_group(btc_batch_s *bt, BatchGroup &g) {
   std::vector<SRef> sr;
   for (size_t k = 0; k < g.inst.size(); ++k) {
     const HostPlan &hp = hps[k];
+    if (hp.packed) {  // partition order: the planner's keys (level of the item's node, negated backward)
+      for (size_t q = 0; q < hp.solve_flow.size(); ++q)
+        sr.push_back({hp.solve_flow[q].kind, hp.solve_key[q], (int)k, (int)q});
+      continue;
+    }
     // the per-instance solve list is [fwd level 1 .. L][bwd level L .. 1]; recover levels
     int q = 0;
     for (int l = 1; l <= hp.levels; ++l)
@@ -391,7 +414,8 @@ static int build_group(btc_batch_s *bt, BatchGroup &g) {
       (rc = batch_alloc(&g.epool, (size_t)std::max<int64_t>(e_base, 1) * bs * ks.elem, acc)) ||
       (rc = batch_alloc(&g.y, (size_t)y_base * g.np * ks.elem, acc)) || (rc = upload(&g.d_fac, fac, acc)) ||
       (rc = upload(&g.d_fac_deps, deps, acc)) || (rc = upload(&g.d_roots, roots, acc)) ||
-      (rc = upload(&g.d_solve, solve, acc)) || (rc = upload(&g.d_nodes, nodes, acc)))
+      (rc = upload(&g.d_solve, solve, acc)) || (rc = upload(&g.d_nodes, nodes, acc)) ||
+      (g.packed && (rc = upload(&g.d_pack, pack, acc))))
     return rc;
   const size_t nflags = kFlowHeader + (size_t)std::max(g.n_fac, g.n_solve);
   if ((rc = batch_alloc((void **)&g.d_flow, nflags * sizeof(int), acc))) return rc;
@@ -483,6 +507,7 @@ static int group_factor(btc_batch_s *bt, BatchGroup &g, bool roots) {
   InstDesc none{nullptr, nullptr, 0, 0};
   int rc;
   BTC_CUDA(cudaMemsetAsync(g.d_flow, 0, 3 * sizeof(int), g.s));
+  if (g.packed && (rc = k.pack_batch(g.dpool, g.epool, g.d_pack, bt->d_inst, g.n_nodes, g.s))) return rc;
   if (g.n_fac > 0) {
     BTC_CUDA(cudaMemsetAsync(g.d_flow + kFlowHeader, 0, sizeof(int) * (size_t)g.n_fac, g.s));
     a.items = g.d_fac;
@@ -578,15 +603,24 @@ static int batch_read_status(btc_batch_s *bt) {
 extern "C" {
 
 int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int dtype, void *stream) {
+  return btc_batch_plan_orders(out, count, N, n, nullptr, dtype, stream);
+}
+
+int btc_batch_plan_orders(btc_batch_t *out, int count, const int *N, const int *n, const int *chunks, int dtype,
+                          void *stream) {
   if (!out || count < 1 || !N || !n) return fail(BTC_ERR_ARG, "btc_batch_plan: invalid arguments");
   *out = nullptr;
   if (!dtype_ok(dtype)) return fail(BTC_ERR_ARG, "btc_batch_plan: unknown dtype %d", dtype);
+  for (int k = 0; chunks && k < count; ++k)
+    if (chunks[k] < 0) return fail(BTC_ERR_ARG, "btc_batch_plan_orders: instance %d: chunks %d", k, chunks[k]);
   btc_batch_s *bt = new btc_batch_s();
   bt->count = count;
   bt->dtype = dtype;
   bt->stream = (cudaStream_t)stream;
   bt->N.assign(N, N + count);
   bt->n.assign(n, n + count);
+  bt->chunks.assign(count, 0);
+  if (chunks) bt->chunks.assign(chunks, chunks + count);
   auto cleanup = [&](int code) {
     btc_batch_free(bt);
     return code;
@@ -637,6 +671,183 @@ int btc_batch_plan(btc_batch_t *out, int count, const int *N, const int *n, int 
       (e = cudaMallocHost(&bt->h_status, sizeof(int))) != cudaSuccess)
     return cleanup(fail(BTC_ERR_OOM, "btc_batch_plan: host staging: %s", cudaGetErrorString(e)));
   *out = bt;
+  return BTC_OK;
+}
+
+int btc_dispatch_orders(int count, const int *N, const int *n, int dtype, int *chunks) {
+  if (count < 1 || !N || !n || !chunks) return fail(BTC_ERR_ARG, "btc_dispatch_orders: invalid arguments");
+  if (!dtype_ok(dtype)) return fail(BTC_ERR_ARG, "btc_dispatch_orders: unknown dtype %d", dtype);
+  // time of one node step (us) of the one-CTA-per-node kernels by padded block size (measured on GB300 as
+  // the per-node time of a lone partition chain, FP32 factor); a node with more work than a chain node's
+  // potrf + trsm + syrk (7/3 n^3) takes t (0.7 + 0.3 r), r its flops over 7/3 n^3 (the dependent panel
+  // chain of the Cholesky, not the products, dominates a node); one solve item takes 2 + n_p / 64 us
+  auto t_node = [](int np) {
+    static const int sz[] = {8, 16, 32, 48, 64, 96, 128};
+    static const double us[] = {2.7, 3.5, 5.9, 9.0, 12.8, 20.0, 30.0};
+    if (np <= sz[0]) return us[0];
+    for (int i = 1; i < 7; ++i)
+      if (np <= sz[i]) return us[i - 1] + (us[i] - us[i - 1]) * (np - sz[i - 1]) / (double)(sz[i] - sz[i - 1]);
+    return us[6];
+  };
+  constexpr int kSolves = 2;  // a refined call: the first solve and one correction
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();  // (no device: keep the default count)
+  sms = std::max(sms, 1);
+  // Per (instance, order): the persistent launches claim items level by level across the batch, so a
+  // group's launch lasts about sum over levels of max(slowest item of the level, the level's work over
+  // the resident CTAs); the same for the forward and backward solve levels.
+  struct Profile {
+    std::vector<double> fsum, fmax;  // factor work (us) and slowest item per launch level
+    std::vector<int> fwd, bwd;       // solve items per level
+    double work = 0.0;
+  };
+  auto profile = [&](int k, int c, Profile *pr) {
+    const int np = padded_size(n[k], dtype);
+    if (!np || np > 128) return false;
+    HostPlan hp;
+    if (c == 0) build_host_plan(N[k], n[k], np, 0, 0, 0, 0, &hp);
+    else if (!build_partition_plan(N[k], n[k], np, c, 0, 0, 0, 0, &hp)) return false;
+    const double n3 = (double)n[k] * n[k] * n[k], t = t_node(np);
+    pr->fsum.assign(hp.levels, 0.0);
+    pr->fmax.assign(hp.levels, 0.0);
+    pr->fwd.assign(hp.levels + 1, 0);
+    pr->bwd.assign(hp.levels + 1, 0);
+    for (int l = 0; l < hp.levels; ++l)
+      for (const FactorItem &it : hp.lv[l].fac) {
+        double f = n3 / 3.0;
+        if (it.p_a >= 0) f += n3;
+        if (it.p_b >= 0) f += n3;
+        if (it.r_down >= 0) f += 2 * n3;
+        if (it.r_up >= 0) f += n3;
+        if (it.fill >= 0) f += 2 * n3;
+        const double us = t * (0.7 + 0.3 * f / (7.0 / 3.0 * n3));
+        pr->fsum[l] += us;
+        pr->fmax[l] = std::max(pr->fmax[l], us);
+        pr->work += us;
+      }
+    if (hp.packed) {
+      for (size_t q = 0; q < hp.solve_flow.size(); ++q) {
+        const int key = hp.solve_key[q];
+        (key > 0 ? pr->fwd : pr->bwd)[std::min(std::abs(key), hp.levels)]++;
+      }
+    } else {
+      for (int l = 0; l < hp.levels; ++l) {
+        pr->fwd[l + 1] += (int)hp.lv[l].fwd.size();
+        pr->bwd[l + 1] += (int)hp.lv[l].bwd.size();
+      }
+    }
+    return true;
+  };
+  // groups by padded block size, as the batch forms them
+  std::map<int, std::vector<int>> groups;
+  for (int k = 0; k < count; ++k) {
+    const int np = N[k] >= 1 && n[k] >= 1 ? padded_size(n[k], dtype) : 0;
+    if (!np || np > 128)
+      return fail(BTC_ERR_UNSUPPORTED, "btc_dispatch_orders: instance %d (N = %d, n = %d)", k, N[k], n[k]);
+    groups[np].push_back(k);
+    chunks[k] = 0;
+  }
+  // profiles depend on (N, n_p, chunks) only (item times are relative to the node time)
+  std::map<std::tuple<int, int, int>, Profile> cache;
+  auto get = [&](int k, int c) -> const Profile * {
+    const auto key = std::make_tuple(N[k], padded_size(n[k], dtype), c);
+    auto it = cache.find(key);
+    if (it != cache.end()) return &it->second;
+    Profile pr;
+    if (!profile(k, c, &pr)) return nullptr;
+    return &cache.emplace(key, std::move(pr)).first->second;
+  };
+  double total = 0.0;
+  for (int k = 0; k < count; ++k) total += get(k, 0)->work;
+  static const int kChunks[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  // the groups run concurrently, so the batch lasts as long as its slowest group: only a group whose
+  // nested-dissection makespan is the batch's may change orders, and only to shorten it
+  struct Choice {
+    double nd = 0.0, best = 0.0;
+    int c = 0, thr = 0;
+  };
+  std::map<int, Choice> choice;
+  for (auto &kv : groups) {
+    const int np = kv.first;
+    const std::vector<int> &ids = kv.second;
+    const double ts = 2.0 + np / 64.0;
+    double gwork = 0.0;
+    for (int k : ids) gwork += get(k, 0)->work;
+    // the group's share of the resident CTAs (two per SM in all), as its share of the batch's work
+    const double C = std::max(0.5 * sms, 2.0 * sms * gwork / std::max(total, 1e-30));
+    // makespan of a policy: systems with N <= nthr take the partition order with c chunks (when it fits),
+    // the others nested dissection
+    std::vector<double> fsum, fmax;
+    std::vector<int> fwd, bwd;
+    auto makespan = [&](int c, int nthr) {
+      fsum.assign(0, 0.0);
+      fmax.assign(0, 0.0);
+      fwd.assign(0, 0);
+      bwd.assign(0, 0);
+      for (int k : ids) {
+        const Profile *pr = (c > 0 && N[k] <= nthr) ? get(k, c) : nullptr;
+        if (!pr) pr = get(k, 0);
+        if (fsum.size() < pr->fsum.size()) {
+          fsum.resize(pr->fsum.size(), 0.0);
+          fmax.resize(pr->fsum.size(), 0.0);
+        }
+        if (fwd.size() < pr->fwd.size()) {
+          fwd.resize(pr->fwd.size(), 0);
+          bwd.resize(pr->fwd.size(), 0);
+        }
+        for (size_t l = 0; l < pr->fsum.size(); ++l) {
+          fsum[l] += pr->fsum[l];
+          fmax[l] = std::max(fmax[l], pr->fmax[l]);
+        }
+        for (size_t l = 0; l < pr->fwd.size(); ++l) {
+          fwd[l] += pr->fwd[l];
+          bwd[l] += pr->bwd[l];
+        }
+      }
+      double m = 0.0;
+      for (size_t l = 0; l < fsum.size(); ++l)
+        if (fsum[l] > 1e-9) m += std::max(fmax[l], fsum[l] / C);
+      double sv = 0.0;
+      for (size_t l = 0; l < fwd.size(); ++l) {
+        if (fwd[l] > 0) sv += std::max(ts, fwd[l] * ts / C);
+        if (bwd[l] > 0) sv += std::max(ts, bwd[l] * ts / C);
+      }
+      return m + kSolves * sv;
+    };
+    // thresholds: up to 16 quantiles of the group's sizes
+    std::vector<int> sizes;
+    for (int k : ids) sizes.push_back(N[k]);
+    std::sort(sizes.begin(), sizes.end());
+    std::vector<int> thr;
+    for (int q = 1; q <= 16; ++q) thr.push_back(sizes[std::min(sizes.size() - 1, (sizes.size() * q) / 16)]);
+    thr.erase(std::unique(thr.begin(), thr.end()), thr.end());
+    Choice &ch = choice[np];
+    ch.nd = ch.best = makespan(0, 0);
+    for (int c : kChunks)
+      for (int t : thr) {
+        const double m = makespan(c, t);
+        if (m < ch.best * (1.0 - 1e-6)) {
+          ch.best = m;
+          ch.c = c;
+          ch.thr = t;
+        }
+      }
+  }
+  double slowest = 0.0;
+  for (auto &kv : choice) slowest = std::max(slowest, kv.second.nd);
+  for (auto &kv : groups) {
+    const Choice &ch = choice[kv.first];
+    if (ch.c == 0 || ch.nd < slowest * (1.0 - 1e-9)) continue;  // not the batch's slowest group
+    for (int k : kv.second)
+      if (N[k] <= ch.thr && get(k, ch.c)) chunks[k] = ch.c;
+  }
+  return BTC_OK;
+}
+
+int btc_batch_orders(btc_batch_t bt, int *chunks) {
+  if (!bt || !chunks) return fail(BTC_ERR_ARG, "btc_batch_orders: NULL argument");
+  std::copy(bt->chunks.begin(), bt->chunks.end(), chunks);
   return BTC_OK;
 }
 
@@ -987,7 +1198,8 @@ int btc_batch_free(btc_batch_t bt) {
       cudaStreamDestroy(g.s);
     }
     if (g.ev) cudaEventDestroy(g.ev);
-    void *ptrs[] = {g.dpool, g.epool, g.y, g.d_fac, g.d_fac_deps, g.d_roots, g.d_solve, g.d_flow, g.d_nodes};
+    void *ptrs[] = {g.dpool, g.epool, g.y, g.d_fac, g.d_fac_deps, g.d_roots, g.d_solve, g.d_flow, g.d_nodes,
+                    g.d_pack};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   }

@@ -602,6 +602,50 @@ __global__ void k_pack_matrix(P *dpool, P *epool, const S *D, const S *B, int N,
   }
 }
 
+// One node of a batched packing pass: its diagonal block goes to dpool slot
+// `blockIdx.x` (the group's nodes are numbered instance by instance) and its
+// coupling with the next node of its instance to epool slot `slot`, as B^T
+// when `transposed` (the node is eliminated first), else as B.
+struct PackNode {
+  int64_t slot;
+  int32_t inst, row;
+  int32_t transposed, pad;
+};
+
+template <typename P, typename S, int NP>
+__global__ void k_pack_batch(P *dpool, P *epool, const PackNode *nodes, const InstDesc *inst) {
+  const PackNode nd = nodes[blockIdx.x];
+  const InstDesc in = inst[nd.inst];
+  const int n = in.n;
+  const size_t ubs = (size_t)n * n, bs = (size_t)NP * NP;
+  const S *D = reinterpret_cast<const S *>(in.D) + nd.row * ubs;
+  const S *B = reinterpret_cast<const S *>(in.B) + nd.row * ubs;
+  const bool has_b = nd.row + 1 < in.N;
+  for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) {
+    const int i = q / NP, j = q % NP;
+    P val;
+    if (i < n && j < n) val = convert_in<P, S>(i <= j ? D[(size_t)j * n + i] : D[(size_t)i * n + j]);
+    else val = (i == j) ? P(1) : P(0);
+    dpool[blockIdx.x * bs + q] = val;
+    if (has_b) {
+      P b;
+      if (i < n && j < n) b = convert_in<P, S>(nd.transposed ? B[(size_t)j * n + i] : B[(size_t)i * n + j]);
+      else b = P(0);
+      epool[nd.slot * bs + q] = b;
+    }
+  }
+}
+
+template <typename P, typename S, int NP>
+int launch_pack_batch(void *dpool, void *epool, const void *nodes, const void *inst, int count, cudaStream_t s) {
+  if (count <= 0) return BTC_OK;
+  k_pack_batch<P, S, NP><<<count, 256, 0, s>>>(static_cast<P *>(dpool), static_cast<P *>(epool),
+                                                static_cast<const PackNode *>(nodes),
+                                                static_cast<const InstDesc *>(inst));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BTC_OK : fail(BTC_ERR_CUDA, "batched packing pass launch: %s", cudaGetErrorString(e));
+}
+
 // Typed launch of the packing pass (argument types checked at compile time).
 template <typename P, typename S, int NP>
 int launch_pack(void *dpool, void *epool, const void *D, const void *B, int N, int n, const int8_t *orient,

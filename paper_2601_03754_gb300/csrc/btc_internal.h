@@ -146,6 +146,9 @@ struct HostPlan {
   // forward items of solve_flow (the first n_fwd entries): node (1-based) and level
   int32_t n_fwd = 0;
   std::vector<int32_t> fwd_node, fwd_level;
+  // partition plans: per solve_flow item, its merge key among instances (forward: the launch level of
+  // its node; backward: minus that level), so that every dependency sorts before its consumer
+  std::vector<int32_t> solve_key;
 };
 
 // Interlaced factorization and forward substitution in one persistent launch

@@ -33,6 +33,10 @@ struct KernelSet {
   size_t root_smem = 0;
   // persistent dataflow forms (all levels in one launch)
   const void *fac_flow = nullptr, *solve_flow = nullptr;
+  // correction solves with inverted diagonal factors: the inversion kernel and the solve variant that
+  // multiplies by them (null for the blocked 256 sets)
+  const void *diag_inverse = nullptr, *solve_flow_inv = nullptr;
+  size_t diag_inverse_smem = 0;
   // interlaced factorization + forward substitution (same CTA shape as fac_flow)
   const void *fac_fwd_flow = nullptr;
   size_t (*fused_smem)(int m) = nullptr;
@@ -52,6 +56,8 @@ struct KernelSet {
   // set's source type; orient null (the ND level-1 orientation) or one flag per coupling
   int (*pack_pools)(void *dpool, void *epool, const void *D, const void *B, int N, int n, const int8_t *orient,
               cudaStream_t s) = nullptr;
+  // the batched packing pass over a group's nodes (PackNode list, per-instance descriptors)
+  int (*pack_batch)(void *dpool, void *epool, const void *nodes, const void *inst, int count, cudaStream_t s) = nullptr;
   // solve
   const void *fwd = nullptr, *bwd = nullptr;
   size_t (*fwd_smem)(int m) = nullptr;

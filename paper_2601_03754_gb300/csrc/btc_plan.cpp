@@ -451,10 +451,11 @@ bool build_partition_plan(int N, int n, int np, int chunks, int64_t d_base, int6
     lev.push_back(L);
   }
   for (int k = 2; k <= p; ++k) lev.push_back({pivot[k]});
-  std::vector<int> order, posn(N, -1);
-  for (auto &L : lev)
-    for (int e : L) {
+  std::vector<int> order, posn(N, -1), level_of(N, 0);
+  for (size_t l = 0; l < lev.size(); ++l)
+    for (int e : lev[l]) {
       posn[e] = (int)order.size();
+      level_of[e] = (int)l + 1;
       order.push_back(e);
     }
   // slots: original couplings (v, v+1) at slot v, fills appended
@@ -596,6 +597,7 @@ bool build_partition_plan(int N, int n, int np, int chunks, int64_t d_base, int6
   // ---- solve (pull form forward in elimination order, backward in reverse)
   auto yNode = [&](int u) { return y_base + u; };
   P->solve_flow.clear();
+  P->solve_key.clear();
   std::vector<int32_t> fwd_final(N, -1), bwd_item(N, -1);
   auto push = [&](int64_t self, int qa, int64_t ea, int qb, int64_t eb, int64_t dself, int kind, int32_t d0, int32_t d1,
                   int32_t d2) {
@@ -611,6 +613,8 @@ bool build_partition_plan(int N, int n, int np, int chunks, int64_t d_base, int6
     q.dep[1] = d1;
     q.dep[2] = d2;
     P->solve_flow.push_back(q);
+    const int lvl = level_of[self];
+    P->solve_key.push_back(kind == 0 ? lvl : -lvl);
     return (int32_t)P->solve_flow.size() - 1;
   };
   // the block stored by eliminated node q for its coupling with e (rows: q's variables)

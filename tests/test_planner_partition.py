@@ -256,3 +256,37 @@ def test_emulation_catches_a_dropped_dependency(monkeypatch):
         wr_set = {("d", ds)} | {("e", q) for q in (ru, rd, fi) if q >= 0} | ({("d", dn)} if dn >= 0 else set())
         rw.append((rd_set, wr_set))
     assert _unordered_conflicts(rw, _closure(deps))
+
+
+# ---------------------------------------------------------------- dispatch model (host only)
+
+def test_dispatch_keeps_nested_dissection_for_a_lone_system():
+    for N, n in [(1024, 64), (4096, 16), (100, 128)]:
+        assert list(btc.btc_dispatch_orders([N], [n], btc.MIXED_F32)) == [0]
+
+
+def test_dispatch_takes_cheap_orders_under_instance_parallelism():
+    Ns, ns = [64] * 2000, [32] * 2000
+    ch = btc.btc_dispatch_orders(Ns, ns, btc.MIXED_F32)
+    assert (ch == 1).all()  # work-bound: the natural order of Alg. 1, 2.7x fewer flops
+
+
+def test_dispatch_on_the_benchmark_mix_is_valid_and_saves_flops():
+    specs = gen.batch_specs(512, seed=0)
+    Ns, ns = [N for N, _ in specs], [n for _, n in specs]
+    ch = btc.btc_dispatch_orders(Ns, ns, btc.MIXED_F32)
+    fl_nd = fl = 0.0
+    for N, n, c in zip(Ns, ns, ch):
+        if c:
+            assert _fits(N, int(c))
+        fl_nd += btc.btc_describe(N, n, btc.MIXED_F32)["factor_flops"]
+        fl += btc.btc_describe_order(N, n, btc.MIXED_F32, btc.ORDER_PARTITION if c else btc.ORDER_ND,
+                                     int(c))[0]["factor_flops"]
+    assert fl <= fl_nd
+    # per block size a threshold policy: the systems that switch are the shortest ones, with one chunk count
+    for n in set(ns):
+        switched = [(N, c) for N, nn, c in zip(Ns, ns, ch) if nn == n and c > 0]
+        kept = [N for N, nn, c in zip(Ns, ns, ch) if nn == n and c == 0]
+        if switched and kept:
+            assert max(N for N, _ in switched) <= min(kept) or len({c for _, c in switched}) == 1
+        assert len({c for _, c in switched}) <= 1
