@@ -407,9 +407,10 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
     delta = 1e-2; mixed FP32 factor + FP64 refinement to 1e-10, beside the plain FP64 batch. A step is
     btc_batch_factor_solve_refined: after the first (tuning) call, one captured graph with the
     refinement loop on the device. The tuned launch configuration of every block-size group is
-    reported. Method dispatch (btc_dispatch_orders) is measured against nested dissection on this mix
-    and on a throughput mix of 600 short systems (n in {16, 32}, N log-uniform in [32, 128]), and a
-    forced partition order on the benchmark mix's n <= 16 systems shows what the model avoids."""
+    reported. Method dispatch (btc_dispatch_orders) is measured against nested dissection on this mix,
+    on a throughput mix of 600 short systems (n in {16, 32}, N log-uniform in [32, 128]) and on a wide
+    batch of 2000 systems N=64, n=32; a forced partition order on the benchmark mix's n <= 16 systems
+    shows what the model avoids."""
     specs = gen.batch_specs(512, seed=0)
     Ns = [N for N, _ in specs]
     ns = [n for _, n in specs]
@@ -431,6 +432,14 @@ def batched_measure(btc, gen, torch, steps, stream, flush):
                             "dispatch": _batch_run(btc, torch, short, btc.MIXED_F32, sd, steps, stream, flush, 7000)}
     out["short_systems"]["dispatch_speedup"] = (out["short_systems"]["nested_dissection"]["ms_per_batch"] /
                                                 out["short_systems"]["dispatch"]["ms_per_batch"])
+    # a wide batch of identical short systems, where the model takes the partition order
+    wide = [(64, 32)] * 2000
+    wd = btc.btc_dispatch_orders([N for N, _ in wide], [n for _, n in wide], btc.MIXED_F32)
+    out["wide_batch_2000xN64n32"] = {
+        "nested_dissection": _batch_run(btc, torch, wide, btc.MIXED_F32, None, steps, stream, flush, 20000),
+        "dispatch": _batch_run(btc, torch, wide, btc.MIXED_F32, wd, steps, stream, flush, 20000)}
+    w = out["wide_batch_2000xN64n32"]
+    w["dispatch_speedup"] = w["nested_dissection"]["ms_per_batch"] / w["dispatch"]["ms_per_batch"]
     return out
 
 
@@ -845,7 +854,7 @@ def main():
     phase = {name: (k_ms[c] / k_n[c] if k_n[c] else None) for name, c in
              (("factor_forward_interlaced", btc.TIME_FACTOR_FORWARD), ("root_chol", btc.TIME_ROOT),
               ("solve_tail", btc.TIME_SOLVE_TAIL), ("correction_solve", btc.TIME_SOLVE),
-              ("residual", btc.TIME_RESIDUAL), ("diag_inverse", btc.TIME_INVERSE))}
+              ("residual", btc.TIME_RESIDUAL))}
     t_fused = phase["factor_forward_interlaced"]
 
     # ---- the plain FP64 GPU path on the same workload

@@ -385,8 +385,7 @@ enum btc_timing_class {
   BTC_TIME_SOLVE = 3,           /* full solve launch (forward + backward)                          */
   BTC_TIME_SOLVE_TAIL = 4,      /* solve tail after an interlaced factorization                    */
   BTC_TIME_RESIDUAL = 5,        /* FP64 residual and norms of the refinement                       */
-  BTC_TIME_INVERSE = 6,         /* inversion of the diagonal factors for the correction solves     */
-  BTC_TIMING_CLASSES = 7
+  BTC_TIMING_CLASSES = 6
 };
 int btc_plan_set_timing(btc_plan_t p, int enable);
 int btc_plan_timing(btc_plan_t p, double *ms, int *launches);
@@ -554,8 +553,9 @@ int btc_batch_orders(btc_batch_t b, int *chunks);
  * chunks[k] for btc_batch_plan_orders (0 = nested dissection). Model of a
  * block-size group's persistent launches, which claim items level by level
  * across the batch: each factor launch level lasts max(its slowest item, its
- * total item time over the group's share of two resident CTAs per SM), and so
- * does each forward and backward solve level (two solves per refined call);
+ * total item time over the group's share of two resident CTAs per SM) plus
+ * the latency of one dependency hop (2 us), and so does each forward and
+ * backward solve level (two solves per refined call);
  * an item's time follows a per-block-size node time measured on GB300. Per
  * group, the policy "systems with N <= t take the partition order with c
  * chunks, the rest nested dissection" with the smallest modelled makespan is

@@ -277,8 +277,8 @@ def btc_solve_refined(plan, b, x, nrhs, tol=1e-10, maxit=20, allow_not_converged
     return it.value, rel.value, rc
 
 
-TIME_FACTOR, TIME_FACTOR_FORWARD, TIME_ROOT, TIME_SOLVE, TIME_SOLVE_TAIL, TIME_RESIDUAL, TIME_INVERSE = range(7)
-TIMING_CLASSES = 7
+TIME_FACTOR, TIME_FACTOR_FORWARD, TIME_ROOT, TIME_SOLVE, TIME_SOLVE_TAIL, TIME_RESIDUAL = range(6)
+TIMING_CLASSES = 6
 
 
 def btc_plan_set_graphs(plan, enable=True):

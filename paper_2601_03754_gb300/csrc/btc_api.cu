@@ -175,13 +175,6 @@ struct btc_plan_s {
   bool graphs = true;
   cudaStream_t gstream = nullptr, gstream2 = nullptr;
   cudaEvent_t gevent = nullptr;
-  // inverted diagonal factors for the correction solves (mixed dtypes): [N][np][np], valid once the
-  // inversion after the last factorization is queued; the graph runs it on a side branch
-  void *d_inv = nullptr;
-  bool inv_valid = false;
-  int inv_grid = 0;
-  cudaStream_t istream = nullptr;
-  cudaEvent_t iev_fork = nullptr, iev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<double> gkey;
   unsigned long long *trace_fac = nullptr, *trace_solve = nullptr;  // caller-owned trace buffers
@@ -633,7 +626,6 @@ static int tiled_factor(btc_plan_s *p, const void *D, const void *B) {
   p->B = B;
   p->factored = true;
   p->anorm_valid = false;
-  p->inv_valid = false;
   return BTC_OK;
 }
 
@@ -696,7 +688,6 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   p->B = B;
   p->factored = true;
   p->anorm_valid = false;
-  p->inv_valid = false;
   return BTC_OK;
 }
 
@@ -882,38 +873,6 @@ static bool can_interlace(const btc_plan_s *p, int m) {
 }
 
 
-// Invert every diagonal factor block (U_v^{-1} into d_inv) on the plan's stream.
-static int launch_inverse(btc_plan_s *p) {
-  const KernelSet &k = *p->ks;
-  KernelTimer timer(p, BTC_TIME_INVERSE);
-  int rc = launch_n(k.diag_inverse, std::min(p->inv_grid, p->N), 256, k.diag_inverse_smem, p->stream, p->d_inv,
-                    (const void *)p->dpool, p->N);
-  if (rc == BTC_OK) p->inv_valid = true;
-  return rc;
-}
-
-// A correction solve of the refinement: with inverted diagonal factors (the triangular solves of
-// Alg. 7 become products), inverting them first if the factor is new; otherwise run_solve.
-static int run_correction(btc_plan_s *p, int m) {
-  const KernelSet &k = *p->ks;
-  if (!p->d_inv || !(p->sched == BTC_SCHED_FLOW || p->hp.packed)) return run_solve(p, m);
-  int rc;
-  if (!p->inv_valid && (rc = launch_inverse(p))) return rc;
-  SolveArgs a;
-  a.dpool = p->dpool;
-  a.epool = p->epool;
-  a.y = p->d_y;
-  a.m = m;
-  a.inv = p->d_inv;
-  a.items = p->d_solve_flow;
-  a.count = p->n_solve;
-  KernelTimer timer(p, BTC_TIME_SOLVE);
-  BTC_CUDA(cudaMemsetAsync(p->d_flow + 1, 0, sizeof(int), p->stream));
-  BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_solve, p->stream));
-  return launch_n(k.solve_flow_inv, std::min(p->solve_grid, p->n_solve), kSolveThreads, k.fwd_smem(m), p->stream, a,
-                  flow_sync(p, 1));
-}
-
 // FP64 iterative refinement, chunk by chunk of at most max_cols columns:
 // x = solve(b), then while ||b - Psi x|| > tol ||Psi|| ||x||: x += solve(r).
 // first_done: the first chunk of x already holds its first solve (interlaced
@@ -970,7 +929,7 @@ static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, dou
         break;
       }
       if (it >= maxit) break;
-      if ((rc = run_correction(p, m))) return rc;
+      if ((rc = run_solve(p, m))) return rc;
       if ((rc = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
                          (const void *)p->d_y, p->N, p->n, p->np, m, nrhs, c0, base, accumulate)))
         return rc;
@@ -1013,11 +972,6 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
     BTC_CUDA(cudaStreamCreateWithFlags(&p->gstream2, cudaStreamNonBlocking));
     BTC_CUDA(cudaEventCreateWithFlags(&p->gevent, cudaEventDisableTiming));
   }
-  if (p->d_inv && !p->istream) {
-    BTC_CUDA(cudaStreamCreateWithFlags(&p->istream, cudaStreamNonBlocking));
-    BTC_CUDA(cudaEventCreateWithFlags(&p->iev_fork, cudaEventDisableTiming));
-    BTC_CUDA(cudaEventCreateWithFlags(&p->iev_join, cudaEventDisableTiming));
-  }
   const KernelSet &k = *p->ks;
   cudaStream_t user = p->stream;
   cudaGraph_t g = nullptr;
@@ -1036,18 +990,7 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
     int r;
     if ((r = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)b, p->N,
                       p->n, p->np, m, m, c0, base)) ||
-        (r = factor_impl(p, D, B, m)))
-      return r;
-    if (p->d_inv) {  // the diagonal inversion on a side branch, joined before the correction loop
-      BTC_CUDA(cudaEventRecord(p->iev_fork, p->gstream));
-      BTC_CUDA(cudaStreamWaitEvent(p->istream, p->iev_fork, 0));
-      p->stream = p->istream;
-      r = launch_inverse(p);
-      p->stream = p->gstream;
-      if (r) return r;
-      BTC_CUDA(cudaEventRecord(p->iev_join, p->istream));
-    }
-    if ((r = run_solve_tail(p, m)) ||
+        (r = factor_impl(p, D, B, m)) || (r = run_solve_tail(p, m)) ||
         (r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
                       (const void *)p->d_y, p->N, p->n, p->np, m, m, c0, base, assign)))
       return r;
@@ -1057,7 +1000,6 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
                       p->d_norms, one)) ||
         (r = launch_n((const void *)&k_refine_decide, 1, 1, 0, p->stream, p->d_rb, tol, maxit, one, h)))
       return r;
-    if (p->d_inv) BTC_CUDA(cudaStreamWaitEvent(p->gstream, p->iev_join, 0));
     // the correction loop as a while node
     const cudaGraphNode_t *deps = nullptr;
     const cudaGraphEdgeData *edata = nullptr;
@@ -1075,7 +1017,7 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
     BTC_CUDA(cudaStreamUpdateCaptureDependencies(p->gstream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
     BTC_CUDA(cudaStreamBeginCaptureToGraph(p->gstream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     p->stream = p->gstream2;
-    r = run_correction(p, m);
+    r = run_solve(p, m);
     if (!r)
       r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x, (const void *)p->d_y,
                    p->N, p->n, p->np, m, m, c0, base, accumulate);
@@ -1097,7 +1039,6 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
   rc = body_cuda();
   e = cudaStreamEndCapture(p->gstream, &g);
   p->stream = user;
-  p->inv_valid = false;  // the inversion is in the graph: valid once the graph has run
   if (rc == BTC_OK && e != cudaSuccess) rc = fail(BTC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   if (rc == BTC_OK && (e = cudaGraphInstantiate(&p->gexec, g, 0)) != cudaSuccess)
     rc = fail(BTC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -1133,7 +1074,6 @@ static int refine_graph_run(btc_plan_s *p, const void *D, const void *B, const d
   p->B = B;
   p->factored = true;
   p->anorm_valid = true;
-  p->inv_valid = p->d_inv != nullptr;
   int blk, col;
   int rc = decode_info(p, &blk, &col);
   if (rc == BTC_ERR_TIMEOUT) return fail(rc, "factorization failed: a bounded device-side wait gave up");
@@ -1161,8 +1101,7 @@ int btc_describe(int N, int n, int dtype, btc_plan_info *info) {
   build_host_plan(N, n, np, 0, 0, 0, 0, &hp);
   fill_info(hp, dtype, info);
   const double pe = dtype == BTC_F64 ? 8.0 : 4.0;
-  const int inv_blocks = dtype_mixed(dtype) && np <= 128 ? N : 0;  // inverted diagonal factors
-  info->device_bytes = (int64_t)(pe * (double)np * np * (N + inv_blocks + std::max<int64_t>(hp.offdiag, 1)) +
+  info->device_bytes = (int64_t)(pe * (double)np * np * (N + std::max<int64_t>(hp.offdiag, 1)) +
                                  pe * (double)N * np * kMaxCols);
   return BTC_OK;
 }
@@ -1198,8 +1137,7 @@ int btc_describe_order(int N, int n, int dtype, int order, int chunks, btc_plan_
   if (info) {
     fill_info(hp, dtype, info);
     const double pe = dtype == BTC_F64 ? 8.0 : 4.0;
-    const int inv_blocks = dtype_mixed(dtype) && np <= 128 ? N : 0;
-    info->device_bytes = (int64_t)(pe * (double)np * np * (N + inv_blocks + std::max<int64_t>(hp.offdiag, 1)) +
+    info->device_bytes = (int64_t)(pe * (double)np * np * (N + std::max<int64_t>(hp.offdiag, 1)) +
                                    pe * (double)N * np * kMaxCols);
   }
   int t = 0;
@@ -1403,7 +1341,6 @@ static int plan_schedule(btc_plan_s *p) {
       (rc = set_smem(ks.fac_flow, ks.fac_smem)) || (rc = set_smem(ks.fac_flow_rl, ks.fac_smem)) ||
       (rc = set_smem(ks.fac_rl, ks.fac_smem)) || (rc = set_smem(ks.root_rl, ks.root_smem)) ||
       (rc = set_smem(ks.solve_flow, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
-      (rc = set_smem(ks.solve_flow_inv, ks.fwd_smem(std::min(kMaxCols, ks.max_cols)))) ||
       (rc = set_smem(ks.fac_fwd_flow, ks.fused_smem(std::min(kMaxCols, ks.max_cols)))))
     return cleanup(rc);
   {
@@ -1498,21 +1435,6 @@ int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
   if ((e = cudaMemset(p->d_rb, 0, sizeof(Readback))) != cudaSuccess)
     return cleanup(fail(BTC_ERR_CUDA, "btc_plan: %s", cudaGetErrorString(e)));
   p->fixed_bytes = (int64_t)(dbytes + (size_t)N * np * kMaxCols * ks.elem);
-  if (ks.solve_flow_inv && dtype_mixed(dtype)) {  // inverted diagonal factors for the correction solves
-    if ((e = cudaMalloc(&p->d_inv, dbytes)) != cudaSuccess)
-      return cleanup(fail(e == cudaErrorMemoryAllocation ? BTC_ERR_OOM : BTC_ERR_CUDA, "btc_plan: allocation: %s",
-                          cudaGetErrorString(e)));
-    p->fixed_bytes += (int64_t)dbytes;
-    int occ = 0;
-    if ((rc = set_smem(ks.diag_inverse, ks.diag_inverse_smem)) ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.diag_inverse, 256, ks.diag_inverse_smem)) !=
-            cudaSuccess)
-      return cleanup(rc ? rc : fail(BTC_ERR_CUDA, "btc_plan: occupancy: %s", cudaGetErrorString(e)));
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    p->inv_grid = std::max(1, occ) * std::max(1, sms);
-  }
   if ((rc = plan_schedule(p))) return cleanup(rc);
   *out = p;
   return BTC_OK;
@@ -1971,13 +1893,7 @@ int btc_free(btc_plan_t p) {
     cudaStreamDestroy(p->gstream2);
     cudaEventDestroy(p->gevent);
   }
-  if (p->istream) {
-    cudaStreamSynchronize(p->istream);
-    cudaStreamDestroy(p->istream);
-    cudaEventDestroy(p->iev_fork);
-    cudaEventDestroy(p->iev_join);
-  }
-  if (p->d_inv) cudaFree(p->d_inv);
+
   void *dev[] = {p->dpool,        p->epool,        p->d_fac,    p->d_fwd,  p->d_bwd,     p->d_rb,
                  p->d_y,          p->s_D,          p->d_fac_deps, p->d_solve_flow, p->d_flow, p->s_B,
                  p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail,

@@ -690,6 +690,9 @@ int btc_dispatch_orders(int count, const int *N, const int *n, int dtype, int *c
     return us[6];
   };
   constexpr int kSolves = 2;  // a refined call: the first solve and one correction
+  // every dependent launch level also waits for its producers' completion flags and stages its inputs
+  // (about 1.5 us measured between a producer's end and its consumer's start, plus the input loads)
+  constexpr double kLevelLatency = 2.0;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();  // (no device: keep the default count)
@@ -807,11 +810,11 @@ int btc_dispatch_orders(int count, const int *N, const int *n, int dtype, int *c
       }
       double m = 0.0;
       for (size_t l = 0; l < fsum.size(); ++l)
-        if (fsum[l] > 1e-9) m += std::max(fmax[l], fsum[l] / C);
+        if (fsum[l] > 1e-9) m += std::max(fmax[l], fsum[l] / C) + kLevelLatency;
       double sv = 0.0;
       for (size_t l = 0; l < fwd.size(); ++l) {
-        if (fwd[l] > 0) sv += std::max(ts, fwd[l] * ts / C);
-        if (bwd[l] > 0) sv += std::max(ts, bwd[l] * ts / C);
+        if (fwd[l] > 0) sv += std::max(ts, fwd[l] * ts / C) + kLevelLatency;
+        if (bwd[l] > 0) sv += std::max(ts, bwd[l] * ts / C) + kLevelLatency;
       }
       return m + kSolves * sv;
     };

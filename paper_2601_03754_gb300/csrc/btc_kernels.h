@@ -33,10 +33,6 @@ struct KernelSet {
   size_t root_smem = 0;
   // persistent dataflow forms (all levels in one launch)
   const void *fac_flow = nullptr, *solve_flow = nullptr;
-  // correction solves with inverted diagonal factors: the inversion kernel and the solve variant that
-  // multiplies by them (null for the blocked 256 sets)
-  const void *diag_inverse = nullptr, *solve_flow_inv = nullptr;
-  size_t diag_inverse_smem = 0;
   // interlaced factorization + forward substitution (same CTA shape as fac_flow)
   const void *fac_fwd_flow = nullptr;
   size_t (*fused_smem)(int m) = nullptr;

@@ -74,9 +74,6 @@ KernelSet make_set() {
   k.pack_batch = &launch_pack_batch<T, S, NP>;
   k.fac_rl = (const void *)&k_factor_level<T, T, S, NP, R, false, true>;
   k.solve_flow = (const void *)&k_solve_flow<T, NP>;
-  k.solve_flow_inv = (const void *)&k_solve_flow<T, NP, true>;
-  k.diag_inverse = (const void *)&k_diag_inverse<T, NP>;
-  k.diag_inverse_smem = diag_inverse_smem_bytes<T, NP>();
   k.fwd = (const void *)&k_fwd_level<T, NP>;
   k.bwd = (const void *)&k_bwd_level<T, NP>;
   k.fwd_smem = &fwd_smem_fn<T, NP>;

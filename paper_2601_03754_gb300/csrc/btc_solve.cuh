@@ -156,9 +156,6 @@ struct SolveArgs {
   const void *epool;
   void *y;  // work vector
   int m;
-  // the inverted diagonal factors (same layout as dpool), read by the solve items instead of the
-  // triangular solves when the kernel is instantiated with INV (null otherwise)
-  const void *inv = nullptr;
 };
 
 // Shared-memory layout of one solve item: the node's own factor block and
@@ -166,7 +163,7 @@ struct SolveArgs {
 // and three np x m vectors.
 template <typename T, int NP>
 struct SolveSmem {
-  T *U0, *U1, *U2, *dinv, *y0, *y1, *y2;
+  T *U0, *U1, *U2, *dinv, *y0, *y1, *y2, *part;
   __device__ __forceinline__ explicit SolveSmem(unsigned char *raw, int m) {
     constexpr int LDL = SolveCfg<T, NP>::LDL;
     constexpr int NB = SolveCfg<T, NP>::DIAG_GLOBAL ? 0 : SolveCfg<T, NP>::STREAM ? 1 : 3;
@@ -177,17 +174,25 @@ struct SolveSmem {
     y0 = dinv + NP;
     y1 = y0 + NP * m;
     y2 = y1 + NP * m;
+    part = y2 + NP * m;  // partial sums of the second half of split products (NP * m)
   }
 };
+
+// The products of a solve item split each output's sum between two threads when there are at
+// least two threads per output among the first kSolveThreads (one right-hand side and n_p <= 64):
+// the second half's partial sum passes through SolveSmem::part and is added after the first half's
+// (a fixed order). The condition does not depend on the block size, so the interlaced launch (more
+// threads) and the solve launches do the same arithmetic.
+__device__ __forceinline__ bool split_outputs(int nm) { return 2 * nm <= kSolveThreads; }
 
 // Issue the copies of an item's factor blocks (they do not depend on other
 // items of the solve, so a persistent CTA starts them before it waits for
 // the item's inputs). d0: dpool offset or -1; e1/e2: epool offsets, used when
 // the matching vector index v1/v2 is >= 0.
-template <typename T, int NP, bool INV = false>
+template <typename T, int NP>
 __device__ __forceinline__ void stage_item_blocks(const SolveSmem<T, NP> &sm, const SolveArgs &a, int64_t d0,
                                                   int64_t v1, int64_t e1, int64_t v2, int64_t e2) {
-  const T *dpool = reinterpret_cast<const T *>(INV ? a.inv : a.dpool);
+  const T *dpool = reinterpret_cast<const T *>(a.dpool);
   const T *epool = reinterpret_cast<const T *>(a.epool);
   if (!SolveCfg<T, NP>::DIAG_GLOBAL && d0 >= 0) stage_block<T, NP>(sm.U0, dpool + d0);
   if constexpr (!SolveCfg<T, NP>::STREAM) {
@@ -200,12 +205,9 @@ __device__ __forceinline__ void stage_item_blocks(const SolveSmem<T, NP> &sm, co
 //   y_j -= U(j-h, j)^T y_{j-h} + U(j+h, j)^T y_{j+h}   (contributions of level l-1)
 //   y_j <- U_j^{-T} y_j                                 (if j is eliminated at this level)
 // STAGED: the factor blocks were already issued by stage_item_blocks.
-// INV: the item's diagonal block is U_j^{-1} (k_diag_inverse), and the triangular solve is the
-// product y_j <- (U_j^{-1})^T y_j.
-template <typename T, int NP, bool STAGED = false, bool INV = false>
+template <typename T, int NP, bool STAGED = false>
 __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_l, int64_t y_r, int64_t e_r,
                                          int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
-  static_assert(!(INV && SolveCfg<T, NP>::DIAG_GLOBAL), "inverted diagonal blocks are staged in shared memory");
   constexpr int LDL = SolveCfg<T, NP>::LDL, LDU = SolveCfg<T, NP>::LDU;
   const int m = a.m;
   const SolveSmem<T, NP> sm(smem_raw, m);
@@ -215,13 +217,13 @@ __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_
   T *y = reinterpret_cast<T *>(a.y);
   const int nm = NP * m;
   T *yself = y + y_self * nm;
-  if (!STAGED) stage_item_blocks<T, NP, INV>(sm, a, d_self, y_l, e_l, y_r, e_r);
+  if (!STAGED) stage_item_blocks<T, NP>(sm, a, d_self, y_l, e_l, y_r, e_r);
   stage_vec<T>(ys, yself, nm);
   if (y_l >= 0) stage_vec<T>(yl, y + y_l * nm, nm);
   if (y_r >= 0) stage_vec<T>(yr, y + y_r * nm, nm);
   cp_async_wait_all_s();
   __syncthreads();
-  if (!INV && d_self >= 0)
+  if (d_self >= 0)
     for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDU + j];
   if (y_l >= 0) {
     const bool right = y_r >= 0;
@@ -238,6 +240,21 @@ __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_
           for (int r = 0; r < NP; ++r) acc = fma(-__ldcg(gr + r * NP + c), yr[r * m + col], acc);
         ys[q] = acc;
       }
+    } else if (split_outputs(nm)) {  // rows 0 .. NP/2-1 and NP/2 .. NP-1 of both blocks on two threads
+      const int t = threadIdx.x, q = t % nm, h = t / nm;
+      T acc = T(0);
+      if (h < 2) {
+        const int c = q / m, col = q % m, r0 = h * (NP / 2);
+        acc = h == 0 ? ys[q] : T(0);
+#pragma unroll 8
+        for (int r = r0; r < r0 + NP / 2; ++r) acc = fma(-Ul[r * LDL + c], yl[r * m + col], acc);
+        if (right)
+#pragma unroll 8
+          for (int r = r0; r < r0 + NP / 2; ++r) acc = fma(-Ur[r * LDL + c], yr[r * m + col], acc);
+        if (h == 1) sm.part[q] = acc;
+      }
+      __syncthreads();
+      if (h == 0) ys[q] = acc + sm.part[q];
     } else {
       for (int q = threadIdx.x; q < nm; q += blockDim.x) {
         const int c = q / m, col = q % m;
@@ -252,20 +269,7 @@ __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_
     }
   }
   __syncthreads();
-  if constexpr (INV) {
-    if (d_self >= 0) {  // y_j <- (U_j^{-1})^T y_j: column c of the inverse (rows r <= c) against y_j
-      for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-        const int c = q / m, col = q % m;
-        T acc = T(0);
-#pragma unroll 8
-        for (int r = 0; r <= c; ++r) acc = fma(Us[r * LDL + c], ys[r * m + col], acc);
-        yl[q] = acc;
-      }
-      __syncthreads();
-      for (int q = threadIdx.x; q < nm; q += blockDim.x) yself[q] = yl[q];
-      return;
-    }
-  } else if (d_self >= 0) {
+  if (d_self >= 0) {
     warp_trsv_ut<T, NP>(ys, m, Us, dinv);
     __syncthreads();
   }
@@ -281,11 +285,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
 
 // Backward step for one eliminated node e (Alg. 7 backward sweep):
 //   x_e <- U_e^{-1} (y_e - U(e, e+s) x_{e+s} - U(e, e-s) x_{e-s})
-// INV: x_e <- U_e^{-1} (...) as a product with the inverted diagonal block.
-template <typename T, int NP, bool STAGED = false, bool INV = false>
+template <typename T, int NP, bool STAGED = false>
 __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e_dn, int64_t x_up, int64_t e_up,
                                          int64_t d_self, const SolveArgs &a, unsigned char *smem_raw) {
-  static_assert(!(INV && SolveCfg<T, NP>::DIAG_GLOBAL), "inverted diagonal blocks are staged in shared memory");
   constexpr int LDL = SolveCfg<T, NP>::LDL, LDU = SolveCfg<T, NP>::LDU;
   const int m = a.m;
   const SolveSmem<T, NP> sm(smem_raw, m);
@@ -294,14 +296,13 @@ __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e
   T *y = reinterpret_cast<T *>(a.y);
   const int nm = NP * m;
   T *yself = y + x_self * nm;
-  if (!STAGED) stage_item_blocks<T, NP, INV>(sm, a, d_self, x_dn, e_dn, x_up, e_up);
+  if (!STAGED) stage_item_blocks<T, NP>(sm, a, d_self, x_dn, e_dn, x_up, e_up);
   stage_vec<T>(ys, yself, nm);
   if (x_dn >= 0) stage_vec<T>(xd, y + x_dn * nm, nm);
   if (x_up >= 0) stage_vec<T>(xu, y + x_up * nm, nm);
   cp_async_wait_all_s();
   __syncthreads();
-  if (!INV)
-    for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDU + j];
+  for (int j = threadIdx.x; j < NP; j += blockDim.x) dinv[j] = T(1) / Us[j * LDU + j];
   if (x_dn >= 0 || x_up >= 0) {
     const bool dn = x_dn >= 0, up = x_up >= 0;
     if constexpr (SolveCfg<T, NP>::STREAM) {
@@ -322,6 +323,22 @@ __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if (lane == 0) ys[q] -= part;
       }
+    } else if (split_outputs(nm)) {  // columns 0 .. NP/2-1 and NP/2 .. NP-1 of both blocks on two threads
+      const int t = threadIdx.x, q = t % nm, h = t / nm;
+      T acc = T(0);
+      if (h < 2) {
+        const int r = q / m, col = q % m, c0 = h * (NP / 2);
+        acc = h == 0 ? ys[q] : T(0);
+        if (dn)
+#pragma unroll 8
+          for (int c = c0; c < c0 + NP / 2; ++c) acc = fma(-Ud[r * LDL + c], xd[c * m + col], acc);
+        if (up)
+#pragma unroll 8
+          for (int c = c0; c < c0 + NP / 2; ++c) acc = fma(-Uu[r * LDL + c], xu[c * m + col], acc);
+        if (h == 1) sm.part[q] = acc;
+      }
+      __syncthreads();
+      if (h == 0) ys[q] = acc + sm.part[q];
     } else {
       for (int q = threadIdx.x; q < nm; q += blockDim.x) {
         const int r = q / m, col = q % m;
@@ -337,18 +354,6 @@ __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e
     }
   }
   __syncthreads();
-  if constexpr (INV) {  // x_e <- U_e^{-1} ys: row r of the inverse (columns c >= r)
-    for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-      const int r = q / m, col = q % m;
-      T acc = T(0);
-#pragma unroll 8
-      for (int c = r; c < NP; ++c) acc = fma(Us[r * LDL + c], ys[c * m + col], acc);
-      xd[q] = acc;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < nm; q += blockDim.x) yself[q] = xd[q];
-    return;
-  }
   warp_trsv_u<T, NP>(ys, m, Us, dinv);
   __syncthreads();
   for (int q = threadIdx.x; q < nm; q += blockDim.x) yself[q] = ys[q];
@@ -364,9 +369,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
 // Persistent dataflow form of the whole solve (forward items of all levels,
 // then backward items top-down) in one launch; each item waits only for the
 // items that produce its inputs.
-// INV: the diagonal steps multiply by the inverted diagonal blocks of a.inv (the correction solves
-// of the refinement, after k_diag_inverse).
-template <typename T, int NP, bool INV = false>
+template <typename T, int NP>
 __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowSync fs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
@@ -377,13 +380,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowS
     const SolveFlowItem it = items[t];
     flow_trace(fs, t, 0);
     // the factor blocks load while the item waits for its inputs
-    stage_item_blocks<T, NP, INV>(SolveSmem<T, NP>(smem_raw, a.m), a, it.d_self, it.y_a, it.e_a, it.y_b, it.e_b);
+    stage_item_blocks<T, NP>(SolveSmem<T, NP>(smem_raw, a.m), a, it.d_self, it.y_a, it.e_a, it.y_b, it.e_b);
     if (flow_wait(fs, it.dep, 3, &s_ok)) {
       flow_trace(fs, t, 1);
-      if (it.kind == 0)
-        fwd_node<T, NP, true, INV>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
-      else
-        bwd_node<T, NP, true, INV>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
+      if (it.kind == 0) fwd_node<T, NP, true>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
+      else bwd_node<T, NP, true>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, a, smem_raw);
     } else {
       cp_async_wait_all_s();  // no copy may still target shared memory when the CTA moves on
     }
@@ -396,48 +397,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowS
 template <typename T, int NP>
 constexpr size_t fwd_smem_bytes(int m) {
   constexpr size_t nb = SolveCfg<T, NP>::DIAG_GLOBAL ? 0 : SolveCfg<T, NP>::STREAM ? 1 : 3;
-  return sizeof(T) * (nb * NP * SolveCfg<T, NP>::LDL + NP + 3 * (size_t)NP * m);
+  return sizeof(T) * (nb * NP * SolveCfg<T, NP>::LDL + NP + 4 * (size_t)NP * m);
 }
 template <typename T, int NP>
 constexpr size_t bwd_smem_bytes(int m) {
   return fwd_smem_bytes<T, NP>(m);
-}
-
-// X_v = U_v^{-1} for the diagonal factor of every node (upper triangular, NP x NP, row-major, zeros
-// below the diagonal), by back substitution on all columns at once: for k = NP-1 .. 0, row k of X
-// is scaled by 1 / U_kk (it is then final) and eliminated from the rows above it. Once per
-// factorization; afterwards every triangular solve of Alg. 7 with U_v is a product with X_v.
-template <typename T, int NP>
-__global__ void __launch_bounds__(256) k_diag_inverse(T *inv, const T *dpool, int N) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int LDL = SolveCfg<T, NP>::LDL;
-  T *U = reinterpret_cast<T *>(smem_raw);
-  T *X = U + NP * LDL;
-  for (int v = blockIdx.x; v < N; v += gridDim.x) {
-    __syncthreads();  // the previous node's X is written out
-    stage_block<T, NP>(U, dpool + (size_t)v * NP * NP);
-    for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) X[(q / NP) * LDL + q % NP] = (q / NP == q % NP) ? T(1) : T(0);
-    cp_async_wait_all_s();
-    __syncthreads();
-    for (int k = NP - 1; k >= 0; --k) {
-      const T d = T(1) / U[k * LDL + k];
-      for (int j = k + threadIdx.x; j < NP; j += blockDim.x) X[k * LDL + j] *= d;
-      __syncthreads();
-      const int w = NP - k;  // row k of X is nonzero in columns k .. NP-1
-      for (int q = threadIdx.x; q < k * w; q += blockDim.x) {
-        const int i = q / w, j = k + q % w;
-        X[i * LDL + j] = fma(-U[i * LDL + k], X[k * LDL + j], X[i * LDL + j]);
-      }
-      __syncthreads();
-    }
-    T *out = inv + (size_t)v * NP * NP;
-    for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) out[q] = X[(q / NP) * LDL + q % NP];
-  }
-}
-
-template <typename T, int NP>
-constexpr size_t diag_inverse_smem_bytes() {
-  return sizeof(T) * 2 * (size_t)NP * SolveCfg<T, NP>::LDL;
 }
 
 // ---------------------------------------------------------------- vectors

@@ -484,13 +484,14 @@ __device__ __forceinline__ bool flow_wait(const FlowSync &fs, const int32_t *dep
   return *s_ok != 0;
 }
 
-// Publish item t as done (after all of this CTA's global writes for it).
+// Publish item t as done (after all of this CTA's global writes for it). The CTA barrier orders
+// every thread's writes before thread 0's release store (barriers synchronize the threads of a CTA
+// in the memory model's causality order, and a release is cumulative over it), so no separate
+// sequentially consistent fence is needed; a consumer's acquire load of the flag followed by its
+// own CTA barrier makes the writes visible to all of its threads.
 __device__ __forceinline__ void flow_publish(const FlowSync &fs, int t) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    st_release_gpu(fs.done + t, 1);
-  }
+  if (threadIdx.x == 0) st_release_gpu(fs.done + t, 1);
 }
 
 // Result of a failed pivot: packed (node, column) for an atomicMin.
