@@ -694,6 +694,19 @@ def interlace_measure(btc, gen, torch, stream, flush, steps=30):
     return out
 
 
+def _latency_by_n(pool, which, results, ok_status):
+    """p50 / p99 latency (us) per block size of the request mix (the service time spans two orders of
+    magnitude between the smallest and the largest systems, so the overall p99 is mostly the largest
+    ones' service time)."""
+    import numpy as np
+    by = {}
+    for k, r in enumerate(results):
+        if r["status"] == ok_status:
+            by.setdefault(pool[which[k]]["n"], []).append(r["latency_us"])
+    return {str(n): {"p50": round(float(np.percentile(v, 50)), 1), "p99": round(float(np.percentile(v, 99)), 1),
+                     "count": len(v)} for n, v in sorted(by.items())}
+
+
 def serving_measure(btc, torch, rates=(1000.0, 5000.0, 20000.0, 50000.0), count=5000, pool_size=128):
     """Config: Poisson stream of factor+solve requests, n uniform in {12,24,48,96}, N log-uniform
     in [50, 5000], MPC-like generator, 30% re-solves of a cached factor, HBM-footprint admission;
@@ -732,6 +745,7 @@ def serving_measure(btc, torch, rates=(1000.0, 5000.0, 20000.0, 50000.0), count=
                    "max_relres": max(r["relres"] for r in results if r["status"] == btc.OK),
                    "queue_and_service_us": {k: round(st[k], 1) for k in (
                        "p50_queue_us", "p99_queue_us", "p50_service_us", "p99_service_us")},
+                   "latency_by_n_us": _latency_by_n(pool, which, results, btc.OK),
                    **serve.check_results(pool, xs, which, rhs)}
             res[str(int(rate))] = row
             if knee is None and sustained < 0.9 * rate:

@@ -112,7 +112,9 @@ int btc_schedule(int N, int *order_out, int *levels_out);
  * is the capacity of the arrays (all four may be NULL to query the length);
  * on output it is the number of entries. Entry t: kind[t] 0 = factor item,
  * 1 = forward item; node[t] 1-based node; level[t] dissection level;
- * deps[6t .. 6t+5] earlier entries it waits for (-1: none). *tail_count (may
+ * deps[6t .. 6t+5] earlier entries it waits for (-1: none; d >= 0: entry d
+ * complete; d <= -2: only the factor blocks of entry -d-2, which a factor
+ * entry stores and publishes before its trailing products). *tail_count (may
  * be NULL): items of the second launch (top-separator forward item when
  * root_separate, then every backward item).
  */
@@ -198,7 +200,9 @@ int btc_describe_order(int N, int n, int dtype, int order, int chunks, btc_plan_
  *   d_next, r_up, r_down, p_a, p_b, fill, d_prev (diagonal pool indices d_*,
  *   off-diagonal pool indices r_*, p_*, fill; -1: none), node (0-based),
  *   flags (1: the fill block holds S'(up, down), else S'(down, up); 2: top
- *   separator), then the three items it waits for (-1: none).
+ *   separator), then the three items it waits for (-1: none; d >= 0: item d
+ *   complete; d <= -2: only item -d-2's factor blocks, i.e. its U blocks are
+ *   stored before its trailing products: the next diagonal block and the fill).
  *   One item eliminates node e with the Schur complement S_e = Dhat[d_self]
  *   - P^T P (P = U[p_a]): S_e = U_e^T U_e; U[r_up] <- U_e^-T S(e, up);
  *   U[r_down] <- U_e^-T S(e, down); Dhat[d_next] -= U[r_down]^T U[r_down]

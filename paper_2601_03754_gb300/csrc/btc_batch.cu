@@ -367,7 +367,7 @@ static int build_group(btc_batch_s *bt, BatchGroup &g) {
     if (m < 0) continue;
     for (int j = 0; j < 3; ++j) {
       const int32_t d = hps[r.k].fac_deps[3 * (size_t)r.local + j];
-      deps[3 * (size_t)m + j] = d >= 0 ? merged_of[r.k][d] : -1;
+      deps[3 * (size_t)m + j] = d == -1 ? -1 : d >= 0 ? merged_of[r.k][d] : core_dep(merged_of[r.k][dep_item(d)]);
     }
   }
   g.n_fac = (int)fac.size();

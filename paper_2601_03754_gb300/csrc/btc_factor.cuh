@@ -41,6 +41,19 @@ struct FactorArgs {
   unsigned long long *phase = nullptr;  // optional per-node phase stamps (phase_stamp), or null
 };
 
+// Dataflow control of a factor item inside a persistent launch (null elsewhere): the kernel has
+// waited for the factor blocks of every dependency; factor_node applies the deferred products
+// (which read only those blocks), then waits for the dependencies that must be complete (the
+// diagonal block and the fill blocks it reads), and publishes its own factor blocks as soon as
+// they are stored, before its trailing products.
+struct FlowCtl {
+  const FlowSync *fs;
+  const int32_t *deps;
+  int ndeps;
+  int t;
+  int *s_ok;
+};
+
 // Optional phase stamps of one node e (8 words per node): the global timer
 // (ns) at entry (0), when its operands and deferred updates are in place (1),
 // after the Cholesky and its two triangular solves (2), after U_e, U(e,e-s),
@@ -88,9 +101,10 @@ __device__ __forceinline__ void tile_atomic_sub_xty(P *g, const T *X, const T *Y
 // after its trsm the node subtracts U(e,e-s)^T U(e,e-s) from Dhat_{e-s} and
 // U(e,e+s)^T U(e,e+s) from Dhat_{e+s} with atomics. Every level reads the
 // pools, which a packing pass has initialized (FIRST must be false).
+// Returns false when a bounded wait of fc gave up (the node is then abandoned; the caller publishes it).
 template <typename T, typename P, typename S, int NP, int R, bool FIRST, bool RL = false>
-__device__ __forceinline__ void factor_node(const FactorItem &it, const FactorArgs &args, const InstDesc &single,
-                                            unsigned char *smem_raw) {
+__device__ __forceinline__ bool factor_node(const FactorItem &it, const FactorArgs &args, const InstDesc &single,
+                                            unsigned char *smem_raw, const FlowCtl *fc = nullptr) {
   static_assert(!(FIRST && RL), "the right-looking form reads packed pools at every level");
   using C = TileCfg<T, NP, R>;
   T *sS = reinterpret_cast<T *>(smem_raw);  // S_e -> U_e
@@ -127,31 +141,73 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
     if (has_next && upper_tile)
       tile_from_user<C>(d, uD + (e + 1) * ubs, ins.n, r0, c0, true, T(1), mD ? mD + (e + 1) * ubs : nullptr);
     __syncthreads();
-  } else {
-    const bool pa = !RL && it.p_a >= 0, pb = !RL && it.p_b >= 0;
+  } else if constexpr (RL) {
     if constexpr (ASYNC) {
       block_to_smem_async<C>(sS, dpool + it.d_self);
-      if (pa) block_to_smem_async<C>(sA, epool + it.p_a);
-      if (pb) block_to_smem_async<C>(sB, epool + it.p_b);
-    }
-    if (!RL && has_next && upper_tile) tile_from_pool<C>(d, dpool + it.d_next, r0, c0);
-    if constexpr (ASYNC) {
       cp_async_commit_wait_all();
     } else {
       block_to_smem<C>(sS, dpool + it.d_self);
+    }
+    __syncthreads();
+    // the off-diagonal operands arrive while the Cholesky runs
+    if constexpr (ASYNC) {
+      if (has_up) block_to_smem_async<C>(sA, epool + it.r_up);
+      if (has_dn) block_to_smem_async<C>(sB, epool + it.r_down);
+    } else {
+      if (has_up) block_to_smem<C>(sA, epool + it.r_up);
+      if (has_dn) block_to_smem<C>(sB, epool + it.r_down);
+    }
+  } else {
+    // deferred updates of level l-1, -P_a^T P_a for S_e and -P_b^T P_b for S_{e+s}: they read only the
+    // factor blocks of the previous level, so they run before the diagonal blocks are complete
+    const bool pa = it.p_a >= 0, pb = it.p_b >= 0;
+    if constexpr (ASYNC) {
+      if (pa) block_to_smem_async<C>(sA, epool + it.p_a);
+      if (pb) block_to_smem_async<C>(sB, epool + it.p_b);
+      cp_async_commit_wait_all();
+    } else {
       if (pa) block_to_smem<C>(sA, epool + it.p_a);
       if (pb) block_to_smem<C>(sB, epool + it.p_b);
     }
     __syncthreads();
-    // deferred updates of level l-1: S_e -= P_a^T P_a, S_{e+s} -= P_b^T P_b
+    T acc[R][R];
+    tile_zero<C>(acc);
+    tile_zero<C>(d);
     if (upper_tile) {
-      if (pa) {
-        T a[R][R];
-        tile_from_smem<C>(a, sS, r0, c0);
-        tile_sub_xty<C, NP>(a, sA, sA, r0, c0);
-        tile_to_smem<C>(sS, a, r0, c0);
-      }
+      if (pa) tile_sub_xty<C, NP>(acc, sA, sA, r0, c0);
       if (pb && has_next) tile_sub_xty<C, NP>(d, sB, sB, r0, c0);
+    }
+    // then the blocks that must be complete: S_e and S_{e+s} (the fill blocks follow below)
+    if (fc) {
+      if (!flow_wait(*fc->fs, fc->deps, fc->ndeps, fc->s_ok, kWaitFullOnly)) return false;
+    } else {
+      __syncthreads();
+    }
+    if constexpr (ASYNC) {
+      block_to_smem_async<C>(sS, dpool + it.d_self);
+    }
+    if (has_next && upper_tile) {
+      T dn[R][R];
+      tile_from_pool<C>(dn, dpool + it.d_next, r0, c0);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < R; ++c) d[r][c] = dn[r][c] + d[r][c];
+    }
+    if constexpr (ASYNC) {
+      cp_async_commit_wait_all();
+    } else {
+      block_to_smem<C>(sS, dpool + it.d_self);
+    }
+    __syncthreads();
+    if (pa && upper_tile) {
+      T a[R][R];
+      tile_from_smem<C>(a, sS, r0, c0);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < R; ++c) a[r][c] = a[r][c] + acc[r][c];
+      tile_to_smem<C>(sS, a, r0, c0);
     }
     __syncthreads();
     // the off-diagonal operands arrive while the Cholesky runs
@@ -173,6 +229,7 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
   smem_to_block<C>(dpool + it.d_self, sS, true);
   if (has_up) smem_to_block<C>(epool + it.r_up, sA, false);
   if (has_dn) smem_to_block<C>(epool + it.r_down, sB, false);
+  if (fc) flow_publish_core(*fc->fs, fc->t);  // the factor blocks are in the pools
 
   phase_stamp(args.phase, e, 3);
   // ---- S_{e+s} -= U_dn^T U_dn (and, right-looking, S_{e-s} -= U_up^T U_up)
@@ -195,6 +252,7 @@ __device__ __forceinline__ void factor_node(const FactorItem &it, const FactorAr
     tile_to_pool<C>(epool + it.fill, f, r0, c0);
   }
   phase_stamp(args.phase, e, 5);
+  return true;
 }
 
 // One launch per dissection level: CTA b eliminates item b of the level.
@@ -228,10 +286,12 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     if (t < 0) break;
     const FactorItem it = args.items[t];
     flow_trace(fs, t, 0);
-    if (flow_wait(fs, deps + 3 * t, 3, &s_ok)) {
+    // first the factor blocks of every dependency; factor_node waits for the rest itself
+    if (flow_wait(fs, deps + 3 * t, 3, &s_ok, kWaitCoreOnly)) {
       flow_trace(fs, t, 1);
-      if (t < nfirst) factor_node<T, P, S, NP, R, true>(it, args, single, smem_raw);
-      else factor_node<T, P, S, NP, R, false>(it, args, single, smem_raw);
+      const FlowCtl fc{&fs, deps + 3 * t, 3, t, &s_ok};
+      if (t < nfirst) factor_node<T, P, S, NP, R, true>(it, args, single, smem_raw, &fc);
+      else factor_node<T, P, S, NP, R, false>(it, args, single, smem_raw, &fc);
     }
     __syncthreads();
     flow_trace(fs, t, 2);

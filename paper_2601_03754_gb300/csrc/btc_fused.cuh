@@ -32,12 +32,14 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     if (t < 0) break;
     const int c = code[t];
     flow_trace(fs, t, 0);
-    if (flow_wait(fs, deps + (size_t)kInterDeps * t, kInterDeps, &s_ok)) {
+    // a factor entry first waits for its dependencies' factor blocks (factor_node waits for the rest)
+    if (flow_wait(fs, deps + (size_t)kInterDeps * t, kInterDeps, &s_ok, c >= 0 ? kWaitCoreOnly : kWaitAll)) {
       flow_trace(fs, t, 1);
       if (c >= 0) {
         const FactorItem it = fa.items[c];
-        if (c < nfirst) factor_node<T, P, S, NP, R, true>(it, fa, single, smem_raw);
-        else factor_node<T, P, S, NP, R, false>(it, fa, single, smem_raw);
+        const FlowCtl fc{&fs, deps + (size_t)kInterDeps * t, kInterDeps, t, &s_ok};
+        if (c < nfirst) factor_node<T, P, S, NP, R, true>(it, fa, single, smem_raw, &fc);
+        else factor_node<T, P, S, NP, R, false>(it, fa, single, smem_raw, &fc);
       } else {
         const SolveFlowItem it = fwd[-1 - c];
         fwd_node<T, NP>(it.y_self, it.y_a, it.e_a, it.y_b, it.e_b, it.d_self, sa, smem_raw);

@@ -27,6 +27,13 @@ enum : int32_t {
 
 // One eliminated node e at level l (Alg. 5, one iteration of the parallel loop).
 // Offsets are in ELEMENTS into the Dhat / U pools, -1 when the step is absent.
+// Dependency encoding of the persistent launches: d >= 0 waits for item d to be
+// complete; core_dep(d) (<= -2) waits only until item d has stored its factor
+// blocks (U_e and its two off-diagonal blocks), before its trailing products;
+// -1 is none.
+constexpr int32_t core_dep(int32_t item) { return -item - 2; }
+constexpr int32_t dep_item(int32_t d) { return d >= 0 ? d : -d - 2; }
+
 struct FactorItem {
   int64_t d_self;  // Dhat_e
   int64_t d_next;  // Dhat_{e+s}                      (syrk target)

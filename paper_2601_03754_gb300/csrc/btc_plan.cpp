@@ -149,6 +149,10 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
           const int64_t cand[3] = {e - h, e + h, e + 3 * h};
           for (int k = 0; k < 3; ++k)
             if (cand[k] >= 1 && cand[k] <= N) P->fac_deps[3 * (size_t)idx + k] = fac_index[cand[k]];
+          // of e+3h only the deferred block P_b is read, which it stores with its factor blocks (its
+          // next-diagonal update and fill go to nodes other than e)
+          if (P->fac_deps[3 * (size_t)idx + 2] >= 0)
+            P->fac_deps[3 * (size_t)idx + 2] = core_dep(P->fac_deps[3 * (size_t)idx + 2]);
           // Alg. 6: Dhat_e receives its last (atomic) updates at level l-1 from e-h and e+h,
           // which also write the two fill blocks e reads; nothing is deferred.
           for (int k = 0; k < 2; ++k)
@@ -251,7 +255,7 @@ void build_interlaced(const HostPlan &P, bool root_separate, std::vector<int32_t
       int32_t d[kInterDeps] = {-1, -1, -1, -1, -1, -1};
       for (int k = 0; k < 3; ++k) {
         const int32_t src = P.fac_deps[3 * (size_t)f + k];
-        d[k] = src >= 0 ? fac_ticket[src] : -1;
+        d[k] = src == -1 ? -1 : src >= 0 ? fac_ticket[src] : core_dep(fac_ticket[dep_item(src)]);
       }
       fac_ticket[f] = push(f, d);
     }
@@ -260,10 +264,11 @@ void build_interlaced(const HostPlan &P, bool root_separate, std::vector<int32_t
       const int64_t j = P.fwd_node[w];
       int32_t d[kInterDeps] = {-1, -1, -1, -1, -1, -1};
       for (int k = 0; k < 3; ++k) d[k] = it.dep[k] >= 0 ? fwd_ticket[it.dep[k]] : -1;
-      // the factor items that write U_j (level l), U(j-h, j) and U(j+h, j) (level l-1)
-      if (it.d_self >= 0) d[3] = fac_ticket[fac_of_node[j]];
-      if (it.y_a >= 0) d[4] = fac_ticket[fac_of_node[j - h]];
-      if (it.y_b >= 0) d[5] = fac_ticket[fac_of_node[j + h]];
+      // the factor items that write U_j (level l), U(j-h, j) and U(j+h, j) (level l-1): their factor
+      // blocks suffice
+      if (it.d_self >= 0) d[3] = core_dep(fac_ticket[fac_of_node[j]]);
+      if (it.y_a >= 0) d[4] = core_dep(fac_ticket[fac_of_node[j - h]]);
+      if (it.y_b >= 0) d[5] = core_dep(fac_ticket[fac_of_node[j + h]]);
       fwd_ticket[w] = push(-1 - w, d);
     }
   }
@@ -325,7 +330,10 @@ void build_tile_tasks(const HostPlan &P, std::vector<TileTask> *tasks, std::vect
         t.counter = f;
         t.wait_self = before;
         for (int k = 0; k < 3; ++k) {
-          const int32_t d = P.fac_deps.empty() ? -1 : P.fac_deps[3 * (size_t)f + k];
+          // the tile tasks count a node's completed tasks only: a dependency on another node's
+          // factor blocks waits for the whole node
+          const int32_t raw = P.fac_deps.empty() ? -1 : P.fac_deps[3 * (size_t)f + k];
+          const int32_t d = raw == -1 ? -1 : dep_item(raw);
           t.dep[k] = d;
           t.dep_n[k] = d >= 0 ? (*node_total)[d] : 0;
         }

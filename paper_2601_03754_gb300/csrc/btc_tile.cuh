@@ -459,16 +459,32 @@ __device__ __forceinline__ int flow_claim(const FlowSync &fs, int total, int *s_
   return t < total ? t : -1;
 }
 
-// Wait until the listed items (index < 0: none) are done. Thread 0 polls;
-// returns false (for every thread) when the wait gave up.
-__device__ __forceinline__ bool flow_wait(const FlowSync &fs, const int32_t *deps, int ndeps, int *s_ok) {
+// Completion flags take two values: kFlagCore when a factor item has stored
+// its factor blocks (U_e and the two off-diagonal blocks; its trailing
+// products may still run), kFlagDone when the item is complete. A dependency
+// d >= 0 waits for item d to be done; d <= -2 waits only for item -d-2's
+// factor blocks (kFlagCore or later); -1 is none. Items that publish only at
+// the end satisfy both kinds of wait.
+constexpr int kFlagCore = 1;
+constexpr int kFlagDone = 2;
+
+// Wait until the listed dependencies are met (all: done for d >= 0, factor blocks
+// for d <= -2; core_only: the factor blocks of every listed item; full_only: only
+// the d >= 0 ones, done). Thread 0 polls; returns false (for every thread) when
+// the wait gave up.
+enum FlowWaitKind { kWaitAll = 0, kWaitCoreOnly = 1, kWaitFullOnly = 2 };
+__device__ __forceinline__ bool flow_wait(const FlowSync &fs, const int32_t *deps, int ndeps, int *s_ok,
+                                          int kind = kWaitAll) {
   if (threadIdx.x == 0) {
     int ok = 1;
     for (int k = 0; k < ndeps && ok; ++k) {
-      const int d = deps[k];
-      if (d < 0) continue;
+      const int dd = deps[k];
+      if (dd == -1) continue;
+      const int d = dd >= 0 ? dd : -dd - 2;
+      if (kind == kWaitFullOnly && dd < 0) continue;
+      const int need = (dd < 0 || kind == kWaitCoreOnly) ? kFlagCore : kFlagDone;
       long long polls = 0;
-      while (ld_acquire_gpu(fs.done + d) == 0) {
+      while (ld_acquire_gpu(fs.done + d) < need) {
         // the status word is checked every 64 polls; the first polls spin without sleeping
         if ((++polls & 63) == 0 && (polls > fs.max_polls || *((volatile int *)fs.status) != 0)) {
           atomicOr(fs.status, kFlowTimeout);
@@ -491,7 +507,13 @@ __device__ __forceinline__ bool flow_wait(const FlowSync &fs, const int32_t *dep
 // own CTA barrier makes the writes visible to all of its threads.
 __device__ __forceinline__ void flow_publish(const FlowSync &fs, int t) {
   __syncthreads();
-  if (threadIdx.x == 0) st_release_gpu(fs.done + t, 1);
+  if (threadIdx.x == 0) st_release_gpu(fs.done + t, kFlagDone);
+}
+
+// Publish that factor item t has stored its factor blocks (kFlagCore); the same ordering as flow_publish.
+__device__ __forceinline__ void flow_publish_core(const FlowSync &fs, int t) {
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_gpu(fs.done + t, kFlagCore);
 }
 
 // Result of a failed pivot: packed (node, column) for an atomicMin.

@@ -70,8 +70,19 @@ def test_trace_shows_every_interlaced_item_after_its_dependencies(N, n):
     assert np.all((sm >= 0) & (sm < 1024))
     for t in range(cnt):
         for d in deps[t]:
+            if d == -1:
+                continue
+            q = int(d) if d >= 0 else -int(d) - 2
+            # every entry starts after its dependencies started; a forward entry's "ready" stamp
+            # follows the completion of its complete-dependencies; a factor entry's "ready" stamp
+            # follows only its dependencies' factor blocks (it waits for the rest inside), and it
+            # completes after them
+            assert ready[t] >= ready[q], (t, q)
             if d >= 0:
-                assert ready[t] >= done[d], (t, int(d))
+                if kind[t] == 1:
+                    assert ready[t] >= done[q], (t, q)
+                else:
+                    assert done[t] >= done[q], (t, q)
     S = ts.view(-1, 4).cpu().numpy()
     assert np.all(S[:ntail, 2] > 0), "every item of the solve tail ran"
     # tracing does not change the result
@@ -112,11 +123,13 @@ def test_phase_stamps_are_ordered_and_leave_results_unchanged(dt, variant):
     assert np.array_equal(stamped, expect)
     assert np.all(np.diff(P[stamped, :6], axis=1) >= 0), "phases in order"
     assert np.all(P[stamped, 6] < 1024)
-    # a node starts only after the nodes of the previous level that write its operands have finished:
-    # node e at level l (stride s = 2^(l-1)) depends on e - s/2 and e + s/2
+    # a node's operands are in place only after the nodes of the previous level that write them have
+    # finished: node e at level l (stride s = 2^(l-1)) depends on e - s/2 and e + s/2 (its deferred
+    # products may start earlier, from their factor blocks)
     lev = np.array([((i + 1) & -(i + 1)).bit_length() for i in range(N)])
     for e in np.where(stamped & (lev > 1))[0]:
         h = 1 << (lev[e] - 2)
         for q in (e - h, e + h):
             if 0 <= q < N and stamped[q]:
-                assert P[e, 0] >= P[q, 5], (int(e), int(q))
+                assert P[e, 1] >= P[q, 5], (int(e), int(q))
+                assert P[e, 0] >= P[q, 0], (int(e), int(q))

@@ -24,16 +24,22 @@ def elim_level(e):
 
 
 def closure(deps):
-    reach = []
+    """(entries complete before t starts, entries whose factor blocks are stored before t starts). A
+    dependency d >= 0 waits for entry d to complete; d <= -2 only for the factor blocks of entry -d-2."""
+    full, core = [], []
     for t in range(len(deps)):
-        r = set()
+        f, c = set(), set()
         for d in deps[t]:
-            if d >= 0:
-                assert d < t, "a dependency must be an earlier entry"
-                r.add(int(d))
-                r |= reach[d]
-        reach.append(r)
-    return reach
+            if d == -1:
+                continue
+            q = int(d) if d >= 0 else -int(d) - 2
+            assert q < t, "a dependency must be an earlier entry"
+            f |= full[q]
+            c |= core[q]
+            (f if d >= 0 else c).add(q)
+        full.append(f)
+        core.append(c | f)
+    return full, core
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 7, 8, 13, 64, 100, 257])
@@ -61,22 +67,28 @@ def test_interlaced_schedule_dependencies(N, root_separate):
                 continue  # the top separator's forward item runs in the tail
             want_fwd.add((1, j, l))
     assert {k for k in entry if k[0] == 1} == want_fwd
-    reach = closure(deps)
+    full, core = closure(deps)
     for (k, j, l), t in entry.items():
         s, h = 1 << (l - 1), (1 << (l - 1)) // 2
-        need = []
+        need_full, need_core = [], []
         if k == 0 and l > 1:
-            need = [(0, c, l - 1) for c in (j - h, j + h, j + 3 * h) if 1 <= c <= N]
+            # e-h and e+h update S_e and write the fill blocks it reads; of e+3h only the deferred block
+            # (a factor block) is read
+            need_full = [(0, c, l - 1) for c in (j - h, j + h) if 1 <= c <= N]
+            need_core = [(0, c, l - 1) for c in (j + 3 * h,) if 1 <= c <= N]
         if k == 1:
             if elim_level(j) == l:
-                need.append((0, j, l))
+                need_core.append((0, j, l))
             if l > 1:
                 for c in (j - h, j + h):
                     if 1 <= c <= N:
-                        need += [(0, c, l - 1), (1, c, l - 1)]
-                need += [(1, j, lp) for lp in range(1, l) if (1, j, lp) in entry]
-        for q in need:
-            assert entry[q] in reach[t], f"{(k, j, l)} does not wait for {q}"
+                        need_core.append((0, c, l - 1))
+                        need_full.append((1, c, l - 1))
+                need_full += [(1, j, lp) for lp in range(1, l) if (1, j, lp) in entry]
+        for q in need_full:
+            assert entry[q] in full[t], f"{(k, j, l)} does not wait for {q} to complete"
+        for q in need_core:
+            assert entry[q] in core[t], f"{(k, j, l)} does not wait for the factor blocks of {q}"
     assert tail == N + (1 if root_separate else 0)
 
 

@@ -95,6 +95,99 @@ def test_partition_rejections():
 
 
 # ---------------------------------------------------------------- item emulation
+# A factor item runs in phases separated by four events: S (its dependencies' factor blocks are
+# stored: it reads the deferred blocks P_a, P_b), B (its complete-dependencies are done: it reads
+# S_e, S_{e+s} and the off-diagonal blocks), C (its factor blocks U_e, U(e, up), U(e, down) are
+# stored and published), E (its trailing products, the next diagonal block and the fill, are
+# written). A dependency d >= 0 orders E_d before B and C_d before S; d <= -2 orders only C_(-d-2)
+# before S.
+
+def _decode(d):
+    d = int(d)
+    return (None, None) if d == -1 else ((d, "full") if d >= 0 else (-d - 2, "core"))
+
+
+def _event_graph(deps):
+    n = len(deps)
+    S, B, C, E = (lambda i: 4 * i), (lambda i: 4 * i + 1), (lambda i: 4 * i + 2), (lambda i: 4 * i + 3)
+    succ = [[] for _ in range(4 * n)]
+    for i in range(n):
+        succ[S(i)].append(B(i))
+        succ[B(i)].append(C(i))
+        succ[C(i)].append(E(i))
+        for d in deps[i]:
+            q, kind = _decode(d)
+            if q is None:
+                continue
+            assert q < i, (i, list(deps[i]))
+            succ[C(q)].append(S(i))
+            if kind == "full":
+                succ[E(q)].append(B(i))
+    # reachability (events are numbered in a topological order: every edge goes forward)
+    reach = [None] * (4 * n)
+    for v in reversed(range(4 * n)):
+        r = {v}
+        for w in succ[v]:
+            r |= reach[w]
+        reach[v] = r
+    return succ, reach, (S, B, C, E)
+
+
+def _factor_accesses(r, ev):
+    S, B, C, E = ev
+    _, ds, dn, ru, rd, pa, pb, fi = (int(v) for v in r[:8])
+    acc = []  # (block, writes, first event, last event) for item i (filled by the caller)
+    for q in (pa, pb):
+        if q >= 0:
+            acc.append((("e", q), False, S, B))
+    acc.append((("d", ds), True, B, C))
+    for q in (ru, rd):
+        if q >= 0:
+            acc.append((("e", q), True, B, C))
+    if dn >= 0:
+        acc.append((("d", dn), True, B, E))
+    if fi >= 0:
+        acc.append((("e", fi), True, C, E))
+    return acc
+
+
+def _factor_hazards(fac):
+    deps = [list(r[11:14]) for r in fac]
+    succ, reach, ev = _event_graph(deps)
+    items = []
+    for i, r in enumerate(fac):
+        for blk, w, a, b in _factor_accesses(r, ev):
+            items.append((i, blk, w, a(i), b(i)))
+    bad = []
+    for x in range(len(items)):
+        i, bx, wx, ax, zx = items[x]
+        for y in range(x):
+            j, by, wy, ay, zy = items[y]
+            if i == j or bx != by or not (wx or wy):
+                continue
+            if ay not in reach[zx] and ax not in reach[zy]:
+                bad.append((j, i, bx))
+    return bad, succ
+
+
+def _random_topological_events(succ, rng):
+    n = len(succ)
+    indeg = [0] * n
+    for v in range(n):
+        for w in succ[v]:
+            indeg[w] += 1
+    ready = [v for v in range(n) if indeg[v] == 0]
+    out = []
+    while ready:
+        v = ready.pop(rng.randrange(len(ready)))
+        out.append(v)
+        for w in succ[v]:
+            indeg[w] -= 1
+            if indeg[w] == 0:
+                ready.append(w)
+    assert len(out) == n
+    return out
+
 
 def _closure(deps):
     anc = []
@@ -142,47 +235,37 @@ def _emulate(N, n, order_kind, c, seed):
     for s in range(N - 1):
         assert slots[s, 2] in (0, 1)
         ep[s] = B[s].T.copy() if slots[s, 2] else B[s].copy()
-    # factor items
-    deps = [list(r[11:14]) for r in fac]
-    anc = _closure(deps)
+    # factor items: every dependency in an earlier launch level, every conflicting pair of accesses ordered
     for i, r in enumerate(fac):
-        for x in deps[i]:
-            assert x < 0 or fac[x, 0] < r[0], "a dependency in the same launch level"
-    rw = []
-    for r in fac:
-        _, ds, dn, ru, rd, pa, pb, fi = (int(v) for v in r[:8])
-        rd_set, wr_set = {("d", ds)}, {("d", ds)}
-        for q in (pa, pb):
-            if q >= 0:
-                rd_set.add(("e", q))
-        for q in (ru, rd):
-            if q >= 0:
-                rd_set.add(("e", q))
-                wr_set.add(("e", q))
-        if dn >= 0:
-            rd_set.add(("d", dn))
-            wr_set.add(("d", dn))
-        if fi >= 0:
-            wr_set.add(("e", fi))
-        rw.append((rd_set, wr_set))
-    assert not _unordered_conflicts(rw, anc)
+        for x in r[11:14]:
+            q, _ = _decode(x)
+            assert q is None or fac[q, 0] < r[0], "a dependency in the same launch level"
+    bad, succ = _factor_hazards(fac)
+    assert not bad, bad[:5]
     assert fac[-1, 10] & 2 and not any(fac[:-1, 10] & 2)
-    for i in _random_topological(deps, rng):
-        _, ds, dn, ru, rd, pa, pb, fi, _, _, flags = (int(v) for v in fac[i, :11])
-        S = dp[ds].copy()
-        if pa >= 0:
-            S -= ep[pa].T @ ep[pa]
-        U = np.linalg.cholesky(S).T
-        Zu = Zd = None
-        if ru >= 0:
-            Zu = ep[ru] = np.linalg.solve(U.T, ep[ru])
-        if rd >= 0:
-            Zd = ep[rd] = np.linalg.solve(U.T, ep[rd])
-        if dn >= 0:
-            dp[dn] = dp[dn] - Zd.T @ Zd - (ep[pb].T @ ep[pb] if pb >= 0 else 0.0)
-        if fi >= 0:
-            ep[fi] = -(Zu.T @ Zd) if flags & 1 else -(Zd.T @ Zu)
-        dp[ds] = U
+    state = {}
+    for v in _random_topological_events(succ, rng):
+        i, phase = divmod(v, 4)
+        _, ds, dn, ru, rd, pa, pb, fi, _, _, flags = (int(x) for x in fac[i, :11])
+        st = state.setdefault(i, {})
+        if phase == 0:  # S: the deferred products
+            st["acc"] = -(ep[pa].T @ ep[pa]) if pa >= 0 else 0.0
+            st["accb"] = -(ep[pb].T @ ep[pb]) if pb >= 0 else 0.0
+        elif phase == 1:  # B .. C: Cholesky, triangular solves, factor blocks stored
+            U = np.linalg.cholesky(dp[ds] + st["acc"]).T
+            st["Zu"] = np.linalg.solve(U.T, ep[ru]) if ru >= 0 else None
+            st["Zd"] = np.linalg.solve(U.T, ep[rd]) if rd >= 0 else None
+            st["dn"] = dp[dn].copy() if dn >= 0 else None
+            dp[ds] = U
+            if ru >= 0:
+                ep[ru] = st["Zu"]
+            if rd >= 0:
+                ep[rd] = st["Zd"]
+        elif phase == 3:  # C .. E: trailing products
+            if dn >= 0:
+                dp[dn] = st["dn"] + st["accb"] - st["Zd"].T @ st["Zd"]
+            if fi >= 0:
+                ep[fi] = -(st["Zu"].T @ st["Zd"]) if flags & 1 else -(st["Zd"].T @ st["Zu"])
     # solve items
     sdeps = [list(r[7:10]) for r in sol]
     sanc = _closure(sdeps)
@@ -242,20 +325,24 @@ def test_nd_items_reproduce_the_oracle_factor_and_solve(N):
     assert oracle.relres(D, B, x, b) <= 1e-13
 
 
-def test_emulation_catches_a_dropped_dependency(monkeypatch):
-    """The hazard check is live: removing one declared dependency of a partition plan is reported."""
+def test_emulation_catches_a_dropped_or_weakened_dependency():
+    """The hazard check is live: removing a declared dependency of a partition plan, or weakening a
+    nested-dissection dependency on a complete item to its factor blocks only, is reported."""
     fac, sol, slots = btc.btc_schedule_items(21, btc.ORDER_PARTITION, 3)
-    deps = [list(r[11:14]) for r in fac]
     # the first pivot waits on the last node of chunk 3, which also updates the next pivot
     i = [k for k, r in enumerate(fac) if r[10] & 2 == 0 and r[0] == fac[:, 0].max() - 1][0]
-    deps[i] = [-1, -1, -1]
-    rw = []
-    for r in fac:
-        _, ds, dn, ru, rd, pa, pb, fi = (int(v) for v in r[:8])
-        rd_set = {("d", ds)} | {("e", q) for q in (pa, pb, ru, rd) if q >= 0} | ({("d", dn)} if dn >= 0 else set())
-        wr_set = {("d", ds)} | {("e", q) for q in (ru, rd, fi) if q >= 0} | ({("d", dn)} if dn >= 0 else set())
-        rw.append((rd_set, wr_set))
-    assert _unordered_conflicts(rw, _closure(deps))
+    assert not _factor_hazards(fac)[0]
+    bad = fac.copy()
+    bad[i, 11:14] = -1
+    assert _factor_hazards(bad)[0]
+    fac, sol, slots = btc.btc_schedule_items(16, btc.ORDER_ND, 0)
+    assert not _factor_hazards(fac)[0]
+    k = [t for t, r in enumerate(fac) if r[11] >= 0][0]  # a level-2 item's dependency on its left neighbour
+    weak = fac.copy()
+    weak[k, 11] = -weak[k, 11] - 2
+    assert _factor_hazards(weak)[0]
+    # the planner's own weak dependency (e+3h: only its factor blocks are read) passes
+    assert any((r[11:14] <= -2).any() for r in fac)
 
 
 # ---------------------------------------------------------------- dispatch model (host only)
