@@ -110,6 +110,22 @@ __global__ void k_refine_decide(Readback *rb, double tol, int maxit, int first, 
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// The state of one persistent launch reset before it runs (its ticket and `count` completion flags),
+// and optionally the launch status, the pivot report and the first `nnorms` residual norms: one small
+// kernel in place of up to five memsets (fewer nodes in the captured graphs).
+__global__ void k_flow_reset(int *ticket, int *flags, int count, int *status, unsigned long long *info,
+                             double *norms, int nnorms) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) flags[q] = 0;
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      *ticket = 0;
+      if (status) *status = 0;
+      if (info) *info = ~0ull;
+    }
+    if (threadIdx.x < nnorms) norms[threadIdx.x] = 0.0;
+  }
+}
+
 // Diagonal entries of nblocks consecutive n x n FP64 blocks set to 1 (the pad blocks of a server's
 // bucketed plans).
 __global__ void k_set_unit_diagonal(double *D, int64_t nblocks, int n) {
@@ -281,8 +297,17 @@ static FlowSync flow_sync(btc_plan_s *p, int which) {
   return fs;
 }
 
-// Forward + backward substitution of the work vector (m columns), Alg. 7.
-static int run_solve(btc_plan_s *p, int m) {
+// Reset a launch's flow state (ticket `which`, `count` flags; optionally status, info, norms).
+static int flow_reset(btc_plan_s *p, int which, int count, bool status, bool info, int nnorms) {
+  const int grid = std::max(1, std::min((count + 255) / 256, 64));
+  return launch_n((const void *)&k_flow_reset, grid, 256, 0, p->stream, p->d_flow + which, p->d_flow + kFlowHeader,
+                  count, status ? p->d_status : (int *)nullptr, info ? p->d_info : (unsigned long long *)nullptr,
+                  p->d_norms, nnorms);
+}
+
+// Forward + backward substitution of the work vector (m columns), Alg. 7. clear_norms: also zero the
+// first clear_norms residual norms (the captured refinement folds that memset in here).
+static int run_solve(btc_plan_s *p, int m, int clear_norms = 0) {
   const KernelSet &k = *p->ks;
   SolveArgs a;
   a.dpool = p->dpool;
@@ -291,13 +316,14 @@ static int run_solve(btc_plan_s *p, int m) {
   a.m = m;
   KernelTimer timer(p, BTC_TIME_SOLVE);
   if (p->sched == BTC_SCHED_FLOW || p->hp.packed) {  // partition orders have no per-level solve lists
-    BTC_CUDA(cudaMemsetAsync(p->d_flow + 1, 0, sizeof(int), p->stream));
-    BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_solve, p->stream));
+    int rc = flow_reset(p, 1, p->n_solve, false, false, clear_norms);
+    if (rc) return rc;
     a.items = p->d_solve_flow;
     a.count = p->n_solve;
     return launch_n(k.solve_flow, std::min(p->solve_grid, p->n_solve), kSolveThreads, k.fwd_smem(m), p->stream, a,
                     flow_sync(p, 1));
   }
+  if (clear_norms) BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, clear_norms * sizeof(double), p->stream));
   for (int l = 0; l < p->hp.levels; ++l) {
     a.items = p->d_fwd + p->fwd_off[l];
     a.count = (int)(p->fwd_off[l + 1] - p->fwd_off[l]);
@@ -472,10 +498,8 @@ static int launch_factor_flow(btc_plan_s *p, const void *D, const void *B) {
   if ((rl || p->hp.packed) &&
       (rc = k.pack_pools(p->dpool, p->epool, D, B, p->N, p->n, orient, p->stream)))
     return rc;
-  BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  if ((rc = flow_reset(p, 0, nflow, true, true, 0))) return rc;
   if (nflow == 0) return BTC_OK;
-  BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
-  BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)nflow, p->stream));
   KernelTimer timer(p, BTC_TIME_FACTOR);
   if (rl) {
     int zero = 0;
@@ -503,9 +527,8 @@ static int launch_interlaced(btc_plan_s *p, const void *D, const void *B, int m)
   a.items = p->d_fac;
   a.count = p->n_inter;
   const InstDesc d = inst_desc(p, D, B);
-  BTC_CUDA(cudaMemsetAsync(p->d_flow, 0, sizeof(int), p->stream));
-  BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
-  BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_inter, p->stream));
+  int rc = flow_reset(p, 0, p->n_inter, true, true, 0);
+  if (rc) return rc;
   SolveArgs sa;
   sa.items = p->d_solve_flow;
   sa.count = p->hp.n_fwd;
@@ -641,7 +664,6 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
     if (inter && !p->tuned[2] && (rc = autotune_inter(p, D, B, m_inter))) return rc;
     if (!inter && !p->tuned[rl ? 1 : 0] && (rc = autotune_flow(p, D, B))) return rc;
   }
-  BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
   FactorArgs a;
   a.dpool = p->dpool;
   a.epool = p->epool;
@@ -652,7 +674,7 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
   const InstDesc d = inst_desc(p, D, B);
   const bool mixed_root = dtype_mixed(p->dtype);
   const int last = p->hp.levels - 1;
-  if (p->sched == BTC_SCHED_FLOW) {
+  if (p->sched == BTC_SCHED_FLOW) {  // (the launch's reset kernel also clears the pivot report)
     if (inter) {
       rc = launch_interlaced(p, D, B, m_inter);
     } else {
@@ -661,6 +683,7 @@ static int factor_impl(btc_plan_s *p, const void *D, const void *B, int m_inter)
     if (rc) return rc;
   } else {
     // one launch per level (Alg. 5 or Alg. 6 level loops; the positions of a partition order)
+    BTC_CUDA(cudaMemsetAsync(p->d_info, 0xFF, sizeof(unsigned long long), p->stream));
     BTC_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
     const int8_t *orient = p->d_orient;
     if ((rl || p->hp.packed) &&
@@ -848,7 +871,7 @@ static int gmres_ir_impl(btc_plan_s *p, const double *b, double *x, double tol, 
 // The rest of the solve after an interlaced factorization: the top
 // separator's forward item (mixed path) and the whole backward sweep, in one
 // persistent launch.
-static int run_solve_tail(btc_plan_s *p, int m) {
+static int run_solve_tail(btc_plan_s *p, int m, int clear_norms = 0) {
   const KernelSet &k = *p->ks;
   SolveArgs a;
   a.dpool = p->dpool;
@@ -858,8 +881,8 @@ static int run_solve_tail(btc_plan_s *p, int m) {
   a.items = p->d_tail;
   a.count = p->n_tail;
   KernelTimer timer(p, BTC_TIME_SOLVE_TAIL);
-  BTC_CUDA(cudaMemsetAsync(p->d_flow + 1, 0, sizeof(int), p->stream));
-  BTC_CUDA(cudaMemsetAsync(p->d_flow + kFlowHeader, 0, sizeof(int) * (size_t)p->n_tail, p->stream));
+  int rc = flow_reset(p, 1, p->n_tail, false, false, clear_norms);
+  if (rc) return rc;
   return launch_n(k.solve_flow, std::min(p->solve_grid, p->n_tail), kSolveThreads, k.fwd_smem(m), p->stream, a,
                   flow_sync(p, 1));
 }
@@ -990,11 +1013,10 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
     int r;
     if ((r = launch_n(k.pack, grid_for((int64_t)p->N * p->np * m), 256, 0, p->stream, p->d_y, (const void *)b, p->N,
                       p->n, p->np, m, m, c0, base)) ||
-        (r = factor_impl(p, D, B, m)) || (r = run_solve_tail(p, m)) ||
+        (r = factor_impl(p, D, B, m)) || (r = run_solve_tail(p, m, 3)) ||
         (r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
                       (const void *)p->d_y, p->N, p->n, p->np, m, m, c0, base, assign)))
       return r;
-    BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, 3 * sizeof(double), p->stream));
     if ((r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
                       (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base,
                       p->d_norms, one)) ||
@@ -1017,12 +1039,10 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
     BTC_CUDA(cudaStreamUpdateCaptureDependencies(p->gstream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
     BTC_CUDA(cudaStreamBeginCaptureToGraph(p->gstream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     p->stream = p->gstream2;
-    r = run_solve(p, m);
+    r = run_solve(p, m, 2);
     if (!r)
       r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x, (const void *)p->d_y,
                    p->N, p->n, p->np, m, m, c0, base, accumulate);
-    if (!r && cudaMemsetAsync(p->d_norms, 0, 2 * sizeof(double), p->stream) != cudaSuccess)
-      r = fail(BTC_ERR_CUDA, "graph capture: memset");
     if (!r)
       r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
                    (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base, p->d_norms,
