@@ -179,6 +179,13 @@ struct btc_plan_s {
   int32_t *d_inter_code = nullptr, *d_inter_deps = nullptr;
   SolveFlowItem *d_tail = nullptr;
   int n_inter = 0, n_tail = 0, inter_grid = 0;
+  // small plans (KernelSet::solve_small): the solve's and the tail's items by dependency waves, for
+  // the one-CTA solve; d_waves holds [solve order | solve wave offsets | tail order | tail offsets].
+  // waves_* = 0: that launch stays on the persistent dataflow kernel
+  int32_t *d_waves = nullptr;
+  int waves_solve = 0, waves_tail = 0, small_threads_solve = 0, small_threads_tail = 0;
+  int small_y_solve = 0, small_y_tail = 0;  // work-vector nodes the launch touches
+  int64_t off_solve_waves = 0, off_tail_order = 0, off_tail_waves = 0;
   // persistent-kernel configuration: residency variant and CTAs per SM (autotuned)
   int sms = 0;
   int flow_var = 0, ctas_per_sm = 0;
@@ -315,6 +322,12 @@ static int run_solve(btc_plan_s *p, int m, int clear_norms = 0) {
   a.y = p->d_y;
   a.m = m;
   KernelTimer timer(p, BTC_TIME_SOLVE);
+  if (m == 1 && p->waves_solve > 0 && !p->trace_solve && (p->sched == BTC_SCHED_FLOW || p->hp.packed)) {
+    if (clear_norms) BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, clear_norms * sizeof(double), p->stream));
+    return k.solve_small(p->d_solve_flow, p->n_solve, p->dpool, p->epool, p->d_y, p->d_waves,
+                         p->d_waves + p->off_solve_waves, p->waves_solve, p->small_y_solve, p->small_threads_solve,
+                         p->stream);
+  }
   if (p->sched == BTC_SCHED_FLOW || p->hp.packed) {  // partition orders have no per-level solve lists
     int rc = flow_reset(p, 1, p->n_solve, false, false, clear_norms);
     if (rc) return rc;
@@ -881,6 +894,12 @@ static int run_solve_tail(btc_plan_s *p, int m, int clear_norms = 0) {
   a.items = p->d_tail;
   a.count = p->n_tail;
   KernelTimer timer(p, BTC_TIME_SOLVE_TAIL);
+  if (m == 1 && p->waves_tail > 0 && !p->trace_solve) {
+    if (clear_norms) BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, clear_norms * sizeof(double), p->stream));
+    return k.solve_small(p->d_tail, p->n_tail, p->dpool, p->epool, p->d_y, p->d_waves + p->off_tail_order,
+                         p->d_waves + p->off_tail_waves, p->waves_tail, p->small_y_tail, p->small_threads_tail,
+                         p->stream);
+  }
   int rc = flow_reset(p, 1, p->n_tail, false, false, clear_norms);
   if (rc) return rc;
   return launch_n(k.solve_flow, std::min(p->solve_grid, p->n_tail), kSolveThreads, k.fwd_smem(m), p->stream, a,
@@ -1308,6 +1327,50 @@ static int plan_schedule(btc_plan_s *p) {
                                         cudaMemcpyHostToDevice)) != cudaSuccess))
     return cleanup(fail(BTC_ERR_CUDA, "btc_plan: interlaced schedule upload: %s", cudaGetErrorString(e)));
   p->device_bytes += (int64_t)((icode.size() + ideps.size()) * sizeof(int32_t) + tail.size() * sizeof(SolveFlowItem));
+  p->waves_solve = p->waves_tail = 0;
+  if (ks.solve_small) {  // small plans: the one-CTA solve when no wave is wider than two rounds of its warps
+    std::vector<int32_t> so, sw, to, tw;
+    const int ws = build_solve_waves(p->hp.solve_flow, &so, &sw);
+    const int wt = tail.empty() ? -1 : build_solve_waves(tail, &to, &tw);
+    auto nodes = [](const std::vector<SolveFlowItem> &v) {
+      int64_t top = 0;
+      for (const SolveFlowItem &it : v) top = std::max({top, it.y_self + 1, it.y_a + 1, it.y_b + 1});
+      return (int)top;
+    };
+    p->small_y_solve = nodes(p->hp.solve_flow);
+    p->small_y_tail = nodes(tail);
+    auto fits = [&](int width, size_t count, int ycount, size_t nwaves) {  // shared memory within 48 KB
+      return width >= 1 && width <= kSmallSolveWidth &&
+             small_solve_smem((int)count, ycount, (int)nwaves, ks.np, ks.elem) <= (size_t)48 * 1024;
+    };
+    const bool use_s = fits(ws, p->hp.solve_flow.size(), p->small_y_solve, sw.size()),
+               use_t = fits(wt, tail.size(), p->small_y_tail, tw.size());
+    if (use_s || use_t) {
+      std::vector<int32_t> all;
+      if (use_s) all.insert(all.end(), so.begin(), so.end());
+      p->off_solve_waves = (int64_t)all.size();
+      if (use_s) all.insert(all.end(), sw.begin(), sw.end());
+      p->off_tail_order = (int64_t)all.size();
+      if (use_t) all.insert(all.end(), to.begin(), to.end());
+      p->off_tail_waves = (int64_t)all.size();
+      if (use_t) all.insert(all.end(), tw.begin(), tw.end());
+      if ((e = cudaMalloc(&p->d_waves, all.size() * sizeof(int32_t))) != cudaSuccess)
+        return cleanup(fail(BTC_ERR_OOM, "btc_plan: wave list allocation: %s", cudaGetErrorString(e)));
+      if ((e = cudaMemcpy(p->d_waves, all.data(), all.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return cleanup(fail(BTC_ERR_CUDA, "btc_plan: wave list upload: %s", cudaGetErrorString(e)));
+      p->device_bytes += (int64_t)(all.size() * sizeof(int32_t));
+      const int g = std::max(1, 32 / ks.np);  // items per warp (lane groups of np lanes)
+      if (use_s) {
+        p->waves_solve = (int)sw.size() - 1;
+        p->small_threads_solve = 32 * std::min((ws + g - 1) / g, 32);
+      }
+      if (use_t) {
+        p->waves_tail = (int)tw.size() - 1;
+        p->small_threads_tail = 32 * std::min((wt + g - 1) / g, 32);
+      }
+    }
+  }
   if (ks.tiled) {
     std::vector<TileTask> tiles;
     std::vector<int32_t> totals;
@@ -1399,7 +1462,7 @@ static void plan_unschedule(btc_plan_s *p) {
   }
   void *dev[] = {p->epool,        p->d_fac,        p->d_fwd,      p->d_bwd,     p->d_fac_deps, p->d_fac_deps_rl,
                  p->d_solve_flow, p->d_flow,       p->d_inter_code, p->d_inter_deps, p->d_tail, p->d_tiles,
-                 p->d_tile_cnt,   p->d_orient};
+                 p->d_tile_cnt,   p->d_orient,     p->d_waves};
   for (void *q : dev)
     if (q) cudaFree(q);
   p->epool = nullptr;
@@ -1414,6 +1477,8 @@ static void plan_unschedule(btc_plan_s *p) {
   p->d_tiles = nullptr;
   p->d_tile_cnt = nullptr;
   p->d_orient = nullptr;
+  p->d_waves = nullptr;
+  p->waves_solve = p->waves_tail = 0;
 }
 
 int btc_plan(btc_plan_t *out, int N, int n, int dtype, void *stream) {
@@ -1917,7 +1982,7 @@ int btc_free(btc_plan_t p) {
   void *dev[] = {p->dpool,        p->epool,        p->d_fac,    p->d_fwd,  p->d_bwd,     p->d_rb,
                  p->d_y,          p->s_D,          p->d_fac_deps, p->d_solve_flow, p->d_flow, p->s_B,
                  p->s_b,          p->s_x,          p->d_fac_deps_rl, p->d_inter_code, p->d_inter_deps, p->d_tail,
-                 p->kry,          p->d_tiles,      p->d_tile_cnt, p->d_orient};
+                 p->kry,          p->d_tiles,      p->d_tile_cnt, p->d_orient, p->d_waves};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_rb) cudaFreeHost(p->h_rb);

@@ -181,6 +181,12 @@ void build_host_plan(int N, int n, int np, int64_t d_base, int64_t e_base, int64
 
 // Tile tasks of a plan in launch order (level by level, phase by phase within
 // a level) and the task total of every node (indexed like the flat factor list).
+// Dependency waves of a solve item list (for the one-CTA small solve): `order` lists the items wave
+// by wave (an item's dependencies all lie in earlier waves), `wave_off` holds the waves' start
+// offsets and the total. Returns the widest wave, or -1 when a dependency is not an earlier item.
+int build_solve_waves(const std::vector<SolveFlowItem> &items, std::vector<int32_t> *order,
+                      std::vector<int32_t> *wave_off);
+
 void build_tile_tasks(const HostPlan &P, std::vector<TileTask> *tasks, std::vector<int32_t> *node_total);
 
 // The partition permutation (Sec. 4.1, Alg. 4, chunk sizes by Proposition 1) as a plan: chunk interiors

@@ -56,6 +56,11 @@ struct KernelSet {
   int (*pack_batch)(void *dpool, void *epool, const void *nodes, const void *inst, int count, cudaStream_t s) = nullptr;
   // solve
   const void *fwd = nullptr, *bwd = nullptr;
+  // the whole solve of a small plan in one CTA, items by dependency waves (FP32 factor, np <= 16,
+  // one right-hand side; null otherwise)
+  int (*solve_small)(const void *items, int count, const void *dpool, const void *epool, void *y,
+                     const int32_t *order, const int32_t *wave_off, int nwaves, int ycount, int threads,
+                     cudaStream_t s) = nullptr;
   size_t (*fwd_smem)(int m) = nullptr;
   int max_cols = 16;  // right-hand sides per solve launch that fit in shared memory
   size_t (*bwd_smem)(int m) = nullptr;

@@ -74,6 +74,9 @@ KernelSet make_set() {
   k.pack_batch = &launch_pack_batch<T, S, NP>;
   k.fac_rl = (const void *)&k_factor_level<T, T, S, NP, R, false, true>;
   k.solve_flow = (const void *)&k_solve_flow<T, NP>;
+  // FP32 and n_p <= 16 only: an FP64 solve confined to one SM is bound by that SM's FP64 rate, and at
+  // n_p = 32 the longer chains of a lane-per-output item lose to the dataflow kernel's CTA per item
+  if constexpr (NP <= 16 && sizeof(T) == 4) k.solve_small = &launch_solve_small<T, NP>;
   k.fwd = (const void *)&k_fwd_level<T, NP>;
   k.bwd = (const void *)&k_bwd_level<T, NP>;
   k.fwd_smem = &fwd_smem_fn<T, NP>;

@@ -293,6 +293,32 @@ void build_interlaced(const HostPlan &P, bool root_separate, std::vector<int32_t
 
 namespace btc {
 
+int build_solve_waves(const std::vector<SolveFlowItem> &items, std::vector<int32_t> *order,
+                      std::vector<int32_t> *wave_off) {
+  const int n = (int)items.size();
+  std::vector<int32_t> depth(n, 0);
+  int nw = 0;
+  for (int i = 0; i < n; ++i) {
+    for (int32_t d : items[i].dep) {
+      if (d == -1) continue;
+      if (d < 0 || d >= i) return -1;
+      depth[i] = std::max(depth[i], depth[d] + 1);
+    }
+    nw = std::max(nw, depth[i] + 1);
+  }
+  wave_off->assign(nw + 1, 0);
+  for (int i = 0; i < n; ++i) ++(*wave_off)[depth[i] + 1];
+  int widest = 0;
+  for (int w = 0; w < nw; ++w) {
+    widest = std::max(widest, (*wave_off)[w + 1]);
+    (*wave_off)[w + 1] += (*wave_off)[w];
+  }
+  order->assign(n, 0);
+  std::vector<int32_t> pos(wave_off->begin(), wave_off->end() - 1);
+  for (int i = 0; i < n; ++i) (*order)[pos[depth[i]]++] = i;
+  return widest;
+}
+
 void build_tile_tasks(const HostPlan &P, std::vector<TileTask> *tasks, std::vector<int32_t> *node_total) {
   constexpr int64_t T = kTileT, LDG = kTileNP;
   tasks->clear();

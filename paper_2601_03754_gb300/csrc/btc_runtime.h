@@ -19,6 +19,8 @@ bool dtype_mixed(int dtype);  // FP64 inputs, FP32 factor, FP64 (or double-FP32)
 
 constexpr int kMaxCols = 16;     // right-hand sides per solve launch
 constexpr int kFlowHeader = 4;   // ints before the done flags of a flow state array
+// widest dependency wave of a solve that the one-CTA small solve takes (two rounds of its 32 warps)
+constexpr int kSmallSolveWidth = 64;
 
 #define BTC_CUDA(call)                                                                                       \
   do {                                                                                                       \

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "btc_internal.h"
+#include "btc_runtime.h"
 #include "btc_tile.cuh"
 
 namespace btc {
@@ -392,6 +393,184 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowS
     flow_trace(fs, t, 2);
     flow_publish(fs, t);
   }
+}
+
+// ---------------------------------------------------------------- small systems
+// A whole solve (or the tail of an interlaced one) in one CTA for small plans (FP32 factor,
+// n_p <= 16, one right-hand side): the items are grouped in waves (an item's dependencies all lie in earlier waves)
+// and a CTA barrier separates the waves, instead of one completion flag per item between CTAs. A
+// group of n_p lanes takes one item (32 / n_p items per warp); lane c of the group owns output c
+// and reads its column (forward) or row (backward) of the blocks straight into registers. An item
+// does exactly the arithmetic of fwd_node / bwd_node for this case (the two-halves products, the
+// one-chunk triangular solve with z_j = y_j * (1 / U_jj) formed on lane j), so both forms give the
+// same bits. The item descriptors and the work vector live in shared memory for the whole launch.
+template <typename T, int NP>
+struct SmallCfg {
+  static_assert(NP == 8 || NP == 16 || NP == 32, "lane groups of n_p lanes (n_p = 32: one item per warp)");
+  static_assert(2 * NP <= kSolveThreads, "one chunk, two threads per output in fwd_node");
+  static constexpr int G = 32 / NP;  // items per warp
+  // register budget: a lane holds a row or column of the diagonal block and one of each coupling block
+  static constexpr int MAXT = (int)sizeof(T) * NP <= 32 ? 1024 : (int)sizeof(T) * NP <= 128 ? 512 : 256;
+};
+
+template <typename T, int V>
+__device__ __forceinline__ void small_vload(const T *p, T *dst) {
+  T w[V];
+  vload<T, V>(p, w);
+#pragma unroll
+  for (int t = 0; t < V; ++t) dst[t] = w[t];
+}
+
+// Forward step (kind 0) for the lanes with act set; every lane of the warp runs the substitution's
+// shuffles. y: the work vector in shared memory.
+template <typename T, int NP>
+__device__ __forceinline__ void group_fwd_item(const SolveFlowItem &it, bool act, const SolveArgs &a, T *y) {
+  const int c = threadIdx.x & (NP - 1);
+  const T *dpool = reinterpret_cast<const T *>(a.dpool);
+  const T *epool = reinterpret_cast<const T *>(a.epool);
+  T *ys = y + it.y_self * NP;
+  const bool diag = act && it.d_self >= 0;
+  T u[NP], dl = T(0);  // column c of U_j (u[k] = U_j(k, c)) and 1 / U_j(c, c)
+  if (diag) {
+    const T *U = dpool + it.d_self;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) u[k] = U[k * NP + c];
+    dl = T(1) / U[c * NP + c];
+  }
+  T v = act ? ys[c] : T(0);
+  if (act && it.y_a >= 0) {
+    const bool right = it.y_b >= 0;
+    const T *ya = y + it.y_a * NP, *Ua = epool + it.e_a;
+    const T *yb = right ? y + it.y_b * NP : ya, *Ub = right ? epool + it.e_b : Ua;
+    T acc0 = v, acc1 = T(0);
+#pragma unroll
+    for (int r = 0; r < NP / 2; ++r) acc0 = fma(-Ua[r * NP + c], ya[r], acc0);
+    if (right)
+#pragma unroll
+      for (int r = 0; r < NP / 2; ++r) acc0 = fma(-Ub[r * NP + c], yb[r], acc0);
+#pragma unroll
+    for (int r = NP / 2; r < NP; ++r) acc1 = fma(-Ua[r * NP + c], ya[r], acc1);
+    if (right)
+#pragma unroll
+      for (int r = NP / 2; r < NP; ++r) acc1 = fma(-Ub[r * NP + c], yb[r], acc1);
+    v = acc0 + acc1;
+  }
+  if (__any_sync(0xffffffffu, diag)) {  // y_j <- U_j^{-T} y_j
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const T zj = __shfl_sync(0xffffffffu, v * dl, j, NP);
+      if (diag && c > j) v = fma(-u[j], zj, v);
+      if (diag && c == j) v = zj;
+    }
+  }
+  if (act) ys[c] = v;
+}
+
+// Backward step (kind 1) for the lanes with act set.
+template <typename T, int NP>
+__device__ __forceinline__ void group_bwd_item(const SolveFlowItem &it, bool act, const SolveArgs &a, T *y) {
+  constexpr int V = 16 / (int)sizeof(T) < NP ? 16 / (int)sizeof(T) : NP;
+  constexpr int HV = NP / 2 >= V ? V : NP / 2;
+  const int c = threadIdx.x & (NP - 1);
+  const T *dpool = reinterpret_cast<const T *>(a.dpool);
+  const T *epool = reinterpret_cast<const T *>(a.epool);
+  T *ys = y + it.y_self * NP;
+  const T *U = dpool + it.d_self;
+  T u[NP], dl = T(0), v = T(0);  // row c of U_e, 1 / U_e(c, c)
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < NP; k += V) small_vload<T, V>(U + c * NP + k, u + k);
+    dl = T(1) / U[c * NP + c];
+    v = ys[c];
+  }
+  const bool dn = act && it.y_a >= 0, up = act && it.y_b >= 0;
+  if (dn || up) {
+    const T *xd = dn ? y + it.y_a * NP : ys, *Ud = dn ? epool + it.e_a : U;
+    const T *xu = up ? y + it.y_b * NP : ys, *Uu = up ? epool + it.e_b : U;
+    T acc[2] = {v, T(0)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // columns h * NP/2 .. of both blocks into acc[h]
+      T wd[NP / 2], wu[NP / 2];
+#pragma unroll
+      for (int k = 0; k < NP / 2; k += HV) {
+        small_vload<T, HV>(Ud + c * NP + h * (NP / 2) + k, wd + k);
+        small_vload<T, HV>(Uu + c * NP + h * (NP / 2) + k, wu + k);
+      }
+      if (dn)
+#pragma unroll
+        for (int k = 0; k < NP / 2; ++k) acc[h] = fma(-wd[k], xd[h * (NP / 2) + k], acc[h]);
+      if (up)
+#pragma unroll
+        for (int k = 0; k < NP / 2; ++k) acc[h] = fma(-wu[k], xu[h * (NP / 2) + k], acc[h]);
+    }
+    v = acc[0] + acc[1];
+  }
+#pragma unroll
+  for (int j = NP - 1; j >= 0; --j) {  // x_e <- U_e^{-1} (...)
+    const T xj = __shfl_sync(0xffffffffu, v * dl, j, NP);
+    if (act && c < j) v = fma(-u[j], xj, v);
+    if (act && c == j) v = xj;
+  }
+  if (act) ys[c] = v;
+}
+
+// order: the items of a.items grouped by wave; wave_off: nwaves + 1 offsets into order; ycount: the
+// work-vector nodes the items touch. The item descriptors (in wave order), those nodes of the
+// work vector and the wave offsets are staged in shared memory for the whole launch, so a wave
+// reads only the factor blocks from global memory; the vector is written back at the end.
+template <typename T, int NP>
+__global__ void __launch_bounds__(SmallCfg<T, NP>::MAXT) k_solve_small(SolveArgs a, const int32_t *order,
+                                                                     const int32_t *wave_off, int nwaves,
+                                                                     int ycount) {
+  constexpr int G = SmallCfg<T, NP>::G;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SolveFlowItem *sit = reinterpret_cast<SolveFlowItem *>(smem_raw);
+  T *sy = reinterpret_cast<T *>(sit + a.count);
+  int *soff = reinterpret_cast<int *>(sy + ycount * NP);
+  const SolveFlowItem *items = reinterpret_cast<const SolveFlowItem *>(a.items);
+  T *y = reinterpret_cast<T *>(a.y);
+  for (int q = threadIdx.x; q < a.count; q += blockDim.x) sit[q] = items[order[q]];
+  for (int q = threadIdx.x; q < ycount * NP; q += blockDim.x) sy[q] = y[q];
+  for (int q = threadIdx.x; q <= nwaves; q += blockDim.x) soff[q] = wave_off[q];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, grp = (threadIdx.x & 31) / NP;
+  for (int w = 0; w < nwaves; ++w) {
+    const int t1 = soff[w + 1];
+    for (int t0 = soff[w] + warp * G; t0 < t1; t0 += nw * G) {  // warp-uniform loop
+      const int t = t0 + grp;
+      const SolveFlowItem it = sit[t < t1 ? t : t0];
+      const bool fwd = t < t1 && it.kind == 0, bwd = t < t1 && it.kind != 0;
+      if (__any_sync(0xffffffffu, fwd)) group_fwd_item<T, NP>(it, fwd, a, sy);
+      if (__any_sync(0xffffffffu, bwd)) group_bwd_item<T, NP>(it, bwd, a, sy);
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < ycount * NP; q += blockDim.x) y[q] = sy[q];
+}
+
+// Shared memory of k_solve_small.
+inline size_t small_solve_smem(int count, int ycount, int nwaves, int np, size_t elem) {
+  return (size_t)count * sizeof(SolveFlowItem) + (size_t)ycount * np * elem + sizeof(int) * ((size_t)nwaves + 1);
+}
+
+// Typed launch of k_solve_small (one CTA of `threads` threads, a multiple of 32).
+template <typename T, int NP>
+int launch_solve_small(const void *items, int count, const void *dpool, const void *epool, void *y,
+                       const int32_t *order, const int32_t *wave_off, int nwaves, int ycount, int threads,
+                       cudaStream_t s) {
+  if (count <= 0) return BTC_OK;
+  SolveArgs a;
+  a.items = items;
+  a.count = count;
+  a.dpool = dpool;
+  a.epool = epool;
+  a.y = y;
+  a.m = 1;
+  threads = threads < SmallCfg<T, NP>::MAXT ? threads : SmallCfg<T, NP>::MAXT;
+  k_solve_small<T, NP><<<1, threads, small_solve_smem(count, ycount, nwaves, NP, sizeof(T)), s>>>(
+      a, order, wave_off, nwaves, ycount);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BTC_OK : fail(BTC_ERR_CUDA, "small solve launch: %s", cudaGetErrorString(e));
 }
 
 template <typename T, int NP>
