@@ -7,10 +7,13 @@
 
 namespace btc {
 
-// Register tile edge per padded block size: (np/R)^2 threads per CTA.
-template <int NP>
+// Register tile edge per padded block size: (np/R)^2 threads per CTA. FP64 at n_p = 16 takes R = 1
+// (256 threads): a warp's FP64 instruction occupies its SM sub-partition's FP64 pipe for the same
+// time whatever its active lanes, so the node's products need warps on all four sub-partitions.
+template <typename T, int NP>
 struct TileEdge {
-  static constexpr int R = NP == 8 ? 1 : NP == 16 ? 2 : NP == 32 ? 2 : NP == 128 ? 8 : 4;  // 96 -> 576 threads
+  static constexpr int R =
+      NP == 8 ? 1 : NP == 16 ? (sizeof(T) == 8 ? 1 : 2) : NP == 32 ? 2 : NP == 128 ? 8 : 4;  // 96 -> 576 threads
 };
 
 template <typename T, int NP>
@@ -37,7 +40,7 @@ void add_flow_variant(KernelSet &k) {
 
 template <typename T, typename S, int NP, bool MIXED>
 KernelSet make_set() {
-  constexpr int R = TileEdge<NP>::R;
+  constexpr int R = TileEdge<T, NP>::R;
   KernelSet k;
   k.valid = true;
   k.np = NP;
