@@ -70,6 +70,7 @@ const KernelSet &kernels_for(int dtype, int np) {
 
 // ||Psi||_inf: max absolute row sum (lower triangles of D read), into norms[2].
 __global__ void k_anorm(const double *D, const double *B, int N, int n, double *norms) {
+  grid_dep_enter();
   const int i = blockIdx.x;
   const size_t bs = (size_t)n * n;
   double best = 0.0;
@@ -101,6 +102,7 @@ struct Readback {
 // tol, finite, and fewer than maxit steps were taken; the decision drives the
 // graph's while node.
 __global__ void k_refine_decide(Readback *rb, double tol, int maxit, int first, cudaGraphConditionalHandle h) {
+  grid_dep_enter();
   const double rn = rb->norms[0], xn = rb->norms[1], an = rb->norms[2];
   const double rel = (an * xn > 0) ? rn / (an * xn) : rn;
   if (first) rb->iters = 0;
@@ -115,6 +117,7 @@ __global__ void k_refine_decide(Readback *rb, double tol, int maxit, int first, 
 // kernel in place of up to five memsets (fewer nodes in the captured graphs).
 __global__ void k_flow_reset(int *ticket, int *flags, int count, int *status, unsigned long long *info,
                              double *norms, int nnorms) {
+  grid_dep_enter();
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) flags[q] = 0;
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) {
@@ -129,6 +132,7 @@ __global__ void k_flow_reset(int *ticket, int *flags, int count, int *status, un
 // Diagonal entries of nblocks consecutive n x n FP64 blocks set to 1 (the pad blocks of a server's
 // bucketed plans).
 __global__ void k_set_unit_diagonal(double *D, int64_t nblocks, int n) {
+  grid_dep_enter();
   const int64_t total = nblocks * n;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = q / n, i = q % n;
@@ -283,7 +287,7 @@ static void fill_info(const HostPlan &hp, int dtype, btc_plan_info *info) {
 static int launch(const void *fn, int grid, int block, size_t smem, cudaStream_t s, void *arg) {
   if (grid <= 0) return BTC_OK;
   void *args[] = {arg};
-  BTC_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
+  BTC_CUDA(launch_ex(fn, dim3(grid), dim3(block), args, smem, s));
   return BTC_OK;
 }
 

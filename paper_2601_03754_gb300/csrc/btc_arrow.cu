@@ -32,6 +32,7 @@ constexpr int kArrowK = 32;          // inner rows staged per step of a slice
 
 // ct[i][k] = C[c0 + k][i]: columns c0 .. c0+cw-1 of C^T, row-major with cw columns.
 __global__ void k_arrow_ct(double *ct, const double *C, int64_t L, int c0, int cw) {
+  grid_dep_enter();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L * cw; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / cw;
     const int k = (int)(q % cw);
@@ -41,6 +42,7 @@ __global__ void k_arrow_ct(double *ct, const double *C, int64_t L, int c0, int c
 
 // Z[i][c0 + k] = zc[i][k]
 __global__ void k_arrow_scatter(double *Z, const double *zc, int64_t L, int m, int c0, int cw) {
+  grid_dep_enter();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L * cw; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / cw;
     const int k = (int)(q % cw);
@@ -51,6 +53,7 @@ __global__ void k_arrow_scatter(double *Z, const double *zc, int64_t L, int m, i
 // part[p] = C[:, I_p] Z[I_p, :] over slice p of the inner dimension (m x m, FP64, fixed order).
 __global__ void __launch_bounds__(256) k_arrow_schur_part(double *part, const double *C, const double *Z, int64_t L,
                                                           int m) {
+  grid_dep_enter();
   __shared__ double Cs[kArrowMax * kArrowK];
   __shared__ double Zs[kArrowK * kArrowMax];
   const int64_t per = (L + gridDim.x - 1) / gridDim.x;
@@ -89,6 +92,7 @@ __global__ void __launch_bounds__(256) k_arrow_schur_part(double *part, const do
 
 // S = A - sum_p part[p] (A: lower triangle read, mirrored; the partials added in slice order).
 __global__ void k_arrow_schur_reduce(double *S, const double *A, const double *part, int parts, int m) {
+  grid_dep_enter();
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m * m; q += gridDim.x * blockDim.x) {
     const int r = q / m, c = q % m;
     double s = 0.0;
@@ -100,6 +104,7 @@ __global__ void k_arrow_schur_reduce(double *S, const double *A, const double *p
 // In-place lower Cholesky of S (m x m, FP64) by one CTA, right-looking, in shared memory. A pivot
 // that is not positive (or NaN) is reported as (node = N, column) and replaced by 1.
 __global__ void k_arrow_chol(double *S, int m, int N, unsigned long long *info) {
+  grid_dep_enter();
   __shared__ double a[kArrowMax * (kArrowMax + 1)];
   constexpr int LD = kArrowMax + 1;
   for (int q = threadIdx.x; q < m * m; q += blockDim.x) a[(q / m) * LD + q % m] = S[q];
@@ -131,6 +136,7 @@ __global__ void k_arrow_chol(double *S, int m, int N, unsigned long long *info) 
 // y[r] = bA[r] - sum_i C[r][i] z[i], one CTA per border row (fixed-order tree reduction).
 __global__ void __launch_bounds__(256) k_arrow_cz(double *y, const double *bA, const double *C, const double *z,
                                                   int64_t L) {
+  grid_dep_enter();
   __shared__ double red[256];
   const int r = blockIdx.x;
   double s = 0.0;
@@ -146,6 +152,7 @@ __global__ void __launch_bounds__(256) k_arrow_cz(double *y, const double *bA, c
 
 // x = L_S^{-T} L_S^{-1} y (forward then backward substitution, one warp).
 __global__ void k_arrow_trsv(double *x, const double *Ls, const double *y, int m) {
+  grid_dep_enter();
   __shared__ double w[kArrowMax];
   const int lane = threadIdx.x;
   for (int j = 0; j < m; ++j) {
@@ -168,6 +175,7 @@ __global__ void k_arrow_trsv(double *x, const double *Ls, const double *y, int m
 // xT[i] = z[i] - sum_c Z[i][c] xA[c]  (accumulate: xT[i] += that)
 __global__ void k_arrow_zx(double *xT, const double *z, const double *Z, const double *xA, int64_t L, int m,
                            int accumulate) {
+  grid_dep_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
     double v = z[i];
     for (int c = 0; c < m; ++c) v = fma(-Z[i * m + c], xA[c], v);
@@ -177,6 +185,7 @@ __global__ void k_arrow_zx(double *xT, const double *z, const double *Z, const d
 
 // bp[i] = bT[i] - sum_r C[r][i] xA[r]  (the border's contribution moved to the right-hand side)
 __global__ void k_arrow_ctx(double *bp, const double *bT, const double *C, const double *xA, int64_t L, int m) {
+  grid_dep_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
     double v = bT[i];
     for (int r = 0; r < m; ++r) v = fma(-C[(int64_t)r * L + i], xA[r], v);
@@ -189,6 +198,7 @@ __global__ void k_arrow_ctx(double *bp, const double *bT, const double *C, const
 __global__ void __launch_bounds__(256) k_arrow_border_resid(double *rA, double *norms, const double *bA,
                                                             const double *C, const double *xT, const double *A,
                                                             const double *xA, int64_t L, int m) {
+  grid_dep_enter();
   __shared__ double red[256];
   const int r = blockIdx.x;
   double s = 0.0;
@@ -210,12 +220,14 @@ __global__ void __launch_bounds__(256) k_arrow_border_resid(double *rA, double *
 
 // x[i] += d[i] for the m border entries.
 __global__ void k_arrow_add(double *x, const double *d, int m) {
+  grid_dep_enter();
   for (int i = threadIdx.x; i < m; i += blockDim.x) x[i] += d[i];
 }
 
 // ||Psi_a||_inf over the border rows: sum_i |C[r][i]| + sum_c |A[r][c]| (one CTA per row), into norms[2].
 __global__ void __launch_bounds__(256) k_arrow_anorm_border(double *norms, const double *C, const double *A,
                                                             int64_t L, int m) {
+  grid_dep_enter();
   __shared__ double red[256];
   const int r = blockIdx.x;
   double s = 0.0;
@@ -234,6 +246,7 @@ __global__ void __launch_bounds__(256) k_arrow_anorm_border(double *norms, const
 // column C^T (one CTA per block row), into norms[2].
 __global__ void k_arrow_anorm_rows(const double *D, const double *B, const double *C, int N, int n, int m,
                                    double *norms) {
+  grid_dep_enter();
   const int i = blockIdx.x;
   const size_t bs = (size_t)n * n;
   const int64_t L = (int64_t)N * n;

@@ -28,6 +28,7 @@ namespace btc {
 // D' [N][n][n] and B' [N-1][n][n] from the band A [w+1][Nb][b][b] (FP64). Of A_0 only the lower
 // triangles are read; every other referenced block is read whole.
 __global__ void k_band_group(double *Dg, double *Bg, const double *A, int Nb, int b, int w, int N) {
+  grid_dep_enter();
   const int n = w * b;
   const int64_t nn = (int64_t)n * n, bb = (int64_t)b * b, slab = (int64_t)Nb * bb;
   const int64_t totalD = (int64_t)N * nn, total = totalD + (int64_t)(N - 1) * nn;

@@ -41,6 +41,7 @@ struct BatchVec {
 // y (group layout [node][np]) <- b of each node's instance (type S), zero padding.
 template <typename T, typename S>
 __global__ void k_batch_pack(T *y, const BatchNode *nodes, const InstDesc *inst, const BatchVec *vec, int np) {
+  grid_dep_enter();
   const BatchNode nd = nodes[blockIdx.x];
   const int n = inst[nd.inst].n;
   const S *b = reinterpret_cast<const S *>(vec[nd.inst].b);
@@ -52,6 +53,7 @@ __global__ void k_batch_pack(T *y, const BatchNode *nodes, const InstDesc *inst,
 template <typename T, typename S>
 __global__ void k_batch_unpack(const T *y, const BatchNode *nodes, const InstDesc *inst, const BatchVec *vec, int np,
                                int accumulate) {
+  grid_dep_enter();
   const BatchNode nd = nodes[blockIdx.x];
   const int n = inst[nd.inst].n;
   S *x = reinterpret_cast<S *>(vec[nd.inst].x);
@@ -75,6 +77,7 @@ template <typename T>
 __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const BatchNode *nodes, int n_nodes,
                                                                 const InstDesc *inst, const BatchVec *vec, int np,
                                                                 double *norms, int with_anorm) {
+  grid_dep_enter();
   constexpr int NMAX = 128;  // largest block size of a batch
   __shared__ double xs[3 * NMAX * 2];
   __shared__ double ps[kResParts * NMAX * 2];
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kResThreads) k_batch_residual(T *y, const Batc
 // instance in one launch; the matrix-norm slot norms[3k+2] too when the next
 // residual forms the matrix-norm bound.
 __global__ void k_batch_clear_norms(double *norms, int count, int with_anorm) {
+  grid_dep_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < count) {
     norms[3 * k] = 0.0;
@@ -179,6 +183,7 @@ __global__ void k_batch_clear_norms(double *norms, int count, int with_anorm) {
 // is above tol and fewer than maxit steps were taken.
 __global__ void k_batch_decide(const double *norms, int count, double tol, int maxit, int first, void *rb_,
                                cudaGraphConditionalHandle h) {
+  grid_dep_enter();
   __shared__ double red[32];
   double worst = 0.0;
   for (int k = threadIdx.x; k < count; k += blockDim.x) {

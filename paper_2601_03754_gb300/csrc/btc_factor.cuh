@@ -258,6 +258,7 @@ __device__ __forceinline__ bool factor_node(const FactorItem &it, const FactorAr
 // One launch per dissection level: CTA b eliminates item b of the level.
 template <typename T, typename P, typename S, int NP, int R, bool FIRST, bool RL = false>
 __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT) k_factor_level(FactorArgs args, InstDesc single) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FactorItem it = args.items[blockIdx.x];
   factor_node<T, P, S, NP, R, FIRST, RL>(it, args, single, smem_raw);
@@ -279,6 +280,7 @@ struct FlowFit {  // resident CTAs per SM that shared memory and threads allow
 template <typename T, typename P, typename S, int NP, int R, int MINB>
 __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     k_factor_flow(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   for (;;) {
@@ -305,6 +307,7 @@ __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
 template <typename T, typename P, typename S, int NP, int R, int MINB>
 __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     k_factor_flow_rl(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   (void)nfirst;
@@ -397,6 +400,7 @@ constexpr size_t root_smem_bytes() {
 
 template <typename P, typename S, int NP, int R, bool FIRST, bool RL>
 __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorArgs args, InstDesc single) {
+  grid_dep_enter();
   static_assert(sizeof(P) == 4, "the double-FP32 top-separator kernel serves FP32 pools");
   using C = TileCfg<float, NP, R>;
   using RC = RootCfg<NP>;
@@ -523,6 +527,7 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol(FactorA
 // single-warp panels and tile masks here too.
 template <typename P, typename S, int NP, int R, bool FIRST, bool RL>
 __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol_f64(FactorArgs args, InstDesc single) {
+  grid_dep_enter();
   static_assert(sizeof(P) == 4, "the FP64 top-separator kernel serves FP32 pools");
   using C = TileCfg<float, NP, R>;
   using RC = RootCfg<NP>;
@@ -644,6 +649,7 @@ __global__ void __launch_bounds__(TileCfg<float, NP, R>::NT) k_root_chol_f64(Fac
 template <typename P, typename S, int NP>
 __global__ void k_pack_matrix(P *dpool, P *epool, const S *D, const S *B, int N, int n,
                               const int8_t *transposed) {
+  grid_dep_enter();
   const int v = blockIdx.x;  // 0-based node
   const size_t ubs = (size_t)n * n, bs = (size_t)NP * NP;
   for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) {
@@ -674,6 +680,7 @@ struct PackNode {
 
 template <typename P, typename S, int NP>
 __global__ void k_pack_batch(P *dpool, P *epool, const PackNode *nodes, const InstDesc *inst) {
+  grid_dep_enter();
   const PackNode nd = nodes[blockIdx.x];
   const InstDesc in = inst[nd.inst];
   const int n = in.n;

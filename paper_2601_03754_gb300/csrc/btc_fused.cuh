@@ -24,6 +24,7 @@ template <typename T, typename P, typename S, int NP, int R, int MINB>
 __global__ void __launch_bounds__(TileCfg<T, NP, R>::NT, MINB)
     k_factor_fwd_flow(FactorArgs fa, InstDesc single, SolveArgs sa, const int32_t *code, const int32_t *deps,
                       int nfirst, int count, FlowSync fs) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   const SolveFlowItem *fwd = reinterpret_cast<const SolveFlowItem *>(sa.items);

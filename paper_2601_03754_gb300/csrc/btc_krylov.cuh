@@ -13,6 +13,7 @@ constexpr int kKryThreads = 512;
 // strided partial sums, then a shared-memory tree.
 __global__ void __launch_bounds__(kKryThreads) k_mdot(const double *V, int64_t ldv, const double *w, int64_t L,
                                                       double *out) {
+  grid_dep_enter();
   __shared__ double red[kKryThreads];
   const double *v = V + (int64_t)blockIdx.x * ldv;
   double s = 0.0;
@@ -28,6 +29,7 @@ __global__ void __launch_bounds__(kKryThreads) k_mdot(const double *V, int64_t l
 
 // w += sign * sum_{j < k} h[j] V_j (h on the device).
 __global__ void k_mupdate(double *w, const double *V, int64_t ldv, const double *h, int k, int64_t L, double sign) {
+  grid_dep_enter();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
     double a = w[i];
     for (int j = 0; j < k; ++j) a = fma(sign * h[j], V[(int64_t)j * ldv + i], a);
@@ -37,6 +39,7 @@ __global__ void k_mupdate(double *w, const double *V, int64_t ldv, const double 
 
 // v = s * w, with s = scale, or s = 1 / sqrt(*nrm2) when nrm2 is given (a squared norm on the device).
 __global__ void k_vscale(double *v, const double *w, double scale, const double *nrm2, int64_t L) {
+  grid_dep_enter();
   const double s = nrm2 ? (*nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0) : scale;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = s * w[i];

@@ -279,6 +279,7 @@ __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_
 
 template <typename T, int NP>
 __global__ void __launch_bounds__(kSolveThreads) k_fwd_level(SolveArgs a) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FwdItem it = reinterpret_cast<const FwdItem *>(a.items)[blockIdx.x];
   fwd_node<T, NP>(it.y_self, it.y_l, it.e_l, it.y_r, it.e_r, it.d_self, a, smem_raw);
@@ -362,6 +363,7 @@ __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e
 
 template <typename T, int NP>
 __global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BwdItem it = reinterpret_cast<const BwdItem *>(a.items)[blockIdx.x];
   bwd_node<T, NP>(it.x_self, it.x_dn, it.e_dn, it.x_up, it.e_up, it.d_self, a, smem_raw);
@@ -372,6 +374,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bwd_level(SolveArgs a) {
 // items that produce its inputs.
 template <typename T, int NP>
 __global__ void __launch_bounds__(kSolveThreads) k_solve_flow(SolveArgs a, FlowSync fs) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   const SolveFlowItem *items = reinterpret_cast<const SolveFlowItem *>(a.items);
@@ -522,6 +525,7 @@ template <typename T, int NP>
 __global__ void __launch_bounds__(SmallCfg<T, NP>::MAXT) k_solve_small(SolveArgs a, const int32_t *order,
                                                                      const int32_t *wave_off, int nwaves,
                                                                      int ycount) {
+  grid_dep_enter();
   constexpr int G = SmallCfg<T, NP>::G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SolveFlowItem *sit = reinterpret_cast<SolveFlowItem *>(smem_raw);
@@ -588,6 +592,7 @@ constexpr size_t bwd_smem_bytes(int m) {
 // (type T), zero padding.
 template <typename T, typename S>
 __global__ void k_pack_rhs(T *y, const S *b, int N, int n, int np, int m, int ldb, int col0, int64_t node_base) {
+  grid_dep_enter();
   const int64_t total = (int64_t)N * np * m;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / ((int64_t)np * m);
@@ -601,6 +606,7 @@ __global__ void k_pack_rhs(T *y, const S *b, int N, int n, int np, int m, int ld
 template <typename T, typename S>
 __global__ void k_unpack(S *x, const T *y, int N, int n, int np, int m, int ldx, int col0, int64_t node_base,
                          int accumulate) {
+  grid_dep_enter();
   const int64_t total = (int64_t)N * n * m;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / ((int64_t)n * m);
@@ -656,6 +662,7 @@ template <typename T>
 __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D, const double *B, const double *x,
                                                           const double *b, int N, int n, int np, int m,
                                                           int64_t node_base, double *norms, int with_anorm) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i = blockIdx.x;
   const int nm = n * m;

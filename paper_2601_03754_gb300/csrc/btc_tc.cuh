@@ -448,6 +448,7 @@ constexpr int kTcThreads = TileCfg<float, kTcNP, 8>::NT;
 
 template <typename S, bool FIRST, int OPB>
 __global__ void __launch_bounds__(kTcThreads, 1) k_factor_level_tc(FactorArgs args, InstDesc single) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_mbar[2];
@@ -461,6 +462,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_factor_level_tc(FactorArgs ar
 template <typename S, int OPB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_factor_flow_tc(FactorArgs args, InstDesc single, const int32_t *deps, int nfirst, FlowSync fs) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   __shared__ uint32_t s_tmem;
@@ -488,6 +490,7 @@ template <typename S, int OPB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_factor_fwd_flow_tc(FactorArgs fa, InstDesc single, SolveArgs sa, const int32_t *code, const int32_t *deps,
                          int nfirst, int count, FlowSync fs) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   __shared__ uint32_t s_tmem;

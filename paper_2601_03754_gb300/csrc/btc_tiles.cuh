@@ -216,6 +216,7 @@ __device__ __forceinline__ void tile_trsm(const TileTask &tk, const TileArgs &a,
 // (about 200 KB of shared memory), holding its TMEM for its lifetime.
 template <int OPB>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile_flow(TileArgs a, FlowSync fs) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_slot, s_ok;
   __shared__ uint32_t s_tmem;
