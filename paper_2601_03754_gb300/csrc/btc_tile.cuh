@@ -595,6 +595,88 @@ __device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned
   }
 }
 
+// FP64 blocks of one panel (n_p = 8 or 16) whose rows fit one per lane group
+// of the CTA's warps: the elimination of block_potrf_trsm with the rows spread
+// over the warps instead of one warp. A warp's FP64 instruction holds its SM
+// sub-partition's FP64 pipe for the same time whatever its active lanes, so the
+// single panel warp's rank-1 updates and column substitutions (one instruction
+// per row and step) made that warp's pipe the chain; here the lanes of a group
+// of n_p lanes hold one row (lane = column), the owner of row k forms the pivot
+// and scales its row, stores it, and after a CTA barrier every row below takes
+// its update: one FP64 instruction per warp and step. The solve of Z0, Z1 runs
+// the same way (the lanes of a 2 n_p group hold one row of both blocks). Every
+// element receives the same operations in the same order as block_potrf_trsm
+// (pivot d_k, U(k, j) = S(k, j) rsqrt(d_k), S(t, j) -= U(k, t) U(k, j); then
+// z_t *= 1 / U_tt, z_u -= U(t, u) z_t), so the factors are the same bits.
+template <class C, typename T>
+struct RowsPotrf {
+  static constexpr int NP = C::NP, NW = C::NT / 32, HALF = 32 / C::NP, ZG = HALF / 2;
+  static constexpr bool value = sizeof(T) == 8 && C::NPAN == 1 && (NP == 8 || NP == 16) && NW * HALF >= NP;
+};
+
+template <class C, typename T, class WaitOperands>
+__device__ __forceinline__ void block_potrf_trsm_rows(T *S, T *dinv, T *Z0, T *Z1, unsigned long long *info,
+                                                      int node, WaitOperands &&wait_operands, int col_base) {
+  using RP = RowsPotrf<C, T>;
+  constexpr int NP = RP::NP, LD = C::LD, NW = RP::NW, ZG = RP::ZG;
+  constexpr int ZS = (NP + NW * ZG - 1) / (NW * ZG);  // row slots per lane in the solve
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // ---- Cholesky: lane group hf of warp w holds row hf * NW + w, lane col its column
+  {
+    const int hf = lane / NP, col = lane % NP, t_own = hf * NW + warp;
+    T v = t_own < NP ? S[t_own * LD + col] : T(0);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int ow = k % NW, oh = k / NW;
+      if (warp == ow) {  // warp-uniform: the owner of row k
+        T d = __shfl_sync(0xffffffffu, v, oh * NP + k);
+        if (!(d > T(0))) {
+          if (lane == 0 && info) atomicMin(info, pack_info(node, col_base + k));
+          d = T(1);
+          if (hf == oh && col == k) v = T(1);
+        }
+        const T rs = rsqrt(d);
+        if (hf == oh) {
+          v *= rs;  // row k of U (the pivot becomes sqrt(d))
+          S[k * LD + col] = v;
+        }
+        if (lane == 0) dinv[k] = rs;
+      }
+      __syncthreads();
+      if (t_own > k && t_own < NP) v = fma(-S[k * LD + t_own], S[k * LD + col], v);
+    }
+  }
+  wait_operands();
+  if (!Z0 && !Z1) return;
+  __syncthreads();
+  // ---- Z <- U^{-T} Z: lane group zg of warp w holds rows s * NW * ZG + zg * NW + w of Z0 (lanes
+  // 0 .. NP-1 of the group) and Z1 (the next NP lanes)
+  {
+    const int zg = lane / (2 * NP), zc = lane % (2 * NP), col = zc % NP;
+    T *Z = zc < NP ? Z0 : Z1;
+    T z[ZS];
+#pragma unroll
+    for (int sl = 0; sl < ZS; ++sl) {
+      const int u = sl * NW * ZG + zg * NW + warp;
+      z[sl] = (Z && u < NP) ? Z[u * LD + col] : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      const int ow = t % NW, og = (t / NW) % ZG, os = t / (NW * ZG);
+      if (warp == ow && zg == og && Z) {
+        z[os] *= dinv[t];
+        Z[t * LD + col] = z[os];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int sl = 0; sl < ZS; ++sl) {
+        const int u = sl * NW * ZG + zg * NW + warp;
+        if (Z && u > t && u < NP) z[sl] = fma(-S[t * LD + u], Z[t * LD + col], z[sl]);
+      }
+    }
+  }
+}
+
 // Blocked upper Cholesky S = U^T U fused with Z <- U^{-T} Z for up to two
 // right-hand-side blocks (either may be null), pipelined by panels: while
 // warp 0 factors panel p, the other warps apply panel p-1 to the rows of S
@@ -610,6 +692,11 @@ __device__ __forceinline__ void warp_panel_potrf(T *S, int p0, T *dinv, unsigned
 template <class C, typename T, class WaitOperands>
 __device__ __forceinline__ void block_potrf_trsm(T *S, T *dinv, T *Z0, T *Z1, unsigned long long *info, int node,
                                                  WaitOperands &&wait_operands, int col_base = 0) {
+  if constexpr (RowsPotrf<C, T>::value) {
+    block_potrf_trsm_rows<C>(S, dinv, Z0, Z1, info, node, wait_operands, col_base);
+    __syncthreads();
+    return;
+  }
   constexpr int PB = C::PB, NP = C::NP, R = C::R, TXN = C::TXN, NT = C::NT;
   const int tid = threadIdx.x;
   const bool solve = Z0 || Z1;
