@@ -265,7 +265,8 @@ def cpu_baseline_sample(budget_s=12.0, max_reps=200):
 
 def run_profile(which):
     """The benchmark workload without timing: warm-up pass + one pass, for ncu launch lists. The
-    blocked-256 modes factor N=128, n=256 (TF32 or BF16 tile tasks) twice instead."""
+    blocked-256 modes factor N=128, n=256 (TF32 or BF16 tile tasks) twice instead; the small modes run the
+    small case N=64, n=16 (mixed path: its solves run as the one-CTA small solve; plain FP64)."""
     import torch
     from paper_2601_03754_gb300 import btc, build, gen
     build.build()
@@ -284,12 +285,14 @@ def run_profile(which):
     N, n, m = W["N"], W["n"], W["nrhs"]
     if which == "tf32":  # the tensor-core path on a smaller large-block case (inputs 134 MB > L2)
         N, n = 512, 128
+    if which in ("small", "small_f64"):
+        N, n, m = 64, 16, 1
     D, B = gen.bt_random(N, n, delta=W["delta"], seed=W["seed"])
     b = gen.rhs(N, n, m, seed=W["seed"])
     Dd, Bd, bd = (torch.from_numpy(a).cuda() for a in (D, B, b))
     xd = torch.zeros_like(bd)
     dts = {"mixed": [btc.MIXED_F32], "f64": [btc.F64], "both": [btc.MIXED_F32, btc.F64],
-           "tf32": [btc.MIXED_TF32]}[which]
+           "tf32": [btc.MIXED_TF32], "small": [btc.MIXED_F32], "small_f64": [btc.F64]}[which]
     for dt in dts:
         p = btc.btc_plan(N, n, dt)
         btc.btc_plan_set_graphs(p, False)  # ncu does not profile kernels inside graphs with conditional nodes
@@ -771,7 +774,8 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the N=4096, n in {128, 256} measurement")
     ap.add_argument("--no-c2", action="store_true", help="skip the N=1024 delta/MPC/16-RHS rows")
     ap.add_argument("--phases", action="store_true", help="per-level node phase times of the factor launch")
-    ap.add_argument("--profile", choices=["mixed", "f64", "both", "tf32", "tiles_tf32", "tiles_bf16"], default=None,
+    ap.add_argument("--profile", choices=["mixed", "f64", "both", "tf32", "tiles_tf32", "tiles_bf16", "small", "small_f64"],
+                    default=None,
                     help="run the workload's factor + refined solve twice (no timing) for an ncu capture")
     args = ap.parse_args()
     if args.profile:
