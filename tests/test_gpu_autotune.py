@@ -37,9 +37,9 @@ def test_every_configuration_gives_the_same_result(N, n, dt):
     p = btc.btc_plan(N, n, dt)
     btc.btc_plan_set_autotune(p, False)
     ref_f, ref_x = _run(p, Dd, Bd, b, dt)
-    configs = btc.btc_plan_flow_configs(p)
-    assert configs and all(c >= 1 and m >= 1 for c, m in configs)
-    for cap, most in configs:
+    variants = btc.btc_plan_flow_configs(p)
+    assert variants and all(c >= 1 and m >= 1 for c, m in variants)
+    for cap, most in variants:
         for ctas in sorted({1, most}):
             btc.btc_plan_set_flow_config(p, cap, ctas)
             f, x = _run(p, Dd, Bd, b, dt)
@@ -48,10 +48,10 @@ def test_every_configuration_gives_the_same_result(N, n, dt):
     # right-looking variant (Alg. 6) under every configuration as well: its two atomic updates of a
     # diagonal block within a level land in either order, so results agree to rounding, not bitwise
     btc.btc_plan_set_variant(p, btc.VARIANT_RIGHT_LOOKING)
-    btc.btc_plan_set_flow_config(p, configs[0][0], 0)
+    btc.btc_plan_set_flow_config(p, variants[0][0], 0)
     _, x0 = _run(p, Dd, Bd, b, dt)
     tol = 1e-4 if dt == btc.F32 else (1e-4 if dt == btc.MIXED_F32 else 1e-11)
-    for cap, most in configs[1:]:
+    for cap, most in variants[1:]:
         btc.btc_plan_set_flow_config(p, cap, most)
         _, x = _run(p, Dd, Bd, b, dt)
         assert np.abs(x - x0).max() <= tol * np.abs(x0).max(), cap
