@@ -291,8 +291,14 @@ static int launch(const void *fn, int grid, int block, size_t smem, cudaStream_t
   return BTC_OK;
 }
 
+// Allow `bytes` of dynamic shared memory for fn. The limit is per function and shared by every plan (and
+// every copy of a template kernel a launcher may reach), so it is only ever raised: lowering it for a
+// small plan would make a larger plan's launches fail.
 int set_smem(const void *fn, size_t bytes) {
   if (!fn) return BTC_OK;
+  cudaFuncAttributes fa;
+  BTC_CUDA(cudaFuncGetAttributes(&fa, fn));
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return BTC_OK;
   BTC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return BTC_OK;
 }
@@ -764,8 +770,8 @@ static int gmres_ir_impl(btc_plan_s *p, const double *b, double *x, double tol, 
   auto apply_precond = [&](const double *rhs_b, const double *xv, double *out, int with_anorm) -> int {
     // y = rhs_b - Psi xv (FP64, rounded to the factor precision), y <- M^{-1} y, out = y (FP64)
     int rc;
-    if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, 1), p->stream, p->d_y, (const double *)p->D,
-                       (const double *)p->B, xv, rhs_b, p->N, p->n, p->np, one, base, p->d_norms, with_anorm)) ||
+    if ((rc = k.residual(p->d_y, (const double *)p->D, (const double *)p->B, xv, rhs_b, p->N, p->n, p->np, one, base,
+                         p->d_norms, with_anorm, p->stream)) ||
         (rc = run_solve(p, 1)) ||
         (rc = launch_n(k.unpack, grid_for(L), 256, 0, p->stream, (void *)out, (const void *)p->d_y, p->N, p->n, p->np,
                        one, one, c0, base, assign)))
@@ -952,9 +958,8 @@ static int refined_impl(btc_plan_s *p, const double *b, double *x, int nrhs, dou
       BTC_CUDA(cudaMemsetAsync(p->d_norms, 0, (2 + with_anorm) * sizeof(double), p->stream));
       {
         KernelTimer timer(p, BTC_TIME_RESIDUAL);
-        if ((rc = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream,
-                           p->d_y, (const double *)p->D, (const double *)p->B, (const double *)x, b, p->N, p->n,
-                           p->np, m, base, p->d_norms, with_anorm)))
+        if ((rc = k.residual(p->d_y, (const double *)p->D, (const double *)p->B, (const double *)x, b, p->N, p->n,
+                             p->np, m, base, p->d_norms, with_anorm, p->stream)))
           return rc;
       }
       BTC_CUDA(cudaMemcpyAsync(p->h_rb, p->d_rb, sizeof(Readback), cudaMemcpyDeviceToHost, p->stream));
@@ -1040,9 +1045,8 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
         (r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x,
                       (const void *)p->d_y, p->N, p->n, p->np, m, m, c0, base, assign)))
       return r;
-    if ((r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
-                      (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base,
-                      p->d_norms, one)) ||
+    if ((r = k.residual(p->d_y, (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m,
+                        base, p->d_norms, one, p->stream)) ||
         (r = launch_n((const void *)&k_refine_decide, 1, 1, 0, p->stream, p->d_rb, tol, maxit, one, h)))
       return r;
     // the correction loop as a while node
@@ -1067,9 +1071,8 @@ static int build_refine_graph(btc_plan_s *p, const void *D, const void *B, const
       r = launch_n(k.unpack, grid_for((int64_t)p->N * p->n * m), 256, 0, p->stream, (void *)x, (const void *)p->d_y,
                    p->N, p->n, p->np, m, m, c0, base, accumulate);
     if (!r)
-      r = launch_n(k.resid, p->N, kResThreads, residual_smem_bytes(p->n, m), p->stream, p->d_y,
-                   (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base, p->d_norms,
-                   zero);
+      r = k.residual(p->d_y, (const double *)D, (const double *)B, (const double *)x, b, p->N, p->n, p->np, m, base,
+                     p->d_norms, zero, p->stream);
     if (!r) r = launch_n((const void *)&k_refine_decide, 1, 1, 0, p->stream, p->d_rb, tol, maxit, zero, h);
     cudaGraph_t body_out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(p->gstream2, &body_out);
@@ -1851,15 +1854,10 @@ int btc_residual(int N, int n, int nrhs, const double *D, const double *B, const
   const size_t rsm = residual_smem_bytes(n, nrhs);
   if (rsm > 220 * 1024) return fail(BTC_ERR_UNSUPPORTED, "btc_residual: n * nrhs too large for one block row");
   const void *rk = (const void *)&k_residual<double>;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+  if (e == cudaSuccess && (rc = set_smem(rk, rsm))) e = cudaErrorInvalidValue;
   if (e == cudaSuccess) {
     rc = launch_n((const void *)&k_anorm, N, 64, 0, s, D, B, N, n, d);
-    double *ynull = nullptr;
-    int np = n;
-    int64_t base = 0;
-    int no_bound = 0;
-    if (!rc)
-      rc = launch_n(rk, N, kResThreads, rsm, s, ynull, D, B, x, b, N, n, np, nrhs, base, d, no_bound);
+    if (!rc) rc = launch_residual<double>(nullptr, D, B, x, b, N, n, n, nrhs, 0, d, 0, s);
   }
   double h[3] = {0, 0, 0};
   if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);

@@ -324,11 +324,9 @@ static int arrow_residual(btc_arrow_s *a, const double *b, const double *x, doub
   if ((rc = launch_n((const void *)&k_arrow_ctx, gv, 256, 0, a->stream, a->bp, b, a->C, x + a->L, a->L, a->m)))
     return rc;
   double *yT = r_out ? a->r : nullptr;
-  int64_t base = 0;
-  int one = 1, no_bound = 0;  // the matrix norm is exact and known from the factorization
-  const size_t rsm = residual_smem_bytes(a->n, 1);
-  if ((rc = launch_n((const void *)&k_residual<double>, a->N, kResThreads, rsm, a->stream, yT, a->D, a->B, x,
-                     (const double *)a->bp, a->N, a->n, a->n, one, base, a->norms, no_bound)) ||
+  // no matrix-norm bound: the norm is exact and known from the factorization
+  if ((rc = launch_residual<double>(yT, a->D, a->B, x, (const double *)a->bp, a->N, a->n, a->n, 1, 0, a->norms, 0,
+                                    a->stream)) ||
       (rc = launch_n((const void *)&k_arrow_border_resid, a->m, 256, 0, a->stream, r_out ? a->r + a->L : nullptr,
                      a->norms, b + a->L, a->C, x, a->A, x + a->L, a->L, a->m)))
     return rc;

@@ -65,6 +65,9 @@ struct KernelSet {
   int max_cols = 16;  // right-hand sides per solve launch that fit in shared memory
   size_t (*bwd_smem)(int m) = nullptr;
   const void *pack = nullptr, *unpack = nullptr, *resid = nullptr;
+  // the FP64 residual (k_residual<T>), launched through a typed wrapper: y the work vector (pool type)
+  int (*residual)(void *y, const double *D, const double *B, const double *x, const double *b, int N, int n, int np,
+                  int m, int64_t node_base, double *norms, int with_anorm, cudaStream_t s) = nullptr;
 };
 
 // dtype codes as in btc.h

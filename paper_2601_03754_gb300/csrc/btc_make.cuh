@@ -89,6 +89,7 @@ KernelSet make_set() {
   k.pack = (const void *)&k_pack_rhs<T, S>;
   k.unpack = (const void *)&k_unpack<T, S>;
   k.resid = (const void *)&k_residual<T>;
+  k.residual = &launch_residual<T>;
   return k;
 }
 

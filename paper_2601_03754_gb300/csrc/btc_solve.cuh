@@ -74,46 +74,85 @@ struct TrsvCfg {
 };
 
 // Y <- U^{-T} Y (forward, with the upper factor U) for the m columns of Y
-// (np x m in shared memory), by warps: warp w takes columns w, w + nwarps, ...
-// Row j of U is read (U[j][i], i > j), contiguous across lanes. U: shared
-// memory, or global memory for the blocks of SolveCfg::DIAG_GLOBAL.
-template <typename T, int NP>
-__device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *dinv) {
+// (np x m in shared memory), by warps: warp w takes columns w, w + nwarps, ...,
+// QG of them at a time (their substitution chains interleaved, the same
+// operations per column). Row j of U is read (U[j][i], i > j), contiguous
+// across lanes. U: shared memory, or global memory for the blocks of
+// SolveCfg::DIAG_GLOBAL.
+template <typename T, int NP, int QG>
+__device__ __forceinline__ void warp_trsv_ut_cols(T *Y, int m, const T *Us, const T *dinv) {
   constexpr int LDL = SolveCfg<T, NP>::LDU, CH = TrsvCfg<T, NP>::CH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
-  for (int q = warp; q < m && warp < nw; q += nw) {
+  for (int q0 = warp; q0 < m && warp < nw; q0 += QG * nw) {
+    int qc[QG];
+    bool ok[QG];
+#pragma unroll
+    for (int c = 0; c < QG; ++c) {
+      qc[c] = q0 + c * nw;
+      ok[c] = qc[c] < m;
+    }
 #pragma unroll 1
     for (int base = 0; base < NP; base += CH) {
-      T v = lane < CH ? Y[(base + lane) * m + q] : T(0);
+      T v[QG];
+#pragma unroll
+      for (int c = 0; c < QG; ++c) v[c] = (ok[c] && lane < CH) ? Y[(base + lane) * m + qc[c]] : T(0);
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
-        const T zj = warp_bcast(v, j) * dinv[base + j];
-        if (lane > j && lane < CH) v = fma(-Us[(base + j) * LDL + base + lane], zj, v);
-        if (lane == j) v = zj;
+        T zj[QG];
+#pragma unroll
+        for (int c = 0; c < QG; ++c) zj[c] = warp_bcast(v[c], j) * dinv[base + j];
+        if (lane > j && lane < CH) {
+          const T uj = Us[(base + j) * LDL + base + lane];
+#pragma unroll
+          for (int c = 0; c < QG; ++c) v[c] = fma(-uj, zj[c], v[c]);
+        }
+        if (lane == j)
+#pragma unroll
+          for (int c = 0; c < QG; ++c) v[c] = zj[c];
       }
-      if (lane < CH) Y[(base + lane) * m + q] = v;
+#pragma unroll
+      for (int c = 0; c < QG; ++c)
+        if (ok[c] && lane < CH) Y[(base + lane) * m + qc[c]] = v[c];
       __syncwarp();
-      for (int i = base + CH + lane; i < NP; i += 32) {  // rows below the chunk
-        T acc = Y[i * m + q];
+#pragma unroll
+      for (int c = 0; c < QG; ++c) {
+        if (!ok[c]) continue;
+        const int q = qc[c];
+        for (int i = base + CH + lane; i < NP; i += 32) {  // rows below the chunk
+          T acc = Y[i * m + q];
 #pragma unroll 8
-        for (int j = 0; j < CH; ++j) acc = fma(-Us[(base + j) * LDL + i], Y[(base + j) * m + q], acc);
-        Y[i * m + q] = acc;
+          for (int j = 0; j < CH; ++j) acc = fma(-Us[(base + j) * LDL + i], Y[(base + j) * m + q], acc);
+          Y[i * m + q] = acc;
+        }
       }
       __syncwarp();
     }
   }
 }
 
-// Y <- U^{-1} Y (backward substitution with the upper factor), chunks from the
-// bottom. A lane's row of the chunk's diagonal block is loaded into registers
-// with 16-byte loads (conflict-free at the padded leading dimension), so the
-// substitution chain reads no shared memory.
 template <typename T, int NP>
-__device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *dinv) {
+__device__ __forceinline__ void warp_trsv_ut(T *Y, int m, const T *Us, const T *dinv) {
+  if (m == 1) warp_trsv_ut_cols<T, NP, 1>(Y, m, Us, dinv);
+  else warp_trsv_ut_cols<T, NP, 4>(Y, m, Us, dinv);
+}
+
+// Y <- U^{-1} Y (backward substitution with the upper factor), chunks from the
+// bottom, QG columns of a warp at a time. A lane's row of the chunk's diagonal
+// block is loaded into registers with 16-byte loads (conflict-free at the
+// padded leading dimension), so the substitution chain reads no shared memory.
+template <typename T, int NP, int QG>
+__device__ __forceinline__ void warp_trsv_u_cols(T *Y, int m, const T *Us, const T *dinv) {
   constexpr int LDL = SolveCfg<T, NP>::LDU, CH = TrsvCfg<T, NP>::CH, V = TrsvCfg<T, NP>::V;
   static_assert(CH % V == 0, "chunk rows must hold whole 16-byte loads");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;  // full warps only
-  for (int q = warp; q < m && warp < nw; q += nw) {
+  for (int q0 = warp; q0 < m && warp < nw; q0 += QG * nw) {
+    int qc[QG];
+    bool ok[QG];
+#pragma unroll
+    for (int c = 0; c < QG; ++c) {
+      qc[c] = q0 + c * nw;
+      ok[c] = qc[c] < m;
+    }
 #pragma unroll 1
     for (int base = NP - CH; base >= 0; base -= CH) {
       T u[CH];
@@ -125,29 +164,50 @@ __device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *d
 #pragma unroll
         for (int t = 0; t < V; ++t) u[j + t] = w[t];
       }
-      T v = lane < CH ? Y[(base + lane) * m + q] : T(0);
+      T v[QG];
+#pragma unroll
+      for (int c = 0; c < QG; ++c) v[c] = (ok[c] && lane < CH) ? Y[(base + lane) * m + qc[c]] : T(0);
 #pragma unroll
       for (int j = CH - 1; j >= 0; --j) {
-        const T xj = warp_bcast(v, j) * dinv[base + j];
-        if (lane < j) v = fma(-u[j], xj, v);
-        if (lane == j) v = xj;
+        T xj[QG];
+#pragma unroll
+        for (int c = 0; c < QG; ++c) xj[c] = warp_bcast(v[c], j) * dinv[base + j];
+        if (lane < j)
+#pragma unroll
+          for (int c = 0; c < QG; ++c) v[c] = fma(-u[j], xj[c], v[c]);
+        if (lane == j)
+#pragma unroll
+          for (int c = 0; c < QG; ++c) v[c] = xj[c];
       }
-      if (lane < CH) Y[(base + lane) * m + q] = v;
+#pragma unroll
+      for (int c = 0; c < QG; ++c)
+        if (ok[c] && lane < CH) Y[(base + lane) * m + qc[c]] = v[c];
       __syncwarp();
-      for (int i = lane; i < base; i += 32) {  // rows above the chunk
-        T acc = Y[i * m + q];
 #pragma unroll
-        for (int j = 0; j < CH; j += V) {
-          T w[V];
-          vload<T, V>(Us + i * LDL + base + j, w);
+      for (int c = 0; c < QG; ++c) {
+        if (!ok[c]) continue;
+        const int q = qc[c];
+        for (int i = lane; i < base; i += 32) {  // rows above the chunk
+          T acc = Y[i * m + q];
 #pragma unroll
-          for (int t = 0; t < V; ++t) acc = fma(-w[t], Y[(base + j + t) * m + q], acc);
+          for (int j = 0; j < CH; j += V) {
+            T w[V];
+            vload<T, V>(Us + i * LDL + base + j, w);
+#pragma unroll
+            for (int t = 0; t < V; ++t) acc = fma(-w[t], Y[(base + j + t) * m + q], acc);
+          }
+          Y[i * m + q] = acc;
         }
-        Y[i * m + q] = acc;
       }
       __syncwarp();
     }
   }
+}
+
+template <typename T, int NP>
+__device__ __forceinline__ void warp_trsv_u(T *Y, int m, const T *Us, const T *dinv) {
+  if (m == 1) warp_trsv_u_cols<T, NP, 1>(Y, m, Us, dinv);
+  else warp_trsv_u_cols<T, NP, 4>(Y, m, Us, dinv);
 }
 
 struct SolveArgs {
@@ -654,25 +714,29 @@ __device__ __forceinline__ float abs_lower_f32(double a) {
 // bound of ||Psi||_inf into norms[2] (each |a_ij| truncated to FP32, row sums
 // with round-toward-zero additions, so the stopping test
 // ||r|| <= tol ||Psi|| ||x|| is never met early). Dynamic shared memory:
-// residual_smem_bytes(n, m).
+// residual_smem_bytes(n, m). Grid: residual_grid(N, m) CTAs, each one block row and one group of
+// residual_cols(m) right-hand sides (mg).
 constexpr int kResParts = 4;
 constexpr int kResThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D, const double *B, const double *x,
                                                           const double *b, int N, int n, int np, int m,
-                                                          int64_t node_base, double *norms, int with_anorm) {
+                                                          int64_t node_base, double *norms, int with_anorm, int mg) {
   grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int i = blockIdx.x;
-  const int nm = n * m;
-  double *xs = reinterpret_cast<double *>(smem_raw);  // [3][n*m]: x_{i-1}, x_i, x_{i+1}
-  double *ps = xs + 3 * nm;                            // [kResParts][n*m]
+  // CTA: block row i, columns cb .. cb + mc - 1 of the m right-hand sides (mg per CTA)
+  const int ng = (m + mg - 1) / mg;
+  const int i = blockIdx.x / ng, cb = (blockIdx.x % ng) * mg;
+  const int mc = min(mg, m - cb);
+  const int nm = n * mc;
+  double *xs = reinterpret_cast<double *>(smem_raw);  // [3][n*mc]: x_{i-1}, x_i, x_{i+1}
+  double *ps = xs + 3 * nm;                            // [kResParts][n*mc]
   float *as = reinterpret_cast<float *>(ps + kResParts * nm);  // [kResParts][n] row-sum parts
   const size_t bs = (size_t)n * n;
   for (int q = threadIdx.x; q < 3 * nm; q += blockDim.x) {
     const int which = q / nm, off = q % nm, row = i - 1 + which;
-    xs[q] = (row >= 0 && row < N) ? x[(size_t)row * nm + off] : 0.0;
+    xs[q] = (row >= 0 && row < N) ? x[((size_t)row * n + off / mc) * m + cb + off % mc] : 0.0;
   }
   __syncthreads();
   const double *Di = D + i * bs;
@@ -683,7 +747,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
   const double *x0 = xs, *x1 = xs + nm, *x2 = xs + 2 * nm;
   for (int idx = threadIdx.x; idx < kResParts * nm; idx += blockDim.x) {
     const int part = idx / nm, q = idx % nm;
-    const int r = q / m, col = q % m;
+    const int r = q / mc, cc = q % mc, col = cb + cc;
     const int c0 = part * chunk, c1 = min(n, c0 + chunk);
     const bool lb = with_anorm && col == 0;
     double vd = 0.0, vl = 0.0, vu = 0.0;
@@ -693,9 +757,9 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
       const double ad = __ldg(r >= c ? Di + r * n + c : Di + c * n + r);
       const double al = has_l ? __ldg(Bl + r * n + c) : 0.0;
       const double au = has_u ? __ldg(Br + c * n + r) : 0.0;
-      vd = fma(ad, x1[c * m + col], vd);
-      vl = fma(al, x0[c * m + col], vl);
-      vu = fma(au, x2[c * m + col], vu);
+      vd = fma(ad, x1[c * mc + cc], vd);
+      vl = fma(al, x0[c * mc + cc], vl);
+      vu = fma(au, x2[c * mc + cc], vu);
       if (lb) s = __fadd_rz(__fadd_rz(__fadd_rz(s, abs_lower_f32(ad)), abs_lower_f32(al)), abs_lower_f32(au));
     }
     ps[part * nm + q] = (vd + vl) + vu;
@@ -708,8 +772,8 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
     double ax = 0.0;
 #pragma unroll
     for (int k = 0; k < kResParts; ++k) ax += ps[k * nm + q];
-    const int r = q / m, col = q % m;
-    const double v = b[(size_t)i * nm + q] - ax;
+    const int r = q / mc, col = cb + q % mc;
+    const double v = b[((size_t)i * n + r) * m + col] - ax;
     if (y) y[(node_base + i) * np * m + r * m + col] = convert_in<T, double>(v);
     rmax = nan_max(rmax, fabs(v));
     xmax = nan_max(xmax, fabs(xs[nm + q]));
@@ -721,7 +785,8 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
     }
   }
   if (y) {
-    for (int q = threadIdx.x; q < (np - n) * m; q += blockDim.x) y[(node_base + i) * np * m + n * m + q] = T(0);
+    for (int q = threadIdx.x; q < (np - n) * mc; q += blockDim.x)
+      y[(node_base + i) * np * m + (n + q / mc) * m + cb + q % mc] = T(0);
   }
   for (int o = 16; o > 0; o >>= 1) {
     rmax = nan_max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
@@ -735,8 +800,31 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
   }
 }
 
+// Columns per CTA of k_residual for m right-hand sides: up to 4 in one CTA, else groups of 8 (about two
+// waves of resident CTAs at N=1024, n=64, m=16 instead of 2.25 waves of three per SM).
+inline int residual_cols(int m) { return m <= 4 ? m : 8; }
+inline int residual_grid(int N, int m) { return N * ((m + residual_cols(m) - 1) / residual_cols(m)); }
+
+// Dynamic shared memory of k_residual for m right-hand sides (its column group).
 inline size_t residual_smem_bytes(int n, int m) {
-  return sizeof(double) * (size_t)(3 + kResParts) * n * m + sizeof(float) * (size_t)kResParts * n;
+  const int mc = residual_cols(m) < m ? residual_cols(m) : m;
+  return sizeof(double) * (size_t)(3 + kResParts) * n * mc + sizeof(float) * (size_t)kResParts * n;
+}
+
+// Typed launch of k_residual over N block rows and m right-hand sides (argument types checked at
+// compile time; the dynamic shared memory attribute must allow residual_smem_bytes(n, m)).
+template <typename T>
+static int launch_residual(void *y, const double *D, const double *B, const double *x, const double *b, int N, int n,
+                    int np, int m, int64_t node_base, double *norms, int with_anorm, cudaStream_t s) {
+  if (N <= 0) return BTC_OK;
+  T *yt = static_cast<T *>(y);
+  int mg = residual_cols(m);
+  // the argument list of k_residual, in order and with its parameter types
+  void *args[] = {&yt, &D, &B, &x, &b, &N, &n, &np, &m, &node_base, &norms, &with_anorm, &mg};
+  static_assert(sizeof(args) / sizeof(args[0]) == 13, "one entry per parameter of k_residual");
+  BTC_CUDA(launch_ex((const void *)&k_residual<T>, dim3(residual_grid(N, m)), dim3(kResThreads), args,
+                     residual_smem_bytes(n, m), s));
+  return BTC_OK;
 }
 
 

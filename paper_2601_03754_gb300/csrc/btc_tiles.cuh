@@ -272,6 +272,7 @@ KernelSet make_set_tiled() {
   k.pack = (const void *)&k_pack_rhs<float, double>;
   k.unpack = (const void *)&k_unpack<float, double>;
   k.resid = (const void *)&k_residual<float>;
+  k.residual = &launch_residual<float>;
   return k;
 }
 
