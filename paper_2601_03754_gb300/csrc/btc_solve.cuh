@@ -316,16 +316,30 @@ __device__ __forceinline__ void fwd_node(int64_t y_self, int64_t y_l, int64_t e_
       }
       __syncthreads();
       if (h == 0) ys[q] = acc + sm.part[q];
-    } else {
-      for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-        const int c = q / m, col = q % m;
-        T acc = ys[q];
-#pragma unroll 8
-        for (int r = 0; r < NP; ++r) acc = fma(-Ul[r * LDL + c], yl[r * m + col], acc);
+    } else {  // several outputs per thread, OG of them interleaved (each output's sum in the same order)
+      constexpr int OG = 4;
+      for (int q0 = threadIdx.x; q0 < nm; q0 += OG * blockDim.x) {
+        int cq[OG], colq[OG];
+        T acc[OG];
+#pragma unroll
+        for (int k = 0; k < OG; ++k) {
+          const int q = min(q0 + k * (int)blockDim.x, nm - 1);
+          cq[k] = q / m;
+          colq[k] = q % m;
+          acc[k] = ys[q];
+        }
+#pragma unroll 4
+        for (int r = 0; r < NP; ++r)
+#pragma unroll
+          for (int k = 0; k < OG; ++k) acc[k] = fma(-Ul[r * LDL + cq[k]], yl[r * m + colq[k]], acc[k]);
         if (right)
-#pragma unroll 8
-          for (int r = 0; r < NP; ++r) acc = fma(-Ur[r * LDL + c], yr[r * m + col], acc);
-        ys[q] = acc;
+#pragma unroll 4
+          for (int r = 0; r < NP; ++r)
+#pragma unroll
+            for (int k = 0; k < OG; ++k) acc[k] = fma(-Ur[r * LDL + cq[k]], yr[r * m + colq[k]], acc[k]);
+#pragma unroll
+        for (int k = 0; k < OG; ++k)
+          if (q0 + k * (int)blockDim.x < nm) ys[q0 + k * blockDim.x] = acc[k];
       }
     }
   }
@@ -401,17 +415,31 @@ __device__ __forceinline__ void bwd_node(int64_t x_self, int64_t x_dn, int64_t e
       }
       __syncthreads();
       if (h == 0) ys[q] = acc + sm.part[q];
-    } else {
-      for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-        const int r = q / m, col = q % m;
-        T acc = ys[q];
+    } else {  // several outputs per thread, OG of them interleaved (each output's sum in the same order)
+      constexpr int OG = 4;
+      for (int q0 = threadIdx.x; q0 < nm; q0 += OG * blockDim.x) {
+        int rq[OG], colq[OG];
+        T acc[OG];
+#pragma unroll
+        for (int k = 0; k < OG; ++k) {
+          const int q = min(q0 + k * (int)blockDim.x, nm - 1);
+          rq[k] = q / m;
+          colq[k] = q % m;
+          acc[k] = ys[q];
+        }
         if (dn)
-#pragma unroll 8
-          for (int c = 0; c < NP; ++c) acc = fma(-Ud[r * LDL + c], xd[c * m + col], acc);
+#pragma unroll 4
+          for (int c = 0; c < NP; ++c)
+#pragma unroll
+            for (int k = 0; k < OG; ++k) acc[k] = fma(-Ud[rq[k] * LDL + c], xd[c * m + colq[k]], acc[k]);
         if (up)
-#pragma unroll 8
-          for (int c = 0; c < NP; ++c) acc = fma(-Uu[r * LDL + c], xu[c * m + col], acc);
-        ys[q] = acc;
+#pragma unroll 4
+          for (int c = 0; c < NP; ++c)
+#pragma unroll
+            for (int k = 0; k < OG; ++k) acc[k] = fma(-Uu[rq[k] * LDL + c], xu[c * m + colq[k]], acc[k]);
+#pragma unroll
+        for (int k = 0; k < OG; ++k)
+          if (q0 + k * (int)blockDim.x < nm) ys[q0 + k * blockDim.x] = acc[k];
       }
     }
   }
