@@ -733,7 +733,7 @@ __device__ __forceinline__ float abs_lower_f32(double a) {
 // r = b - Psi x in FP64 for one block row per CTA; writes r (converted to T)
 // into the padded work vector y when y != nullptr, and max|r|, max|x| into
 // norms[0], norms[1]. D: lower triangles read. Each output's 3n-term dot
-// product is split into kResParts contiguous column ranges, each with one
+// product is split into kResParts interleaved column sets, each with one
 // FP64 chain per block (D_i, B_{i-1}, B_i^T terms, interleaved so three
 // multiply-adds are in flight per thread), added in a fixed order
 // (deterministic). Matrix entries are read straight from global memory (each
@@ -771,17 +771,17 @@ __global__ void __launch_bounds__(kResThreads) k_residual(T *y, const double *D,
   const double *Bl = i > 0 ? B + (i - 1) * bs : D;  // a valid address when the block is absent
   const double *Br = i + 1 < N ? B + i * bs : D;
   const bool has_l = i > 0, has_u = i + 1 < N;
-  const int chunk = (n + kResParts - 1) / kResParts;
   const double *x0 = xs, *x1 = xs + nm, *x2 = xs + 2 * nm;
   for (int idx = threadIdx.x; idx < kResParts * nm; idx += blockDim.x) {
-    const int part = idx / nm, q = idx % nm;
+    // part fastest: the kResParts threads of an output are neighbours and part p sums the columns
+    // c = p, p + kResParts, ..., so a row-major read of the warp touches consecutive columns
+    const int part = idx % kResParts, q = idx / kResParts;
     const int r = q / mc, cc = q % mc, col = cb + cc;
-    const int c0 = part * chunk, c1 = min(n, c0 + chunk);
     const bool lb = with_anorm && col == 0;
     double vd = 0.0, vl = 0.0, vu = 0.0;
     float s = 0.0f;
 #pragma unroll 4
-    for (int c = c0; c < c1; ++c) {
+    for (int c = part; c < n; c += kResParts) {
       const double ad = __ldg(r >= c ? Di + r * n + c : Di + c * n + r);
       const double al = has_l ? __ldg(Bl + r * n + c) : 0.0;
       const double au = has_u ? __ldg(Br + c * n + r) : 0.0;
